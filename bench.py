@@ -1,0 +1,301 @@
+"""Benchmark: cost+grad evaluations/s of the D-VQLS global cost at n = 10, L = 64.
+
+Workload (the n = 10 tridiagonal Toeplitz throughput system): a batch of 32
+instances (seeds 0..31; a ~ U(2,4), c ~ U(-1.5,-0.5) with a > 2|c|), each
+decomposed on the GPU and pruned to its top 64 Pauli terms, b = |+>^10,
+depth-4 Ry + CZ-ring ansatz (50 angles).  One step = one cost + parameter-
+shift gradient evaluation of every instance: 32 x 101 shifted states x
+(64^2 + 64) Hadamard-test terms, FP32 state and term arithmetic with FP64
+weighted sums (dvqls_cost_grad_batched).  Inputs are resident in HBM; L2 is
+flushed (a 256 MB write) between timed steps, outside the timed events.
+
+`value`  : instances x steps / device time of the timed steps (CUDA events).
+`e2e`    : the same, through the C-ABI with host buffers (pinned staging,
+           host-to-device inputs and device-to-host results inside the time).
+`roofline`: the term-tile kernel against the FP32 FMA peak.
+`cpu_baseline` / --impl reference: the CPU circuit-level oracle on a bounded
+           sample of shifts of one instance, scaled to whole evaluations.
+
+Multi-GPU: one process per GPU (torchrun); each rank evaluates its own batch
+of 32 instances (weak scaling, no data-path collective); the time is the
+maximum over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_QUBITS, DEPTH, L_TERMS, BATCH = 10, 4, 64, 32
+METRIC = "cost+grad evals/sec at n=10, L=64 (FP32 batched vs FP64 circuit path)"
+UNIT = "evals/s"
+SMS, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def workload_config(n_gpus):
+    return {"workload": "tridiagonal Toeplitz n=10 (N=1024), top-64 Pauli terms, depth-4 Ry+CZ-ring ansatz "
+                        "(P=50, S=101 shifts), batch of 32 instances per GPU",
+            "n": N_QUBITS, "L": L_TERMS, "depth": DEPTH, "angles": 50, "shifts": 101,
+            "instances_per_gpu": BATCH, "terms_per_eval": 101 * (L_TERMS ** 2 + L_TERMS),
+            "l2": "flushed between timed steps (256 MB write)", "parallelism": "dp%d" % n_gpus}
+
+
+def terms_per_step(batch=BATCH):
+    return batch * 101 * (L_TERMS ** 2 + L_TERMS)
+
+
+def flops_per_step(batch=BATCH):
+    """Algorithmic FLOPs of the term reductions: 8 N per term (one complex
+    multiply-accumulate per amplitude)."""
+    return terms_per_step(batch) * 8 * (1 << N_QUBITS)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
+
+
+def make_batch(D, ctx, torch, rank):
+    """Decompose the 32 instances of this rank on the GPU (not timed) and
+    build the device-resident instance array."""
+    from paper_2604_14435_gb300 import workloads as wl
+    dev = torch.device("cuda", torch.cuda.current_device())
+    keep, items, host_items = [], [], []
+    for k in range(BATCH):
+        inst = wl.throughput_instance(rank * BATCH + k, n=N_QUBITS, d=DEPTH, L_max=L_TERMS)
+        coef = torch.zeros(2 * L_TERMS, dtype=torch.float64, device=dev)
+        xm = torch.zeros(L_TERMS, dtype=torch.int32, device=dev)
+        zm = torch.zeros(L_TERMS, dtype=torch.int32, device=dev)
+        bands = torch.tensor(inst["bands"], dtype=torch.float64, device=dev)
+        L, _, _ = D.dvqls_pauli_decompose_banded(ctx, N_QUBITS, inst["offsets"], bands, 0.0, L_TERMS, coef, xm, zm)
+        assert L == L_TERMS
+        alpha = torch.tensor(inst["alpha"], dtype=torch.float64, device=dev)
+        b = torch.tensor(inst["b"].view(np.float64), dtype=torch.float64, device=dev)
+        keep.append((coef, xm, zm, alpha, b))
+        items.append((D.make_ansatz(N_QUBITS, DEPTH), D.make_lcu(L, coef, xm, zm), alpha, b))
+        h = tuple(t.cpu().numpy().copy() for t in (coef, xm, zm, alpha, b))
+        keep.append(h)
+        host_items.append((D.make_ansatz(N_QUBITS, DEPTH), D.make_lcu(L, h[0], h[1], h[2]), h[3], h[4]))
+    return D.make_instances(items), D.make_instances(host_items), keep
+
+
+def cpu_oracle_rate(budget_s=10.0, max_shifts=101):
+    """Circuit-level oracle on shifts of instance 0 until `budget_s` elapses.
+    Returns (evals/s, threads, sample description)."""
+    from oracle import circuit as ocirc
+    from oracle import decompose as odec
+    from oracle import terms as oterms
+    from paper_2604_14435_gb300 import workloads as wl
+    inst = wl.throughput_instance(0, n=N_QUBITS, d=DEPTH, L_max=L_TERMS)
+    dec = odec.decompose_banded(N_QUBITS, inst["offsets"], inst["bands"], 0.0, L_TERMS)
+    shifts = oterms.shifted_angles(inst["alpha"])
+    t0 = time.perf_counter()
+    done, threads = 0, 0
+    while done < max_shifts:
+        _, _, threads = ocirc.circuit_terms(N_QUBITS, DEPTH, shifts[done], inst["b"], dec["x"], dec["z"])
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    per_eval = el / done * 101
+    sample = ("%d of 101 shifted angle vectors of instance 0 (%d Hadamard-test circuits of 11 qubits, "
+              "%.1f s wall), scaled to whole cost+grad evaluations" % (done, done * 2 * 4160, el))
+    return 1.0 / per_eval, threads, sample
+
+
+def run_reference(args):
+    rank, _, ws = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    times = []
+    cores = 0
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        rate, cores, sample = cpu_oracle_rate(budget_s=2.0, max_shifts=101)
+        if i >= args.warmup:
+            times.append(1.0 / rate)
+    value = 1.0 / float(np.mean(times))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args.gpus),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "each step: " + sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    import torch
+    rank, local, ws = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    import __graft_entry__
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if pg:
+        pg.barrier()
+    from paper_2604_14435_gb300 import dvqls as D
+
+    stream = torch.cuda.current_stream()
+    ctx = D.dvqls_create(local, stream.cuda_stream)
+    dev_arr, host_arr, keep = make_batch(D, ctx, torch, rank)
+    P = 50
+    costs = torch.zeros(BATCH, dtype=torch.float64, device="cuda")
+    grads = torch.zeros(BATCH * P, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        D.dvqls_cost_grad_batched(ctx, dev_arr, D.DVQLS_FP32, costs, grads)
+
+    for _ in range(args.warmup):
+        step()
+    D.dvqls_sync(ctx)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    D.dvqls_profile_enable(ctx, 1)
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    D.dvqls_sync(ctx)
+    torch.cuda.synchronize()
+    D.dvqls_profile_enable(ctx, 0)
+    clk = clocks.stop()
+    if pg:
+        pg.barrier()
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    n_terms_launch, ms_terms = D.dvqls_profile_read(ctx, 1)
+    n_prep, ms_prep = D.dvqls_profile_read(ctx, 0)
+    n_comb, ms_comb = D.dvqls_profile_read(ctx, 2)
+    if pg:
+        t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        dev_ms = t.item()
+    value = ws * BATCH * args.steps / (dev_ms / 1000.0)
+
+    # End to end through the C-ABI with host buffers.
+    hcost = np.zeros(BATCH)
+    hgrad = np.zeros(BATCH * P)
+    for _ in range(3):
+        D.dvqls_cost_grad_batched(ctx, host_arr, D.DVQLS_FP32, hcost, hgrad)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        D.dvqls_cost_grad_batched(ctx, host_arr, D.DVQLS_FP32, hcost, hgrad)
+    e2e_s = time.perf_counter() - t0
+    if pg:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = t.item()
+    h2d = BATCH * (L_TERMS * 24 + P * 8 + (1 << N_QUBITS) * 16)
+    d2h = BATCH * (8 + P * 8)
+    gpu_check = float(np.max(np.abs(hcost - costs.cpu().numpy())))
+
+    if rank == 0:
+        avg_terms_ms = ms_terms / max(1, n_terms_launch)
+        achieved = flops_per_step() / (avg_terms_ms / 1000.0) / 1e12
+        peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(ws),
+                "terms_per_s": ws * terms_per_step() * args.steps / (dev_ms / 1000.0),
+                "roofline": {"bound": "alu", "kernel": "k_terms_smem<float>", "achieved": achieved,
+                             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                             "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max SM clock)",
+                             "kernel_ms_avg": avg_terms_ms,
+                             "phase_ms_avg": {"prepare": ms_prep / max(1, n_prep), "terms": avg_terms_ms,
+                                              "combine": ms_comb / max(1, n_comb)}},
+                "e2e": {"value": ws * BATCH * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "max_abs_cost_diff_vs_device_path": gpu_check},
+                "gpu_launches": n_terms_launch + n_prep + n_comb,
+                "clocks": clk}
+        if not args.no_cpu_baseline and ws == 1:
+            rate, cores, sample = cpu_oracle_rate(budget_s=10.0)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        print(json.dumps(line))
+    D.dvqls_destroy(ctx)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * dvqls.h - C-ABI of the GB300 (sm_103a) D-VQLS hot path.
+ *
+ * Two parts of the Distributed Variational Quantum Linear Solver:
+ *   1. the FWHT-based Pauli decomposition of A with tau pruning / top-L
+ *      selection that produces the L weighted Pauli strings (Sec. 2.2,
+ *      Eq. 3, Eq. 5; Algorithm 1, Steps 1-2), and
+ *   2. the ideal state-vector evaluation of every Hadamard-test term of the
+ *      global cost (Eq. 1 with A = sum_l c_l A_l):
+ *          beta_lm  = <psi(alpha)| A_l^dag A_m |psi(alpha)>
+ *          delta_l  = <b| A_l |psi(alpha)>
+ *          C        = 1 - |sum_l c_l delta_l|^2 / sum_lm c_l^* c_m beta_lm
+ *      and of the parameter-shift gradient (2P+1 shifted evaluations),
+ *      i.e. Stages I-III of Sec. 2.3 (Algorithm 1, Steps 4a-4c) collapsed
+ *      into one device pass.
+ *
+ * Conventions used by every entry point:
+ *   - Basis index i = sum_k i_k 2^k; qubit k is bit k.  N = 2^n.
+ *   - Pauli string from two bitmasks: sigma(x,z) = i^popc(x&z) X^x Z^z
+ *     (Y where both bits are set), so sigma|i> = i^popc(x&z) (-1)^popc(z&i)
+ *     |i XOR x>.  It is Hermitian, hence A_l^dag = A_l.
+ *   - Complex numbers are interleaved (re, im) doubles.
+ *   - Ansatz DVQLS_ANSATZ_RY_CZRING (the hardware-efficient ansatz of Sec.
+ *     2.3 / Sec. 3 in its Ry + CZ form): an Ry layer with angles alpha[0..n),
+ *     then `depth` times { CZ ring ; Ry layer alpha[l*n .. l*n+n) }, so
+ *     P = n (depth+1) angles.  Ry(t) = [[cos t/2, -sin t/2], [sin t/2,
+ *     cos t/2]]; the CZ ring is CZ(q,q+1) for q < n-1 plus CZ(n-1,0) when
+ *     n >= 3.
+ *   - Gradient: the parameter-shift rule, exact for both the numerator and
+ *     the denominator of Eq. 1 because every angle enters one
+ *     exp(-i a Y / 2) gate: f' = [f(a + pi/2) - f(a - pi/2)] / 2.
+ *
+ * Memory: every pointer argument may be host memory or device memory of the
+ * context's device (told apart with cudaPointerGetAttributes).  The caller
+ * owns all buffers; the library never frees caller memory and never keeps a
+ * caller pointer after the call returns.  The context owns its workspace,
+ * staging buffers and CUDA graphs.  Work is ordered on the context's stream.
+ * Unless a function says otherwise it returns after its results are in the
+ * caller's buffers.
+ *
+ * Errors: every function returns a dvqls_status.  No exception crosses the
+ * ABI.  dvqls_last_error() gives a one-line description of the last failure
+ * on the context.
+ */
+#ifndef DVQLS_H
+#define DVQLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DVQLS_OK = 0,
+    DVQLS_ERR_INVALID_ARG = 1, /* bad size, mask, pointer or non-finite input */
+    DVQLS_ERR_UNSUPPORTED = 2, /* valid request this build does not serve    */
+    DVQLS_ERR_CUDA = 3,        /* a CUDA runtime call failed                  */
+    DVQLS_ERR_TIMEOUT = 4,     /* a bounded device wait gave up               */
+    DVQLS_ERR_NUMERIC = 5,     /* D <= 0 or a non-finite result               */
+    DVQLS_ERR_ALLOC = 6        /* device or pinned allocation failed          */
+} dvqls_status;
+
+/* Arithmetic of the state build and the term reductions.  The FP32 path
+ * keeps the coefficient-weighted L^2 sum, the cost ratio and the gradient
+ * combine in FP64. */
+typedef enum { DVQLS_FP64 = 0, DVQLS_FP32 = 1 } dvqls_precision;
+
+typedef enum { DVQLS_ANSATZ_RY_CZRING = 0 } dvqls_ansatz_kind;
+
+/* Largest n served with the state resident in shared memory; above it (up to
+ * DVQLS_MAX_QUBITS) states are streamed through HBM. */
+#define DVQLS_MAX_SMEM_QUBITS 12
+#define DVQLS_MAX_QUBITS 20
+/* Largest n for a dense decomposition input (N x N doubles). */
+#define DVQLS_MAX_DENSE_QUBITS 12
+
+typedef struct dvqls_ctx dvqls_ctx;
+
+/* Create a context on CUDA device `device`.  `stream` is the cudaStream_t
+ * every call of this context is ordered on (passed as void* so this header
+ * needs no CUDA include); NULL is the default stream.  The context never
+ * creates or destroys streams.  *out receives the context.
+ * Errors: INVALID_ARG (out == NULL or no such device), CUDA, ALLOC. */
+int dvqls_create(dvqls_ctx** out, int device, void* stream);
+
+/* Synchronise the context's stream and release everything the context owns.
+ * NULL is accepted and ignored. */
+void dvqls_destroy(dvqls_ctx* ctx);
+
+/* One-line description of the last failure on `ctx` ("" if none).  The
+ * string lives until the next call on the context. */
+const char* dvqls_last_error(const dvqls_ctx* ctx);
+
+/* Wait for all work enqueued on the context's stream and return the first
+ * deferred error of an asynchronous call (see dvqls_cost_grad_batched). */
+int dvqls_sync(dvqls_ctx* ctx);
+
+/* Kernel timing for measurement.  While enabled, each kernel launch of the
+ * batched cost pass is bracketed by CUDA events recorded on the context's
+ * stream.  Enabling (enable = 1) resets the counters; disabling keeps them.
+ * dvqls_profile_read synchronises the stream and returns, for `phase`
+ * (0: prepare, 1: term tiles, 2: combine), the number of launches and their
+ * total duration in milliseconds since the last reset.
+ * Errors: INVALID_ARG (phase out of range), CUDA. */
+int dvqls_profile_enable(dvqls_ctx* ctx, int enable);
+int dvqls_profile_read(dvqls_ctx* ctx, int phase, long long* launches, double* ms);
+
+/* ------------------------------------------------------------------------
+ * Pauli decomposition (Sec. 2.2, Eq. 5; Algorithm 1, Steps 1-2).
+ *
+ * c(x,z) = Tr(sigma(x,z)^dag A) / N, computed by grouping the entries of A by
+ * X-mask x = row XOR column, a Walsh-Hadamard transform of each diagonal
+ * d_x(i) = A[i XOR x, i] (radix-2, strides 1, 2, ..., N/2), the phase
+ * (-i)^popc(x&z) and the 1/N scale.  Pruning (one scan): with
+ * key = re*re + im*im (no fused multiply-add) and thr = (tau*tau) * max key
+ * (thr = 0 when tau <= 0), keep the coefficients with key > thr, i.e.
+ * |c| > tau * max|c| -- the largest coefficient normalised to one, as in
+ * Sec. 2.5.1.  Order: key descending, ties by (x << n) | z ascending.  At
+ * most L_max rows are written.
+ *
+ * A:      dense real N x N, row-major, FP64; 1 <= n <= DVQLS_MAX_DENSE_QUBITS.
+ * coef:   L_max complex128 (2 L_max doubles), xmask, zmask: L_max uint32.
+ * L_out:  rows written = min(L_post, L_max).       (host int)
+ * L_pre:  number of nonzero coefficients.          (host int)
+ * L_post: number passing the tau filter (before the L_max cap). (host int)
+ * Errors: INVALID_ARG (n out of range, L_max < 1, tau NaN or negative
+ * infinity, NULL output), ALLOC, CUDA. */
+int dvqls_pauli_decompose(dvqls_ctx* ctx, const double* A, int n, double tau, int L_max,
+                          double* coef, uint32_t* xmask, uint32_t* zmask,
+                          int* L_out, int* L_pre, int* L_post);
+
+/* Same for a banded real matrix, for sizes whose dense form does not fit
+ * (up to n = DVQLS_MAX_QUBITS).  offsets[k] is the diagonal offset (column -
+ * row) of band k; band_values is nbands x N, band_values[k*N + r] =
+ * A[r, r + offsets[k]] (entries that fall outside the matrix are ignored).
+ * Offsets must be distinct with |offset| < N.  offsets is a host array. */
+int dvqls_pauli_decompose_banded(dvqls_ctx* ctx, int n, int nbands, const int* offsets,
+                                 const double* band_values, double tau, int L_max,
+                                 double* coef, uint32_t* xmask, uint32_t* zmask,
+                                 int* L_out, int* L_pre, int* L_post);
+
+/* ------------------------------------------------------------------------
+ * Cost and gradient (Eq. 1, Eq. 3; Sec. 2.3 Stages I-III).
+ */
+typedef struct {
+    int n;     /* system qubits, 1 <= n <= DVQLS_MAX_QUBITS               */
+    int depth; /* ansatz layers d >= 0; P = n (d + 1) angles              */
+    int kind;  /* dvqls_ansatz_kind                                       */
+} dvqls_ansatz;
+
+typedef struct {
+    int L;                 /* number of terms, >= 1                       */
+    const double* coef;    /* L complex128 c_l                            */
+    const uint32_t* xmask; /* L X-masks, each < 2^n                       */
+    const uint32_t* zmask; /* L Z-masks, each < 2^n                       */
+} dvqls_lcu;
+
+/* Cost C(alpha) of Eq. 1 for one instance.
+ * alpha: P doubles.  b: N complex128 right-hand side; the library uses
+ * b / ||b|| (||b|| = 0 is an INVALID_ARG).
+ * Outputs (any may be NULL except cost): cost (1 double), beta (L x L
+ * complex128, row l, column m), delta (L complex128), both at alpha.
+ * Errors: INVALID_ARG, UNSUPPORTED, NUMERIC (D <= 0 or non-finite), ALLOC,
+ * CUDA. */
+int dvqls_cost(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alpha,
+               const dvqls_lcu* lcu, const double* b, int precision,
+               double* cost, double* beta, double* delta);
+
+/* Cost and parameter-shift gradient for one instance: the 2P+1 angle
+ * vectors alpha, alpha + (pi/2) e_k, alpha - (pi/2) e_k each take all
+ * L^2 + L terms; then C = 1 - N0/D0 and
+ * dC/dalpha_k = -(N'_k D0 - N0 D'_k) / D0^2 with N'_k, D'_k half the
+ * difference of the shifted values.  grad: P doubles.  Other arguments as
+ * dvqls_cost. */
+int dvqls_cost_grad(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alpha,
+                    const dvqls_lcu* lcu, const double* b, int precision,
+                    double* cost, double* grad, double* beta, double* delta);
+
+/* One problem of a batch. */
+typedef struct {
+    dvqls_ansatz ansatz;
+    dvqls_lcu lcu;
+    const double* alpha; /* P doubles      */
+    const double* b;     /* N complex128    */
+} dvqls_instance;
+
+/* Cost and gradient of `count` independent instances (mixed n, depth, L)
+ * in one device pass: all S_i (L_i^2 + L_i) terms of every instance are
+ * work items of one persistent launch, ordered longest-first.
+ * costs: count doubles; grads: sum_i P_i doubles, instance i at offset
+ * sum_{j<i} P_j.  Either may be NULL.
+ * When costs and grads are both device memory (or NULL) and every input is
+ * device memory, the call only enqueues work and returns; numeric errors are
+ * then reported by the next dvqls_sync().  Otherwise it returns after the
+ * results are in place.  `count` instances of the same shapes and pointers
+ * as the previous call replay a captured CUDA graph. */
+int dvqls_cost_grad_batched(dvqls_ctx* ctx, int count, const dvqls_instance* inst,
+                            int precision, double* costs, double* grads);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DVQLS_H */

@@ -58,18 +58,23 @@ def banded_xmask_diagonals(n, offsets, band_values):
     band_values[k][r] = A[r, r + offsets[k]] (entries outside the matrix are
     ignored).  Used where the dense matrix would not fit (n = 20)."""
     N = 1 << n
-    entries = {}
-    for off, vals in zip(offsets, band_values):
-        for r in range(N):
-            c = r + int(off)
-            if 0 <= c < N and vals[r] != 0.0:
-                entries[(r, c)] = float(vals[r])
-    by_mask = {}
-    for (r, c), v in entries.items():
-        x = r ^ c
-        by_mask.setdefault(x, np.zeros(N))[c] = v  # d_x(i) = A[i ^ x, i], column i = c
-    masks = np.array(sorted(by_mask), dtype=np.uint32)
-    d = np.stack([by_mask[int(x)] for x in masks]) if len(masks) else np.zeros((0, N))
+    rows, cols, vals = [], [], []
+    for off, v in zip(offsets, band_values):
+        r = np.arange(N)
+        c = r + int(off)
+        ok = (c >= 0) & (c < N)
+        v = np.asarray(v, dtype=np.float64)
+        ok &= v != 0.0
+        rows.append(r[ok])
+        cols.append(c[ok])
+        vals.append(v[ok])
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    v = np.concatenate(vals)
+    x = r ^ c
+    masks = np.unique(x).astype(np.uint32)
+    d = np.zeros((masks.size, N))
+    d[np.searchsorted(masks, x), c] = v  # d_x(i) = A[i ^ x, i]: column i = c
     return masks, d
 
 

@@ -1,0 +1,799 @@
+// Batched Hadamard-test term evaluation: cost and parameter-shift gradient
+// of the VQLS global cost (Eq. 1 with A = sum_l c_l A_l, Eq. 3), i.e. the
+// work of Stages I-III of Sec. 2.3 done as one persistent device pass.
+//
+// Work items.  For instance i with P angles there are S = 2P+1 shifted angle
+// vectors (s = 0: alpha; s = 2k+1: alpha + pi/2 e_k; s = 2k+2: alpha - pi/2
+// e_k).  With T = ceil(L/64) term tiles, item (s, tl, tm, ks) is one CTA's
+// share: the 64 x 64 block (tl, tm) of
+//     G~_lm = sum_j conj(phi_l[j]) phi_m[j],  phi_l[j] = (-1)^popc(z_l & (j^x_l)) psi_s[j ^ x_l]
+// over the amplitude range ks of K-split `ks`, where psi_s = V(alpha_s)|0>.
+// This is beta_lm = <psi|A_l^dag A_m|psi> up to the exact phase
+// conj(i^popc(x_l&z_l)) i^popc(x_m&z_m) (the masked permute-and-sign
+// reduction).  Diagonal tiles also reduce delta~_l = sum_j conj(b_j) phi_l[j].
+//
+// Each CTA builds psi_s in shared memory (n <= 12), then streams chunks of
+// 32 amplitudes: it materialises phi_l / phi_m for the chunk in shared memory
+// and every thread accumulates a 4 x 4 block of complex products in
+// registers (4 FMA per complex product).  The tile's contribution to
+// D_s = sum_lm conj(c_l) c_m beta_lm and T_s = sum_l c_l delta_l is formed in
+// FP64 from the FP32 (or FP64) tile and written to a per-item slot; the
+// combine kernel adds the slots in a fixed order, so results do not depend
+// on scheduling.  C = 1 - N_0/D_0 with N_s = |T_s|^2/||b||^2 and
+// dC/dalpha_k = -(N'_k D_0 - N_0 D'_k)/D_0^2 (parameter-shift rule).
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace dvqls {
+
+constexpr int TT = 64;    // term tile edge (l and m)
+constexpr int NT = 256;   // threads per CTA
+constexpr int JC = 32;    // amplitudes per chunk
+constexpr int MAX_ANGLES = 1024;
+
+struct Inst {
+    int n, d, L, P, S, T, ks;
+    int items;
+    long long item_base;
+    const double2* coef;
+    const uint32_t* xm;
+    const uint32_t* zm;
+    const double* alpha;
+    const double2* b;
+    double2* ctil;   // L: c_l i^popc(x_l & z_l)
+    double2* w;      // L*L: conj(ctil_l) ctil_m
+    double2* cs;     // 3P: (cos, sin) of half angles: base, +pi/2, -pi/2
+    double* bn2;     // ||b||^2
+    double2* Dpart;  // S*T*T*ks
+    double2* Tpart;  // S*T*ks
+    void* Gpart;     // ks*L*L (shift 0 only; null when beta is not requested)
+    void* dpart;     // ks*L   (shift 0 only; null when delta is not requested)
+    double* NsDs;    // 3S: N_s, Re D_s, Im D_s
+    double* cost;
+    double* grad;    // P or null
+    double2* beta;   // L*L or null
+    double2* delta;  // L or null
+};
+
+struct GraphCacheEntry {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<char> key;  // byte image of the launch plan it was captured for
+};
+
+void release_graph_cache(dvqls_ctx* ctx) {
+    if (ctx->graph) {
+        if (ctx->graph->exec) cudaGraphExecDestroy(ctx->graph->exec);
+        delete ctx->graph;
+        ctx->graph = nullptr;
+    }
+}
+
+template <typename R>
+struct V2;
+template <>
+struct V2<float> {
+    using t = float2;
+};
+template <>
+struct V2<double> {
+    using t = double2;
+};
+
+__device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+
+// ---------------------------------------------------------------- prepare
+__global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, int* status) {
+    const Inst I = insts[blockIdx.x];
+    const int t = threadIdx.x;
+    const long long N = 1LL << I.n;
+    __shared__ double red[NT / 32];
+    double acc = 0.0;
+    for (long long j = t; j < N; j += NT) {
+        const double2 v = I.b[j];
+        acc += v.x * v.x + v.y * v.y;
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((t & 31) == 0) red[t >> 5] = acc;
+    for (int l = t; l < I.L; l += NT) {
+        const uint32_t x = I.xm[l], z = I.zm[l];
+        if (x >= N || z >= N) set_status(status, DEV_BAD_MASK);
+        const double2 c = I.coef[l];
+        if (!isfinite(c.x) || !isfinite(c.y)) set_status(status, DEV_NONFINITE_INPUT);
+        double2 r;
+        switch (__popc(x & z) & 3) {
+            case 0: r = c; break;
+            case 1: r = make_double2(-c.y, c.x); break;
+            case 2: r = make_double2(-c.x, -c.y); break;
+            default: r = make_double2(c.y, -c.x); break;
+        }
+        I.ctil[l] = r;
+    }
+    for (int a = t; a < I.P; a += NT) {
+        const double al = I.alpha[a];
+        if (!isfinite(al)) set_status(status, DEV_NONFINITE_INPUT);
+        double s0, c0, s1, c1, s2, c2;
+        sincos(0.5 * al, &s0, &c0);
+        sincos(0.5 * (al + 0.5 * M_PI), &s1, &c1);
+        sincos(0.5 * (al - 0.5 * M_PI), &s2, &c2);
+        I.cs[a] = make_double2(c0, s0);
+        I.cs[I.P + a] = make_double2(c1, s1);
+        I.cs[2 * I.P + a] = make_double2(c2, s2);
+    }
+    __syncthreads();
+    if (t == 0) {
+        double s = 0.0;
+        for (int k = 0; k < NT / 32; ++k) s += red[k];
+        *I.bn2 = s;
+        if (!(s > 0.0) || !isfinite(s)) set_status(status, DEV_BAD_NORM);
+    }
+    const long long LL = (long long)I.L * I.L;
+    for (long long e = t; e < LL; e += NT) {
+        const double2 a = I.ctil[e / I.L], b = I.ctil[e % I.L];
+        I.w[e] = make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+    }
+}
+
+// ------------------------------------------------------------ term tiles
+template <typename R2>
+__device__ __forceinline__ R2 neg2(R2 v) {
+    v.x = -v.x;
+    v.y = -v.y;
+    return v;
+}
+
+__device__ __forceinline__ int czring_parity(int i, int n) {
+    int p = __popc(i & (i >> 1) & ((1 << (n - 1)) - 1));
+    if (n >= 3) p += (i >> (n - 1)) & i & 1;
+    return p & 1;
+}
+
+// psi = V(alpha_s)|0> in shared memory (all threads; ends with a barrier).
+template <typename R>
+__device__ void build_state(typename V2<R>::t* psi, typename V2<R>::t* scs, const Inst& I, int s) {
+    using R2 = typename V2<R>::t;
+    const int n = I.n, N = 1 << n, P = I.P, t = threadIdx.x;
+    int k = -1, which = 0;
+    if (s > 0) {
+        k = (s - 1) >> 1;
+        which = ((s - 1) & 1) ? 2 : 1;
+    }
+    for (int a = t; a < P; a += NT) {
+        const double2 v = I.cs[(a == k ? which : 0) * P + a];
+        R2 r;
+        r.x = (R)v.x;
+        r.y = (R)v.y;
+        scs[a] = r;
+    }
+    __syncthreads();
+    for (int i = t; i < N; i += NT) {  // initial Ry layer on |0>: a product state
+        R v = (R)1;
+        for (int q = 0; q < n; ++q) v *= ((i >> q) & 1) ? scs[q].y : scs[q].x;
+        R2 r;
+        r.x = v;
+        r.y = (R)0;
+        psi[i] = r;
+    }
+    __syncthreads();
+    for (int layer = 1; layer <= I.d; ++layer) {
+        for (int q = 0; q < n; ++q) {
+            const R c = scs[layer * n + q].x, sn = scs[layer * n + q].y;
+            for (int p = t; p < N / 2; p += NT) {
+                const int i0 = ((p >> q) << (q + 1)) | (p & ((1 << q) - 1)), i1 = i0 | (1 << q);
+                R2 a = psi[i0], b = psi[i1];
+                if (q == 0) {  // the CZ ring (diagonal) precedes the layer's rotations
+                    if (czring_parity(i0, n)) a = neg2(a);
+                    if (czring_parity(i1, n)) b = neg2(b);
+                }
+                R2 u, v;
+                u.x = c * a.x - sn * b.x;
+                u.y = c * a.y - sn * b.y;
+                v.x = sn * a.x + c * b.x;
+                v.y = sn * a.y + c * b.y;
+                psi[i0] = u;
+                psi[i1] = v;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void load4(const typename V2<R>::t* p, typename V2<R>::t (&v)[4]);
+template <>
+__device__ __forceinline__ void load4<float>(const float2* p, float2 (&v)[4]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0];
+    const float4 b = reinterpret_cast<const float4*>(p)[1];
+    v[0] = make_float2(a.x, a.y);
+    v[1] = make_float2(a.z, a.w);
+    v[2] = make_float2(b.x, b.y);
+    v[3] = make_float2(b.z, b.w);
+}
+template <>
+__device__ __forceinline__ void load4<double>(const double2* p, double2 (&v)[4]) {
+    v[0] = p[0];
+    v[1] = p[1];
+    v[2] = p[2];
+    v[3] = p[3];
+}
+
+__device__ __forceinline__ double2 block_sum2(double2 v, double2* red) {
+    for (int o = 16; o; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double2 s = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NT / 32; ++k) {
+            s.x += red[k].x;
+            s.y += red[k].y;
+        }
+    return s;  // valid in thread 0
+}
+
+template <typename R>
+__device__ void process_item(const Inst& I, int local, unsigned char* smem, uint32_t* smask, double2* red) {
+    using R2 = typename V2<R>::t;
+    const int n = I.n, N = 1 << n, L = I.L, T = I.T, ks = I.ks, t = threadIdx.x;
+    const int ksi = local % ks;
+    const int rest = local / ks;
+    const int tile = rest % (T * T), s = rest / (T * T);
+    const int tl = tile / T, tm = tile % T;
+    const bool diag = tl == tm;
+    const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
+
+    R2* psi = reinterpret_cast<R2*>(smem);
+    R2* Phl = psi + N;
+    R2* Phm = Phl + JC * TT;
+    R2* bch = Phm + JC * TT;
+    R2* scs = bch + JC;  // P entries (only used during the state build)
+    uint32_t* sxl = smask;
+    uint32_t* szl = smask + TT;
+    uint32_t* sxm = smask + 2 * TT;
+    uint32_t* szm = smask + 3 * TT;
+    if (t < TT) {
+        const int l = tl * TT + t;
+        sxl[t] = l < L ? I.xm[l] : 0u;
+        szl[t] = l < L ? I.zm[l] : 0u;
+        const int m = tm * TT + t;
+        sxm[t] = m < L ? I.xm[m] : 0u;
+        szm[t] = m < L ? I.zm[m] : 0u;
+    }
+    build_state<R>(psi, scs, I, s);
+
+    const int lane = t & 31, warp = t >> 5;
+    const int lb = (warp >> 1) * 4 + (lane >> 3);
+    const int mb = (warp & 1) * 8 + (lane & 7);
+    R are[4][4], aim[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) are[a][b] = aim[a][b] = (R)0;
+    R2 dacc;
+    dacc.x = dacc.y = (R)0;
+    const int lcount = min(TT, L - tl * TT), mcount = min(TT, L - tm * TT);
+
+    for (int j0 = kbeg; j0 < kend; j0 += JC) {
+        for (int e = t; e < JC * TT; e += NT) {
+            const int jj = e / TT, l = e % TT, j = j0 + jj;
+            R2 v;
+            v.x = v.y = (R)0;
+            if (j < kend && l < lcount) {
+                const int src = (j ^ int(sxl[l])) & (N - 1);  // masks >= 2^n are reported, never followed
+                v = psi[src];
+                if (__popc(szl[l] & uint32_t(src)) & 1) v = neg2(v);
+            }
+            Phl[e] = v;
+            if (!diag) {
+                R2 u;
+                u.x = u.y = (R)0;
+                if (j < kend && l < mcount) {
+                    const int src = (j ^ int(sxm[l])) & (N - 1);
+                    u = psi[src];
+                    if (__popc(szm[l] & uint32_t(src)) & 1) u = neg2(u);
+                }
+                Phm[e] = u;
+            }
+        }
+        if (diag && t < JC) {
+            R2 v;
+            v.x = v.y = (R)0;
+            if (j0 + t < kend) {
+                const double2 bb = I.b[j0 + t];
+                v.x = (R)bb.x;
+                v.y = (R)bb.y;
+            }
+            bch[t] = v;
+        }
+        __syncthreads();
+        const R2* Pm = diag ? Phl : Phm;
+        R cre[4][4], cim[4][4];  // chunk accumulators (two-level summation)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) cre[a][b] = cim[a][b] = (R)0;
+#pragma unroll 4
+        for (int jj = 0; jj < JC; ++jj) {
+            R2 lv[4], mv[4];
+            load4<R>(Phl + jj * TT + lb * 4, lv);
+            load4<R>(Pm + jj * TT + mb * 4, mv);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    cre[a][b] = fma(lv[a].x, mv[b].x, cre[a][b]);
+                    cre[a][b] = fma(lv[a].y, mv[b].y, cre[a][b]);
+                    cim[a][b] = fma(lv[a].x, mv[b].y, cim[a][b]);
+                    cim[a][b] = fma(-lv[a].y, mv[b].x, cim[a][b]);
+                }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                are[a][b] += cre[a][b];
+                aim[a][b] += cim[a][b];
+            }
+        if (diag) {  // delta~_l partial: thread t owns l = t % 64, chunk rows (t / 64) * 8 ..
+            const int l = t % TT, g = t / TT;
+#pragma unroll
+            for (int jj = g * (JC / 4); jj < (g + 1) * (JC / 4); ++jj) {
+                const R2 v = Phl[jj * TT + l], bb = bch[jj];
+                dacc.x = fma(bb.x, v.x, fma(bb.y, v.y, dacc.x));
+                dacc.y = fma(bb.x, v.y, fma(-bb.y, v.x, dacc.y));
+            }
+        }
+        __syncthreads();
+    }
+
+    // FP64 weighting of the tile: contribution to D_s.
+    double2 dsum = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int l = tl * TT + lb * 4 + a, m = tm * TT + mb * 4 + b;
+            if (l < L && m < L) {
+                const double2 w = I.w[(long long)l * L + m];
+                const double gr = (double)are[a][b], gi = (double)aim[a][b];
+                dsum.x += w.x * gr - w.y * gi;
+                dsum.y += w.x * gi + w.y * gr;
+            }
+        }
+    const long long slot = ((long long)(s * T + tl) * T + tm) * ks + ksi;
+    const double2 dtot = block_sum2(dsum, red);
+    if (t == 0) I.Dpart[slot] = dtot;
+    if (s == 0 && I.Gpart) {
+        R2* G = reinterpret_cast<R2*>(I.Gpart) + (long long)ksi * L * L;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int l = tl * TT + lb * 4 + a, m = tm * TT + mb * 4 + b;
+                if (l < L && m < L) {
+                    R2 v;
+                    v.x = are[a][b];
+                    v.y = aim[a][b];
+                    G[(long long)l * L + m] = v;
+                }
+            }
+    }
+    if (diag) {
+        // Reduce the four row-group partials of each l, then weight by ctil in FP64.
+        R2* dred = Phl;  // chunk buffer is free now
+        dred[t] = dacc;
+        __syncthreads();
+        double2 tsum = make_double2(0.0, 0.0);
+        if (t < TT) {
+            const int l = tl * TT + t;
+            R2 v = dred[t];
+#pragma unroll
+            for (int g = 1; g < 4; ++g) {
+                v.x += dred[g * TT + t].x;
+                v.y += dred[g * TT + t].y;
+            }
+            if (l < L) {
+                const double2 c = I.ctil[l];
+                const double vr = (double)v.x, vi = (double)v.y;
+                tsum = make_double2(c.x * vr - c.y * vi, c.x * vi + c.y * vr);
+                if (s == 0 && I.dpart) reinterpret_cast<R2*>(I.dpart)[(long long)ksi * L + l] = v;
+            }
+        }
+        const double2 ttot = block_sum2(tsum, red);
+        if (t == 0) I.Tpart[((long long)s * T + tl) * ks + ksi] = ttot;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int find_instance(const Inst* insts, int count, long long g) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (insts[mid].item_base <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT) k_terms_smem(const Inst* __restrict__ insts, int count, long long total,
+                                                  unsigned long long* queue) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t smask[4 * TT];
+    __shared__ double2 red[NT / 32];
+    __shared__ long long s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, 1ull);
+        __syncthreads();
+        const long long g = s_item;
+        __syncthreads();
+        if (g >= total) break;
+        const int idx = find_instance(insts, count, g);
+        const Inst& I = insts[idx];
+        process_item<R>(I, int(g - I.item_base), smem, smask, red);
+    }
+}
+
+// ---------------------------------------------------------------- combine
+template <typename R>
+__global__ void __launch_bounds__(NT) k_combine(const Inst* __restrict__ insts, int* status) {
+    using R2 = typename V2<R>::t;
+    const Inst I = insts[blockIdx.x];
+    const int t = threadIdx.x, T = I.T, ks = I.ks, L = I.L;
+    const double bn2 = *I.bn2;
+    for (int s = t; s < I.S; s += NT) {
+        double2 D = make_double2(0.0, 0.0), Tv = make_double2(0.0, 0.0);
+        const double2* dp = I.Dpart + (long long)s * T * T * ks;
+        for (int e = 0; e < T * T * ks; ++e) {
+            D.x += dp[e].x;
+            D.y += dp[e].y;
+        }
+        const double2* tp = I.Tpart + (long long)s * T * ks;
+        for (int e = 0; e < T * ks; ++e) {
+            Tv.x += tp[e].x;
+            Tv.y += tp[e].y;
+        }
+        I.NsDs[3 * s] = (Tv.x * Tv.x + Tv.y * Tv.y) / bn2;
+        I.NsDs[3 * s + 1] = D.x;
+        I.NsDs[3 * s + 2] = D.y;
+    }
+    __syncthreads();
+    const double N0 = I.NsDs[0], D0 = I.NsDs[1];
+    if (t == 0) {
+        if (!(D0 > 0.0) || !isfinite(D0) || !isfinite(N0)) set_status(status, DEV_BAD_DENOMINATOR);
+        *I.cost = 1.0 - N0 / D0;
+    }
+    if (I.grad && I.S > 1)
+        for (int k = t; k < I.P; k += NT) {
+            const double dN = 0.5 * (I.NsDs[3 * (2 * k + 1)] - I.NsDs[3 * (2 * k + 2)]);
+            const double dD = 0.5 * (I.NsDs[3 * (2 * k + 1) + 1] - I.NsDs[3 * (2 * k + 2) + 1]);
+            I.grad[k] = -(dN * D0 - N0 * dD) / (D0 * D0);
+        }
+    if (I.beta) {
+        const R2* G = reinterpret_cast<const R2*>(I.Gpart);
+        const long long LL = (long long)L * L;
+        for (long long e = t; e < LL; e += NT) {
+            double gr = 0.0, gi = 0.0;
+            for (int k = 0; k < ks; ++k) {
+                gr += (double)G[k * LL + e].x;
+                gi += (double)G[k * LL + e].y;
+            }
+            const int l = int(e / L), m = int(e % L);
+            const int r = ((__popc(I.xm[m] & I.zm[m]) - __popc(I.xm[l] & I.zm[l])) % 4 + 4) % 4;
+            double2 v;
+            if (r == 0) v = make_double2(gr, gi);
+            else if (r == 1) v = make_double2(-gi, gr);
+            else if (r == 2) v = make_double2(-gr, -gi);
+            else v = make_double2(gi, -gr);
+            I.beta[e] = v;
+        }
+    }
+    if (I.delta) {
+        const R2* dpp = reinterpret_cast<const R2*>(I.dpart);
+        const double inv = 1.0 / sqrt(bn2);
+        for (int l = t; l < L; l += NT) {
+            double vr = 0.0, vi = 0.0;
+            for (int k = 0; k < ks; ++k) {
+                vr += (double)dpp[(long long)k * L + l].x;
+                vi += (double)dpp[(long long)k * L + l].y;
+            }
+            double2 v;
+            switch (__popc(I.xm[l] & I.zm[l]) & 3) {
+                case 0: v = make_double2(vr, vi); break;
+                case 1: v = make_double2(-vi, vr); break;
+                case 2: v = make_double2(-vr, -vi); break;
+                default: v = make_double2(vi, -vr); break;
+            }
+            I.delta[l] = make_double2(v.x * inv, v.y * inv);
+        }
+    }
+}
+
+// ------------------------------------------------------------------- host
+struct HostInst {
+    int n, d, L, P, S, T, ks;
+    long long N;
+    int order;  // position in the caller's array
+};
+
+template <typename R>
+size_t smem_bytes(int nmax, int Pmax) {
+    using R2 = typename V2<R>::t;
+    return sizeof(R2) * (size_t(1) << nmax) + sizeof(R2) * (2 * JC * TT + JC) + sizeof(R2) * Pmax;
+}
+
+int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precision, bool want_grad,
+              double* costs, double* grads, double* beta_out, double* delta_out) {
+    if (!ctx) return DVQLS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (count < 1 || !inst) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "count must be >= 1");
+    if (precision != DVQLS_FP32 && precision != DVQLS_FP64)
+        return set_error(ctx, DVQLS_ERR_INVALID_ARG, "unknown precision %d", precision);
+    std::vector<HostInst> hi(count);
+    int nmax = 1, Pmax = 1;
+    for (int i = 0; i < count; ++i) {
+        const dvqls_instance& q = inst[i];
+        const int n = q.ansatz.n, d = q.ansatz.depth;
+        if (n < 1 || n > DVQLS_MAX_QUBITS) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "instance %d: n = %d", i, n);
+        if (n > DVQLS_MAX_SMEM_QUBITS)
+            return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "instance %d: n = %d above %d", i, n, DVQLS_MAX_SMEM_QUBITS);
+        if (d < 0) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "instance %d: depth < 0", i);
+        if (q.ansatz.kind != DVQLS_ANSATZ_RY_CZRING)
+            return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "instance %d: ansatz kind %d", i, q.ansatz.kind);
+        const int L = q.lcu.L;
+        if (L < 1 || !q.lcu.coef || !q.lcu.xmask || !q.lcu.zmask || !q.alpha || !q.b)
+            return set_error(ctx, DVQLS_ERR_INVALID_ARG, "instance %d: empty LCU or NULL input", i);
+        const long long P = (long long)n * (d + 1);
+        if (P > MAX_ANGLES) return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "instance %d: %lld angles", i, P);
+        HostInst& h = hi[i];
+        h.n = n;
+        h.d = d;
+        h.L = L;
+        h.P = int(P);
+        h.S = want_grad ? 2 * h.P + 1 : 1;
+        h.T = ceil_div(L, TT);
+        h.N = 1LL << n;
+        h.order = i;
+        nmax = std::max(nmax, n);
+        Pmax = std::max(Pmax, h.P);
+    }
+    cudaSetDevice(ctx->device);
+    const bool fp32 = precision == DVQLS_FP32;
+    const size_t smem = fp32 ? smem_bytes<float>(nmax, Pmax) : smem_bytes<double>(nmax, Pmax);
+    const size_t r2 = fp32 ? 8 : 16;
+    auto kfun = fp32 ? (const void*)k_terms_smem<float> : (const void*)k_terms_smem<double>;
+    DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    int bps = 0;
+    DVQLS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfun, NT, smem));
+    if (bps < 1) return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "term kernel does not fit (%zu B shared)", smem);
+    const long long slots = (long long)ctx->num_sms * bps;
+
+    // K split: enough items to fill the machine twice over, at most 8 ways,
+    // at least one chunk per split.
+    long long base_items = 0;
+    for (auto& h : hi) base_items += (long long)h.S * h.T * h.T;
+    int ks = 1;
+    while (ks < 8 && base_items * ks < 2 * slots) ks *= 2;
+    // Longest items first (LPT): sort by per-item work, then caller order.
+    std::vector<int> ord(count);
+    for (int i = 0; i < count; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+        const long long wa = hi[a].N / std::min<long long>(ks, std::max<long long>(1, hi[a].N / JC));
+        const long long wb = hi[b].N / std::min<long long>(ks, std::max<long long>(1, hi[b].N / JC));
+        return wa > wb;
+    });
+
+    // Plan the workspace.
+    Arena ar;
+    Arena pin;
+    struct Off {
+        size_t coef, xm, zm, alpha, b;       // staged inputs (ws) ...
+        size_t pcoef, pxm, pzm, palpha, pb;  // ... and their pinned slots
+        size_t ctil, w, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta;
+        size_t pcost, pgrad, pbeta, pdelta;
+    };
+    std::vector<Off> off(count);
+    long long item_base = 0;
+    const size_t o_table = ar.reserve(sizeof(Inst) * count);
+    const size_t p_table = pin.reserve(sizeof(Inst) * count);
+    for (int oi = 0; oi < count; ++oi) {
+        const int i = ord[oi];
+        HostInst& h = hi[i];
+        h.ks = (int)std::min<long long>(ks, std::max<long long>(1, h.N / JC));
+        Off& o = off[i];
+        const size_t L = h.L;
+        o.coef = ar.reserve(L * 16);
+        o.pcoef = pin.reserve(L * 16);
+        o.xm = ar.reserve(L * 4);
+        o.pxm = pin.reserve(L * 4);
+        o.zm = ar.reserve(L * 4);
+        o.pzm = pin.reserve(L * 4);
+        o.alpha = ar.reserve(size_t(h.P) * 8);
+        o.palpha = pin.reserve(size_t(h.P) * 8);
+        o.b = ar.reserve(size_t(h.N) * 16);
+        o.pb = pin.reserve(size_t(h.N) * 16);
+        o.ctil = ar.reserve(L * 16);
+        o.w = ar.reserve(L * L * 16);
+        o.cs = ar.reserve(size_t(3) * h.P * 16);
+        o.bn2 = ar.reserve(8);
+        o.Dp = ar.reserve(size_t(h.S) * h.T * h.T * h.ks * 16);
+        o.Tp = ar.reserve(size_t(h.S) * h.T * h.ks * 16);
+        o.Gp = beta_out ? ar.reserve(size_t(h.ks) * L * L * r2) : 0;
+        o.dp = delta_out ? ar.reserve(size_t(h.ks) * L * r2) : 0;
+        o.NsDs = ar.reserve(size_t(h.S) * 24);
+        o.cost = ar.reserve(8);
+        o.pcost = pin.reserve(8);
+        o.grad = ar.reserve(size_t(h.P) * 8);
+        o.pgrad = pin.reserve(size_t(h.P) * 8);
+        o.beta = beta_out ? ar.reserve(L * L * 16) : 0;
+        o.pbeta = beta_out ? pin.reserve(L * L * 16) : 0;
+        o.delta = delta_out ? ar.reserve(L * 16) : 0;
+        o.pdelta = delta_out ? pin.reserve(L * 16) : 0;
+    }
+    int rc = ensure_workspace(ctx, ar.total());
+    if (!rc) rc = ensure_pinned(ctx, pin.total());
+    if (rc) return rc;
+    char* ws = ctx->ws;
+
+    // Host inputs are staged through pinned memory: wait until the previous
+    // call's copies out of it are done before writing it again.
+    bool all_device = true;
+    for (int i = 0; i < count && all_device; ++i) {
+        const dvqls_instance& q = inst[i];
+        all_device = is_device_ptr(ctx, q.lcu.coef) && is_device_ptr(ctx, q.lcu.xmask) &&
+                     is_device_ptr(ctx, q.lcu.zmask) && is_device_ptr(ctx, q.alpha) && is_device_ptr(ctx, q.b);
+    }
+    if (!all_device) {
+        rc = pin_acquire(ctx);
+        if (rc) return rc;
+    }
+    std::vector<Inst> table(count);
+    std::vector<long long> grad_off(count, 0);
+    {
+        long long g = 0;
+        for (int i = 0; i < count; ++i) {
+            grad_off[i] = g;
+            g += hi[i].P;
+        }
+    }
+    for (int oi = 0; oi < count; ++oi) {
+        const int i = ord[oi];
+        const HostInst& h = hi[i];
+        const Off& o = off[i];
+        const dvqls_instance& q = inst[i];
+        Inst I;
+        memset(&I, 0, sizeof I);
+        I.n = h.n;
+        I.d = h.d;
+        I.L = h.L;
+        I.P = h.P;
+        I.S = h.S;
+        I.T = h.T;
+        I.ks = h.ks;
+        I.items = h.S * h.T * h.T * h.ks;
+        I.item_base = item_base;
+        item_base += I.items;
+        I.coef = (const double2*)stage_in(ctx, q.lcu.coef, size_t(h.L) * 16, o.pcoef, o.coef);
+        I.xm = (const uint32_t*)stage_in(ctx, q.lcu.xmask, size_t(h.L) * 4, o.pxm, o.xm);
+        I.zm = (const uint32_t*)stage_in(ctx, q.lcu.zmask, size_t(h.L) * 4, o.pzm, o.zm);
+        I.alpha = (const double*)stage_in(ctx, q.alpha, size_t(h.P) * 8, o.palpha, o.alpha);
+        I.b = (const double2*)stage_in(ctx, q.b, size_t(h.N) * 16, o.pb, o.b);
+        I.ctil = (double2*)(ws + o.ctil);
+        I.w = (double2*)(ws + o.w);
+        I.cs = (double2*)(ws + o.cs);
+        I.bn2 = (double*)(ws + o.bn2);
+        I.Dpart = (double2*)(ws + o.Dp);
+        I.Tpart = (double2*)(ws + o.Tp);
+        I.Gpart = beta_out ? (void*)(ws + o.Gp) : nullptr;
+        I.dpart = delta_out ? (void*)(ws + o.dp) : nullptr;
+        I.NsDs = (double*)(ws + o.NsDs);
+        // Device outputs are written in place by the combine kernel.
+        const bool dev_cost = costs && is_device_ptr(ctx, costs);
+        const bool dev_grad = grads && is_device_ptr(ctx, grads);
+        I.cost = dev_cost ? costs + i : (double*)(ws + o.cost);
+        I.grad = !want_grad ? nullptr : dev_grad ? grads + grad_off[i] : (double*)(ws + o.grad);
+        I.beta = beta_out ? (double2*)(ws + o.beta) : nullptr;
+        I.delta = delta_out ? (double2*)(ws + o.delta) : nullptr;
+        table[oi] = I;
+    }
+    const Inst* dtable = (const Inst*)(ws + o_table);
+    const size_t tbytes = sizeof(Inst) * count;
+    const char* tb = reinterpret_cast<const char*>(table.data());
+    const bool same_table = ctx->last_table.size() == tbytes && memcmp(ctx->last_table.data(), tb, tbytes) == 0;
+    if (!same_table) {
+        if (all_device) {
+            rc = pin_acquire(ctx);
+            if (rc) return rc;
+        }
+        memcpy(ctx->pin + p_table, tb, tbytes);
+        DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync((void*)dtable, ctx->pin + p_table, tbytes, cudaMemcpyHostToDevice,
+                                            ctx->stream));
+        ctx->last_table.assign(tb, tb + tbytes);
+    }
+    if (!same_table || !all_device) {
+        rc = pin_release(ctx);
+        if (rc) return rc;
+    }
+    DVQLS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_queue, 0, sizeof(unsigned long long), ctx->stream));
+    prof_begin(ctx, 0);
+    k_prepare<<<count, NT, 0, ctx->stream>>>(dtable, ctx->d_status);
+    prof_end(ctx);
+    const long long total = item_base;
+    const int grid = (int)std::min<long long>(total, slots);
+    prof_begin(ctx, 1);
+    if (fp32) k_terms_smem<float><<<grid, NT, smem, ctx->stream>>>(dtable, count, total, ctx->d_queue);
+    else k_terms_smem<double><<<grid, NT, smem, ctx->stream>>>(dtable, count, total, ctx->d_queue);
+    prof_end(ctx);
+    prof_begin(ctx, 2);
+    if (fp32) k_combine<float><<<count, NT, 0, ctx->stream>>>(dtable, ctx->d_status);
+    else k_combine<double><<<count, NT, 0, ctx->stream>>>(dtable, ctx->d_status);
+    prof_end(ctx);
+    DVQLS_CUDA_TRY(ctx, cudaGetLastError());
+
+    // Results.
+    std::vector<PendingOut> pend;
+    for (int i = 0; i < count; ++i) {
+        const Off& o = off[i];
+        const HostInst& h = hi[i];
+        if (costs && !is_device_ptr(ctx, costs)) {
+            rc = enqueue_out(ctx, costs + i, ws + o.cost, 8, o.pcost, pend);
+            if (rc) return rc;
+        }
+        if (want_grad && grads && !is_device_ptr(ctx, grads)) {
+            rc = enqueue_out(ctx, grads + grad_off[i], ws + o.grad, size_t(h.P) * 8, o.pgrad, pend);
+            if (rc) return rc;
+        }
+        if (beta_out) {
+            rc = enqueue_out(ctx, beta_out, ws + o.beta, size_t(h.L) * h.L * 16, o.pbeta, pend);
+            if (rc) return rc;
+        }
+        if (delta_out) {
+            rc = enqueue_out(ctx, delta_out, ws + o.delta, size_t(h.L) * 16, o.pdelta, pend);
+            if (rc) return rc;
+        }
+    }
+    const bool async_ok = all_device && pend.empty() && !beta_out && !delta_out;
+    if (async_ok) return DVQLS_OK;
+    rc = sync_and_check(ctx);
+    if (rc) return rc;
+    finish_out(ctx, pend);
+    return DVQLS_OK;
+}
+
+}  // namespace dvqls
+
+using namespace dvqls;
+
+static int single(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alpha, const dvqls_lcu* lcu,
+                  const double* b, int precision, bool grad, double* cost, double* g, double* beta, double* delta) {
+    if (!ctx) return DVQLS_ERR_INVALID_ARG;
+    if (!ansatz || !lcu || !cost) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "NULL ansatz, lcu or cost");
+    dvqls_instance in;
+    in.ansatz = *ansatz;
+    in.lcu = *lcu;
+    in.alpha = alpha;
+    in.b = b;
+    int rc = run_batch(ctx, 1, &in, precision, grad, cost, g, beta, delta);
+    if (rc == DVQLS_OK && is_device_ptr(ctx, cost)) rc = sync_and_check(ctx);
+    return rc;
+}
+
+extern "C" int dvqls_cost(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alpha, const dvqls_lcu* lcu,
+                          const double* b, int precision, double* cost, double* beta, double* delta) {
+    return single(ctx, ansatz, alpha, lcu, b, precision, false, cost, nullptr, beta, delta);
+}
+
+extern "C" int dvqls_cost_grad(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alpha,
+                               const dvqls_lcu* lcu, const double* b, int precision, double* cost, double* grad,
+                               double* beta, double* delta) {
+    if (ctx && !grad) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "grad is NULL");
+    return single(ctx, ansatz, alpha, lcu, b, precision, true, cost, grad, beta, delta);
+}
+
+extern "C" int dvqls_cost_grad_batched(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precision,
+                                       double* costs, double* grads) {
+    return run_batch(ctx, count, inst, precision, true, costs, grads, nullptr, nullptr);
+}

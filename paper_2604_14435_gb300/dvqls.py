@@ -1,0 +1,192 @@
+"""Thin ctypes binding of libdvqls.so (include/dvqls.h): argument marshalling only.
+
+Every function keeps the C name and order of arguments; array arguments may
+be numpy arrays (host memory) or torch tensors (host or CUDA memory of the
+context's device).  Nothing here computes any part of the method: a missing
+library is an error, never a fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdvqls.so")
+
+DVQLS_OK = 0
+DVQLS_ERR_INVALID_ARG = 1
+DVQLS_ERR_UNSUPPORTED = 2
+DVQLS_ERR_CUDA = 3
+DVQLS_ERR_TIMEOUT = 4
+DVQLS_ERR_NUMERIC = 5
+DVQLS_ERR_ALLOC = 6
+DVQLS_FP64 = 0
+DVQLS_FP32 = 1
+DVQLS_ANSATZ_RY_CZRING = 0
+DVQLS_MAX_SMEM_QUBITS = 12
+DVQLS_MAX_QUBITS = 20
+DVQLS_MAX_DENSE_QUBITS = 12
+
+EXPORTED = [
+    "dvqls_create", "dvqls_destroy", "dvqls_last_error", "dvqls_sync",
+    "dvqls_pauli_decompose", "dvqls_pauli_decompose_banded",
+    "dvqls_cost", "dvqls_cost_grad", "dvqls_cost_grad_batched",
+    "dvqls_profile_enable", "dvqls_profile_read",
+]
+
+
+class DvqlsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("dvqls status %d: %s" % (code, msg))
+        self.code = code
+
+
+class dvqls_ansatz(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("depth", ctypes.c_int), ("kind", ctypes.c_int)]
+
+
+class dvqls_lcu(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("coef", ctypes.c_void_p), ("xmask", ctypes.c_void_p),
+                ("zmask", ctypes.c_void_p)]
+
+
+class dvqls_instance(ctypes.Structure):
+    _fields_ = [("ansatz", dvqls_ansatz), ("lcu", dvqls_lcu), ("alpha", ctypes.c_void_p),
+                ("b", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Open libdvqls.so (built by paper_2604_14435_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libdvqls.so is not built (run __graft_entry__.build()); "
+                               "there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p
+        L.dvqls_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, vp]
+        L.dvqls_destroy.argtypes = [vp]
+        L.dvqls_destroy.restype = None
+        L.dvqls_last_error.argtypes = [vp]
+        L.dvqls_last_error.restype = ctypes.c_char_p
+        L.dvqls_sync.argtypes = [vp]
+        L.dvqls_pauli_decompose.argtypes = [vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                            dp, vp, vp, ip, ip, ip]
+        L.dvqls_pauli_decompose_banded.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, dp, ctypes.c_double,
+                                                   ctypes.c_int, dp, vp, vp, ip, ip, ip]
+        L.dvqls_cost.argtypes = [vp, ctypes.POINTER(dvqls_ansatz), dp, ctypes.POINTER(dvqls_lcu), dp,
+                                 ctypes.c_int, dp, dp, dp]
+        L.dvqls_cost_grad.argtypes = [vp, ctypes.POINTER(dvqls_ansatz), dp, ctypes.POINTER(dvqls_lcu), dp,
+                                      ctypes.c_int, dp, dp, dp, dp]
+        L.dvqls_cost_grad_batched.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dvqls_instance), ctypes.c_int,
+                                              dp, dp]
+        L.dvqls_profile_enable.argtypes = [vp, ctypes.c_int]
+        L.dvqls_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.POINTER(ctypes.c_double)]
+        _lib = L
+    return _lib
+
+
+def ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr() or None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data or None
+    raise TypeError("expected a numpy array or a torch tensor, got %r" % type(a))
+
+
+def _check(ctx, code):
+    if code != DVQLS_OK:
+        msg = lib().dvqls_last_error(ctx).decode() if ctx else ""
+        raise DvqlsError(code, msg)
+
+
+def dvqls_create(device=0, stream=None):
+    """Returns the context handle.  stream: a cudaStream_t as int (or None)."""
+    h = ctypes.c_void_p()
+    _check(None, lib().dvqls_create(ctypes.byref(h), int(device), stream))
+    return h
+
+
+def dvqls_destroy(ctx):
+    lib().dvqls_destroy(ctx)
+
+
+def dvqls_last_error(ctx):
+    return lib().dvqls_last_error(ctx).decode()
+
+
+def dvqls_sync(ctx):
+    _check(ctx, lib().dvqls_sync(ctx))
+
+
+def _ints():
+    return ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+
+
+def dvqls_pauli_decompose(ctx, A, n, tau, L_max, coef, xmask, zmask):
+    """Returns (L_out, L_pre, L_post); coef/xmask/zmask are filled in place."""
+    a, b, c = _ints()
+    _check(ctx, lib().dvqls_pauli_decompose(ctx, ptr(A), int(n), float(tau), int(L_max), ptr(coef), ptr(xmask),
+                                            ptr(zmask), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def dvqls_pauli_decompose_banded(ctx, n, offsets, band_values, tau, L_max, coef, xmask, zmask):
+    offs = np.ascontiguousarray(offsets, dtype=np.int32)
+    a, b, c = _ints()
+    _check(ctx, lib().dvqls_pauli_decompose_banded(ctx, int(n), offs.size, ptr(offs), ptr(band_values),
+                                                   float(tau), int(L_max), ptr(coef), ptr(xmask), ptr(zmask),
+                                                   ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def make_ansatz(n, depth, kind=DVQLS_ANSATZ_RY_CZRING):
+    return dvqls_ansatz(int(n), int(depth), int(kind))
+
+
+def make_lcu(L, coef, xmask, zmask):
+    return dvqls_lcu(int(L), ptr(coef), ptr(xmask), ptr(zmask))
+
+
+def dvqls_cost(ctx, ansatz, alpha, lcu, b, precision, cost, beta=None, delta=None):
+    _check(ctx, lib().dvqls_cost(ctx, ctypes.byref(ansatz), ptr(alpha), ctypes.byref(lcu), ptr(b), int(precision),
+                                 ptr(cost), ptr(beta), ptr(delta)))
+
+
+def dvqls_cost_grad(ctx, ansatz, alpha, lcu, b, precision, cost, grad, beta=None, delta=None):
+    _check(ctx, lib().dvqls_cost_grad(ctx, ctypes.byref(ansatz), ptr(alpha), ctypes.byref(lcu), ptr(b),
+                                      int(precision), ptr(cost), ptr(grad), ptr(beta), ptr(delta)))
+
+
+def make_instances(items):
+    """items: sequence of (ansatz, lcu, alpha, b) -> ctypes array of dvqls_instance."""
+    arr = (dvqls_instance * len(items))()
+    for k, (an, lc, al, bb) in enumerate(items):
+        arr[k].ansatz = an
+        arr[k].lcu = lc
+        arr[k].alpha = ptr(al)
+        arr[k].b = ptr(bb)
+    return arr
+
+
+def dvqls_cost_grad_batched(ctx, instances, precision, costs, grads):
+    _check(ctx, lib().dvqls_cost_grad_batched(ctx, len(instances), instances, int(precision), ptr(costs),
+                                              ptr(grads)))
+
+
+def dvqls_profile_enable(ctx, enable):
+    _check(ctx, lib().dvqls_profile_enable(ctx, int(enable)))
+
+
+def dvqls_profile_read(ctx, phase):
+    """Returns (launches, total milliseconds) of one kernel phase."""
+    n, ms = ctypes.c_longlong(), ctypes.c_double()
+    _check(ctx, lib().dvqls_profile_read(ctx, int(phase), ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
