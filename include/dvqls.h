@@ -199,6 +199,40 @@ typedef struct {
 int dvqls_cost_grad_batched(dvqls_ctx* ctx, int count, const dvqls_instance* inst,
                             int precision, double* costs, double* grads);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free cost and gradient.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate GPU memory, such as
+ * code running inside a memory pool or allocator that owns the whole device,
+ * a real-time loop whose allocation pattern is fixed, or a plugin host that
+ * forbids cudaMalloc.  It computes exactly what dvqls_cost_grad computes
+ * (same kernels, no beta/delta output) without a context: it calls no
+ * cudaMalloc, cudaFree, cudaMallocHost or other allocating routine.
+ *
+ * Its scratch is one fixed device array of DVQLS_NOALLOC_SCRATCH_BYTES
+ * inside this library; every GPU that loads the library holds it until the
+ * process exits.  A request whose scratch exceeds it is rejected with
+ * INVALID_ARG.  The scratch it needs is, in bytes (each term rounded up to
+ * 256): sizeof record + 256 + 16 L + 16 L^2 + 48 P + 8 + 16 S T^2 k
+ * + 16 S T k + 24 S, with S = 2P+1, T = ceil(L/64) and k <= 8 the split of
+ * the amplitude range; for example n = 10, L = 64, P = 50 needs about 100 KB
+ * and L up to about 200 fits.
+ *
+ * The call runs on the current CUDA device, ordered on `stream` (a
+ * cudaStream_t, NULL = default stream), and returns after cost and grad are
+ * written.  alpha, b, the lcu arrays, cost and grad must all be device memory
+ * of the current device (nothing is staged): a host pointer is INVALID_ARG.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) once; make that first call before any stream
+ * capture.  Every call shares the one array: two calls that overlap on the
+ * GPU (other streams, other threads) race and give wrong results, so keep
+ * calls ordered on one stream or serialise them.
+ * Errors: INVALID_ARG, UNSUPPORTED (n > DVQLS_MAX_SMEM_QUBITS or another
+ * ansatz), NUMERIC, CUDA.  No error text is kept (there is no context). */
+#define DVQLS_NOALLOC_SCRATCH_BYTES (1u << 20)
+int dvqls_cost_grad_noalloc(void* stream, const dvqls_ansatz* ansatz, const double* alpha,
+                            const dvqls_lcu* lcu, const double* b, int precision,
+                            double* cost, double* grad);
+
 #ifdef __cplusplus
 }
 #endif

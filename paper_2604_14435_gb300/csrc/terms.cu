@@ -22,6 +22,7 @@
 // on scheduling.  C = 1 - N_0/D_0 with N_s = |T_s|^2/||b||^2 and
 // dC/dalpha_k = -(N'_k D_0 - N_0 D'_k)/D_0^2 (parameter-shift rule).
 #include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -796,4 +797,168 @@ extern "C" int dvqls_cost_grad(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const
 extern "C" int dvqls_cost_grad_batched(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precision,
                                        double* costs, double* grads) {
     return run_batch(ctx, count, inst, precision, true, costs, grads, nullptr, nullptr);
+}
+
+// ------------------------------------------------- allocation-free variant
+// dvqls_cost_grad_noalloc runs the same three kernels as dvqls_cost_grad for
+// one instance, but takes its scratch (instance record, weights, per-item
+// partial sums, queue counter, status word) from the file-scope device array
+// below instead of a context workspace, so it needs no cudaMalloc, no pinned
+// staging and no context.  Every GPU that loads the library holds the array
+// until the process exits.
+namespace dvqls {
+
+constexpr size_t NOALLOC_BYTES = size_t(DVQLS_NOALLOC_SCRATCH_BYTES);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+__global__ void k_noalloc_store(Inst I, Inst* dst) { *dst = I; }
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static void* g_noalloc_addr[NOALLOC_MAX_DEVICES];  // device address of the array, per device
+
+// Device address of g_noalloc_scratch on the current device `dev`.  In host
+// code the symbol's name is only a host-side stand-in; the address comes from
+// cudaGetSymbolAddress, called once per device with that device current.
+static int noalloc_scratch_address(int dev, char** out) {
+    static std::mutex m;
+    std::lock_guard<std::mutex> g(m);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return DVQLS_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<char*>(g_noalloc_addr[dev]);
+    return DVQLS_OK;
+}
+
+static bool noalloc_dev_ptr(const void* p, int dev) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace dvqls
+
+extern "C" int dvqls_cost_grad_noalloc(void* stream_arg, const dvqls_ansatz* ansatz, const double* alpha,
+                                       const dvqls_lcu* lcu, const double* b, int precision, double* cost,
+                                       double* grad) {
+    using namespace dvqls;
+    cudaStream_t stream = (cudaStream_t)stream_arg;
+    if (!ansatz || !lcu || !cost || !grad) return DVQLS_ERR_INVALID_ARG;
+    if (precision != DVQLS_FP32 && precision != DVQLS_FP64) return DVQLS_ERR_INVALID_ARG;
+    const int n = ansatz->n, d = ansatz->depth, L = lcu->L;
+    if (n < 1 || n > DVQLS_MAX_QUBITS || d < 0 || L < 1) return DVQLS_ERR_INVALID_ARG;
+    if (n > DVQLS_MAX_SMEM_QUBITS || ansatz->kind != DVQLS_ANSATZ_RY_CZRING) return DVQLS_ERR_UNSUPPORTED;
+    const long long Pl = (long long)n * (d + 1);
+    if (Pl > MAX_ANGLES) return DVQLS_ERR_UNSUPPORTED;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        cudaGetLastError();
+        return DVQLS_ERR_CUDA;
+    }
+    const void* ptrs[] = {alpha, b, lcu->coef, lcu->xmask, lcu->zmask, cost, grad};
+    for (const void* p : ptrs)
+        if (!noalloc_dev_ptr(p, dev)) return DVQLS_ERR_INVALID_ARG;  // device memory only: nothing is staged
+
+    const bool fp32 = precision == DVQLS_FP32;
+    const int P = int(Pl), S = 2 * P + 1, T = ceil_div(L, TT);
+    const long long N = 1LL << n;
+    const size_t smem = fp32 ? smem_bytes<float>(n, P) : smem_bytes<double>(n, P);
+    auto kfun = fp32 ? (const void*)k_terms_smem<float> : (const void*)k_terms_smem<double>;
+    if (cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) {
+        cudaGetLastError();
+        return DVQLS_ERR_CUDA;
+    }
+    int bps = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfun, NT, smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return DVQLS_ERR_CUDA;
+    }
+    if (bps < 1) return DVQLS_ERR_UNSUPPORTED;
+    const long long slots = (long long)sms * bps, base_items = (long long)S * T * T;
+    int ks = 1;
+    while (ks < 8 && base_items * ks < 2 * slots) ks *= 2;
+    ks = (int)std::min<long long>(ks, std::max<long long>(1, N / JC));
+
+    // Scratch layout (offsets 256-byte aligned).
+    Arena ar;
+    const size_t o_table = ar.reserve(sizeof(Inst));
+    const size_t o_words = ar.reserve(256);  // status word, queue counter
+    const size_t o_ctil = ar.reserve(size_t(L) * 16);
+    const size_t o_w = ar.reserve(size_t(L) * L * 16);
+    const size_t o_cs = ar.reserve(size_t(3) * P * 16);
+    const size_t o_bn2 = ar.reserve(8);
+    const size_t o_Dp = ar.reserve(size_t(S) * T * T * ks * 16);
+    const size_t o_Tp = ar.reserve(size_t(S) * T * ks * 16);
+    const size_t o_NsDs = ar.reserve(size_t(S) * 24);
+    if (ar.total() > NOALLOC_BYTES) return DVQLS_ERR_INVALID_ARG;  // beyond the fixed scratch
+    char* base = nullptr;
+    int rc = noalloc_scratch_address(dev, &base);
+    if (rc) return rc;
+
+    Inst I;
+    memset(&I, 0, sizeof I);
+    I.n = n;
+    I.d = d;
+    I.L = L;
+    I.P = P;
+    I.S = S;
+    I.T = T;
+    I.ks = ks;
+    I.items = S * T * T * ks;
+    I.item_base = 0;
+    I.coef = (const double2*)lcu->coef;
+    I.xm = lcu->xmask;
+    I.zm = lcu->zmask;
+    I.alpha = alpha;
+    I.b = (const double2*)b;
+    I.ctil = (double2*)(base + o_ctil);
+    I.w = (double2*)(base + o_w);
+    I.cs = (double2*)(base + o_cs);
+    I.bn2 = (double*)(base + o_bn2);
+    I.Dpart = (double2*)(base + o_Dp);
+    I.Tpart = (double2*)(base + o_Tp);
+    I.NsDs = (double*)(base + o_NsDs);
+    I.cost = cost;
+    I.grad = grad;
+    Inst* table = (Inst*)(base + o_table);
+    int* status = (int*)(base + o_words);
+    unsigned long long* queue = (unsigned long long*)(base + o_words + 64);
+
+    // The array keeps the previous call's contents: the status word and the
+    // work-queue counter must start at zero; everything else is overwritten.
+    if (cudaMemsetAsync(base + o_words, 0, 256, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DVQLS_ERR_CUDA;
+    }
+    k_noalloc_store<<<1, 1, 0, stream>>>(I, table);
+    k_prepare<<<1, NT, 0, stream>>>(table, status);
+    const long long total = I.items;
+    const int grid = (int)std::min<long long>(total, slots);
+    if (fp32) k_terms_smem<float><<<grid, NT, smem, stream>>>(table, 1, total, queue);
+    else k_terms_smem<double><<<grid, NT, smem, stream>>>(table, 1, total, queue);
+    if (fp32) k_combine<float><<<1, NT, 0, stream>>>(table, status);
+    else k_combine<double><<<1, NT, 0, stream>>>(table, status);
+    int st = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DVQLS_ERR_CUDA;
+    }
+    switch (st) {
+        case DEV_OK: return DVQLS_OK;
+        case DEV_BAD_MASK:
+        case DEV_NONFINITE_INPUT:
+        case DEV_BAD_NORM: return DVQLS_ERR_INVALID_ARG;
+        default: return DVQLS_ERR_NUMERIC;
+    }
 }

@@ -31,7 +31,7 @@ EXPORTED = [
     "dvqls_create", "dvqls_destroy", "dvqls_last_error", "dvqls_sync",
     "dvqls_pauli_decompose", "dvqls_pauli_decompose_banded",
     "dvqls_cost", "dvqls_cost_grad", "dvqls_cost_grad_batched",
-    "dvqls_profile_enable", "dvqls_profile_read",
+    "dvqls_profile_enable", "dvqls_profile_read", "dvqls_cost_grad_noalloc",
 ]
 
 
@@ -86,6 +86,8 @@ def lib():
         L.dvqls_profile_enable.argtypes = [vp, ctypes.c_int]
         L.dvqls_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(ctypes.c_double)]
+        L.dvqls_cost_grad_noalloc.argtypes = [vp, ctypes.POINTER(dvqls_ansatz), dp, ctypes.POINTER(dvqls_lcu), dp,
+                                              ctypes.c_int, dp, dp]
         _lib = L
     return _lib
 
@@ -190,3 +192,10 @@ def dvqls_profile_read(ctx, phase):
     n, ms = ctypes.c_longlong(), ctypes.c_double()
     _check(ctx, lib().dvqls_profile_read(ctx, int(phase), ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+def dvqls_cost_grad_noalloc(stream, ansatz, alpha, lcu, b, precision, cost, grad):
+    """Allocation-free cost + gradient (device buffers only).  Returns the
+    status code instead of raising, since there is no context to describe it."""
+    return lib().dvqls_cost_grad_noalloc(stream, ctypes.byref(ansatz), ptr(alpha), ctypes.byref(lcu), ptr(b),
+                                         int(precision), ptr(cost), ptr(grad))
