@@ -269,6 +269,48 @@ def main():
     d2h = BATCH * (8 + P * 8)
     gpu_check = float(np.max(np.abs(hcost - costs.cpu().numpy())))
 
+    # Comparison path: the per-circuit FP64 evaluation of instance 0 (all
+    # 840,320 circuits of one cost+grad), and the decomposition of instance 0.
+    circ = None
+    decomp = None
+    if rank == 0:
+        coef0, xm0, zm0, alpha0, b0 = keep[0]
+        an = D.make_ansatz(N_QUBITS, DEPTH)
+        lcu0 = D.make_lcu(L_TERMS, coef0, xm0, zm0)
+        c1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        g1 = torch.zeros(P, dtype=torch.float64, device="cuda")
+        D.dvqls_circuit_cost_grad_fp64(ctx, an, alpha0, lcu0, b0, c1, g1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 2
+        for _ in range(reps):
+            D.dvqls_circuit_cost_grad_fp64(ctx, an, alpha0, lcu0, b0, c1, g1)
+        torch.cuda.synchronize()
+        circ_s = (time.perf_counter() - t0) / reps
+        circ = {"value": 1.0 / circ_s, "unit": UNIT, "dtype": "f64", "s_per_eval": circ_s,
+                "circuits_per_eval": 2 * 101 * (L_TERMS ** 2 + L_TERMS),
+                "cost_diff_vs_fp32_batched": abs(c1.item() - costs[0].item())}
+        from paper_2604_14435_gb300 import workloads as wl
+        inst0 = wl.throughput_instance(0, n=N_QUBITS, d=DEPTH, L_max=L_TERMS)
+        bands = torch.tensor(inst0["bands"], dtype=torch.float64, device="cuda")
+        A = torch.tensor(wl.dense_from_bands(N_QUBITS, inst0["offsets"], inst0["bands"]), device="cuda")
+        cc = torch.zeros(2 * L_TERMS, dtype=torch.float64, device="cuda")
+        xx = torch.zeros(L_TERMS, dtype=torch.int32, device="cuda")
+        zz = torch.zeros(L_TERMS, dtype=torch.int32, device="cuda")
+        def tdec(fn, reps=20):
+            fn()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            torch.cuda.synchronize()
+            return 1000.0 * (time.perf_counter() - t) / reps
+        ms_b = tdec(lambda: D.dvqls_pauli_decompose_banded(ctx, N_QUBITS, inst0["offsets"], bands, 0.01, L_TERMS,
+                                                           cc, xx, zz))
+        ms_d = tdec(lambda: D.dvqls_pauli_decompose(ctx, A, N_QUBITS, 0.01, L_TERMS, cc, xx, zz))
+        decomp = {"banded_ms": ms_b, "dense_ms": ms_d, "n": N_QUBITS, "L_max": L_TERMS,
+                  "note": "host wall time per call incl. the count read-back; dense input 8 MB (N x N FP64)"}
+
     if rank == 0:
         avg_terms_ms = ms_terms / max(1, n_terms_launch)
         achieved = flops_per_step() / (avg_terms_ms / 1000.0) / 1e12
@@ -287,6 +329,9 @@ def main():
                 "e2e": {"value": ws * BATCH * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "max_abs_cost_diff_vs_device_path": gpu_check},
                 "gpu_launches": n_terms_launch + n_prep + n_comb,
+                "fp64_circuit_path": circ,
+                "speedup_vs_fp64_circuit_path": value / circ["value"] if circ else None,
+                "decomposition": decomp,
                 "clocks": clk}
         if not args.no_cpu_baseline and ws == 1:
             rate, cores, sample = cpu_oracle_rate(budget_s=10.0)

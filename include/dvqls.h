@@ -199,6 +199,66 @@ typedef struct {
 int dvqls_cost_grad_batched(dvqls_ctx* ctx, int count, const dvqls_instance* inst,
                             int precision, double* costs, double* grads);
 
+/* Per-circuit FP64 path (Sec. 2.3 execution model; Sec. 2.2 after Eq. 4):
+ * each Hadamard-test circuit -- S (L^2 + L) expectation values, real and
+ * imaginary part each from its own circuit, 2 S (L^2 + L) circuits -- is
+ * simulated on its own (n+1)-qubit complex128 state vector gate by gate
+ * (H, Ry / controlled Ry, CZ / CCZ, controlled X / Y / Z per Pauli factor,
+ * controlled U_b^dag, S^dag) and measured as <Z_ancilla>; then the same FP64
+ * combine as dvqls_cost_grad.  U_b is H^(x)n when b = |+>^n, else the phased
+ * Householder reflection mapping |0> to b/||b||.  Same arguments and outputs
+ * as dvqls_cost_grad (FP64 only); n + 1 <= 13.  It is the comparison path of
+ * the batched evaluation and a second FP64 check of it. */
+int dvqls_circuit_cost_grad_fp64(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alpha,
+                                 const dvqls_lcu* lcu, const double* b,
+                                 double* cost, double* grad, double* beta, double* delta);
+
+/* ------------------------------------------------------------------------
+ * Fidelity, classical solve and the optimizer loop (Sec. 3.1; Algorithm 1).
+ */
+
+/* F = |<xhat|psi(alpha)>|^2 / ||xhat||^2 with psi(alpha) = V(alpha)|0> built
+ * in FP64 (Sec. 3.1: fidelity against the classical solution).  xhat: N
+ * complex128, any nonzero norm.  n <= DVQLS_MAX_SMEM_QUBITS. */
+int dvqls_fidelity(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alpha,
+                   const double* xhat, double* F);
+
+/* Classical solution x = A~^{-1} b of the system the LCU encodes,
+ * A~ = sum_l c_l A_l applied as a Pauli-string matvec in FP64: conjugate
+ * gradients (A~ Hermitian positive definite), falling back to CG on the
+ * normal equations when CG breaks down (p^dag A~ p <= 0).  Stops when
+ * ||r|| / ||rhs|| <= tol or after max_iter iterations.  x: N complex128
+ * (not normalised).  iters, rel_resid may be NULL.  Returns NUMERIC when tol
+ * was not reached (x then holds the last iterate). */
+int dvqls_lcu_solve(dvqls_ctx* ctx, int n, const dvqls_lcu* lcu, const double* b, double tol,
+                    int max_iter, double* x, int* iters, double* rel_resid);
+
+typedef struct {
+    double lr, beta1, beta2, eps; /* Adam step size and moment decay rates   */
+    int max_iter;                 /* updates at most                          */
+    double target_fidelity;       /* stop an instance once F >= this          */
+    int precision;                /* dvqls_precision of the cost pass         */
+} dvqls_adam;
+
+typedef struct {
+    int iters;       /* Adam updates made before the stop                */
+    int converged;   /* 1 when F >= target_fidelity was reached          */
+    double cost;     /* C at the final angles                            */
+    double fidelity; /* F at the final angles                            */
+} dvqls_opt_result;
+
+/* Adam on the angles of `count` instances in lock step (Algorithm 1's loop
+ * with Adam as the optimizer): each iteration evaluates, for every instance
+ * still running, F(alpha) against xhat and the batched cost and parameter-
+ * shift gradient, stops the instances with F >= target_fidelity, and updates
+ * the others.  Starts from inst[i].alpha; inst[i].alpha is not written.
+ * xhat: packed N_i complex128 per instance (the classical solution).
+ * alpha_out: packed P_i doubles per instance (final angles).  results: count
+ * entries (host memory).  The optimizer allocates its own state for the
+ * call and frees it before returning. */
+int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* inst, const double* xhat,
+                   const dvqls_adam* opt, double* alpha_out, dvqls_opt_result* results);
+
 /* ------------------------------------------------------------------------
  * Allocation-free cost and gradient.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate GPU memory, such as

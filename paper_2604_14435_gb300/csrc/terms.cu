@@ -25,6 +25,7 @@
 #include <mutex>
 
 #include "internal.cuh"
+#include "state.cuh"
 
 namespace dvqls {
 
@@ -69,17 +70,6 @@ void release_graph_cache(dvqls_ctx* ctx) {
         ctx->graph = nullptr;
     }
 }
-
-template <typename R>
-struct V2;
-template <>
-struct V2<float> {
-    using t = float2;
-};
-template <>
-struct V2<double> {
-    using t = double2;
-};
 
 __device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
 
@@ -136,69 +126,6 @@ __global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, 
 }
 
 // ------------------------------------------------------------ term tiles
-template <typename R2>
-__device__ __forceinline__ R2 neg2(R2 v) {
-    v.x = -v.x;
-    v.y = -v.y;
-    return v;
-}
-
-__device__ __forceinline__ int czring_parity(int i, int n) {
-    int p = __popc(i & (i >> 1) & ((1 << (n - 1)) - 1));
-    if (n >= 3) p += (i >> (n - 1)) & i & 1;
-    return p & 1;
-}
-
-// psi = V(alpha_s)|0> in shared memory (all threads; ends with a barrier).
-template <typename R>
-__device__ void build_state(typename V2<R>::t* psi, typename V2<R>::t* scs, const Inst& I, int s) {
-    using R2 = typename V2<R>::t;
-    const int n = I.n, N = 1 << n, P = I.P, t = threadIdx.x;
-    int k = -1, which = 0;
-    if (s > 0) {
-        k = (s - 1) >> 1;
-        which = ((s - 1) & 1) ? 2 : 1;
-    }
-    for (int a = t; a < P; a += NT) {
-        const double2 v = I.cs[(a == k ? which : 0) * P + a];
-        R2 r;
-        r.x = (R)v.x;
-        r.y = (R)v.y;
-        scs[a] = r;
-    }
-    __syncthreads();
-    for (int i = t; i < N; i += NT) {  // initial Ry layer on |0>: a product state
-        R v = (R)1;
-        for (int q = 0; q < n; ++q) v *= ((i >> q) & 1) ? scs[q].y : scs[q].x;
-        R2 r;
-        r.x = v;
-        r.y = (R)0;
-        psi[i] = r;
-    }
-    __syncthreads();
-    for (int layer = 1; layer <= I.d; ++layer) {
-        for (int q = 0; q < n; ++q) {
-            const R c = scs[layer * n + q].x, sn = scs[layer * n + q].y;
-            for (int p = t; p < N / 2; p += NT) {
-                const int i0 = ((p >> q) << (q + 1)) | (p & ((1 << q) - 1)), i1 = i0 | (1 << q);
-                R2 a = psi[i0], b = psi[i1];
-                if (q == 0) {  // the CZ ring (diagonal) precedes the layer's rotations
-                    if (czring_parity(i0, n)) a = neg2(a);
-                    if (czring_parity(i1, n)) b = neg2(b);
-                }
-                R2 u, v;
-                u.x = c * a.x - sn * b.x;
-                u.y = c * a.y - sn * b.y;
-                v.x = sn * a.x + c * b.x;
-                v.y = sn * a.y + c * b.y;
-                psi[i0] = u;
-                psi[i1] = v;
-            }
-            __syncthreads();
-        }
-    }
-}
-
 template <typename R>
 __device__ __forceinline__ void load4(const typename V2<R>::t* p, typename V2<R>::t (&v)[4]);
 template <>
@@ -263,7 +190,7 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
         sxm[t] = m < L ? I.xm[m] : 0u;
         szm[t] = m < L ? I.zm[m] : 0u;
     }
-    build_state<R>(psi, scs, I, s);
+    build_state<R>(psi, scs, I.n, I.d, I.P, I.cs, s);
 
     const int lane = t & 31, warp = t >> 5;
     const int lb = (warp >> 1) * 4 + (lane >> 3);

@@ -32,6 +32,7 @@ EXPORTED = [
     "dvqls_pauli_decompose", "dvqls_pauli_decompose_banded",
     "dvqls_cost", "dvqls_cost_grad", "dvqls_cost_grad_batched",
     "dvqls_profile_enable", "dvqls_profile_read", "dvqls_cost_grad_noalloc",
+    "dvqls_circuit_cost_grad_fp64", "dvqls_fidelity", "dvqls_lcu_solve", "dvqls_optimize",
 ]
 
 
@@ -53,6 +54,17 @@ class dvqls_lcu(ctypes.Structure):
 class dvqls_instance(ctypes.Structure):
     _fields_ = [("ansatz", dvqls_ansatz), ("lcu", dvqls_lcu), ("alpha", ctypes.c_void_p),
                 ("b", ctypes.c_void_p)]
+
+
+class dvqls_adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("max_iter", ctypes.c_int), ("target_fidelity", ctypes.c_double),
+                ("precision", ctypes.c_int)]
+
+
+class dvqls_opt_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("cost", ctypes.c_double),
+                ("fidelity", ctypes.c_double)]
 
 
 _lib = None
@@ -88,6 +100,13 @@ def lib():
                                          ctypes.POINTER(ctypes.c_double)]
         L.dvqls_cost_grad_noalloc.argtypes = [vp, ctypes.POINTER(dvqls_ansatz), dp, ctypes.POINTER(dvqls_lcu), dp,
                                               ctypes.c_int, dp, dp]
+        L.dvqls_circuit_cost_grad_fp64.argtypes = [vp, ctypes.POINTER(dvqls_ansatz), dp, ctypes.POINTER(dvqls_lcu),
+                                                   dp, dp, dp, dp, dp]
+        L.dvqls_fidelity.argtypes = [vp, ctypes.POINTER(dvqls_ansatz), dp, dp, dp]
+        L.dvqls_lcu_solve.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dvqls_lcu), dp, ctypes.c_double, ctypes.c_int,
+                                      dp, ip, ctypes.POINTER(ctypes.c_double)]
+        L.dvqls_optimize.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dvqls_instance), dp, ctypes.POINTER(dvqls_adam),
+                                     dp, ctypes.POINTER(dvqls_opt_result)]
         _lib = L
     return _lib
 
@@ -199,3 +218,33 @@ def dvqls_cost_grad_noalloc(stream, ansatz, alpha, lcu, b, precision, cost, grad
     status code instead of raising, since there is no context to describe it."""
     return lib().dvqls_cost_grad_noalloc(stream, ctypes.byref(ansatz), ptr(alpha), ctypes.byref(lcu), ptr(b),
                                          int(precision), ptr(cost), ptr(grad))
+
+
+def dvqls_circuit_cost_grad_fp64(ctx, ansatz, alpha, lcu, b, cost, grad, beta=None, delta=None):
+    _check(ctx, lib().dvqls_circuit_cost_grad_fp64(ctx, ctypes.byref(ansatz), ptr(alpha), ctypes.byref(lcu), ptr(b),
+                                                   ptr(cost), ptr(grad), ptr(beta), ptr(delta)))
+
+
+def dvqls_fidelity(ctx, ansatz, alpha, xhat, F):
+    _check(ctx, lib().dvqls_fidelity(ctx, ctypes.byref(ansatz), ptr(alpha), ptr(xhat), ptr(F)))
+
+
+def dvqls_lcu_solve(ctx, n, lcu, b, tol, max_iter, x):
+    """Returns (iterations, relative residual)."""
+    it, rr = ctypes.c_int(), ctypes.c_double()
+    _check(ctx, lib().dvqls_lcu_solve(ctx, int(n), ctypes.byref(lcu), ptr(b), float(tol), int(max_iter), ptr(x),
+                                      ctypes.byref(it), ctypes.byref(rr)))
+    return it.value, rr.value
+
+
+def make_adam(lr=0.02, beta1=0.9, beta2=0.999, eps=1e-8, max_iter=5000, target_fidelity=0.9999,
+              precision=DVQLS_FP64):
+    return dvqls_adam(lr, beta1, beta2, eps, int(max_iter), target_fidelity, int(precision))
+
+
+def dvqls_optimize(ctx, instances, xhat, opt, alpha_out):
+    """Returns a list of dvqls_opt_result, one per instance."""
+    res = (dvqls_opt_result * len(instances))()
+    _check(ctx, lib().dvqls_optimize(ctx, len(instances), instances, ptr(xhat), ctypes.byref(opt), ptr(alpha_out),
+                                     res))
+    return list(res)
