@@ -30,8 +30,10 @@
 namespace dvqls {
 
 constexpr int TT = 64;    // term tile edge (l and m)
-constexpr int NT = 256;   // threads per CTA
-constexpr int JC = 32;    // amplitudes per chunk
+constexpr int KG = 2;     // K-groups per CTA (each sums half of every chunk)
+constexpr int KSLOT = 144; // task slots per K-group (136 used on diagonal tiles, 128 off-diagonal)
+constexpr int NT = KG * KSLOT;  // threads per CTA (9 warps)
+constexpr int JC = 64;    // amplitudes per chunk (a power of two)
 constexpr int MAX_ANGLES = 1024;
 
 struct Inst {
@@ -162,15 +164,35 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* red) {
     return s;  // valid in thread 0
 }
 
+// One work item (see the file comment).  Item u of a shift: u < T is the
+// diagonal tile (u, u); u >= T is half h of the off-diagonal tile pair
+// (tl < tm) number (u - T) / 2.  Only blocks with l <= m are computed:
+// beta_ml = conj(beta_lm) exactly, so the pair contributes 2 Re(w_lm G~_lm) to
+// D_s and nothing to its imaginary part.  Threads: two K-groups of KSLOT task
+// slots; each active slot owns one 4 x 4 block of complex products and
+// accumulates it over its K-group's half of every chunk, in registers.
 template <typename R>
 __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint32_t* smask, double2* red) {
     using R2 = typename V2<R>::t;
     const int n = I.n, N = 1 << n, L = I.L, T = I.T, ks = I.ks, t = threadIdx.x;
     const int ksi = local % ks;
     const int rest = local / ks;
-    const int tile = rest % (T * T), s = rest / (T * T);
-    const int tl = tile / T, tm = tile % T;
-    const bool diag = tl == tm;
+    const int u = rest % (T * T), s = rest / (T * T);
+    int tl, tm, half = 0;
+    const bool diag = u < T;
+    if (diag) {
+        tl = tm = u;
+    } else {
+        const int v = u - T, pr = v >> 1;
+        half = v & 1;
+        int a = 0, rem = pr;
+        while (rem >= T - 1 - a) {
+            rem -= T - 1 - a;
+            ++a;
+        }
+        tl = a;
+        tm = a + 1 + rem;
+    }
     const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
 
     R2* psi = reinterpret_cast<R2*>(smem);
@@ -182,6 +204,8 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
     uint32_t* szl = smask + TT;
     uint32_t* sxm = smask + 2 * TT;
     uint32_t* szm = smask + 3 * TT;
+    const int mofs = diag ? 0 : half * (TT / 2);  // first m column of this item within tile tm
+    const int mcols = diag ? TT : TT / 2;
     if (t < TT) {
         const int l = tl * TT + t;
         sxl[t] = l < L ? I.xm[l] : 0u;
@@ -192,9 +216,25 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
     }
     build_state<R>(psi, scs, I.n, I.d, I.P, I.cs, s);
 
-    const int lane = t & 31, warp = t >> 5;
-    const int lb = (warp >> 1) * 4 + (lane >> 3);
-    const int mb = (warp & 1) * 8 + (lane & 7);
+    // Task of this thread: block (a, b) = rows 4a.., columns 4b.. of the tile.
+    const int g = t / KSLOT, slot = t % KSLOT;
+    const int ntask = diag ? 136 : 128;
+    const bool active = slot < ntask;
+    int ba = 0, bb = 0;
+    if (active) {
+        if (diag) {  // upper-triangle blocks (a <= b) of the 16 x 16 block grid, row-major
+            int rem = slot;
+            while (rem >= 16 - ba) {
+                rem -= 16 - ba;
+                ++ba;
+            }
+            bb = ba + rem;
+        } else {
+            ba = slot >> 3;
+            bb = half * 8 + (slot & 7);
+        }
+    }
+    const R2* Pm = diag ? Phl : Phm;
     R are[4][4], aim[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -205,8 +245,13 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
     const int lcount = min(TT, L - tl * TT), mcount = min(TT, L - tm * TT);
 
     for (int j0 = kbeg; j0 < kend; j0 += JC) {
+        // phi chunk rows jj = 0..JC-1: a warp takes 32 consecutive rows of one
+        // term, so its gather reads one aligned 32-amplitude block of psi
+        // (permuted by the low bits of x_l): no bank conflicts.  Rows are
+        // stored with the 4-term groups XOR-swizzled by the row index.
         for (int e = t; e < JC * TT; e += NT) {
-            const int jj = e / TT, l = e % TT, j = j0 + jj;
+            const int jj = e & (JC - 1), l = e / JC, j = j0 + jj;
+            const int at = jj * TT + (l ^ ((jj & 15) << 2));
             R2 v;
             v.x = v.y = (R)0;
             if (j < kend && l < lcount) {
@@ -214,114 +259,140 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
                 v = psi[src];
                 if (__popc(szl[l] & uint32_t(src)) & 1) v = neg2(v);
             }
-            Phl[e] = v;
-            if (!diag) {
-                R2 u;
-                u.x = u.y = (R)0;
-                if (j < kend && l < mcount) {
-                    const int src = (j ^ int(sxm[l])) & (N - 1);
-                    u = psi[src];
-                    if (__popc(szm[l] & uint32_t(src)) & 1) u = neg2(u);
+            Phl[at] = v;
+        }
+        if (!diag) {
+            for (int e = t; e < JC * mcols; e += NT) {
+                const int jj = e & (JC - 1), m = mofs + e / JC, j = j0 + jj;
+                const int at = jj * TT + (m ^ ((jj & 15) << 2));
+                R2 v;
+                v.x = v.y = (R)0;
+                if (j < kend && m < mcount) {
+                    const int src = (j ^ int(sxm[m])) & (N - 1);
+                    v = psi[src];
+                    if (__popc(szm[m] & uint32_t(src)) & 1) v = neg2(v);
                 }
-                Phm[e] = u;
+                Phm[at] = v;
             }
         }
         if (diag && t < JC) {
             R2 v;
             v.x = v.y = (R)0;
             if (j0 + t < kend) {
-                const double2 bb = I.b[j0 + t];
-                v.x = (R)bb.x;
-                v.y = (R)bb.y;
+                const double2 b2 = I.b[j0 + t];
+                v.x = (R)b2.x;
+                v.y = (R)b2.y;
             }
             bch[t] = v;
         }
         __syncthreads();
-        const R2* Pm = diag ? Phl : Phm;
-        R cre[4][4], cim[4][4];  // chunk accumulators (two-level summation)
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) cre[a][b] = cim[a][b] = (R)0;
+        if (active) {
+            const int r0 = g * (JC / KG);
 #pragma unroll 4
-        for (int jj = 0; jj < JC; ++jj) {
-            R2 lv[4], mv[4];
-            load4<R>(Phl + jj * TT + lb * 4, lv);
-            load4<R>(Pm + jj * TT + mb * 4, mv);
+            for (int jj = r0; jj < r0 + JC / KG; ++jj) {
+                R2 lv[4], mv[4];
+                const int sw = (jj & 15) << 2;
+                load4<R>(Phl + jj * TT + ((ba * 4) ^ sw), lv);
+                load4<R>(Pm + jj * TT + ((bb * 4) ^ sw), mv);
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    cre[a][b] = fma(lv[a].x, mv[b].x, cre[a][b]);
-                    cre[a][b] = fma(lv[a].y, mv[b].y, cre[a][b]);
-                    cim[a][b] = fma(lv[a].x, mv[b].y, cim[a][b]);
-                    cim[a][b] = fma(-lv[a].y, mv[b].x, cim[a][b]);
-                }
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                are[a][b] += cre[a][b];
-                aim[a][b] += cim[a][b];
+                    for (int b = 0; b < 4; ++b) {
+                        are[a][b] = fma(lv[a].x, mv[b].x, are[a][b]);
+                        are[a][b] = fma(lv[a].y, mv[b].y, are[a][b]);
+                        aim[a][b] = fma(lv[a].x, mv[b].y, aim[a][b]);
+                        aim[a][b] = fma(-lv[a].y, mv[b].x, aim[a][b]);
+                    }
             }
-        if (diag) {  // delta~_l partial: thread t owns l = t % 64, chunk rows (t / 64) * 8 ..
-            const int l = t % TT, g = t / TT;
+        }
+        if (diag && t < 4 * TT) {  // delta~_l partial: thread t owns l = t % 64, a quarter of the chunk rows
+            const int l = t % TT, q = t / TT;
 #pragma unroll
-            for (int jj = g * (JC / 4); jj < (g + 1) * (JC / 4); ++jj) {
-                const R2 v = Phl[jj * TT + l], bb = bch[jj];
-                dacc.x = fma(bb.x, v.x, fma(bb.y, v.y, dacc.x));
-                dacc.y = fma(bb.x, v.y, fma(-bb.y, v.x, dacc.y));
+            for (int jj = q * (JC / 4); jj < (q + 1) * (JC / 4); ++jj) {
+                const R2 v = Phl[jj * TT + (l ^ ((jj & 15) << 2))], b2 = bch[jj];
+                dacc.x = fma(b2.x, v.x, fma(b2.y, v.y, dacc.x));
+                dacc.y = fma(b2.x, v.y, fma(-b2.y, v.x, dacc.y));
             }
         }
         __syncthreads();
     }
 
-    // FP64 weighting of the tile: contribution to D_s.
-    double2 dsum = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int l = tl * TT + lb * 4 + a, m = tm * TT + mb * 4 + b;
-            if (l < L && m < L) {
-                const double2 w = I.w[(long long)l * L + m];
-                const double gr = (double)are[a][b], gi = (double)aim[a][b];
-                dsum.x += w.x * gr - w.y * gi;
-                dsum.y += w.x * gi + w.y * gr;
-            }
-        }
-    const long long slot = ((long long)(s * T + tl) * T + tm) * ks + ksi;
-    const double2 dtot = block_sum2(dsum, red);
-    if (t == 0) I.Dpart[slot] = dtot;
-    if (s == 0 && I.Gpart) {
-        R2* G = reinterpret_cast<R2*>(I.Gpart) + (long long)ksi * L * L;
+    // Add the second K-group's block into the first (through shared memory).
+    R* kred = reinterpret_cast<R*>(Phl);  // chunk buffer is free now
+    if (g == 1 && active) {
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const int l = tl * TT + lb * 4 + a, m = tm * TT + mb * 4 + b;
-                if (l < L && m < L) {
-                    R2 v;
-                    v.x = are[a][b];
-                    v.y = aim[a][b];
-                    G[(long long)l * L + m] = v;
-                }
+                kred[(a * 4 + b) * KSLOT + slot] = are[a][b];
+                kred[(16 + a * 4 + b) * KSLOT + slot] = aim[a][b];
             }
     }
+    __syncthreads();
+    double2 dsum = make_double2(0.0, 0.0);
+    if (g == 0 && active) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                are[a][b] += kred[(a * 4 + b) * KSLOT + slot];
+                aim[a][b] += kred[(16 + a * 4 + b) * KSLOT + slot];
+            }
+        // FP64 weighting: contribution of this block (and its mirror) to D_s.
+        const bool mirror = !(diag && ba == bb);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int l = tl * TT + ba * 4 + a, m = tm * TT + bb * 4 + b;
+                if (l < L && m < L) {
+                    const double2 w = I.w[(long long)l * L + m];
+                    const double gr = (double)are[a][b], gi = (double)aim[a][b];
+                    const double re = w.x * gr - w.y * gi;
+                    if (mirror) {
+                        dsum.x += 2.0 * re;
+                    } else {
+                        dsum.x += re;
+                        dsum.y += w.x * gi + w.y * gr;
+                    }
+                }
+            }
+        if (s == 0 && I.Gpart) {
+            R2* G = reinterpret_cast<R2*>(I.Gpart) + (long long)ksi * L * L;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int l = tl * TT + ba * 4 + a, m = tm * TT + bb * 4 + b;
+                    if (l < L && m < L) {
+                        R2 v;
+                        v.x = are[a][b];
+                        v.y = aim[a][b];
+                        G[(long long)l * L + m] = v;
+                        if (mirror) {
+                            v.y = -v.y;
+                            G[(long long)m * L + l] = v;
+                        }
+                    }
+                }
+        }
+    }
+    const long long slotD = ((long long)s * T * T + u) * ks + ksi;
+    const double2 dtot = block_sum2(dsum, red);
+    if (t == 0) I.Dpart[slotD] = dtot;
     if (diag) {
-        // Reduce the four row-group partials of each l, then weight by ctil in FP64.
-        R2* dred = Phl;  // chunk buffer is free now
-        dred[t] = dacc;
+        // Reduce the four row-quarter partials of each l, then weight by ctil in FP64.
+        R2* dred = Phm;  // free (diagonal items do not use it)
+        if (t < 4 * TT) dred[t] = dacc;
         __syncthreads();
         double2 tsum = make_double2(0.0, 0.0);
         if (t < TT) {
             const int l = tl * TT + t;
             R2 v = dred[t];
 #pragma unroll
-            for (int g = 1; g < 4; ++g) {
-                v.x += dred[g * TT + t].x;
-                v.y += dred[g * TT + t].y;
+            for (int q = 1; q < 4; ++q) {
+                v.x += dred[q * TT + t].x;
+                v.y += dred[q * TT + t].y;
             }
             if (l < L) {
                 const double2 c = I.ctil[l];
@@ -347,7 +418,7 @@ __device__ __forceinline__ int find_instance(const Inst* insts, int count, long 
 }
 
 template <typename R>
-__global__ void __launch_bounds__(NT) k_terms_smem(const Inst* __restrict__ insts, int count, long long total,
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 1) k_terms_smem(const Inst* __restrict__ insts, int count, long long total,
                                                   unsigned long long* queue) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t smask[4 * TT];
