@@ -260,6 +260,53 @@ int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* inst, const 
                    const dvqls_adam* opt, double* alpha_out, dvqls_opt_result* results);
 
 /* ------------------------------------------------------------------------
+ * Learned warm start.  Algorithm 1, Step 3 initialises theta randomly; this
+ * replaces that step with a prediction (the paper has no learned
+ * initialisation; random or fixed initialisation stays the fallback).  A
+ * small MLP maps a problem description (features) to initial angles:
+ *   h1 = GELU(W1 x + b1), h2 = GELU(W2 h1 + b2), y = W3 h2 + b3,
+ *   GELU(z) = z (1 + erf(z / sqrt 2)) / 2,
+ * trained on the GPU by these kernels (FP32) on the masked mean squared
+ * error sum M (y - t)^2 / sum M with Adam (beta 0.9, 0.999, eps 1e-8).
+ * Parameters are one flat FP32 vector: W1 [H x I], b1 [H], W2 [H x H],
+ * b2 [H], W3 [O x H], b3 [O] (row-major), dvqls_ws_param_count() floats.
+ * Batch arrays are row-major: feats [batch x I], target and mask
+ * [batch x O] (mask 1 where the target entry counts, else 0).  Pointers may
+ * be host or device memory.
+ */
+typedef struct dvqls_ws dvqls_ws;
+
+/* Number of parameters, or -1 for a dimension < 1. */
+long long dvqls_ws_param_count(int in_dim, int hidden, int out_dim);
+
+/* New network on ctx's device with the given initial parameters (the
+ * caller draws them); Adam moments start at zero. */
+int dvqls_ws_create(dvqls_ctx* ctx, int in_dim, int hidden, int out_dim, const float* params,
+                    dvqls_ws** out);
+void dvqls_ws_destroy(dvqls_ws* ws);
+
+/* out [batch x O] = y(feats). */
+int dvqls_ws_infer(dvqls_ws* ws, int batch, const float* feats, float* out);
+
+/* Loss (may be NULL) and its gradient with respect to the parameters
+ * (param_count floats), without updating anything. */
+int dvqls_ws_grad(dvqls_ws* ws, int batch, const float* feats, const float* target,
+                  const float* mask, float* loss, float* grad);
+
+/* One Adam step on the batch with step size lr.  loss (may be NULL) is the
+ * batch loss before the step; passing NULL avoids a synchronisation. */
+int dvqls_ws_train_step(dvqls_ws* ws, int batch, const float* feats, const float* target,
+                        const float* mask, float lr, float* loss);
+
+int dvqls_ws_get_params(dvqls_ws* ws, float* params);
+
+/* Checkpoint: "DVQLSWS1", int32 I, H, O, int64 Adam step, then the
+ * parameters and both Adam moments (FP32).  Loading restores training
+ * state exactly. */
+int dvqls_ws_save(dvqls_ws* ws, const char* path);
+int dvqls_ws_load(dvqls_ctx* ctx, const char* path, dvqls_ws** out);
+
+/* ------------------------------------------------------------------------
  * Allocation-free cost and gradient.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate GPU memory, such as
  * code running inside a memory pool or allocator that owns the whole device,

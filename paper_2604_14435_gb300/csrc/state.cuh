@@ -65,23 +65,64 @@ __device__ void build_state(typename V2<R>::t* psi, typename V2<R>::t* scs, int 
         psi[i] = r;
     }
     __syncthreads();
+    // Layers: the CZ ring (diagonal) is applied while loading the first pass;
+    // the Ry rotations of qubits q and q+1 are fused into one pass over groups
+    // of four amplitudes (bits q, q+1 = 00, 01, 10, 11), so a layer takes
+    // ceil(n/2) passes and barriers.
     for (int layer = 1; layer <= d; ++layer) {
-        for (int q = 0; q < n; ++q) {
-            const R c = scs[layer * n + q].x, sn = scs[layer * n + q].y;
-            for (int p = t; p < N / 2; p += NTH) {
-                const int i0 = ((p >> q) << (q + 1)) | (p & ((1 << q) - 1)), i1 = i0 | (1 << q);
-                R2 a = psi[i0], b = psi[i1];
-                if (q == 0) {  // the CZ ring (diagonal) precedes the layer's rotations
-                    if (czring_parity(i0, n)) a = neg2(a);
-                    if (czring_parity(i1, n)) b = neg2(b);
+        for (int q = 0; q < n; q += 2) {
+            const R c0 = scs[layer * n + q].x, s0 = scs[layer * n + q].y;
+            if (q + 1 < n) {
+                const R c1 = scs[layer * n + q + 1].x, s1 = scs[layer * n + q + 1].y;
+                for (int p = t; p < N / 4; p += NTH) {
+                    const int i00 = ((p >> q) << (q + 2)) | (p & ((1 << q) - 1));
+                    const int i01 = i00 | (1 << q), i10 = i00 | (2 << q), i11 = i00 | (3 << q);
+                    R2 a = psi[i00], b = psi[i01], c = psi[i10], e = psi[i11];
+                    if (q == 0) {
+                        if (czring_parity(i00, n)) a = neg2(a);
+                        if (czring_parity(i01, n)) b = neg2(b);
+                        if (czring_parity(i10, n)) c = neg2(c);
+                        if (czring_parity(i11, n)) e = neg2(e);
+                    }
+                    R2 a1, b1, c1r, e1;  // Ry on qubit q: pairs (a, b) and (c, e)
+                    a1.x = c0 * a.x - s0 * b.x;
+                    a1.y = c0 * a.y - s0 * b.y;
+                    b1.x = s0 * a.x + c0 * b.x;
+                    b1.y = s0 * a.y + c0 * b.y;
+                    c1r.x = c0 * c.x - s0 * e.x;
+                    c1r.y = c0 * c.y - s0 * e.y;
+                    e1.x = s0 * c.x + c0 * e.x;
+                    e1.y = s0 * c.y + c0 * e.y;
+                    R2 u;  // Ry on qubit q+1: pairs (a1, c1r) and (b1, e1)
+                    u.x = c1 * a1.x - s1 * c1r.x;
+                    u.y = c1 * a1.y - s1 * c1r.y;
+                    psi[i00] = u;
+                    u.x = s1 * a1.x + c1 * c1r.x;
+                    u.y = s1 * a1.y + c1 * c1r.y;
+                    psi[i10] = u;
+                    u.x = c1 * b1.x - s1 * e1.x;
+                    u.y = c1 * b1.y - s1 * e1.y;
+                    psi[i01] = u;
+                    u.x = s1 * b1.x + c1 * e1.x;
+                    u.y = s1 * b1.y + c1 * e1.y;
+                    psi[i11] = u;
                 }
-                R2 u, v;
-                u.x = c * a.x - sn * b.x;
-                u.y = c * a.y - sn * b.y;
-                v.x = sn * a.x + c * b.x;
-                v.y = sn * a.y + c * b.y;
-                psi[i0] = u;
-                psi[i1] = v;
+            } else {
+                for (int p = t; p < N / 2; p += NTH) {
+                    const int i0 = ((p >> q) << (q + 1)) | (p & ((1 << q) - 1)), i1 = i0 | (1 << q);
+                    R2 a = psi[i0], b = psi[i1];
+                    if (q == 0) {
+                        if (czring_parity(i0, n)) a = neg2(a);
+                        if (czring_parity(i1, n)) b = neg2(b);
+                    }
+                    R2 u, v;
+                    u.x = c0 * a.x - s0 * b.x;
+                    u.y = c0 * a.y - s0 * b.y;
+                    v.x = s0 * a.x + c0 * b.x;
+                    v.y = s0 * a.y + c0 * b.y;
+                    psi[i0] = u;
+                    psi[i1] = v;
+                }
             }
             __syncthreads();
         }

@@ -33,6 +33,8 @@ EXPORTED = [
     "dvqls_cost", "dvqls_cost_grad", "dvqls_cost_grad_batched",
     "dvqls_profile_enable", "dvqls_profile_read", "dvqls_cost_grad_noalloc",
     "dvqls_circuit_cost_grad_fp64", "dvqls_fidelity", "dvqls_lcu_solve", "dvqls_optimize",
+    "dvqls_ws_param_count", "dvqls_ws_create", "dvqls_ws_destroy", "dvqls_ws_infer", "dvqls_ws_grad",
+    "dvqls_ws_train_step", "dvqls_ws_get_params", "dvqls_ws_save", "dvqls_ws_load",
 ]
 
 
@@ -107,6 +109,17 @@ def lib():
                                       dp, ip, ctypes.POINTER(ctypes.c_double)]
         L.dvqls_optimize.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dvqls_instance), dp, ctypes.POINTER(dvqls_adam),
                                      dp, ctypes.POINTER(dvqls_opt_result)]
+        L.dvqls_ws_param_count.argtypes = [ctypes.c_int] * 3
+        L.dvqls_ws_param_count.restype = ctypes.c_longlong
+        L.dvqls_ws_create.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_void_p)]
+        L.dvqls_ws_destroy.argtypes = [vp]
+        L.dvqls_ws_destroy.restype = None
+        L.dvqls_ws_infer.argtypes = [vp, ctypes.c_int, vp, vp]
+        L.dvqls_ws_grad.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_float), vp]
+        L.dvqls_ws_train_step.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]
+        L.dvqls_ws_get_params.argtypes = [vp, vp]
+        L.dvqls_ws_save.argtypes = [vp, ctypes.c_char_p]
+        L.dvqls_ws_load.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
         _lib = L
     return _lib
 
@@ -248,3 +261,63 @@ def dvqls_optimize(ctx, instances, xhat, opt, alpha_out):
     _check(ctx, lib().dvqls_optimize(ctx, len(instances), instances, ptr(xhat), ctypes.byref(opt), ptr(alpha_out),
                                      res))
     return list(res)
+
+
+# -------------------------------------------------------------- warm start
+# A dvqls_ws handle is paired with its context so errors can be described.
+
+
+class WarmStart:
+    """Handle of a dvqls_ws network (ctx, ws pointer, dimensions)."""
+
+    def __init__(self, ctx, handle, I, H, O):
+        self.ctx, self.handle, self.I, self.H, self.O = ctx, handle, I, H, O
+
+
+def dvqls_ws_param_count(I, H, O):
+    return lib().dvqls_ws_param_count(int(I), int(H), int(O))
+
+
+def dvqls_ws_create(ctx, I, H, O, params):
+    h = ctypes.c_void_p()
+    _check(ctx, lib().dvqls_ws_create(ctx, int(I), int(H), int(O), ptr(params), ctypes.byref(h)))
+    return WarmStart(ctx, h, I, H, O)
+
+
+def dvqls_ws_destroy(ws):
+    lib().dvqls_ws_destroy(ws.handle)
+
+
+def dvqls_ws_infer(ws, batch, feats, out):
+    _check(ws.ctx, lib().dvqls_ws_infer(ws.handle, int(batch), ptr(feats), ptr(out)))
+
+
+def dvqls_ws_grad(ws, batch, feats, target, mask, grad):
+    loss = ctypes.c_float()
+    _check(ws.ctx, lib().dvqls_ws_grad(ws.handle, int(batch), ptr(feats), ptr(target), ptr(mask), ctypes.byref(loss),
+                                       ptr(grad)))
+    return loss.value
+
+
+def dvqls_ws_train_step(ws, batch, feats, target, mask, lr, want_loss=True):
+    loss = ctypes.c_float()
+    _check(ws.ctx, lib().dvqls_ws_train_step(ws.handle, int(batch), ptr(feats), ptr(target), ptr(mask), float(lr),
+                                             ctypes.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def dvqls_ws_get_params(ws, params):
+    _check(ws.ctx, lib().dvqls_ws_get_params(ws.handle, ptr(params)))
+
+
+def dvqls_ws_save(ws, path):
+    _check(ws.ctx, lib().dvqls_ws_save(ws.handle, str(path).encode()))
+
+
+def dvqls_ws_load(ctx, path):
+    h = ctypes.c_void_p()
+    _check(ctx, lib().dvqls_ws_load(ctx, str(path).encode(), ctypes.byref(h)))
+    with open(path, "rb") as f:
+        f.read(8)
+        I, H, O = np.frombuffer(f.read(12), dtype=np.int32)
+    return WarmStart(ctx, h, int(I), int(H), int(O))
