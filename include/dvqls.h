@@ -238,6 +238,8 @@ typedef struct {
     int max_iter;                 /* updates at most                          */
     double target_fidelity;       /* stop an instance once F >= this          */
     int precision;                /* dvqls_precision of the cost pass         */
+    const double* targets;        /* NULL, or one target per instance (host
+                                     memory) used instead of target_fidelity */
 } dvqls_adam;
 
 typedef struct {

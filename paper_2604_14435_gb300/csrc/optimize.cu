@@ -446,7 +446,8 @@ extern "C" int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* i
             results[i].iters = it;
             results[i].cost = hC[a];
             results[i].fidelity = hF[i];
-            if (hF[i] >= opt->target_fidelity) results[i].converged = 1;
+            const double target = opt->targets ? opt->targets[i] : opt->target_fidelity;
+            if (hF[i] >= target) results[i].converged = 1;
             else if (it < opt->max_iter) still.push_back(i);
         }
         if (still.size() != active.size()) {

@@ -61,7 +61,7 @@ class dvqls_instance(ctypes.Structure):
 class dvqls_adam(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("eps", ctypes.c_double), ("max_iter", ctypes.c_int), ("target_fidelity", ctypes.c_double),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("targets", ctypes.c_void_p)]
 
 
 class dvqls_opt_result(ctypes.Structure):
@@ -251,8 +251,10 @@ def dvqls_lcu_solve(ctx, n, lcu, b, tol, max_iter, x):
 
 
 def make_adam(lr=0.02, beta1=0.9, beta2=0.999, eps=1e-8, max_iter=5000, target_fidelity=0.9999,
-              precision=DVQLS_FP64):
-    return dvqls_adam(lr, beta1, beta2, eps, int(max_iter), target_fidelity, int(precision))
+              precision=DVQLS_FP64, targets=None):
+    """targets: optional float64 numpy array, one fidelity target per instance
+    (keep it alive for the call)."""
+    return dvqls_adam(lr, beta1, beta2, eps, int(max_iter), target_fidelity, int(precision), ptr(targets))
 
 
 def dvqls_optimize(ctx, instances, xhat, opt, alpha_out):

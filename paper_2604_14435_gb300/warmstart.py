@@ -1,0 +1,233 @@
+"""Learned warm start for D-VQLS (replaces the random initialisation of
+Algorithm 1, Step 3 with a prediction; random / fixed initialisation stays
+the fallback and the exact cost and fidelity judge the result).
+
+Every numeric step runs in the CUDA library: decomposition
+(dvqls_pauli_decompose_banded), classical solve (dvqls_lcu_solve), optimizer
+runs (dvqls_optimize: batched cost + parameter-shift gradient, FP64
+fidelity), network training and inference (dvqls_ws_*).  This module only
+orchestrates the calls and builds the feature / target arrays.
+
+Problem family (tridiagonal Toeplitz, Sec. 2.5.1): n in 6..10, a ~ U(2,4),
+c ~ U(-1.5,-0.5) with a > 2|c|, b = |+>^n, top-64 Pauli terms, depth-4
+Ry + CZ-ring ansatz (P = 5n <= 50 angles).  Features: [a/4, c/1.5,
+one-hot(n - 6) (5)].  Targets: the converged angles of runs started from the
+|+> initialisation (first-layer angles pi/2, the rest 0: with an even depth
+the CZ rings cancel and V|0> = |+>^n), zero-padded to 50 with a mask.
+"""
+import time
+
+import numpy as np
+
+from . import dvqls as D
+from . import workloads as wl
+
+DEPTH = 4
+N_MIN, N_MAX = 6, 10
+P_MAX = N_MAX * (DEPTH + 1)
+FEATURES = 2 + (N_MAX - N_MIN + 1)
+L_TERMS = 64
+
+
+def features(a, c, n):
+    f = np.zeros(FEATURES, dtype=np.float32)
+    f[0] = a / 4.0
+    f[1] = c / 1.5
+    f[2 + n - N_MIN] = 1.0
+    return f
+
+
+def plus_init(n, d=DEPTH):
+    alpha = np.zeros(n * (d + 1))
+    alpha[:n] = 0.5 * np.pi
+    return alpha
+
+
+class Problem:
+    """One system prepared on the GPU: LCU (host copies), b, xhat, features."""
+
+    def __init__(self, ctx, seed, n):
+        inst = wl.throughput_instance(seed, n=n, d=DEPTH, L_max=L_TERMS)
+        self.seed, self.n, self.a, self.c = seed, n, inst["a"], inst["c"]
+        self.P = n * (DEPTH + 1)
+        coef = np.zeros(2 * L_TERMS)
+        xm = np.zeros(L_TERMS, np.uint32)
+        zm = np.zeros(L_TERMS, np.uint32)
+        bands = np.ascontiguousarray(inst["bands"], dtype=np.float64)
+        L, _, _ = D.dvqls_pauli_decompose_banded(ctx, n, inst["offsets"], bands, 0.0, L_TERMS, coef, xm, zm)
+        self.L = L
+        self.coef, self.xm, self.zm = coef[: 2 * L].copy(), xm[:L].copy(), zm[:L].copy()
+        self.b = np.ascontiguousarray(inst["b"]).view(np.float64).copy()
+        self.lcu = D.make_lcu(L, self.coef, self.xm, self.zm)
+        x = np.zeros(2 << n)
+        D.dvqls_lcu_solve(ctx, n, self.lcu, self.b, 1e-12, 20000, x)
+        self.xhat = x
+        self.feat = features(self.a, self.c, n)
+
+
+def prepare(ctx, seeds_and_n):
+    return [Problem(ctx, s, n) for s, n in seeds_and_n]
+
+
+def optimize(ctx, problems, inits, precision=D.DVQLS_FP32, lr=0.02, max_iter=3000, target=0.9999):
+    """Adam runs of all problems in lock step; `target` is one fidelity for all
+    or an array with one per problem.  Returns (results, final angles, seconds)."""
+    keep = [np.ascontiguousarray(a, dtype=np.float64) for a in inits]
+    items = [(D.make_ansatz(p.n, DEPTH), p.lcu, a, p.b) for p, a in zip(problems, keep)]
+    inst = D.make_instances(items)
+    xhat = np.concatenate([p.xhat for p in problems])
+    out = np.zeros(sum(p.P for p in problems))
+    targets = None
+    if np.ndim(target) == 1:
+        targets = np.ascontiguousarray(target, dtype=np.float64)
+        target = 1.0
+    opt = D.make_adam(lr=lr, max_iter=max_iter, target_fidelity=target, precision=precision, targets=targets)
+    t0 = time.perf_counter()
+    res = D.dvqls_optimize(ctx, inst, xhat, opt, out)
+    secs = time.perf_counter() - t0
+    alphas, off = [], 0
+    for p in problems:
+        alphas.append(out[off:off + p.P].copy())
+        off += p.P
+    return res, alphas, secs
+
+
+def training_arrays(problems, alphas):
+    X = np.stack([p.feat for p in problems]).astype(np.float32)
+    Y = np.zeros((len(problems), P_MAX), np.float32)
+    M = np.zeros((len(problems), P_MAX), np.float32)
+    for k, (p, a) in enumerate(zip(problems, alphas)):
+        Y[k, : p.P] = a
+        M[k, : p.P] = 1.0
+    return X, Y, M
+
+
+def init_params(hidden, seed):
+    """Seeded uniform(+-sqrt(6/(fan_in+fan_out))) weights, zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in ((FEATURES, hidden), (hidden, hidden), (hidden, P_MAX)):
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        parts.append(rng.uniform(-lim, lim, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def train(ctx, X, Y, M, hidden=256, steps=3000, lr=2e-3, seed=0, batch=None, log_every=0):
+    ws = D.dvqls_ws_create(ctx, FEATURES, hidden, P_MAX, init_params(hidden, seed))
+    rng = np.random.default_rng(seed + 1)
+    losses = []
+    B = len(X) if batch is None else min(batch, len(X))
+    for step in range(steps):
+        if B < len(X):
+            idx = rng.choice(len(X), B, replace=False)
+            xb, yb, mb = X[idx], Y[idx], M[idx]
+        else:
+            xb, yb, mb = X, Y, M
+        want = log_every and (step % log_every == 0 or step == steps - 1)
+        loss = D.dvqls_ws_train_step(ws, B, np.ascontiguousarray(xb), np.ascontiguousarray(yb),
+                                     np.ascontiguousarray(mb), lr, want_loss=bool(want))
+        if want:
+            losses.append((step, loss))
+    return ws, losses
+
+
+def predict(ws, problems):
+    X = np.stack([p.feat for p in problems]).astype(np.float32)
+    out = np.zeros((len(problems), P_MAX), np.float32)
+    D.dvqls_ws_infer(ws, len(problems), X, out)
+    return [out[k, : p.P].astype(np.float64) for k, p in enumerate(problems)]
+
+
+def summarize(res, secs, cap):
+    it = np.array([r.iters if r.converged else cap for r in res])
+    conv = np.array([r.converged for r in res], bool)
+    return {"reached": int(conv.sum()), "count": len(res), "iters_median": float(np.median(it)),
+            "iters_mean": float(it.mean()), "seconds": secs,
+            "final_fidelity_median": float(np.median([r.fidelity for r in res]))}
+
+
+def attainable(ctx, problems, iters):
+    """Fidelity each problem reaches after `iters` Adam updates from the |+>
+    start with an unreachable target: the reference the evaluation is
+    measured against (the ansatz caps the fidelity below 1)."""
+    res, alphas, secs = optimize(ctx, problems, [plus_init(p.n) for p in problems], max_iter=iters, target=2.0)
+    return np.array([r.fidelity for r in res]), alphas, secs
+
+
+def run(ctx, n_train=2000, n_eval=200, train_iters=1000, max_iter=3000, train_steps=3000, gap=1e-4, seed=0,
+        log=print):
+    """The full pipeline: training targets from optimizer runs, training, and
+    the held-out comparison of initialisations.  Returns a summary dict.
+
+    Training targets: the angles after `train_iters` updates from the |+>
+    start.  Evaluation: iterations (and wall time) for each initialisation to
+    reach F >= F_ref - gap, F_ref being what `train_iters` updates from |+>
+    reach on that problem; also the counts reaching F >= 0.99 and 0.9999."""
+    rng = np.random.default_rng(seed)
+    train_specs = [(10_000 + k, int(rng.integers(N_MIN, N_MAX + 1))) for k in range(n_train)]
+    eval_specs = [(90_000 + k, N_MAX) for k in range(n_eval)]
+    t0 = time.perf_counter()
+    tr = prepare(ctx, train_specs)
+    ev = prepare(ctx, eval_specs)
+    log("prepared %d + %d problems in %.1f s" % (len(tr), len(ev), time.perf_counter() - t0))
+    F_tr, alphas, secs = attainable(ctx, tr, train_iters)
+    log("training targets: %d runs of %d updates in %.1f s, median F %.6f" % (len(tr), train_iters, secs,
+                                                                             np.median(F_tr)))
+    X, Y, M = training_arrays(tr, alphas)
+    t1 = time.perf_counter()
+    ws, losses = train(ctx, X, Y, M, steps=train_steps, log_every=max(1, train_steps // 10))
+    train_s = time.perf_counter() - t1
+    log("trained in %.1f s, loss %s" % (train_s, losses[-1] if losses else None))
+    F_ref, _, ref_s = attainable(ctx, ev, train_iters)
+    out = {"train": {"runs": len(tr), "updates_per_run": train_iters, "optimizer_seconds": secs,
+                     "median_fidelity": float(np.median(F_tr)), "train_seconds": train_s, "loss_curve": losses},
+           "eval": {"problems": len(ev), "n": N_MAX, "gap": gap,
+                    "reference_fidelity_median": float(np.median(F_ref)),
+                    "reference_fidelity_min": float(F_ref.min()), "reference_fidelity_max": float(F_ref.max())},
+           "inits": {}}
+    inits = {
+        "zero": [np.zeros(p.P) for p in ev],
+        "random": [np.random.default_rng(p.seed).uniform(-np.pi, np.pi, p.P) for p in ev],
+        "plus": [plus_init(p.n) for p in ev],
+        "mlp": predict(ws, ev),
+    }
+    for name, a0 in inits.items():
+        row = {}
+        r, _, s = optimize(ctx, ev, a0, max_iter=max_iter, target=F_ref - gap)
+        row["to_reference"] = summarize(r, s, max_iter)
+        for level in (0.99, 0.9999):
+            r, _, s = optimize(ctx, ev, a0, max_iter=max_iter, target=level)
+            row["to_%g" % level] = summarize(r, s, max_iter)
+        r, _, s = optimize(ctx, ev, a0, max_iter=0, target=2.0)
+        row["initial_fidelity_median"] = float(np.median([x.fidelity for x in r]))
+        out["inits"][name] = row
+        log("eval %-6s %s" % (name, row))
+    D.dvqls_ws_destroy(ws)
+    return out
+
+
+def main():
+    import argparse
+    import json
+
+    import torch
+
+    ap = argparse.ArgumentParser(description="learned warm start: train and evaluate")
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--eval", type=int, default=200)
+    ap.add_argument("--train-iters", type=int, default=1000)
+    ap.add_argument("--max-iter", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=3000)
+    args = ap.parse_args()
+    assert torch.cuda.is_available()
+    ctx = D.dvqls_create(0, torch.cuda.current_stream().cuda_stream)
+    try:
+        out = run(ctx, args.train, args.eval, args.train_iters, args.max_iter, args.steps)
+    finally:
+        D.dvqls_destroy(ctx)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
