@@ -70,7 +70,8 @@ typedef enum { DVQLS_FP64 = 0, DVQLS_FP32 = 1 } dvqls_precision;
 typedef enum { DVQLS_ANSATZ_RY_CZRING = 0 } dvqls_ansatz_kind;
 
 /* Largest n served with the state resident in shared memory; above it (up to
- * DVQLS_MAX_QUBITS) states are streamed through HBM. */
+ * DVQLS_MAX_QUBITS) the cost passes build every shifted state in HBM
+ * (S x 2^n amplitudes of workspace) and stream it through L2. */
 #define DVQLS_MAX_SMEM_QUBITS 12
 #define DVQLS_MAX_QUBITS 20
 /* Largest n for a dense decomposition input (N x N doubles). */
@@ -101,7 +102,8 @@ int dvqls_sync(dvqls_ctx* ctx);
  * batched cost pass is bracketed by CUDA events recorded on the context's
  * stream.  Enabling (enable = 1) resets the counters; disabling keeps them.
  * dvqls_profile_read synchronises the stream and returns, for `phase`
- * (0: prepare, 1: term tiles, 2: combine), the number of launches and their
+ * (0: prepare, 1: term tiles, 2: combine, 3: state passes in HBM for n > 12),
+ * the number of launches and their
  * total duration in milliseconds since the last reset.
  * Errors: INVALID_ARG (phase out of range), CUDA. */
 int dvqls_profile_enable(dvqls_ctx* ctx, int enable);

@@ -168,7 +168,7 @@ extern "C" int dvqls_profile_enable(dvqls_ctx* ctx, int enable) {
     int rc = prof_drain(ctx);
     if (rc) return rc;
     if (enable) {
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < 4; ++k) {
             ctx->prof_launches[k] = 0;
             ctx->prof_ms[k] = 0.0;
         }
@@ -178,7 +178,7 @@ extern "C" int dvqls_profile_enable(dvqls_ctx* ctx, int enable) {
 }
 
 extern "C" int dvqls_profile_read(dvqls_ctx* ctx, int phase, long long* launches, double* ms) {
-    if (!ctx || phase < 0 || phase > 2 || !launches || !ms) return DVQLS_ERR_INVALID_ARG;
+    if (!ctx || phase < 0 || phase > 3 || !launches || !ms) return DVQLS_ERR_INVALID_ARG;
     cudaSetDevice(ctx->device);
     int rc = prof_drain(ctx);
     if (rc) return rc;

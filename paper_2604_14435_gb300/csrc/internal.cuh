@@ -61,8 +61,8 @@ struct dvqls_ctx {
     struct Mark { int phase; cudaEvent_t a, b; };
     std::vector<Mark> marks;
     std::vector<cudaEvent_t> event_pool;
-    long long prof_launches[3] = {0, 0, 0};
-    double prof_ms[3] = {0, 0, 0};
+    long long prof_launches[4] = {0, 0, 0, 0};
+    double prof_ms[4] = {0, 0, 0, 0};
 
     // Cached batched-call state (see terms.cu).
     dvqls::GraphCacheEntry* graph = nullptr;

@@ -54,6 +54,7 @@ struct Inst {
     void* Gpart;     // ks*L*L (shift 0 only; null when beta is not requested)
     void* dpart;     // ks*L   (shift 0 only; null when delta is not requested)
     double* NsDs;    // 3S: N_s, Re D_s, Im D_s
+    void* states;    // n > 12: the S shifted states in HBM (S x N), else null
     double* cost;
     double* grad;    // P or null
     double2* beta;   // L*L or null
@@ -195,8 +196,11 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
     }
     const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
 
-    R2* psi = reinterpret_cast<R2*>(smem);
-    R2* Phl = psi + N;
+    // n <= 12: psi_s is built in shared memory; n > 12: it was built in HBM
+    // by the state passes and is read from there (L2-resident while in use).
+    R2* psi_smem = reinterpret_cast<R2*>(smem);
+    const R2* psi = I.states ? reinterpret_cast<const R2*>(I.states) + (size_t)s * N : psi_smem;
+    R2* Phl = psi_smem + (I.states ? 0 : N);
     R2* Phm = Phl + JC * TT;
     R2* bch = Phm + JC * TT;
     R2* scs = bch + JC;  // P entries (only used during the state build)
@@ -214,7 +218,8 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
         sxm[t] = m < L ? I.xm[m] : 0u;
         szm[t] = m < L ? I.zm[m] : 0u;
     }
-    build_state<R>(psi, scs, I.n, I.d, I.P, I.cs, s);
+    if (I.states) __syncthreads();
+    else build_state<R>(psi_smem, scs, I.n, I.d, I.P, I.cs, s);
 
     // Task of this thread: block (a, b) = rows 4a.., columns 4b.. of the tile.
     const int g = t / KSLOT, slot = t % KSLOT;
@@ -436,6 +441,131 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 1) k_terms_smem(const
     }
 }
 
+// ------------------------------------------------- states in HBM (n > 12)
+// The S shifted states of one instance, S x N amplitudes, built by passes
+// over HBM: the initial Ry layer on |0> is a product state written directly;
+// each further layer is one pass over 4096-amplitude chunks (CZ ring signs and
+// the Ry rotations of qubits 0..11 in shared memory) and one pass over column
+// tiles of HC consecutive low indices x all high indices (Ry of qubits 12..).
+constexpr int LOQ = 12, LOC = 1 << LOQ, HC = 16;
+
+template <typename R>
+__device__ __forceinline__ void shift_angle(const Inst& I, int s, int a, R& c, R& sn) {
+    int k = -1, which = 0;
+    if (s > 0) {
+        k = (s - 1) >> 1;
+        which = ((s - 1) & 1) ? 2 : 1;
+    }
+    const double2 v = I.cs[(a == k ? which : 0) * I.P + a];
+    c = (R)v.x;
+    sn = (R)v.y;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_hbm_init(const Inst* __restrict__ insts, int idx) {
+    using R2 = typename V2<R>::t;
+    const Inst& I = insts[idx];
+    __shared__ R cq[32], sq[32];
+    const int s = blockIdx.y, n = I.n;
+    const size_t N = size_t(1) << n;
+    if (threadIdx.x < n) shift_angle<R>(I, s, threadIdx.x, cq[threadIdx.x], sq[threadIdx.x]);
+    __syncthreads();
+    R2* st = reinterpret_cast<R2*>(I.states) + s * N;
+    for (int e = threadIdx.x; e < LOC; e += blockDim.x) {
+        const int i = (blockIdx.x << LOQ) + e;
+        R v = (R)1;
+        for (int q = 0; q < n; ++q) v *= ((i >> q) & 1) ? sq[q] : cq[q];
+        R2 r;
+        r.x = v;
+        r.y = (R)0;
+        st[i] = r;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_hbm_lo(const Inst* __restrict__ insts, int idx, int layer) {
+    using R2 = typename V2<R>::t;
+    extern __shared__ __align__(16) unsigned char sm[];
+    R2* w = reinterpret_cast<R2*>(sm);
+    const Inst& I = insts[idx];
+    __shared__ R cq[LOQ], sq[LOQ];
+    const int s = blockIdx.y, n = I.n, base = blockIdx.x << LOQ;
+    const size_t N = size_t(1) << n;
+    if (threadIdx.x < LOQ) shift_angle<R>(I, s, layer * n + threadIdx.x, cq[threadIdx.x], sq[threadIdx.x]);
+    R2* st = reinterpret_cast<R2*>(I.states) + s * N + base;
+    for (int e = threadIdx.x; e < LOC; e += blockDim.x) {
+        R2 v = st[e];
+        if (czring_parity(base + e, n)) v = neg2(v);
+        w[e] = v;
+    }
+    __syncthreads();
+    for (int q = 0; q < LOQ; ++q) {
+        const R c = cq[q], sn = sq[q];
+        for (int p = threadIdx.x; p < LOC / 2; p += blockDim.x) {
+            const int i0 = ((p >> q) << (q + 1)) | (p & ((1 << q) - 1)), i1 = i0 | (1 << q);
+            const R2 a = w[i0], b = w[i1];
+            R2 u, v;
+            u.x = c * a.x - sn * b.x;
+            u.y = c * a.y - sn * b.y;
+            v.x = sn * a.x + c * b.x;
+            v.y = sn * a.y + c * b.y;
+            w[i0] = u;
+            w[i1] = v;
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < LOC; e += blockDim.x) st[e] = w[e];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_hbm_hi(const Inst* __restrict__ insts, int idx, int layer) {
+    using R2 = typename V2<R>::t;
+    extern __shared__ __align__(16) unsigned char sm[];
+    R2* w = reinterpret_cast<R2*>(sm);  // [H][HC]
+    const Inst& I = insts[idx];
+    __shared__ R cq[32], sq[32];
+    const int s = blockIdx.y, n = I.n, H = 1 << (n - LOQ), lo0 = blockIdx.x * HC;
+    const size_t N = size_t(1) << n;
+    if (threadIdx.x < n - LOQ)
+        shift_angle<R>(I, s, layer * n + LOQ + threadIdx.x, cq[threadIdx.x], sq[threadIdx.x]);
+    R2* st = reinterpret_cast<R2*>(I.states) + s * N;
+    for (int e = threadIdx.x; e < H * HC; e += blockDim.x) w[e] = st[((size_t)(e / HC) << LOQ) + lo0 + e % HC];
+    __syncthreads();
+    for (int q = 0; q < n - LOQ; ++q) {
+        const R c = cq[q], sn = sq[q];
+        for (int p = threadIdx.x; p < (H / 2) * HC; p += blockDim.x) {
+            const int hp = p / HC, lo = p % HC;
+            const int h0 = ((hp >> q) << (q + 1)) | (hp & ((1 << q) - 1)), h1 = h0 | (1 << q);
+            const R2 a = w[h0 * HC + lo], b = w[h1 * HC + lo];
+            R2 u, v;
+            u.x = c * a.x - sn * b.x;
+            u.y = c * a.y - sn * b.y;
+            v.x = sn * a.x + c * b.x;
+            v.y = sn * a.y + c * b.y;
+            w[h0 * HC + lo] = u;
+            w[h1 * HC + lo] = v;
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < H * HC; e += blockDim.x) st[((size_t)(e / HC) << LOQ) + lo0 + e % HC] = w[e];
+}
+
+template <typename R>
+int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, int S) {
+    using R2 = typename V2<R>::t;
+    const int chunks = 1 << (n - LOQ), tiles = LOC / HC;
+    const size_t lo_smem = sizeof(R2) * LOC, hi_smem = sizeof(R2) * ((size_t)chunks * HC);
+    DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_hbm_lo<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lo_smem)));
+    DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_hbm_hi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hi_smem)));
+    k_hbm_init<R><<<dim3(chunks, S), 256, 0, ctx->stream>>>(dtable, idx);
+    for (int layer = 1; layer <= d; ++layer) {
+        k_hbm_lo<R><<<dim3(chunks, S), 256, lo_smem, ctx->stream>>>(dtable, idx, layer);
+        k_hbm_hi<R><<<dim3(tiles, S), 256, hi_smem, ctx->stream>>>(dtable, idx, layer);
+    }
+    DVQLS_CUDA_TRY(ctx, cudaGetLastError());
+    return DVQLS_OK;
+}
+
 // ---------------------------------------------------------------- combine
 template <typename R>
 __global__ void __launch_bounds__(NT) k_combine(const Inst* __restrict__ insts, int* status) {
@@ -516,7 +646,12 @@ struct HostInst {
     int n, d, L, P, S, T, ks;
     long long N;
     int order;  // position in the caller's array
+    bool hbm;   // n > 12: states built in HBM
 };
+
+// Amplitudes per work item for states in HBM (each FP32 sum runs over half
+// of them; items are added in FP64).
+constexpr long long HBM_K = 2048;
 
 template <typename R>
 size_t smem_bytes(int nmax, int Pmax) {
@@ -537,8 +672,6 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         const dvqls_instance& q = inst[i];
         const int n = q.ansatz.n, d = q.ansatz.depth;
         if (n < 1 || n > DVQLS_MAX_QUBITS) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "instance %d: n = %d", i, n);
-        if (n > DVQLS_MAX_SMEM_QUBITS)
-            return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "instance %d: n = %d above %d", i, n, DVQLS_MAX_SMEM_QUBITS);
         if (d < 0) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "instance %d: depth < 0", i);
         if (q.ansatz.kind != DVQLS_ANSATZ_RY_CZRING)
             return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "instance %d: ansatz kind %d", i, q.ansatz.kind);
@@ -556,7 +689,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         h.T = ceil_div(L, TT);
         h.N = 1LL << n;
         h.order = i;
-        nmax = std::max(nmax, n);
+        h.hbm = n > DVQLS_MAX_SMEM_QUBITS;
+        if (!h.hbm) nmax = std::max(nmax, n);
         Pmax = std::max(Pmax, h.P);
     }
     cudaSetDevice(ctx->device);
@@ -572,18 +706,19 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
 
     // K split: enough items to fill the machine twice over, at most 8 ways,
     // at least one chunk per split.
+    // States in HBM take a fixed HBM_K amplitudes per item.
     long long base_items = 0;
     for (auto& h : hi) base_items += (long long)h.S * h.T * h.T;
     int ks = 1;
     while (ks < 8 && base_items * ks < 2 * slots) ks *= 2;
-    // Longest items first (LPT): sort by per-item work, then caller order.
+    for (auto& h : hi)
+        h.ks = h.hbm ? (int)std::max<long long>(1, h.N / HBM_K)
+                     : (int)std::min<long long>(ks, std::max<long long>(1, h.N / JC));
+    // Longest items first (LPT): sort by amplitudes per item, then caller order.
     std::vector<int> ord(count);
     for (int i = 0; i < count; ++i) ord[i] = i;
-    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
-        const long long wa = hi[a].N / std::min<long long>(ks, std::max<long long>(1, hi[a].N / JC));
-        const long long wb = hi[b].N / std::min<long long>(ks, std::max<long long>(1, hi[b].N / JC));
-        return wa > wb;
-    });
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int a, int b) { return hi[a].N / hi[a].ks > hi[b].N / hi[b].ks; });
 
     // Plan the workspace.
     Arena ar;
@@ -591,7 +726,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     struct Off {
         size_t coef, xm, zm, alpha, b;       // staged inputs (ws) ...
         size_t pcoef, pxm, pzm, palpha, pb;  // ... and their pinned slots
-        size_t ctil, w, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta;
+        size_t ctil, w, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta, states;
         size_t pcost, pgrad, pbeta, pdelta;
     };
     std::vector<Off> off(count);
@@ -601,7 +736,6 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     for (int oi = 0; oi < count; ++oi) {
         const int i = ord[oi];
         HostInst& h = hi[i];
-        h.ks = (int)std::min<long long>(ks, std::max<long long>(1, h.N / JC));
         Off& o = off[i];
         const size_t L = h.L;
         o.coef = ar.reserve(L * 16);
@@ -623,6 +757,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         o.Gp = beta_out ? ar.reserve(size_t(h.ks) * L * L * r2) : 0;
         o.dp = delta_out ? ar.reserve(size_t(h.ks) * L * r2) : 0;
         o.NsDs = ar.reserve(size_t(h.S) * 24);
+        o.states = h.hbm ? ar.reserve(size_t(h.S) * size_t(h.N) * r2) : 0;
         o.cost = ar.reserve(8);
         o.pcost = pin.reserve(8);
         o.grad = ar.reserve(size_t(h.P) * 8);
@@ -689,6 +824,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         I.Gpart = beta_out ? (void*)(ws + o.Gp) : nullptr;
         I.dpart = delta_out ? (void*)(ws + o.dp) : nullptr;
         I.NsDs = (double*)(ws + o.NsDs);
+        I.states = h.hbm ? (void*)(ws + o.states) : nullptr;
         // Device outputs are written in place by the combine kernel.
         const bool dev_cost = costs && is_device_ptr(ctx, costs);
         const bool dev_grad = grads && is_device_ptr(ctx, grads);
@@ -720,6 +856,15 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     prof_begin(ctx, 0);
     k_prepare<<<count, NT, 0, ctx->stream>>>(dtable, ctx->d_status);
     prof_end(ctx);
+    for (int oi = 0; oi < count; ++oi) {
+        const HostInst& h = hi[ord[oi]];
+        if (!h.hbm) continue;
+        prof_begin(ctx, 3);
+        rc = fp32 ? build_hbm_states<float>(ctx, dtable, oi, h.n, h.d, h.S)
+                  : build_hbm_states<double>(ctx, dtable, oi, h.n, h.d, h.S);
+        prof_end(ctx);
+        if (rc) return rc;
+    }
     const long long total = item_base;
     const int grid = (int)std::min<long long>(total, slots);
     prof_begin(ctx, 1);
