@@ -1,24 +1,33 @@
 """Benchmark: cost+grad evaluations/s of the D-VQLS global cost at n = 10, L = 64.
 
-Workload (the n = 10 tridiagonal Toeplitz throughput system): a batch of 32
-instances (seeds 0..31; a ~ U(2,4), c ~ U(-1.5,-0.5) with a > 2|c|), each
-decomposed on the GPU and pruned to its top 64 Pauli terms, b = |+>^10,
-depth-4 Ry + CZ-ring ansatz (50 angles).  One step = one cost + parameter-
-shift gradient evaluation of every instance: 32 x 101 shifted states x
-(64^2 + 64) Hadamard-test terms, FP32 state and term arithmetic with FP64
-weighted sums (dvqls_cost_grad_batched).  Inputs are resident in HBM; L2 is
-flushed (a 256 MB write) between timed steps, outside the timed events.
+Default workload (the n = 10 tridiagonal Toeplitz throughput system): a batch
+of 32 instances per GPU (seeds 0..31; a ~ U(2,4), c ~ U(-1.5,-0.5) with
+a > 2|c|), each decomposed on the GPU and pruned to its top 64 Pauli terms,
+b = |+>^10, depth-4 Ry + CZ-ring ansatz (50 angles).  One step = one cost +
+parameter-shift gradient evaluation of every instance: 32 x 101 shifted
+states x (64^2 + 64) Hadamard-test terms, FP32 state and term arithmetic with
+FP64 weighted sums (dvqls_cost_grad_batched).  Inputs are resident in HBM; L2
+is flushed (a 256 MB write) between timed steps, outside the timed events.
 
-`value`  : instances x steps / device time of the timed steps (CUDA events).
-`e2e`    : the same, through the C-ABI with host buffers (pinned staging,
-           host-to-device inputs and device-to-host results inside the time).
-`roofline`: the term-tile kernel against the FP32 FMA peak.
+`value`   : instances x steps / device time of the timed steps (CUDA events,
+            the library replaying its captured graph of the pass).
+`roofline`: the term-tile kernel against the FP32 FMA peak; its duration comes
+            from a second pass over the same steps with per-kernel CUDA
+            events on the launching stream (graph replay off).
+`e2e`     : the same metric through the C-ABI with host buffers (pinned
+            staging, host-to-device inputs and device-to-host results inside
+            the time).
 `cpu_baseline` / --impl reference: the CPU circuit-level oracle on a bounded
-           sample of shifts of one instance, scaled to whole evaluations.
+            sample of shifts of one instance, scaled to whole evaluations.
+`fp64_circuit_path`: the per-circuit FP64 GPU path on instance 0.
+
+Other workloads (--workload; not the headline line): `uneven` (62 Toeplitz
+instances, n in {4,...,12}, tri/pentadiagonal, plus two n = 20 instances with
+states in HBM, depth n/2) and `hele_shaw` (8 variable-permeability 32 x 32
+Laplacians, top-256 terms, depth 6).
 
 Multi-GPU: one process per GPU (torchrun); each rank evaluates its own batch
-of 32 instances (weak scaling, no data-path collective); the time is the
-maximum over ranks.
+(weak scaling, no data-path collective); the time is the maximum over ranks.
 """
 import argparse
 import json
@@ -36,33 +45,16 @@ N_QUBITS, DEPTH, L_TERMS, BATCH = 10, 4, 64, 32
 METRIC = "cost+grad evals/sec at n=10, L=64 (FP32 batched vs FP64 circuit path)"
 UNIT = "evals/s"
 SMS, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
 
 
-def workload_config(n_gpus):
-    return {"workload": "tridiagonal Toeplitz n=10 (N=1024), top-64 Pauli terms, depth-4 Ry+CZ-ring ansatz "
-                        "(P=50, S=101 shifts), batch of 32 instances per GPU",
-            "n": N_QUBITS, "L": L_TERMS, "depth": DEPTH, "angles": 50, "shifts": 101,
-            "instances_per_gpu": BATCH, "terms_per_eval": 101 * (L_TERMS ** 2 + L_TERMS),
-            "l2": "flushed between timed steps (256 MB write)", "parallelism": "dp%d" % n_gpus}
-
-
-def terms_per_step(batch=BATCH):
-    return batch * 101 * (L_TERMS ** 2 + L_TERMS)
-
-
-def flops_per_step(batch=BATCH):
-    """Algorithmic FLOPs of the term reductions: 8 N per term (one complex
-    multiply-accumulate per amplitude), every ordered pair (l, m) counted."""
-    return terms_per_step(batch) * 8 * (1 << N_QUBITS)
-
-
-def executed_flops_per_step(batch=BATCH):
-    """FLOPs the term kernel executes: beta_ml = conj(beta_lm) is taken from
-    its mirror, so a 64 x 64 diagonal tile computes its 136 upper-triangle
-    4 x 4 blocks (2,176 entries, 96 of them below the diagonal inside the
-    diagonal blocks) plus the 64 delta reductions."""
-    per_shift = (136 * 16 + L_TERMS) * 8 * (1 << N_QUBITS)
-    return batch * 101 * per_shift
+def executed_gram_entries(L):
+    """Complex products per amplitude the term kernel executes for one shift:
+    per 64-tile of terms, the 136 upper-triangle 4 x 4 blocks of a diagonal
+    tile (plus 64 delta rows) and 128 blocks per half of an off-diagonal tile
+    pair (beta_ml = conj(beta_lm) is taken from its mirror)."""
+    T = (L + 63) // 64
+    return T * (136 * 16 + 64) + T * (T - 1) * (128 * 16)
 
 
 class Clocks:
@@ -118,28 +110,65 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
 
 
-def make_batch(D, ctx, torch, rank):
-    """Decompose the 32 instances of this rank on the GPU (not timed) and
-    build the device-resident instance array."""
+def rank_seeds(rank, count):
+    """Instances are sharded by rank: rank r takes seeds r*count .. r*count+count-1."""
+    return [rank * count + k for k in range(count)]
+
+
+def workload_specs(name, rank):
+    """List of (kind, seed, n, depth, L_max) for this rank's batch."""
+    from paper_2604_14435_gb300 import workloads as wl
+    if name == "toeplitz10":
+        return [("throughput", s, N_QUBITS, DEPTH, L_TERMS) for s in rank_seeds(rank, BATCH)]
+    if name == "hele_shaw":
+        return [("hele_shaw", s, 10, 6, 256) for s in rank_seeds(rank, 8)]
+    if name == "uneven":
+        return [("uneven", (rank, k), inst["n"], inst["d"], inst["L_max"])
+                for k, inst in enumerate(wl.uneven_batch(seed=rank))]
+    raise ValueError(name)
+
+
+def make_batch(D, ctx, torch, rank, name):
+    """Decompose this rank's instances on the GPU (not timed) and build the
+    device-resident and host-resident instance arrays."""
     from paper_2604_14435_gb300 import workloads as wl
     dev = torch.device("cuda", torch.cuda.current_device())
-    keep, items, host_items = [], [], []
-    for k in range(BATCH):
-        inst = wl.throughput_instance(rank * BATCH + k, n=N_QUBITS, d=DEPTH, L_max=L_TERMS)
-        coef = torch.zeros(2 * L_TERMS, dtype=torch.float64, device=dev)
-        xm = torch.zeros(L_TERMS, dtype=torch.int32, device=dev)
-        zm = torch.zeros(L_TERMS, dtype=torch.int32, device=dev)
-        bands = torch.tensor(inst["bands"], dtype=torch.float64, device=dev)
-        L, _, _ = D.dvqls_pauli_decompose_banded(ctx, N_QUBITS, inst["offsets"], bands, 0.0, L_TERMS, coef, xm, zm)
-        assert L == L_TERMS
+    keep, items, host_items, shapes = [], [], [], []
+    uneven = wl.uneven_batch(seed=rank) if name == "uneven" else None
+    for kind, seed, n, d, L_max in workload_specs(name, rank):
+        coef = torch.zeros(2 * L_max, dtype=torch.float64, device=dev)
+        xm = torch.zeros(L_max, dtype=torch.int32, device=dev)
+        zm = torch.zeros(L_max, dtype=torch.int32, device=dev)
+        if kind == "hele_shaw":
+            inst = wl.hele_shaw_pressure(seed)
+            A = torch.tensor(inst["A"], dtype=torch.float64, device=dev)
+            L, _, _ = D.dvqls_pauli_decompose(ctx, A, n, 0.0, L_max, coef, xm, zm)
+        else:
+            inst = uneven[seed[1]] if kind == "uneven" else wl.throughput_instance(seed, n=n, d=d, L_max=L_max)
+            bands = torch.tensor(inst["bands"], dtype=torch.float64, device=dev)
+            tau = inst["tau"] if kind == "uneven" else 0.0
+            L, _, _ = D.dvqls_pauli_decompose_banded(ctx, n, inst["offsets"], bands, tau, L_max, coef, xm, zm)
         alpha = torch.tensor(inst["alpha"], dtype=torch.float64, device=dev)
-        b = torch.tensor(inst["b"].view(np.float64), dtype=torch.float64, device=dev)
+        b = torch.tensor(np.ascontiguousarray(inst["b"]).view(np.float64), dtype=torch.float64, device=dev)
         keep.append((coef, xm, zm, alpha, b))
-        items.append((D.make_ansatz(N_QUBITS, DEPTH), D.make_lcu(L, coef, xm, zm), alpha, b))
+        items.append((D.make_ansatz(n, d), D.make_lcu(L, coef, xm, zm), alpha, b))
         h = tuple(t.cpu().numpy().copy() for t in (coef, xm, zm, alpha, b))
         keep.append(h)
-        host_items.append((D.make_ansatz(N_QUBITS, DEPTH), D.make_lcu(L, h[0], h[1], h[2]), h[3], h[4]))
-    return D.make_instances(items), D.make_instances(host_items), keep
+        host_items.append((D.make_ansatz(n, d), D.make_lcu(L, h[0], h[1], h[2]), h[3], h[4]))
+        shapes.append((n, d, L))
+    return D.make_instances(items), D.make_instances(host_items), keep, shapes
+
+
+def work_of(shapes):
+    """Paper terms, algorithmic and executed FLOPs of one cost+grad pass."""
+    terms = alg = exe = 0
+    for n, d, L in shapes:
+        S = 2 * n * (d + 1) + 1
+        N = 1 << n
+        terms += S * (L * L + L)
+        alg += S * (L * L + L) * 8 * N
+        exe += S * executed_gram_entries(L) * 8 * N
+    return terms, alg, exe
 
 
 def cpu_oracle_rate(budget_s=10.0, max_shifts=101):
@@ -166,6 +195,24 @@ def cpu_oracle_rate(budget_s=10.0, max_shifts=101):
     return 1.0 / per_eval, threads, sample
 
 
+def workload_config(name, n_gpus, shapes):
+    base = {"parallelism": "dp%d" % n_gpus, "instances_per_gpu": len(shapes),
+            "l2": "flushed between timed steps (256 MB write)"}
+    if name == "toeplitz10":
+        base.update({"workload": "tridiagonal Toeplitz n=10 (N=1024), top-64 Pauli terms, depth-4 Ry+CZ-ring "
+                                 "ansatz (P=50, S=101 shifts), batch of 32 instances per GPU",
+                     "n": N_QUBITS, "L": L_TERMS, "depth": DEPTH, "angles": 50, "shifts": 101,
+                     "terms_per_eval": 101 * (L_TERMS ** 2 + L_TERMS)})
+    elif name == "hele_shaw":
+        base.update({"workload": "Hele-Shaw-type pressure: 32x32 variable-k 5-point Laplacian (n=10), top-256 "
+                                 "Pauli terms, depth-6 ansatz (P=70, S=141), 8 instances per GPU"})
+    else:
+        base.update({"workload": "uneven batch: 62 Toeplitz instances n in {4,6,8,10,12} (tri/penta-diagonal, "
+                                 "tau=0.01, L<=64) + 2 tridiagonal n=20 (states in HBM), depth n/2",
+                     "n_list": [s[0] for s in shapes], "L_list": [s[2] for s in shapes]})
+    return base
+
+
 def run_reference(args):
     rank, _, ws = dist_env()
     if ws > 1 and rank != 0:
@@ -182,7 +229,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.gpus),
+            "data": "synthetic", "config": workload_config("toeplitz10", args.gpus, [(10, 4, 64)] * BATCH),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "each step: " + sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -195,11 +242,13 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="toeplitz10", choices=["toeplitz10", "uneven", "hele_shaw"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     assert args.warmup >= 3, "at least 3 warm-up steps"
+    headline = args.workload == "toeplitz10"
 
     import torch
     rank, local, ws = dist_env()
@@ -218,10 +267,11 @@ def main():
 
     stream = torch.cuda.current_stream()
     ctx = D.dvqls_create(local, stream.cuda_stream)
-    dev_arr, host_arr, keep = make_batch(D, ctx, torch, rank)
-    P = 50
-    costs = torch.zeros(BATCH, dtype=torch.float64, device="cuda")
-    grads = torch.zeros(BATCH * P, dtype=torch.float64, device="cuda")
+    dev_arr, host_arr, keep, shapes = make_batch(D, ctx, torch, rank, args.workload)
+    count = len(shapes)
+    P = sum(n * (d + 1) for n, d, L in shapes)
+    costs = torch.zeros(count, dtype=torch.float64, device="cuda")
+    grads = torch.zeros(P, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def step():
@@ -232,66 +282,74 @@ def main():
     D.dvqls_sync(ctx)
     torch.cuda.synchronize()
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    def timed(profile):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            D.dvqls_profile_enable(ctx, 1)
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        D.dvqls_sync(ctx)
+        torch.cuda.synchronize()
+        if profile:
+            D.dvqls_profile_enable(ctx, 0)
+        if pg:
+            pg.barrier()
+        return sum(a.elapsed_time(b) for a, b in ev)
+
     clocks = Clocks(local)
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    D.dvqls_profile_enable(ctx, 1)
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        ev[k][0].record(stream)
-        step()
-        ev[k][1].record(stream)
-    D.dvqls_sync(ctx)
-    torch.cuda.synchronize()
-    D.dvqls_profile_enable(ctx, 0)
+    dev_ms = timed(profile=False)
     clk = clocks.stop()
-    if pg:
-        pg.barrier()
-    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
-    n_terms_launch, ms_terms = D.dvqls_profile_read(ctx, 1)
-    n_prep, ms_prep = D.dvqls_profile_read(ctx, 0)
-    n_comb, ms_comb = D.dvqls_profile_read(ctx, 2)
+    prof_ms = timed(profile=True)
+    phases = {name: D.dvqls_profile_read(ctx, k) for k, name in
+              enumerate(("prepare", "terms", "combine", "hbm_states"))}
     if pg:
         t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         dev_ms = t.item()
-    value = ws * BATCH * args.steps / (dev_ms / 1000.0)
+    value = ws * count * args.steps / (dev_ms / 1000.0)
 
-    # End to end through the C-ABI with host buffers.
-    hcost = np.zeros(BATCH)
-    hgrad = np.zeros(BATCH * P)
-    for _ in range(3):
-        D.dvqls_cost_grad_batched(ctx, host_arr, D.DVQLS_FP32, hcost, hgrad)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        D.dvqls_cost_grad_batched(ctx, host_arr, D.DVQLS_FP32, hcost, hgrad)
-    e2e_s = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = t.item()
-    h2d = BATCH * (L_TERMS * 24 + P * 8 + (1 << N_QUBITS) * 16)
-    d2h = BATCH * (8 + P * 8)
-    gpu_check = float(np.max(np.abs(hcost - costs.cpu().numpy())))
+    e2e = None
+    if headline:
+        hcost = np.zeros(count)
+        hgrad = np.zeros(P)
+        for _ in range(3):
+            D.dvqls_cost_grad_batched(ctx, host_arr, D.DVQLS_FP32, hcost, hgrad)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            D.dvqls_cost_grad_batched(ctx, host_arr, D.DVQLS_FP32, hcost, hgrad)
+        e2e_s = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_s = t.item()
+        h2d = sum(L * 24 + n * (d + 1) * 8 + (1 << n) * 16 for n, d, L in shapes)
+        d2h = sum(8 + n * (d + 1) * 8 for n, d, L in shapes)
+        e2e = {"value": ws * count * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h,
+               "max_abs_cost_diff_vs_device_path": float(np.max(np.abs(hcost - costs.cpu().numpy())))}
 
-    # Comparison path: the per-circuit FP64 evaluation of instance 0 (all
-    # 840,320 circuits of one cost+grad), and the decomposition of instance 0.
-    circ = None
-    decomp = None
-    if rank == 0:
+    # Comparison path (headline only): the per-circuit FP64 evaluation of
+    # instance 0 (all 840,320 circuits of one cost+grad) and its decomposition.
+    circ = decomp = None
+    if rank == 0 and headline:
         coef0, xm0, zm0, alpha0, b0 = keep[0]
         an = D.make_ansatz(N_QUBITS, DEPTH)
         lcu0 = D.make_lcu(L_TERMS, coef0, xm0, zm0)
         c1 = torch.zeros(1, dtype=torch.float64, device="cuda")
-        g1 = torch.zeros(P, dtype=torch.float64, device="cuda")
+        g1 = torch.zeros(50, dtype=torch.float64, device="cuda")
         D.dvqls_circuit_cost_grad_fp64(ctx, an, alpha0, lcu0, b0, c1, g1)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
         reps = 2
+        t0 = time.perf_counter()
         for _ in range(reps):
             D.dvqls_circuit_cost_grad_fp64(ctx, an, alpha0, lcu0, b0, c1, g1)
         torch.cuda.synchronize()
@@ -306,6 +364,7 @@ def main():
         cc = torch.zeros(2 * L_TERMS, dtype=torch.float64, device="cuda")
         xx = torch.zeros(L_TERMS, dtype=torch.int32, device="cuda")
         zz = torch.zeros(L_TERMS, dtype=torch.int32, device="cuda")
+
         def tdec(fn, reps=20):
             fn()
             torch.cuda.synchronize()
@@ -314,43 +373,49 @@ def main():
                 fn()
             torch.cuda.synchronize()
             return 1000.0 * (time.perf_counter() - t) / reps
-        ms_b = tdec(lambda: D.dvqls_pauli_decompose_banded(ctx, N_QUBITS, inst0["offsets"], bands, 0.01, L_TERMS,
-                                                           cc, xx, zz))
-        ms_d = tdec(lambda: D.dvqls_pauli_decompose(ctx, A, N_QUBITS, 0.01, L_TERMS, cc, xx, zz))
-        decomp = {"banded_ms": ms_b, "dense_ms": ms_d, "n": N_QUBITS, "L_max": L_TERMS,
+
+        decomp = {"banded_ms": tdec(lambda: D.dvqls_pauli_decompose_banded(ctx, N_QUBITS, inst0["offsets"], bands,
+                                                                           0.01, L_TERMS, cc, xx, zz)),
+                  "dense_ms": tdec(lambda: D.dvqls_pauli_decompose(ctx, A, N_QUBITS, 0.01, L_TERMS, cc, xx, zz)),
+                  "n": N_QUBITS, "L_max": L_TERMS,
                   "note": "host wall time per call incl. the count read-back; dense input 8 MB (N x N FP64)"}
 
     if rank == 0:
-        avg_terms_ms = ms_terms / max(1, n_terms_launch)
-        achieved = flops_per_step() / (avg_terms_ms / 1000.0) / 1e12
-        executed = executed_flops_per_step() / (avg_terms_ms / 1000.0) / 1e12
-        peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        terms, alg, exe = work_of(shapes)
+        n_t, ms_t = phases["terms"]
+        avg_terms_ms = ms_t / max(1, n_t)
+        achieved = alg / (avg_terms_ms / 1000.0) / 1e12
+        executed = exe / (avg_terms_ms / 1000.0) / 1e12
+        launches_per_step = sum(phases[k][0] for k in ("prepare", "terms", "combine", "hbm_states")) / args.steps
+        metric = METRIC if headline else "cost+grad evals/sec (%s workload)" % args.workload
+        line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(ws),
-                "terms_per_s": ws * terms_per_step() * args.steps / (dev_ms / 1000.0),
+                "config": workload_config(args.workload, ws, shapes),
+                "terms_per_s": ws * terms * args.steps / (dev_ms / 1000.0),
                 "roofline": {"bound": "alu", "kernel": "k_terms_smem<float>", "achieved": achieved,
-                             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                             "peak": FP32_PEAK, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK, "traffic": None,
                              "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max SM clock)",
                              "achieved_note": "algorithmic: 8N FLOP per paper term, all L^2 ordered pairs + L",
-                             "executed": {"tflops": executed, "frac": executed / peak,
-                                          "flops_per_launch": executed_flops_per_step(),
-                                          "note": "Hermitian pairs computed once: 2,176 of 4,096 Gram entries "
-                                                  "per 64-tile plus 64 delta reductions per shift"},
+                             "executed": {"tflops": executed, "frac": executed / FP32_PEAK,
+                                          "flops_per_launch": exe,
+                                          "note": "Hermitian pairs computed once (upper-triangle 4x4 blocks of "
+                                                  "each 64-tile) plus the delta reductions"},
                              "kernel_ms_avg": avg_terms_ms,
-                             "phase_ms_avg": {"prepare": ms_prep / max(1, n_prep), "terms": avg_terms_ms,
-                                              "combine": ms_comb / max(1, n_comb)}},
-                "e2e": {"value": ws * BATCH * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h, "max_abs_cost_diff_vs_device_path": gpu_check},
-                "gpu_launches": n_terms_launch + n_prep + n_comb,
-                "fp64_circuit_path": circ,
-                "speedup_vs_fp64_circuit_path": value / circ["value"] if circ else None,
-                "decomposition": decomp,
+                             "kernel_timing": "per-kernel CUDA events in a second pass over the same steps",
+                             "phase_ms_avg": {k: v[1] / max(1, v[0]) for k, v in phases.items()},
+                             "profiled_pass_ms_per_step": prof_ms / args.steps},
+                "gpu_launches": int(launches_per_step * args.steps),
                 "clocks": clk}
-        if not args.no_cpu_baseline and ws == 1:
-            rate, cores, sample = cpu_oracle_rate(budget_s=10.0)
-            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        if headline:
+            line["e2e"] = e2e
+            line["fp64_circuit_path"] = circ
+            line["speedup_vs_fp64_circuit_path"] = value / circ["value"]
+            line["decomposition"] = decomp
+            if not args.no_cpu_baseline and ws == 1:
+                rate, cores, sample = cpu_oracle_rate(budget_s=10.0)
+                line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                        "sample": sample}
         print(json.dumps(line))
     D.dvqls_destroy(ctx)
     if pg:

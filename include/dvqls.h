@@ -82,7 +82,9 @@ typedef struct dvqls_ctx dvqls_ctx;
 /* Create a context on CUDA device `device`.  `stream` is the cudaStream_t
  * every call of this context is ordered on (passed as void* so this header
  * needs no CUDA include); NULL is the default stream.  The context never
- * creates or destroys streams.  *out receives the context.
+ * destroys the caller's stream; it creates one private stream of its own,
+ * used only to record CUDA graphs of the cost pass.  *out receives the
+ * context.
  * Errors: INVALID_ARG (out == NULL or no such device), CUDA, ALLOC. */
 int dvqls_create(dvqls_ctx** out, int device, void* stream);
 
@@ -196,8 +198,14 @@ typedef struct {
  * When costs and grads are both device memory (or NULL) and every input is
  * device memory, the call only enqueues work and returns; numeric errors are
  * then reported by the next dvqls_sync().  Otherwise it returns after the
- * results are in place.  `count` instances of the same shapes and pointers
- * as the previous call replay a captured CUDA graph. */
+ * results are in place.
+ * Launch: the first call of a problem signature (precision and every
+ * instance's n, depth, L) times each split of the amplitude range among the
+ * candidates 1, 2, 4, 8 on the real inputs and keeps the fastest for the
+ * context (an autotuner; that call is synchronous).  The kernel sequence of a
+ * pass is captured once as a CUDA graph and replayed while the instance
+ * table (shapes and pointers) is unchanged; with profiling enabled, or when
+ * the caller is capturing the stream, kernels are launched directly. */
 int dvqls_cost_grad_batched(dvqls_ctx* ctx, int count, const dvqls_instance* inst,
                             int precision, double* costs, double* grads);
 

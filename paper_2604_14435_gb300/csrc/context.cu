@@ -30,6 +30,7 @@ int ensure_workspace(dvqls_ctx* ctx, size_t bytes) {
     if (bytes <= ctx->ws_cap) return DVQLS_OK;
     DVQLS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->last_table.clear();
+    release_graph_cache(ctx);
     if (ctx->ws) cudaFree(ctx->ws);
     ctx->ws = nullptr;
     ctx->ws_cap = 0;
@@ -224,15 +225,12 @@ extern "C" int dvqls_create(dvqls_ctx** out, int device, void* stream) {
     return DVQLS_OK;
 }
 
-namespace dvqls {
-void release_graph_cache(dvqls_ctx* ctx);  // terms.cu
-}
-
 extern "C" void dvqls_destroy(dvqls_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     dvqls::release_graph_cache(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->pin) cudaFreeHost(ctx->pin);
     if (ctx->d_status) cudaFree(ctx->d_status);

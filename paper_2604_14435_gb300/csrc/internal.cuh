@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -64,13 +65,20 @@ struct dvqls_ctx {
     long long prof_launches[4] = {0, 0, 0, 0};
     double prof_ms[4] = {0, 0, 0, 0};
 
-    // Cached batched-call state (see terms.cu).
+    // Cached batched-call state (see terms.cu): the last captured graph of a
+    // cost pass, the private stream graphs are captured on, and the
+    // autotuned amplitude split per problem signature.
     dvqls::GraphCacheEntry* graph = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::map<std::string, int> tune;
 };
 
 namespace dvqls {
 
 int set_error(dvqls_ctx* ctx, int code, const char* fmt, ...);
+
+// Drop the captured cost-pass graph (terms.cu).
+void release_graph_cache(dvqls_ctx* ctx);
 
 #define DVQLS_CUDA_TRY(ctx, call)                                                           \
     do {                                                                                    \

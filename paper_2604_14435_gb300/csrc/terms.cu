@@ -23,6 +23,7 @@
 // dC/dalpha_k = -(N'_k D_0 - N_0 D'_k)/D_0^2 (parameter-shift rule).
 #include <algorithm>
 #include <mutex>
+#include <string>
 
 #include "internal.cuh"
 #include "state.cuh"
@@ -659,6 +660,91 @@ size_t smem_bytes(int nmax, int Pmax) {
     return sizeof(R2) * (size_t(1) << nmax) + sizeof(R2) * (2 * JC * TT + JC) + sizeof(R2) * Pmax;
 }
 
+// Launch parameters of one cost pass (everything but the table contents).
+struct PassShape {
+    int fp32, count, grid;
+    long long total;
+    size_t smem;
+};
+
+// The kernel sequence of one cost pass on stream `st`: queue reset, prepare,
+// state passes of the instances with states in HBM, term tiles, combine.
+static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, const PassShape& ps,
+                       const std::vector<const HostInst*>& tab, bool marks) {
+    DVQLS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_queue, 0, sizeof(unsigned long long), st));
+    if (marks) prof_begin(ctx, 0);
+    k_prepare<<<ps.count, NT, 0, st>>>(dtable, ctx->d_status);
+    if (marks) prof_end(ctx);
+    for (int oi = 0; oi < ps.count; ++oi) {
+        const HostInst& h = *tab[oi];
+        if (!h.hbm) continue;
+        if (marks) prof_begin(ctx, 3);
+        cudaStream_t keep = ctx->stream;
+        ctx->stream = st;
+        const int rc = ps.fp32 ? build_hbm_states<float>(ctx, dtable, oi, h.n, h.d, h.S)
+                               : build_hbm_states<double>(ctx, dtable, oi, h.n, h.d, h.S);
+        ctx->stream = keep;
+        if (marks) prof_end(ctx);
+        if (rc) return rc;
+    }
+    if (marks) prof_begin(ctx, 1);
+    if (ps.fp32) k_terms_smem<float><<<ps.grid, NT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue);
+    else k_terms_smem<double><<<ps.grid, NT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue);
+    if (marks) prof_end(ctx);
+    if (marks) prof_begin(ctx, 2);
+    if (ps.fp32) k_combine<float><<<ps.count, NT, 0, st>>>(dtable, ctx->d_status);
+    else k_combine<double><<<ps.count, NT, 0, st>>>(dtable, ctx->d_status);
+    if (marks) prof_end(ctx);
+    DVQLS_CUDA_TRY(ctx, cudaGetLastError());
+    return DVQLS_OK;
+}
+
+// Replays a captured graph of the pass when the launch (table bytes and
+// shape) is the one captured last; otherwise captures it on the context's
+// private capture stream first.  Profiling and callers that are capturing
+// the stream themselves get direct launches.
+static int run_pass(dvqls_ctx* ctx, const Inst* dtable, const PassShape& ps, const std::vector<const HostInst*>& tab,
+                    const std::vector<char>& table_bytes) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;
+    }
+    if (ctx->profiling || cap != cudaStreamCaptureStatusNone)
+        return launch_pass(ctx, ctx->stream, dtable, ps, tab, ctx->profiling);
+    std::vector<char> key(table_bytes);
+    const char* pk = reinterpret_cast<const char*>(&ps);
+    key.insert(key.end(), pk, pk + sizeof ps);
+    if (!ctx->graph || ctx->graph->key != key) {
+        release_graph_cache(ctx);
+        if (!ctx->cap_stream) DVQLS_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        DVQLS_CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = launch_pass(ctx, ctx->cap_stream, dtable, ps, tab, false);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ctx, DVQLS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        }
+        GraphCacheEntry* ge = new GraphCacheEntry();
+        const cudaError_t ei = cudaGraphInstantiate(&ge->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            cudaGetLastError();
+            delete ge;
+            return set_error(ctx, DVQLS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+        }
+        ge->key.swap(key);
+        ctx->graph = ge;
+    }
+    DVQLS_CUDA_TRY(ctx, cudaGraphLaunch(ctx->graph->exec, ctx->stream));
+    return DVQLS_OK;
+}
+
 int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precision, bool want_grad,
               double* costs, double* grads, double* beta_out, double* delta_out) {
     if (!ctx) return DVQLS_ERR_INVALID_ARG;
@@ -668,6 +754,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         return set_error(ctx, DVQLS_ERR_INVALID_ARG, "unknown precision %d", precision);
     std::vector<HostInst> hi(count);
     int nmax = 1, Pmax = 1;
+    bool any_smem = false;
     for (int i = 0; i < count; ++i) {
         const dvqls_instance& q = inst[i];
         const int n = q.ansatz.n, d = q.ansatz.depth;
@@ -690,7 +777,10 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         h.N = 1LL << n;
         h.order = i;
         h.hbm = n > DVQLS_MAX_SMEM_QUBITS;
-        if (!h.hbm) nmax = std::max(nmax, n);
+        if (!h.hbm) {
+            nmax = std::max(nmax, n);
+            any_smem = true;
+        }
         Pmax = std::max(Pmax, h.P);
     }
     cudaSetDevice(ctx->device);
@@ -704,23 +794,21 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     if (bps < 1) return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "term kernel does not fit (%zu B shared)", smem);
     const long long slots = (long long)ctx->num_sms * bps;
 
-    // K split: enough items to fill the machine twice over, at most 8 ways,
-    // at least one chunk per split.
-    // States in HBM take a fixed HBM_K amplitudes per item.
-    long long base_items = 0;
-    for (auto& h : hi) base_items += (long long)h.S * h.T * h.T;
-    int ks = 1;
-    while (ks < 8 && base_items * ks < 2 * slots) ks *= 2;
-    for (auto& h : hi)
-        h.ks = h.hbm ? (int)std::max<long long>(1, h.N / HBM_K)
+    // Amplitude split of the shared-memory instances: autotuned per problem
+    // signature (first call times each candidate); states in HBM take a fixed
+    // HBM_K amplitudes per item.
+    std::string sig = std::to_string(precision) + (want_grad ? "g" : "c") + (beta_out ? "b" : "") +
+                      (delta_out ? "d" : "");
+    for (const auto& h : hi) sig += "|" + std::to_string(h.n) + "," + std::to_string(h.d) + "," + std::to_string(h.L);
+    const int cands[] = {1, 2, 4, 8};
+    auto tuned = ctx->tune.find(sig);
+    const bool tuning = any_smem && tuned == ctx->tune.end();
+    auto ks_for = [&](const HostInst& h, int ks) {
+        return h.hbm ? (int)std::max<long long>(1, h.N / HBM_K)
                      : (int)std::min<long long>(ks, std::max<long long>(1, h.N / JC));
-    // Longest items first (LPT): sort by amplitudes per item, then caller order.
-    std::vector<int> ord(count);
-    for (int i = 0; i < count; ++i) ord[i] = i;
-    std::stable_sort(ord.begin(), ord.end(),
-                     [&](int a, int b) { return hi[a].N / hi[a].ks > hi[b].N / hi[b].ks; });
+    };
 
-    // Plan the workspace.
+    // Plan the workspace (caller order; sized for the largest split tried).
     Arena ar;
     Arena pin;
     struct Off {
@@ -730,12 +818,12 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         size_t pcost, pgrad, pbeta, pdelta;
     };
     std::vector<Off> off(count);
-    long long item_base = 0;
     const size_t o_table = ar.reserve(sizeof(Inst) * count);
     const size_t p_table = pin.reserve(sizeof(Inst) * count);
-    for (int oi = 0; oi < count; ++oi) {
-        const int i = ord[oi];
+    const int ks_plan_smem = tuning ? 8 : (tuned != ctx->tune.end() ? tuned->second : 1);
+    for (int i = 0; i < count; ++i) {
         HostInst& h = hi[i];
+        const int kp = ks_for(h, ks_plan_smem);
         Off& o = off[i];
         const size_t L = h.L;
         o.coef = ar.reserve(L * 16);
@@ -752,10 +840,10 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         o.w = ar.reserve(L * L * 16);
         o.cs = ar.reserve(size_t(3) * h.P * 16);
         o.bn2 = ar.reserve(8);
-        o.Dp = ar.reserve(size_t(h.S) * h.T * h.T * h.ks * 16);
-        o.Tp = ar.reserve(size_t(h.S) * h.T * h.ks * 16);
-        o.Gp = beta_out ? ar.reserve(size_t(h.ks) * L * L * r2) : 0;
-        o.dp = delta_out ? ar.reserve(size_t(h.ks) * L * r2) : 0;
+        o.Dp = ar.reserve(size_t(h.S) * h.T * h.T * kp * 16);
+        o.Tp = ar.reserve(size_t(h.S) * h.T * kp * 16);
+        o.Gp = beta_out ? ar.reserve(size_t(kp) * L * L * r2) : 0;
+        o.dp = delta_out ? ar.reserve(size_t(kp) * L * r2) : 0;
         o.NsDs = ar.reserve(size_t(h.S) * 24);
         o.states = h.hbm ? ar.reserve(size_t(h.S) * size_t(h.N) * r2) : 0;
         o.cost = ar.reserve(8);
@@ -784,7 +872,6 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         rc = pin_acquire(ctx);
         if (rc) return rc;
     }
-    std::vector<Inst> table(count);
     std::vector<long long> grad_off(count, 0);
     {
         long long g = 0;
@@ -793,12 +880,15 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
             g += hi[i].P;
         }
     }
-    for (int oi = 0; oi < count; ++oi) {
-        const int i = ord[oi];
+    // Per-instance records in caller order (staging happens once here).
+    std::vector<Inst> rec(count);
+    const bool dev_cost = costs && is_device_ptr(ctx, costs);
+    const bool dev_grad = grads && is_device_ptr(ctx, grads);
+    for (int i = 0; i < count; ++i) {
         const HostInst& h = hi[i];
         const Off& o = off[i];
         const dvqls_instance& q = inst[i];
-        Inst I;
+        Inst& I = rec[i];
         memset(&I, 0, sizeof I);
         I.n = h.n;
         I.d = h.d;
@@ -806,10 +896,6 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         I.P = h.P;
         I.S = h.S;
         I.T = h.T;
-        I.ks = h.ks;
-        I.items = h.S * h.T * h.T * h.ks;
-        I.item_base = item_base;
-        item_base += I.items;
         I.coef = (const double2*)stage_in(ctx, q.lcu.coef, size_t(h.L) * 16, o.pcoef, o.coef);
         I.xm = (const uint32_t*)stage_in(ctx, q.lcu.xmask, size_t(h.L) * 4, o.pxm, o.xm);
         I.zm = (const uint32_t*)stage_in(ctx, q.lcu.zmask, size_t(h.L) * 4, o.pzm, o.zm);
@@ -826,67 +912,105 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         I.NsDs = (double*)(ws + o.NsDs);
         I.states = h.hbm ? (void*)(ws + o.states) : nullptr;
         // Device outputs are written in place by the combine kernel.
-        const bool dev_cost = costs && is_device_ptr(ctx, costs);
-        const bool dev_grad = grads && is_device_ptr(ctx, grads);
         I.cost = dev_cost ? costs + i : (double*)(ws + o.cost);
         I.grad = !want_grad ? nullptr : dev_grad ? grads + grad_off[i] : (double*)(ws + o.grad);
         I.beta = beta_out ? (double2*)(ws + o.beta) : nullptr;
         I.delta = delta_out ? (double2*)(ws + o.delta) : nullptr;
-        table[oi] = I;
     }
     const Inst* dtable = (const Inst*)(ws + o_table);
     const size_t tbytes = sizeof(Inst) * count;
-    const char* tb = reinterpret_cast<const char*>(table.data());
-    const bool same_table = ctx->last_table.size() == tbytes && memcmp(ctx->last_table.data(), tb, tbytes) == 0;
-    if (!same_table) {
+
+    // Table for split `ks`: instances ordered longest item first (LPT),
+    // item ranges assigned in that order.
+    std::vector<Inst> table(count);
+    std::vector<const HostInst*> tab(count);
+    auto build_table = [&](int ks, PassShape& ps) {
+        std::vector<int> ord(count);
+        for (int i = 0; i < count; ++i) ord[i] = i;
+        std::vector<int> kk(count);
+        for (int i = 0; i < count; ++i) kk[i] = ks_for(hi[i], ks);
+        std::stable_sort(ord.begin(), ord.end(),
+                         [&](int a, int b) { return hi[a].N / kk[a] > hi[b].N / kk[b]; });
+        long long base = 0;
+        for (int oi = 0; oi < count; ++oi) {
+            const int i = ord[oi];
+            Inst I = rec[i];
+            I.ks = kk[i];
+            I.items = I.S * I.T * I.T * I.ks;
+            I.item_base = base;
+            base += I.items;
+            table[oi] = I;
+            tab[oi] = &hi[i];
+        }
+        ps.fp32 = fp32;
+        ps.count = count;
+        ps.total = base;
+        ps.grid = (int)std::min<long long>(base, slots);
+        ps.smem = smem;
+    };
+    auto upload = [&]() -> int {
+        const char* tb = reinterpret_cast<const char*>(table.data());
+        if (ctx->last_table.size() == tbytes && memcmp(ctx->last_table.data(), tb, tbytes) == 0) return DVQLS_OK;
         if (all_device) {
-            rc = pin_acquire(ctx);
-            if (rc) return rc;
+            int r = pin_acquire(ctx);
+            if (r) return r;
         }
         memcpy(ctx->pin + p_table, tb, tbytes);
         DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync((void*)dtable, ctx->pin + p_table, tbytes, cudaMemcpyHostToDevice,
                                             ctx->stream));
         ctx->last_table.assign(tb, tb + tbytes);
+        return pin_release(ctx);
+    };
+
+    PassShape ps{};
+    int ks_use = tuned != ctx->tune.end() ? tuned->second : 1;
+    if (tuning) {
+        // Time one full pass per candidate split and keep the fastest.
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        DVQLS_CUDA_TRY(ctx, cudaEventCreate(&e0));
+        DVQLS_CUDA_TRY(ctx, cudaEventCreate(&e1));
+        float best = 0.f;
+        for (int c : cands) {
+            build_table(c, ps);
+            rc = upload();
+            if (!rc) rc = (cudaEventRecord(e0, ctx->stream) == cudaSuccess) ? DVQLS_OK : DVQLS_ERR_CUDA;
+            if (!rc) rc = launch_pass(ctx, ctx->stream, dtable, ps, tab, false);
+            if (!rc) rc = (cudaEventRecord(e1, ctx->stream) == cudaSuccess) ? DVQLS_OK : DVQLS_ERR_CUDA;
+            if (!rc) rc = (cudaEventSynchronize(e1) == cudaSuccess) ? DVQLS_OK : DVQLS_ERR_CUDA;
+            float ms = 0.f;
+            if (!rc) rc = (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ? DVQLS_OK : DVQLS_ERR_CUDA;
+            if (rc) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                cudaGetLastError();
+                return rc == DVQLS_ERR_CUDA ? set_error(ctx, rc, "autotune pass failed") : rc;
+            }
+            if (c == cands[0] || ms < best) {
+                best = ms;
+                ks_use = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ctx->tune[sig] = ks_use;
     }
-    if (!same_table || !all_device) {
-        rc = pin_release(ctx);
-        if (rc) return rc;
-    }
-    DVQLS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_queue, 0, sizeof(unsigned long long), ctx->stream));
-    prof_begin(ctx, 0);
-    k_prepare<<<count, NT, 0, ctx->stream>>>(dtable, ctx->d_status);
-    prof_end(ctx);
-    for (int oi = 0; oi < count; ++oi) {
-        const HostInst& h = hi[ord[oi]];
-        if (!h.hbm) continue;
-        prof_begin(ctx, 3);
-        rc = fp32 ? build_hbm_states<float>(ctx, dtable, oi, h.n, h.d, h.S)
-                  : build_hbm_states<double>(ctx, dtable, oi, h.n, h.d, h.S);
-        prof_end(ctx);
-        if (rc) return rc;
-    }
-    const long long total = item_base;
-    const int grid = (int)std::min<long long>(total, slots);
-    prof_begin(ctx, 1);
-    if (fp32) k_terms_smem<float><<<grid, NT, smem, ctx->stream>>>(dtable, count, total, ctx->d_queue);
-    else k_terms_smem<double><<<grid, NT, smem, ctx->stream>>>(dtable, count, total, ctx->d_queue);
-    prof_end(ctx);
-    prof_begin(ctx, 2);
-    if (fp32) k_combine<float><<<count, NT, 0, ctx->stream>>>(dtable, ctx->d_status);
-    else k_combine<double><<<count, NT, 0, ctx->stream>>>(dtable, ctx->d_status);
-    prof_end(ctx);
-    DVQLS_CUDA_TRY(ctx, cudaGetLastError());
+    build_table(ks_use, ps);
+    rc = upload();
+    if (!rc && !all_device) rc = pin_release(ctx);
+    if (rc) return rc;
+    rc = run_pass(ctx, dtable, ps, tab, ctx->last_table);
+    if (rc) return rc;
 
     // Results.
     std::vector<PendingOut> pend;
     for (int i = 0; i < count; ++i) {
         const Off& o = off[i];
         const HostInst& h = hi[i];
-        if (costs && !is_device_ptr(ctx, costs)) {
+        if (costs && !dev_cost) {
             rc = enqueue_out(ctx, costs + i, ws + o.cost, 8, o.pcost, pend);
             if (rc) return rc;
         }
-        if (want_grad && grads && !is_device_ptr(ctx, grads)) {
+        if (want_grad && grads && !dev_grad) {
             rc = enqueue_out(ctx, grads + grad_off[i], ws + o.grad, size_t(h.P) * 8, o.pgrad, pend);
             if (rc) return rc;
         }
