@@ -28,6 +28,8 @@ def lib():
                                             ctypes.c_uint32, ctypes.c_uint32, dp, dp]
         L.oracle_circuit_terms.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int,
                                            up, up, dp, dp, ctypes.c_int]
+        L.oracle_circuit_local_terms.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int,
+                                                 up, up, dp, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -116,3 +118,38 @@ def circuit_cost_grad(n, d, alpha, b, coef, xs, zs, nthreads=0, shifts=None):
         out["cost"] = 1.0 - N[0] / D[0]
         out["grad"] = -(dN * D[0] - N[0] * dD) / D[0] ** 2
     return out
+
+
+def circuit_local_terms(n, d, alpha, b, xs, zs, nthreads=0, b_plus=None):
+    """gamma[j, l, m] = <psi| A_l^dag U_b Z_j U_b^dag A_m |psi> from 2 n L^2
+    simulated circuits.  Returns (gamma, threads used)."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    bv = _cvec(b)
+    if b_plus is None:
+        b_plus = is_plus_state(bv)
+    x = np.ascontiguousarray(xs, dtype=np.uint32)
+    z = np.ascontiguousarray(zs, dtype=np.uint32)
+    L = x.size
+    gamma = np.zeros((n, L, L), dtype=np.complex128)
+    used = lib().oracle_circuit_local_terms(n, d, _dp(a), _dp(bv.view(np.float64)), int(b_plus), L, _up(x),
+                                            _up(z), _dp(gamma.view(np.float64)), int(nthreads))
+    assert used > 0
+    return gamma, used
+
+
+def circuit_local_cost_grad(n, d, alpha, b, coef, xs, zs, nthreads=0):
+    """Local cost C_L and its parameter-shift gradient with every overlap from
+    its Hadamard-test circuits (2 (n+1) L^2 per angle vector)."""
+    from .terms import local_combine
+    A = shifted_angles(alpha)
+    E = np.zeros(A.shape[0])
+    D = np.zeros(A.shape[0])
+    for s in range(A.shape[0]):
+        beta, _, _ = circuit_terms(n, d, A[s], b, xs, zs, nthreads)
+        gamma, _ = circuit_local_terms(n, d, A[s], b, xs, zs, nthreads)
+        _, E[s], D[s] = local_combine(coef, beta, gamma)
+    n_ = float(n)
+    dE = 0.5 * (E[1::2] - E[2::2])
+    dD = 0.5 * (D[1::2] - D[2::2])
+    return {"cost": 0.5 - 0.5 * E[0] / (n_ * D[0]),
+            "grad": -0.5 * (dE * D[0] - E[0] * dD) / (n_ * D[0] ** 2)}

@@ -11,6 +11,9 @@
  *   - Each overlap is measured by a Hadamard test with a single ancilla
  *     measurement (Sec. 2.1, last paragraph; Sec. 2.2 after Eq. 4: separate
  *     circuits for the real and the imaginary part).
+ *   - The local cost (Eq. 2, expanded in Eq. 4): the numerator overlaps
+ *     <x| A_l^dag U_b P_j U_b^dag A_m |x> with P_j = (I + Z_j)/2 need the
+ *     extra Hadamard tests gamma^j_lm = <x| A_l^dag U_b Z_j U_b^dag A_m |x>.
  *   - The circuit body of Sec. 2.3: ansatz V(theta), two controlled Pauli
  *     strings, ancilla preparation and measurement.  For delta_l the whole
  *     U = U_b^dag A_l V(theta) is controlled; the ansatz is the Ry + CZ-ring
@@ -155,6 +158,33 @@ static void controlled_ub_dag(cplx* psi, int nq, int n, int anc, const cplx* b, 
     free(w);
 }
 
+/* Controlled U_b (see the header for U_b). */
+static void controlled_ub(cplx* psi, int nq, int n, int anc, const cplx* b, int b_plus) {
+    if (b_plus) {
+        for (int q = 0; q < n; ++q) gate_h(psi, nq, q, anc);
+        return;
+    }
+    const size_t N = (size_t)1 << n;
+    cplx ph = 1.0;
+    if (cabs(b[0]) > 0.0) ph = b[0] / cabs(b[0]);
+    cplx* w = (cplx*)malloc(N * sizeof(cplx));
+    double ww = 0.0;
+    for (size_t i = 0; i < N; ++i) {
+        w[i] = (i == 0 ? ph : 0.0) - b[i];
+        ww += creal(conj(w[i]) * w[i]);
+    }
+    cplx* v = psi + ((size_t)1 << anc);
+    if (ww > 0.0) {
+        cplx wv = 0.0;
+        for (size_t i = 0; i < N; ++i) wv += conj(w[i]) * v[i];
+        const cplx f = 2.0 * wv / ww;
+        for (size_t i = 0; i < N; ++i) v[i] -= f * w[i];
+    }
+    /* U_b = e^{i phi} (I - 2 w w^dag / w^dag w) */
+    for (size_t i = 0; i < N; ++i) v[i] *= ph;
+    free(w);
+}
+
 static double z_ancilla(const cplx* psi, int n) {
     const size_t N = (size_t)1 << n;
     double p0 = 0.0, p1 = 0.0;
@@ -189,6 +219,26 @@ static double hadamard_delta(cplx* buf, int n, int d, const double* alpha, const
     ansatz(buf, nq, n, d, alpha, anc);
     controlled_pauli(buf, nq, n, anc, xl, zl);
     controlled_ub_dag(buf, nq, n, anc, b, b_plus);
+    if (part) gate_sdg(buf, nq, anc);
+    gate_h(buf, nq, anc, -1);
+    return z_ancilla(buf, n);
+}
+
+/* One Hadamard test for gamma^j_lm = <psi| A_l^dag U_b Z_j U_b^dag A_m |psi>,
+ * the numerator overlaps of the local cost (Eq. 2, Eq. 4): controlled A_m,
+ * controlled U_b^dag, controlled Z_j, controlled U_b, controlled A_l. */
+static double hadamard_gamma(cplx* buf, int n, int d, const double* alpha, const cplx* b, int b_plus,
+                             uint32_t xl, uint32_t zl, uint32_t xm, uint32_t zm, int j, int part) {
+    const int nq = n + 1, anc = n;
+    memset(buf, 0, sizeof(cplx) << nq);
+    buf[0] = 1.0;
+    gate_h(buf, nq, anc, -1);
+    ansatz(buf, nq, n, d, alpha, -1);
+    controlled_pauli(buf, nq, n, anc, xm, zm);
+    controlled_ub_dag(buf, nq, n, anc, b, b_plus);
+    gate_phase_flip(buf, nq, ((size_t)1 << anc) | ((size_t)1 << j));
+    controlled_ub(buf, nq, n, anc, b, b_plus);
+    controlled_pauli(buf, nq, n, anc, xl, zl);
     if (part) gate_sdg(buf, nq, anc);
     gate_h(buf, nq, anc, -1);
     return z_ancilla(buf, n);
@@ -262,6 +312,40 @@ int oracle_circuit_terms(int n, int d, const double* alpha, const double* b, int
                 delta[2 * l + part] =
                     hadamard_delta(buf, n, d, alpha, (const cplx*)b, b_plus, x[l], z[l], part);
             }
+        }
+        free(buf);
+    }
+    return used;
+}
+
+/* All n L^2 numerator overlaps gamma^j_lm of the local cost at one angle
+ * vector, two circuits each (real, imaginary), OpenMP over circuits.
+ * gamma: n * L * L complex, index (j * L + l) * L + m, interleaved.
+ * Returns the number of threads used. */
+int oracle_circuit_local_terms(int n, int d, const double* alpha, const double* b, int b_plus, int L,
+                               const uint32_t* x, const uint32_t* z, double* gamma, int nthreads) {
+    if (bad_args(n, d, L)) return -1;
+    const long nterm = (long)n * L * L;
+    int used = 1;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        cplx* buf = (cplx*)malloc(sizeof(cplx) << (n + 1));
+#ifdef _OPENMP
+#pragma omp single
+        used = omp_get_num_threads();
+#pragma omp for schedule(dynamic, 4)
+#endif
+        for (long t = 0; t < 2 * nterm; ++t) {
+            const long term = t >> 1;
+            const int part = (int)(t & 1);
+            const int j = (int)(term / ((long)L * L));
+            const long r = term % ((long)L * L);
+            const int l = (int)(r / L), m = (int)(r % L);
+            gamma[2 * term + part] =
+                hadamard_gamma(buf, n, d, alpha, (const cplx*)b, b_plus, x[l], z[l], x[m], z[m], j, part);
         }
         free(buf);
     }

@@ -19,6 +19,12 @@ What it computes, each quantity straight from its definition:
     dC = -(N' D - N D') / D^2.  Shift s = 0 is alpha, s = 2k+1 is
     alpha + (pi/2) e_k and s = 2k+2 is alpha - (pi/2) e_k.
   - Fidelity F = |<xhat|psi>|^2 (Sec. 3.1).
+  - The local cost (Eq. 2, expanded in Eq. 4) for b = |+>^n, where
+    U_b Z_j U_b^dag = X_j: with P_j = (I + Z_j)/2,
+    C_L = 1 - (1/n) sum_j sum_lm conj(c_l) c_m (beta_lm + gamma^j_lm) / (2 D)
+        = 1/2 - Re[E / (n D)] / 2,  E = sum_j sum_lm conj(c_l) c_m gamma^j_lm,
+    gamma^j_lm = <psi| A_l^dag X_j A_m |psi> (the closed form of Sec. 2.3,
+    Stage III), and its parameter-shift gradient from E and D.
 
 Conventions: qubit k is bit k of the basis index; Ry(t) = [[cos t/2,
 -sin t/2], [sin t/2, cos t/2]]; CZ ring = CZ(q, q+1) for q < n-1 plus
@@ -159,3 +165,42 @@ def classical_solution(M, b):
 
 def fidelity(psi, xhat):
     return float(np.abs(np.vdot(xhat, psi)) ** 2)
+
+
+def apply_x(j, v):
+    """X on qubit j: amplitude i takes the value at i XOR 2^j."""
+    i = np.arange(v.size)
+    return v[i ^ (1 << j)]
+
+
+def local_terms(psi, xs, zs, n):
+    """beta (L x L) and gamma (n x L x L) for b = |+>^n by their definitions."""
+    Phi = np.stack([apply_pauli(x, z, psi) for x, z in zip(xs, zs)], axis=1)
+    beta = Phi.conj().T @ Phi
+    gamma = np.stack([Phi.conj().T @ np.stack([apply_x(j, Phi[:, m]) for m in range(Phi.shape[1])], axis=1)
+                      for j in range(n)])
+    return beta, gamma
+
+
+def local_combine(coef, beta, gamma):
+    """(C_L, E, D): E = sum_j conj(c)^T gamma^j c, D = conj(c)^T beta c."""
+    coef = np.asarray(coef, dtype=np.complex128)
+    D = (np.conj(coef) @ beta @ coef).real
+    E = sum((np.conj(coef) @ g @ coef).real for g in gamma)
+    n = len(gamma)
+    return 0.5 - 0.5 * E / (n * D), E, D
+
+
+def local_cost_grad(n, d, alpha, coef, xs, zs):
+    """Local cost (b = |+>^n) and its parameter-shift gradient."""
+    shifts = shifted_angles(alpha)
+    S = shifts.shape[0]
+    E = np.zeros(S)
+    D = np.zeros(S)
+    for s in range(S):
+        beta, gamma = local_terms(ansatz_state(n, d, shifts[s]), xs, zs, n)
+        _, E[s], D[s] = local_combine(coef, beta, gamma)
+    dE = 0.5 * (E[1::2] - E[2::2])
+    dD = 0.5 * (D[1::2] - D[2::2])
+    return {"cost": 0.5 - 0.5 * E[0] / (n * D[0]), "grad": -0.5 * (dE * D[0] - E[0] * dD) / (n * D[0] ** 2),
+            "E_s": E, "D_s": D}
