@@ -209,6 +209,26 @@ typedef struct {
 int dvqls_cost_grad_batched(dvqls_ctx* ctx, int count, const dvqls_instance* inst,
                             int precision, double* costs, double* grads);
 
+/* Local cost (Eq. 2, expanded in Eq. 4; closed form of Sec. 2.3 Stage III):
+ *   C_L = 1 - (1/n) sum_j <x|A^dag U_b P_j U_b^dag A|x> / <x|A^dag A|x>,
+ *   P_j = (I + Z_j)/2, which is C_L = 1/2 - E / (2 n D) with
+ *   D = sum_lm c_l^* c_m beta_lm and E = sum_j sum_lm c_l^* c_m gamma^j_lm,
+ *   gamma^j_lm = <x| A_l^dag U_b Z_j U_b^dag A_m |x>
+ * -- the paper's (n+1) L^2 expectation values per evaluation.  Served for
+ * b = |+>^n (U_b = H^(x)n, so U_b Z_j U_b^dag = X_j and every gamma^j_lm is a
+ * Pauli-string overlap); b is not an argument.  grad may be NULL (cost only);
+ * with grad, the 2P+1 shifted evaluations give the exact parameter-shift
+ * gradient of E and D.  Same arithmetic split as dvqls_cost_grad (FP32 or
+ * FP64 terms, FP64 sums). */
+int dvqls_local_cost_grad(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alpha,
+                          const dvqls_lcu* lcu, int precision, double* cost, double* grad);
+
+/* Local cost of `count` instances in one pass (inst[i].b is ignored); costs,
+ * grads and the asynchronous behaviour as dvqls_cost_grad_batched; grads NULL
+ * evaluates the cost only. */
+int dvqls_local_cost_grad_batched(dvqls_ctx* ctx, int count, const dvqls_instance* inst,
+                                  int precision, double* costs, double* grads);
+
 /* Per-circuit FP64 path (Sec. 2.3 execution model; Sec. 2.2 after Eq. 4):
  * each Hadamard-test circuit -- S (L^2 + L) expectation values, real and
  * imaginary part each from its own circuit, 2 S (L^2 + L) circuits -- is

@@ -20,7 +20,7 @@
 namespace dvqls {
 
 int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precision, bool want_grad, double* costs,
-              double* grads, double* beta_out, double* delta_out);
+              double* grads, double* beta_out, double* delta_out, bool local);
 
 namespace {
 
@@ -434,7 +434,7 @@ extern "C" int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* i
         }
         const int na = int(active.size());
         k_fidelity<<<na, FT, fsmem, ctx->stream>>>((const FidInst*)(base + o_ft), ctx->d_status);
-        rc = run_batch(ctx, na, ainst.data(), opt->precision, true, costs, g, nullptr, nullptr);
+        rc = run_batch(ctx, na, ainst.data(), opt->precision, true, costs, g, nullptr, nullptr, false);
         if (rc) return rc;
         DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(hF.data(), F, size_t(count) * 8, cudaMemcpyDeviceToHost, ctx->stream));
         DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(hC.data(), costs, size_t(na) * 8, cudaMemcpyDeviceToHost, ctx->stream));

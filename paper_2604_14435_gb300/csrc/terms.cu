@@ -39,6 +39,8 @@ constexpr int MAX_ANGLES = 1024;
 
 struct Inst {
     int n, d, L, P, S, T, ks;
+    int F;      // term flavors per shift: 1 (global cost) or n + 1 (local cost)
+    int local;  // 1: local cost C_L (b = |+>^n), 0: global cost
     int items;
     long long item_base;
     const double2* coef;
@@ -84,10 +86,11 @@ __global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, 
     const long long N = 1LL << I.n;
     __shared__ double red[NT / 32];
     double acc = 0.0;
-    for (long long j = t; j < N; j += NT) {
+    for (long long j = t; j < N && I.b; j += NT) {
         const double2 v = I.b[j];
         acc += v.x * v.x + v.y * v.y;
     }
+    if (!I.b && t == 0) acc = 1.0;  // local cost: b = |+>^n is implied and never read
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((t & 31) == 0) red[t >> 5] = acc;
     for (int l = t; l < I.L; l += NT) {
@@ -179,7 +182,8 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
     const int n = I.n, N = 1 << n, L = I.L, T = I.T, ks = I.ks, t = threadIdx.x;
     const int ksi = local % ks;
     const int rest = local / ks;
-    const int u = rest % (T * T), s = rest / (T * T);
+    const int u = rest % (T * T), rest2 = rest / (T * T);
+    const int f = rest2 % I.F, s = rest2 / I.F;  // flavor 0: beta; j + 1: gamma^j (X_j on the m side)
     int tl, tm, half = 0;
     const bool diag = u < T;
     if (diag) {
@@ -211,12 +215,15 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
     uint32_t* szm = smask + 3 * TT;
     const int mofs = diag ? 0 : half * (TT / 2);  // first m column of this item within tile tm
     const int mcols = diag ? TT : TT / 2;
+    const bool same = diag && f == 0;                     // phi_m is phi_l
+    const bool want_delta = diag && f == 0 && !I.local;   // delta~ rows (global cost only)
+    const uint32_t xflip = f > 0 ? (1u << (f - 1)) : 0u;  // X_j A_m = sigma(x_m ^ e_j, z_m)
     if (t < TT) {
         const int l = tl * TT + t;
         sxl[t] = l < L ? I.xm[l] : 0u;
         szl[t] = l < L ? I.zm[l] : 0u;
         const int m = tm * TT + t;
-        sxm[t] = m < L ? I.xm[m] : 0u;
+        sxm[t] = m < L ? (I.xm[m] ^ xflip) : 0u;
         szm[t] = m < L ? I.zm[m] : 0u;
     }
     if (I.states) __syncthreads();
@@ -240,7 +247,7 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
             bb = half * 8 + (slot & 7);
         }
     }
-    const R2* Pm = diag ? Phl : Phm;
+    const R2* Pm = same ? Phl : Phm;
     R are[4][4], aim[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -267,7 +274,7 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
             }
             Phl[at] = v;
         }
-        if (!diag) {
+        if (!same) {
             for (int e = t; e < JC * mcols; e += NT) {
                 const int jj = e & (JC - 1), m = mofs + e / JC, j = j0 + jj;
                 const int at = jj * TT + (m ^ ((jj & 15) << 2));
@@ -281,7 +288,7 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
                 Phm[at] = v;
             }
         }
-        if (diag && t < JC) {
+        if (want_delta && t < JC) {
             R2 v;
             v.x = v.y = (R)0;
             if (j0 + t < kend) {
@@ -311,7 +318,7 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
                     }
             }
         }
-        if (diag && t < 4 * TT) {  // delta~_l partial: thread t owns l = t % 64, a quarter of the chunk rows
+        if (want_delta && t < 4 * TT) {  // delta~_l partial: thread t owns l = t % 64, a quarter of the chunk rows
             const int l = t % TT, q = t / TT;
 #pragma unroll
             for (int jj = q * (JC / 4); jj < (q + 1) * (JC / 4); ++jj) {
@@ -363,7 +370,7 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
                     }
                 }
             }
-        if (s == 0 && I.Gpart) {
+        if (s == 0 && f == 0 && I.Gpart) {
             R2* G = reinterpret_cast<R2*>(I.Gpart) + (long long)ksi * L * L;
 #pragma unroll
             for (int a = 0; a < 4; ++a)
@@ -383,10 +390,10 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
                 }
         }
     }
-    const long long slotD = ((long long)s * T * T + u) * ks + ksi;
+    const long long slotD = (((long long)s * I.F + f) * T * T + u) * ks + ksi;
     const double2 dtot = block_sum2(dsum, red);
     if (t == 0) I.Dpart[slotD] = dtot;
-    if (diag) {
+    if (want_delta) {
         // Reduce the four row-quarter partials of each l, then weight by ctil in FP64.
         R2* dred = Phm;  // free (diagonal items do not use it)
         if (t < 4 * TT) dred[t] = dacc;
@@ -576,10 +583,18 @@ __global__ void __launch_bounds__(NT) k_combine(const Inst* __restrict__ insts, 
     const double bn2 = *I.bn2;
     for (int s = t; s < I.S; s += NT) {
         double2 D = make_double2(0.0, 0.0), Tv = make_double2(0.0, 0.0);
-        const double2* dp = I.Dpart + (long long)s * T * T * ks;
+        const double2* dp = I.Dpart + (long long)s * I.F * T * T * ks;
         for (int e = 0; e < T * T * ks; ++e) {
             D.x += dp[e].x;
             D.y += dp[e].y;
+        }
+        if (I.local) {  // E_s = sum over the gamma flavors (real parts)
+            double E = 0.0;
+            for (int e = T * T * ks; e < I.F * T * T * ks; ++e) E += dp[e].x;
+            I.NsDs[3 * s] = E;
+            I.NsDs[3 * s + 1] = D.x;
+            I.NsDs[3 * s + 2] = D.y;
+            continue;
         }
         const double2* tp = I.Tpart + (long long)s * T * ks;
         for (int e = 0; e < T * ks; ++e) {
@@ -592,15 +607,17 @@ __global__ void __launch_bounds__(NT) k_combine(const Inst* __restrict__ insts, 
     }
     __syncthreads();
     const double N0 = I.NsDs[0], D0 = I.NsDs[1];
+    // Global cost: C = 1 - N/D.  Local cost: C_L = 1/2 - E / (2 n D) (N holds E).
+    const double scale = I.local ? 0.5 / I.n : 1.0;
     if (t == 0) {
         if (!(D0 > 0.0) || !isfinite(D0) || !isfinite(N0)) set_status(status, DEV_BAD_DENOMINATOR);
-        *I.cost = 1.0 - N0 / D0;
+        *I.cost = (I.local ? 0.5 : 1.0) - scale * N0 / D0;
     }
     if (I.grad && I.S > 1)
         for (int k = t; k < I.P; k += NT) {
             const double dN = 0.5 * (I.NsDs[3 * (2 * k + 1)] - I.NsDs[3 * (2 * k + 2)]);
             const double dD = 0.5 * (I.NsDs[3 * (2 * k + 1) + 1] - I.NsDs[3 * (2 * k + 2) + 1]);
-            I.grad[k] = -(dN * D0 - N0 * dD) / (D0 * D0);
+            I.grad[k] = -scale * (dN * D0 - N0 * dD) / (D0 * D0);
         }
     if (I.beta) {
         const R2* G = reinterpret_cast<const R2*>(I.Gpart);
@@ -644,7 +661,7 @@ __global__ void __launch_bounds__(NT) k_combine(const Inst* __restrict__ insts, 
 
 // ------------------------------------------------------------------- host
 struct HostInst {
-    int n, d, L, P, S, T, ks;
+    int n, d, L, P, S, T, ks, F;
     long long N;
     int order;  // position in the caller's array
     bool hbm;   // n > 12: states built in HBM
@@ -746,8 +763,10 @@ static int run_pass(dvqls_ctx* ctx, const Inst* dtable, const PassShape& ps, con
 }
 
 int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precision, bool want_grad,
-              double* costs, double* grads, double* beta_out, double* delta_out) {
+              double* costs, double* grads, double* beta_out, double* delta_out, bool local) {
     if (!ctx) return DVQLS_ERR_INVALID_ARG;
+    if (local && (beta_out || delta_out))
+        return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "the local cost has no beta / delta output");
     ctx->err.clear();
     if (count < 1 || !inst) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "count must be >= 1");
     if (precision != DVQLS_FP32 && precision != DVQLS_FP64)
@@ -763,11 +782,12 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         if (q.ansatz.kind != DVQLS_ANSATZ_RY_CZRING)
             return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "instance %d: ansatz kind %d", i, q.ansatz.kind);
         const int L = q.lcu.L;
-        if (L < 1 || !q.lcu.coef || !q.lcu.xmask || !q.lcu.zmask || !q.alpha || !q.b)
+        if (L < 1 || !q.lcu.coef || !q.lcu.xmask || !q.lcu.zmask || !q.alpha || (!q.b && !local))
             return set_error(ctx, DVQLS_ERR_INVALID_ARG, "instance %d: empty LCU or NULL input", i);
         const long long P = (long long)n * (d + 1);
         if (P > MAX_ANGLES) return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "instance %d: %lld angles", i, P);
         HostInst& h = hi[i];
+        h.F = local ? n + 1 : 1;
         h.n = n;
         h.d = d;
         h.L = L;
@@ -798,7 +818,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     // signature (first call times each candidate); states in HBM take a fixed
     // HBM_K amplitudes per item.
     std::string sig = std::to_string(precision) + (want_grad ? "g" : "c") + (beta_out ? "b" : "") +
-                      (delta_out ? "d" : "");
+                      (delta_out ? "d" : "") + (local ? "L" : "");
     for (const auto& h : hi) sig += "|" + std::to_string(h.n) + "," + std::to_string(h.d) + "," + std::to_string(h.L);
     const int cands[] = {1, 2, 4, 8};
     auto tuned = ctx->tune.find(sig);
@@ -834,13 +854,13 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         o.pzm = pin.reserve(L * 4);
         o.alpha = ar.reserve(size_t(h.P) * 8);
         o.palpha = pin.reserve(size_t(h.P) * 8);
-        o.b = ar.reserve(size_t(h.N) * 16);
-        o.pb = pin.reserve(size_t(h.N) * 16);
+        o.b = local ? 0 : ar.reserve(size_t(h.N) * 16);
+        o.pb = local ? 0 : pin.reserve(size_t(h.N) * 16);
         o.ctil = ar.reserve(L * 16);
         o.w = ar.reserve(L * L * 16);
         o.cs = ar.reserve(size_t(3) * h.P * 16);
         o.bn2 = ar.reserve(8);
-        o.Dp = ar.reserve(size_t(h.S) * h.T * h.T * kp * 16);
+        o.Dp = ar.reserve(size_t(h.S) * h.F * h.T * h.T * kp * 16);
         o.Tp = ar.reserve(size_t(h.S) * h.T * kp * 16);
         o.Gp = beta_out ? ar.reserve(size_t(kp) * L * L * r2) : 0;
         o.dp = delta_out ? ar.reserve(size_t(kp) * L * r2) : 0;
@@ -866,7 +886,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     for (int i = 0; i < count && all_device; ++i) {
         const dvqls_instance& q = inst[i];
         all_device = is_device_ptr(ctx, q.lcu.coef) && is_device_ptr(ctx, q.lcu.xmask) &&
-                     is_device_ptr(ctx, q.lcu.zmask) && is_device_ptr(ctx, q.alpha) && is_device_ptr(ctx, q.b);
+                     is_device_ptr(ctx, q.lcu.zmask) && is_device_ptr(ctx, q.alpha) &&
+                     (local || is_device_ptr(ctx, q.b));
     }
     if (!all_device) {
         rc = pin_acquire(ctx);
@@ -900,7 +921,9 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         I.xm = (const uint32_t*)stage_in(ctx, q.lcu.xmask, size_t(h.L) * 4, o.pxm, o.xm);
         I.zm = (const uint32_t*)stage_in(ctx, q.lcu.zmask, size_t(h.L) * 4, o.pzm, o.zm);
         I.alpha = (const double*)stage_in(ctx, q.alpha, size_t(h.P) * 8, o.palpha, o.alpha);
-        I.b = (const double2*)stage_in(ctx, q.b, size_t(h.N) * 16, o.pb, o.b);
+        I.b = local ? nullptr : (const double2*)stage_in(ctx, q.b, size_t(h.N) * 16, o.pb, o.b);
+        I.F = h.F;
+        I.local = local ? 1 : 0;
         I.ctil = (double2*)(ws + o.ctil);
         I.w = (double2*)(ws + o.w);
         I.cs = (double2*)(ws + o.cs);
@@ -936,7 +959,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
             const int i = ord[oi];
             Inst I = rec[i];
             I.ks = kk[i];
-            I.items = I.S * I.T * I.T * I.ks;
+            I.items = I.S * I.F * I.T * I.T * I.ks;
             I.item_base = base;
             base += I.items;
             table[oi] = I;
@@ -1044,7 +1067,7 @@ static int single(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alph
     in.lcu = *lcu;
     in.alpha = alpha;
     in.b = b;
-    int rc = run_batch(ctx, 1, &in, precision, grad, cost, g, beta, delta);
+    int rc = run_batch(ctx, 1, &in, precision, grad, cost, g, beta, delta, false);
     if (rc == DVQLS_OK && is_device_ptr(ctx, cost)) rc = sync_and_check(ctx);
     return rc;
 }
@@ -1063,7 +1086,26 @@ extern "C" int dvqls_cost_grad(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const
 
 extern "C" int dvqls_cost_grad_batched(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precision,
                                        double* costs, double* grads) {
-    return run_batch(ctx, count, inst, precision, true, costs, grads, nullptr, nullptr);
+    return run_batch(ctx, count, inst, precision, true, costs, grads, nullptr, nullptr, false);
+}
+
+extern "C" int dvqls_local_cost_grad_batched(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precision,
+                                             double* costs, double* grads) {
+    return run_batch(ctx, count, inst, precision, grads != nullptr, costs, grads, nullptr, nullptr, true);
+}
+
+extern "C" int dvqls_local_cost_grad(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alpha,
+                                     const dvqls_lcu* lcu, int precision, double* cost, double* grad) {
+    if (!ctx) return DVQLS_ERR_INVALID_ARG;
+    if (!ansatz || !lcu || !cost) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "NULL ansatz, lcu or cost");
+    dvqls_instance in;
+    in.ansatz = *ansatz;
+    in.lcu = *lcu;
+    in.alpha = alpha;
+    in.b = nullptr;
+    int rc = run_batch(ctx, 1, &in, precision, grad != nullptr, cost, grad, nullptr, nullptr, true);
+    if (rc == DVQLS_OK && is_device_ptr(ctx, cost)) rc = sync_and_check(ctx);
+    return rc;
 }
 
 // ------------------------------------------------- allocation-free variant
@@ -1180,6 +1222,7 @@ extern "C" int dvqls_cost_grad_noalloc(void* stream_arg, const dvqls_ansatz* ans
     I.S = S;
     I.T = T;
     I.ks = ks;
+    I.F = 1;
     I.items = S * T * T * ks;
     I.item_base = 0;
     I.coef = (const double2*)lcu->coef;

@@ -35,6 +35,7 @@ EXPORTED = [
     "dvqls_circuit_cost_grad_fp64", "dvqls_fidelity", "dvqls_lcu_solve", "dvqls_optimize",
     "dvqls_ws_param_count", "dvqls_ws_create", "dvqls_ws_destroy", "dvqls_ws_infer", "dvqls_ws_grad",
     "dvqls_ws_train_step", "dvqls_ws_get_params", "dvqls_ws_save", "dvqls_ws_load",
+    "dvqls_local_cost_grad", "dvqls_local_cost_grad_batched",
 ]
 
 
@@ -120,6 +121,10 @@ def lib():
         L.dvqls_ws_get_params.argtypes = [vp, vp]
         L.dvqls_ws_save.argtypes = [vp, ctypes.c_char_p]
         L.dvqls_ws_load.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
+        L.dvqls_local_cost_grad.argtypes = [vp, ctypes.POINTER(dvqls_ansatz), dp, ctypes.POINTER(dvqls_lcu),
+                                            ctypes.c_int, dp, dp]
+        L.dvqls_local_cost_grad_batched.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dvqls_instance), ctypes.c_int,
+                                                    dp, dp]
         _lib = L
     return _lib
 
@@ -323,3 +328,13 @@ def dvqls_ws_load(ctx, path):
         f.read(8)
         I, H, O = np.frombuffer(f.read(12), dtype=np.int32)
     return WarmStart(ctx, h, int(I), int(H), int(O))
+
+
+def dvqls_local_cost_grad(ctx, ansatz, alpha, lcu, precision, cost, grad=None):
+    _check(ctx, lib().dvqls_local_cost_grad(ctx, ctypes.byref(ansatz), ptr(alpha), ctypes.byref(lcu),
+                                            int(precision), ptr(cost), ptr(grad)))
+
+
+def dvqls_local_cost_grad_batched(ctx, instances, precision, costs, grads):
+    _check(ctx, lib().dvqls_local_cost_grad_batched(ctx, len(instances), instances, int(precision), ptr(costs),
+                                                    ptr(grads)))
