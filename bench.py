@@ -46,6 +46,15 @@ METRIC = "cost+grad evals/sec at n=10, L=64 (FP32 batched vs FP64 circuit path)"
 UNIT = "evals/s"
 SMS, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates (PFLOP/s) of the two input types
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "of measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
 
 
 def executed_gram_entries(L):
@@ -159,15 +168,18 @@ def make_batch(D, ctx, torch, rank, name):
     return D.make_instances(items), D.make_instances(host_items), keep, shapes
 
 
-def work_of(shapes):
-    """Paper terms, algorithmic and executed FLOPs of one cost+grad pass."""
+def work_of(shapes, tensor=False):
+    """Paper terms, algorithmic and executed FLOPs of one cost+grad pass.
+    The tensor-core kernel executes, per shift and amplitude, three real
+    128 x 128 rank-1 updates (hi hi^T + hi lo^T + lo hi^T) of the stacked
+    real and imaginary term rows."""
     terms = alg = exe = 0
     for n, d, L in shapes:
         S = 2 * n * (d + 1) + 1
         N = 1 << n
         terms += S * (L * L + L)
         alg += S * (L * L + L) * 8 * N
-        exe += S * executed_gram_entries(L) * 8 * N
+        exe += S * (3 * 2 * 128 * 128 * N if tensor else executed_gram_entries(L) * 8 * N)
     return terms, alg, exe
 
 
@@ -244,6 +256,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="toeplitz10", choices=["toeplitz10", "uneven", "hele_shaw"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_tc"],
+                    help="term kernel: FP32 CUDA cores, or 3xTF32 tcgen05 tensor cores (L <= 64)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -265,9 +279,11 @@ def main():
         pg.barrier()
     from paper_2604_14435_gb300 import dvqls as D
 
+    PREC = D.DVQLS_FP32_TC if args.precision == "fp32_tc" else D.DVQLS_FP32
     stream = torch.cuda.current_stream()
     ctx = D.dvqls_create(local, stream.cuda_stream)
     dev_arr, host_arr, keep, shapes = make_batch(D, ctx, torch, rank, args.workload)
+    tensor = args.precision == "fp32_tc" and all(L <= 64 for _, _, L in shapes)
     count = len(shapes)
     P = sum(n * (d + 1) for n, d, L in shapes)
     costs = torch.zeros(count, dtype=torch.float64, device="cuda")
@@ -275,7 +291,7 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def step():
-        D.dvqls_cost_grad_batched(ctx, dev_arr, D.DVQLS_FP32, costs, grads)
+        D.dvqls_cost_grad_batched(ctx, dev_arr, PREC, costs, grads)
 
     for _ in range(args.warmup):
         step()
@@ -321,11 +337,11 @@ def main():
         hcost = np.zeros(count)
         hgrad = np.zeros(P)
         for _ in range(3):
-            D.dvqls_cost_grad_batched(ctx, host_arr, D.DVQLS_FP32, hcost, hgrad)
+            D.dvqls_cost_grad_batched(ctx, host_arr, PREC, hcost, hgrad)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            D.dvqls_cost_grad_batched(ctx, host_arr, D.DVQLS_FP32, hcost, hgrad)
+            D.dvqls_cost_grad_batched(ctx, host_arr, PREC, hcost, hgrad)
         e2e_s = time.perf_counter() - t0
         if pg:
             t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
@@ -336,6 +352,36 @@ def main():
         e2e = {"value": ws * count * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
                "max_abs_cost_diff_vs_device_path": float(np.max(np.abs(hcost - costs.cpu().numpy())))}
+
+    # The paper's own workload (headline only): the local cost of Eq. 2/4,
+    # (n+1) L^2 = 45,056 overlaps = 90,112 Hadamard-test circuits per
+    # evaluation, cost only and cost + gradient, same batch and timing.
+    local = None
+    if headline:
+        lcosts, lgrads = torch.zeros_like(costs), torch.zeros_like(grads)  # the global results stay intact
+
+        def local_rate(with_grad, steps):
+            g = lgrads if with_grad else None
+            for _ in range(3):
+                D.dvqls_local_cost_grad_batched(ctx, dev_arr, D.DVQLS_FP32, lcosts, g)
+            D.dvqls_sync(ctx)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for k in range(steps):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(stream)
+                D.dvqls_local_cost_grad_batched(ctx, dev_arr, D.DVQLS_FP32, lcosts, g)
+                ev[k][1].record(stream)
+            D.dvqls_sync(ctx)
+            torch.cuda.synchronize()
+            return count * steps / (sum(a.elapsed_time(b) for a, b in ev) / 1000.0)
+        r_cost = local_rate(False, max(20, args.steps))
+        r_grad = local_rate(True, max(5, args.steps // 10))
+        circuits = 2 * (N_QUBITS + 1) * L_TERMS ** 2
+        local = {"cost_evals_per_s": r_cost, "cost_grad_evals_per_s": r_grad,
+                 "circuits_per_cost_eval": circuits, "circuit_equivalents_per_s": r_cost * circuits,
+                 "note": "C_L of Eq. 2/4 for b = |+>^10: the paper's 90,112-circuit optimizer-iteration workload; "
+                         "the paper reports 17.15 s per iteration on 4 A100s (context only, other hardware)"}
 
     # Comparison path (headline only): the per-circuit FP64 evaluation of
     # instance 0 (all 840,320 circuits of one cost+grad) and its decomposition.
@@ -381,30 +427,44 @@ def main():
                   "note": "host wall time per call incl. the count read-back; dense input 8 MB (N x N FP64)"}
 
     if rank == 0:
-        terms, alg, exe = work_of(shapes)
+        terms, alg, exe = work_of(shapes, tensor)
         n_t, ms_t = phases["terms"]
         avg_terms_ms = ms_t / max(1, n_t)
         achieved = alg / (avg_terms_ms / 1000.0) / 1e12
         executed = exe / (avg_terms_ms / 1000.0) / 1e12
+        if tensor:
+            peaks, peak_src = measured_peaks()
+            peak = peaks["bf16_tflops"] * TF32_PER_BF16
+            roof = {"bound": "tensor", "kernel": "k_terms_tc", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "peak_note": "TF32 dense = bf16 burst %.0f TFLOP/s (%s) x nominal 1.1/2.25"
+                                 % (peaks["bf16_tflops"], peak_src.split()[1]),
+                    "frac_note": peak_src,
+                    "achieved_note": "algorithmic: 8N FLOP per paper term, all L^2 ordered pairs + L",
+                    "executed": {"tflops": executed, "frac": executed / peak, "flops_per_launch": exe,
+                                 "note": "three TF32 passes (hi hi, hi lo, lo hi) over the real 128 x 128 "
+                                         "embedding of each 64-term tile"}}
+        else:
+            roof = {"bound": "alu", "kernel": "k_terms_smem<float>", "achieved": achieved,
+                    "peak": FP32_PEAK, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK, "traffic": None,
+                    "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max SM clock)",
+                    "achieved_note": "algorithmic: 8N FLOP per paper term, all L^2 ordered pairs + L",
+                    "executed": {"tflops": executed, "frac": executed / FP32_PEAK, "flops_per_launch": exe,
+                                 "note": "Hermitian pairs computed once (upper-triangle 4x4 blocks of "
+                                         "each 64-tile) plus the delta reductions"}}
+        roof.update({"kernel_ms_avg": avg_terms_ms,
+                     "kernel_timing": "per-kernel CUDA events in a second pass over the same steps",
+                     "phase_ms_avg": {k: v[1] / max(1, v[0]) for k, v in phases.items()},
+                     "profiled_pass_ms_per_step": prof_ms / args.steps})
         launches_per_step = sum(phases[k][0] for k in ("prepare", "terms", "combine", "hbm_states")) / args.steps
         metric = METRIC if headline else "cost+grad evals/sec (%s workload)" % args.workload
         line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3" if tensor else "f32",
+                "data": "synthetic", "precision": args.precision,
                 "config": workload_config(args.workload, ws, shapes),
                 "terms_per_s": ws * terms * args.steps / (dev_ms / 1000.0),
-                "roofline": {"bound": "alu", "kernel": "k_terms_smem<float>", "achieved": achieved,
-                             "peak": FP32_PEAK, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK, "traffic": None,
-                             "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max SM clock)",
-                             "achieved_note": "algorithmic: 8N FLOP per paper term, all L^2 ordered pairs + L",
-                             "executed": {"tflops": executed, "frac": executed / FP32_PEAK,
-                                          "flops_per_launch": exe,
-                                          "note": "Hermitian pairs computed once (upper-triangle 4x4 blocks of "
-                                                  "each 64-tile) plus the delta reductions"},
-                             "kernel_ms_avg": avg_terms_ms,
-                             "kernel_timing": "per-kernel CUDA events in a second pass over the same steps",
-                             "phase_ms_avg": {k: v[1] / max(1, v[0]) for k, v in phases.items()},
-                             "profiled_pass_ms_per_step": prof_ms / args.steps},
+                "roofline": roof,
                 "gpu_launches": int(launches_per_step * args.steps),
                 "clocks": clk}
         if headline:
@@ -412,6 +472,7 @@ def main():
             line["fp64_circuit_path"] = circ
             line["speedup_vs_fp64_circuit_path"] = value / circ["value"]
             line["decomposition"] = decomp
+            line["local_cost"] = local
             if not args.no_cpu_baseline and ws == 1:
                 rate, cores, sample = cpu_oracle_rate(budget_s=10.0)
                 line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -62,10 +62,17 @@ typedef enum {
     DVQLS_ERR_ALLOC = 6        /* device or pinned allocation failed          */
 } dvqls_status;
 
-/* Arithmetic of the state build and the term reductions.  The FP32 path
- * keeps the coefficient-weighted L^2 sum, the cost ratio and the gradient
- * combine in FP64. */
-typedef enum { DVQLS_FP64 = 0, DVQLS_FP32 = 1 } dvqls_precision;
+/* Arithmetic of the state build and the term reductions.  The FP32 paths
+ * keep the coefficient-weighted L^2 sum, the cost ratio and the gradient
+ * combine in FP64.
+ *   DVQLS_FP32:    FP32 states, FP32 term reductions on the CUDA cores.
+ *   DVQLS_FP32_TC: FP32 states; the term Gram of each 64-term tile on the
+ *                  tensor cores (tcgen05, TF32 inputs split hi + lo, three
+ *                  products hi hi + hi lo + lo hi, FP32 accumulation), which
+ *                  keeps FP32-level accuracy.  Served for the global cost
+ *                  when every instance has L <= 64; other calls run as
+ *                  DVQLS_FP32. */
+typedef enum { DVQLS_FP64 = 0, DVQLS_FP32 = 1, DVQLS_FP32_TC = 2 } dvqls_precision;
 
 typedef enum { DVQLS_ANSATZ_RY_CZRING = 0 } dvqls_ansatz_kind;
 

@@ -38,11 +38,19 @@ __device__ __forceinline__ int czring_parity(int i, int n) {
 // angles: [0, P) at alpha, [P, 2P) at alpha + pi/2, [2P, 3P) at alpha - pi/2;
 // shift s selects alpha (s = 0), alpha + pi/2 e_k (s = 2k+1) or
 // alpha - pi/2 e_k (s = 2k+2).  scs receives the P (cos, sin) pairs used.
+// Barrier over the threads that build a state: the whole block (bar = 0) or
+// the NTH threads that share named barrier `bar`.
+__device__ __forceinline__ void group_sync(int bar, int NTH) {
+    if (bar == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(NTH) : "memory");
+}
+
+// Builds shifted state s with threads t = 0 .. NTH-1 of a group.
 template <typename R>
-__device__ void build_state(typename V2<R>::t* psi, typename V2<R>::t* scs, int n, int d, int P,
-                            const double2* cs, int s) {
+__device__ void build_state_group(typename V2<R>::t* psi, typename V2<R>::t* scs, int n, int d, int P,
+                                  const double2* cs, int s, int t, int NTH, int bar) {
     using R2 = typename V2<R>::t;
-    const int N = 1 << n, t = threadIdx.x, NTH = blockDim.x;
+    const int N = 1 << n;
     int k = -1, which = 0;
     if (s > 0) {
         k = (s - 1) >> 1;
@@ -55,7 +63,7 @@ __device__ void build_state(typename V2<R>::t* psi, typename V2<R>::t* scs, int 
         r.y = (R)v.y;
         scs[a] = r;
     }
-    __syncthreads();
+    group_sync(bar, NTH);
     for (int i = t; i < N; i += NTH) {  // initial Ry layer on |0>: a product state
         R v = (R)1;
         for (int q = 0; q < n; ++q) v *= ((i >> q) & 1) ? scs[q].y : scs[q].x;
@@ -64,7 +72,7 @@ __device__ void build_state(typename V2<R>::t* psi, typename V2<R>::t* scs, int 
         r.y = (R)0;
         psi[i] = r;
     }
-    __syncthreads();
+    group_sync(bar, NTH);
     // Layers: the CZ ring (diagonal) is applied while loading the first pass;
     // the Ry rotations of qubits q and q+1 are fused into one pass over groups
     // of four amplitudes (bits q, q+1 = 00, 01, 10, 11), so a layer takes
@@ -124,9 +132,15 @@ __device__ void build_state(typename V2<R>::t* psi, typename V2<R>::t* scs, int 
                     psi[i1] = v;
                 }
             }
-            __syncthreads();
+            group_sync(bar, NTH);
         }
     }
+}
+
+template <typename R>
+__device__ void build_state(typename V2<R>::t* psi, typename V2<R>::t* scs, int n, int d, int P,
+                            const double2* cs, int s) {
+    build_state_group<R>(psi, scs, n, d, P, cs, s, threadIdx.x, blockDim.x, 0);
 }
 
 }  // namespace dvqls

@@ -21,6 +21,8 @@
 // combine kernel adds the slots in a fixed order, so results do not depend
 // on scheduling.  C = 1 - N_0/D_0 with N_s = |T_s|^2/||b||^2 and
 // dC/dalpha_k = -(N'_k D_0 - N_0 D'_k)/D_0^2 (parameter-shift rule).
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <mutex>
 #include <string>
@@ -50,6 +52,8 @@ struct Inst {
     const double2* b;
     double2* ctil;   // L: c_l i^popc(x_l & z_l)
     double2* w;      // L*L: conj(ctil_l) ctil_m
+    float4* wf;      // L*L or null: w as float pairs (Re hi, Re lo, Im hi, Im lo)
+    float4* cf;      // L or null: ctil as float pairs
     double2* cs;     // 3P: (cos, sin) of half angles: base, +pi/2, -pi/2
     double* bn2;     // ||b||^2
     double2* Dpart;  // S*T*T*ks
@@ -80,6 +84,12 @@ void release_graph_cache(dvqls_ctx* ctx) {
 __device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
 
 // ---------------------------------------------------------------- prepare
+// A complex FP64 value as two float pairs: x = hi + lo with hi = RN_f32(x).
+__device__ __forceinline__ float4 split_ff(double2 v) {
+    const float xh = (float)v.x, yh = (float)v.y;
+    return make_float4(xh, (float)(v.x - (double)xh), yh, (float)(v.y - (double)yh));
+}
+
 __global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, int* status) {
     const Inst I = insts[blockIdx.x];
     const int t = threadIdx.x;
@@ -106,6 +116,7 @@ __global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, 
             default: r = make_double2(c.y, -c.x); break;
         }
         I.ctil[l] = r;
+        if (I.cf) I.cf[l] = split_ff(r);
     }
     for (int a = t; a < I.P; a += NT) {
         const double al = I.alpha[a];
@@ -128,7 +139,9 @@ __global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, 
     const long long LL = (long long)I.L * I.L;
     for (long long e = t; e < LL; e += NT) {
         const double2 a = I.ctil[e / I.L], b = I.ctil[e % I.L];
-        I.w[e] = make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+        const double2 wv = make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+        I.w[e] = wv;
+        if (I.wf) I.wf[e] = split_ff(wv);
     }
 }
 
@@ -176,6 +189,23 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* red) {
 // D_s and nothing to its imaginary part.  Threads: two K-groups of KSLOT task
 // slots; each active slot owns one 4 x 4 block of complex products and
 // accumulates it over its K-group's half of every chunk, in registers.
+__device__ __forceinline__ double2 block_sum2_n(double2 v, double2* red, int nthreads) {
+    for (int o = 16; o; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double2 s = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < nthreads / 32; ++k) {
+            s.x += red[k].x;
+            s.y += red[k].y;
+        }
+    return s;  // valid in thread 0
+}
+
 template <typename R>
 __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint32_t* smask, double2* red) {
     using R2 = typename V2<R>::t;
@@ -574,6 +604,429 @@ int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, 
     return DVQLS_OK;
 }
 
+// ------------------------------------------------- tensor-core term tiles
+// Precision DVQLS_FP32_TC: the Gram of a 64-term tile on the tensor cores.
+// With Z the 128 x K real matrix whose rows are Re phi_l (rows 0..63) and
+// Im phi_l (rows 64..127),
+//   Re G~_lm = (Z Z^T)[l][m] + (Z Z^T)[64+l][64+m],
+//   Im G~_lm = (Z Z^T)[l][64+m] - (Z Z^T)[64+l][m].
+// Every entry of 2^12 Z is split x = hi + lo into two FP16 numbers (round to
+// nearest; the scale keeps lo clear of FP16 subnormals for amplitudes above
+// ~3e-5, and below that lo's absolute error stays under 2^-37) and
+// Z Z^T ~ hi hi^T + hi lo^T + lo hi^T (lo lo^T, ~2^-22 relative, dropped):
+// three tcgen05.mma kind::f16 (M = N = 128, K = 16) per 16 amplitudes with
+// FP32 accumulation in tensor memory.  FP16 carries the 11-bit significand
+// of TF32 at twice its tensor rate and half its operand bytes.
+//
+// A kernel that allocates tensor memory runs one CTA per SM, so a CTA holds
+// two independent pipelines of 8 warps.  Each takes items from the queue with
+// its own named barrier, half of the shared memory and 256 tensor-memory
+// columns; one pipeline's state preparation, operand building and epilogue
+// overlap the other's MMAs.  Within a pipeline all threads stage the operands
+// in shared memory (K-major, no swizzle: core matrices of 8 rows x 16 bytes;
+// LBO 128 B between the two halves of a k-step, SBO 256 B between 8-row
+// groups), two stages deep; one thread issues the MMAs and commits each
+// stage to an mbarrier (bounded polls).
+// The tensor core folds each MMA's sum into the accumulator with a rounding
+// that is not to nearest (measured with TF32 operands: a one-sided drift of
+// ~2^-24 |acc| per MMA, 1.2e-5 on a unit diagonal after 384 MMAs).  So the
+// accumulator (columns 0..127 of a pipeline) restarts every TC_FLUSH stages
+// and each block is added into an FP32 running sum (columns 128..255) with
+// round-to-nearest adds: the drift is bounded by the MMAs of one block.
+// The epilogue combines the four real blocks into the complex tile and
+// weights it in float-float arithmetic (two-product by FMA, two-sum; ~2^-44
+// relative), since FP64 instructions issue at 1/64 of the FP32 rate on this
+// part; only the last eight partial sums per pipeline are added in FP64.
+// Served for tiles with L <= 64 (T = 1) of the global cost.
+constexpr int TCK = 64;        // amplitudes per stage (4 MMA k-steps of 16)
+constexpr int TCH = 256;       // threads per pipeline
+constexpr int TCT = 2 * TCH;   // threads per CTA
+constexpr int TC_FLUSH = 2;    // stages per accumulator block
+constexpr int TC_COLS = 256;   // TMEM columns per pipeline: block accumulator + running sum
+// kind::f16 instruction descriptor: F32 accumulator (bits 4-5 = 1), A and B
+// FP16 (bits 7-9, 10-12 = 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t TC_IDESC = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr long long TC_POLLS = 1LL << 26;
+constexpr float TC_SCALE = 4096.f;                     // 2^12 on the operands
+constexpr float TC_UNSCALE = 1.f / (4096.f * 4096.f);  // 2^-24 on the Gram
+constexpr int TC_STAGE_BYTES = 2 * 128 * TCK * 2;      // hi and lo FP16 operands of one stage
+constexpr int TC_X = 64 * 129;                         // readout floats: rows 64..127 of Z Z^T, then G~ [64][65]
+constexpr int TC_REGION_BYTES = ((TC_X + 2 * 64 * 65) * 4 + 1023) & ~1023;
+static_assert(TC_REGION_BYTES >= 2 * TC_STAGE_BYTES, "two stages fit the readout region");
+
+// Shared bytes of one pipeline for states of up to 2^nmax amplitudes in
+// shared memory (0: states in HBM) and Pmax angles, and of the whole CTA.
+inline size_t tc_half_bytes(int nmax_smem, int Pmax) {
+    size_t off = (size_t)(nmax_smem > 0 ? (1 << nmax_smem) : 0) * 8 + (size_t)Pmax * 8;
+    off = (off + 1023) & ~size_t(1023);
+    return off + TC_REGION_BYTES;
+}
+inline size_t tc_smem_bytes(int nmax_smem, int Pmax) { return 2 * tc_half_bytes(nmax_smem, Pmax) + 1024; }
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(128u >> 4) << 16;  // LBO: next 16-byte half along K
+    d |= (uint64_t)(256u >> 4) << 32;  // SBO: next 8-row group
+    d |= (uint64_t)1 << 46;            // descriptor version
+    return d;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+    for (long long it = 0; it < TC_POLLS; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Byte offset of Z[row][kk .. kk+7] (FP16, kk a multiple of 8 below TCK)
+// inside one operand array of a stage.
+__device__ __forceinline__ int tc_off16(int row, int kk) {
+    return (((kk >> 4) * 16 + (row >> 3)) * 2 + ((kk >> 3) & 1)) * 128 + (row & 7) * 16;
+}
+
+// hi = RN_fp16(a), lo = RN_fp16(a - hi) for a pair; a - hi is exact in FP32.
+__device__ __forceinline__ void split_h2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 r = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&r);
+}
+
+// Float-float accumulation: (S, E) += p exactly (two-sum), and
+// (S, E) += (wh + wl) g with wh g exact by FMA (two-product).
+__device__ __forceinline__ void ff_add(float& S, float& E, float p) {
+    const float s = S + p, bv = s - S;
+    E += (S - (s - bv)) + (p - bv);
+    S = s;
+}
+__device__ __forceinline__ void ff_mac(float& S, float& E, float wh, float wl, float g) {
+    const float p = wh * g;
+    const float err = fmaf(wl, g, fmaf(wh, g, -p));
+    ff_add(S, E, p);
+    E += err;
+}
+__device__ __forceinline__ void ff_warp_sum(float& S, float& E) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, S, o), e2 = __shfl_xor_sync(0xffffffffu, E, o);
+        ff_add(S, E, s2);
+        E += e2;
+    }
+}
+
+__device__ __forceinline__ void half_sync(int bar) { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(TCH) : "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+        "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+        "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
+// Adds a pipeline's block accumulator (its columns 0..127) into its running
+// sum (columns 128..255), or starts the sum with it.  Warp wl of the pipeline
+// owns TMEM lanes 32 (wl % 4) .. + 31 (the lanes its position in the
+// warpgroup may access) and columns 64 (wl / 4) .. + 63.  On the last block,
+// lanes 64..127 (the imaginary rows) go to X[row - 64][col] in shared memory
+// for the readout instead.
+__device__ __forceinline__ void tc_flush(uint32_t tmem, int wl, int lane, bool first, bool last, float* X) {
+    const uint32_t lrow = 32u * uint32_t(wl & 3);
+    const int c0 = (wl >> 2) * 64;
+    const uint32_t base = tmem + (lrow << 16);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const int col = c0 + 16 * g;
+        float v[16];
+        tmem_ld16(base + col, v);
+        if (!first) {
+            float u[16];
+            tmem_ld16(base + 128 + col, u);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] += u[j];
+        }
+        if (last && (wl & 3) >= 2) {
+            const int row = int(lrow) + lane - 64;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) X[row * 129 + col + j] = v[j];
+        } else {
+            tmem_st16(base + 128 + col, v);
+        }
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ insts, int count, long long total,
+                                                     unsigned long long* queue, int* status, int half_bytes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long mbar[2][2];
+    __shared__ uint32_t s_tmem;
+    __shared__ long long s_item[2];
+    __shared__ int s_abort[2];  // set by a pipeline's own threads only
+    __shared__ uint32_t sxl[2][TT], szl[2][TT];
+    __shared__ float2 sbf[2][2][TCK];     // b of the current and the next chunk, FP32
+    __shared__ float sred[2][3][2][8];    // per pipeline: D, Re T, Im T as float-float, per warp
+    const int t = threadIdx.x, h = t >> 8, tt = t & (TCH - 1), w = t >> 5, wl = tt >> 5, lane = t & 31;
+    const int bar = 1 + h;
+    if (t == 0) {
+        for (int k = 0; k < 4; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar[k >> 1][k & 1])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        s_abort[0] = s_abort[1] = 0;
+    }
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
+                     "r"(2 * TC_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem + uint32_t(h * TC_COLS);  // column offset in the low half
+    unsigned char* hbase;
+    {
+        const uint32_t a = su32(smem);
+        hbase = smem + ((1024u - (a & 1023u)) & 1023u) + (size_t)h * half_bytes;
+    }
+    uint32_t phase = 0u, pending = 0u;  // bit st: parity to wait for / commit outstanding, per stage
+
+    for (;;) {
+        if (tt == 0) s_item[h] = (s_abort[0] | s_abort[1]) ? total : (long long)atomicAdd(queue, 1ull);
+        half_sync(bar);
+        const long long gi = s_item[h];
+        half_sync(bar);
+        if (gi >= total) break;
+        const Inst& I = insts[find_instance(insts, count, gi)];
+        const int local = int(gi - I.item_base);
+        const int n = I.n, N = 1 << n, L = I.L, ks = I.ks;
+        const int ksi = local % ks, s = (local / ks) / I.F;
+        const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
+        float2* psi_smem = reinterpret_cast<float2*>(hbase);
+        const float2* psi = I.states ? reinterpret_cast<const float2*>(I.states) + (size_t)s * N : psi_smem;
+        float2* scs = psi_smem + (I.states ? 0 : N);
+        unsigned char* stage0;  // two stages of TC_STAGE_BYTES, then the readout overlay
+        {
+            size_t off = (size_t)(I.states ? 0 : N) * 8 + (size_t)I.P * 8;
+            stage0 = hbase + ((off + 1023) & ~size_t(1023));
+        }
+        if (tt < TT) {
+            sxl[h][tt] = tt < L ? I.xm[tt] : 0u;
+            szl[h][tt] = tt < L ? I.zm[tt] : 0u;
+        }
+        // b is converted once per amplitude, one chunk ahead of its use.
+        if (tt < TCK) {
+            const int j = kbeg + tt;
+            const double2 bb = j < kend ? I.b[j] : make_double2(0.0, 0.0);
+            sbf[h][0][tt] = make_float2((float)bb.x, (float)bb.y);
+        }
+        if (I.states) half_sync(bar);
+        else build_state_group<float>(psi_smem, scs, n, I.d, I.P, I.cs, s, tt, TCH, bar);  // ends with a barrier
+
+        // Build mapping: term l = 8 * warp + lane % 8, amplitudes sub*16 ..
+        // sub*16+15 of the stage (one MMA k-step) with sub = lane / 8, so
+        // each quarter-warp stores contiguous 128-byte core-matrix columns.
+        const int l = (tt & 7) | (wl << 3), sub = (lane >> 3) & 3;
+        float2 dacc = make_float2(0.f, 0.f);
+        const int nch = (kend - kbeg + TCK - 1) / TCK;
+        float* X = reinterpret_cast<float*>(stage0);  // [64][129] readout of rows 64..127, once every MMA is done
+        for (int c = 0; c < nch; ++c) {
+            const int j0 = kbeg + c * TCK;
+            const int st = c & 1;
+            if ((pending >> st) & 1u) {  // MMAs that read this stage two chunks ago must be done
+                if (!mbar_wait(su32(&mbar[h][st]), (phase >> st) & 1u)) s_abort[h] = 1;
+                phase ^= 1u << st;
+                pending &= ~(1u << st);
+            }
+            unsigned char* zhi = stage0 + st * TC_STAGE_BYTES;
+            unsigned char* zlo = zhi + 128 * TCK * 2;
+            if (tt < TCK && c + 1 < nch) {
+                const int j = j0 + TCK + tt;
+                const double2 bb = j < kend ? I.b[j] : make_double2(0.0, 0.0);
+                sbf[h][st ^ 1][tt] = make_float2((float)bb.x, (float)bb.y);
+            }
+            float re[16], im[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int j = j0 + sub * 16 + i;
+                float2 v = make_float2(0.f, 0.f);
+                if (j < kend && l < L) {
+                    const int src = (j ^ int(sxl[h][l])) & (N - 1);  // masks >= 2^n are reported, never followed
+                    v = psi[src];
+                    if (__popc(szl[h][l] & uint32_t(src)) & 1) {
+                        v.x = -v.x;
+                        v.y = -v.y;
+                    }
+                    const float2 bb = sbf[h][st][sub * 16 + i];
+                    dacc.x = fmaf(bb.x, v.x, fmaf(bb.y, v.y, dacc.x));
+                    dacc.y = fmaf(bb.x, v.y, fmaf(-bb.y, v.x, dacc.y));
+                }
+                re[i] = v.x * TC_SCALE;
+                im[i] = v.y * TC_SCALE;
+            }
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    split_h2(re[8 * g + 2 * q], re[8 * g + 2 * q + 1], rh[q], rl[q]);
+                    split_h2(im[8 * g + 2 * q], im[8 * g + 2 * q + 1], ih[q], il[q]);
+                }
+                const int kk = sub * 16 + 8 * g;
+                *reinterpret_cast<uint4*>(zhi + tc_off16(l, kk)) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+                *reinterpret_cast<uint4*>(zlo + tc_off16(l, kk)) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+                *reinterpret_cast<uint4*>(zhi + tc_off16(64 + l, kk)) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+                *reinterpret_cast<uint4*>(zlo + tc_off16(64 + l, kk)) = make_uint4(il[0], il[1], il[2], il[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            half_sync(bar);
+            if (s_abort[h]) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (tt == 0) {
+                const uint32_t hb = su32(zhi), lb = su32(zlo);
+#pragma unroll
+                for (int ksx = 0; ksx < TCK / 16; ++ksx) {
+                    const uint64_t dh = tc_desc(hb + ksx * 4096), dl = tc_desc(lb + ksx * 4096);
+                    const uint32_t acc0 = (c % TC_FLUSH == 0 && ksx == 0) ? 0u : 1u;
+                    asm volatile(
+                        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.eq.b32 q, %4, %4;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %1, %3, p;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %1, %3, q;\n\t}\n" ::"r"(tmem),
+                        "l"(dh), "l"(dl), "r"(TC_IDESC), "r"(acc0));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    su32(&mbar[h][st])));
+            }
+            pending |= 1u << st;
+            const bool last = c + 1 == nch;
+            if (last || (c + 1) % TC_FLUSH == 0) {
+                // Every MMA of the block has completed once both stages are drained.
+                for (int q = 0; q < 2; ++q)
+                    if ((pending >> q) & 1u) {
+                        if (!mbar_wait(su32(&mbar[h][q]), (phase >> q) & 1u)) s_abort[h] = 1;
+                        phase ^= 1u << q;
+                        pending &= ~(1u << q);
+                    }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                half_sync(bar);
+                if (s_abort[h]) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                tc_flush(tmem, wl, lane, c < TC_FLUSH, last, X);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        half_sync(bar);
+        if (s_abort[h]) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+
+        // Readout: rows 64..127 are in X; rows 0..63 (warps 0, 1, 4, 5 of the
+        // pipeline) combine with them into the complex tile G~ (float2,
+        // 64 x 64, scaled by 2^24).  Row strides 129 floats / 65 complex keep
+        // the transposing accesses free of bank conflicts.
+        float2* G = reinterpret_cast<float2*>(X + TC_X);  // [64][65]
+        if ((wl & 3) < 2) {
+            const int row = 32 * (wl & 3) + lane;  // = l
+            const int c0 = (wl >> 2) * 64;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * (wl & 3)) << 16) + 128 + c0 + 16 * g, v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = c0 + 16 * g + j;
+                    if (col < 64) G[row * 65 + col].x = v[j] + X[row * 129 + 64 + col];  // Re: [l][m] + [64+l][64+m]
+                    else G[row * 65 + col - 64].y = v[j] - X[row * 129 + col - 64];     // Im: [l][64+m] - [64+l][m]
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        half_sync(bar);
+        // Weighting.  w_ba G~_ba = conj(w_ab G~_ab) and only the real part of
+        // the sum is used: Re(w G~) over the upper triangle, doubled off the
+        // diagonal.
+        float S = 0.f, E = 0.f;
+        for (int e = tt; e < 64 * 64; e += TCH) {
+            const int a = e >> 6, b = e & 63;
+            if (a < L && b < L) {
+                const float2 gv = G[a * 65 + b];
+                if (a <= b) {
+                    const float4 wv = I.wf[a * L + b];  // (Re hi, Re lo, Im hi, Im lo)
+                    const float f = a < b ? 2.f : 1.f;
+                    ff_mac(S, E, wv.x, wv.y, f * gv.x);
+                    ff_mac(S, E, -wv.z, -wv.w, f * gv.y);
+                }
+                if (s == 0 && I.Gpart) {
+                    float2* Gp = reinterpret_cast<float2*>(I.Gpart) + (long long)ksi * L * L;
+                    Gp[(long long)a * L + b] = make_float2(gv.x * TC_UNSCALE, gv.y * TC_UNSCALE);
+                }
+            }
+        }
+        // delta: the four sub lanes of term l are lane bits 3 and 4.
+        dacc.x += __shfl_xor_sync(0xffffffffu, dacc.x, 8);
+        dacc.y += __shfl_xor_sync(0xffffffffu, dacc.y, 8);
+        dacc.x += __shfl_xor_sync(0xffffffffu, dacc.x, 16);
+        dacc.y += __shfl_xor_sync(0xffffffffu, dacc.y, 16);
+        float TrS = 0.f, TrE = 0.f, TiS = 0.f, TiE = 0.f;
+        if (sub == 0 && l < L) {
+            const float4 cv = I.cf[l];  // c~_l as (Re hi, Re lo, Im hi, Im lo)
+            ff_mac(TrS, TrE, cv.x, cv.y, dacc.x);
+            ff_mac(TrS, TrE, -cv.z, -cv.w, dacc.y);
+            ff_mac(TiS, TiE, cv.x, cv.y, dacc.y);
+            ff_mac(TiS, TiE, cv.z, cv.w, dacc.x);
+            if (s == 0 && I.dpart) reinterpret_cast<float2*>(I.dpart)[(long long)ksi * L + l] = dacc;
+        }
+        ff_warp_sum(S, E);
+        ff_warp_sum(TrS, TrE);
+        ff_warp_sum(TiS, TiE);
+        if (lane == 0) {
+            sred[h][0][0][wl] = S;
+            sred[h][0][1][wl] = E;
+            sred[h][1][0][wl] = TrS;
+            sred[h][1][1][wl] = TrE;
+            sred[h][2][0][wl] = TiS;
+            sred[h][2][1][wl] = TiE;
+        }
+        half_sync(bar);
+        if (tt == 0) {
+            double q[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < 3; ++k)
+                for (int v = 0; v < 8; ++v) q[k] += (double)sred[h][k][0][v] + (double)sred[h][k][1][v];
+            I.Dpart[(long long)s * ks + ksi] = make_double2(q[0] * (double)TC_UNSCALE, 0.0);
+            I.Tpart[(long long)s * ks + ksi] = make_double2(q[1], q[2]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (t == 0 && (s_abort[0] | s_abort[1])) atomicCAS(status, 0, DEV_TIMEOUT);
+    if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(2 * TC_COLS));
+}
+
 // ---------------------------------------------------------------- combine
 template <typename R>
 __global__ void __launch_bounds__(NT) k_combine(const Inst* __restrict__ insts, int* status) {
@@ -679,9 +1132,10 @@ size_t smem_bytes(int nmax, int Pmax) {
 
 // Launch parameters of one cost pass (everything but the table contents).
 struct PassShape {
-    int fp32, count, grid;
+    int fp32, tc, count, grid;
     long long total;
     size_t smem;
+    int half;  // tensor-core kernel: shared bytes of one pipeline
 };
 
 // The kernel sequence of one cost pass on stream `st`: queue reset, prepare,
@@ -705,7 +1159,9 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
         if (rc) return rc;
     }
     if (marks) prof_begin(ctx, 1);
-    if (ps.fp32) k_terms_smem<float><<<ps.grid, NT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue);
+    if (ps.tc)
+        k_terms_tc<<<ps.grid, TCT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue, ctx->d_status, ps.half);
+    else if (ps.fp32) k_terms_smem<float><<<ps.grid, NT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue);
     else k_terms_smem<double><<<ps.grid, NT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue);
     if (marks) prof_end(ctx);
     if (marks) prof_begin(ctx, 2);
@@ -769,7 +1225,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "the local cost has no beta / delta output");
     ctx->err.clear();
     if (count < 1 || !inst) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "count must be >= 1");
-    if (precision != DVQLS_FP32 && precision != DVQLS_FP64)
+    if (precision != DVQLS_FP32 && precision != DVQLS_FP64 && precision != DVQLS_FP32_TC)
         return set_error(ctx, DVQLS_ERR_INVALID_ARG, "unknown precision %d", precision);
     std::vector<HostInst> hi(count);
     int nmax = 1, Pmax = 1;
@@ -804,13 +1260,27 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         Pmax = std::max(Pmax, h.P);
     }
     cudaSetDevice(ctx->device);
-    const bool fp32 = precision == DVQLS_FP32;
-    const size_t smem = fp32 ? smem_bytes<float>(nmax, Pmax) : smem_bytes<double>(nmax, Pmax);
+    const bool fp32 = precision != DVQLS_FP64;
+    // Tensor-core tiles serve the global cost when every LCU fits one 64-term
+    // tile; anything else runs the FP32 CUDA-core tiles.
+    bool tc = precision == DVQLS_FP32_TC && !local;
+    for (const auto& h : hi) tc = tc && h.T == 1;
+    if (tc) {  // and when both pipelines' shared memory fits one CTA
+        int optin = 0;
+        cudaFuncAttributes fa;
+        DVQLS_CUDA_TRY(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+        DVQLS_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, (const void*)k_terms_tc));
+        tc = tc_smem_bytes(any_smem ? nmax : 0, Pmax) + fa.sharedSizeBytes <= (size_t)optin;
+    }
+    const int tc_half = tc ? (int)tc_half_bytes(any_smem ? nmax : 0, Pmax) : 0;
+    const size_t smem = tc ? tc_smem_bytes(any_smem ? nmax : 0, Pmax)
+                           : fp32 ? smem_bytes<float>(nmax, Pmax) : smem_bytes<double>(nmax, Pmax);
     const size_t r2 = fp32 ? 8 : 16;
-    auto kfun = fp32 ? (const void*)k_terms_smem<float> : (const void*)k_terms_smem<double>;
+    auto kfun = tc ? (const void*)k_terms_tc : fp32 ? (const void*)k_terms_smem<float> : (const void*)k_terms_smem<double>;
     DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     int bps = 0;
-    DVQLS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfun, NT, smem));
+    DVQLS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfun, tc ? TCT : NT, smem));
+    if (tc) bps = std::min(bps, 1);  // one CTA per SM, two item pipelines in it
     if (bps < 1) return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "term kernel does not fit (%zu B shared)", smem);
     const long long slots = (long long)ctx->num_sms * bps;
 
@@ -834,7 +1304,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     struct Off {
         size_t coef, xm, zm, alpha, b;       // staged inputs (ws) ...
         size_t pcoef, pxm, pzm, palpha, pb;  // ... and their pinned slots
-        size_t ctil, w, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta, states;
+        size_t ctil, w, wf, cf, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta, states;
         size_t pcost, pgrad, pbeta, pdelta;
     };
     std::vector<Off> off(count);
@@ -858,6 +1328,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         o.pb = local ? 0 : pin.reserve(size_t(h.N) * 16);
         o.ctil = ar.reserve(L * 16);
         o.w = ar.reserve(L * L * 16);
+        o.wf = tc ? ar.reserve(L * L * 16) : 0;
+        o.cf = tc ? ar.reserve(L * 16) : 0;
         o.cs = ar.reserve(size_t(3) * h.P * 16);
         o.bn2 = ar.reserve(8);
         o.Dp = ar.reserve(size_t(h.S) * h.F * h.T * h.T * kp * 16);
@@ -926,6 +1398,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         I.local = local ? 1 : 0;
         I.ctil = (double2*)(ws + o.ctil);
         I.w = (double2*)(ws + o.w);
+        I.wf = tc ? (float4*)(ws + o.wf) : nullptr;
+        I.cf = tc ? (float4*)(ws + o.cf) : nullptr;
         I.cs = (double2*)(ws + o.cs);
         I.bn2 = (double*)(ws + o.bn2);
         I.Dpart = (double2*)(ws + o.Dp);
@@ -966,10 +1440,12 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
             tab[oi] = &hi[i];
         }
         ps.fp32 = fp32;
+        ps.tc = tc;
         ps.count = count;
         ps.total = base;
-        ps.grid = (int)std::min<long long>(base, slots);
+        ps.grid = (int)std::min<long long>(tc ? (base + 1) / 2 : base, slots);
         ps.smem = smem;
+        ps.half = tc_half;
     };
     auto upload = [&]() -> int {
         const char* tb = reinterpret_cast<const char*>(table.data());
