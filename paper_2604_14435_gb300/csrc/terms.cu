@@ -606,15 +606,19 @@ int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, 
 
 // ------------------------------------------------- tensor-core term tiles
 // Precision DVQLS_FP32_TC: the Gram of a 64-term tile on the tensor cores.
-// With Z the 128 x K real matrix whose rows are Re phi_l (rows 0..63) and
-// Im phi_l (rows 64..127),
-//   Re G~_lm = (Z Z^T)[l][m] + (Z Z^T)[64+l][64+m],
-//   Im G~_lm = (Z Z^T)[l][64+m] - (Z Z^T)[64+l][m].
+// The Ry + CZ-ring ansatz state is real, so with the phase i^popc(x & z) in
+// c~_l every phi_l[j] = (-1)^popc(z_l & (j ^ x_l)) psi[j ^ x_l] is real and
+// G~ is a real symmetric 64 x 64 Gram.  A stage of TCK amplitudes is laid out
+// as the 128 x (TCK/2) matrix Z whose rows 0..63 hold phi_l on the first half
+// of the stage's amplitudes and rows 64..127 phi_l on the second half, so
+//   G~_lm = sum over stages of (Z Z^T)[l][m] + (Z Z^T)[64+l][64+m]
+// (the two diagonal quadrants; the off-diagonal ones are not used), which
+// covers 2 x 16 amplitudes per 128 x 128 x 16 MMA.
 // Every entry of 2^12 Z is split x = hi + lo into two FP16 numbers (round to
 // nearest; the scale keeps lo clear of FP16 subnormals for amplitudes above
 // ~3e-5, and below that lo's absolute error stays under 2^-37) and
 // Z Z^T ~ hi hi^T + hi lo^T + lo hi^T (lo lo^T, ~2^-22 relative, dropped):
-// three tcgen05.mma kind::f16 (M = N = 128, K = 16) per 16 amplitudes with
+// three tcgen05.mma kind::f16 (M = N = 128, K = 16) per 32 amplitudes with
 // FP32 accumulation in tensor memory.  FP16 carries the 11-bit significand
 // of TF32 at twice its tensor rate and half its operand bytes.
 //
@@ -631,14 +635,14 @@ int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, 
 // that is not to nearest (measured with TF32 operands: a one-sided drift of
 // ~2^-24 |acc| per MMA, 1.2e-5 on a unit diagonal after 384 MMAs).  So the
 // accumulator (columns 0..127 of a pipeline) restarts every TC_FLUSH stages
-// and each block is added into an FP32 running sum (columns 128..255) with
-// round-to-nearest adds: the drift is bounded by the MMAs of one block.
-// The epilogue combines the four real blocks into the complex tile and
+// and the two diagonal quadrants of each block are added into an FP32 running
+// sum (columns 128..191) with round-to-nearest adds: the drift is bounded by
+// the MMAs of one block.  The epilogue adds the two quadrants into G~ and
 // weights it in float-float arithmetic (two-product by FMA, two-sum; ~2^-44
 // relative), since FP64 instructions issue at 1/64 of the FP32 rate on this
 // part; only the last eight partial sums per pipeline are added in FP64.
 // Served for tiles with L <= 64 (T = 1) of the global cost.
-constexpr int TCK = 64;        // amplitudes per stage (4 MMA k-steps of 16)
+constexpr int TCK = 128;       // amplitudes per stage: 2 x 64, i.e. 4 MMA k-steps of 16 in each row half
 constexpr int TCH = 256;       // threads per pipeline
 constexpr int TCT = 2 * TCH;   // threads per CTA
 constexpr int TC_FLUSH = 2;    // stages per accumulator block
@@ -649,10 +653,10 @@ constexpr uint32_t TC_IDESC = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 
 constexpr long long TC_POLLS = 1LL << 26;
 constexpr float TC_SCALE = 4096.f;                     // 2^12 on the operands
 constexpr float TC_UNSCALE = 1.f / (4096.f * 4096.f);  // 2^-24 on the Gram
-constexpr int TC_STAGE_BYTES = 2 * 128 * TCK * 2;      // hi and lo FP16 operands of one stage
-constexpr int TC_X = 64 * 129;                         // readout floats: rows 64..127 of Z Z^T, then G~ [64][65]
-constexpr int TC_REGION_BYTES = ((TC_X + 2 * 64 * 65) * 4 + 1023) & ~1023;
-static_assert(TC_REGION_BYTES >= 2 * TC_STAGE_BYTES, "two stages fit the readout region");
+constexpr int TC_STAGE_BYTES = 2 * 128 * (TCK / 2) * 2;  // hi and lo FP16 operands (128 rows x TCK/2) of one stage
+constexpr int TC_X = 64 * 65;                            // readout floats: the lower quadrant, then G~ [64][65]
+constexpr int TC_REGION_BYTES = 2 * TC_STAGE_BYTES;
+static_assert(TC_REGION_BYTES >= 2 * TC_X * 4, "the readout fits the two stages");
 
 // Shared bytes of one pipeline for states of up to 2^nmax amplitudes in
 // shared memory (0: states in HBM) and Pmax angles, and of the whole CTA.
@@ -686,7 +690,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
     return false;
 }
 
-// Byte offset of Z[row][kk .. kk+7] (FP16, kk a multiple of 8 below TCK)
+// Byte offset of Z[row][kk .. kk+7] (FP16, kk a multiple of 8 below TCK/2)
 // inside one operand array of a stage.
 __device__ __forceinline__ int tc_off16(int row, int kk) {
     return (((kk >> 4) * 16 + (row >> 3)) * 2 + ((kk >> 3) & 1)) * 128 + (row & 7) * 16;
@@ -749,31 +753,33 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
         : "memory");
 }
 
-// Adds a pipeline's block accumulator (its columns 0..127) into its running
-// sum (columns 128..255), or starts the sum with it.  Warp wl of the pipeline
-// owns TMEM lanes 32 (wl % 4) .. + 31 (the lanes its position in the
-// warpgroup may access) and columns 64 (wl / 4) .. + 63.  On the last block,
-// lanes 64..127 (the imaginary rows) go to X[row - 64][col] in shared memory
+// Adds the two diagonal quadrants of a pipeline's block accumulator (lanes
+// 0..63 x columns 0..63 and lanes 64..127 x columns 64..127) into its running
+// sum (columns 128..191 of the same lanes), or starts the sum with them.
+// Warp wl of the pipeline owns TMEM lanes 32 (wl % 4) .. + 31 (the lanes its
+// position in the warpgroup may access) and 32 of its quadrant's columns.  On
+// the last block, lanes 64..127 go to X[row - 64][col - 64] in shared memory
 // for the readout instead.
 __device__ __forceinline__ void tc_flush(uint32_t tmem, int wl, int lane, bool first, bool last, float* X) {
     const uint32_t lrow = 32u * uint32_t(wl & 3);
-    const int c0 = (wl >> 2) * 64;
+    const int c0 = (wl >> 2) * 32;  // column within the quadrant
+    const int cq = lrow < 64 ? 0 : 64;
     const uint32_t base = tmem + (lrow << 16);
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
+    for (int g = 0; g < 2; ++g) {
         const int col = c0 + 16 * g;
         float v[16];
-        tmem_ld16(base + col, v);
+        tmem_ld16(base + cq + col, v);
         if (!first) {
             float u[16];
             tmem_ld16(base + 128 + col, u);
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] += u[j];
         }
-        if (last && (wl & 3) >= 2) {
+        if (last && lrow >= 64) {
             const int row = int(lrow) + lane - 64;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) X[row * 129 + col + j] = v[j];
+            for (int j = 0; j < 16; ++j) X[row * 65 + col + j] = v[j];
         } else {
             tmem_st16(base + 128 + col, v);
         }
@@ -847,13 +853,14 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         if (I.states) half_sync(bar);
         else build_state_group<float>(psi_smem, scs, n, I.d, I.P, I.cs, s, tt, TCH, bar);  // ends with a barrier
 
-        // Build mapping: term l = 8 * warp + lane % 8, amplitudes sub*16 ..
-        // sub*16+15 of the stage (one MMA k-step) with sub = lane / 8, so
-        // each quarter-warp stores contiguous 128-byte core-matrix columns.
+        // Build mapping: term l = 8 * warp + lane % 8 and MMA k-step sub =
+        // lane / 8: amplitudes sub*16 .. sub*16+15 of the stage go to row l,
+        // the same 16 of its second half to row 64 + l; each quarter-warp
+        // stores contiguous 128-byte core-matrix columns.
         const int l = (tt & 7) | (wl << 3), sub = (lane >> 3) & 3;
         float2 dacc = make_float2(0.f, 0.f);
         const int nch = (kend - kbeg + TCK - 1) / TCK;
-        float* X = reinterpret_cast<float*>(stage0);  // [64][129] readout of rows 64..127, once every MMA is done
+        float* X = reinterpret_cast<float*>(stage0);  // [64][65] readout of the lower quadrant, once every MMA is done
         for (int c = 0; c < nch; ++c) {
             const int j0 = kbeg + c * TCK;
             const int st = c & 1;
@@ -863,30 +870,29 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 pending &= ~(1u << st);
             }
             unsigned char* zhi = stage0 + st * TC_STAGE_BYTES;
-            unsigned char* zlo = zhi + 128 * TCK * 2;
+            unsigned char* zlo = zhi + 128 * (TCK / 2) * 2;
             if (tt < TCK && c + 1 < nch) {
                 const int j = j0 + TCK + tt;
                 const double2 bb = j < kend ? I.b[j] : make_double2(0.0, 0.0);
                 sbf[h][st ^ 1][tt] = make_float2((float)bb.x, (float)bb.y);
             }
-            float re[16], im[16];
+            float re[16], im[16];  // row l: first half of the stage; row 64 + l: second half
+            const uint32_t xl = sxl[h][l], zl = szl[h][l];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int j = j0 + sub * 16 + i;
-                float2 v = make_float2(0.f, 0.f);
+            for (int i = 0; i < 32; ++i) {
+                const int kk = (i >> 4) * (TCK / 2) + sub * 16 + (i & 15);
+                const int j = j0 + kk;
+                float v = 0.f;
                 if (j < kend && l < L) {
-                    const int src = (j ^ int(sxl[h][l])) & (N - 1);  // masks >= 2^n are reported, never followed
-                    v = psi[src];
-                    if (__popc(szl[h][l] & uint32_t(src)) & 1) {
-                        v.x = -v.x;
-                        v.y = -v.y;
-                    }
-                    const float2 bb = sbf[h][st][sub * 16 + i];
-                    dacc.x = fmaf(bb.x, v.x, fmaf(bb.y, v.y, dacc.x));
-                    dacc.y = fmaf(bb.x, v.y, fmaf(-bb.y, v.x, dacc.y));
+                    const int src = (j ^ int(xl)) & (N - 1);  // masks >= 2^n are reported, never followed
+                    v = psi[src].x;                           // the state is real
+                    if (__popc(zl & uint32_t(src)) & 1) v = -v;
+                    const float2 bb = sbf[h][st][kk];
+                    dacc.x = fmaf(bb.x, v, dacc.x);  // conj(b) phi with phi real
+                    dacc.y = fmaf(-bb.y, v, dacc.y);
                 }
-                re[i] = v.x * TC_SCALE;
-                im[i] = v.y * TC_SCALE;
+                if (i < 16) re[i] = v * TC_SCALE;
+                else im[i - 16] = v * TC_SCALE;
             }
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
@@ -896,7 +902,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                     split_h2(re[8 * g + 2 * q], re[8 * g + 2 * q + 1], rh[q], rl[q]);
                     split_h2(im[8 * g + 2 * q], im[8 * g + 2 * q + 1], ih[q], il[q]);
                 }
-                const int kk = sub * 16 + 8 * g;
+                const int kk = sub * 16 + 8 * g;  // k within the stage's TCK/2
                 *reinterpret_cast<uint4*>(zhi + tc_off16(l, kk)) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
                 *reinterpret_cast<uint4*>(zlo + tc_off16(l, kk)) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
                 *reinterpret_cast<uint4*>(zhi + tc_off16(64 + l, kk)) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
@@ -910,7 +916,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             if (tt == 0) {
                 const uint32_t hb = su32(zhi), lb = su32(zlo);
 #pragma unroll
-                for (int ksx = 0; ksx < TCK / 16; ++ksx) {
+                for (int ksx = 0; ksx < TCK / 32; ++ksx) {
                     const uint64_t dh = tc_desc(hb + ksx * 4096), dl = tc_desc(lb + ksx * 4096);
                     const uint32_t acc0 = (c % TC_FLUSH == 0 && ksx == 0) ? 0u : 1u;
                     asm volatile(
@@ -945,45 +951,47 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         if (s_abort[h]) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
 
-        // Readout: rows 64..127 are in X; rows 0..63 (warps 0, 1, 4, 5 of the
-        // pipeline) combine with them into the complex tile G~ (float2,
-        // 64 x 64, scaled by 2^24).  Row strides 129 floats / 65 complex keep
-        // the transposing accesses free of bank conflicts.
-        float2* G = reinterpret_cast<float2*>(X + TC_X);  // [64][65]
+        // Readout: the lower quadrant's sum is in X; lanes 0..63 (warps 0, 1,
+        // 4, 5 of the pipeline) add the upper one into G~ (64 x 64, real,
+        // scaled by 2^24).  Row strides of 65 floats keep the accesses free of
+        // bank conflicts.
+        float* G = X + TC_X;  // [64][65]
         if ((wl & 3) < 2) {
             const int row = 32 * (wl & 3) + lane;  // = l
-            const int c0 = (wl >> 2) * 64;
+            const int c0 = (wl >> 2) * 32;
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
+            for (int g = 0; g < 2; ++g) {
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(32 * (wl & 3)) << 16) + 128 + c0 + 16 * g, v);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = c0 + 16 * g + j;
-                    if (col < 64) G[row * 65 + col].x = v[j] + X[row * 129 + 64 + col];  // Re: [l][m] + [64+l][64+m]
-                    else G[row * 65 + col - 64].y = v[j] - X[row * 129 + col - 64];     // Im: [l][64+m] - [64+l][m]
-                }
+                for (int j = 0; j < 16; ++j) G[row * 65 + c0 + 16 * g + j] = v[j] + X[row * 65 + c0 + 16 * g + j];
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         half_sync(bar);
-        // Weighting.  w_ba G~_ba = conj(w_ab G~_ab) and only the real part of
-        // the sum is used: Re(w G~) over the upper triangle, doubled off the
-        // diagonal.
+        // Weighting.  G~ is real symmetric and only the real part of the sum
+        // is used: Re(w) G~ over the upper triangle, doubled off the diagonal.
+        // Entries (a, b) with b = tt % 64 and a = tt / 64 + 4k; the weights of
+        // four rows are loaded before they are used.
         float S = 0.f, E = 0.f;
-        for (int e = tt; e < 64 * 64; e += TCH) {
-            const int a = e >> 6, b = e & 63;
-            if (a < L && b < L) {
-                const float2 gv = G[a * 65 + b];
-                if (a <= b) {
-                    const float4 wv = I.wf[a * L + b];  // (Re hi, Re lo, Im hi, Im lo)
-                    const float f = a < b ? 2.f : 1.f;
-                    ff_mac(S, E, wv.x, wv.y, f * gv.x);
-                    ff_mac(S, E, -wv.z, -wv.w, f * gv.y);
+        {
+            const int b = tt & 63, a0 = tt >> 6;
+            float2* Gp = (s == 0 && I.Gpart) ? reinterpret_cast<float2*>(I.Gpart) + (long long)ksi * L * L : nullptr;
+#pragma unroll 1
+            for (int kb = 0; kb < 16; kb += 4) {
+                float2 wv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int a = a0 + 4 * (kb + k);
+                    const float4 w4 = (a <= b && b < L) ? I.wf[a * L + b] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    wv[k] = make_float2(w4.x, w4.y);  // Re hi, Re lo
                 }
-                if (s == 0 && I.Gpart) {
-                    float2* Gp = reinterpret_cast<float2*>(I.Gpart) + (long long)ksi * L * L;
-                    Gp[(long long)a * L + b] = make_float2(gv.x * TC_UNSCALE, gv.y * TC_UNSCALE);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int a = a0 + 4 * (kb + k);
+                    const float gv = G[a * 65 + b];
+                    ff_mac(S, E, wv[k].x, wv[k].y, a < b ? 2.f * gv : gv);
+                    if (Gp && a < L && b < L) Gp[(long long)a * L + b] = make_float2(gv * TC_UNSCALE, 0.f);
                 }
             }
         }
