@@ -661,7 +661,7 @@ static_assert(TC_REGION_BYTES >= 2 * TC_X * 4, "the readout fits the two stages"
 // Shared bytes of one pipeline for states of up to 2^nmax amplitudes in
 // shared memory (0: states in HBM) and Pmax angles, and of the whole CTA.
 inline size_t tc_half_bytes(int nmax_smem, int Pmax) {
-    size_t off = (size_t)(nmax_smem > 0 ? (1 << nmax_smem) : 0) * 8 + (size_t)Pmax * 8;
+    size_t off = (((size_t)(nmax_smem > 0 ? (1 << nmax_smem) : 0) * 4 + 7) & ~size_t(7)) + (size_t)Pmax * 8;
     off = (off + 1023) & ~size_t(1023);
     return off + TC_REGION_BYTES;
 }
@@ -787,6 +787,65 @@ __device__ __forceinline__ void tc_flush(uint32_t tmem, int wl, int lane, bool f
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+// Builds the FP16 hi / lo operands of term l for MMA k-step `sub` of a stage:
+// the 16 amplitudes at jb = j0 + sub * 16 (row l) and at jb + TCK/2 (row
+// 64 + l), and adds their delta products conj(b_j) phi_l[j] (scaled by
+// 2^12) into dacc.  With jb a multiple of 16, the sources j ^ x_l of a block
+// are rb | (i ^ xlo) with rb = (jb ^ x_l) & ~15: a permutation of 16
+// consecutive amplitudes, whose signs are the parity of z_l & rb times the
+// per-term 16-bit pattern smask (bit i: parity of z_l & (i ^ xlo)).
+// psi_r holds 2^12 psi (shared memory); psi_g the FP32 complex state in HBM.
+template <bool HBM>
+__device__ __forceinline__ void tc_build_stage(const float* psi_r, const float2* psi_g, int N, int j0, int kend,
+                                               bool act, uint32_t xl, uint32_t zl, uint32_t smask, const float4* sb,
+                                               int sub, int l, unsigned char* zhi, unsigned char* zlo, float2& dacc) {
+    const uint32_t xhi = xl & ~15u, xlo = xl & 15u & uint32_t(N - 1);
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+        const int jb = j0 + hf * (TCK / 2) + sub * 16;
+        const int nval = act ? min(16, max(0, kend - jb)) : 0;
+        const uint32_t rb = (uint32_t(jb) ^ xhi) & uint32_t(N - 1) & ~15u;
+        const uint32_t sm = smask ^ ((__popc(zl & rb) & 1) ? 0xFFFFu : 0u);
+        float v[16];
+        if (nval == 16) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const uint32_t src = rb | (uint32_t(i) ^ xlo);
+                const float x = HBM ? psi_g[src].x * TC_SCALE : psi_r[src];
+                v[i] = __uint_as_float(__float_as_uint(x) ^ (((sm >> i) & 1u) << 31));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                float x = 0.f;
+                if (i < nval) {
+                    const uint32_t src = rb | (uint32_t(i) ^ xlo);
+                    x = HBM ? psi_g[src].x * TC_SCALE : psi_r[src];
+                }
+                v[i] = __uint_as_float(__float_as_uint(x) ^ (((sm >> i) & 1u) << 31));
+            }
+        }
+        // b of these 16 positions, two per float4: (re, im, re, im)
+        const float4* b4 = sb + (hf * (TCK / 2) + sub * 16) / 2;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float4 bb = b4[i];
+            dacc.x = fmaf(bb.x, v[2 * i], fmaf(bb.z, v[2 * i + 1], dacc.x));  // conj(b) phi with phi real
+            dacc.y = fmaf(-bb.y, v[2 * i], fmaf(-bb.w, v[2 * i + 1], dacc.y));
+        }
+        const int row = hf ? 64 + l : l;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            uint32_t ph[4], pl[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) split_h2(v[8 * g + 2 * q], v[8 * g + 2 * q + 1], ph[q], pl[q]);
+            const int kk = sub * 16 + 8 * g;  // k within the stage's TCK/2
+            *reinterpret_cast<uint4*>(zhi + tc_off16(row, kk)) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+            *reinterpret_cast<uint4*>(zlo + tc_off16(row, kk)) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ insts, int count, long long total,
                                                      unsigned long long* queue, int* status, int half_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -795,7 +854,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
     __shared__ long long s_item[2];
     __shared__ int s_abort[2];  // set by a pipeline's own threads only
     __shared__ uint32_t sxl[2][TT], szl[2][TT];
-    __shared__ float2 sbf[2][2][TCK];     // b of the current and the next chunk, FP32
+    __shared__ __align__(16) float2 sbf[2][2][TCK];  // b of the current and the next chunk, FP32
     __shared__ float sred[2][3][2][8];    // per pipeline: D, Re T, Im T as float-float, per warp
     const int t = threadIdx.x, h = t >> 8, tt = t & (TCH - 1), w = t >> 5, wl = tt >> 5, lane = t & 31;
     const int bar = 1 + h;
@@ -832,12 +891,12 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         const int n = I.n, N = 1 << n, L = I.L, ks = I.ks;
         const int ksi = local % ks, s = (local / ks) / I.F;
         const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
-        float2* psi_smem = reinterpret_cast<float2*>(hbase);
-        const float2* psi = I.states ? reinterpret_cast<const float2*>(I.states) + (size_t)s * N : psi_smem;
-        float2* scs = psi_smem + (I.states ? 0 : N);
+        float* psi_r = reinterpret_cast<float*>(hbase);  // 2^12 psi, real
+        const float2* psi_g = I.states ? reinterpret_cast<const float2*>(I.states) + (size_t)s * N : nullptr;
+        float2* scs = reinterpret_cast<float2*>(hbase + (I.states ? 0 : ((size_t)N * 4 + 7) & ~size_t(7)));
         unsigned char* stage0;  // two stages of TC_STAGE_BYTES, then the readout overlay
         {
-            size_t off = (size_t)(I.states ? 0 : N) * 8 + (size_t)I.P * 8;
+            size_t off = (I.states ? 0 : (((size_t)N * 4 + 7) & ~size_t(7))) + (size_t)I.P * 8;
             stage0 = hbase + ((off + 1023) & ~size_t(1023));
         }
         if (tt < TT) {
@@ -851,13 +910,20 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             sbf[h][0][tt] = make_float2((float)bb.x, (float)bb.y);
         }
         if (I.states) half_sync(bar);
-        else build_state_group<float>(psi_smem, scs, n, I.d, I.P, I.cs, s, tt, TCH, bar);  // ends with a barrier
+        else build_state_real(psi_r, scs, n, I.d, I.P, I.cs, s, tt, TCH, bar, TC_SCALE);  // ends with a barrier
 
         // Build mapping: term l = 8 * warp + lane % 8 and MMA k-step sub =
         // lane / 8: amplitudes sub*16 .. sub*16+15 of the stage go to row l,
         // the same 16 of its second half to row 64 + l; each quarter-warp
         // stores contiguous 128-byte core-matrix columns.
         const int l = (tt & 7) | (wl << 3), sub = (lane >> 3) & 3;
+        const uint32_t xl = sxl[h][l], zl = szl[h][l];
+        uint32_t smask = 0u;  // bit i: parity of z_l & (i ^ (x_l mod 16))
+        {
+            const uint32_t xlo = xl & 15u & uint32_t(N - 1);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) smask |= uint32_t(__popc(zl & 15u & (uint32_t(i) ^ xlo)) & 1) << i;
+        }
         float2 dacc = make_float2(0.f, 0.f);
         const int nch = (kend - kbeg + TCK - 1) / TCK;
         float* X = reinterpret_cast<float*>(stage0);  // [64][65] readout of the lower quadrant, once every MMA is done
@@ -876,38 +942,9 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 const double2 bb = j < kend ? I.b[j] : make_double2(0.0, 0.0);
                 sbf[h][st ^ 1][tt] = make_float2((float)bb.x, (float)bb.y);
             }
-            float re[16], im[16];  // row l: first half of the stage; row 64 + l: second half
-            const uint32_t xl = sxl[h][l], zl = szl[h][l];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const int kk = (i >> 4) * (TCK / 2) + sub * 16 + (i & 15);
-                const int j = j0 + kk;
-                float v = 0.f;
-                if (j < kend && l < L) {
-                    const int src = (j ^ int(xl)) & (N - 1);  // masks >= 2^n are reported, never followed
-                    v = psi[src].x;                           // the state is real
-                    if (__popc(zl & uint32_t(src)) & 1) v = -v;
-                    const float2 bb = sbf[h][st][kk];
-                    dacc.x = fmaf(bb.x, v, dacc.x);  // conj(b) phi with phi real
-                    dacc.y = fmaf(-bb.y, v, dacc.y);
-                }
-                if (i < 16) re[i] = v * TC_SCALE;
-                else im[i - 16] = v * TC_SCALE;
-            }
-#pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                uint32_t rh[4], rl[4], ih[4], il[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    split_h2(re[8 * g + 2 * q], re[8 * g + 2 * q + 1], rh[q], rl[q]);
-                    split_h2(im[8 * g + 2 * q], im[8 * g + 2 * q + 1], ih[q], il[q]);
-                }
-                const int kk = sub * 16 + 8 * g;  // k within the stage's TCK/2
-                *reinterpret_cast<uint4*>(zhi + tc_off16(l, kk)) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-                *reinterpret_cast<uint4*>(zlo + tc_off16(l, kk)) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
-                *reinterpret_cast<uint4*>(zhi + tc_off16(64 + l, kk)) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
-                *reinterpret_cast<uint4*>(zlo + tc_off16(64 + l, kk)) = make_uint4(il[0], il[1], il[2], il[3]);
-            }
+            const float4* sb = reinterpret_cast<const float4*>(sbf[h][st]);
+            if (I.states) tc_build_stage<true>(nullptr, psi_g, N, j0, kend, l < L, xl, zl, smask, sb, sub, l, zhi, zlo, dacc);
+            else tc_build_stage<false>(psi_r, nullptr, N, j0, kend, l < L, xl, zl, smask, sb, sub, l, zhi, zlo, dacc);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;");
             half_sync(bar);
@@ -1000,6 +1037,8 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         dacc.y += __shfl_xor_sync(0xffffffffu, dacc.y, 8);
         dacc.x += __shfl_xor_sync(0xffffffffu, dacc.x, 16);
         dacc.y += __shfl_xor_sync(0xffffffffu, dacc.y, 16);
+        dacc.x *= 1.f / TC_SCALE;  // exact: a power of two
+        dacc.y *= 1.f / TC_SCALE;
         float TrS = 0.f, TrE = 0.f, TiS = 0.f, TiE = 0.f;
         if (sub == 0 && l < L) {
             const float4 cv = I.cf[l];  // c~_l as (Re hi, Re lo, Im hi, Im lo)
@@ -1021,10 +1060,19 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             sred[h][2][1][wl] = TiE;
         }
         half_sync(bar);
+        if (tt < 3) {  // one quantity per thread; FP64 only for the final pair
+            float S2 = 0.f, E2 = 0.f;
+            for (int v = 0; v < 8; ++v) {
+                ff_add(S2, E2, sred[h][tt][0][v]);
+                E2 += sred[h][tt][1][v];
+            }
+            sred[h][tt][0][0] = S2;
+            sred[h][tt][1][0] = E2;
+        }
+        half_sync(bar);
         if (tt == 0) {
-            double q[3] = {0.0, 0.0, 0.0};
-            for (int k = 0; k < 3; ++k)
-                for (int v = 0; v < 8; ++v) q[k] += (double)sred[h][k][0][v] + (double)sred[h][k][1][v];
+            double q[3];
+            for (int k = 0; k < 3; ++k) q[k] = (double)sred[h][k][0][0] + (double)sred[h][k][1][0];
             I.Dpart[(long long)s * ks + ksi] = make_double2(q[0] * (double)TC_UNSCALE, 0.0);
             I.Tpart[(long long)s * ks + ksi] = make_double2(q[1], q[2]);
         }
