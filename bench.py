@@ -384,7 +384,7 @@ def main():
         d2h = sum(8 + n * (d + 1) * 8 for n, d, L in shapes)
         e2e = {"value": ws * count * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
-               "max_abs_cost_diff_vs_device_path": float(np.max(np.abs(hcost - costs.cpu().numpy())))}
+               "max_abs_cost_diff_vs_device_path": float(np.max(np.abs(hcost - head_costs)))}
 
     # The paper's own workload (headline only): the local cost of Eq. 2/4,
     # (n+1) L^2 = 45,056 overlaps = 90,112 Hadamard-test circuits per

@@ -77,7 +77,8 @@ const void* stage_in(dvqls_ctx* ctx, const void* p, size_t bytes, size_t pin_off
     if (is_device_ptr(ctx, p)) return p;
     memcpy(ctx->pin + pin_off, p, bytes);
     void* dst = ctx->ws + ws_off;
-    cudaMemcpyAsync(dst, ctx->pin + pin_off, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (ctx->defer) ctx->seg_in.push_back({pin_off, ws_off, bytes});
+    else cudaMemcpyAsync(dst, ctx->pin + pin_off, bytes, cudaMemcpyHostToDevice, ctx->stream);
     return dst;
 }
 
@@ -89,10 +90,53 @@ int enqueue_out(dvqls_ctx* ctx, void* dst, const void* dev_src, size_t bytes, si
             DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(dst, dev_src, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
         return DVQLS_OK;
     }
-    DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pin + pin_off, dev_src, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    const char* src = static_cast<const char*>(dev_src);
+    if (ctx->defer && src >= ctx->ws && src + bytes <= ctx->ws + ctx->ws_cap)
+        ctx->seg_out.push_back({pin_off, size_t(src - ctx->ws), bytes});
+    else
+        DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pin + pin_off, dev_src, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     pending.push_back({dst, pin_off, bytes});
     return DVQLS_OK;
 }
+
+void begin_staging(dvqls_ctx* ctx) {
+    ctx->defer = true;
+    ctx->seg_in.clear();
+    ctx->seg_out.clear();
+}
+
+void end_staging(dvqls_ctx* ctx) {
+    ctx->defer = false;
+    ctx->seg_in.clear();
+    ctx->seg_out.clear();
+}
+
+// Issues the recorded segments in order, one copy per run of segments that
+// follow each other (next offset = previous offset + bytes rounded up to the
+// 256-byte Arena granule) in both arenas.
+static int flush_segs(dvqls_ctx* ctx, std::vector<dvqls_ctx::CopySeg>& segs, bool to_device) {
+    size_t i = 0;
+    while (i < segs.size()) {
+        const size_t p0 = segs[i].pin_off, d0 = segs[i].dev_off;
+        size_t end = segs[i].bytes, j = i + 1;
+        while (j < segs.size()) {
+            const size_t gap = (end + 255) & ~size_t(255);
+            if (segs[j].pin_off != p0 + gap || segs[j].dev_off != d0 + gap) break;
+            end = gap + segs[j].bytes;
+            ++j;
+        }
+        if (to_device)
+            DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ws + d0, ctx->pin + p0, end, cudaMemcpyHostToDevice, ctx->stream));
+        else
+            DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pin + p0, ctx->ws + d0, end, cudaMemcpyDeviceToHost, ctx->stream));
+        i = j;
+    }
+    segs.clear();
+    return DVQLS_OK;
+}
+
+int flush_in(dvqls_ctx* ctx) { return flush_segs(ctx, ctx->seg_in, true); }
+int flush_out(dvqls_ctx* ctx) { return flush_segs(ctx, ctx->seg_out, false); }
 
 int finish_out(dvqls_ctx* ctx, const std::vector<PendingOut>& pending) {
     for (const auto& p : pending) memcpy(p.dst, ctx->pin + p.pin_off, p.bytes);

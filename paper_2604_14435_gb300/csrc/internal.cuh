@@ -71,6 +71,13 @@ struct dvqls_ctx {
     dvqls::GraphCacheEntry* graph = nullptr;
     cudaStream_t cap_stream = nullptr;
     std::map<std::string, int> tune;
+    // Deferred staging (stage_in / enqueue_out between begin_staging and
+    // flush_in / flush_out): copies are recorded and issued merged.
+    struct CopySeg {
+        size_t pin_off, dev_off, bytes;
+    };
+    bool defer = false;
+    std::vector<CopySeg> seg_in, seg_out;
 };
 
 namespace dvqls {
@@ -119,6 +126,17 @@ int ensure_pinned(dvqls_ctx* ctx, size_t bytes);
 // data is copied to pinned memory at pin_off and then to the device region
 // at ws_off.  Returns the device pointer.
 const void* stage_in(dvqls_ctx* ctx, const void* p, size_t bytes, size_t pin_off, size_t ws_off);
+
+// Deferred staging: after begin_staging, stage_in and enqueue_out record
+// their host <-> device copies; flush_in / flush_out issue them, merging
+// segments that follow each other in both the pinned and the device arena
+// (consecutive Arena reservations, so only alignment padding is copied
+// along) into one cudaMemcpyAsync each.  end_staging returns to immediate
+// copies.
+void begin_staging(dvqls_ctx* ctx);
+int flush_in(dvqls_ctx* ctx);
+int flush_out(dvqls_ctx* ctx);
+void end_staging(dvqls_ctx* ctx);
 
 // Copy a device result to the caller's buffer (device or host).  Host
 // destinations go through pinned memory at pin_off; the copy to the caller

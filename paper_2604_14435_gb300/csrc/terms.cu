@@ -1367,9 +1367,11 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     const size_t o_table = ar.reserve(sizeof(Inst) * count);
     const size_t p_table = pin.reserve(sizeof(Inst) * count);
     const int ks_plan_smem = tuning ? 8 : (tuned != ctx->tune.end() ? tuned->second : 1);
+    // Staged inputs of all instances first, then the results, each reserved
+    // in both arenas in the same order, so that the copies of a call merge
+    // into one host-to-device and one device-to-host transfer.
     for (int i = 0; i < count; ++i) {
-        HostInst& h = hi[i];
-        const int kp = ks_for(h, ks_plan_smem);
+        const HostInst& h = hi[i];
         Off& o = off[i];
         const size_t L = h.L;
         o.coef = ar.reserve(L * 16);
@@ -1382,6 +1384,25 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         o.palpha = pin.reserve(size_t(h.P) * 8);
         o.b = local ? 0 : ar.reserve(size_t(h.N) * 16);
         o.pb = local ? 0 : pin.reserve(size_t(h.N) * 16);
+    }
+    for (int i = 0; i < count; ++i) {
+        const HostInst& h = hi[i];
+        Off& o = off[i];
+        const size_t L = h.L;
+        o.cost = ar.reserve(8);
+        o.pcost = pin.reserve(8);
+        o.grad = ar.reserve(size_t(h.P) * 8);
+        o.pgrad = pin.reserve(size_t(h.P) * 8);
+        o.beta = beta_out ? ar.reserve(L * L * 16) : 0;
+        o.pbeta = beta_out ? pin.reserve(L * L * 16) : 0;
+        o.delta = delta_out ? ar.reserve(L * 16) : 0;
+        o.pdelta = delta_out ? pin.reserve(L * 16) : 0;
+    }
+    for (int i = 0; i < count; ++i) {
+        HostInst& h = hi[i];
+        const int kp = ks_for(h, ks_plan_smem);
+        Off& o = off[i];
+        const size_t L = h.L;
         o.ctil = ar.reserve(L * 16);
         o.w = ar.reserve(L * L * 16);
         o.wf = tc ? ar.reserve(L * L * 16) : 0;
@@ -1394,14 +1415,6 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         o.dp = delta_out ? ar.reserve(size_t(kp) * L * r2) : 0;
         o.NsDs = ar.reserve(size_t(h.S) * 24);
         o.states = h.hbm ? ar.reserve(size_t(h.S) * size_t(h.N) * r2) : 0;
-        o.cost = ar.reserve(8);
-        o.pcost = pin.reserve(8);
-        o.grad = ar.reserve(size_t(h.P) * 8);
-        o.pgrad = pin.reserve(size_t(h.P) * 8);
-        o.beta = beta_out ? ar.reserve(L * L * 16) : 0;
-        o.pbeta = beta_out ? pin.reserve(L * L * 16) : 0;
-        o.delta = delta_out ? ar.reserve(L * 16) : 0;
-        o.pdelta = delta_out ? pin.reserve(L * 16) : 0;
     }
     int rc = ensure_workspace(ctx, ar.total());
     if (!rc) rc = ensure_pinned(ctx, pin.total());
@@ -1430,6 +1443,11 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         }
     }
     // Per-instance records in caller order (staging happens once here).
+    struct StagingScope {
+        dvqls_ctx* c;
+        ~StagingScope() { end_staging(c); }
+    } staging{ctx};
+    begin_staging(ctx);
     std::vector<Inst> rec(count);
     const bool dev_cost = costs && is_device_ptr(ctx, costs);
     const bool dev_grad = grads && is_device_ptr(ctx, grads);
@@ -1472,6 +1490,9 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     }
     const Inst* dtable = (const Inst*)(ws + o_table);
     const size_t tbytes = sizeof(Inst) * count;
+
+    rc = flush_in(ctx);
+    if (rc) return rc;
 
     // Table for split `ks`: instances ordered longest item first (LPT),
     // item ranges assigned in that order.
@@ -1578,6 +1599,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
             if (rc) return rc;
         }
     }
+    rc = flush_out(ctx);
+    if (rc) return rc;
     const bool async_ok = all_device && pend.empty() && !beta_out && !delta_out;
     if (async_ok) return DVQLS_OK;
     rc = sync_and_check(ctx);
