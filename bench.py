@@ -52,6 +52,9 @@ UNIT = "evals/s"
 SMS, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
 FP16_PER_BF16 = 1.0  # kind::f16 runs FP16 and BF16 operands at the same nominal dense rate (2.25 PFLOP/s)
+# DRAM bytes (read + write) per launch of the tensor-core term kernel on this workload, from the ncu
+# capture summarised in profiles/k_terms_tc_n10_L64_batch32.md; None once the kernel changes.
+TC_TRAFFIC_BYTES = 1901056
 
 
 def measured_peaks():
@@ -469,7 +472,9 @@ def main():
             peaks, peak_src = measured_peaks()
             peak = peaks["bf16_tflops"] * FP16_PER_BF16
             roof = {"bound": "tensor", "kernel": "k_terms_tc", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": TC_TRAFFIC_BYTES if args.workload == "toeplitz10" else None,
+                    "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch (ncu)",
                     "peak_note": "FP16 dense = bf16 burst %.0f TFLOP/s (%s; same nominal rate)"
                                  % (peaks["bf16_tflops"], peak_src.split()[1]),
                     "frac_note": peak_src,
