@@ -127,6 +127,20 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
 
 
+def max_over_ranks(dist, torch, v, device):
+    """The largest of one float per rank (the job's time is its slowest rank's)."""
+    if dist is None:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_rate(world_size, count, steps, ms):
+    """Whole-job evaluations per second: every rank evaluates `count` instances per step."""
+    return world_size * count * steps / (ms / 1000.0)
+
+
 def rank_seeds(rank, count):
     """Instances are sharded by rank: rank r takes seeds r*count .. r*count+count-1."""
     return [rank * count + k for k in range(count)]
@@ -337,11 +351,8 @@ def main():
     prof_ms = timed(profile=True)
     phases = {name: D.dvqls_profile_read(ctx, k) for k, name in
               enumerate(("prepare", "terms", "combine", "hbm_states"))}
-    if pg:
-        t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        dev_ms = t.item()
-    value = ws * count * args.steps / (dev_ms / 1000.0)
+    dev_ms = max_over_ranks(pg, torch, dev_ms, "cuda")
+    value = job_rate(ws, count, args.steps, dev_ms)
     head_costs = costs.cpu().numpy().copy()
 
     # The other term kernel on the same batch (headline only): device rate,
@@ -357,13 +368,10 @@ def main():
         alt_ms = timed(profile=False)
         timed(profile=True)
         n_a, ms_a = D.dvqls_profile_read(ctx, 1)
-        if pg:
-            t = torch.tensor([alt_ms], dtype=torch.float64, device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            alt_ms = t.item()
+        alt_ms = max_over_ranks(pg, torch, alt_ms, "cuda")
         alt = {"precision": "fp32" if other == D.DVQLS_FP32 else "fp32_tc",
                "kernel": "k_terms_smem<float>" if other == D.DVQLS_FP32 else "k_terms_tc",
-               "value": ws * count * args.steps / (alt_ms / 1000.0), "unit": UNIT,
+               "value": job_rate(ws, count, args.steps, alt_ms), "unit": UNIT,
                "ms_per_step": alt_ms / args.steps, "kernel_ms_avg": ms_a / max(1, n_a),
                "max_abs_cost_diff_vs_headline": float(np.max(np.abs(costs.cpu().numpy() - head_costs)))}
         cur["prec"] = PREC
@@ -379,13 +387,10 @@ def main():
         for _ in range(args.steps):
             D.dvqls_cost_grad_batched(ctx, host_arr, PREC, hcost, hgrad)
         e2e_s = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_s = t.item()
+        e2e_s = max_over_ranks(pg, torch, e2e_s, "cuda")
         h2d = sum(L * 24 + n * (d + 1) * 8 + (1 << n) * 16 for n, d, L in shapes)
         d2h = sum(8 + n * (d + 1) * 8 for n, d, L in shapes)
-        e2e = {"value": ws * count * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": job_rate(ws, count, args.steps, 1000.0 * e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
                "max_abs_cost_diff_vs_device_path": float(np.max(np.abs(hcost - head_costs)))}
 

@@ -1,0 +1,89 @@
+"""The multi-process path of bench.py on CPU: two `gloo` ranks.
+
+The path shards instances across ranks with no data-path exchange; the only
+collectives are the timing barrier and the max over ranks.  These tests check
+that the ranks' batches are disjoint and cover the job, that every rank sees
+the slowest rank's time, and the whole-job rate."""
+import os
+import socket
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        r, local, ws = bench.dist_env()
+        assert (r, local, ws) == (rank, rank, world)
+        specs = bench.workload_specs("toeplitz10", r)
+        seeds = [sp[1] for sp in specs]
+        gathered = [None] * world
+        dist.all_gather_object(gathered, seeds)
+        # a rank's slow step: rank r took (r + 1) * 10 ms
+        t = bench.max_over_ranks(dist, torch, float(10 * (rank + 1)), "cpu")
+        dist.barrier()
+        if rank == 0:
+            out.put((gathered, t))
+        else:
+            out.put((None, t))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_instances_and_take_the_slowest_time():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    results = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    gathered = next(g for g, _ in results if g is not None)
+    times = [t for _, t in results]
+    assert times == [20.0, 20.0]  # every rank sees the slowest rank
+    flat = [s for shard in gathered for s in shard]
+    assert len(flat) == len(set(flat)) == world * bench.BATCH  # disjoint, complete
+    assert sorted(flat) == list(range(world * bench.BATCH))
+    # whole-job rate: both ranks' instances over the slowest rank's time
+    assert bench.job_rate(world, bench.BATCH, 5, 20.0) == pytest.approx(2 * 32 * 5 / 0.02)
+
+
+def test_uneven_batches_differ_per_rank():
+    a = bench.workload_specs("uneven", 0)
+    b = bench.workload_specs("uneven", 1)
+    assert len(a) == len(b) == 64
+    assert [s[1] for s in a] != [s[1] for s in b]
+
+
+def test_reference_arm_nonzero_rank_does_no_work(monkeypatch):
+    """Under torchrun only rank 0 runs the oracle; the others return at once."""
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    called = []
+    monkeypatch.setattr(bench, "cpu_oracle_rate", lambda *a, **k: called.append(1))
+
+    class Args:
+        gpus, steps, warmup = 2, 3, 3
+
+    assert bench.run_reference(Args()) is None
+    assert not called
