@@ -197,6 +197,165 @@ __device__ inline void build_state_real(float* psi, float2* scs, int n, int d, i
     }
 }
 
+// ---- Register-resident real state build for a group of 256 threads.
+//
+// The group holds 2^n = 256 A amplitudes with A per thread.  Mapping M1:
+// i = (r << 8) | (warp << 5) | lane (qubits 0-4 on lanes, 5-7 on warps, 8+ on
+// registers); mapping M2: i = (r << 8) | (lane << 3) | warp (qubits 3-7 on
+// lanes, 0-2 on warps).  A qubit on a lane bit rotates with one shuffle, on a
+// register bit in place; the warp-bit qubits of a layer are reached by one
+// transpose through shared memory (padded by one word per 32, conflict-free),
+// alternating M1 and M2 from layer to layer.  Ry gates of a layer commute, so
+// the layer splits across the transpose; the CZ ring is a sign per amplitude.
+
+__device__ __forceinline__ int st_index(int M, int r, int w, int lane) {
+    return M == 0 ? (r << 8) | (w << 5) | lane : (r << 8) | (lane << 3) | w;
+}
+__device__ __forceinline__ int st_pad(int i) { return i + (i >> 5); }
+
+// Ry(theta) on the qubit of lane bit b: v' = c v -+ s v_partner.
+__device__ __forceinline__ float ry_lane(float v, int lane, int b, float c, float s) {
+    const float p = __shfl_xor_sync(0xffffffffu, v, 1 << b);
+    return fmaf(c, v, ((lane >> b) & 1) ? s * p : -s * p);
+}
+
+template <int A, int LOGA>
+__device__ void state_regs_multiwarp(float* psi, float* scr0, float* scr1, const float2* scs, int n, int d, int t,
+                                     int bar, float scale) {
+    const int lane = t & 31, w = t >> 5;
+    float v[A];
+#pragma unroll
+    for (int r = 0; r < A; ++r) {  // initial Ry layer on |0>: a product state
+        const int i = st_index(0, r, w, lane);
+        float x = scale;
+        for (int q = 0; q < n; ++q) x *= ((i >> q) & 1) ? scs[q].y : scs[q].x;
+        v[r] = x;
+    }
+    int M = 0, k = 0;
+    for (int layer = 1; layer <= d; ++layer) {
+        const float2* ang = scs + layer * n;
+#pragma unroll
+        for (int r = 0; r < A; ++r)
+            if (czring_parity(st_index(M, r, w, lane), n)) v[r] = -v[r];
+        const int qlane = M == 0 ? 0 : 3;  // qubit of lane bit 0
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+            const float c = ang[qlane + b].x, sn = ang[qlane + b].y;
+#pragma unroll
+            for (int r = 0; r < A; ++r) v[r] = ry_lane(v[r], lane, b, c, sn);
+        }
+#pragma unroll
+        for (int kb = 0; kb < LOGA; ++kb) {  // register-bit qubits 8 + kb
+            const float c = ang[8 + kb].x, sn = ang[8 + kb].y;
+#pragma unroll
+            for (int r = 0; r < A; ++r)
+                if (!((r >> kb) & 1)) {
+                    const float a0 = v[r], a1 = v[r | (1 << kb)];
+                    v[r] = c * a0 - sn * a1;
+                    v[r | (1 << kb)] = sn * a0 + c * a1;
+                }
+        }
+        // transpose to the other mapping through scratch buffer k
+        float* scr = k ? scr1 : scr0;
+#pragma unroll
+        for (int r = 0; r < A; ++r) scr[st_pad(st_index(M, r, w, lane))] = v[r];
+        group_sync(bar, 256);
+        M ^= 1;
+        k ^= 1;
+#pragma unroll
+        for (int r = 0; r < A; ++r) v[r] = scr[st_pad(st_index(M, r, w, lane))];
+        // the qubits that were on warp bits are now on lanes: M1 lanes 0-2 = qubits 0-2,
+        // M2 lanes 2-4 = qubits 5-7
+        const int b0 = M == 0 ? 0 : 2, q0 = M == 0 ? 0 : 5;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float c = ang[q0 + j].x, sn = ang[q0 + j].y;
+#pragma unroll
+            for (int r = 0; r < A; ++r) v[r] = ry_lane(v[r], lane, b0 + j, c, sn);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < A; ++r) psi[st_index(M, r, w, lane)] = v[r];
+    group_sync(bar, 256);
+}
+
+// n <= 8: one warp holds the whole state (i = (r << 5) | lane; for n < 5 lane
+// i is lane mod 2^n), no barrier inside.
+template <int A, int LOGA>
+__device__ void state_regs_warp(float* psi, const float2* scs, int n, int d, int lane, float scale) {
+    const int N = 1 << n, lmask = N < 32 ? N - 1 : 31, nl = n < 5 ? n : 5;
+    float v[A];
+#pragma unroll
+    for (int r = 0; r < A; ++r) {
+        const int i = (r << 5) | (lane & lmask);
+        float x = scale;
+        for (int q = 0; q < n; ++q) x *= ((i >> q) & 1) ? scs[q].y : scs[q].x;
+        v[r] = x;
+    }
+    for (int layer = 1; layer <= d; ++layer) {
+        const float2* ang = scs + layer * n;
+#pragma unroll
+        for (int r = 0; r < A; ++r)
+            if (czring_parity((r << 5) | (lane & lmask), n)) v[r] = -v[r];
+        for (int b = 0; b < nl; ++b) {
+            const float c = ang[b].x, sn = ang[b].y;
+#pragma unroll
+            for (int r = 0; r < A; ++r) v[r] = ry_lane(v[r], lane, b, c, sn);
+        }
+#pragma unroll
+        for (int kb = 0; kb < LOGA; ++kb) {  // register-bit qubits 5 + kb
+            const float c = ang[5 + kb].x, sn = ang[5 + kb].y;
+#pragma unroll
+            for (int r = 0; r < A; ++r)
+                if (!((r >> kb) & 1)) {
+                    const float a0 = v[r], a1 = v[r | (1 << kb)];
+                    v[r] = c * a0 - sn * a1;
+                    v[r | (1 << kb)] = sn * a0 + c * a1;
+                }
+        }
+    }
+    if (lane < N || N >= 32) {
+#pragma unroll
+        for (int r = 0; r < A; ++r) psi[(r << 5) | lane] = v[r];
+    }
+}
+
+// The real state of shift s, times `scale`, for a group of 256 threads (ids t,
+// named barrier `bar`) into psi[0 .. 2^n); n <= 12.  scratch: 2 x (2^n +
+// 2^n / 32) floats of shared memory that nothing else uses meanwhile.
+__device__ inline void build_state_regs(float* psi, float* scratch, float2* scs, int n, int d, int P,
+                                        const double2* cs, int s, int t, int bar, float scale) {
+    int k = -1, which = 0;
+    if (s > 0) {
+        k = (s - 1) >> 1;
+        which = ((s - 1) & 1) ? 2 : 1;
+    }
+    for (int a = t; a < P; a += 256) {
+        const double2 v = cs[(a == k ? which : 0) * P + a];
+        scs[a] = make_float2((float)v.x, (float)v.y);
+    }
+    group_sync(bar, 256);
+    const int N = 1 << n;
+    float* scr1 = scratch + N + N / 32;
+    switch (n) {
+        case 9: state_regs_multiwarp<2, 1>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
+        case 10: state_regs_multiwarp<4, 2>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
+        case 11: state_regs_multiwarp<8, 3>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
+        case 12: state_regs_multiwarp<16, 4>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
+        default: break;
+    }
+    if ((t >> 5) == 0) {
+        const int lane = t & 31;
+        switch (n) {
+            case 6: state_regs_warp<2, 1>(psi, scs, n, d, lane, scale); break;
+            case 7: state_regs_warp<4, 2>(psi, scs, n, d, lane, scale); break;
+            case 8: state_regs_warp<8, 3>(psi, scs, n, d, lane, scale); break;
+            default: state_regs_warp<1, 0>(psi, scs, n, d, lane, scale); break;  // n <= 5
+        }
+    }
+    group_sync(bar, 256);
+}
+
 template <typename R>
 __device__ void build_state(typename V2<R>::t* psi, typename V2<R>::t* scs, int n, int d, int P,
                             const double2* cs, int s) {

@@ -90,35 +90,52 @@ __device__ __forceinline__ float4 split_ff(double2 v) {
     return make_float4(xh, (float)(v.x - (double)xh), yh, (float)(v.y - (double)yh));
 }
 
+// c~_l = c_l i^popc(x_l & z_l): the phase of sigma(x, z) as an exact swap / sign.
+__device__ __forceinline__ double2 ctil_of(const Inst& I, int l) {
+    const double2 c = I.coef[l];
+    switch (__popc(I.xm[l] & I.zm[l]) & 3) {
+        case 0: return c;
+        case 1: return make_double2(-c.y, c.x);
+        case 2: return make_double2(-c.x, -c.y);
+        default: return make_double2(c.y, -c.x);
+    }
+}
+
+// Per-instance tables of a pass (Sec. 2.3 Stage I inputs).  Grid (instances,
+// parts): part 0 checks the inputs, forms ||b||^2 and c~; every part takes its
+// share of the shift angle tables and of the L^2 weights w_lm = conj(c~_l) c~_m.
 __global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, int* status) {
     const Inst I = insts[blockIdx.x];
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, part = blockIdx.y, parts = gridDim.y;
     const long long N = 1LL << I.n;
-    __shared__ double red[NT / 32];
-    double acc = 0.0;
-    for (long long j = t; j < N && I.b; j += NT) {
-        const double2 v = I.b[j];
-        acc += v.x * v.x + v.y * v.y;
-    }
-    if (!I.b && t == 0) acc = 1.0;  // local cost: b = |+>^n is implied and never read
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((t & 31) == 0) red[t >> 5] = acc;
-    for (int l = t; l < I.L; l += NT) {
-        const uint32_t x = I.xm[l], z = I.zm[l];
-        if (x >= N || z >= N) set_status(status, DEV_BAD_MASK);
-        const double2 c = I.coef[l];
-        if (!isfinite(c.x) || !isfinite(c.y)) set_status(status, DEV_NONFINITE_INPUT);
-        double2 r;
-        switch (__popc(x & z) & 3) {
-            case 0: r = c; break;
-            case 1: r = make_double2(-c.y, c.x); break;
-            case 2: r = make_double2(-c.x, -c.y); break;
-            default: r = make_double2(c.y, -c.x); break;
+    if (part == 0) {
+        __shared__ double red[NT / 32];
+        double acc = 0.0;
+        for (long long j = t; j < N && I.b; j += NT) {
+            const double2 v = I.b[j];
+            acc += v.x * v.x + v.y * v.y;
         }
-        I.ctil[l] = r;
-        if (I.cf) I.cf[l] = split_ff(r);
+        if (!I.b && t == 0) acc = 1.0;  // local cost: b = |+>^n is implied and never read
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((t & 31) == 0) red[t >> 5] = acc;
+        for (int l = t; l < I.L; l += NT) {
+            const uint32_t x = I.xm[l], z = I.zm[l];
+            if (x >= N || z >= N) set_status(status, DEV_BAD_MASK);
+            const double2 c = I.coef[l];
+            if (!isfinite(c.x) || !isfinite(c.y)) set_status(status, DEV_NONFINITE_INPUT);
+            const double2 r = ctil_of(I, l);
+            I.ctil[l] = r;
+            if (I.cf) I.cf[l] = split_ff(r);
+        }
+        __syncthreads();
+        if (t == 0) {
+            double sum = 0.0;
+            for (int k = 0; k < NT / 32; ++k) sum += red[k];
+            *I.bn2 = sum;
+            if (!(sum > 0.0) || !isfinite(sum)) set_status(status, DEV_BAD_NORM);
+        }
     }
-    for (int a = t; a < I.P; a += NT) {
+    for (int a = t + part * NT; a < I.P; a += NT * parts) {
         const double al = I.alpha[a];
         if (!isfinite(al)) set_status(status, DEV_NONFINITE_INPUT);
         double s0, c0, s1, c1, s2, c2;
@@ -129,16 +146,10 @@ __global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, 
         I.cs[I.P + a] = make_double2(c1, s1);
         I.cs[2 * I.P + a] = make_double2(c2, s2);
     }
-    __syncthreads();
-    if (t == 0) {
-        double s = 0.0;
-        for (int k = 0; k < NT / 32; ++k) s += red[k];
-        *I.bn2 = s;
-        if (!(s > 0.0) || !isfinite(s)) set_status(status, DEV_BAD_NORM);
-    }
     const long long LL = (long long)I.L * I.L;
-    for (long long e = t; e < LL; e += NT) {
-        const double2 a = I.ctil[e / I.L], b = I.ctil[e % I.L];
+    const long long per = (LL + parts - 1) / parts, e0 = part * per, e1 = min(LL, e0 + per);
+    for (long long e = e0 + t; e < e1; e += NT) {
+        const double2 a = ctil_of(I, int(e / I.L)), b = ctil_of(I, int(e % I.L));
         const double2 wv = make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
         I.w[e] = wv;
         if (I.wf) I.wf[e] = split_ff(wv);
@@ -910,7 +921,8 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             sbf[h][0][tt] = make_float2((float)bb.x, (float)bb.y);
         }
         if (I.states) half_sync(bar);
-        else build_state_real(psi_r, scs, n, I.d, I.P, I.cs, s, tt, TCH, bar, TC_SCALE);  // ends with a barrier
+        else  // in registers; the operand stages are free and serve as transpose scratch; ends with a barrier
+            build_state_regs(psi_r, reinterpret_cast<float*>(stage0), scs, n, I.d, I.P, I.cs, s, tt, bar, TC_SCALE);
 
         // Build mapping: term l = 8 * warp + lane % 8 and MMA k-step sub =
         // lane / 8: amplitudes sub*16 .. sub*16+15 of the stage go to row l,
@@ -1191,7 +1203,8 @@ struct PassShape {
     int fp32, tc, count, grid;
     long long total;
     size_t smem;
-    int half;  // tensor-core kernel: shared bytes of one pipeline
+    int half;        // tensor-core kernel: shared bytes of one pipeline
+    int prep_parts;  // CTAs per instance of k_prepare (weights split ~256 per CTA)
 };
 
 // The kernel sequence of one cost pass on stream `st`: queue reset, prepare,
@@ -1200,7 +1213,7 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
                        const std::vector<const HostInst*>& tab, bool marks) {
     DVQLS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_queue, 0, sizeof(unsigned long long), st));
     if (marks) prof_begin(ctx, 0);
-    k_prepare<<<ps.count, NT, 0, st>>>(dtable, ctx->d_status);
+    k_prepare<<<dim3(ps.count, ps.prep_parts), NT, 0, st>>>(dtable, ctx->d_status);
     if (marks) prof_end(ctx);
     for (int oi = 0; oi < ps.count; ++oi) {
         const HostInst& h = *tab[oi];
@@ -1285,6 +1298,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         return set_error(ctx, DVQLS_ERR_INVALID_ARG, "unknown precision %d", precision);
     std::vector<HostInst> hi(count);
     int nmax = 1, Pmax = 1;
+    long long LLmax = 1;
     bool any_smem = false;
     for (int i = 0; i < count; ++i) {
         const dvqls_instance& q = inst[i];
@@ -1314,6 +1328,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
             any_smem = true;
         }
         Pmax = std::max(Pmax, h.P);
+        LLmax = std::max(LLmax, (long long)L * L);
     }
     cudaSetDevice(ctx->device);
     const bool fp32 = precision != DVQLS_FP64;
@@ -1523,6 +1538,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         ps.grid = (int)std::min<long long>(tc ? (base + 1) / 2 : base, slots);
         ps.smem = smem;
         ps.half = tc_half;
+        ps.prep_parts = (int)std::min<long long>(16, std::max<long long>(1, LLmax / NT));
     };
     auto upload = [&]() -> int {
         const char* tb = reinterpret_cast<const char*>(table.data());
