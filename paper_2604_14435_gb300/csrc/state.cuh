@@ -5,6 +5,8 @@
 // and the CZ ring CZ(q,q+1), q < n-1, plus CZ(n-1,0) when n >= 3.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include <cuda_runtime.h>
 
 namespace dvqls {
@@ -208,6 +210,13 @@ __device__ inline void build_state_real(float* psi, float2* scs, int n, int d, i
 // alternating M1 and M2 from layer to layer.  Ry gates of a layer commute, so
 // the layer splits across the transpose; the CZ ring is a sign per amplitude.
 
+// x = hi + lo with hi = RN_fp16(x), lo = RN_fp16(x - hi), packed as hi | lo << 16.
+__device__ __forceinline__ uint32_t split_hl(float x) {
+    const __half h = __float2half_rn(x);
+    const __half l = __float2half_rn(x - __half2float(h));
+    return (uint32_t)__half_as_ushort(h) | ((uint32_t)__half_as_ushort(l) << 16);
+}
+
 __device__ __forceinline__ int st_index(int M, int r, int w, int lane) {
     return M == 0 ? (r << 8) | (w << 5) | lane : (r << 8) | (lane << 3) | w;
 }
@@ -220,7 +229,7 @@ __device__ __forceinline__ float ry_lane(float v, int lane, int b, float c, floa
 }
 
 template <int A, int LOGA>
-__device__ void state_regs_multiwarp(float* psi, float* scr0, float* scr1, const float2* scs, int n, int d, int t,
+__device__ void state_regs_multiwarp(uint32_t* psi, float* scr0, float* scr1, const float2* scs, int n, int d, int t,
                                      int bar, float scale) {
     const int lane = t & 31, w = t >> 5;
     float v[A];
@@ -275,14 +284,14 @@ __device__ void state_regs_multiwarp(float* psi, float* scr0, float* scr1, const
         }
     }
 #pragma unroll
-    for (int r = 0; r < A; ++r) psi[st_index(M, r, w, lane)] = v[r];
+    for (int r = 0; r < A; ++r) psi[st_index(M, r, w, lane)] = split_hl(v[r]);
     group_sync(bar, 256);
 }
 
 // n <= 8: one warp holds the whole state (i = (r << 5) | lane; for n < 5 lane
 // i is lane mod 2^n), no barrier inside.
 template <int A, int LOGA>
-__device__ void state_regs_warp(float* psi, const float2* scs, int n, int d, int lane, float scale) {
+__device__ void state_regs_warp(uint32_t* psi, const float2* scs, int n, int d, int lane, float scale) {
     const int N = 1 << n, lmask = N < 32 ? N - 1 : 31, nl = n < 5 ? n : 5;
     float v[A];
 #pragma unroll
@@ -316,14 +325,15 @@ __device__ void state_regs_warp(float* psi, const float2* scs, int n, int d, int
     }
     if (lane < N || N >= 32) {
 #pragma unroll
-        for (int r = 0; r < A; ++r) psi[(r << 5) | lane] = v[r];
+        for (int r = 0; r < A; ++r) psi[(r << 5) | lane] = split_hl(v[r]);
     }
 }
 
 // The real state of shift s, times `scale`, for a group of 256 threads (ids t,
-// named barrier `bar`) into psi[0 .. 2^n); n <= 12.  scratch: 2 x (2^n +
-// 2^n / 32) floats of shared memory that nothing else uses meanwhile.
-__device__ inline void build_state_regs(float* psi, float* scratch, float2* scs, int n, int d, int P,
+// named barrier `bar`) into psi[0 .. 2^n) as packed FP16 (hi, lo) pairs
+// (split_hl); n <= 12.  scratch: 2 x (2^n + 2^n / 32) floats of shared memory
+// that nothing else uses meanwhile.
+__device__ inline void build_state_regs(uint32_t* psi, float* scratch, float2* scs, int n, int d, int P,
                                         const double2* cs, int s, int t, int bar, float scale) {
     int k = -1, which = 0;
     if (s > 0) {

@@ -54,6 +54,7 @@ struct Inst {
     double2* w;      // L*L: conj(ctil_l) ctil_m
     float4* wf;      // L*L or null: w as float pairs (Re hi, Re lo, Im hi, Im lo)
     float4* cf;      // L or null: ctil as float pairs
+    void* bop;       // tensor-core tiles: the b rows of the B operand, TC_BOP_STAGE bytes per stage, or null
     double2* cs;     // 3P: (cos, sin) of half angles: base, +pi/2, -pi/2
     double* bn2;     // ||b||^2
     double2* Dpart;  // S*T*T*ks
@@ -619,19 +620,24 @@ int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, 
 // Precision DVQLS_FP32_TC: the Gram of a 64-term tile on the tensor cores.
 // The Ry + CZ-ring ansatz state is real, so with the phase i^popc(x & z) in
 // c~_l every phi_l[j] = (-1)^popc(z_l & (j ^ x_l)) psi[j ^ x_l] is real and
-// G~ is a real symmetric 64 x 64 Gram.  A stage of TCK amplitudes is laid out
-// as the 128 x (TCK/2) matrix Z whose rows 0..63 hold phi_l on the first half
-// of the stage's amplitudes and rows 64..127 phi_l on the second half, so
+// G~ is a real symmetric 64 x 64 Gram.  A stage of TCK = 128 amplitudes is
+// laid out as the 128 x 64 matrix Z whose rows 0..63 hold phi_l on the first
+// half of the stage's amplitudes and rows 64..127 phi_l on the second half, so
 //   G~_lm = sum over stages of (Z Z^T)[l][m] + (Z Z^T)[64+l][64+m]
-// (the two diagonal quadrants; the off-diagonal ones are not used), which
-// covers 2 x 16 amplitudes per 128 x 128 x 16 MMA.
-// Every entry of 2^12 Z is split x = hi + lo into two FP16 numbers (round to
-// nearest; the scale keeps lo clear of FP16 subnormals for amplitudes above
-// ~3e-5, and below that lo's absolute error stays under 2^-37) and
-// Z Z^T ~ hi hi^T + hi lo^T + lo hi^T (lo lo^T, ~2^-22 relative, dropped):
-// three tcgen05.mma kind::f16 (M = N = 128, K = 16) per 32 amplitudes with
-// FP32 accumulation in tensor memory.  FP16 carries the 11-bit significand
-// of TF32 at twice its tensor rate and half its operand bytes.
+// (the two diagonal quadrants; the off-diagonal ones are not used).  The B
+// operand carries four more rows, Re b and Im b on each half of the stage, so
+// the same MMA also gives delta_l = sum_j conj(b_j) phi_l[j] in columns
+// 128..131 of the accumulator (M = 128, N = 144, K = 16: 32 amplitudes of 64
+// terms and of b per instruction).
+// Every entry of 2^12 Z (and of 2^e b, e from ||b||) is split x = hi + lo into
+// two FP16 numbers (round to nearest; the scale keeps lo clear of FP16
+// subnormals for amplitudes above ~3e-5, and below that lo's absolute error
+// stays under 2^-37) and Z B^T ~ hi hi^T + hi lo^T + lo hi^T (lo lo^T, ~2^-22
+// relative, dropped): three tcgen05.mma kind::f16 per k-step with FP32
+// accumulation in tensor memory.  FP16 carries the 11-bit significand of TF32
+// at twice its tensor rate and half its operand bytes.  The state is split
+// once per item (packed hi | lo << 16 per amplitude), so a term value costs a
+// permuted 32-bit load, a sign flip of both halves and half a byte permute.
 //
 // A kernel that allocates tensor memory runs one CTA per SM, so a CTA holds
 // two independent pipelines of 8 warps.  Each takes items from the queue with
@@ -640,34 +646,42 @@ int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, 
 // overlap the other's MMAs.  Within a pipeline all threads stage the operands
 // in shared memory (K-major, no swizzle: core matrices of 8 rows x 16 bytes;
 // LBO 128 B between the two halves of a k-step, SBO 256 B between 8-row
-// groups), two stages deep; one thread issues the MMAs and commits each
-// stage to an mbarrier (bounded polls).
+// groups, 18 row groups per k-step), two stages deep; one thread issues the
+// MMAs and commits each stage to an mbarrier (bounded polls).
 // The tensor core folds each MMA's sum into the accumulator with a rounding
 // that is not to nearest (measured with TF32 operands: a one-sided drift of
 // ~2^-24 |acc| per MMA, 1.2e-5 on a unit diagonal after 384 MMAs).  So the
-// accumulator (columns 0..127 of a pipeline) restarts every TC_FLUSH stages
-// and the two diagonal quadrants of each block are added into an FP32 running
-// sum (columns 128..191) with round-to-nearest adds: the drift is bounded by
-// the MMAs of one block.  The epilogue adds the two quadrants into G~ and
-// weights it in float-float arithmetic (two-product by FMA, two-sum; ~2^-44
-// relative), since FP64 instructions issue at 1/64 of the FP32 rate on this
-// part; only the last eight partial sums per pipeline are added in FP64.
+// accumulator (columns 0..143 of a pipeline) restarts every TC_FLUSH stages
+// and the used parts of each block (the two diagonal Gram quadrants, two delta
+// columns per lane) are added into FP32 running sums (columns 144..209) with
+// round-to-nearest adds: the drift is bounded by the MMAs of one block.  The
+// epilogue adds the two quadrants into G~ and weights it in float-float
+// arithmetic (two-product by FMA, two-sum; ~2^-44 relative), since FP64
+// instructions issue at 1/64 of the FP32 rate on this part; only the last
+// partial sums per pipeline are added in FP64.
 // Served for tiles with L <= 64 (T = 1) of the global cost.
 constexpr int TCK = 128;       // amplitudes per stage: 2 x 64, i.e. 4 MMA k-steps of 16 in each row half
 constexpr int TCH = 256;       // threads per pipeline
 constexpr int TCT = 2 * TCH;   // threads per CTA
 constexpr int TC_FLUSH = 2;    // stages per accumulator block
-constexpr int TC_COLS = 256;   // TMEM columns per pipeline: block accumulator + running sum
+constexpr int TC_COLS = 256;   // TMEM columns per pipeline
+constexpr int TC_NB = 144;     // B rows: 128 term rows, then Re b / Im b of both halves (4 rows) and 12 unused
+constexpr int TC_SUM = 144;    // TMEM: running sum of the Gram quadrants (64 columns)
+constexpr int TC_DSUM = 208;   // TMEM: running sum of the two delta columns of a lane
 // kind::f16 instruction descriptor: F32 accumulator (bits 4-5 = 1), A and B
 // FP16 (bits 7-9, 10-12 = 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t TC_IDESC = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t TC_IDESC = (1u << 4) | ((uint32_t(TC_NB) >> 3) << 17) | ((128u >> 4) << 24);
 constexpr long long TC_POLLS = 1LL << 26;
-constexpr float TC_SCALE = 4096.f;                     // 2^12 on the operands
+constexpr float TC_SCALE = 4096.f;                     // 2^12 on the state
 constexpr float TC_UNSCALE = 1.f / (4096.f * 4096.f);  // 2^-24 on the Gram
-constexpr int TC_STAGE_BYTES = 2 * 128 * (TCK / 2) * 2;  // hi and lo FP16 operands (128 rows x TCK/2) of one stage
-constexpr int TC_X = 64 * 65;                            // readout floats: the lower quadrant, then G~ [64][65]
+constexpr int TC_KSTEP_BYTES = (TC_NB / 8) * 2 * 128;           // 18 row groups x 2 halves x 128 B
+constexpr int TC_OPND_BYTES = (TCK / 32) * TC_KSTEP_BYTES;      // one operand array (hi or lo) of a stage
+constexpr int TC_STAGE_BYTES = 2 * TC_OPND_BYTES;
+constexpr int TC_X = 64 * 65;                                   // readout floats: lower quadrant, then G~ [64][65]
 constexpr int TC_REGION_BYTES = 2 * TC_STAGE_BYTES;
-static_assert(TC_REGION_BYTES >= 2 * TC_X * 4, "the readout fits the two stages");
+constexpr int TC_BOP_STAGE = 1024;  // bytes of the b rows of one stage (hi and lo)
+static_assert(TC_REGION_BYTES >= (2 * TC_X + 128) * 4, "the readout fits the two stages");
+static_assert(TC_REGION_BYTES >= 2 * (4096 + 128) * 4, "the state transposes fit the two stages");
 
 // Shared bytes of one pipeline for states of up to 2^nmax amplitudes in
 // shared memory (0: states in HBM) and Pmax angles, and of the whole CTA.
@@ -677,6 +691,45 @@ inline size_t tc_half_bytes(int nmax_smem, int Pmax) {
     return off + TC_REGION_BYTES;
 }
 inline size_t tc_smem_bytes(int nmax_smem, int Pmax) { return 2 * tc_half_bytes(nmax_smem, Pmax) + 1024; }
+// Stages of the b rows of an instance with 2^n amplitudes.
+__host__ __device__ inline long long tc_bop_stages(long long N) { return (N + TCK - 1) / TCK; }
+
+// Power of two 2^e with |b_j| 2^e <= 2^12 for every j (from ||b||^2).
+__device__ __forceinline__ float tc_bscale(double bn2) {
+    int ex;
+    frexp(sqrt(bn2), &ex);  // ||b|| <= 2^ex
+    return ldexpf(1.f, 12 - ex);
+}
+
+// The b rows of the B operand, stage by stage, as FP16 hi / lo in the
+// shared-memory order of one stage: [hi, lo][k-step 0..3][half 0..1][row
+// 128..131][8 values], rows Re b and Im b of the stage's first half (128, 129)
+// and of its second half (130, 131), scaled by tc_bscale.  Grid (instances,
+// parts) of 256 threads, after k_prepare (which forms ||b||^2).
+__global__ void __launch_bounds__(256) k_prep_bop(const Inst* __restrict__ insts) {
+    const Inst I = insts[blockIdx.x];
+    if (!I.bop || !I.b) return;
+    const long long N = 1LL << I.n, chunks = tc_bop_stages(N) * (TC_BOP_STAGE / 16);
+    const float sb = tc_bscale(*I.bn2);
+    for (long long c = blockIdx.y * 256 + threadIdx.x; c < chunks; c += 256LL * gridDim.y) {
+        const long long stage = c >> 6;
+        const int u = int(c & 63), which = u >> 5, ks4 = (u >> 3) & 3, hh = (u >> 2) & 1, row = u & 3;
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            float x[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const long long j = stage * TCK + (row >= 2 ? TCK / 2 : 0) + ks4 * 16 + hh * 8 + e + q;
+                const double v = j < N ? ((row & 1) ? I.b[j].y : I.b[j].x) : 0.0;
+                x[q] = (float)(v * (double)sb);
+            }
+            const uint32_t a = split_hl(x[0]), b = split_hl(x[1]);
+            w[e >> 1] = which ? ((a >> 16) | (b & 0xFFFF0000u)) : ((a & 0xFFFFu) | (b << 16));
+        }
+        reinterpret_cast<uint4*>(I.bop)[c] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -704,16 +757,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
 // Byte offset of Z[row][kk .. kk+7] (FP16, kk a multiple of 8 below TCK/2)
 // inside one operand array of a stage.
 __device__ __forceinline__ int tc_off16(int row, int kk) {
-    return (((kk >> 4) * 16 + (row >> 3)) * 2 + ((kk >> 3) & 1)) * 128 + (row & 7) * 16;
-}
-
-// hi = RN_fp16(a), lo = RN_fp16(a - hi) for a pair; a - hi is exact in FP32.
-__device__ __forceinline__ void split_h2(float a, float b, uint32_t& hi, uint32_t& lo) {
-    const __half2 h = __floats2half2_rn(a, b);
-    const float2 hf = __half22float2(h);
-    const __half2 r = __floats2half2_rn(a - hf.x, b - hf.y);
-    hi = *reinterpret_cast<const uint32_t*>(&h);
-    lo = *reinterpret_cast<const uint32_t*>(&r);
+    return (((kk >> 4) * (TC_NB / 8) + (row >> 3)) * 2 + ((kk >> 3) & 1)) * 128 + (row & 7) * 16;
 }
 
 // Float-float accumulation: (S, E) += p exactly (two-sum), and
@@ -764,14 +808,29 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
         : "memory");
 }
 
-// Adds the two diagonal quadrants of a pipeline's block accumulator (lanes
-// 0..63 x columns 0..63 and lanes 64..127 x columns 64..127) into its running
-// sum (columns 128..191 of the same lanes), or starts the sum with them.
+__device__ __forceinline__ float2 tmem_ld2(uint32_t taddr) {
+    uint32_t a, b;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(a), "=r"(b) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    return make_float2(__uint_as_float(a), __uint_as_float(b));
+}
+
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(taddr), "r"(__float_as_uint(v.x)),
+                 "r"(__float_as_uint(v.y))
+                 : "memory");
+}
+
+// Adds the used parts of a pipeline's block accumulator into its running sums,
+// or starts the sums with them: the two diagonal Gram quadrants (lanes 0..63 x
+// columns 0..63 and lanes 64..127 x columns 64..127, into columns 144..207)
+// and each lane's two delta columns (128, 129 for lanes 0..63, which carry the
+// first half of a stage; 130, 131 for lanes 64..127; into columns 208, 209).
 // Warp wl of the pipeline owns TMEM lanes 32 (wl % 4) .. + 31 (the lanes its
-// position in the warpgroup may access) and 32 of its quadrant's columns.  On
-// the last block, lanes 64..127 go to X[row - 64][col - 64] in shared memory
-// for the readout instead.
-__device__ __forceinline__ void tc_flush(uint32_t tmem, int wl, int lane, bool first, bool last, float* X) {
+// position in the warpgroup may access) and 32 of its quadrant's columns; warps
+// 0..3 also take the delta columns.  On the last block, lanes 64..127 go to
+// X[row - 64][col - 64] and XD[row - 64] in shared memory for the readout.
+__device__ __forceinline__ void tc_flush(uint32_t tmem, int wl, int lane, bool first, bool last, float* X, float2* XD) {
     const uint32_t lrow = 32u * uint32_t(wl & 3);
     const int c0 = (wl >> 2) * 32;  // column within the quadrant
     const int cq = lrow < 64 ? 0 : 64;
@@ -783,7 +842,7 @@ __device__ __forceinline__ void tc_flush(uint32_t tmem, int wl, int lane, bool f
         tmem_ld16(base + cq + col, v);
         if (!first) {
             float u[16];
-            tmem_ld16(base + 128 + col, u);
+            tmem_ld16(base + TC_SUM + col, u);
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] += u[j];
         }
@@ -792,24 +851,33 @@ __device__ __forceinline__ void tc_flush(uint32_t tmem, int wl, int lane, bool f
 #pragma unroll
             for (int j = 0; j < 16; ++j) X[row * 65 + col + j] = v[j];
         } else {
-            tmem_st16(base + 128 + col, v);
+            tmem_st16(base + TC_SUM + col, v);
         }
+    }
+    if ((wl >> 2) == 0) {
+        float2 dv = tmem_ld2(base + 128 + (lrow < 64 ? 0 : 2));
+        if (!first) {
+            const float2 du = tmem_ld2(base + TC_DSUM);
+            dv.x += du.x;
+            dv.y += du.y;
+        }
+        if (last && lrow >= 64) XD[int(lrow) + lane - 64] = dv;
+        else tmem_st2(base + TC_DSUM, dv);
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // Builds the FP16 hi / lo operands of term l for MMA k-step `sub` of a stage:
 // the 16 amplitudes at jb = j0 + sub * 16 (row l) and at jb + TCK/2 (row
-// 64 + l), and adds their delta products conj(b_j) phi_l[j] (scaled by
-// 2^12) into dacc.  With jb a multiple of 16, the sources j ^ x_l of a block
-// are rb | (i ^ xlo) with rb = (jb ^ x_l) & ~15: a permutation of 16
-// consecutive amplitudes, whose signs are the parity of z_l & rb times the
-// per-term 16-bit pattern smask (bit i: parity of z_l & (i ^ xlo)).
-// psi_r holds 2^12 psi (shared memory); psi_g the FP32 complex state in HBM.
+// 64 + l).  With jb a multiple of 16, the sources j ^ x_l of a block are
+// rb | (i ^ xlo) with rb = (jb ^ x_l) & ~15: a permutation of 16 consecutive
+// amplitudes, whose signs are the parity of z_l & rb times the per-term 16-bit
+// pattern smask (bit i: parity of z_l & (i ^ xlo)).  psi_hl holds 2^12 psi as
+// packed FP16 (hi, lo) (shared memory); psi_g the FP32 complex state in HBM.
 template <bool HBM>
-__device__ __forceinline__ void tc_build_stage(const float* psi_r, const float2* psi_g, int N, int j0, int kend,
-                                               bool act, uint32_t xl, uint32_t zl, uint32_t smask, const float4* sb,
-                                               int sub, int l, unsigned char* zhi, unsigned char* zlo, float2& dacc) {
+__device__ __forceinline__ void tc_build_stage(const uint32_t* psi_hl, const float2* psi_g, int N, int j0, int kend,
+                                               bool act, uint32_t xl, uint32_t zl, uint32_t smask, int sub, int l,
+                                               unsigned char* zhi, unsigned char* zlo) {
     const uint32_t xhi = xl & ~15u, xlo = xl & 15u & uint32_t(N - 1);
 #pragma unroll
     for (int hf = 0; hf < 2; ++hf) {
@@ -817,42 +885,31 @@ __device__ __forceinline__ void tc_build_stage(const float* psi_r, const float2*
         const int nval = act ? min(16, max(0, kend - jb)) : 0;
         const uint32_t rb = (uint32_t(jb) ^ xhi) & uint32_t(N - 1) & ~15u;
         const uint32_t sm = smask ^ ((__popc(zl & rb) & 1) ? 0xFFFFu : 0u);
-        float v[16];
-        if (nval == 16) {
+        uint32_t w[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
+        for (int i = 0; i < 16; ++i) {
+            uint32_t x = 0u;
+            if (i < nval) {
                 const uint32_t src = rb | (uint32_t(i) ^ xlo);
-                const float x = HBM ? psi_g[src].x * TC_SCALE : psi_r[src];
-                v[i] = __uint_as_float(__float_as_uint(x) ^ (((sm >> i) & 1u) << 31));
+                x = HBM ? split_hl(psi_g[src].x * TC_SCALE) : psi_hl[src];
             }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                float x = 0.f;
-                if (i < nval) {
-                    const uint32_t src = rb | (uint32_t(i) ^ xlo);
-                    x = HBM ? psi_g[src].x * TC_SCALE : psi_r[src];
-                }
-                v[i] = __uint_as_float(__float_as_uint(x) ^ (((sm >> i) & 1u) << 31));
-            }
-        }
-        // b of these 16 positions, two per float4: (re, im, re, im)
-        const float4* b4 = sb + (hf * (TCK / 2) + sub * 16) / 2;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const float4 bb = b4[i];
-            dacc.x = fmaf(bb.x, v[2 * i], fmaf(bb.z, v[2 * i + 1], dacc.x));  // conj(b) phi with phi real
-            dacc.y = fmaf(-bb.y, v[2 * i], fmaf(-bb.w, v[2 * i + 1], dacc.y));
+            w[i] = ((sm >> i) & 1u) ? x ^ 0x80008000u : x;
         }
         const int row = hf ? 64 + l : l;
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
-            uint32_t ph[4], pl[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) split_h2(v[8 * g + 2 * q], v[8 * g + 2 * q + 1], ph[q], pl[q]);
+            uint4 hi, lo;
+            hi.x = __byte_perm(w[8 * g + 0], w[8 * g + 1], 0x5410);
+            hi.y = __byte_perm(w[8 * g + 2], w[8 * g + 3], 0x5410);
+            hi.z = __byte_perm(w[8 * g + 4], w[8 * g + 5], 0x5410);
+            hi.w = __byte_perm(w[8 * g + 6], w[8 * g + 7], 0x5410);
+            lo.x = __byte_perm(w[8 * g + 0], w[8 * g + 1], 0x7632);
+            lo.y = __byte_perm(w[8 * g + 2], w[8 * g + 3], 0x7632);
+            lo.z = __byte_perm(w[8 * g + 4], w[8 * g + 5], 0x7632);
+            lo.w = __byte_perm(w[8 * g + 6], w[8 * g + 7], 0x7632);
             const int kk = sub * 16 + 8 * g;  // k within the stage's TCK/2
-            *reinterpret_cast<uint4*>(zhi + tc_off16(row, kk)) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-            *reinterpret_cast<uint4*>(zlo + tc_off16(row, kk)) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+            *reinterpret_cast<uint4*>(zhi + tc_off16(row, kk)) = hi;
+            *reinterpret_cast<uint4*>(zlo + tc_off16(row, kk)) = lo;
         }
     }
 }
@@ -865,8 +922,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
     __shared__ long long s_item[2];
     __shared__ int s_abort[2];  // set by a pipeline's own threads only
     __shared__ uint32_t sxl[2][TT], szl[2][TT];
-    __shared__ __align__(16) float2 sbf[2][2][TCK];  // b of the current and the next chunk, FP32
-    __shared__ float sred[2][3][2][8];    // per pipeline: D, Re T, Im T as float-float, per warp
+    __shared__ float sred[2][3][2][8];  // per pipeline: D, Re T, Im T as float-float, per warp
     const int t = threadIdx.x, h = t >> 8, tt = t & (TCH - 1), w = t >> 5, wl = tt >> 5, lane = t & 31;
     const int bar = 1 + h;
     if (t == 0) {
@@ -902,7 +958,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         const int n = I.n, N = 1 << n, L = I.L, ks = I.ks;
         const int ksi = local % ks, s = (local / ks) / I.F;
         const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
-        float* psi_r = reinterpret_cast<float*>(hbase);  // 2^12 psi, real
+        uint32_t* psi_hl = reinterpret_cast<uint32_t*>(hbase);  // 2^12 psi as packed FP16 (hi, lo)
         const float2* psi_g = I.states ? reinterpret_cast<const float2*>(I.states) + (size_t)s * N : nullptr;
         float2* scs = reinterpret_cast<float2*>(hbase + (I.states ? 0 : ((size_t)N * 4 + 7) & ~size_t(7)));
         unsigned char* stage0;  // two stages of TC_STAGE_BYTES, then the readout overlay
@@ -914,15 +970,9 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             sxl[h][tt] = tt < L ? I.xm[tt] : 0u;
             szl[h][tt] = tt < L ? I.zm[tt] : 0u;
         }
-        // b is converted once per amplitude, one chunk ahead of its use.
-        if (tt < TCK) {
-            const int j = kbeg + tt;
-            const double2 bb = j < kend ? I.b[j] : make_double2(0.0, 0.0);
-            sbf[h][0][tt] = make_float2((float)bb.x, (float)bb.y);
-        }
         if (I.states) half_sync(bar);
         else  // in registers; the operand stages are free and serve as transpose scratch; ends with a barrier
-            build_state_regs(psi_r, reinterpret_cast<float*>(stage0), scs, n, I.d, I.P, I.cs, s, tt, bar, TC_SCALE);
+            build_state_regs(psi_hl, reinterpret_cast<float*>(stage0), scs, n, I.d, I.P, I.cs, s, tt, bar, TC_SCALE);
 
         // Build mapping: term l = 8 * warp + lane % 8 and MMA k-step sub =
         // lane / 8: amplitudes sub*16 .. sub*16+15 of the stage go to row l,
@@ -936,9 +986,9 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
 #pragma unroll
             for (int i = 0; i < 16; ++i) smask |= uint32_t(__popc(zl & 15u & (uint32_t(i) ^ xlo)) & 1) << i;
         }
-        float2 dacc = make_float2(0.f, 0.f);
         const int nch = (kend - kbeg + TCK - 1) / TCK;
         float* X = reinterpret_cast<float*>(stage0);  // [64][65] readout of the lower quadrant, once every MMA is done
+        float2* XD = reinterpret_cast<float2*>(X + 2 * TC_X);  // [64] lower delta sums
         for (int c = 0; c < nch; ++c) {
             const int j0 = kbeg + c * TCK;
             const int st = c & 1;
@@ -948,15 +998,17 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 pending &= ~(1u << st);
             }
             unsigned char* zhi = stage0 + st * TC_STAGE_BYTES;
-            unsigned char* zlo = zhi + 128 * (TCK / 2) * 2;
-            if (tt < TCK && c + 1 < nch) {
-                const int j = j0 + TCK + tt;
-                const double2 bb = j < kend ? I.b[j] : make_double2(0.0, 0.0);
-                sbf[h][st ^ 1][tt] = make_float2((float)bb.x, (float)bb.y);
+            unsigned char* zlo = zhi + TC_OPND_BYTES;
+            if (tt < TC_BOP_STAGE / 16) {  // the b rows of this stage (j0 is a multiple of TCK)
+                const uint4 v = reinterpret_cast<const uint4*>(I.bop)[(long long)(j0 / TCK) * (TC_BOP_STAGE / 16) + tt];
+                const int which = tt >> 5, ks4 = (tt >> 3) & 3, hh = (tt >> 2) & 1, row = tt & 3;
+                *reinterpret_cast<uint4*>((which ? zlo : zhi) + ((ks4 * (TC_NB / 8) + 16) * 2 + hh) * 128 +
+                                          row * 16) = v;
             }
-            const float4* sb = reinterpret_cast<const float4*>(sbf[h][st]);
-            if (I.states) tc_build_stage<true>(nullptr, psi_g, N, j0, kend, l < L, xl, zl, smask, sb, sub, l, zhi, zlo, dacc);
-            else tc_build_stage<false>(psi_r, nullptr, N, j0, kend, l < L, xl, zl, smask, sb, sub, l, zhi, zlo, dacc);
+            if (I.states)
+                tc_build_stage<true>(nullptr, psi_g, N, j0, kend, l < L, xl, zl, smask, sub, l, zhi, zlo);
+            else
+                tc_build_stage<false>(psi_hl, nullptr, N, j0, kend, l < L, xl, zl, smask, sub, l, zhi, zlo);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;");
             half_sync(bar);
@@ -966,7 +1018,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 const uint32_t hb = su32(zhi), lb = su32(zlo);
 #pragma unroll
                 for (int ksx = 0; ksx < TCK / 32; ++ksx) {
-                    const uint64_t dh = tc_desc(hb + ksx * 4096), dl = tc_desc(lb + ksx * 4096);
+                    const uint64_t dh = tc_desc(hb + ksx * TC_KSTEP_BYTES), dl = tc_desc(lb + ksx * TC_KSTEP_BYTES);
                     const uint32_t acc0 = (c % TC_FLUSH == 0 && ksx == 0) ? 0u : 1u;
                     asm volatile(
                         "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.eq.b32 q, %4, %4;\n\t"
@@ -992,7 +1044,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 half_sync(bar);
                 if (s_abort[h]) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                tc_flush(tmem, wl, lane, c < TC_FLUSH, last, X);
+                tc_flush(tmem, wl, lane, c < TC_FLUSH, last, X, XD);
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1003,17 +1055,33 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         // Readout: the lower quadrant's sum is in X; lanes 0..63 (warps 0, 1,
         // 4, 5 of the pipeline) add the upper one into G~ (64 x 64, real,
         // scaled by 2^24).  Row strides of 65 floats keep the accesses free of
-        // bank conflicts.
+        // bank conflicts.  Warps 0 and 1 also form delta_l and its product with
+        // c~_l.
         float* G = X + TC_X;  // [64][65]
+        float TrS = 0.f, TrE = 0.f, TiS = 0.f, TiE = 0.f;
         if ((wl & 3) < 2) {
             const int row = 32 * (wl & 3) + lane;  // = l
+            const uint32_t base = tmem + ((uint32_t)(32 * (wl & 3)) << 16);
             const int c0 = (wl >> 2) * 32;
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * (wl & 3)) << 16) + 128 + c0 + 16 * g, v);
+                tmem_ld16(base + TC_SUM + c0 + 16 * g, v);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) G[row * 65 + c0 + 16 * g + j] = v[j] + X[row * 65 + c0 + 16 * g + j];
+            }
+            if ((wl >> 2) == 0) {
+                const float2 du = tmem_ld2(base + TC_DSUM), dl = XD[row];
+                const float dsc = 1.f / (TC_SCALE * tc_bscale(*I.bn2));  // exact: a power of two
+                const float2 dacc = make_float2((du.x + dl.x) * dsc, -(du.y + dl.y) * dsc);  // conj(b) phi
+                if (row < L) {
+                    const float4 cv = I.cf[row];  // c~_l as (Re hi, Re lo, Im hi, Im lo)
+                    ff_mac(TrS, TrE, cv.x, cv.y, dacc.x);
+                    ff_mac(TrS, TrE, -cv.z, -cv.w, dacc.y);
+                    ff_mac(TiS, TiE, cv.x, cv.y, dacc.y);
+                    ff_mac(TiS, TiE, cv.z, cv.w, dacc.x);
+                    if (s == 0 && I.dpart) reinterpret_cast<float2*>(I.dpart)[(long long)ksi * L + row] = dacc;
+                }
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1043,22 +1111,6 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                     if (Gp && a < L && b < L) Gp[(long long)a * L + b] = make_float2(gv * TC_UNSCALE, 0.f);
                 }
             }
-        }
-        // delta: the four sub lanes of term l are lane bits 3 and 4.
-        dacc.x += __shfl_xor_sync(0xffffffffu, dacc.x, 8);
-        dacc.y += __shfl_xor_sync(0xffffffffu, dacc.y, 8);
-        dacc.x += __shfl_xor_sync(0xffffffffu, dacc.x, 16);
-        dacc.y += __shfl_xor_sync(0xffffffffu, dacc.y, 16);
-        dacc.x *= 1.f / TC_SCALE;  // exact: a power of two
-        dacc.y *= 1.f / TC_SCALE;
-        float TrS = 0.f, TrE = 0.f, TiS = 0.f, TiE = 0.f;
-        if (sub == 0 && l < L) {
-            const float4 cv = I.cf[l];  // c~_l as (Re hi, Re lo, Im hi, Im lo)
-            ff_mac(TrS, TrE, cv.x, cv.y, dacc.x);
-            ff_mac(TrS, TrE, -cv.z, -cv.w, dacc.y);
-            ff_mac(TiS, TiE, cv.x, cv.y, dacc.y);
-            ff_mac(TiS, TiE, cv.z, cv.w, dacc.x);
-            if (s == 0 && I.dpart) reinterpret_cast<float2*>(I.dpart)[(long long)ksi * L + l] = dacc;
         }
         ff_warp_sum(S, E);
         ff_warp_sum(TrS, TrE);
@@ -1205,6 +1257,7 @@ struct PassShape {
     size_t smem;
     int half;        // tensor-core kernel: shared bytes of one pipeline
     int prep_parts;  // CTAs per instance of k_prepare (weights split ~256 per CTA)
+    int bop_parts;   // CTAs per instance of k_prep_bop
 };
 
 // The kernel sequence of one cost pass on stream `st`: queue reset, prepare,
@@ -1214,6 +1267,7 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
     DVQLS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_queue, 0, sizeof(unsigned long long), st));
     if (marks) prof_begin(ctx, 0);
     k_prepare<<<dim3(ps.count, ps.prep_parts), NT, 0, st>>>(dtable, ctx->d_status);
+    if (ps.tc) k_prep_bop<<<dim3(ps.count, ps.bop_parts), 256, 0, st>>>(dtable);
     if (marks) prof_end(ctx);
     for (int oi = 0; oi < ps.count; ++oi) {
         const HostInst& h = *tab[oi];
@@ -1298,7 +1352,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         return set_error(ctx, DVQLS_ERR_INVALID_ARG, "unknown precision %d", precision);
     std::vector<HostInst> hi(count);
     int nmax = 1, Pmax = 1;
-    long long LLmax = 1;
+    long long LLmax = 1, Nmax = 1;
     bool any_smem = false;
     for (int i = 0; i < count; ++i) {
         const dvqls_instance& q = inst[i];
@@ -1329,6 +1383,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         }
         Pmax = std::max(Pmax, h.P);
         LLmax = std::max(LLmax, (long long)L * L);
+        Nmax = std::max(Nmax, h.N);
     }
     cudaSetDevice(ctx->device);
     const bool fp32 = precision != DVQLS_FP64;
@@ -1364,9 +1419,9 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     const int cands[] = {1, 2, 4, 8};
     auto tuned = ctx->tune.find(sig);
     const bool tuning = any_smem && tuned == ctx->tune.end();
-    auto ks_for = [&](const HostInst& h, int ks) {
+    auto ks_for = [&](const HostInst& h, int ks) {  // tensor-core items start on whole 128-amplitude stages
         return h.hbm ? (int)std::max<long long>(1, h.N / HBM_K)
-                     : (int)std::min<long long>(ks, std::max<long long>(1, h.N / JC));
+                     : (int)std::min<long long>(ks, std::max<long long>(1, h.N / (tc ? TCK : JC)));
     };
 
     // Plan the workspace (caller order; sized for the largest split tried).
@@ -1375,7 +1430,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     struct Off {
         size_t coef, xm, zm, alpha, b;       // staged inputs (ws) ...
         size_t pcoef, pxm, pzm, palpha, pb;  // ... and their pinned slots
-        size_t ctil, w, wf, cf, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta, states;
+        size_t ctil, w, wf, cf, bop, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta, states;
         size_t pcost, pgrad, pbeta, pdelta;
     };
     std::vector<Off> off(count);
@@ -1422,6 +1477,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         o.w = ar.reserve(L * L * 16);
         o.wf = tc ? ar.reserve(L * L * 16) : 0;
         o.cf = tc ? ar.reserve(L * 16) : 0;
+        o.bop = tc ? ar.reserve(size_t(tc_bop_stages(h.N)) * TC_BOP_STAGE) : 0;
         o.cs = ar.reserve(size_t(3) * h.P * 16);
         o.bn2 = ar.reserve(8);
         o.Dp = ar.reserve(size_t(h.S) * h.F * h.T * h.T * kp * 16);
@@ -1489,6 +1545,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         I.w = (double2*)(ws + o.w);
         I.wf = tc ? (float4*)(ws + o.wf) : nullptr;
         I.cf = tc ? (float4*)(ws + o.cf) : nullptr;
+        I.bop = tc ? (void*)(ws + o.bop) : nullptr;
         I.cs = (double2*)(ws + o.cs);
         I.bn2 = (double*)(ws + o.bn2);
         I.Dpart = (double2*)(ws + o.Dp);
@@ -1539,6 +1596,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         ps.smem = smem;
         ps.half = tc_half;
         ps.prep_parts = (int)std::min<long long>(16, std::max<long long>(1, LLmax / NT));
+        ps.bop_parts = (int)std::min<long long>(64, std::max<long long>(1, tc_bop_stages(Nmax) * (TC_BOP_STAGE / 16) / 256));
     };
     auto upload = [&]() -> int {
         const char* tb = reinterpret_cast<const char*>(table.data());
