@@ -351,7 +351,13 @@ __device__ inline void build_state_regs(uint32_t* psi, float* scratch, float2* s
         case 9: state_regs_multiwarp<2, 1>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
         case 10: state_regs_multiwarp<4, 2>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
         case 11: state_regs_multiwarp<8, 3>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
-        case 12: state_regs_multiwarp<16, 4>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
+        case 12: {  // 16 amplitudes per thread would crowd the registers: gate passes in shared memory
+            float* f = reinterpret_cast<float*>(psi);
+            build_state_real(f, scs, n, d, P, cs, s, t, 256, bar, scale);  // ends with a barrier
+            for (int i = t; i < N; i += 256) psi[i] = split_hl(f[i]);    // in place, one word each
+            group_sync(bar, 256);
+            return;
+        }
         default: break;
     }
     if ((t >> 5) == 0) {

@@ -662,7 +662,7 @@ int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, 
 // Served for tiles with L <= 64 (T = 1) of the global cost.
 constexpr int TCK = 128;       // amplitudes per stage: 2 x 64, i.e. 4 MMA k-steps of 16 in each row half
 constexpr int TCH = 256;       // threads per pipeline
-constexpr int TCT = 2 * TCH;   // threads per CTA
+constexpr int TCT = 2 * TCH + 32;  // threads per CTA: two builder pipelines and the MMA issuer warp
 constexpr int TC_FLUSH = 2;    // stages per accumulator block
 constexpr int TC_COLS = 256;   // TMEM columns per pipeline
 constexpr int TC_NB = 144;     // B rows: 128 term rows, then Re b / Im b of both halves (4 rows) and 12 unused
@@ -879,7 +879,7 @@ __device__ __forceinline__ void tc_build_stage(const uint32_t* psi_hl, const flo
                                                bool act, uint32_t xl, uint32_t zl, uint32_t smask, int sub, int l,
                                                unsigned char* zhi, unsigned char* zlo) {
     const uint32_t xhi = xl & ~15u, xlo = xl & 15u & uint32_t(N - 1);
-#pragma unroll
+#pragma unroll 1
     for (int hf = 0; hf < 2; ++hf) {
         const int jb = j0 + hf * (TCK / 2) + sub * 16;
         const int nval = act ? min(16, max(0, kend - jb)) : 0;
@@ -914,22 +914,49 @@ __device__ __forceinline__ void tc_build_stage(const uint32_t* psi_hl, const flo
     }
 }
 
+// One non-blocking look at an mbarrier phase.
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t phase) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(bar) : "memory");
+}
+
+constexpr uint32_t TC_EXIT = 0xFFFFFFFFu;  // stage record of a pipeline that has no more items
+constexpr long long TC_IDLE_POLLS = 1LL << 30;
+
+// Warp roles: warps 0..7 and 8..15 are the two builder pipelines; warp 16
+// issues the MMAs of both.  A pipeline hands a stage over by arriving on its
+// `full` mbarrier (all 256 threads, after a proxy fence); the stage record
+// (shared address of the hi operands, first-of-block flag) is written before.
+// The issuer commits each stage's MMAs to the stage's `empty` mbarrier, which
+// the builders wait on before they write the buffer again or read the
+// accumulator.  Neither side waits at a CTA barrier per stage.
 __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ insts, int count, long long total,
                                                      unsigned long long* queue, int* status, int half_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ __align__(8) unsigned long long mbar[2][2];
+    __shared__ __align__(8) unsigned long long full[2][2], empty[2][2];
+    __shared__ uint32_t srec[2][2][2];  // per pipeline and buffer: hi operand address, first-of-block flag
     __shared__ uint32_t s_tmem;
     __shared__ long long s_item[2];
-    __shared__ int s_abort[2];  // set by a pipeline's own threads only
+    __shared__ int s_abort[3];  // per pipeline (set by its own threads), and the issuer
     __shared__ uint32_t sxl[2][TT], szl[2][TT];
     __shared__ float sred[2][3][2][8];  // per pipeline: D, Re T, Im T as float-float, per warp
-    const int t = threadIdx.x, h = t >> 8, tt = t & (TCH - 1), w = t >> 5, wl = tt >> 5, lane = t & 31;
-    const int bar = 1 + h;
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     if (t == 0) {
-        for (int k = 0; k < 4; ++k)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar[k >> 1][k & 1])), "r"(1));
+        for (int k = 0; k < 4; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&full[k >> 1][k & 1])), "r"(TCH));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&empty[k >> 1][k & 1])), "r"(1));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
-        s_abort[0] = s_abort[1] = 0;
+        s_abort[0] = s_abort[1] = s_abort[2] = 0;
     }
     if (w == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
@@ -939,211 +966,256 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t tmem = s_tmem + uint32_t(h * TC_COLS);  // column offset in the low half
-    unsigned char* hbase;
-    {
-        const uint32_t a = su32(smem);
-        hbase = smem + ((1024u - (a & 1023u)) & 1023u) + (size_t)h * half_bytes;
-    }
-    uint32_t phase = 0u, pending = 0u;  // bit st: parity to wait for / commit outstanding, per stage
 
-    for (;;) {
-        if (tt == 0) s_item[h] = (s_abort[0] | s_abort[1]) ? total : (long long)atomicAdd(queue, 1ull);
-        half_sync(bar);
-        const long long gi = s_item[h];
-        half_sync(bar);
-        if (gi >= total) break;
-        const Inst& I = insts[find_instance(insts, count, gi)];
-        const int local = int(gi - I.item_base);
-        const int n = I.n, N = 1 << n, L = I.L, ks = I.ks;
-        const int ksi = local % ks, s = (local / ks) / I.F;
-        const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
-        uint32_t* psi_hl = reinterpret_cast<uint32_t*>(hbase);  // 2^12 psi as packed FP16 (hi, lo)
-        const float2* psi_g = I.states ? reinterpret_cast<const float2*>(I.states) + (size_t)s * N : nullptr;
-        float2* scs = reinterpret_cast<float2*>(hbase + (I.states ? 0 : ((size_t)N * 4 + 7) & ~size_t(7)));
-        unsigned char* stage0;  // two stages of TC_STAGE_BYTES, then the readout overlay
-        {
-            size_t off = (I.states ? 0 : (((size_t)N * 4 + 7) & ~size_t(7))) + (size_t)I.P * 8;
-            stage0 = hbase + ((off + 1023) & ~size_t(1023));
-        }
-        if (tt < TT) {
-            sxl[h][tt] = tt < L ? I.xm[tt] : 0u;
-            szl[h][tt] = tt < L ? I.zm[tt] : 0u;
-        }
-        if (I.states) half_sync(bar);
-        else  // in registers; the operand stages are free and serve as transpose scratch; ends with a barrier
-            build_state_regs(psi_hl, reinterpret_cast<float*>(stage0), scs, n, I.d, I.P, I.cs, s, tt, bar, TC_SCALE);
-
-        // Build mapping: term l = 8 * warp + lane % 8 and MMA k-step sub =
-        // lane / 8: amplitudes sub*16 .. sub*16+15 of the stage go to row l,
-        // the same 16 of its second half to row 64 + l; each quarter-warp
-        // stores contiguous 128-byte core-matrix columns.
-        const int l = (tt & 7) | (wl << 3), sub = (lane >> 3) & 3;
-        const uint32_t xl = sxl[h][l], zl = szl[h][l];
-        uint32_t smask = 0u;  // bit i: parity of z_l & (i ^ (x_l mod 16))
-        {
-            const uint32_t xlo = xl & 15u & uint32_t(N - 1);
+    if (w == 2 * (TCH / 32)) {  // ------------------------------------------------ issuer warp
+        if (lane == 0) {
+            uint32_t fph = 0u, nst = 0u;  // bit 2h+st: parity of full[h][st]; bit h: next buffer of pipeline h
+            bool done0 = false, done1 = false;
+            long long idle = 0;
+            while (!(done0 && done1)) {
+                bool progressed = false;
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 0 ? done0 : done1) continue;
+                    const int st = (nst >> h) & 1, pb = 2 * h + st;
+                    if (!mbar_test(su32(&full[h][st]), (fph >> pb) & 1u)) continue;
+                    fph ^= 1u << pb;
+                    nst ^= 1u << h;
+                    progressed = true;
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t hb = srec[h][st][0], first = srec[h][st][1];
+                    if (hb == TC_EXIT) {
+                        if (h == 0) done0 = true;
+                        else done1 = true;
+                        continue;
+                    }
+                    const uint32_t lb = hb + TC_OPND_BYTES, tm = s_tmem + uint32_t(h * TC_COLS);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) smask |= uint32_t(__popc(zl & 15u & (uint32_t(i) ^ xlo)) & 1) << i;
+                    for (int ksx = 0; ksx < TCK / 32; ++ksx) {
+                        const uint64_t dh = tc_desc(hb + ksx * TC_KSTEP_BYTES), dl = tc_desc(lb + ksx * TC_KSTEP_BYTES);
+                        const uint32_t acc0 = (first && ksx == 0) ? 0u : 1u;
+                        asm volatile(
+                            "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.eq.b32 q, %4, %4;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %1, %3, p;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %1, %3, q;\n\t}\n" ::"r"(tm),
+                            "l"(dh), "l"(dl), "r"(TC_IDESC), "r"(acc0));
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        su32(&empty[h][st])));
+                }
+                if (progressed) idle = 0;
+                else if (++idle > TC_IDLE_POLLS) {
+                    s_abort[2] = 1;
+                    break;
+                }
+            }
         }
-        const int nch = (kend - kbeg + TCK - 1) / TCK;
-        float* X = reinterpret_cast<float*>(stage0);  // [64][65] readout of the lower quadrant, once every MMA is done
-        float2* XD = reinterpret_cast<float2*>(X + 2 * TC_X);  // [64] lower delta sums
-        for (int c = 0; c < nch; ++c) {
-            const int j0 = kbeg + c * TCK;
-            const int st = c & 1;
-            if ((pending >> st) & 1u) {  // MMAs that read this stage two chunks ago must be done
-                if (!mbar_wait(su32(&mbar[h][st]), (phase >> st) & 1u)) s_abort[h] = 1;
-                phase ^= 1u << st;
-                pending &= ~(1u << st);
+        __syncwarp();
+    } else {  // ------------------------------------------------------------------ builders
+        const int h = t >> 8, tt = t & (TCH - 1), wl = tt >> 5;
+        const int bar = 1 + h;
+        const uint32_t tmem = s_tmem + uint32_t(h * TC_COLS);  // column offset in the low half
+        unsigned char* hbase;
+        {
+            const uint32_t a = su32(smem);
+            hbase = smem + ((1024u - (a & 1023u)) & 1023u) + (size_t)h * half_bytes;
+        }
+        uint32_t phase = 0u, pending = 0u;  // bit st: parity of empty[h][st] to wait for / commit outstanding
+        uint32_t gc = 0u;                   // stages handed over so far (the buffer is gc & 1)
+        // A pipeline checks only its own flag after its barriers (the issuer's
+        // flag can change between two threads' reads; an issuer that gave up
+        // shows here as bounded `empty` waits that give up too).
+        auto abort_seen = [&]() { return s_abort[h]; };
+
+        for (;;) {
+            if (tt == 0) s_item[h] = (s_abort[0] | s_abort[1] | s_abort[2]) ? total : (long long)atomicAdd(queue, 1ull);
+            half_sync(bar);
+            const long long gi = s_item[h];
+            half_sync(bar);
+            if (gi >= total) break;
+            const Inst& I = insts[find_instance(insts, count, gi)];
+            const int local = int(gi - I.item_base);
+            const int n = I.n, N = 1 << n, L = I.L, ks = I.ks;
+            const int ksi = local % ks, s = (local / ks) / I.F;
+            const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
+            uint32_t* psi_hl = reinterpret_cast<uint32_t*>(hbase);  // 2^12 psi as packed FP16 (hi, lo)
+            const float2* psi_g = I.states ? reinterpret_cast<const float2*>(I.states) + (size_t)s * N : nullptr;
+            float2* scs = reinterpret_cast<float2*>(hbase + (I.states ? 0 : ((size_t)N * 4 + 7) & ~size_t(7)));
+            unsigned char* stage0;  // two stages of TC_STAGE_BYTES, then the readout overlay
+            {
+                size_t off = (I.states ? 0 : (((size_t)N * 4 + 7) & ~size_t(7))) + (size_t)I.P * 8;
+                stage0 = hbase + ((off + 1023) & ~size_t(1023));
             }
-            unsigned char* zhi = stage0 + st * TC_STAGE_BYTES;
-            unsigned char* zlo = zhi + TC_OPND_BYTES;
-            if (tt < TC_BOP_STAGE / 16) {  // the b rows of this stage (j0 is a multiple of TCK)
-                const uint4 v = reinterpret_cast<const uint4*>(I.bop)[(long long)(j0 / TCK) * (TC_BOP_STAGE / 16) + tt];
-                const int which = tt >> 5, ks4 = (tt >> 3) & 3, hh = (tt >> 2) & 1, row = tt & 3;
-                *reinterpret_cast<uint4*>((which ? zlo : zhi) + ((ks4 * (TC_NB / 8) + 16) * 2 + hh) * 128 +
-                                          row * 16) = v;
+            if (tt < TT) {
+                sxl[h][tt] = tt < L ? I.xm[tt] : 0u;
+                szl[h][tt] = tt < L ? I.zm[tt] : 0u;
             }
-            if (I.states)
-                tc_build_stage<true>(nullptr, psi_g, N, j0, kend, l < L, xl, zl, smask, sub, l, zhi, zlo);
-            else
-                tc_build_stage<false>(psi_hl, nullptr, N, j0, kend, l < L, xl, zl, smask, sub, l, zhi, zlo);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (I.states) half_sync(bar);
+            else  // in registers; the operand stages are free and serve as transpose scratch; ends with a barrier
+                build_state_regs(psi_hl, reinterpret_cast<float*>(stage0), scs, n, I.d, I.P, I.cs, s, tt, bar, TC_SCALE);
+
+            // Build mapping: term l = 8 * warp + lane % 8 and MMA k-step sub =
+            // lane / 8: amplitudes sub*16 .. sub*16+15 of the stage go to row l,
+            // the same 16 of its second half to row 64 + l; each quarter-warp
+            // stores contiguous 128-byte core-matrix columns.
+            const int l = (tt & 7) | (wl << 3), sub = (lane >> 3) & 3;
+            const uint32_t xl = sxl[h][l], zl = szl[h][l];
+            uint32_t smask = 0u;  // bit i: parity of z_l & (i ^ (x_l mod 16))
+            {
+                const uint32_t xlo = xl & 15u & uint32_t(N - 1);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) smask |= uint32_t(__popc(zl & 15u & (uint32_t(i) ^ xlo)) & 1) << i;
+            }
+            const int nch = (kend - kbeg + TCK - 1) / TCK;
+            float* X = reinterpret_cast<float*>(stage0);  // [64][65] readout of the lower quadrant, once every MMA is done
+            float2* XD = reinterpret_cast<float2*>(X + 2 * TC_X);  // [64] lower delta sums
+            for (int c = 0; c < nch; ++c, ++gc) {
+                const int j0 = kbeg + c * TCK;
+                const int st = gc & 1;
+                if ((pending >> st) & 1u) {  // MMAs that read this buffer two stages ago must be done
+                    if (!mbar_wait(su32(&empty[h][st]), (phase >> st) & 1u)) s_abort[h] = 1;
+                    phase ^= 1u << st;
+                    pending &= ~(1u << st);
+                }
+                unsigned char* zhi = stage0 + st * TC_STAGE_BYTES;
+                unsigned char* zlo = zhi + TC_OPND_BYTES;
+                if (tt < TC_BOP_STAGE / 16) {  // the b rows of this stage (j0 is a multiple of TCK)
+                    const uint4 v =
+                        reinterpret_cast<const uint4*>(I.bop)[(long long)(j0 / TCK) * (TC_BOP_STAGE / 16) + tt];
+                    const int which = tt >> 5, ks4 = (tt >> 3) & 3, hh = (tt >> 2) & 1, row = tt & 3;
+                    *reinterpret_cast<uint4*>((which ? zlo : zhi) + ((ks4 * (TC_NB / 8) + 16) * 2 + hh) * 128 +
+                                              row * 16) = v;
+                }
+                if (I.states)
+                    tc_build_stage<true>(nullptr, psi_g, N, j0, kend, l < L, xl, zl, smask, sub, l, zhi, zlo);
+                else
+                    tc_build_stage<false>(psi_hl, nullptr, N, j0, kend, l < L, xl, zl, smask, sub, l, zhi, zlo);
+                if (tt == 0) {
+                    srec[h][st][0] = su32(zhi);
+                    srec[h][st][1] = (c % TC_FLUSH == 0) ? 1u : 0u;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                mbar_arrive(su32(&full[h][st]));
+                pending |= 1u << st;
+                const bool last = c + 1 == nch;
+                if (last || (c + 1) % TC_FLUSH == 0) {
+                    // Every MMA of the block has completed once both buffers are drained.
+                    for (int q = 0; q < 2; ++q)
+                        if ((pending >> q) & 1u) {
+                            if (!mbar_wait(su32(&empty[h][q]), (phase >> q) & 1u)) s_abort[h] = 1;
+                            phase ^= 1u << q;
+                            pending &= ~(1u << q);
+                        }
+                    half_sync(bar);
+                    if (abort_seen()) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    tc_flush(tmem, wl, lane, c < TC_FLUSH, last, X, XD);
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                }
+            }
+            half_sync(bar);
+            if (abort_seen()) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+
+            // Readout: the lower quadrant's sum is in X; lanes 0..63 (warps 0, 1,
+            // 4, 5 of the pipeline) add the upper one into G~ (64 x 64, real,
+            // scaled by 2^24).  Row strides of 65 floats keep the accesses free of
+            // bank conflicts.  Warps 0 and 1 also form delta_l and its product
+            // with c~_l.
+            float* G = X + TC_X;  // [64][65]
+            float TrS = 0.f, TrE = 0.f, TiS = 0.f, TiE = 0.f;
+            if ((wl & 3) < 2) {
+                const int row = 32 * (wl & 3) + lane;  // = l
+                const uint32_t base = tmem + ((uint32_t)(32 * (wl & 3)) << 16);
+                const int c0 = (wl >> 2) * 32;
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    float v[16];
+                    tmem_ld16(base + TC_SUM + c0 + 16 * g, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) G[row * 65 + c0 + 16 * g + j] = v[j] + X[row * 65 + c0 + 16 * g + j];
+                }
+                if ((wl >> 2) == 0) {
+                    const float2 du = tmem_ld2(base + TC_DSUM), dl = XD[row];
+                    const float dsc = 1.f / (TC_SCALE * tc_bscale(*I.bn2));  // exact: a power of two
+                    const float2 dacc = make_float2((du.x + dl.x) * dsc, -(du.y + dl.y) * dsc);  // conj(b) phi
+                    if (row < L) {
+                        const float4 cv = I.cf[row];  // c~_l as (Re hi, Re lo, Im hi, Im lo)
+                        ff_mac(TrS, TrE, cv.x, cv.y, dacc.x);
+                        ff_mac(TrS, TrE, -cv.z, -cv.w, dacc.y);
+                        ff_mac(TiS, TiE, cv.x, cv.y, dacc.y);
+                        ff_mac(TiS, TiE, cv.z, cv.w, dacc.x);
+                        if (s == 0 && I.dpart) reinterpret_cast<float2*>(I.dpart)[(long long)ksi * L + row] = dacc;
+                    }
+                }
+            }
             asm volatile("tcgen05.fence::before_thread_sync;");
             half_sync(bar);
-            if (s_abort[h]) break;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            if (tt == 0) {
-                const uint32_t hb = su32(zhi), lb = su32(zlo);
-#pragma unroll
-                for (int ksx = 0; ksx < TCK / 32; ++ksx) {
-                    const uint64_t dh = tc_desc(hb + ksx * TC_KSTEP_BYTES), dl = tc_desc(lb + ksx * TC_KSTEP_BYTES);
-                    const uint32_t acc0 = (c % TC_FLUSH == 0 && ksx == 0) ? 0u : 1u;
-                    asm volatile(
-                        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.eq.b32 q, %4, %4;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %1, %3, p;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %1, %3, q;\n\t}\n" ::"r"(tmem),
-                        "l"(dh), "l"(dl), "r"(TC_IDESC), "r"(acc0));
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    su32(&mbar[h][st])));
-            }
-            pending |= 1u << st;
-            const bool last = c + 1 == nch;
-            if (last || (c + 1) % TC_FLUSH == 0) {
-                // Every MMA of the block has completed once both stages are drained.
-                for (int q = 0; q < 2; ++q)
-                    if ((pending >> q) & 1u) {
-                        if (!mbar_wait(su32(&mbar[h][q]), (phase >> q) & 1u)) s_abort[h] = 1;
-                        phase ^= 1u << q;
-                        pending &= ~(1u << q);
-                    }
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                half_sync(bar);
-                if (s_abort[h]) break;
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                tc_flush(tmem, wl, lane, c < TC_FLUSH, last, X, XD);
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        half_sync(bar);
-        if (s_abort[h]) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-
-        // Readout: the lower quadrant's sum is in X; lanes 0..63 (warps 0, 1,
-        // 4, 5 of the pipeline) add the upper one into G~ (64 x 64, real,
-        // scaled by 2^24).  Row strides of 65 floats keep the accesses free of
-        // bank conflicts.  Warps 0 and 1 also form delta_l and its product with
-        // c~_l.
-        float* G = X + TC_X;  // [64][65]
-        float TrS = 0.f, TrE = 0.f, TiS = 0.f, TiE = 0.f;
-        if ((wl & 3) < 2) {
-            const int row = 32 * (wl & 3) + lane;  // = l
-            const uint32_t base = tmem + ((uint32_t)(32 * (wl & 3)) << 16);
-            const int c0 = (wl >> 2) * 32;
-#pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                float v[16];
-                tmem_ld16(base + TC_SUM + c0 + 16 * g, v);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) G[row * 65 + c0 + 16 * g + j] = v[j] + X[row * 65 + c0 + 16 * g + j];
-            }
-            if ((wl >> 2) == 0) {
-                const float2 du = tmem_ld2(base + TC_DSUM), dl = XD[row];
-                const float dsc = 1.f / (TC_SCALE * tc_bscale(*I.bn2));  // exact: a power of two
-                const float2 dacc = make_float2((du.x + dl.x) * dsc, -(du.y + dl.y) * dsc);  // conj(b) phi
-                if (row < L) {
-                    const float4 cv = I.cf[row];  // c~_l as (Re hi, Re lo, Im hi, Im lo)
-                    ff_mac(TrS, TrE, cv.x, cv.y, dacc.x);
-                    ff_mac(TrS, TrE, -cv.z, -cv.w, dacc.y);
-                    ff_mac(TiS, TiE, cv.x, cv.y, dacc.y);
-                    ff_mac(TiS, TiE, cv.z, cv.w, dacc.x);
-                    if (s == 0 && I.dpart) reinterpret_cast<float2*>(I.dpart)[(long long)ksi * L + row] = dacc;
-                }
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        half_sync(bar);
-        // Weighting.  G~ is real symmetric and only the real part of the sum
-        // is used: Re(w) G~ over the upper triangle, doubled off the diagonal.
-        // Entries (a, b) with b = tt % 64 and a = tt / 64 + 4k; the weights of
-        // four rows are loaded before they are used.
-        float S = 0.f, E = 0.f;
-        {
-            const int b = tt & 63, a0 = tt >> 6;
-            float2* Gp = (s == 0 && I.Gpart) ? reinterpret_cast<float2*>(I.Gpart) + (long long)ksi * L * L : nullptr;
+            // Weighting.  G~ is real symmetric and only the real part of the sum
+            // is used: Re(w) G~ over the upper triangle, doubled off the diagonal.
+            // Entries (a, b) with b = tt % 64 and a = tt / 64 + 4k; the weights of
+            // four rows are loaded before they are used.
+            float S = 0.f, E = 0.f;
+            {
+                const int b = tt & 63, a0 = tt >> 6;
+                float2* Gp = (s == 0 && I.Gpart) ? reinterpret_cast<float2*>(I.Gpart) + (long long)ksi * L * L : nullptr;
 #pragma unroll 1
-            for (int kb = 0; kb < 16; kb += 4) {
-                float2 wv[4];
+                for (int kb = 0; kb < 16; kb += 4) {
+                    float2 wv[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int a = a0 + 4 * (kb + k);
-                    const float4 w4 = (a <= b && b < L) ? I.wf[a * L + b] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    wv[k] = make_float2(w4.x, w4.y);  // Re hi, Re lo
-                }
+                    for (int k = 0; k < 4; ++k) {
+                        const int a = a0 + 4 * (kb + k);
+                        const float4 w4 = (a <= b && b < L) ? I.wf[a * L + b] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        wv[k] = make_float2(w4.x, w4.y);  // Re hi, Re lo
+                    }
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int a = a0 + 4 * (kb + k);
-                    const float gv = G[a * 65 + b];
-                    ff_mac(S, E, wv[k].x, wv[k].y, a < b ? 2.f * gv : gv);
-                    if (Gp && a < L && b < L) Gp[(long long)a * L + b] = make_float2(gv * TC_UNSCALE, 0.f);
+                    for (int k = 0; k < 4; ++k) {
+                        const int a = a0 + 4 * (kb + k);
+                        const float gv = G[a * 65 + b];
+                        ff_mac(S, E, wv[k].x, wv[k].y, a < b ? 2.f * gv : gv);
+                        if (Gp && a < L && b < L) Gp[(long long)a * L + b] = make_float2(gv * TC_UNSCALE, 0.f);
+                    }
                 }
             }
-        }
-        ff_warp_sum(S, E);
-        ff_warp_sum(TrS, TrE);
-        ff_warp_sum(TiS, TiE);
-        if (lane == 0) {
-            sred[h][0][0][wl] = S;
-            sred[h][0][1][wl] = E;
-            sred[h][1][0][wl] = TrS;
-            sred[h][1][1][wl] = TrE;
-            sred[h][2][0][wl] = TiS;
-            sred[h][2][1][wl] = TiE;
-        }
-        half_sync(bar);
-        if (tt < 3) {  // one quantity per thread; FP64 only for the final pair
-            float S2 = 0.f, E2 = 0.f;
-            for (int v = 0; v < 8; ++v) {
-                ff_add(S2, E2, sred[h][tt][0][v]);
-                E2 += sred[h][tt][1][v];
+            ff_warp_sum(S, E);
+            ff_warp_sum(TrS, TrE);
+            ff_warp_sum(TiS, TiE);
+            if (lane == 0) {
+                sred[h][0][0][wl] = S;
+                sred[h][0][1][wl] = E;
+                sred[h][1][0][wl] = TrS;
+                sred[h][1][1][wl] = TrE;
+                sred[h][2][0][wl] = TiS;
+                sred[h][2][1][wl] = TiE;
             }
-            sred[h][tt][0][0] = S2;
-            sred[h][tt][1][0] = E2;
+            half_sync(bar);
+            if (tt < 3) {  // one quantity per thread; FP64 only for the final pair
+                float S2 = 0.f, E2 = 0.f;
+                for (int v = 0; v < 8; ++v) {
+                    ff_add(S2, E2, sred[h][tt][0][v]);
+                    E2 += sred[h][tt][1][v];
+                }
+                sred[h][tt][0][0] = S2;
+                sred[h][tt][1][0] = E2;
+            }
+            half_sync(bar);
+            if (tt == 0) {
+                double q[3];
+                for (int k = 0; k < 3; ++k) q[k] = (double)sred[h][k][0][0] + (double)sred[h][k][1][0];
+                I.Dpart[(long long)s * ks + ksi] = make_double2(q[0] * (double)TC_UNSCALE, 0.0);
+                I.Tpart[(long long)s * ks + ksi] = make_double2(q[1], q[2]);
+            }
         }
-        half_sync(bar);
-        if (tt == 0) {
-            double q[3];
-            for (int k = 0; k < 3; ++k) q[k] = (double)sred[h][k][0][0] + (double)sred[h][k][1][0];
-            I.Dpart[(long long)s * ks + ksi] = make_double2(q[0] * (double)TC_UNSCALE, 0.0);
-            I.Tpart[(long long)s * ks + ksi] = make_double2(q[1], q[2]);
-        }
+        // No more items: tell the issuer (every stage of this pipeline has
+        // drained, so the next buffer is free).
+        if (tt == 0) srec[h][gc & 1][0] = TC_EXIT;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(su32(&full[h][gc & 1]));
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (t == 0 && (s_abort[0] | s_abort[1])) atomicCAS(status, 0, DEV_TIMEOUT);
+    if (t == 0 && (s_abort[0] | s_abort[1] | s_abort[2])) atomicCAS(status, 0, DEV_TIMEOUT);
     if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(2 * TC_COLS));
 }
 
