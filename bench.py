@@ -66,12 +66,12 @@ def measured_peaks():
 
 
 def executed_gram_entries(L):
-    """Complex products per amplitude the term kernel executes for one shift:
-    per 64-tile of terms, the 136 upper-triangle 4 x 4 blocks of a diagonal
-    tile (plus 64 delta rows) and 128 blocks per half of an off-diagonal tile
-    pair (beta_ml = conj(beta_lm) is taken from its mirror)."""
+    """Gram products per amplitude the CUDA-core term kernel executes for one
+    shift: per 64-tile of terms, the 136 upper-triangle 4 x 4 blocks of a
+    diagonal tile and 128 blocks per half of an off-diagonal tile pair
+    (beta_ml = beta_lm is taken from its mirror)."""
     T = (L + 63) // 64
-    return T * (136 * 16 + 64) + T * (T - 1) * (128 * 16)
+    return T * 136 * 16 + T * (T - 1) * (128 * 16)
 
 
 class Clocks:
@@ -201,7 +201,9 @@ def work_of(shapes, tensor=False):
         N = 1 << n
         terms += S * (L * L + L)
         alg += S * (L * L + L) * 8 * N
-        exe += S * (3 * 2 * 128 * 128 * N // 2 if tensor else executed_gram_entries(L) * 8 * N)
+        # tensor cores: 3 MMAs of 128 x 144 x 16 per 32 amplitudes (Gram and delta rows); CUDA cores: one
+        # real FMA per Gram product (the ansatz state is real) and 4 flops per delta product (complex b)
+        exe += S * (3 * 2 * 128 * 144 * N // 2 if tensor else executed_gram_entries(L) * 2 * N + L * 4 * N)
     return terms, alg, exe
 
 
@@ -485,16 +487,17 @@ def main():
                     "frac_note": peak_src,
                     "achieved_note": "algorithmic: 8N FLOP per paper term, all L^2 ordered pairs + L",
                     "executed": {"tflops": executed, "frac": executed / peak, "flops_per_launch": exe,
-                                 "note": "three FP16 passes (hi hi, hi lo, lo hi) of 128 x 128 x 16 MMAs, "
-                                         "each covering 2 x 16 amplitudes of a 64-term tile"}}
+                                 "note": "three FP16 passes (hi hi, hi lo, lo hi) of 128 x 144 x 16 MMAs, "
+                                         "each covering 2 x 16 amplitudes of a 64-term tile and of b"}}
         else:
             roof = {"bound": "alu", "kernel": "k_terms_smem<float>", "achieved": achieved,
                     "peak": FP32_PEAK, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK, "traffic": None,
                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max SM clock)",
                     "achieved_note": "algorithmic: 8N FLOP per paper term, all L^2 ordered pairs + L",
                     "executed": {"tflops": executed, "frac": executed / FP32_PEAK, "flops_per_launch": exe,
-                                 "note": "Hermitian pairs computed once (upper-triangle 4x4 blocks of "
-                                         "each 64-tile) plus the delta reductions"}}
+                                 "note": "real products (the ansatz state is real), symmetric pairs computed "
+                                         "once (upper-triangle 4x4 blocks of each 64-tile), plus the delta "
+                                         "reductions"}}
         roof.update({"kernel_ms_avg": avg_terms_ms,
                      "kernel_timing": "per-kernel CUDA events in a second pass over the same steps",
                      "phase_ms_avg": {k: v[1] / max(1, v[0]) for k, v in phases.items()},

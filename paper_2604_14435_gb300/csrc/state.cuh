@@ -140,9 +140,12 @@ __device__ void build_state_group(typename V2<R>::t* psi, typename V2<R>::t* scs
 }
 
 // The same state with real amplitudes (every gate of the ansatz is real),
-// multiplied by `scale`, in FP32: psi[0 .. 2^n), scs[0 .. P) as (cos, sin).
-__device__ inline void build_state_real(float* psi, float2* scs, int n, int d, int P, const double2* cs, int s, int t,
-                                 int NTH, int bar, float scale) {
+// multiplied by `scale`, in precision R: psi[0 .. 2^n), scs[0 .. P) as
+// (cos, sin).
+template <typename R>
+__device__ inline void build_state_real(R* psi, typename V2<R>::t* scs, int n, int d, int P, const double2* cs, int s,
+                                        int t, int NTH, int bar, R scale) {
+    using R2 = typename V2<R>::t;
     const int N = 1 << n;
     int k = -1, which = 0;
     if (s > 0) {
@@ -151,32 +154,35 @@ __device__ inline void build_state_real(float* psi, float2* scs, int n, int d, i
     }
     for (int a = t; a < P; a += NTH) {
         const double2 v = cs[(a == k ? which : 0) * P + a];
-        scs[a] = make_float2((float)v.x, (float)v.y);
+        R2 r;
+        r.x = (R)v.x;
+        r.y = (R)v.y;
+        scs[a] = r;
     }
     group_sync(bar, NTH);
     for (int i = t; i < N; i += NTH) {  // initial Ry layer on |0>: a product state
-        float v = scale;
+        R v = scale;
         for (int q = 0; q < n; ++q) v *= ((i >> q) & 1) ? scs[q].y : scs[q].x;
         psi[i] = v;
     }
     group_sync(bar, NTH);
     for (int layer = 1; layer <= d; ++layer) {
         for (int q = 0; q < n; q += 2) {
-            const float c0 = scs[layer * n + q].x, s0 = scs[layer * n + q].y;
+            const R c0 = scs[layer * n + q].x, s0 = scs[layer * n + q].y;
             if (q + 1 < n) {
-                const float c1 = scs[layer * n + q + 1].x, s1 = scs[layer * n + q + 1].y;
+                const R c1 = scs[layer * n + q + 1].x, s1 = scs[layer * n + q + 1].y;
                 for (int p = t; p < N / 4; p += NTH) {
                     const int i00 = ((p >> q) << (q + 2)) | (p & ((1 << q) - 1));
                     const int i01 = i00 | (1 << q), i10 = i00 | (2 << q), i11 = i00 | (3 << q);
-                    float a = psi[i00], b = psi[i01], c = psi[i10], e = psi[i11];
+                    R a = psi[i00], b = psi[i01], c = psi[i10], e = psi[i11];
                     if (q == 0) {  // the CZ ring, applied while loading the layer's first pass
                         if (czring_parity(i00, n)) a = -a;
                         if (czring_parity(i01, n)) b = -b;
                         if (czring_parity(i10, n)) c = -c;
                         if (czring_parity(i11, n)) e = -e;
                     }
-                    const float a1 = c0 * a - s0 * b, b1 = s0 * a + c0 * b;  // Ry on qubit q
-                    const float c2 = c0 * c - s0 * e, e1 = s0 * c + c0 * e;
+                    const R a1 = c0 * a - s0 * b, b1 = s0 * a + c0 * b;  // Ry on qubit q
+                    const R c2 = c0 * c - s0 * e, e1 = s0 * c + c0 * e;
                     psi[i00] = c1 * a1 - s1 * c2;  // Ry on qubit q + 1
                     psi[i10] = s1 * a1 + c1 * c2;
                     psi[i01] = c1 * b1 - s1 * e1;
@@ -185,7 +191,7 @@ __device__ inline void build_state_real(float* psi, float2* scs, int n, int d, i
             } else {
                 for (int p = t; p < N / 2; p += NTH) {
                     const int i0 = ((p >> q) << (q + 1)) | (p & ((1 << q) - 1)), i1 = i0 | (1 << q);
-                    float a = psi[i0], b = psi[i1];
+                    R a = psi[i0], b = psi[i1];
                     if (q == 0) {
                         if (czring_parity(i0, n)) a = -a;
                         if (czring_parity(i1, n)) b = -b;
@@ -353,7 +359,7 @@ __device__ inline void build_state_regs(uint32_t* psi, float* scratch, float2* s
         case 11: state_regs_multiwarp<8, 3>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
         case 12: {  // 16 amplitudes per thread would crowd the registers: gate passes in shared memory
             float* f = reinterpret_cast<float*>(psi);
-            build_state_real(f, scs, n, d, P, cs, s, t, 256, bar, scale);  // ends with a barrier
+            build_state_real<float>(f, scs, n, d, P, cs, s, t, 256, bar, scale);  // ends with a barrier
             for (int i = t; i < N; i += 256) psi[i] = split_hl(f[i]);    // in place, one word each
             group_sync(bar, 256);
             return;

@@ -219,6 +219,29 @@ __device__ __forceinline__ double2 block_sum2_n(double2 v, double2* red, int nth
 }
 
 template <typename R>
+__device__ __forceinline__ void load4r(const R* p, R (&v)[4]);
+template <>
+__device__ __forceinline__ void load4r<float>(const float* p, float (&v)[4]) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+}
+template <>
+__device__ __forceinline__ void load4r<double>(const double* p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+
+// The Ry + CZ-ring state is real, so with the phase i^popc(x & z) in c~_l
+// every phi_l[j] = (-1)^popc(z_l & (j ^ x_l)) psi[j ^ x_l] is real and the
+// Gram G~ is real symmetric: one FMA per product, and delta_l = sum_j
+// conj(b_j) phi_l[j] takes Re b and Im b separately.
+template <typename R>
 __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint32_t* smask, double2* red) {
     using R2 = typename V2<R>::t;
     const int n = I.n, N = 1 << n, L = I.L, T = I.T, ks = I.ks, t = threadIdx.x;
@@ -244,12 +267,13 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
     const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
 
     // n <= 12: psi_s is built in shared memory; n > 12: it was built in HBM
-    // by the state passes and is read from there (L2-resident while in use).
-    R2* psi_smem = reinterpret_cast<R2*>(smem);
-    const R2* psi = I.states ? reinterpret_cast<const R2*>(I.states) + (size_t)s * N : psi_smem;
-    R2* Phl = psi_smem + (I.states ? 0 : N);
-    R2* Phm = Phl + JC * TT;
-    R2* bch = Phm + JC * TT;
+    // by the state passes (complex, imaginary parts zero) and is read from
+    // there (L2-resident while in use).
+    R* psi_smem = reinterpret_cast<R*>(smem);
+    const R2* psi_g = I.states ? reinterpret_cast<const R2*>(I.states) + (size_t)s * N : nullptr;
+    R* Phl = psi_smem + (I.states ? 0 : ((N + 3) & ~3));  // 16-byte aligned for the vector loads
+    R* Phm = Phl + JC * TT;
+    R2* bch = reinterpret_cast<R2*>(Phm + JC * TT);
     R2* scs = bch + JC;  // P entries (only used during the state build)
     uint32_t* sxl = smask;
     uint32_t* szl = smask + TT;
@@ -269,7 +293,7 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
         szm[t] = m < L ? I.zm[m] : 0u;
     }
     if (I.states) __syncthreads();
-    else build_state<R>(psi_smem, scs, I.n, I.d, I.P, I.cs, s);
+    else build_state_real<R>(psi_smem, scs, I.n, I.d, I.P, I.cs, s, t, NT, 0, (R)1);
 
     // Task of this thread: block (a, b) = rows 4a.., columns 4b.. of the tile.
     const int g = t / KSLOT, slot = t % KSLOT;
@@ -289,12 +313,12 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
             bb = half * 8 + (slot & 7);
         }
     }
-    const R2* Pm = same ? Phl : Phm;
-    R are[4][4], aim[4][4];
+    const R* Pm = same ? Phl : Phm;
+    R acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) are[a][b] = aim[a][b] = (R)0;
+        for (int b = 0; b < 4; ++b) acc[a][b] = (R)0;
     R2 dacc;
     dacc.x = dacc.y = (R)0;
     const int lcount = min(TT, L - tl * TT), mcount = min(TT, L - tm * TT);
@@ -307,12 +331,11 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
         for (int e = t; e < JC * TT; e += NT) {
             const int jj = e & (JC - 1), l = e / JC, j = j0 + jj;
             const int at = jj * TT + (l ^ ((jj & 15) << 2));
-            R2 v;
-            v.x = v.y = (R)0;
+            R v = (R)0;
             if (j < kend && l < lcount) {
                 const int src = (j ^ int(sxl[l])) & (N - 1);  // masks >= 2^n are reported, never followed
-                v = psi[src];
-                if (__popc(szl[l] & uint32_t(src)) & 1) v = neg2(v);
+                v = psi_g ? psi_g[src].x : psi_smem[src];
+                if (__popc(szl[l] & uint32_t(src)) & 1) v = -v;
             }
             Phl[at] = v;
         }
@@ -320,12 +343,11 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
             for (int e = t; e < JC * mcols; e += NT) {
                 const int jj = e & (JC - 1), m = mofs + e / JC, j = j0 + jj;
                 const int at = jj * TT + (m ^ ((jj & 15) << 2));
-                R2 v;
-                v.x = v.y = (R)0;
+                R v = (R)0;
                 if (j < kend && m < mcount) {
                     const int src = (j ^ int(sxm[m])) & (N - 1);
-                    v = psi[src];
-                    if (__popc(szm[m] & uint32_t(src)) & 1) v = neg2(v);
+                    v = psi_g ? psi_g[src].x : psi_smem[src];
+                    if (__popc(szm[m] & uint32_t(src)) & 1) v = -v;
                 }
                 Phm[at] = v;
             }
@@ -345,43 +367,36 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
             const int r0 = g * (JC / KG);
 #pragma unroll 4
             for (int jj = r0; jj < r0 + JC / KG; ++jj) {
-                R2 lv[4], mv[4];
+                R lv[4], mv[4];
                 const int sw = (jj & 15) << 2;
-                load4<R>(Phl + jj * TT + ((ba * 4) ^ sw), lv);
-                load4<R>(Pm + jj * TT + ((bb * 4) ^ sw), mv);
+                load4r<R>(Phl + jj * TT + ((ba * 4) ^ sw), lv);
+                load4r<R>(Pm + jj * TT + ((bb * 4) ^ sw), mv);
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        are[a][b] = fma(lv[a].x, mv[b].x, are[a][b]);
-                        are[a][b] = fma(lv[a].y, mv[b].y, are[a][b]);
-                        aim[a][b] = fma(lv[a].x, mv[b].y, aim[a][b]);
-                        aim[a][b] = fma(-lv[a].y, mv[b].x, aim[a][b]);
-                    }
+                    for (int b = 0; b < 4; ++b) acc[a][b] = fma(lv[a], mv[b], acc[a][b]);
             }
         }
         if (want_delta && t < 4 * TT) {  // delta~_l partial: thread t owns l = t % 64, a quarter of the chunk rows
             const int l = t % TT, q = t / TT;
 #pragma unroll
             for (int jj = q * (JC / 4); jj < (q + 1) * (JC / 4); ++jj) {
-                const R2 v = Phl[jj * TT + (l ^ ((jj & 15) << 2))], b2 = bch[jj];
-                dacc.x = fma(b2.x, v.x, fma(b2.y, v.y, dacc.x));
-                dacc.y = fma(b2.x, v.y, fma(-b2.y, v.x, dacc.y));
+                const R v = Phl[jj * TT + (l ^ ((jj & 15) << 2))];
+                const R2 b2 = bch[jj];
+                dacc.x = fma(b2.x, v, dacc.x);  // conj(b) phi with phi real
+                dacc.y = fma(-b2.y, v, dacc.y);
             }
         }
         __syncthreads();
     }
 
     // Add the second K-group's block into the first (through shared memory).
-    R* kred = reinterpret_cast<R*>(Phl);  // chunk buffer is free now
+    R* kred = Phl;  // chunk buffer is free now
     if (g == 1 && active) {
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                kred[(a * 4 + b) * KSLOT + slot] = are[a][b];
-                kred[(16 + a * 4 + b) * KSLOT + slot] = aim[a][b];
-            }
+            for (int b = 0; b < 4; ++b) kred[(a * 4 + b) * KSLOT + slot] = acc[a][b];
     }
     __syncthreads();
     double2 dsum = make_double2(0.0, 0.0);
@@ -389,11 +404,10 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                are[a][b] += kred[(a * 4 + b) * KSLOT + slot];
-                aim[a][b] += kred[(16 + a * 4 + b) * KSLOT + slot];
-            }
+            for (int b = 0; b < 4; ++b) acc[a][b] += kred[(a * 4 + b) * KSLOT + slot];
         // FP64 weighting: contribution of this block (and its mirror) to D_s.
+        // G~ is real symmetric: Re(w_lm) G~_lm, doubled for the mirror; the
+        // imaginary part is kept as a residual on self-mirrored blocks.
         const bool mirror = !(diag && ba == bb);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -402,13 +416,12 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
                 const int l = tl * TT + ba * 4 + a, m = tm * TT + bb * 4 + b;
                 if (l < L && m < L) {
                     const double2 w = I.w[(long long)l * L + m];
-                    const double gr = (double)are[a][b], gi = (double)aim[a][b];
-                    const double re = w.x * gr - w.y * gi;
+                    const double gr = (double)acc[a][b];
                     if (mirror) {
-                        dsum.x += 2.0 * re;
+                        dsum.x += 2.0 * (w.x * gr);
                     } else {
-                        dsum.x += re;
-                        dsum.y += w.x * gi + w.y * gr;
+                        dsum.x += w.x * gr;
+                        dsum.y += w.y * gr;
                     }
                 }
             }
@@ -421,13 +434,10 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
                     const int l = tl * TT + ba * 4 + a, m = tm * TT + bb * 4 + b;
                     if (l < L && m < L) {
                         R2 v;
-                        v.x = are[a][b];
-                        v.y = aim[a][b];
+                        v.x = acc[a][b];
+                        v.y = (R)0;
                         G[(long long)l * L + m] = v;
-                        if (mirror) {
-                            v.y = -v.y;
-                            G[(long long)m * L + l] = v;
-                        }
+                        if (mirror) G[(long long)m * L + l] = v;
                     }
                 }
         }
@@ -437,7 +447,7 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
     if (t == 0) I.Dpart[slotD] = dtot;
     if (want_delta) {
         // Reduce the four row-quarter partials of each l, then weight by ctil in FP64.
-        R2* dred = Phm;  // free (diagonal items do not use it)
+        R2* dred = reinterpret_cast<R2*>(Phm);  // free (diagonal items do not use it)
         if (t < 4 * TT) dred[t] = dacc;
         __syncthreads();
         double2 tsum = make_double2(0.0, 0.0);
@@ -1317,9 +1327,10 @@ struct HostInst {
 constexpr long long HBM_K = 2048;
 
 template <typename R>
-size_t smem_bytes(int nmax, int Pmax) {
+size_t smem_bytes(int nmax, int Pmax) {  // real state (padded to 4 values), two real chunks, b chunk, angles
     using R2 = typename V2<R>::t;
-    return sizeof(R2) * (size_t(1) << nmax) + sizeof(R2) * (2 * JC * TT + JC) + sizeof(R2) * Pmax;
+    return sizeof(R) * (((size_t(1) << nmax) + 3) & ~size_t(3)) + sizeof(R) * (2 * JC * TT) + sizeof(R2) * JC +
+           sizeof(R2) * Pmax;
 }
 
 // Launch parameters of one cost pass (everything but the table contents).
