@@ -365,8 +365,9 @@ int dvqls_ws_load(dvqls_ctx* ctx, const char* path, dvqls_ws** out);
  * INVALID_ARG.  The scratch it needs is, in bytes (each term rounded up to
  * 256): sizeof record + 256 + 16 L + 16 L^2 + 48 P + 8 + 16 S T^2 k
  * + 16 S T k + 24 S, with S = 2P+1, T = ceil(L/64) and k <= 8 the split of
- * the amplitude range; for example n = 10, L = 64, P = 50 needs about 100 KB
- * and L up to about 200 fits.
+ * the amplitude range, plus 16 L^2 + 16 L in DVQLS_FP32 (the weights as
+ * float pairs); for example n = 10, L = 64, P = 50 needs about 170 KB in
+ * FP32, and L up to about 160 (FP32) or 200 (FP64) fits.
  *
  * The call runs on the current CUDA device, ordered on `stream` (a
  * cudaStream_t, NULL = default stream), and returns after cost and grad are

@@ -218,6 +218,41 @@ __device__ __forceinline__ double2 block_sum2_n(double2 v, double2* red, int nth
     return s;  // valid in thread 0
 }
 
+// Float-float accumulation: (S, E) += p exactly (two-sum), and
+// (S, E) += (wh + wl) g with wh g exact by FMA (two-product).
+__device__ __forceinline__ void ff_add(float& S, float& E, float p) {
+    const float s = S + p, bv = s - S;
+    E += (S - (s - bv)) + (p - bv);
+    S = s;
+}
+__device__ __forceinline__ void ff_mac(float& S, float& E, float wh, float wl, float g) {
+    const float p = wh * g;
+    const float err = fmaf(wl, g, fmaf(wh, g, -p));
+    ff_add(S, E, p);
+    E += err;
+}
+__device__ __forceinline__ void ff_warp_sum(float& S, float& E) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, S, o), e2 = __shfl_xor_sync(0xffffffffu, E, o);
+        ff_add(S, E, s2);
+        E += e2;
+    }
+}
+
+// Sum over the block of a float-float pair per thread: exact pairs within
+// warps, FP64 across the warps.  Valid in thread 0.
+__device__ __forceinline__ double block_sum_ff(float S, float E, double* red) {
+    ff_warp_sum(S, E);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)S + (double)E;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += red[k];
+    return r;
+}
+
 template <typename R>
 __device__ __forceinline__ void load4r(const R* p, R (&v)[4]);
 template <>
@@ -400,14 +435,15 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
     }
     __syncthreads();
     double2 dsum = make_double2(0.0, 0.0);
+    float dS = 0.f, dE = 0.f;  // FP32 path: float-float weighting (FP64 issues at 1/64 rate on this part)
     if (g == 0 && active) {
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] += kred[(a * 4 + b) * KSLOT + slot];
-        // FP64 weighting: contribution of this block (and its mirror) to D_s.
-        // G~ is real symmetric: Re(w_lm) G~_lm, doubled for the mirror; the
-        // imaginary part is kept as a residual on self-mirrored blocks.
+        // Weighting: contribution of this block (and its mirror) to D_s.
+        // G~ is real symmetric: Re(w_lm) G~_lm, doubled for the mirror; in
+        // FP64 the imaginary part is kept as a residual on self-mirrored blocks.
         const bool mirror = !(diag && ba == bb);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -415,13 +451,18 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
             for (int b = 0; b < 4; ++b) {
                 const int l = tl * TT + ba * 4 + a, m = tm * TT + bb * 4 + b;
                 if (l < L && m < L) {
-                    const double2 w = I.w[(long long)l * L + m];
-                    const double gr = (double)acc[a][b];
-                    if (mirror) {
-                        dsum.x += 2.0 * (w.x * gr);
+                    if constexpr (sizeof(R) == 4) {
+                        const float4 wv = I.wf[(long long)l * L + m];  // (Re hi, Re lo, Im hi, Im lo)
+                        ff_mac(dS, dE, wv.x, wv.y, mirror ? 2.f * (float)acc[a][b] : (float)acc[a][b]);
                     } else {
-                        dsum.x += w.x * gr;
-                        dsum.y += w.y * gr;
+                        const double2 w = I.w[(long long)l * L + m];
+                        const double gr = (double)acc[a][b];
+                        if (mirror) {
+                            dsum.x += 2.0 * (w.x * gr);
+                        } else {
+                            dsum.x += w.x * gr;
+                            dsum.y += w.y * gr;
+                        }
                     }
                 }
             }
@@ -443,14 +484,20 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
         }
     }
     const long long slotD = (((long long)s * I.F + f) * T * T + u) * ks + ksi;
-    const double2 dtot = block_sum2(dsum, red);
-    if (t == 0) I.Dpart[slotD] = dtot;
+    if constexpr (sizeof(R) == 4) {
+        const double dtot = block_sum_ff(dS, dE, reinterpret_cast<double*>(red));
+        if (t == 0) I.Dpart[slotD] = make_double2(dtot, 0.0);
+    } else {
+        const double2 dtot = block_sum2(dsum, red);
+        if (t == 0) I.Dpart[slotD] = dtot;
+    }
     if (want_delta) {
         // Reduce the four row-quarter partials of each l, then weight by ctil in FP64.
         R2* dred = reinterpret_cast<R2*>(Phm);  // free (diagonal items do not use it)
         if (t < 4 * TT) dred[t] = dacc;
         __syncthreads();
         double2 tsum = make_double2(0.0, 0.0);
+        float trS = 0.f, trE = 0.f, tiS = 0.f, tiE = 0.f;
         if (t < TT) {
             const int l = tl * TT + t;
             R2 v = dred[t];
@@ -460,14 +507,28 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
                 v.y += dred[q * TT + t].y;
             }
             if (l < L) {
-                const double2 c = I.ctil[l];
-                const double vr = (double)v.x, vi = (double)v.y;
-                tsum = make_double2(c.x * vr - c.y * vi, c.x * vi + c.y * vr);
+                if constexpr (sizeof(R) == 4) {
+                    const float4 cv = I.cf[l];  // c~_l as (Re hi, Re lo, Im hi, Im lo)
+                    ff_mac(trS, trE, cv.x, cv.y, (float)v.x);
+                    ff_mac(trS, trE, -cv.z, -cv.w, (float)v.y);
+                    ff_mac(tiS, tiE, cv.x, cv.y, (float)v.y);
+                    ff_mac(tiS, tiE, cv.z, cv.w, (float)v.x);
+                } else {
+                    const double2 c = I.ctil[l];
+                    const double vr = (double)v.x, vi = (double)v.y;
+                    tsum = make_double2(c.x * vr - c.y * vi, c.x * vi + c.y * vr);
+                }
                 if (s == 0 && I.dpart) reinterpret_cast<R2*>(I.dpart)[(long long)ksi * L + l] = v;
             }
         }
-        const double2 ttot = block_sum2(tsum, red);
-        if (t == 0) I.Tpart[((long long)s * T + tl) * ks + ksi] = ttot;
+        if constexpr (sizeof(R) == 4) {
+            const double tr = block_sum_ff(trS, trE, reinterpret_cast<double*>(red));
+            const double ti = block_sum_ff(tiS, tiE, reinterpret_cast<double*>(red));
+            if (t == 0) I.Tpart[((long long)s * T + tl) * ks + ksi] = make_double2(tr, ti);
+        } else {
+            const double2 ttot = block_sum2(tsum, red);
+            if (t == 0) I.Tpart[((long long)s * T + tl) * ks + ksi] = ttot;
+        }
     }
     __syncthreads();
 }
@@ -768,28 +829,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
 // inside one operand array of a stage.
 __device__ __forceinline__ int tc_off16(int row, int kk) {
     return (((kk >> 4) * (TC_NB / 8) + (row >> 3)) * 2 + ((kk >> 3) & 1)) * 128 + (row & 7) * 16;
-}
-
-// Float-float accumulation: (S, E) += p exactly (two-sum), and
-// (S, E) += (wh + wl) g with wh g exact by FMA (two-product).
-__device__ __forceinline__ void ff_add(float& S, float& E, float p) {
-    const float s = S + p, bv = s - S;
-    E += (S - (s - bv)) + (p - bv);
-    S = s;
-}
-__device__ __forceinline__ void ff_mac(float& S, float& E, float wh, float wl, float g) {
-    const float p = wh * g;
-    const float err = fmaf(wl, g, fmaf(wh, g, -p));
-    ff_add(S, E, p);
-    E += err;
-}
-__device__ __forceinline__ void ff_warp_sum(float& S, float& E) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const float s2 = __shfl_xor_sync(0xffffffffu, S, o), e2 = __shfl_xor_sync(0xffffffffu, E, o);
-        ff_add(S, E, s2);
-        E += e2;
-    }
 }
 
 __device__ __forceinline__ void half_sync(int bar) { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(TCH) : "memory"); }
@@ -1558,8 +1597,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         const size_t L = h.L;
         o.ctil = ar.reserve(L * 16);
         o.w = ar.reserve(L * L * 16);
-        o.wf = tc ? ar.reserve(L * L * 16) : 0;
-        o.cf = tc ? ar.reserve(L * 16) : 0;
+        o.wf = fp32 ? ar.reserve(L * L * 16) : 0;  // float-float weights of the FP32 term kernels
+        o.cf = fp32 ? ar.reserve(L * 16) : 0;
         o.bop = tc ? ar.reserve(size_t(tc_bop_stages(h.N)) * TC_BOP_STAGE) : 0;
         o.cs = ar.reserve(size_t(3) * h.P * 16);
         o.bn2 = ar.reserve(8);
@@ -1626,8 +1665,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         I.local = local ? 1 : 0;
         I.ctil = (double2*)(ws + o.ctil);
         I.w = (double2*)(ws + o.w);
-        I.wf = tc ? (float4*)(ws + o.wf) : nullptr;
-        I.cf = tc ? (float4*)(ws + o.cf) : nullptr;
+        I.wf = fp32 ? (float4*)(ws + o.wf) : nullptr;
+        I.cf = fp32 ? (float4*)(ws + o.cf) : nullptr;
         I.bop = tc ? (void*)(ws + o.bop) : nullptr;
         I.cs = (double2*)(ws + o.cs);
         I.bn2 = (double*)(ws + o.bn2);
@@ -1915,6 +1954,8 @@ extern "C" int dvqls_cost_grad_noalloc(void* stream_arg, const dvqls_ansatz* ans
     const size_t o_words = ar.reserve(256);  // status word, queue counter
     const size_t o_ctil = ar.reserve(size_t(L) * 16);
     const size_t o_w = ar.reserve(size_t(L) * L * 16);
+    const size_t o_wf = fp32 ? ar.reserve(size_t(L) * L * 16) : 0;  // float-float weights (FP32 kernel)
+    const size_t o_cf = fp32 ? ar.reserve(size_t(L) * 16) : 0;
     const size_t o_cs = ar.reserve(size_t(3) * P * 16);
     const size_t o_bn2 = ar.reserve(8);
     const size_t o_Dp = ar.reserve(size_t(S) * T * T * ks * 16);
@@ -1944,6 +1985,8 @@ extern "C" int dvqls_cost_grad_noalloc(void* stream_arg, const dvqls_ansatz* ans
     I.b = (const double2*)b;
     I.ctil = (double2*)(base + o_ctil);
     I.w = (double2*)(base + o_w);
+    I.wf = fp32 ? (float4*)(base + o_wf) : nullptr;
+    I.cf = fp32 ? (float4*)(base + o_cf) : nullptr;
     I.cs = (double2*)(base + o_cs);
     I.bn2 = (double*)(base + o_bn2);
     I.Dpart = (double2*)(base + o_Dp);
