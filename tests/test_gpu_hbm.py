@@ -53,15 +53,16 @@ def test_mixed_batch_smem_and_hbm(dv, ctx, prec):
         off += n * (d + 1)
 
 
-def test_n20_sampled_terms_and_cost_identity(dv, ctx):
-    """n = 20 tridiagonal Toeplitz, top-64 terms, depth 2, FP32: sampled beta and
-    delta against the oracle state, and C = 1 - |<b|A~psi>|^2 / ||A~psi||^2
-    (exact for any size)."""
+@pytest.mark.parametrize("prec", [1, 2])
+def test_n20_sampled_terms_and_cost_identity(dv, ctx, prec):
+    """n = 20 tridiagonal Toeplitz, top-64 terms, depth 2, FP32 (CUDA cores and
+    tensor cores): sampled beta and delta against the oracle state, and
+    C = 1 - |<b|A~psi>|^2 / ||A~psi||^2 (exact for any size)."""
     n, d = 20, 2
     inst = wl.throughput_instance(4, n=n, d=d)
     dec = odec.decompose_banded(n, inst["offsets"], inst["bands"], 0.0, 64)
     alpha = inst["alpha"]
-    got = gpu_cost_grad(dv, ctx, n, d, alpha, inst["b"], dec["coef"], dec["x"], dec["z"], 1, grad=False)
+    got = gpu_cost_grad(dv, ctx, n, d, alpha, inst["b"], dec["coef"], dec["x"], dec["z"], prec, grad=False)
     psi = oterms.ansatz_state(n, d, alpha)
     rng = np.random.default_rng(0)
     phis = {}
@@ -82,13 +83,14 @@ def test_n20_sampled_terms_and_cost_identity(dv, ctx):
     assert abs(got["cost"] - cost) <= TOL32["cost"]
 
 
-def test_n20_gradient_components(dv, ctx):
+@pytest.mark.parametrize("prec", [1, 2])
+def test_n20_gradient_components(dv, ctx, prec):
     """Two gradient components at n = 20 against the shift rule evaluated on
     oracle states (the identity above gives each shifted cost)."""
     n, d = 20, 1
     inst = wl.throughput_instance(5, n=n, d=d)
     dec = odec.decompose_banded(n, inst["offsets"], inst["bands"], 0.0, 16)
-    got = gpu_cost_grad(dv, ctx, n, d, inst["alpha"], inst["b"], dec["coef"], dec["x"], dec["z"], 1)
+    got = gpu_cost_grad(dv, ctx, n, d, inst["alpha"], inst["b"], dec["coef"], dec["x"], dec["z"], prec)
 
     def N_D(alpha):
         psi = oterms.ansatz_state(n, d, alpha)
