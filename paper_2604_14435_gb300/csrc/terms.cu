@@ -302,10 +302,10 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
     const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
 
     // n <= 12: psi_s is built in shared memory; n > 12: it was built in HBM
-    // by the state passes (complex, imaginary parts zero) and is read from
-    // there (L2-resident while in use).
+    // by the state passes (real) and is read from there (L2-resident while in
+    // use).
     R* psi_smem = reinterpret_cast<R*>(smem);
-    const R2* psi_g = I.states ? reinterpret_cast<const R2*>(I.states) + (size_t)s * N : nullptr;
+    const R* psi_g = I.states ? reinterpret_cast<const R*>(I.states) + (size_t)s * N : nullptr;
     R* Phl = psi_smem + (I.states ? 0 : ((N + 3) & ~3));  // 16-byte aligned for the vector loads
     R* Phm = Phl + JC * TT;
     R2* bch = reinterpret_cast<R2*>(Phm + JC * TT);
@@ -369,7 +369,7 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
             R v = (R)0;
             if (j < kend && l < lcount) {
                 const int src = (j ^ int(sxl[l])) & (N - 1);  // masks >= 2^n are reported, never followed
-                v = psi_g ? psi_g[src].x : psi_smem[src];
+                v = psi_g ? psi_g[src] : psi_smem[src];
                 if (__popc(szl[l] & uint32_t(src)) & 1) v = -v;
             }
             Phl[at] = v;
@@ -381,7 +381,7 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
                 R v = (R)0;
                 if (j < kend && m < mcount) {
                     const int src = (j ^ int(sxm[m])) & (N - 1);
-                    v = psi_g ? psi_g[src].x : psi_smem[src];
+                    v = psi_g ? psi_g[src] : psi_smem[src];
                     if (__popc(szm[m] & uint32_t(src)) & 1) v = -v;
                 }
                 Phm[at] = v;
@@ -563,12 +563,13 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 1) k_terms_smem(const
 }
 
 // ------------------------------------------------- states in HBM (n > 12)
-// The S shifted states of one instance, S x N amplitudes, built by passes
-// over HBM: the initial Ry layer on |0> is a product state written directly;
-// each further layer is one pass over 4096-amplitude chunks (CZ ring signs and
-// the Ry rotations of qubits 0..11 in shared memory) and one pass over column
-// tiles of HC consecutive low indices x all high indices (Ry of qubits 12..).
-constexpr int LOQ = 12, LOC = 1 << LOQ, HC = 16;
+// The S shifted states of one instance, S x N real amplitudes (the ansatz is
+// real), built by passes over HBM: the initial Ry layer on |0> is a product
+// state written directly; each further layer is one pass over 4096-amplitude
+// chunks (CZ ring signs and the Ry rotations of qubits 0..11 in shared memory)
+// and one pass over column tiles of HC consecutive low indices x all high
+// indices (Ry of qubits 12..; a warp reads whole 128-byte rows).
+constexpr int LOQ = 12, LOC = 1 << LOQ, HC = 32;
 
 template <typename R>
 __device__ __forceinline__ void shift_angle(const Inst& I, int s, int a, R& c, R& sn) {
@@ -584,54 +585,43 @@ __device__ __forceinline__ void shift_angle(const Inst& I, int s, int a, R& c, R
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_hbm_init(const Inst* __restrict__ insts, int idx) {
-    using R2 = typename V2<R>::t;
     const Inst& I = insts[idx];
     __shared__ R cq[32], sq[32];
     const int s = blockIdx.y, n = I.n;
     const size_t N = size_t(1) << n;
     if (threadIdx.x < n) shift_angle<R>(I, s, threadIdx.x, cq[threadIdx.x], sq[threadIdx.x]);
     __syncthreads();
-    R2* st = reinterpret_cast<R2*>(I.states) + s * N;
+    R* st = reinterpret_cast<R*>(I.states) + s * N;
     for (int e = threadIdx.x; e < LOC; e += blockDim.x) {
         const int i = (blockIdx.x << LOQ) + e;
         R v = (R)1;
         for (int q = 0; q < n; ++q) v *= ((i >> q) & 1) ? sq[q] : cq[q];
-        R2 r;
-        r.x = v;
-        r.y = (R)0;
-        st[i] = r;
+        st[i] = v;
     }
 }
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_hbm_lo(const Inst* __restrict__ insts, int idx, int layer) {
-    using R2 = typename V2<R>::t;
     extern __shared__ __align__(16) unsigned char sm[];
-    R2* w = reinterpret_cast<R2*>(sm);
+    R* w = reinterpret_cast<R*>(sm);
     const Inst& I = insts[idx];
     __shared__ R cq[LOQ], sq[LOQ];
     const int s = blockIdx.y, n = I.n, base = blockIdx.x << LOQ;
     const size_t N = size_t(1) << n;
     if (threadIdx.x < LOQ) shift_angle<R>(I, s, layer * n + threadIdx.x, cq[threadIdx.x], sq[threadIdx.x]);
-    R2* st = reinterpret_cast<R2*>(I.states) + s * N + base;
+    R* st = reinterpret_cast<R*>(I.states) + s * N + base;
     for (int e = threadIdx.x; e < LOC; e += blockDim.x) {
-        R2 v = st[e];
-        if (czring_parity(base + e, n)) v = neg2(v);
-        w[e] = v;
+        const R v = st[e];
+        w[e] = czring_parity(base + e, n) ? -v : v;
     }
     __syncthreads();
     for (int q = 0; q < LOQ; ++q) {
         const R c = cq[q], sn = sq[q];
         for (int p = threadIdx.x; p < LOC / 2; p += blockDim.x) {
             const int i0 = ((p >> q) << (q + 1)) | (p & ((1 << q) - 1)), i1 = i0 | (1 << q);
-            const R2 a = w[i0], b = w[i1];
-            R2 u, v;
-            u.x = c * a.x - sn * b.x;
-            u.y = c * a.y - sn * b.y;
-            v.x = sn * a.x + c * b.x;
-            v.y = sn * a.y + c * b.y;
-            w[i0] = u;
-            w[i1] = v;
+            const R a = w[i0], b = w[i1];
+            w[i0] = c * a - sn * b;
+            w[i1] = sn * a + c * b;
         }
         __syncthreads();
     }
@@ -640,16 +630,15 @@ __global__ void __launch_bounds__(256) k_hbm_lo(const Inst* __restrict__ insts, 
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_hbm_hi(const Inst* __restrict__ insts, int idx, int layer) {
-    using R2 = typename V2<R>::t;
     extern __shared__ __align__(16) unsigned char sm[];
-    R2* w = reinterpret_cast<R2*>(sm);  // [H][HC]
+    R* w = reinterpret_cast<R*>(sm);  // [H][HC]
     const Inst& I = insts[idx];
     __shared__ R cq[32], sq[32];
     const int s = blockIdx.y, n = I.n, H = 1 << (n - LOQ), lo0 = blockIdx.x * HC;
     const size_t N = size_t(1) << n;
     if (threadIdx.x < n - LOQ)
         shift_angle<R>(I, s, layer * n + LOQ + threadIdx.x, cq[threadIdx.x], sq[threadIdx.x]);
-    R2* st = reinterpret_cast<R2*>(I.states) + s * N;
+    R* st = reinterpret_cast<R*>(I.states) + s * N;
     for (int e = threadIdx.x; e < H * HC; e += blockDim.x) w[e] = st[((size_t)(e / HC) << LOQ) + lo0 + e % HC];
     __syncthreads();
     for (int q = 0; q < n - LOQ; ++q) {
@@ -657,14 +646,9 @@ __global__ void __launch_bounds__(256) k_hbm_hi(const Inst* __restrict__ insts, 
         for (int p = threadIdx.x; p < (H / 2) * HC; p += blockDim.x) {
             const int hp = p / HC, lo = p % HC;
             const int h0 = ((hp >> q) << (q + 1)) | (hp & ((1 << q) - 1)), h1 = h0 | (1 << q);
-            const R2 a = w[h0 * HC + lo], b = w[h1 * HC + lo];
-            R2 u, v;
-            u.x = c * a.x - sn * b.x;
-            u.y = c * a.y - sn * b.y;
-            v.x = sn * a.x + c * b.x;
-            v.y = sn * a.y + c * b.y;
-            w[h0 * HC + lo] = u;
-            w[h1 * HC + lo] = v;
+            const R a = w[h0 * HC + lo], b = w[h1 * HC + lo];
+            w[h0 * HC + lo] = c * a - sn * b;
+            w[h1 * HC + lo] = sn * a + c * b;
         }
         __syncthreads();
     }
@@ -673,9 +657,8 @@ __global__ void __launch_bounds__(256) k_hbm_hi(const Inst* __restrict__ insts, 
 
 template <typename R>
 int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, int S) {
-    using R2 = typename V2<R>::t;
     const int chunks = 1 << (n - LOQ), tiles = LOC / HC;
-    const size_t lo_smem = sizeof(R2) * LOC, hi_smem = sizeof(R2) * ((size_t)chunks * HC);
+    const size_t lo_smem = sizeof(R) * LOC, hi_smem = sizeof(R) * ((size_t)chunks * HC);
     DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_hbm_lo<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lo_smem)));
     DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_hbm_hi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hi_smem)));
     k_hbm_init<R><<<dim3(chunks, S), 256, 0, ctx->stream>>>(dtable, idx);
@@ -922,9 +905,9 @@ __device__ __forceinline__ void tc_flush(uint32_t tmem, int wl, int lane, bool f
 // rb | (i ^ xlo) with rb = (jb ^ x_l) & ~15: a permutation of 16 consecutive
 // amplitudes, whose signs are the parity of z_l & rb times the per-term 16-bit
 // pattern smask (bit i: parity of z_l & (i ^ xlo)).  psi_hl holds 2^12 psi as
-// packed FP16 (hi, lo) (shared memory); psi_g the FP32 complex state in HBM.
+// packed FP16 (hi, lo) (shared memory); psi_g the FP32 real state in HBM.
 template <bool HBM>
-__device__ __forceinline__ void tc_build_stage(const uint32_t* psi_hl, const float2* psi_g, int N, int j0, int kend,
+__device__ __forceinline__ void tc_build_stage(const uint32_t* psi_hl, const float* psi_g, int N, int j0, int kend,
                                                bool act, uint32_t xl, uint32_t zl, uint32_t smask, int sub, int l,
                                                unsigned char* zhi, unsigned char* zlo) {
     const uint32_t xhi = xl & ~15u, xlo = xl & 15u & uint32_t(N - 1);
@@ -940,7 +923,7 @@ __device__ __forceinline__ void tc_build_stage(const uint32_t* psi_hl, const flo
             uint32_t x = 0u;
             if (i < nval) {
                 const uint32_t src = rb | (uint32_t(i) ^ xlo);
-                x = HBM ? split_hl(psi_g[src].x * TC_SCALE) : psi_hl[src];
+                x = HBM ? split_hl(psi_g[src] * TC_SCALE) : psi_hl[src];
             }
             w[i] = ((sm >> i) & 1u) ? x ^ 0x80008000u : x;
         }
@@ -1088,7 +1071,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             const int ksi = local % ks, s = (local / ks) / I.F;
             const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
             uint32_t* psi_hl = reinterpret_cast<uint32_t*>(hbase);  // 2^12 psi as packed FP16 (hi, lo)
-            const float2* psi_g = I.states ? reinterpret_cast<const float2*>(I.states) + (size_t)s * N : nullptr;
+            const float* psi_g = I.states ? reinterpret_cast<const float*>(I.states) + (size_t)s * N : nullptr;
             float2* scs = reinterpret_cast<float2*>(hbase + (I.states ? 0 : ((size_t)N * 4 + 7) & ~size_t(7)));
             unsigned char* stage0;  // two stages of TC_STAGE_BYTES, then the readout overlay
             {
@@ -1607,7 +1590,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         o.Gp = beta_out ? ar.reserve(size_t(kp) * L * L * r2) : 0;
         o.dp = delta_out ? ar.reserve(size_t(kp) * L * r2) : 0;
         o.NsDs = ar.reserve(size_t(h.S) * 24);
-        o.states = h.hbm ? ar.reserve(size_t(h.S) * size_t(h.N) * r2) : 0;
+        o.states = h.hbm ? ar.reserve(size_t(h.S) * size_t(h.N) * (r2 / 2)) : 0;  // real amplitudes
     }
     int rc = ensure_workspace(ctx, ar.total());
     if (!rc) rc = ensure_pinned(ctx, pin.total());
