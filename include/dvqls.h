@@ -76,8 +76,16 @@ typedef enum {
  *                  in float-float (~2^-44 relative), combined in FP64.
  *                  Served for the global cost when every instance has
  *                  L <= 64 and both on-chip pipelines' shared memory fits;
- *                  other calls run as DVQLS_FP32. */
-typedef enum { DVQLS_FP64 = 0, DVQLS_FP32 = 1, DVQLS_FP32_TC = 2 } dvqls_precision;
+ *                  other calls run as DVQLS_FP32.
+ *   DVQLS_FP32_WHT: an exact reformulation of the same terms (not the
+ *                  paper's per-term evaluation): the pairs (l, m) are
+ *                  grouped by x_l ^ x_m and one FP32
+ *                  Walsh-Hadamard transform of psi[i] psi[i ^ x] gives every
+ *                  beta of a group (likewise delta by x_l); cost for
+ *                  structured LCUs is (groups) x N log N instead of L^2 N.
+ *                  Served for the global cost when every instance has
+ *                  L <= 64 and n <= 10; other calls run as DVQLS_FP32_TC. */
+typedef enum { DVQLS_FP64 = 0, DVQLS_FP32 = 1, DVQLS_FP32_TC = 2, DVQLS_FP32_WHT = 3 } dvqls_precision;
 
 typedef enum { DVQLS_ANSATZ_RY_CZRING = 0 } dvqls_ansatz_kind;
 

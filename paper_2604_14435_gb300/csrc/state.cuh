@@ -234,8 +234,15 @@ __device__ __forceinline__ float ry_lane(float v, int lane, int b, float c, floa
     return fmaf(c, v, ((lane >> b) & 1) ? s * p : -s * p);
 }
 
-template <int A, int LOGA>
-__device__ void state_regs_multiwarp(uint32_t* psi, float* scr0, float* scr1, const float2* scs, int n, int d, int t,
+// Final store of an amplitude: packed FP16 (hi, lo) (PACK) or FP32.
+template <bool PACK>
+__device__ __forceinline__ void st_out(void* psi, int i, float v) {
+    if (PACK) reinterpret_cast<uint32_t*>(psi)[i] = split_hl(v);
+    else reinterpret_cast<float*>(psi)[i] = v;
+}
+
+template <int A, int LOGA, bool PACK>
+__device__ void state_regs_multiwarp(void* psi, float* scr0, float* scr1, const float2* scs, int n, int d, int t,
                                      int bar, float scale) {
     const int lane = t & 31, w = t >> 5;
     float v[A];
@@ -290,14 +297,14 @@ __device__ void state_regs_multiwarp(uint32_t* psi, float* scr0, float* scr1, co
         }
     }
 #pragma unroll
-    for (int r = 0; r < A; ++r) psi[st_index(M, r, w, lane)] = split_hl(v[r]);
+    for (int r = 0; r < A; ++r) st_out<PACK>(psi, st_index(M, r, w, lane), v[r]);
     group_sync(bar, 256);
 }
 
 // n <= 8: one warp holds the whole state (i = (r << 5) | lane; for n < 5 lane
 // i is lane mod 2^n), no barrier inside.
-template <int A, int LOGA>
-__device__ void state_regs_warp(uint32_t* psi, const float2* scs, int n, int d, int lane, float scale) {
+template <int A, int LOGA, bool PACK>
+__device__ void state_regs_warp(void* psi, const float2* scs, int n, int d, int lane, float scale) {
     const int N = 1 << n, lmask = N < 32 ? N - 1 : 31, nl = n < 5 ? n : 5;
     float v[A];
 #pragma unroll
@@ -331,15 +338,16 @@ __device__ void state_regs_warp(uint32_t* psi, const float2* scs, int n, int d, 
     }
     if (lane < N || N >= 32) {
 #pragma unroll
-        for (int r = 0; r < A; ++r) psi[(r << 5) | lane] = split_hl(v[r]);
+        for (int r = 0; r < A; ++r) st_out<PACK>(psi, (r << 5) | lane, v[r]);
     }
 }
 
 // The real state of shift s, times `scale`, for a group of 256 threads (ids t,
-// named barrier `bar`) into psi[0 .. 2^n) as packed FP16 (hi, lo) pairs
-// (split_hl); n <= 12.  scratch: 2 x (2^n + 2^n / 32) floats of shared memory
-// that nothing else uses meanwhile.
-__device__ inline void build_state_regs(uint32_t* psi, float* scratch, float2* scs, int n, int d, int P,
+// named barrier `bar`) into psi[0 .. 2^n), as packed FP16 (hi, lo) pairs
+// (split_hl; PACK) or as FP32; n <= 12.  scratch: 2 x (2^n + 2^n / 32) floats
+// of shared memory that nothing else uses meanwhile.
+template <bool PACK>
+__device__ inline void build_state_regs(void* psi, float* scratch, float2* scs, int n, int d, int P,
                                         const double2* cs, int s, int t, int bar, float scale) {
     int k = -1, which = 0;
     if (s > 0) {
@@ -354,14 +362,16 @@ __device__ inline void build_state_regs(uint32_t* psi, float* scratch, float2* s
     const int N = 1 << n;
     float* scr1 = scratch + N + N / 32;
     switch (n) {
-        case 9: state_regs_multiwarp<2, 1>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
-        case 10: state_regs_multiwarp<4, 2>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
-        case 11: state_regs_multiwarp<8, 3>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
+        case 9: state_regs_multiwarp<2, 1, PACK>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
+        case 10: state_regs_multiwarp<4, 2, PACK>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
+        case 11: state_regs_multiwarp<8, 3, PACK>(psi, scratch, scr1, scs, n, d, t, bar, scale); return;
         case 12: {  // 16 amplitudes per thread would crowd the registers: gate passes in shared memory
             float* f = reinterpret_cast<float*>(psi);
             build_state_real<float>(f, scs, n, d, P, cs, s, t, 256, bar, scale);  // ends with a barrier
-            for (int i = t; i < N; i += 256) psi[i] = split_hl(f[i]);    // in place, one word each
-            group_sync(bar, 256);
+            if (PACK) {
+                for (int i = t; i < N; i += 256) st_out<true>(psi, i, f[i]);  // in place, one word each
+                group_sync(bar, 256);
+            }
             return;
         }
         default: break;
@@ -369,10 +379,10 @@ __device__ inline void build_state_regs(uint32_t* psi, float* scratch, float2* s
     if ((t >> 5) == 0) {
         const int lane = t & 31;
         switch (n) {
-            case 6: state_regs_warp<2, 1>(psi, scs, n, d, lane, scale); break;
-            case 7: state_regs_warp<4, 2>(psi, scs, n, d, lane, scale); break;
-            case 8: state_regs_warp<8, 3>(psi, scs, n, d, lane, scale); break;
-            default: state_regs_warp<1, 0>(psi, scs, n, d, lane, scale); break;  // n <= 5
+            case 6: state_regs_warp<2, 1, PACK>(psi, scs, n, d, lane, scale); break;
+            case 7: state_regs_warp<4, 2, PACK>(psi, scs, n, d, lane, scale); break;
+            case 8: state_regs_warp<8, 3, PACK>(psi, scs, n, d, lane, scale); break;
+            default: state_regs_warp<1, 0, PACK>(psi, scs, n, d, lane, scale); break;  // n <= 5
         }
     }
     group_sync(bar, 256);

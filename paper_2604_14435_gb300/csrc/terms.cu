@@ -55,6 +55,8 @@ struct Inst {
     float4* wf;      // L*L or null: w as float pairs (Re hi, Re lo, Im hi, Im lo)
     float4* cf;      // L or null: ctil as float pairs
     void* bop;       // tensor-core tiles: the b rows of the B operand, TC_BOP_STAGE bytes per stage, or null
+    void* wht;       // Walsh-Hadamard classes: the class table (WHT_TABLE_BYTES), or null
+    float2* bf;      // Walsh-Hadamard classes: b in FP32, or null
     double2* cs;     // 3P: (cos, sin) of half angles: base, +pi/2, -pi/2
     double* bn2;     // ||b||^2
     double2* Dpart;  // S*T*T*ks
@@ -1084,7 +1086,8 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             }
             if (I.states) half_sync(bar);
             else  // in registers; the operand stages are free and serve as transpose scratch; ends with a barrier
-                build_state_regs(psi_hl, reinterpret_cast<float*>(stage0), scs, n, I.d, I.P, I.cs, s, tt, bar, TC_SCALE);
+                build_state_regs<true>(psi_hl, reinterpret_cast<float*>(stage0), scs, n, I.d, I.P, I.cs, s, tt, bar,
+                                       TC_SCALE);
 
             // Build mapping: term l = 8 * warp + lane % 8 and MMA k-step sub =
             // lane / 8: amplitudes sub*16 .. sub*16+15 of the stage go to row l,
@@ -1251,6 +1254,333 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
     if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(2 * TC_COLS));
 }
 
+// ------------------------------------------- Walsh-Hadamard term classes
+// Precision DVQLS_FP32_WHT, an exact reformulation of the term reductions
+// (the same terms of Sec. 2.2, evaluated by class with fewer operations).  With
+// the real state and the phases in c~ (as in the tile kernels),
+//   G~_lm = (-1)^popc(z_l & x) W_x(z_l ^ z_m),  x = x_l ^ x_m,
+//   W_x(z) = sum_i (-1)^popc(z & i) psi[i] psi[i ^ x],
+// so one Walsh-Hadamard transform of g_x(i) = psi[i] psi[i ^ x] gives the
+// terms of every pair (l, m) in the class of x; likewise
+//   delta_l = sum_i (-1)^popc(z_l & i) conj(b[i ^ x_l]) psi[i]
+// is entry z_l of the transform of h(i) = conj(b[i ^ x_l]) psi[i], one per
+// distinct x_l.  A banded Toeplitz LCU has few classes (n = 10, top 64:
+// 22 pair classes, 11 term classes), against 2,080 pair reductions.
+// One CTA of 8 warps per item (instance, shift); a warp transforms one class
+// at a time with the vector in registers (n <= 10: 2^n / 32 values per lane;
+// register bits butterfly in place, lane bits by shuffles), writes it to its
+// own shared-memory row and looks up the class's terms.  Weighted sums in
+// float-float, FP64 across warps.  Served for the global cost when every
+// instance has L <= 64 and n <= 10.
+constexpr int WHT_MAXP = 64 * 65 / 2;  // pairs l <= m of a 64-term LCU
+constexpr int WHT_NT = 256;
+constexpr int WHT_MAXN = 10;
+constexpr int WHT_CT = 1024;  // threads of the class-table kernel
+// Per-instance class table, built on the device by k_wht_classes (bytes):
+constexpr size_t WHT_OFF_CX = 16;                                   // uint32 class masks [WHT_MAXP]
+constexpr size_t WHT_OFF_CO = WHT_OFF_CX + 4 * WHT_MAXP;            // int class offsets [WHT_MAXP + 1]
+constexpr size_t WHT_OFF_PR = WHT_OFF_CO + 4 * (WHT_MAXP + 1);      // uint16 pairs l | m << 8 by class
+constexpr size_t WHT_OFF_DX = (WHT_OFF_PR + 2 * WHT_MAXP + 15) & ~size_t(15);  // uint32 term-class masks [64]
+constexpr size_t WHT_OFF_DO = WHT_OFF_DX + 4 * 64;                  // int term-class offsets [65]
+constexpr size_t WHT_OFF_DT = WHT_OFF_DO + 4 * 65;                  // uint16 terms by class [64]
+constexpr size_t WHT_OFF_EZ = (WHT_OFF_DT + 2 * 64 + 15) & ~size_t(15);  // uint16 z_l ^ z_m by class
+constexpr size_t WHT_OFF_EK = (WHT_OFF_EZ + 2 * WHT_MAXP + 15) & ~size_t(15);  // float2 signed weights by class
+constexpr size_t WHT_TABLE_BYTES = WHT_OFF_EK + 8 * WHT_MAXP;        // header: int pair classes, term classes
+
+// Class tables of one instance (one CTA of 256 per instance): pairs (l <= m)
+// sorted by x_l ^ x_m (bitonic sort of (mask, pair) keys), each with its
+// transform index z_l ^ z_m and its weight (-1)^popc(z_l & x) Re(w_lm),
+// doubled for l < m, as a float pair; terms by x_l; and b as float2.  Runs
+// after k_prepare (which forms the weights).
+__global__ void __launch_bounds__(WHT_CT) k_wht_classes(const Inst* __restrict__ insts) {
+    const Inst I = insts[blockIdx.x];
+    if (!I.wht) return;
+    __shared__ unsigned long long key[4096];
+    __shared__ uint32_t sx[64], sz[64];
+    unsigned char* tb = reinterpret_cast<unsigned char*>(I.wht);
+    const int L = I.L, t = threadIdx.x, np = L * (L + 1) / 2;
+    const long long N = 1LL << I.n;
+    for (long long j = t; j < N; j += WHT_CT) {
+        const double2 v = I.b[j];
+        I.bf[j] = make_float2((float)v.x, (float)v.y);
+    }
+    if (t < 64) {
+        sx[t] = t < L ? I.xm[t] : 0u;
+        sz[t] = t < L ? I.zm[t] : 0u;
+    }
+    for (int e = np + t; e < 4096; e += WHT_CT) key[e] = ~0ull;
+    __syncthreads();
+    for (int q = t; q < L * L; q += WHT_CT) {  // pair (l, m), l <= m, at e = l L - l (l - 1) / 2 + m - l
+        const int l = q / L, m = q % L;
+        if (l <= m)
+            key[l * L - l * (l - 1) / 2 + (m - l)] =
+                ((unsigned long long)(sx[l] ^ sx[m]) << 16) | (unsigned long long)(l | (m << 8));
+    }
+    __syncthreads();
+    for (int k = 2; k <= 4096; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int e = t; e < 4096; e += WHT_CT) {
+                const int p = e ^ j;
+                if (p > e) {
+                    const unsigned long long a = key[e], b = key[p];
+                    if (((e & k) == 0) == (a > b)) {
+                        key[e] = b;
+                        key[p] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    // Class numbers: a class starts where the mask changes; its number is the
+    // count of starts up to it (block prefix sum over 4096 / WHT_CT keys per
+    // thread).
+    constexpr int PER = 4096 / WHT_CT, LANE_N = WHT_CT / 32;
+    __shared__ int tsum[WHT_CT];
+    uint32_t* cx = reinterpret_cast<uint32_t*>(tb + WHT_OFF_CX);
+    int* co = reinterpret_cast<int*>(tb + WHT_OFF_CO);
+    uint16_t* pr = reinterpret_cast<uint16_t*>(tb + WHT_OFF_PR);
+    const int e0 = t * PER;
+    int cnt = 0;
+    for (int e = e0; e < e0 + PER; ++e)
+        if (e < np && (e == 0 || uint32_t(key[e] >> 16) != uint32_t(key[e - 1] >> 16))) ++cnt;
+    tsum[t] = cnt;
+    __syncthreads();
+    if (t < 32) {  // exclusive scan of the per-thread counts by one warp (LANE_N per lane)
+        int v[LANE_N], run = 0;
+        for (int q = 0; q < LANE_N; ++q) {
+            v[q] = run;
+            run += tsum[t * LANE_N + q];
+        }
+        int incl = run;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (t >= o) incl += y;
+        }
+        const int base = incl - run;
+        for (int q = 0; q < LANE_N; ++q) tsum[t * LANE_N + q] = base + v[q];
+        if (t == 31) reinterpret_cast<int*>(tb)[0] = incl;  // number of pair classes
+    }
+    __syncthreads();
+    int cid = tsum[t];
+    for (int e = e0; e < e0 + PER && e < np; ++e) {
+        const uint32_t x = uint32_t(key[e] >> 16);
+        if (e == 0 || x != uint32_t(key[e - 1] >> 16)) {
+            cx[cid] = x;
+            co[cid] = e;
+            ++cid;
+        }
+        const int p = int(key[e] & 0xFFFFu), l = p & 0xFF, m = p >> 8;
+        pr[e] = uint16_t(p);
+        const uint32_t zl = sz[l], zm = sz[m];
+        reinterpret_cast<uint16_t*>(tb + WHT_OFF_EZ)[e] = uint16_t((zl ^ zm) & uint32_t(N - 1));
+        const float4 wv = I.wf[l * L + m];
+        const float sg = ((__popc(zl & x) & 1) ? -1.f : 1.f) * (l < m ? 2.f : 1.f);  // exact scaling
+        reinterpret_cast<float2*>(tb + WHT_OFF_EK)[e] = make_float2(sg * wv.x, sg * wv.y);
+    }
+    if (t == WHT_CT - 1) co[tsum[WHT_CT - 1] + cnt] = np;  // the end of the last class
+    __shared__ int sfirst[64];  // term k is the first with its mask
+    if (t < L) {
+        bool f = true;
+        for (int q = 0; q < t && f; ++q) f = sx[q] != sx[t];
+        sfirst[t] = f ? 1 : 0;
+    }
+    __syncthreads();
+    if (t < L) {  // term classes by x_l: rank and class number of term l from counts
+        uint32_t* dx = reinterpret_cast<uint32_t*>(tb + WHT_OFF_DX);
+        int* dof = reinterpret_cast<int*>(tb + WHT_OFF_DO);
+        uint16_t* dt = reinterpret_cast<uint16_t*>(tb + WHT_OFF_DT);
+        const uint32_t xl = sx[t];
+        int below = 0, rank = 0, cls = 0, nd = 0;
+        bool first = true;
+        for (int k = 0; k < L; ++k) {
+            const uint32_t xk = sx[k];
+            const bool kfirst = sfirst[k] != 0;
+            if (xk < xl) {
+                ++below;
+                if (kfirst) ++cls;
+            }
+            if (xk < xl || (xk == xl && k < t)) ++rank;
+            if (xk == xl && k < t) first = false;
+            if (kfirst) ++nd;
+        }
+        dt[rank] = uint16_t(t);
+        if (first) {
+            dx[cls] = xl;
+            dof[cls] = below;
+        }
+        if (t == 0) {
+            dof[nd] = L;
+            reinterpret_cast<int*>(tb)[1] = nd;
+        }
+    }
+}
+
+// Unnormalised Walsh-Hadamard transform of a warp's vector, v[r] at index
+// (r << 5) | lane (n >= 5), or lane mod 2^n (n < 5, lanes repeat it):
+// butterflies (a, b) -> (a + b, a - b) on every index bit.
+template <int A, int LOGA>
+__device__ __forceinline__ void wht_warp(float (&v)[A], int lane, int nl) {
+#pragma unroll
+    for (int kb = 0; kb < LOGA; ++kb)
+#pragma unroll
+        for (int r = 0; r < A; ++r)
+            if (!((r >> kb) & 1)) {
+                const float a = v[r], b = v[r | (1 << kb)];
+                v[r] = a + b;
+                v[r | (1 << kb)] = a - b;
+            }
+    for (int b = 0; b < nl; ++b)
+#pragma unroll
+        for (int r = 0; r < A; ++r) {
+            const float p = __shfl_xor_sync(0xffffffffu, v[r], 1 << b);
+            v[r] = ((lane >> b) & 1) ? p - v[r] : v[r] + p;
+        }
+}
+
+// One item: every pair class, then every term class, of one shifted state.
+template <int A, int LOGA>
+__device__ void wht_item(const Inst& I, int s, const float* psi, const float2* sb, float* wb, float* dre, float* dim,
+                         const uint32_t* szl, float& S, float& E, int lane) {
+    const int n = I.n, N = 1 << n, L = I.L, w = threadIdx.x >> 5, nl = n < 5 ? n : 5;
+    const int lm = N < 32 ? N - 1 : 31;
+    const unsigned char* tb = reinterpret_cast<const unsigned char*>(I.wht);
+    const int ncls = reinterpret_cast<const int*>(tb)[0], nd = reinterpret_cast<const int*>(tb)[1];
+    const uint32_t* cx = reinterpret_cast<const uint32_t*>(tb + WHT_OFF_CX);
+    const int* co = reinterpret_cast<const int*>(tb + WHT_OFF_CO);
+    const uint16_t* pr = reinterpret_cast<const uint16_t*>(tb + WHT_OFF_PR);
+    const uint16_t* ez = reinterpret_cast<const uint16_t*>(tb + WHT_OFF_EZ);
+    const float2* ek = reinterpret_cast<const float2*>(tb + WHT_OFF_EK);
+    float2* Gp = (s == 0 && I.Gpart) ? reinterpret_cast<float2*>(I.Gpart) : nullptr;
+    for (int c = w; c < ncls; c += WHT_NT / 32) {
+        const uint32_t x = cx[c];
+        float v[A];
+#pragma unroll
+        for (int r = 0; r < A; ++r) {
+            const int i = (r << 5) | (lane & lm);
+            v[r] = psi[i] * psi[(i ^ int(x)) & (N - 1)];  // masks >= 2^n are reported, never followed
+        }
+        wht_warp<A, LOGA>(v, lane, nl);
+        if (lane < N || N >= 32) {
+#pragma unroll
+            for (int r = 0; r < A; ++r) wb[(r << 5) | lane] = v[r];
+        }
+        __syncwarp();
+        const int e0 = co[c], e1 = co[c + 1];
+        for (int e = e0 + lane; e < e1; e += 4 * 32) {  // four independent lookups per lane in flight
+            uint32_t z[4];
+            float2 k[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int eq = e + 32 * q;
+                z[q] = eq < e1 ? ez[eq] : 0u;
+                k[q] = eq < e1 ? ek[eq] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ff_mac(S, E, k[q].x, k[q].y, wb[z[q]]);
+        }
+        if (Gp)  // the beta output of the unshifted state
+            for (int e = e0 + lane; e < e1; e += 32) {
+                const int p = pr[e], l = p & 0xFF, m = p >> 8;
+                float beta = wb[ez[e]];
+                if (__popc(szl[l] & x) & 1) beta = -beta;
+                Gp[(long long)l * L + m] = make_float2(beta, 0.f);
+                Gp[(long long)m * L + l] = make_float2(beta, 0.f);
+            }
+        __syncwarp();
+    }
+    const uint32_t* dx = reinterpret_cast<const uint32_t*>(tb + WHT_OFF_DX);
+    const int* dof = reinterpret_cast<const int*>(tb + WHT_OFF_DO);
+    const uint16_t* dt = reinterpret_cast<const uint16_t*>(tb + WHT_OFF_DT);
+    for (int c = w; c < nd; c += WHT_NT / 32) {
+        const int x = int(dx[c]);
+#pragma unroll 1
+        for (int part = 0; part < 2; ++part) {  // Re and Im of h(i) = conj(b[i ^ x]) psi[i]
+            float v[A];
+#pragma unroll
+            for (int r = 0; r < A; ++r) {
+                const int i = (r << 5) | (lane & lm);
+                const float2 bb = sb[(i ^ x) & (N - 1)];
+                v[r] = (part ? -bb.y : bb.x) * psi[i];
+            }
+            wht_warp<A, LOGA>(v, lane, nl);
+            if (lane < N || N >= 32) {
+#pragma unroll
+                for (int r = 0; r < A; ++r) wb[(r << 5) | lane] = v[r];
+            }
+            __syncwarp();
+            for (int e = dof[c] + lane; e < dof[c + 1]; e += 32) {
+                const int l = dt[e];
+                (part ? dim : dre)[l] = wb[szl[l] & uint32_t(N - 1)];
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(WHT_NT) k_terms_wht(const Inst* __restrict__ insts, int count, long long total,
+                                                      unsigned long long* queue) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t szl[TT];
+    __shared__ float dre[TT], dim[TT];
+    __shared__ double red[WHT_NT / 32];
+    __shared__ long long s_item;
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    float* psi = reinterpret_cast<float*>(smem);                  // 2^WHT_MAXN
+    float* wb = psi + (1 << WHT_MAXN) + w * (1 << WHT_MAXN);      // this warp's transform row
+    float* scratch = psi + (1 << WHT_MAXN) + 8 * (1 << WHT_MAXN);  // state transposes
+    float2* sb = reinterpret_cast<float2*>(scratch + 2 * ((1 << WHT_MAXN) + (1 << WHT_MAXN) / 32));  // b, FP32
+    float2* scs = sb + (1 << WHT_MAXN);
+    for (;;) {
+        if (t == 0) s_item = (long long)atomicAdd(queue, 1ull);
+        __syncthreads();
+        const long long gi = s_item;
+        __syncthreads();
+        if (gi >= total) break;
+        const Inst& I = insts[find_instance(insts, count, gi)];
+        const int s = int(gi - I.item_base), L = I.L;
+        if (t < TT) {
+            szl[t] = t < L ? I.zm[t] : 0u;
+            dre[t] = dim[t] = 0.f;
+        }
+        for (int j = t; j < (1 << I.n); j += WHT_NT) sb[j] = I.bf[j];
+        build_state_regs<false>(psi, scratch, scs, I.n, I.d, I.P, I.cs, s, t, 0, 1.f);  // ends with a barrier
+        float S = 0.f, E = 0.f;
+        switch (I.n) {
+            case 10: wht_item<32, 5>(I, s, psi, sb, wb, dre, dim, szl, S, E, lane); break;
+            case 9: wht_item<16, 4>(I, s, psi, sb, wb, dre, dim, szl, S, E, lane); break;
+            case 8: wht_item<8, 3>(I, s, psi, sb, wb, dre, dim, szl, S, E, lane); break;
+            case 7: wht_item<4, 2>(I, s, psi, sb, wb, dre, dim, szl, S, E, lane); break;
+            case 6: wht_item<2, 1>(I, s, psi, sb, wb, dre, dim, szl, S, E, lane); break;
+            default: wht_item<1, 0>(I, s, psi, sb, wb, dre, dim, szl, S, E, lane); break;  // n <= 5
+        }
+        __syncthreads();
+        float TrS = 0.f, TrE = 0.f, TiS = 0.f, TiE = 0.f;
+        if (t < L) {
+            const float4 cv = I.cf[t];  // c~_l as (Re hi, Re lo, Im hi, Im lo)
+            const float dr = dre[t], di = dim[t];
+            ff_mac(TrS, TrE, cv.x, cv.y, dr);
+            ff_mac(TrS, TrE, -cv.z, -cv.w, di);
+            ff_mac(TiS, TiE, cv.x, cv.y, di);
+            ff_mac(TiS, TiE, cv.z, cv.w, dr);
+            if (s == 0 && I.dpart) reinterpret_cast<float2*>(I.dpart)[t] = make_float2(dr, di);
+        }
+        const double D = block_sum_ff(S, E, red);
+        const double tr = block_sum_ff(TrS, TrE, red);
+        const double ti = block_sum_ff(TiS, TiE, red);
+        if (t == 0) {
+            I.Dpart[s] = make_double2(D, 0.0);
+            I.Tpart[s] = make_double2(tr, ti);
+        }
+        __syncthreads();
+    }
+}
+
+// Shared bytes of the Walsh-Hadamard term kernel (states up to 2^10, Pmax angles).
+inline size_t wht_smem_bytes(int Pmax) {
+    const size_t N = size_t(1) << WHT_MAXN;
+    return 4 * (N + 8 * N + 2 * (N + N / 32)) + 8 * N + 8 * (size_t)Pmax;
+}
+
 // ---------------------------------------------------------------- combine
 template <typename R>
 __global__ void __launch_bounds__(NT) k_combine(const Inst* __restrict__ insts, int* status) {
@@ -1357,7 +1687,7 @@ size_t smem_bytes(int nmax, int Pmax) {  // real state (padded to 4 values), two
 
 // Launch parameters of one cost pass (everything but the table contents).
 struct PassShape {
-    int fp32, tc, count, grid;
+    int fp32, tc, wht, count, grid;
     long long total;
     size_t smem;
     int half;        // tensor-core kernel: shared bytes of one pipeline
@@ -1373,6 +1703,7 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
     if (marks) prof_begin(ctx, 0);
     k_prepare<<<dim3(ps.count, ps.prep_parts), NT, 0, st>>>(dtable, ctx->d_status);
     if (ps.tc) k_prep_bop<<<dim3(ps.count, ps.bop_parts), 256, 0, st>>>(dtable);
+    if (ps.wht) k_wht_classes<<<ps.count, WHT_CT, 0, st>>>(dtable);
     if (marks) prof_end(ctx);
     for (int oi = 0; oi < ps.count; ++oi) {
         const HostInst& h = *tab[oi];
@@ -1387,7 +1718,9 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
         if (rc) return rc;
     }
     if (marks) prof_begin(ctx, 1);
-    if (ps.tc)
+    if (ps.wht)
+        k_terms_wht<<<ps.grid, WHT_NT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue);
+    else if (ps.tc)
         k_terms_tc<<<ps.grid, TCT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue, ctx->d_status, ps.half);
     else if (ps.fp32) k_terms_smem<float><<<ps.grid, NT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue);
     else k_terms_smem<double><<<ps.grid, NT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue);
@@ -1453,7 +1786,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "the local cost has no beta / delta output");
     ctx->err.clear();
     if (count < 1 || !inst) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "count must be >= 1");
-    if (precision != DVQLS_FP32 && precision != DVQLS_FP64 && precision != DVQLS_FP32_TC)
+    if (precision != DVQLS_FP32 && precision != DVQLS_FP64 && precision != DVQLS_FP32_TC &&
+        precision != DVQLS_FP32_WHT)
         return set_error(ctx, DVQLS_ERR_INVALID_ARG, "unknown precision %d", precision);
     std::vector<HostInst> hi(count);
     int nmax = 1, Pmax = 1;
@@ -1492,9 +1826,13 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     }
     cudaSetDevice(ctx->device);
     const bool fp32 = precision != DVQLS_FP64;
-    // Tensor-core tiles serve the global cost when every LCU fits one 64-term
-    // tile; anything else runs the FP32 CUDA-core tiles.
-    bool tc = precision == DVQLS_FP32_TC && !local;
+    // Walsh-Hadamard classes serve the global cost when every LCU fits one
+    // 64-term tile and every state n <= 10 qubits; tensor-core tiles when
+    // every LCU fits one tile (asked for directly, or as the fallback of the
+    // classes); anything else runs the FP32 CUDA-core tiles.
+    bool wht = precision == DVQLS_FP32_WHT && !local;
+    for (const auto& h : hi) wht = wht && h.T == 1 && h.n <= WHT_MAXN;
+    bool tc = !wht && (precision == DVQLS_FP32_TC || precision == DVQLS_FP32_WHT) && !local;
     for (const auto& h : hi) tc = tc && h.T == 1;
     if (tc) {  // and when both pipelines' shared memory fits one CTA
         int optin = 0;
@@ -1504,13 +1842,16 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         tc = tc_smem_bytes(any_smem ? nmax : 0, Pmax) + fa.sharedSizeBytes <= (size_t)optin;
     }
     const int tc_half = tc ? (int)tc_half_bytes(any_smem ? nmax : 0, Pmax) : 0;
-    const size_t smem = tc ? tc_smem_bytes(any_smem ? nmax : 0, Pmax)
-                           : fp32 ? smem_bytes<float>(nmax, Pmax) : smem_bytes<double>(nmax, Pmax);
+    const size_t smem = wht  ? wht_smem_bytes(Pmax)
+                        : tc ? tc_smem_bytes(any_smem ? nmax : 0, Pmax)
+                        : fp32 ? smem_bytes<float>(nmax, Pmax) : smem_bytes<double>(nmax, Pmax);
     const size_t r2 = fp32 ? 8 : 16;
-    auto kfun = tc ? (const void*)k_terms_tc : fp32 ? (const void*)k_terms_smem<float> : (const void*)k_terms_smem<double>;
+    auto kfun = wht ? (const void*)k_terms_wht
+                : tc ? (const void*)k_terms_tc
+                : fp32 ? (const void*)k_terms_smem<float> : (const void*)k_terms_smem<double>;
     DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     int bps = 0;
-    DVQLS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfun, tc ? TCT : NT, smem));
+    DVQLS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfun, wht ? WHT_NT : tc ? TCT : NT, smem));
     if (tc) bps = std::min(bps, 1);  // one CTA per SM, two item pipelines in it
     if (bps < 1) return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "term kernel does not fit (%zu B shared)", smem);
     const long long slots = (long long)ctx->num_sms * bps;
@@ -1523,8 +1864,9 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     for (const auto& h : hi) sig += "|" + std::to_string(h.n) + "," + std::to_string(h.d) + "," + std::to_string(h.L);
     const int cands[] = {1, 2, 4, 8};
     auto tuned = ctx->tune.find(sig);
-    const bool tuning = any_smem && tuned == ctx->tune.end();
+    const bool tuning = any_smem && !wht && tuned == ctx->tune.end();
     auto ks_for = [&](const HostInst& h, int ks) {  // tensor-core items start on whole 128-amplitude stages
+        if (wht) return 1;                            // a class item covers a whole state
         return h.hbm ? (int)std::max<long long>(1, h.N / HBM_K)
                      : (int)std::min<long long>(ks, std::max<long long>(1, h.N / (tc ? TCK : JC)));
     };
@@ -1535,7 +1877,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     struct Off {
         size_t coef, xm, zm, alpha, b;       // staged inputs (ws) ...
         size_t pcoef, pxm, pzm, palpha, pb;  // ... and their pinned slots
-        size_t ctil, w, wf, cf, bop, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta, states;
+        size_t ctil, w, wf, cf, bop, wht, bf, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta, states;
         size_t pcost, pgrad, pbeta, pdelta;
     };
     std::vector<Off> off(count);
@@ -1583,6 +1925,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         o.wf = fp32 ? ar.reserve(L * L * 16) : 0;  // float-float weights of the FP32 term kernels
         o.cf = fp32 ? ar.reserve(L * 16) : 0;
         o.bop = tc ? ar.reserve(size_t(tc_bop_stages(h.N)) * TC_BOP_STAGE) : 0;
+        o.wht = wht ? ar.reserve(WHT_TABLE_BYTES) : 0;
+        o.bf = wht ? ar.reserve(size_t(h.N) * 8) : 0;
         o.cs = ar.reserve(size_t(3) * h.P * 16);
         o.bn2 = ar.reserve(8);
         o.Dp = ar.reserve(size_t(h.S) * h.F * h.T * h.T * kp * 16);
@@ -1651,6 +1995,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         I.wf = fp32 ? (float4*)(ws + o.wf) : nullptr;
         I.cf = fp32 ? (float4*)(ws + o.cf) : nullptr;
         I.bop = tc ? (void*)(ws + o.bop) : nullptr;
+        I.wht = wht ? (void*)(ws + o.wht) : nullptr;
+        I.bf = wht ? (float2*)(ws + o.bf) : nullptr;
         I.cs = (double2*)(ws + o.cs);
         I.bn2 = (double*)(ws + o.bn2);
         I.Dpart = (double2*)(ws + o.Dp);
@@ -1695,6 +2041,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         }
         ps.fp32 = fp32;
         ps.tc = tc;
+        ps.wht = wht;
         ps.count = count;
         ps.total = base;
         ps.grid = (int)std::min<long long>(tc ? (base + 1) / 2 : base, slots);

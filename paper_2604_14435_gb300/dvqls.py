@@ -23,6 +23,7 @@ DVQLS_ERR_ALLOC = 6
 DVQLS_FP64 = 0
 DVQLS_FP32 = 1
 DVQLS_FP32_TC = 2
+DVQLS_FP32_WHT = 3
 DVQLS_ANSATZ_RY_CZRING = 0
 DVQLS_MAX_SMEM_QUBITS = 12
 DVQLS_MAX_QUBITS = 20

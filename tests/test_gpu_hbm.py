@@ -13,7 +13,7 @@ from test_gpu_terms import TOL32, TOL64, check, gpu_cost_grad, random_problem, c
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("n,d,L", [(13, 1, 9), (14, 1, 66), (16, 0, 5)])
 def test_hbm_states_match_definition(dv, ctx, prec, n, d, L):
     rng = np.random.default_rng(700 + n + L)
@@ -23,7 +23,7 @@ def test_hbm_states_match_definition(dv, ctx, prec, n, d, L):
     check(gpu_cost_grad(dv, ctx, n, d, alpha, b, coef, xs, zs, prec), ref, prec)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_mixed_batch_smem_and_hbm(dv, ctx, prec):
     rng = np.random.default_rng(11)
     probs = []

@@ -80,7 +80,7 @@ def random_problem(rng, n, L, complex_b=True):
     return coef, xs, zs, b / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("n,d,L", [(1, 0, 1), (1, 2, 3), (2, 1, 5), (3, 2, 8), (4, 3, 17), (5, 2, 64),
                                    (6, 2, 65), (7, 1, 130), (8, 2, 40)])
 def test_random_lcu_against_definition(dv, ctx, prec, n, d, L):
@@ -92,7 +92,7 @@ def test_random_lcu_against_definition(dv, ctx, prec, n, d, L):
     check(gpu_cost_grad(dv, ctx, n, d, alpha, b, coef, xs, zs, prec), ref, prec)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_cost_only_and_host_pointers(dv, ctx, prec):
     rng = np.random.default_rng(77)
     n, d, L = 5, 3, 20
@@ -103,7 +103,7 @@ def test_cost_only_and_host_pointers(dv, ctx, prec):
     check(got, ref, prec)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_validation_system_32_angles(dv, ctx, prec):
     """n = 3 Toeplitz, full decomposition (L = 8), 32 seeded angle vectors."""
     s = wl.validation_system()
@@ -113,7 +113,7 @@ def test_validation_system_32_angles(dv, ctx, prec):
         check(gpu_cost_grad(dv, ctx, 3, 2, alpha, s["b"], dec["coef"], dec["x"], dec["z"], prec), ref, prec)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("seed", [0, 1])
 def test_throughput_system_full_size(dv, ctx, prec, seed):
     """n = 10, top-64 terms, depth 4: all 101 x 4160 terms against the
@@ -134,7 +134,7 @@ def test_throughput_system_full_size(dv, ctx, prec, seed):
     assert abs(got["delta"][5] - v) <= (1e-12 if prec == 0 else TOL32["delta"])
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_batched_matches_single(dv, ctx, prec):
     """Mixed n, depth and L in one persistent launch == one call each."""
     rng = np.random.default_rng(5)
