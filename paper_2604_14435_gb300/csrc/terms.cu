@@ -1265,7 +1265,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
 //   delta_l = sum_i (-1)^popc(z_l & i) conj(b[i ^ x_l]) psi[i]
 // is entry z_l of the transform of h(i) = conj(b[i ^ x_l]) psi[i], one per
 // distinct x_l.  A banded Toeplitz LCU has few classes (n = 10, top 64:
-// 22 pair classes, 11 term classes), against 2,080 pair reductions.
+// 22 pair classes, 7 term classes), against 2,080 pair reductions.
 // One CTA of 8 warps per item (instance, shift); a warp transforms one class
 // at a time with the vector in registers (n <= 10: 2^n / 32 values per lane;
 // register bits butterfly in place, lane bits by shuffles), writes it to its
