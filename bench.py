@@ -521,7 +521,8 @@ def main():
                                          "reductions"}}
         roof.update({"kernel_ms_avg": avg_terms_ms,
                      "kernel_timing": "per-kernel CUDA events in a second pass over the same steps",
-                     "phase_ms_avg": {k: v[1] / max(1, v[0]) for k, v in phases.items()},
+                     "phase_ms_per_step": {k: v[1] / args.steps for k, v in phases.items()},
+                     "phase_launches_per_step": {k: v[0] / args.steps for k, v in phases.items()},
                      "profiled_pass_ms_per_step": prof_ms / args.steps})
         launches_per_step = sum(phases[k][0] for k in ("prepare", "terms", "combine", "hbm_states")) / args.steps
         metric = METRIC if headline else "cost+grad evals/sec (%s workload)" % args.workload
