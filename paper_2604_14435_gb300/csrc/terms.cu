@@ -1291,7 +1291,30 @@ constexpr size_t WHT_OFF_DO = WHT_OFF_DX + 4 * 64;                  // int term-
 constexpr size_t WHT_OFF_DT = WHT_OFF_DO + 4 * 65;                  // uint16 terms by class [64]
 constexpr size_t WHT_OFF_EZ = (WHT_OFF_DT + 2 * 64 + 15) & ~size_t(15);  // uint16 z_l ^ z_m by class
 constexpr size_t WHT_OFF_EK = (WHT_OFF_EZ + 2 * WHT_MAXP + 15) & ~size_t(15);  // float2 signed weights by class
-constexpr size_t WHT_TABLE_BYTES = WHT_OFF_EK + 8 * WHT_MAXP;        // header: int pair classes, term classes
+constexpr size_t WHT_OFF_KEY = WHT_OFF_EK + 8 * WHT_MAXP;  // the inputs the table was built from: int L,
+                                                              // uint32 x[64], z[64], double2 coef[64]
+constexpr size_t WHT_OFF_SUM = WHT_OFF_KEY + 16 + 8 * 64 + 16 * 64;  // uint64 checksum of bytes [0, WHT_OFF_SUM)
+constexpr size_t WHT_TABLE_BYTES = WHT_OFF_SUM + 16;                   // header: int pair classes, term classes
+
+// 64-bit checksum of a table (sum of mixed, position-tagged 32-bit words;
+// valid in every thread of the block).
+__device__ inline unsigned long long wht_checksum(const unsigned char* tb, unsigned long long* red) {
+    const uint32_t* wds = reinterpret_cast<const uint32_t*>(tb);
+    unsigned long long h = 0;
+    for (int i = threadIdx.x; i < int(WHT_OFF_SUM / 4); i += blockDim.x) {
+        unsigned long long z = ((unsigned long long)wds[i] | ((unsigned long long)i << 32)) + 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        h += z ^ (z >> 31);
+    }
+    for (int o = 16; o; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = h;
+    __syncthreads();
+    unsigned long long s = 0;
+    for (int k = 0; k < int(blockDim.x >> 5); ++k) s += red[k];
+    return s;
+}
 
 // Class tables of one instance (one CTA of 256 per instance): pairs (l <= m)
 // sorted by x_l ^ x_m (bitonic sort of (mask, pair) keys), each with its
@@ -1314,6 +1337,22 @@ __global__ void __launch_bounds__(WHT_CT) k_wht_classes(const Inst* __restrict__
         sx[t] = t < L ? I.xm[t] : 0u;
         sz[t] = t < L ? I.zm[t] : 0u;
     }
+    // The table is a function of L, the masks and the coefficients alone: when
+    // the copy kept with it matches them exactly, it is still valid.
+    int* kL = reinterpret_cast<int*>(tb + WHT_OFF_KEY);
+    uint32_t* kx = reinterpret_cast<uint32_t*>(tb + WHT_OFF_KEY + 16);
+    uint32_t* kz = kx + 64;
+    double2* kc = reinterpret_cast<double2*>(tb + WHT_OFF_KEY + 16 + 8 * 64);
+    bool differs = false;
+    if (t < L) {
+        const double2 c = I.coef[t], k = kc[t];
+        differs = kx[t] != I.xm[t] || kz[t] != I.zm[t] || __double_as_longlong(c.x) != __double_as_longlong(k.x) ||
+                  __double_as_longlong(c.y) != __double_as_longlong(k.y);
+    }
+    if (t == 0 && *kL != L) differs = true;
+    __shared__ unsigned long long red[WHT_CT / 32];
+    unsigned long long* ksum = reinterpret_cast<unsigned long long*>(tb + WHT_OFF_SUM);
+    if (!__syncthreads_or(differs) && wht_checksum(tb, red) == *ksum) return;  // still valid, untouched
     for (int e = np + t; e < 4096; e += WHT_CT) key[e] = ~0ull;
     __syncthreads();
     for (int q = t; q < L * L; q += WHT_CT) {  // pair (l, m), l <= m, at e = l L - l (l - 1) / 2 + m - l
@@ -1419,6 +1458,16 @@ __global__ void __launch_bounds__(WHT_CT) k_wht_classes(const Inst* __restrict__
             reinterpret_cast<int*>(tb)[1] = nd;
         }
     }
+    __syncthreads();  // the table is complete: record what it was built from
+    if (t < L) {
+        kx[t] = I.xm[t];
+        kz[t] = I.zm[t];
+        kc[t] = I.coef[t];
+    }
+    if (t == 0) *kL = L;
+    __syncthreads();  // every word of the table is written
+    const unsigned long long sum = wht_checksum(tb, red);
+    if (t == 0) *ksum = sum;
 }
 
 // Unnormalised Walsh-Hadamard transform of a warp's vector, v[r] at index
