@@ -1572,7 +1572,7 @@ __device__ void wht_item(const Inst& I, int s, const float* psi, const float2* s
     }
 }
 
-__global__ void __launch_bounds__(WHT_NT) k_terms_wht(const Inst* __restrict__ insts, int count, long long total,
+__global__ void __launch_bounds__(WHT_NT, 4) k_terms_wht(const Inst* __restrict__ insts, int count, long long total,
                                                       unsigned long long* queue) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t szl[TT];
