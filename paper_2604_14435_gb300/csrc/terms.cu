@@ -1492,10 +1492,45 @@ __device__ __forceinline__ void wht_warp(float (&v)[A], int lane, int nl) {
         }
 }
 
+// The same transform for 2^10 values (32 per lane) without shuffles: the
+// register bits butterfly in place, the vector goes through the warp's row
+// (stride 33, conflict-free both ways) so that lane L holds the 32 values whose
+// index has high bits L, and the other five bits butterfly in place too.  The
+// result is left in the row at the padded position i + (i >> 5).
+__device__ __forceinline__ void wht_warp_1024(float (&v)[32], int lane, float* row) {
+#pragma unroll
+    for (int kb = 0; kb < 5; ++kb)
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+            if (!((r >> kb) & 1)) {
+                const float a = v[r], b = v[r | (1 << kb)];
+                v[r] = a + b;
+                v[r | (1 << kb)] = a - b;
+            }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) row[r * 33 + lane] = v[r];  // index (r << 5) | lane
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = row[lane * 33 + j];  // index (lane << 5) | j
+    __syncwarp();
+#pragma unroll
+    for (int kb = 0; kb < 5; ++kb)
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+            if (!((r >> kb) & 1)) {
+                const float a = v[r], b = v[r | (1 << kb)];
+                v[r] = a + b;
+                v[r | (1 << kb)] = a - b;
+            }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) row[lane * 33 + j] = v[j];  // index (lane << 5) | j at i + (i >> 5)
+}
+
 // One item: every pair class, then every term class, of one shifted state.
 template <int A, int LOGA>
 __device__ void wht_item(const Inst& I, int s, const float* psi, const float2* sb, float* wb, float* dre, float* dim,
                          const uint32_t* szl, float& S, float& E, int lane) {
+    constexpr bool PAD = A == 32;  // the 2^10 transform leaves its result at i + (i >> 5)
     const int n = I.n, N = 1 << n, L = I.L, w = threadIdx.x >> 5, nl = n < 5 ? n : 5;
     const int lm = N < 32 ? N - 1 : 31;
     const unsigned char* tb = reinterpret_cast<const unsigned char*>(I.wht);
@@ -1514,10 +1549,14 @@ __device__ void wht_item(const Inst& I, int s, const float* psi, const float2* s
             const int i = (r << 5) | (lane & lm);
             v[r] = psi[i] * psi[(i ^ int(x)) & (N - 1)];  // masks >= 2^n are reported, never followed
         }
-        wht_warp<A, LOGA>(v, lane, nl);
-        if (lane < N || N >= 32) {
+        if constexpr (A == 32) {
+            wht_warp_1024(*reinterpret_cast<float(*)[32]>(v), lane, wb);
+        } else {
+            wht_warp<A, LOGA>(v, lane, nl);
+            if (lane < N || N >= 32) {
 #pragma unroll
-            for (int r = 0; r < A; ++r) wb[(r << 5) | lane] = v[r];
+                for (int r = 0; r < A; ++r) wb[(r << 5) | lane] = v[r];
+            }
         }
         __syncwarp();
         const int e0 = co[c], e1 = co[c + 1];
@@ -1531,12 +1570,13 @@ __device__ void wht_item(const Inst& I, int s, const float* psi, const float2* s
                 k[q] = eq < e1 ? ek[eq] : make_float2(0.f, 0.f);
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) ff_mac(S, E, k[q].x, k[q].y, wb[z[q]]);
+            for (int q = 0; q < 4; ++q) ff_mac(S, E, k[q].x, k[q].y, wb[PAD ? z[q] + (z[q] >> 5) : z[q]]);
         }
         if (Gp)  // the beta output of the unshifted state
             for (int e = e0 + lane; e < e1; e += 32) {
                 const int p = pr[e], l = p & 0xFF, m = p >> 8;
-                float beta = wb[ez[e]];
+                const uint32_t ze = ez[e];
+                float beta = wb[PAD ? ze + (ze >> 5) : ze];
                 if (__popc(szl[l] & x) & 1) beta = -beta;
                 Gp[(long long)l * L + m] = make_float2(beta, 0.f);
                 Gp[(long long)m * L + l] = make_float2(beta, 0.f);
@@ -1557,15 +1597,20 @@ __device__ void wht_item(const Inst& I, int s, const float* psi, const float2* s
                 const float2 bb = sb[(i ^ x) & (N - 1)];
                 v[r] = (part ? -bb.y : bb.x) * psi[i];
             }
-            wht_warp<A, LOGA>(v, lane, nl);
-            if (lane < N || N >= 32) {
+            if constexpr (A == 32) {
+                wht_warp_1024(*reinterpret_cast<float(*)[32]>(v), lane, wb);
+            } else {
+                wht_warp<A, LOGA>(v, lane, nl);
+                if (lane < N || N >= 32) {
 #pragma unroll
-                for (int r = 0; r < A; ++r) wb[(r << 5) | lane] = v[r];
+                    for (int r = 0; r < A; ++r) wb[(r << 5) | lane] = v[r];
+                }
             }
             __syncwarp();
             for (int e = dof[c] + lane; e < dof[c + 1]; e += 32) {
                 const int l = dt[e];
-                (part ? dim : dre)[l] = wb[szl[l] & uint32_t(N - 1)];
+                const uint32_t zz = szl[l] & uint32_t(N - 1);
+                (part ? dim : dre)[l] = wb[PAD ? zz + (zz >> 5) : zz];
             }
             __syncwarp();
         }
@@ -1580,9 +1625,10 @@ __global__ void __launch_bounds__(WHT_NT, 4) k_terms_wht(const Inst* __restrict_
     __shared__ double red[WHT_NT / 32];
     __shared__ long long s_item;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    float* psi = reinterpret_cast<float*>(smem);                  // 2^WHT_MAXN
-    float* wb = psi + (1 << WHT_MAXN) + w * (1 << WHT_MAXN);      // this warp's transform row
-    float* scratch = psi + (1 << WHT_MAXN) + 8 * (1 << WHT_MAXN);  // state transposes
+    constexpr int ROW = (1 << WHT_MAXN) + (1 << WHT_MAXN) / 32;      // a transform row, padded
+    float* psi = reinterpret_cast<float*>(smem);                       // 2^WHT_MAXN
+    float* wb = psi + (1 << WHT_MAXN) + w * ROW;                       // this warp's transform row
+    float* scratch = psi + (1 << WHT_MAXN) + 8 * ROW;                  // state transposes
     float2* sb = reinterpret_cast<float2*>(scratch + 2 * ((1 << WHT_MAXN) + (1 << WHT_MAXN) / 32));  // b, FP32
     float2* scs = sb + (1 << WHT_MAXN);
     for (;;) {
@@ -1633,7 +1679,7 @@ __global__ void __launch_bounds__(WHT_NT, 4) k_terms_wht(const Inst* __restrict_
 // Shared bytes of the Walsh-Hadamard term kernel (states up to 2^10, Pmax angles).
 inline size_t wht_smem_bytes(int Pmax) {
     const size_t N = size_t(1) << WHT_MAXN;
-    return 4 * (N + 8 * N + 2 * (N + N / 32)) + 8 * N + 8 * (size_t)Pmax;
+    return 4 * (N + 8 * (N + N / 32) + 2 * (N + N / 32)) + 8 * N + 8 * (size_t)Pmax;
 }
 
 // ---------------------------------------------------------------- combine
