@@ -1294,6 +1294,7 @@ constexpr size_t WHT_OFF_EK = (WHT_OFF_EZ + 2 * WHT_MAXP + 15) & ~size_t(15);  /
 constexpr size_t WHT_OFF_KEY = WHT_OFF_EK + 8 * WHT_MAXP;  // the inputs the table was built from: int L,
                                                               // uint32 x[64], z[64], double2 coef[64]
 constexpr size_t WHT_OFF_SUM = WHT_OFF_KEY + 16 + 8 * 64 + 16 * 64;  // uint64 checksum of bytes [0, WHT_OFF_SUM)
+constexpr size_t WHT_OFF_BIM = WHT_OFF_SUM + 8;  // int: b has a nonzero imaginary part (rewritten every call)
 constexpr size_t WHT_TABLE_BYTES = WHT_OFF_SUM + 16;                   // header: int pair classes, term classes
 
 // 64-bit checksum of a table (sum of mixed, position-tagged 32-bit words;
@@ -1329,9 +1330,16 @@ __global__ void __launch_bounds__(WHT_CT) k_wht_classes(const Inst* __restrict__
     unsigned char* tb = reinterpret_cast<unsigned char*>(I.wht);
     const int L = I.L, t = threadIdx.x, np = L * (L + 1) / 2;
     const long long N = 1LL << I.n;
+    bool im = false;
     for (long long j = t; j < N; j += WHT_CT) {
         const double2 v = I.b[j];
         I.bf[j] = make_float2((float)v.x, (float)v.y);
+        im |= (float)v.y != 0.f;
+    }
+    if (__syncthreads_or(im) != 0) {
+        if (t == 0) *reinterpret_cast<int*>(tb + WHT_OFF_BIM) = 1;
+    } else if (t == 0) {
+        *reinterpret_cast<int*>(tb + WHT_OFF_BIM) = 0;
     }
     if (t < 64) {
         sx[t] = t < L ? I.xm[t] : 0u;
@@ -1541,7 +1549,43 @@ __device__ void wht_item(const Inst& I, int s, const float* psi, const float2* s
     const uint16_t* ez = reinterpret_cast<const uint16_t*>(tb + WHT_OFF_EZ);
     const float2* ek = reinterpret_cast<const float2*>(tb + WHT_OFF_EK);
     float2* Gp = (s == 0 && I.Gpart) ? reinterpret_cast<float2*>(I.Gpart) : nullptr;
-    for (int c = w; c < ncls; c += WHT_NT / 32) {
+    const uint32_t* dx = reinterpret_cast<const uint32_t*>(tb + WHT_OFF_DX);
+    const int* dof = reinterpret_cast<const int*>(tb + WHT_OFF_DO);
+    const uint16_t* dt = reinterpret_cast<const uint16_t*>(tb + WHT_OFF_DT);
+    // One list of transforms for the warps: the pair classes, then the term
+    // classes (Re, and Im when b has an imaginary part: dim stays zero else).
+    const int parts = 1 + *reinterpret_cast<const int*>(tb + WHT_OFF_BIM);
+    const int jobs = ncls + nd * parts;
+#pragma unroll 1
+    for (int j = w; j < jobs; j += WHT_NT / 32) {
+        if (j >= ncls) {
+            const int c = (j - ncls) / parts, part = (j - ncls) - c * parts, x = int(dx[c]);
+            float v[A];  // h(i) = conj(b[i ^ x]) psi[i], its real or imaginary part
+#pragma unroll
+            for (int r = 0; r < A; ++r) {
+                const int i = (r << 5) | (lane & lm);
+                const float2 bb = sb[(i ^ x) & (N - 1)];
+                v[r] = (part ? -bb.y : bb.x) * psi[i];
+            }
+            if constexpr (A == 32) {
+                wht_warp_1024(*reinterpret_cast<float(*)[32]>(v), lane, wb);
+            } else {
+                wht_warp<A, LOGA>(v, lane, nl);
+                if (lane < N || N >= 32) {
+#pragma unroll
+                    for (int r = 0; r < A; ++r) wb[(r << 5) | lane] = v[r];
+                }
+            }
+            __syncwarp();
+            for (int e = dof[c] + lane; e < dof[c + 1]; e += 32) {
+                const int l = dt[e];
+                const uint32_t zz = szl[l] & uint32_t(N - 1);
+                (part ? dim : dre)[l] = wb[PAD ? zz + (zz >> 5) : zz];
+            }
+            __syncwarp();
+            continue;
+        }
+        const int c = j;
         const uint32_t x = cx[c];
         float v[A];
 #pragma unroll
@@ -1582,38 +1626,6 @@ __device__ void wht_item(const Inst& I, int s, const float* psi, const float2* s
                 Gp[(long long)m * L + l] = make_float2(beta, 0.f);
             }
         __syncwarp();
-    }
-    const uint32_t* dx = reinterpret_cast<const uint32_t*>(tb + WHT_OFF_DX);
-    const int* dof = reinterpret_cast<const int*>(tb + WHT_OFF_DO);
-    const uint16_t* dt = reinterpret_cast<const uint16_t*>(tb + WHT_OFF_DT);
-    for (int c = w; c < nd; c += WHT_NT / 32) {
-        const int x = int(dx[c]);
-#pragma unroll 1
-        for (int part = 0; part < 2; ++part) {  // Re and Im of h(i) = conj(b[i ^ x]) psi[i]
-            float v[A];
-#pragma unroll
-            for (int r = 0; r < A; ++r) {
-                const int i = (r << 5) | (lane & lm);
-                const float2 bb = sb[(i ^ x) & (N - 1)];
-                v[r] = (part ? -bb.y : bb.x) * psi[i];
-            }
-            if constexpr (A == 32) {
-                wht_warp_1024(*reinterpret_cast<float(*)[32]>(v), lane, wb);
-            } else {
-                wht_warp<A, LOGA>(v, lane, nl);
-                if (lane < N || N >= 32) {
-#pragma unroll
-                    for (int r = 0; r < A; ++r) wb[(r << 5) | lane] = v[r];
-                }
-            }
-            __syncwarp();
-            for (int e = dof[c] + lane; e < dof[c + 1]; e += 32) {
-                const int l = dt[e];
-                const uint32_t zz = szl[l] & uint32_t(N - 1);
-                (part ? dim : dre)[l] = wb[PAD ? zz + (zz >> 5) : zz];
-            }
-            __syncwarp();
-        }
     }
 }
 
