@@ -1274,8 +1274,9 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
 // 22 pair classes, 7 term classes), against 2,080 pair reductions.
 // One CTA of 8 warps per item (instance, shift); a warp transforms one class
 // at a time with the vector in registers (n <= 10: 2^n / 32 values per lane;
-// register bits butterfly in place, lane bits by shuffles), writes it to its
-// own shared-memory row and looks up the class's terms.  Weighted sums in
+// register bits butterfly in place, lane bits by shuffles or, at n = 10,
+// through the warp's padded shared-memory row), leaves it in that row and
+// looks up the class's terms.  Weighted sums in
 // float-float, FP64 across warps.  Served for the global cost when every
 // instance has L <= 64 and n <= 10.
 constexpr int WHT_MAXP = 64 * 65 / 2;  // pairs l <= m of a 64-term LCU
