@@ -283,6 +283,14 @@ int dvqls_fidelity(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alp
 int dvqls_lcu_solve(dvqls_ctx* ctx, int n, const dvqls_lcu* lcu, const double* b, double tol,
                     int max_iter, double* x, int* iters, double* rel_resid);
 
+/* The same solve for nrhs >= 1 right-hand sides of one LCU in one launch (one
+ * CTA each).  b and x: nrhs x N complex128, right-hand side k at offset k N.
+ * iters, rel_resid: NULL or nrhs entries (host memory).  Every solve runs to
+ * tol or max_iter; returns NUMERIC when any did not reach tol (x, iters and
+ * rel_resid are still written for all). */
+int dvqls_lcu_solve_batched(dvqls_ctx* ctx, int n, const dvqls_lcu* lcu, int nrhs, const double* b,
+                            double tol, int max_iter, double* x, int* iters, double* rel_resid);
+
 typedef struct {
     double lr, beta1, beta2, eps; /* Adam step size and moment decay rates   */
     int max_iter;                 /* updates at most                          */

@@ -3,7 +3,7 @@
 //
 //   dvqls_fidelity      F = |<xhat|psi(alpha)>|^2 / ||xhat||^2, psi built in
 //                       FP64 in shared memory.
-//   dvqls_lcu_solve     xhat = A~^{-1} b for A~ = sum_l c_l A_l applied as a
+//   dvqls_lcu_solve(_batched)  xhat = A~^{-1} b for A~ = sum_l c_l A_l applied as a
 //                       Pauli-string matvec, by conjugate gradients (A~
 //                       Hermitian positive definite), falling back to CG on
 //                       the normal equations A~^dag A~ x = A~^dag b when CG
@@ -130,6 +130,16 @@ __global__ void __launch_bounds__(CGT) k_cg(int n, int L, const double2* coef, c
                                            double2* tmp, double tol, int max_iter, double* out) {
     __shared__ double2 red[CGT / 32];
     const int N = 1 << n;
+    {  // one CTA per right-hand side: vectors of N entries each, four result words
+        const long long o = (long long)blockIdx.x * N;
+        b += o;
+        x += o;
+        r += o;
+        p += o;
+        Ap += o;
+        tmp += o;
+        out += 4 * blockIdx.x;
+    }
     for (int normal = 0; normal < 2; ++normal) {
         // r = rhs (b, or A~^dag b), x = 0, p = r
         if (normal) lcu_matvec(n, L, coef, xm, zm, b, r, 1);
@@ -266,28 +276,30 @@ extern "C" int dvqls_fidelity(dvqls_ctx* ctx, const dvqls_ansatz* an, const doub
     return DVQLS_OK;
 }
 
-extern "C" int dvqls_lcu_solve(dvqls_ctx* ctx, int n, const dvqls_lcu* lcu, const double* b, double tol, int max_iter,
-                               double* x, int* iters, double* rel_resid) {
+extern "C" int dvqls_lcu_solve_batched(dvqls_ctx* ctx, int n, const dvqls_lcu* lcu, int nrhs, const double* b,
+                                       double tol, int max_iter, double* x, int* iters, double* rel_resid) {
     if (!ctx) return DVQLS_ERR_INVALID_ARG;
     ctx->err.clear();
     if (!lcu || !b || !x || lcu->L < 1 || !lcu->coef || !lcu->xmask || !lcu->zmask)
         return set_error(ctx, DVQLS_ERR_INVALID_ARG, "NULL argument or empty LCU");
     if (n < 1 || n > DVQLS_MAX_QUBITS) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "n = %d", n);
+    if (nrhs < 1) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "nrhs = %d", nrhs);
     if (!(tol > 0.0) || max_iter < 1) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "tol > 0 and max_iter >= 1 needed");
     const int L = lcu->L;
     const long long N = 1LL << n;
+    const size_t vec = size_t(nrhs) * size_t(N) * 16;  // one complex128 vector per right-hand side
     cudaSetDevice(ctx->device);
     Arena ar, pin;
     const size_t o_c = ar.reserve(size_t(L) * 16), p_c = pin.reserve(size_t(L) * 16);
     const size_t o_xm = ar.reserve(size_t(L) * 4), p_xm = pin.reserve(size_t(L) * 4);
     const size_t o_zm = ar.reserve(size_t(L) * 4), p_zm = pin.reserve(size_t(L) * 4);
-    const size_t o_b = ar.reserve(size_t(N) * 16), p_b = pin.reserve(size_t(N) * 16);
-    const size_t o_x = ar.reserve(size_t(N) * 16), p_xo = pin.reserve(size_t(N) * 16);
-    const size_t o_r = ar.reserve(size_t(N) * 16);
-    const size_t o_p = ar.reserve(size_t(N) * 16);
-    const size_t o_ap = ar.reserve(size_t(N) * 16);
-    const size_t o_tmp = ar.reserve(size_t(N) * 16);
-    const size_t o_out = ar.reserve(64), p_out = pin.reserve(64);
+    const size_t o_b = ar.reserve(vec), p_b = pin.reserve(vec);
+    const size_t o_x = ar.reserve(vec), p_xo = pin.reserve(vec);
+    const size_t o_r = ar.reserve(vec);
+    const size_t o_p = ar.reserve(vec);
+    const size_t o_ap = ar.reserve(vec);
+    const size_t o_tmp = ar.reserve(vec);
+    const size_t o_out = ar.reserve(size_t(nrhs) * 32);
     int rc = ensure_workspace(ctx, ar.total());
     if (!rc) rc = ensure_pinned(ctx, pin.total());
     if (!rc) rc = pin_acquire(ctx);
@@ -296,26 +308,37 @@ extern "C" int dvqls_lcu_solve(dvqls_ctx* ctx, int n, const dvqls_lcu* lcu, cons
     auto coef = (const double2*)stage_in(ctx, lcu->coef, size_t(L) * 16, p_c, o_c);
     auto xm = (const uint32_t*)stage_in(ctx, lcu->xmask, size_t(L) * 4, p_xm, o_xm);
     auto zm = (const uint32_t*)stage_in(ctx, lcu->zmask, size_t(L) * 4, p_zm, o_zm);
-    auto bd = (const double2*)stage_in(ctx, b, size_t(N) * 16, p_b, o_b);
+    auto bd = (const double2*)stage_in(ctx, b, vec, p_b, o_b);
     double* out = (double*)(ws + o_out);
-    k_cg<<<1, CGT, 0, ctx->stream>>>(n, L, coef, xm, zm, bd, (double2*)(ws + o_x), (double2*)(ws + o_r),
-                                     (double2*)(ws + o_p), (double2*)(ws + o_ap), (double2*)(ws + o_tmp), tol, max_iter,
-                                     out);
+    k_cg<<<nrhs, CGT, 0, ctx->stream>>>(n, L, coef, xm, zm, bd, (double2*)(ws + o_x), (double2*)(ws + o_r),
+                                        (double2*)(ws + o_p), (double2*)(ws + o_ap), (double2*)(ws + o_tmp), tol,
+                                        max_iter, out);
     DVQLS_CUDA_TRY(ctx, cudaGetLastError());
     rc = pin_release(ctx);
     std::vector<PendingOut> pend;
-    if (!rc) rc = enqueue_out(ctx, x, ws + o_x, size_t(N) * 16, p_xo, pend);
-    double res[4] = {0, 0, 0, 0};
-    if (!rc) DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(res, out, sizeof res, cudaMemcpyDeviceToHost, ctx->stream));
+    if (!rc) rc = enqueue_out(ctx, x, ws + o_x, vec, p_xo, pend);
+    std::vector<double> res(size_t(nrhs) * 4, 0.0);
+    if (!rc)
+        DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(res.data(), out, res.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (!rc) rc = sync_and_check(ctx);
     if (rc) return rc;
     finish_out(ctx, pend);
-    if (iters) *iters = int(res[0]);
-    if (rel_resid) *rel_resid = res[1];
-    if (res[2] != 1.0)
-        return set_error(ctx, DVQLS_ERR_NUMERIC, "solve did not reach tol (relative residual %.3g after %d iterations)",
-                         res[1], int(res[0]));
+    int failed = -1;
+    for (int k = 0; k < nrhs; ++k) {
+        if (iters) iters[k] = int(res[4 * k]);
+        if (rel_resid) rel_resid[k] = res[4 * k + 1];
+        if (res[4 * k + 2] != 1.0 && failed < 0) failed = k;
+    }
+    if (failed >= 0)
+        return set_error(ctx, DVQLS_ERR_NUMERIC,
+                         "solve %d did not reach tol (relative residual %.3g after %d iterations)", failed,
+                         res[4 * failed + 1], int(res[4 * failed]));
     return DVQLS_OK;
+}
+
+extern "C" int dvqls_lcu_solve(dvqls_ctx* ctx, int n, const dvqls_lcu* lcu, const double* b, double tol, int max_iter,
+                               double* x, int* iters, double* rel_resid) {
+    return dvqls_lcu_solve_batched(ctx, n, lcu, 1, b, tol, max_iter, x, iters, rel_resid);
 }
 
 extern "C" int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* inst, const double* xhat,

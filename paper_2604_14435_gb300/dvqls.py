@@ -34,7 +34,8 @@ EXPORTED = [
     "dvqls_pauli_decompose", "dvqls_pauli_decompose_banded",
     "dvqls_cost", "dvqls_cost_grad", "dvqls_cost_grad_batched",
     "dvqls_profile_enable", "dvqls_profile_read", "dvqls_cost_grad_noalloc",
-    "dvqls_circuit_cost_grad_fp64", "dvqls_fidelity", "dvqls_lcu_solve", "dvqls_optimize",
+    "dvqls_circuit_cost_grad_fp64", "dvqls_fidelity", "dvqls_lcu_solve", "dvqls_lcu_solve_batched",
+    "dvqls_optimize",
     "dvqls_ws_param_count", "dvqls_ws_create", "dvqls_ws_destroy", "dvqls_ws_infer", "dvqls_ws_grad",
     "dvqls_ws_train_step", "dvqls_ws_get_params", "dvqls_ws_save", "dvqls_ws_load",
     "dvqls_local_cost_grad", "dvqls_local_cost_grad_batched",
@@ -110,6 +111,8 @@ def lib():
         L.dvqls_fidelity.argtypes = [vp, ctypes.POINTER(dvqls_ansatz), dp, dp, dp]
         L.dvqls_lcu_solve.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dvqls_lcu), dp, ctypes.c_double, ctypes.c_int,
                                       dp, ip, ctypes.POINTER(ctypes.c_double)]
+        L.dvqls_lcu_solve_batched.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dvqls_lcu), ctypes.c_int, dp,
+                                              ctypes.c_double, ctypes.c_int, dp, vp, dp]
         L.dvqls_optimize.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dvqls_instance), dp, ctypes.POINTER(dvqls_adam),
                                      dp, ctypes.POINTER(dvqls_opt_result)]
         L.dvqls_ws_param_count.argtypes = [ctypes.c_int] * 3
@@ -255,6 +258,16 @@ def dvqls_lcu_solve(ctx, n, lcu, b, tol, max_iter, x):
     _check(ctx, lib().dvqls_lcu_solve(ctx, int(n), ctypes.byref(lcu), ptr(b), float(tol), int(max_iter), ptr(x),
                                       ctypes.byref(it), ctypes.byref(rr)))
     return it.value, rr.value
+
+
+def dvqls_lcu_solve_batched(ctx, n, lcu, nrhs, b, tol, max_iter, x):
+    """b, x: nrhs x 2^n complex128 as float64 (packed).  Returns (iterations,
+    relative residuals), one per right-hand side."""
+    it = np.zeros(int(nrhs), np.int32)
+    rr = np.zeros(int(nrhs), np.float64)
+    _check(ctx, lib().dvqls_lcu_solve_batched(ctx, int(n), ctypes.byref(lcu), int(nrhs), ptr(b), float(tol),
+                                              int(max_iter), ptr(x), ptr(it), ptr(rr)))
+    return it, rr
 
 
 def make_adam(lr=0.02, beta1=0.9, beta2=0.999, eps=1e-8, max_iter=5000, target_fidelity=0.9999,
