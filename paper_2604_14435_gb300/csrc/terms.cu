@@ -745,14 +745,26 @@ constexpr int TC_BOP_STAGE = 1024;  // bytes of the b rows of one stage (hi and 
 static_assert(TC_REGION_BYTES >= (2 * TC_X + 128) * 4, "the readout fits the two stages");
 static_assert(TC_REGION_BYTES >= 2 * (4096 + 128) * 4, "the state transposes fit the two stages");
 
+// States in shared memory of up to 2^TC_COPY_NMAX amplitudes are kept in four
+// copies, copy t holding psi[k ^ t] at word t (N + 8) + k: a term's 16
+// amplitudes of a block are then four aligned 16-byte loads in order (the low
+// two bits of x_l pick the copy, the next two permute the loads), and the
+// copies start 32 bytes apart in the banks.
+constexpr int TC_COPY_NMAX = 10;
+__host__ __device__ inline size_t tc_psi_bytes(int n, bool copies) {
+    const size_t N = size_t(1) << n;
+    return copies ? 4 * (4 * N + 32) : ((N * 4 + 7) & ~size_t(7));
+}
 // Shared bytes of one pipeline for states of up to 2^nmax amplitudes in
 // shared memory (0: states in HBM) and Pmax angles, and of the whole CTA.
-inline size_t tc_half_bytes(int nmax_smem, int Pmax) {
-    size_t off = (((size_t)(nmax_smem > 0 ? (1 << nmax_smem) : 0) * 4 + 7) & ~size_t(7)) + (size_t)Pmax * 8;
+inline size_t tc_half_bytes(int nmax_smem, int Pmax, bool copies) {
+    size_t off = (nmax_smem > 0 ? tc_psi_bytes(nmax_smem, copies) : 0) + (size_t)Pmax * 8;
     off = (off + 1023) & ~size_t(1023);
     return off + TC_REGION_BYTES;
 }
-inline size_t tc_smem_bytes(int nmax_smem, int Pmax) { return 2 * tc_half_bytes(nmax_smem, Pmax) + 1024; }
+inline size_t tc_smem_bytes(int nmax_smem, int Pmax, bool copies) {
+    return 2 * tc_half_bytes(nmax_smem, Pmax, copies) + 1024;
+}
 // Stages of the b rows of an instance with 2^n amplitudes.
 __host__ __device__ inline long long tc_bop_stages(long long N) { return (N + TCK - 1) / TCK; }
 
@@ -916,37 +928,53 @@ __device__ __forceinline__ void tc_flush(uint32_t tmem, int wl, int lane, bool f
 // packed FP16 (hi, lo) (shared memory); psi_g the FP32 real state in HBM.
 template <bool HBM>
 __device__ __forceinline__ void tc_build_stage(const uint32_t* psi_hl, const float* psi_g, int N, int j0, int kend,
-                                               bool act, uint32_t xl, uint32_t zl, uint32_t smask, int sub, int l,
-                                               unsigned char* zhi, unsigned char* zlo) {
+                                               bool act, uint32_t xl, uint32_t zl, const uint32_t (&sgn)[8], int sub,
+                                               int l, unsigned char* zhi, unsigned char* zlo, bool copies) {
     const uint32_t xhi = xl & ~15u, xlo = xl & 15u & uint32_t(N - 1);
+    const uint32_t* cpy = psi_hl + (xlo & 3u) * uint32_t(N + 8);  // copy holding psi[k ^ (x_l & 3)]
+    const uint32_t xc = xlo >> 2;
 #pragma unroll 1
     for (int hf = 0; hf < 2; ++hf) {
         const int jb = j0 + hf * (TCK / 2) + sub * 16;
         const int nval = act ? min(16, max(0, kend - jb)) : 0;
         const uint32_t rb = (uint32_t(jb) ^ xhi) & uint32_t(N - 1) & ~15u;
-        const uint32_t sm = smask ^ ((__popc(zl & rb) & 1) ? 0xFFFFu : 0u);
+        const uint32_t flip = (__popc(zl & rb) & 1) ? 0x80008000u : 0u;  // the block's common sign
         uint32_t w[16];
+        if (!HBM && copies && nval == 16) {
+            // w[4c + r] = psi[rb + 4 (c ^ xc) + (r ^ (x_l & 3))] = cpy[rb + 4 (c ^ xc) + r]
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            uint32_t x = 0u;
-            if (i < nval) {
-                const uint32_t src = rb | (uint32_t(i) ^ xlo);
-                x = HBM ? split_hl(psi_g[src] * TC_SCALE) : psi_hl[src];
+            for (int c = 0; c < 4; ++c) {
+                const uint4 v = *reinterpret_cast<const uint4*>(cpy + rb + 4u * (uint32_t(c) ^ xc));
+                w[4 * c + 0] = v.x;
+                w[4 * c + 1] = v.y;
+                w[4 * c + 2] = v.z;
+                w[4 * c + 3] = v.w;
             }
-            w[i] = ((sm >> i) & 1u) ? x ^ 0x80008000u : x;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                uint32_t x = 0u;
+                if (i < nval) {
+                    const uint32_t src = rb | (uint32_t(i) ^ xlo);
+                    x = HBM ? split_hl(psi_g[src] * TC_SCALE) : psi_hl[src];
+                }
+                w[i] = x;
+            }
         }
         const int row = hf ? 64 + l : l;
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
+            // Sign bits of packed pairs sit at bits 15 and 31 of a hi (or lo)
+            // word: one three-input XOR applies the term's and the block's sign.
             uint4 hi, lo;
-            hi.x = __byte_perm(w[8 * g + 0], w[8 * g + 1], 0x5410);
-            hi.y = __byte_perm(w[8 * g + 2], w[8 * g + 3], 0x5410);
-            hi.z = __byte_perm(w[8 * g + 4], w[8 * g + 5], 0x5410);
-            hi.w = __byte_perm(w[8 * g + 6], w[8 * g + 7], 0x5410);
-            lo.x = __byte_perm(w[8 * g + 0], w[8 * g + 1], 0x7632);
-            lo.y = __byte_perm(w[8 * g + 2], w[8 * g + 3], 0x7632);
-            lo.z = __byte_perm(w[8 * g + 4], w[8 * g + 5], 0x7632);
-            lo.w = __byte_perm(w[8 * g + 6], w[8 * g + 7], 0x7632);
+            hi.x = __byte_perm(w[8 * g + 0], w[8 * g + 1], 0x5410) ^ sgn[4 * g + 0] ^ flip;
+            hi.y = __byte_perm(w[8 * g + 2], w[8 * g + 3], 0x5410) ^ sgn[4 * g + 1] ^ flip;
+            hi.z = __byte_perm(w[8 * g + 4], w[8 * g + 5], 0x5410) ^ sgn[4 * g + 2] ^ flip;
+            hi.w = __byte_perm(w[8 * g + 6], w[8 * g + 7], 0x5410) ^ sgn[4 * g + 3] ^ flip;
+            lo.x = __byte_perm(w[8 * g + 0], w[8 * g + 1], 0x7632) ^ sgn[4 * g + 0] ^ flip;
+            lo.y = __byte_perm(w[8 * g + 2], w[8 * g + 3], 0x7632) ^ sgn[4 * g + 1] ^ flip;
+            lo.z = __byte_perm(w[8 * g + 4], w[8 * g + 5], 0x7632) ^ sgn[4 * g + 2] ^ flip;
+            lo.w = __byte_perm(w[8 * g + 6], w[8 * g + 7], 0x7632) ^ sgn[4 * g + 3] ^ flip;
             const int kk = sub * 16 + 8 * g;  // k within the stage's TCK/2
             *reinterpret_cast<uint4*>(zhi + tc_off16(row, kk)) = hi;
             *reinterpret_cast<uint4*>(zlo + tc_off16(row, kk)) = lo;
@@ -980,7 +1008,8 @@ constexpr long long TC_IDLE_POLLS = 1LL << 30;
 // the builders wait on before they write the buffer again or read the
 // accumulator.  Neither side waits at a CTA barrier per stage.
 __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ insts, int count, long long total,
-                                                     unsigned long long* queue, int* status, int half_bytes) {
+                                                     unsigned long long* queue, int* status, int half_bytes,
+                                                     int copy_nmax) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) unsigned long long full[2][2], empty[2][2];
     __shared__ uint32_t srec[2][2][2];  // per pipeline and buffer: hi operand address, first-of-block flag
@@ -1080,10 +1109,12 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
             uint32_t* psi_hl = reinterpret_cast<uint32_t*>(hbase);  // 2^12 psi as packed FP16 (hi, lo)
             const float* psi_g = I.states ? reinterpret_cast<const float*>(I.states) + (size_t)s * N : nullptr;
-            float2* scs = reinterpret_cast<float2*>(hbase + (I.states ? 0 : ((size_t)N * 4 + 7) & ~size_t(7)));
+            const bool copies = !I.states && n >= 4 && n <= copy_nmax;
+            const size_t psi_bytes = I.states ? 0 : tc_psi_bytes(n, copies);
+            float2* scs = reinterpret_cast<float2*>(hbase + psi_bytes);
             unsigned char* stage0;  // two stages of TC_STAGE_BYTES, then the readout overlay
             {
-                size_t off = (I.states ? 0 : (((size_t)N * 4 + 7) & ~size_t(7))) + (size_t)I.P * 8;
+                const size_t off = psi_bytes + (size_t)I.P * 8;
                 stage0 = hbase + ((off + 1023) & ~size_t(1023));
             }
             if (tt < TT) {
@@ -1094,6 +1125,14 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             else  // in registers; the operand stages are free and serve as transpose scratch; ends with a barrier
                 build_state_regs<true>(psi_hl, reinterpret_cast<float*>(stage0), scs, n, I.d, I.P, I.cs, s, tt, bar,
                                        TC_SCALE);
+            if (copies) {  // copy t: psi[k ^ t] at word t (N + 8) + k
+                for (int k = tt; k < N; k += TCH) {
+                    const uint32_t v = psi_hl[k];
+#pragma unroll
+                    for (int t3 = 1; t3 < 4; ++t3) psi_hl[t3 * (N + 8) + (k ^ t3)] = v;
+                }
+                half_sync(bar);
+            }
 
             // Build mapping: term l = 8 * warp + lane % 8 and MMA k-step sub =
             // lane / 8: amplitudes sub*16 .. sub*16+15 of the stage go to row l,
@@ -1101,11 +1140,13 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             // stores contiguous 128-byte core-matrix columns.
             const int l = (tt & 7) | (wl << 3), sub = (lane >> 3) & 3;
             const uint32_t xl = sxl[h][l], zl = szl[h][l];
-            uint32_t smask = 0u;  // bit i: parity of z_l & (i ^ (x_l mod 16))
+            uint32_t sgn[8];  // word g: sign bits of elements 2g (bit 15) and 2g + 1 (bit 31) of a 16-block
             {
                 const uint32_t xlo = xl & 15u & uint32_t(N - 1);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) smask |= uint32_t(__popc(zl & 15u & (uint32_t(i) ^ xlo)) & 1) << i;
+                for (int g = 0; g < 8; ++g)
+                    sgn[g] = ((__popc(zl & 15u & (uint32_t(2 * g) ^ xlo)) & 1) ? 0x8000u : 0u) |
+                             ((__popc(zl & 15u & (uint32_t(2 * g + 1) ^ xlo)) & 1) ? 0x80000000u : 0u);
             }
             const int nch = (kend - kbeg + TCK - 1) / TCK;
             float* X = reinterpret_cast<float*>(stage0);  // [64][65] readout of the lower quadrant, once every MMA is done
@@ -1128,9 +1169,10 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                                               row * 16) = v;
                 }
                 if (I.states)
-                    tc_build_stage<true>(nullptr, psi_g, N, j0, kend, l < L, xl, zl, smask, sub, l, zhi, zlo);
+                    tc_build_stage<true>(nullptr, psi_g, N, j0, kend, l < L, xl, zl, sgn, sub, l, zhi, zlo, false);
                 else
-                    tc_build_stage<false>(psi_hl, nullptr, N, j0, kend, l < L, xl, zl, smask, sub, l, zhi, zlo);
+                    tc_build_stage<false>(psi_hl, nullptr, N, j0, kend, l < L, xl, zl, sgn, sub, l, zhi, zlo,
+                                          copies);
                 if (tt == 0) {
                     srec[h][st][0] = su32(zhi);
                     srec[h][st][1] = (c % TC_FLUSH == 0) ? 1u : 0u;
@@ -1805,6 +1847,7 @@ struct PassShape {
     long long total;
     size_t smem;
     int half;        // tensor-core kernel: shared bytes of one pipeline
+    int copy_nmax;   // tensor-core kernel: states of 2^4 .. 2^copy_nmax amplitudes kept in four copies (0: none)
     int prep_parts;  // CTAs per instance of k_prepare (weights split ~256 per CTA)
     int bop_parts;   // CTAs per instance of k_prep_bop
 };
@@ -1842,7 +1885,8 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
     if (ps.wht)
         k_terms_wht<<<ps.grid, WHT_NT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue);
     else if (ps.tc)
-        k_terms_tc<<<ps.grid, TCT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue, ctx->d_status, ps.half);
+        k_terms_tc<<<ps.grid, TCT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue, ctx->d_status, ps.half,
+                                                  ps.copy_nmax);
     else if (ps.fp32) k_terms_smem<float><<<ps.grid, NT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue);
     else k_terms_smem<double><<<ps.grid, NT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue);
     if (marks) prof_end(ctx);
@@ -1955,16 +1999,19 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     for (const auto& h : hi) wht = wht && h.T == 1 && h.n <= WHT_MAXN;
     bool tc = !wht && (precision == DVQLS_FP32_TC || precision == DVQLS_FP32_WHT) && !local;
     for (const auto& h : hi) tc = tc && h.T == 1;
+    bool tc_copies = false;
     if (tc) {  // and when both pipelines' shared memory fits one CTA
         int optin = 0;
         cudaFuncAttributes fa;
         DVQLS_CUDA_TRY(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
         DVQLS_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, (const void*)k_terms_tc));
-        tc = tc_smem_bytes(any_smem ? nmax : 0, Pmax) + fa.sharedSizeBytes <= (size_t)optin;
+        tc = tc_smem_bytes(any_smem ? nmax : 0, Pmax, false) + fa.sharedSizeBytes <= (size_t)optin;
+        tc_copies = any_smem && nmax <= TC_COPY_NMAX &&
+                    tc_smem_bytes(nmax, Pmax, true) + fa.sharedSizeBytes <= (size_t)optin;
     }
-    const int tc_half = tc ? (int)tc_half_bytes(any_smem ? nmax : 0, Pmax) : 0;
+    const int tc_half = tc ? (int)tc_half_bytes(any_smem ? nmax : 0, Pmax, tc_copies) : 0;
     const size_t smem = wht  ? wht_smem_bytes(Pmax)
-                        : tc ? tc_smem_bytes(any_smem ? nmax : 0, Pmax)
+                        : tc ? tc_smem_bytes(any_smem ? nmax : 0, Pmax, tc_copies)
                         : fp32 ? smem_bytes<float>(nmax, Pmax) : smem_bytes<double>(nmax, Pmax);
     const size_t r2 = fp32 ? 8 : 16;
     auto kfun = wht ? (const void*)k_terms_wht
@@ -2168,6 +2215,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         ps.grid = (int)std::min<long long>(tc ? (base + 1) / 2 : base, slots);
         ps.smem = smem;
         ps.half = tc_half;
+        ps.copy_nmax = tc_copies ? TC_COPY_NMAX : 0;
         ps.prep_parts = (int)std::min<long long>(16, std::max<long long>(1, LLmax / NT));
         ps.bop_parts = (int)std::min<long long>(64, std::max<long long>(1, tc_bop_stages(Nmax) * (TC_BOP_STAGE / 16) / 256));
     };
