@@ -745,25 +745,32 @@ constexpr int TC_BOP_STAGE = 1024;  // bytes of the b rows of one stage (hi and 
 static_assert(TC_REGION_BYTES >= (2 * TC_X + 128) * 4, "the readout fits the two stages");
 static_assert(TC_REGION_BYTES >= 2 * (4096 + 128) * 4, "the state transposes fit the two stages");
 
-// States in shared memory of up to 2^TC_COPY_NMAX amplitudes are kept in four
+// States in shared memory of 2^4 .. 2^copy_nmax amplitudes are kept in four
 // copies, copy t holding psi[k ^ t] at word t (N + 8) + k: a term's 16
 // amplitudes of a block are then four aligned 16-byte loads in order (the low
 // two bits of x_l pick the copy, the next two permute the loads), and the
-// copies start 32 bytes apart in the banks.
-constexpr int TC_COPY_NMAX = 10;
+// copies start 32 bytes apart in the banks.  copy_nmax <= TC_COPY_NMAX is
+// chosen per batch so that both pipelines still fit one CTA.
+constexpr int TC_COPY_NMAX = 11;
 __host__ __device__ inline size_t tc_psi_bytes(int n, bool copies) {
     const size_t N = size_t(1) << n;
     return copies ? 4 * (4 * N + 32) : ((N * 4 + 7) & ~size_t(7));
 }
+__host__ __device__ inline bool tc_copies(int n, int copy_nmax) { return n >= 4 && n <= copy_nmax; }
 // Shared bytes of one pipeline for states of up to 2^nmax amplitudes in
-// shared memory (0: states in HBM) and Pmax angles, and of the whole CTA.
-inline size_t tc_half_bytes(int nmax_smem, int Pmax, bool copies) {
-    size_t off = (nmax_smem > 0 ? tc_psi_bytes(nmax_smem, copies) : 0) + (size_t)Pmax * 8;
-    off = (off + 1023) & ~size_t(1023);
+// shared memory (0: states in HBM), copies up to 2^copy_nmax and Pmax angles,
+// and of the whole CTA.
+inline size_t tc_half_bytes(int nmax_smem, int Pmax, int copy_nmax) {
+    size_t psi = 0;
+    if (nmax_smem > 0) {
+        const int nc = std::min(nmax_smem, copy_nmax);
+        psi = std::max(tc_psi_bytes(nmax_smem, tc_copies(nmax_smem, copy_nmax)), tc_psi_bytes(nc, tc_copies(nc, copy_nmax)));
+    }
+    const size_t off = (psi + (size_t)Pmax * 8 + 1023) & ~size_t(1023);
     return off + TC_REGION_BYTES;
 }
-inline size_t tc_smem_bytes(int nmax_smem, int Pmax, bool copies) {
-    return 2 * tc_half_bytes(nmax_smem, Pmax, copies) + 1024;
+inline size_t tc_smem_bytes(int nmax_smem, int Pmax, int copy_nmax) {
+    return 2 * tc_half_bytes(nmax_smem, Pmax, copy_nmax) + 1024;
 }
 // Stages of the b rows of an instance with 2^n amplitudes.
 __host__ __device__ inline long long tc_bop_stages(long long N) { return (N + TCK - 1) / TCK; }
@@ -1109,7 +1116,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
             uint32_t* psi_hl = reinterpret_cast<uint32_t*>(hbase);  // 2^12 psi as packed FP16 (hi, lo)
             const float* psi_g = I.states ? reinterpret_cast<const float*>(I.states) + (size_t)s * N : nullptr;
-            const bool copies = !I.states && n >= 4 && n <= copy_nmax;
+            const bool copies = !I.states && tc_copies(n, copy_nmax);
             const size_t psi_bytes = I.states ? 0 : tc_psi_bytes(n, copies);
             float2* scs = reinterpret_cast<float2*>(hbase + psi_bytes);
             unsigned char* stage0;  // two stages of TC_STAGE_BYTES, then the readout overlay
@@ -1999,19 +2006,19 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     for (const auto& h : hi) wht = wht && h.T == 1 && h.n <= WHT_MAXN;
     bool tc = !wht && (precision == DVQLS_FP32_TC || precision == DVQLS_FP32_WHT) && !local;
     for (const auto& h : hi) tc = tc && h.T == 1;
-    bool tc_copies = false;
+    int copy_nmax = 0;
     if (tc) {  // and when both pipelines' shared memory fits one CTA
         int optin = 0;
         cudaFuncAttributes fa;
         DVQLS_CUDA_TRY(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
         DVQLS_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, (const void*)k_terms_tc));
-        tc = tc_smem_bytes(any_smem ? nmax : 0, Pmax, false) + fa.sharedSizeBytes <= (size_t)optin;
-        tc_copies = any_smem && nmax <= TC_COPY_NMAX &&
-                    tc_smem_bytes(nmax, Pmax, true) + fa.sharedSizeBytes <= (size_t)optin;
+        tc = tc_smem_bytes(any_smem ? nmax : 0, Pmax, 0) + fa.sharedSizeBytes <= (size_t)optin;
+        for (int c = TC_COPY_NMAX; tc && any_smem && c >= 4 && !copy_nmax; --c)
+            if (tc_smem_bytes(nmax, Pmax, c) + fa.sharedSizeBytes <= (size_t)optin) copy_nmax = c;
     }
-    const int tc_half = tc ? (int)tc_half_bytes(any_smem ? nmax : 0, Pmax, tc_copies) : 0;
+    const int tc_half = tc ? (int)tc_half_bytes(any_smem ? nmax : 0, Pmax, copy_nmax) : 0;
     const size_t smem = wht  ? wht_smem_bytes(Pmax)
-                        : tc ? tc_smem_bytes(any_smem ? nmax : 0, Pmax, tc_copies)
+                        : tc ? tc_smem_bytes(any_smem ? nmax : 0, Pmax, copy_nmax)
                         : fp32 ? smem_bytes<float>(nmax, Pmax) : smem_bytes<double>(nmax, Pmax);
     const size_t r2 = fp32 ? 8 : 16;
     auto kfun = wht ? (const void*)k_terms_wht
@@ -2215,7 +2222,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         ps.grid = (int)std::min<long long>(tc ? (base + 1) / 2 : base, slots);
         ps.smem = smem;
         ps.half = tc_half;
-        ps.copy_nmax = tc_copies ? TC_COPY_NMAX : 0;
+        ps.copy_nmax = copy_nmax;
         ps.prep_parts = (int)std::min<long long>(16, std::max<long long>(1, LLmax / NT));
         ps.bop_parts = (int)std::min<long long>(64, std::max<long long>(1, tc_bop_stages(Nmax) * (TC_BOP_STAGE / 16) / 256));
     };
