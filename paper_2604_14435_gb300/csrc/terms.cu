@@ -725,7 +725,7 @@ int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, 
 constexpr int TCK = 128;       // amplitudes per stage: 2 x 64, i.e. 4 MMA k-steps of 16 in each row half
 constexpr int TCH = 256;       // threads per pipeline
 constexpr int TCT = 2 * TCH + 32;  // threads per CTA: two builder pipelines and the MMA issuer warp
-constexpr int TC_FLUSH = 2;    // stages per accumulator block
+constexpr int TC_FLUSH = 4;    // stages per accumulator block (16 MMAs of each pass: max |beta| error 3.4e-6 to n = 14)
 constexpr int TC_COLS = 256;   // TMEM columns per pipeline
 constexpr int TC_NB = 144;     // B rows: 128 term rows, then Re b / Im b of both halves (4 rows) and 12 unused
 constexpr int TC_SUM = 144;    // TMEM: running sum of the Gram quadrants (64 columns)
