@@ -107,7 +107,18 @@ __device__ __forceinline__ double2 ctil_of(const Inst& I, int l) {
 // Per-instance tables of a pass (Sec. 2.3 Stage I inputs).  Grid (instances,
 // parts): part 0 checks the inputs, forms ||b||^2 and c~; every part takes its
 // share of the shift angle tables and of the L^2 weights w_lm = conj(c~_l) c~_m.
-__global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, int* status) {
+// Programmatic dependent launch: the kernels of a pass after the first are
+// launched so that their CTAs may start while the previous kernel finishes;
+// each waits for the previous grid's completion (and its memory) before its
+// first dependent access, and lets the next kernel start once all its CTAs
+// are running.  Launched without the attribute, both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+__global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, int* status,
+                                                unsigned long long* queue) {
+    pdl_trigger();
+    if (queue && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *queue = 0ull;  // the term kernel's work queue
     const Inst I = insts[blockIdx.x];
     const int t = threadIdx.x, part = blockIdx.y, parts = gridDim.y;
     const long long N = 1LL << I.n;
@@ -141,10 +152,12 @@ __global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, 
     for (int a = t + part * NT; a < I.P; a += NT * parts) {
         const double al = I.alpha[a];
         if (!isfinite(al)) set_status(status, DEV_NONFINITE_INPUT);
-        double s0, c0, s1, c1, s2, c2;
+        double s0, c0;
         sincos(0.5 * al, &s0, &c0);
-        sincos(0.5 * (al + 0.5 * M_PI), &s1, &c1);
-        sincos(0.5 * (al - 0.5 * M_PI), &s2, &c2);
+        // Half angles of alpha +- pi/2 are alpha/2 +- pi/4: sin = (s0 +- c0) / sqrt 2,
+        // cos = (c0 -+ s0) / sqrt 2.
+        const double s1 = (s0 + c0) * M_SQRT1_2, c1 = (c0 - s0) * M_SQRT1_2;
+        const double s2 = (s0 - c0) * M_SQRT1_2, c2 = (c0 + s0) * M_SQRT1_2;
         I.cs[a] = make_double2(c0, s0);
         I.cs[I.P + a] = make_double2(c1, s1);
         I.cs[2 * I.P + a] = make_double2(c2, s2);
@@ -548,6 +561,8 @@ __device__ __forceinline__ int find_instance(const Inst* insts, int count, long 
 template <typename R>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 1) k_terms_smem(const Inst* __restrict__ insts, int count, long long total,
                                                   unsigned long long* queue) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t smask[4 * TT];
     __shared__ double2 red[NT / 32];
@@ -788,6 +803,8 @@ __device__ __forceinline__ float tc_bscale(double bn2) {
 // and of its second half (130, 131), scaled by tc_bscale.  Grid (instances,
 // parts) of 256 threads, after k_prepare (which forms ||b||^2).
 __global__ void __launch_bounds__(256) k_prep_bop(const Inst* __restrict__ insts) {
+    pdl_wait();
+    pdl_trigger();
     const Inst I = insts[blockIdx.x];
     if (!I.bop || !I.b) return;
     const long long N = 1LL << I.n, chunks = tc_bop_stages(N) * (TC_BOP_STAGE / 16);
@@ -1017,6 +1034,8 @@ constexpr long long TC_IDLE_POLLS = 1LL << 30;
 __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ insts, int count, long long total,
                                                      unsigned long long* queue, int* status, int half_bytes,
                                                      int copy_nmax) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) unsigned long long full[2][2], empty[2][2];
     __shared__ uint32_t srec[2][2][2];  // per pipeline and buffer: hi operand address, first-of-block flag
@@ -1373,6 +1392,8 @@ __device__ inline unsigned long long wht_checksum(const unsigned char* tb, unsig
 // doubled for l < m, as a float pair; terms by x_l; and b as float2.  Runs
 // after k_prepare (which forms the weights).
 __global__ void __launch_bounds__(WHT_CT) k_wht_classes(const Inst* __restrict__ insts) {
+    pdl_wait();
+    pdl_trigger();
     const Inst I = insts[blockIdx.x];
     if (!I.wht) return;
     __shared__ unsigned long long key[4096];
@@ -1681,6 +1702,8 @@ __device__ void wht_item(const Inst& I, int s, const float* psi, const float2* s
 
 __global__ void __launch_bounds__(WHT_NT, 4) k_terms_wht(const Inst* __restrict__ insts, int count, long long total,
                                                       unsigned long long* queue) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t szl[TT];
     __shared__ float dre[TT], dim[TT];
@@ -1747,6 +1770,7 @@ inline size_t wht_smem_bytes(int Pmax) {
 // ---------------------------------------------------------------- combine
 template <typename R>
 __global__ void __launch_bounds__(NT) k_combine(const Inst* __restrict__ insts, int* status) {
+    pdl_wait();
     using R2 = typename V2<R>::t;
     const Inst I = insts[blockIdx.x];
     const int t = threadIdx.x, T = I.T, ks = I.ks, L = I.L;
@@ -1859,23 +1883,41 @@ struct PassShape {
     int bop_parts;   // CTAs per instance of k_prep_bop
 };
 
+// Launch with programmatic stream serialization (the kernel starts with
+// pdl_wait, so it observes everything its predecessor wrote).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // The kernel sequence of one cost pass on stream `st`: queue reset, prepare,
 // state passes of the instances with states in HBM, term tiles, combine.
 static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, const PassShape& ps,
                        const std::vector<const HostInst*>& tab, bool marks) {
-    DVQLS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_queue, 0, sizeof(unsigned long long), st));
-    // One profiling mark per kernel, so the launch counts are exact.
+    // One profiling mark per kernel, so the launch counts are exact.  The
+    // prepare kernel also resets the work queue.
     if (marks) prof_begin(ctx, 0);
-    k_prepare<<<dim3(ps.count, ps.prep_parts), NT, 0, st>>>(dtable, ctx->d_status);
+    k_prepare<<<dim3(ps.count, ps.prep_parts), NT, 0, st>>>(dtable, ctx->d_status, ctx->d_queue);
     if (marks) prof_end(ctx);
     if (ps.tc) {
         if (marks) prof_begin(ctx, 0);
-        k_prep_bop<<<dim3(ps.count, ps.bop_parts), 256, 0, st>>>(dtable);
+        DVQLS_CUDA_TRY(ctx, launch_pdl(k_prep_bop, dim3(ps.count, ps.bop_parts), dim3(256), 0, st, dtable));
         if (marks) prof_end(ctx);
     }
     if (ps.wht) {
         if (marks) prof_begin(ctx, 0);
-        k_wht_classes<<<ps.count, WHT_CT, 0, st>>>(dtable);
+        DVQLS_CUDA_TRY(ctx, launch_pdl(k_wht_classes, dim3(ps.count), dim3(WHT_CT), 0, st, dtable));
         if (marks) prof_end(ctx);
     }
     for (int oi = 0; oi < ps.count; ++oi) {
@@ -1890,16 +1932,21 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
     }
     if (marks) prof_begin(ctx, 1);
     if (ps.wht)
-        k_terms_wht<<<ps.grid, WHT_NT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue);
+        DVQLS_CUDA_TRY(ctx, launch_pdl(k_terms_wht, dim3(ps.grid), dim3(WHT_NT), ps.smem, st, dtable, ps.count,
+                                       ps.total, ctx->d_queue));
     else if (ps.tc)
-        k_terms_tc<<<ps.grid, TCT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue, ctx->d_status, ps.half,
-                                                  ps.copy_nmax);
-    else if (ps.fp32) k_terms_smem<float><<<ps.grid, NT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue);
-    else k_terms_smem<double><<<ps.grid, NT, ps.smem, st>>>(dtable, ps.count, ps.total, ctx->d_queue);
+        DVQLS_CUDA_TRY(ctx, launch_pdl(k_terms_tc, dim3(ps.grid), dim3(TCT), ps.smem, st, dtable, ps.count, ps.total,
+                                       ctx->d_queue, ctx->d_status, ps.half, ps.copy_nmax));
+    else if (ps.fp32)
+        DVQLS_CUDA_TRY(ctx, launch_pdl(k_terms_smem<float>, dim3(ps.grid), dim3(NT), ps.smem, st, dtable, ps.count,
+                                       ps.total, ctx->d_queue));
+    else
+        DVQLS_CUDA_TRY(ctx, launch_pdl(k_terms_smem<double>, dim3(ps.grid), dim3(NT), ps.smem, st, dtable, ps.count,
+                                       ps.total, ctx->d_queue));
     if (marks) prof_end(ctx);
     if (marks) prof_begin(ctx, 2);
-    if (ps.fp32) k_combine<float><<<ps.count, NT, 0, st>>>(dtable, ctx->d_status);
-    else k_combine<double><<<ps.count, NT, 0, st>>>(dtable, ctx->d_status);
+    if (ps.fp32) DVQLS_CUDA_TRY(ctx, launch_pdl(k_combine<float>, dim3(ps.count), dim3(NT), 0, st, dtable, ctx->d_status));
+    else DVQLS_CUDA_TRY(ctx, launch_pdl(k_combine<double>, dim3(ps.count), dim3(NT), 0, st, dtable, ctx->d_status));
     if (marks) prof_end(ctx);
     DVQLS_CUDA_TRY(ctx, cudaGetLastError());
     return DVQLS_OK;
@@ -2511,7 +2558,7 @@ extern "C" int dvqls_cost_grad_noalloc(void* stream_arg, const dvqls_ansatz* ans
         return DVQLS_ERR_CUDA;
     }
     k_noalloc_store<<<1, 1, 0, stream>>>(I, table);
-    k_prepare<<<1, NT, 0, stream>>>(table, status);
+    k_prepare<<<1, NT, 0, stream>>>(table, status, nullptr);
     const long long total = I.items;
     const int grid = (int)std::min<long long>(total, slots);
     if (fp32) k_terms_smem<float><<<grid, NT, smem, stream>>>(table, 1, total, queue);
