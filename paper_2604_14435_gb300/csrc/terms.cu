@@ -115,62 +115,6 @@ __device__ __forceinline__ double2 ctil_of(const Inst& I, int l) {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-__global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, int* status,
-                                                unsigned long long* queue) {
-    pdl_trigger();
-    if (queue && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *queue = 0ull;  // the term kernel's work queue
-    const Inst I = insts[blockIdx.x];
-    const int t = threadIdx.x, part = blockIdx.y, parts = gridDim.y;
-    const long long N = 1LL << I.n;
-    if (part == 0) {
-        __shared__ double red[NT / 32];
-        double acc = 0.0;
-        for (long long j = t; j < N && I.b; j += NT) {
-            const double2 v = I.b[j];
-            acc += v.x * v.x + v.y * v.y;
-        }
-        if (!I.b && t == 0) acc = 1.0;  // local cost: b = |+>^n is implied and never read
-        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if ((t & 31) == 0) red[t >> 5] = acc;
-        for (int l = t; l < I.L; l += NT) {
-            const uint32_t x = I.xm[l], z = I.zm[l];
-            if (x >= N || z >= N) set_status(status, DEV_BAD_MASK);
-            const double2 c = I.coef[l];
-            if (!isfinite(c.x) || !isfinite(c.y)) set_status(status, DEV_NONFINITE_INPUT);
-            const double2 r = ctil_of(I, l);
-            I.ctil[l] = r;
-            if (I.cf) I.cf[l] = split_ff(r);
-        }
-        __syncthreads();
-        if (t == 0) {
-            double sum = 0.0;
-            for (int k = 0; k < NT / 32; ++k) sum += red[k];
-            *I.bn2 = sum;
-            if (!(sum > 0.0) || !isfinite(sum)) set_status(status, DEV_BAD_NORM);
-        }
-    }
-    for (int a = t + part * NT; a < I.P; a += NT * parts) {
-        const double al = I.alpha[a];
-        if (!isfinite(al)) set_status(status, DEV_NONFINITE_INPUT);
-        double s0, c0;
-        sincos(0.5 * al, &s0, &c0);
-        // Half angles of alpha +- pi/2 are alpha/2 +- pi/4: sin = (s0 +- c0) / sqrt 2,
-        // cos = (c0 -+ s0) / sqrt 2.
-        const double s1 = (s0 + c0) * M_SQRT1_2, c1 = (c0 - s0) * M_SQRT1_2;
-        const double s2 = (s0 - c0) * M_SQRT1_2, c2 = (c0 + s0) * M_SQRT1_2;
-        I.cs[a] = make_double2(c0, s0);
-        I.cs[I.P + a] = make_double2(c1, s1);
-        I.cs[2 * I.P + a] = make_double2(c2, s2);
-    }
-    const long long LL = (long long)I.L * I.L;
-    const long long per = (LL + parts - 1) / parts, e0 = part * per, e1 = min(LL, e0 + per);
-    for (long long e = e0 + t; e < e1; e += NT) {
-        const double2 a = ctil_of(I, int(e / I.L)), b = ctil_of(I, int(e % I.L));
-        const double2 wv = make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
-        I.w[e] = wv;
-        if (I.wf) I.wf[e] = split_ff(wv);
-    }
-}
 
 // ------------------------------------------------------------ term tiles
 template <typename R>
@@ -802,14 +746,12 @@ __device__ __forceinline__ float tc_bscale(double bn2) {
 // 128..131][8 values], rows Re b and Im b of the stage's first half (128, 129)
 // and of its second half (130, 131), scaled by tc_bscale.  Grid (instances,
 // parts) of 256 threads, after k_prepare (which forms ||b||^2).
-__global__ void __launch_bounds__(256) k_prep_bop(const Inst* __restrict__ insts) {
-    pdl_wait();
-    pdl_trigger();
-    const Inst I = insts[blockIdx.x];
-    if (!I.bop || !I.b) return;
+// The b rows of the tensor-core B operand for stages blk, blk + nblk, ...
+// (chunks of 8 amplitudes, FP16 hi / lo of b scaled by tc_bscale(||b||^2)).
+__device__ __forceinline__ void tc_fill_bop(const Inst& I, double bn2, int blk, int nblk) {
     const long long N = 1LL << I.n, chunks = tc_bop_stages(N) * (TC_BOP_STAGE / 16);
-    const float sb = tc_bscale(*I.bn2);
-    for (long long c = blockIdx.y * 256 + threadIdx.x; c < chunks; c += 256LL * gridDim.y) {
+    const float sb = tc_bscale(bn2);
+    for (long long c = (long long)blk * 256 + threadIdx.x; c < chunks; c += 256LL * nblk) {
         const long long stage = c >> 6;
         const int u = int(c & 63), which = u >> 5, ks4 = (u >> 3) & 3, hh = (u >> 2) & 1, row = u & 3;
         uint32_t w[4];
@@ -826,6 +768,103 @@ __global__ void __launch_bounds__(256) k_prep_bop(const Inst* __restrict__ insts
             w[e >> 1] = which ? ((a >> 16) | (b & 0xFFFF0000u)) : ((a & 0xFFFFu) | (b << 16));
         }
         reinterpret_cast<uint4*>(I.bop)[c] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+// States of up to this many amplitudes get their b rows from the prepare
+// kernel; larger ones from k_prep_bop.
+constexpr long long TC_BOP_FUSED_N = 4096;
+
+__global__ void __launch_bounds__(256) k_prep_bop(const Inst* __restrict__ insts) {
+    pdl_wait();
+    pdl_trigger();
+    const Inst I = insts[blockIdx.x];
+    if (!I.bop || !I.b) return;
+    tc_fill_bop(I, *I.bn2, blockIdx.y, gridDim.y);
+}
+
+// ||b||^2 of an instance (1 for the local cost, whose b = |+>^n is implied),
+// valid in thread 0.  One compiled copy serves every caller, so each CTA that
+// needs it gets the same bits.
+__device__ __noinline__ double b_norm2(const Inst& I, double* red) {
+    const int t = threadIdx.x;
+    const long long N = 1LL << I.n;
+    double acc = 0.0;
+    if (I.b) {
+#pragma unroll 4
+        for (long long j = t; j < N; j += NT) {
+            const double2 v = I.b[j];
+            acc += v.x * v.x + v.y * v.y;
+        }
+    } else if (t == 0) {
+        acc = 1.0;
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((t & 31) == 0) red[t >> 5] = acc;
+    __syncthreads();
+    double sum = 0.0;
+    if (t == 0)
+        for (int k = 0; k < NT / 32; ++k) sum += red[k];
+    return sum;
+}
+
+// Per instance: CTAs 0 .. prep_parts - 1 form ||b||^2 and c~ (part 0), the
+// half-angle tables (part 1, or 0 when alone) and the pair weights (all
+// parts); CTAs from prep_parts on, when launched, build the tensor-core b rows
+// (states of up to TC_BOP_FUSED_N amplitudes) from their own ||b||^2.
+__global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, int* status,
+                                                unsigned long long* queue, int prep_parts) {
+    pdl_trigger();
+    if (queue && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *queue = 0ull;  // the term kernel's work queue
+    const Inst I = insts[blockIdx.x];
+    const int t = threadIdx.x, part = blockIdx.y, parts = prep_parts;
+    const long long N = 1LL << I.n;
+    __shared__ double red[NT / 32];
+    if (part >= parts) {
+        if (!I.bop || !I.b || N > TC_BOP_FUSED_N) return;
+        __shared__ double s_bn2;
+        const double bn2 = b_norm2(I, red);
+        if (t == 0) s_bn2 = bn2;
+        __syncthreads();
+        tc_fill_bop(I, s_bn2, part - parts, int(gridDim.y) - parts);
+        return;
+    }
+    if (part == 0) {
+        const double sum = b_norm2(I, red);
+        for (int l = t; l < I.L; l += NT) {
+            const uint32_t x = I.xm[l], z = I.zm[l];
+            if (x >= N || z >= N) set_status(status, DEV_BAD_MASK);
+            const double2 c = I.coef[l];
+            if (!isfinite(c.x) || !isfinite(c.y)) set_status(status, DEV_NONFINITE_INPUT);
+            const double2 r = ctil_of(I, l);
+            I.ctil[l] = r;
+            if (I.cf) I.cf[l] = split_ff(r);
+        }
+        if (t == 0) {
+            *I.bn2 = sum;
+            if (!(sum > 0.0) || !isfinite(sum)) set_status(status, DEV_BAD_NORM);
+        }
+    }
+    if (part == (parts > 1 ? 1 : 0))
+        for (int a = t; a < I.P; a += NT) {
+            const double al = I.alpha[a];
+            if (!isfinite(al)) set_status(status, DEV_NONFINITE_INPUT);
+            double s0, c0;
+            sincos(0.5 * al, &s0, &c0);
+            // Half angles of alpha +- pi/2 are alpha/2 +- pi/4: sin = (s0 +- c0) / sqrt 2,
+            // cos = (c0 -+ s0) / sqrt 2.
+            const double s1 = (s0 + c0) * M_SQRT1_2, c1 = (c0 - s0) * M_SQRT1_2;
+            const double s2 = (s0 - c0) * M_SQRT1_2, c2 = (c0 + s0) * M_SQRT1_2;
+            I.cs[a] = make_double2(c0, s0);
+            I.cs[I.P + a] = make_double2(c1, s1);
+            I.cs[2 * I.P + a] = make_double2(c2, s2);
+        }
+    const long long LL = (long long)I.L * I.L;
+    const long long per = (LL + parts - 1) / parts, e0 = part * per, e1 = min(LL, e0 + per);
+    for (long long e = e0 + t; e < e1; e += NT) {
+        const double2 a = ctil_of(I, int(e / I.L)), b = ctil_of(I, int(e % I.L));
+        const double2 wv = make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+        I.w[e] = wv;
+        if (I.wf) I.wf[e] = split_ff(wv);
     }
 }
 
@@ -1880,7 +1919,8 @@ struct PassShape {
     int half;        // tensor-core kernel: shared bytes of one pipeline
     int copy_nmax;   // tensor-core kernel: states of 2^4 .. 2^copy_nmax amplitudes kept in four copies (0: none)
     int prep_parts;  // CTAs per instance of k_prepare (weights split ~256 per CTA)
-    int bop_parts;   // CTAs per instance of k_prep_bop
+    int bop_parts;   // CTAs per instance building the tensor-core b rows
+    int bop_fused;   // 1: those CTAs are part of k_prepare (every state has <= TC_BOP_FUSED_N amplitudes)
 };
 
 // Launch with programmatic stream serialization (the kernel starts with
@@ -1908,9 +1948,10 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
     // One profiling mark per kernel, so the launch counts are exact.  The
     // prepare kernel also resets the work queue.
     if (marks) prof_begin(ctx, 0);
-    k_prepare<<<dim3(ps.count, ps.prep_parts), NT, 0, st>>>(dtable, ctx->d_status, ctx->d_queue);
+    k_prepare<<<dim3(ps.count, ps.prep_parts + (ps.tc && ps.bop_fused ? ps.bop_parts : 0)), NT, 0, st>>>(
+        dtable, ctx->d_status, ctx->d_queue, ps.prep_parts);
     if (marks) prof_end(ctx);
-    if (ps.tc) {
+    if (ps.tc && !ps.bop_fused) {
         if (marks) prof_begin(ctx, 0);
         DVQLS_CUDA_TRY(ctx, launch_pdl(k_prep_bop, dim3(ps.count, ps.bop_parts), dim3(256), 0, st, dtable));
         if (marks) prof_end(ctx);
@@ -2272,6 +2313,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         ps.copy_nmax = copy_nmax;
         ps.prep_parts = (int)std::min<long long>(16, std::max<long long>(1, LLmax / NT));
         ps.bop_parts = (int)std::min<long long>(64, std::max<long long>(1, tc_bop_stages(Nmax) * (TC_BOP_STAGE / 16) / 256));
+        ps.bop_fused = Nmax <= TC_BOP_FUSED_N;
     };
     auto upload = [&]() -> int {
         const char* tb = reinterpret_cast<const char*>(table.data());
@@ -2558,7 +2600,7 @@ extern "C" int dvqls_cost_grad_noalloc(void* stream_arg, const dvqls_ansatz* ans
         return DVQLS_ERR_CUDA;
     }
     k_noalloc_store<<<1, 1, 0, stream>>>(I, table);
-    k_prepare<<<1, NT, 0, stream>>>(table, status, nullptr);
+    k_prepare<<<1, NT, 0, stream>>>(table, status, nullptr, 1);
     const long long total = I.items;
     const int grid = (int)std::min<long long>(total, slots);
     if (fp32) k_terms_smem<float><<<grid, NT, smem, stream>>>(table, 1, total, queue);
