@@ -144,9 +144,9 @@ int finish_out(dvqls_ctx* ctx, const std::vector<PendingOut>& pending) {
 }
 
 int sync_and_check(dvqls_ctx* ctx) {
-    int st = 0;
-    DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     DVQLS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    const int st = *ctx->h_status;
     if (st == DEV_OK) return DVQLS_OK;
     DVQLS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
     switch (st) {
@@ -256,6 +256,7 @@ extern "C" int dvqls_create(dvqls_ctx** out, int device, void* stream) {
             break;
         }
         if (cudaMalloc(&ctx->d_status, 256) != cudaSuccess) { rc = DVQLS_ERR_ALLOC; break; }
+        if (cudaMallocHost(&ctx->h_status, 64) != cudaSuccess) { rc = DVQLS_ERR_ALLOC; break; }
         ctx->d_queue = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ctx->d_status) + 64);
         if (cudaMemsetAsync(ctx->d_status, 0, 256, ctx->stream) != cudaSuccess) { rc = DVQLS_ERR_CUDA; break; }
         if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) { rc = DVQLS_ERR_CUDA; break; }
@@ -278,6 +279,7 @@ extern "C" void dvqls_destroy(dvqls_ctx* ctx) {
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->pin) cudaFreeHost(ctx->pin);
     if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->pin_event) cudaEventDestroy(ctx->pin_event);
     for (auto& m : ctx->marks) {
         cudaEventDestroy(m.a);

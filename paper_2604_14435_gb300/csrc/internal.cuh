@@ -48,6 +48,9 @@ struct dvqls_ctx {
     // workspace can grow without invalidating it).
     int* d_status = nullptr;
     unsigned long long* d_queue = nullptr;
+    // Pinned word the status is read into (an asynchronous copy, then one
+    // stream synchronisation).
+    int* h_status = nullptr;
 
     // Pinned staging is reused by every call: pin_event marks the last
     // host-to-device copy out of it; it is waited on before the next write.
