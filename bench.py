@@ -54,7 +54,7 @@ FP32_PEAK = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
 FP16_PER_BF16 = 1.0  # kind::f16 runs FP16 and BF16 operands at the same nominal dense rate (2.25 PFLOP/s)
 # DRAM bytes (read + write) per launch of the tensor-core term kernel on this workload, from the ncu
 # capture summarised in profiles/k_terms_tc_n10_L64_batch32.md; None once the kernel changes.
-TC_TRAFFIC_BYTES = 1672192
+TC_TRAFFIC_BYTES = None
 
 
 def measured_peaks():

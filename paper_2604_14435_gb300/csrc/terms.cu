@@ -1226,18 +1226,22 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 }
                 unsigned char* zhi = stage0 + st * TC_STAGE_BYTES;
                 unsigned char* zlo = zhi + TC_OPND_BYTES;
-                if (tt < TC_BOP_STAGE / 16) {  // the b rows of this stage (j0 is a multiple of TCK)
-                    const uint4 v =
-                        reinterpret_cast<const uint4*>(I.bop)[(long long)(j0 / TCK) * (TC_BOP_STAGE / 16) + tt];
+                const bool brow = tt < TC_BOP_STAGE / 16;
+                if (brow) {  // the b rows of this stage (j0 is a multiple of TCK), copied while the terms are built
+                    const uint4* src = reinterpret_cast<const uint4*>(I.bop) + (long long)(j0 / TCK) * (TC_BOP_STAGE / 16) + tt;
                     const int which = tt >> 5, ks4 = (tt >> 3) & 3, hh = (tt >> 2) & 1, row = tt & 3;
-                    *reinterpret_cast<uint4*>((which ? zlo : zhi) + ((ks4 * (TC_NB / 8) + 16) * 2 + hh) * 128 +
-                                              row * 16) = v;
+                    const uint32_t dst =
+                        su32((which ? zlo : zhi) + ((ks4 * (TC_NB / 8) + 16) * 2 + hh) * 128 + row * 16);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n\tcp.async.commit_group;" ::"r"(dst),
+                                 "l"(__cvta_generic_to_global(src))
+                                 : "memory");
                 }
                 if (I.states)
                     tc_build_stage<true>(nullptr, psi_g, N, j0, kend, l < L, xl, zl, sgn, sub, l, zhi, zlo, false);
                 else
                     tc_build_stage<false>(psi_hl, nullptr, N, j0, kend, l < L, xl, zl, sgn, sub, l, zhi, zlo,
                                           copies);
+                if (brow) asm volatile("cp.async.wait_all;" ::: "memory");
                 if (tt == 0) {
                     srec[h][st][0] = su32(zhi);
                     srec[h][st][1] = (c % TC_FLUSH == 0) ? 1u : 0u;
