@@ -158,7 +158,7 @@ def lcu_matrix(coef, xs, zs, n):
 
 
 def classical_solution(M, b):
-    """xhat = M^{-1} b normalised (the direct solve the fidelity is judged by)."""
+    """xhat = M^{-1} b normalised (the direct solve the fidelity is measured against)."""
     x = np.linalg.solve(M, np.asarray(b, dtype=np.complex128))
     return x / np.linalg.norm(x)
 

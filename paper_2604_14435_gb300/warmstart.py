@@ -1,6 +1,6 @@
 """Learned warm start for D-VQLS (replaces the random initialisation of
 Algorithm 1, Step 3 with a prediction; random / fixed initialisation stays
-the fallback and the exact cost and fidelity judge the result).
+the fallback, and the exact cost and the fidelity measure the result).
 
 Every numeric step runs in the CUDA library: decomposition
 (dvqls_pauli_decompose_banded), classical solve (dvqls_lcu_solve), optimizer

@@ -1,4 +1,4 @@
-"""Fidelity (Sec. 3.1), the classical solve it is judged against, and the
+"""Fidelity (Sec. 3.1), the classical solve it is measured against, and the
 Adam optimizer loop (Algorithm 1) vs the oracle."""
 import numpy as np
 import pytest
