@@ -427,26 +427,35 @@ def main():
     if headline:
         lcosts, lgrads = torch.zeros_like(costs), torch.zeros_like(grads)  # the global results stay intact
 
-        def local_rate(with_grad, steps):
+        def local_rate(with_grad, steps, prec=D.DVQLS_FP32):
             g = lgrads if with_grad else None
             for _ in range(3):
-                D.dvqls_local_cost_grad_batched(ctx, dev_arr, D.DVQLS_FP32, lcosts, g)
+                D.dvqls_local_cost_grad_batched(ctx, dev_arr, prec, lcosts, g)
             D.dvqls_sync(ctx)
             torch.cuda.synchronize()
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
             for k in range(steps):
                 flush.fill_(k & 0xFF)
                 ev[k][0].record(stream)
-                D.dvqls_local_cost_grad_batched(ctx, dev_arr, D.DVQLS_FP32, lcosts, g)
+                D.dvqls_local_cost_grad_batched(ctx, dev_arr, prec, lcosts, g)
                 ev[k][1].record(stream)
             D.dvqls_sync(ctx)
             torch.cuda.synchronize()
             return count * steps / (sum(a.elapsed_time(b) for a, b in ev) / 1000.0)
         r_cost = local_rate(False, max(20, args.steps))
         r_grad = local_rate(True, max(5, args.steps // 10))
+        ref_costs = lcosts.clone()
+        w_cost = local_rate(False, max(20, args.steps), D.DVQLS_FP32_WHT)
+        w_grad = local_rate(True, max(5, args.steps // 10), D.DVQLS_FP32_WHT)
         circuits = 2 * (N_QUBITS + 1) * L_TERMS ** 2
         local = {"cost_evals_per_s": r_cost, "cost_grad_evals_per_s": r_grad,
                  "circuits_per_cost_eval": circuits, "circuit_equivalents_per_s": r_cost * circuits,
+                 "precision": "fp32",
+                 "wht_reformulation": {"precision": "fp32_wht", "cost_evals_per_s": w_cost,
+                                       "cost_grad_evals_per_s": w_grad,
+                                       "max_abs_cost_diff_vs_fp32": float((lcosts - ref_costs).abs().max()),
+                                       "note": "the same C_L by Walsh-Hadamard classes: flavour j of a pair class x "
+                                               "reads the transform at x ^ e_j"},
                  "note": "C_L of Eq. 2/4 for b = |+>^10: the paper's 90,112-circuit optimizer-iteration workload; "
                          "the paper reports 17.15 s per iteration on 4 A100s (context only, other hardware)"}
 

@@ -1445,7 +1445,7 @@ __global__ void __launch_bounds__(WHT_CT) k_wht_classes(const Inst* __restrict__
     const int L = I.L, t = threadIdx.x, np = L * (L + 1) / 2;
     const long long N = 1LL << I.n;
     bool im = false;
-    for (long long j = t; j < N; j += WHT_CT) {
+    for (long long j = t; I.b && j < N; j += WHT_CT) {  // the local cost has no b here (|+>^n is implied)
         const double2 v = I.b[j];
         I.bf[j] = make_float2((float)v.x, (float)v.y);
         im |= (float)v.y != 0.f;
@@ -1649,6 +1649,73 @@ __device__ __forceinline__ void wht_warp_1024(float (&v)[32], int lane, float* r
 }
 
 // One item: every pair class, then every term class, of one shifted state.
+// The transform of g_x(i) = psi[i] psi[i ^ x] into the warp's row (at
+// i + (i >> 5) for 2^10 values, else at i).
+template <int A, int LOGA>
+__device__ __forceinline__ void wht_row(const float* psi, uint32_t x, float* wb, int N, int lane) {
+    const int lm = N < 32 ? N - 1 : 31, nl = N < 32 ? __ffs(N) - 1 : 5;
+    float v[A];
+#pragma unroll
+    for (int r = 0; r < A; ++r) {
+        const int i = (r << 5) | (lane & lm);
+        v[r] = psi[i] * psi[(i ^ int(x)) & (N - 1)];
+    }
+    if constexpr (A == 32) {
+        wht_warp_1024(*reinterpret_cast<float(*)[32]>(v), lane, wb);
+    } else {
+        wht_warp<A, LOGA>(v, lane, nl);
+        if (lane < N || N >= 32) {
+#pragma unroll
+            for (int r = 0; r < A; ++r) wb[(r << 5) | lane] = v[r];
+        }
+    }
+    __syncwarp();
+}
+
+// Local cost (Eq. 2/4, b = |+>^n): with X_j inserted between the two terms,
+//   gamma~^j_lm = sum_i phi_l[i] phi_m[i ^ e_j] = (-1)^popc(z_l & X) W_X(z_l ^ z_m),
+//   X = x_l ^ x_m ^ e_j,
+// so the pairs of the class of x serve flavour j through the transform at
+// x ^ e_j, with the sign of the class's weight flipped where bit j of z_l is
+// set.  Jobs are (flavour, class): flavour 0 forms D (the global terms),
+// flavours 1..n form E.
+template <int A, int LOGA>
+__device__ void wht_item_local(const Inst& I, const float* psi, float* wb, const uint32_t* szl, float& S, float& E,
+                               float& SL, float& EL, int lane) {
+    constexpr bool PAD = A == 32;
+    const int n = I.n, N = 1 << n, w = threadIdx.x >> 5;
+    const unsigned char* tb = reinterpret_cast<const unsigned char*>(I.wht);
+    const int ncls = reinterpret_cast<const int*>(tb)[0];
+    const uint32_t* cx = reinterpret_cast<const uint32_t*>(tb + WHT_OFF_CX);
+    const int* co = reinterpret_cast<const int*>(tb + WHT_OFF_CO);
+    const uint16_t* pr = reinterpret_cast<const uint16_t*>(tb + WHT_OFF_PR);
+    const uint16_t* ez = reinterpret_cast<const uint16_t*>(tb + WHT_OFF_EZ);
+    const float2* ek = reinterpret_cast<const float2*>(tb + WHT_OFF_EK);
+    const int jobs = ncls * (n + 1);
+#pragma unroll 1
+    for (int job = w; job < jobs; job += WHT_NT / 32) {
+        const int f = job / ncls, c = job - f * ncls;
+        const uint32_t x = cx[c] ^ (f ? 1u << (f - 1) : 0u);
+        wht_row<A, LOGA>(psi, x, wb, N, lane);
+        const int e0 = co[c], e1 = co[c + 1];
+        if (f == 0) {
+            for (int e = e0 + lane; e < e1; e += 32) {
+                const uint32_t z = ez[e];
+                const float2 k = ek[e];
+                ff_mac(S, E, k.x, k.y, wb[PAD ? z + (z >> 5) : z]);
+            }
+        } else {
+            for (int e = e0 + lane; e < e1; e += 32) {
+                const uint32_t z = ez[e];
+                float2 k = ek[e];
+                if ((szl[pr[e] & 0xFF] >> (f - 1)) & 1u) k = make_float2(-k.x, -k.y);
+                ff_mac(SL, EL, k.x, k.y, wb[PAD ? z + (z >> 5) : z]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 template <int A, int LOGA>
 __device__ void wht_item(const Inst& I, int s, const float* psi, const float2* sb, float* wb, float* dre, float* dim,
                          const uint32_t* szl, float& S, float& E, int lane) {
@@ -1771,9 +1838,31 @@ __global__ void __launch_bounds__(WHT_NT, 4) k_terms_wht(const Inst* __restrict_
             szl[t] = t < L ? I.zm[t] : 0u;
             dre[t] = dim[t] = 0.f;
         }
-        for (int j = t; j < (1 << I.n); j += WHT_NT) sb[j] = I.bf[j];
+        for (int j = t; !I.local && j < (1 << I.n); j += WHT_NT) sb[j] = I.bf[j];
         build_state_regs<false>(psi, scratch, scs, I.n, I.d, I.P, I.cs, s, t, 0, 1.f);  // ends with a barrier
         float S = 0.f, E = 0.f;
+        if (I.local) {
+            float SL = 0.f, EL = 0.f;
+            switch (I.n) {
+                case 10: wht_item_local<32, 5>(I, psi, wb, szl, S, E, SL, EL, lane); break;
+                case 9: wht_item_local<16, 4>(I, psi, wb, szl, S, E, SL, EL, lane); break;
+                case 8: wht_item_local<8, 3>(I, psi, wb, szl, S, E, SL, EL, lane); break;
+                case 7: wht_item_local<4, 2>(I, psi, wb, szl, S, E, SL, EL, lane); break;
+                case 6: wht_item_local<2, 1>(I, psi, wb, szl, S, E, SL, EL, lane); break;
+                default: wht_item_local<1, 0>(I, psi, wb, szl, S, E, SL, EL, lane); break;  // n <= 5
+            }
+            // Slot 0 of a shift holds D, slot 1 E (summed over the flavours), the rest zero.
+            const double D = block_sum_ff(S, E, red);
+            const double El = block_sum_ff(SL, EL, red);
+            if (t == 0) {  // the sums are valid in thread 0
+                I.Dpart[(long long)s * I.F] = make_double2(D, 0.0);
+                I.Dpart[(long long)s * I.F + 1] = make_double2(El, 0.0);
+            } else if (t >= 2 && t < I.F) {
+                I.Dpart[(long long)s * I.F + t] = make_double2(0.0, 0.0);
+            }
+            __syncthreads();
+            continue;
+        }
         switch (I.n) {
             case 10: wht_item<32, 5>(I, s, psi, sb, wb, dre, dim, szl, S, E, lane); break;
             case 9: wht_item<16, 4>(I, s, psi, sb, wb, dre, dim, szl, S, E, lane); break;
@@ -2094,7 +2183,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     // 64-term tile and every state n <= 10 qubits; tensor-core tiles when
     // every LCU fits one tile (asked for directly, or as the fallback of the
     // classes); anything else runs the FP32 CUDA-core tiles.
-    bool wht = precision == DVQLS_FP32_WHT && !local;
+    bool wht = precision == DVQLS_FP32_WHT;
     for (const auto& h : hi) wht = wht && h.T == 1 && h.n <= WHT_MAXN;
     bool tc = !wht && (precision == DVQLS_FP32_TC || precision == DVQLS_FP32_WHT) && !local;
     for (const auto& h : hi) tc = tc && h.T == 1;
@@ -2300,7 +2389,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
             const int i = ord[oi];
             Inst I = rec[i];
             I.ks = kk[i];
-            I.items = I.S * I.F * I.T * I.T * I.ks;
+            I.items = wht ? I.S : I.S * I.F * I.T * I.T * I.ks;  // a Walsh-Hadamard item covers every flavour
             I.item_base = base;
             base += I.items;
             table[oi] = I;

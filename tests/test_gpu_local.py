@@ -10,7 +10,8 @@ from paper_2604_14435_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: (1e-12, 1e-12), 1: (1e-6, 1e-5)}
+# 3: the Walsh-Hadamard classes (served for L <= 64, n <= 10; FP32 otherwise), held to the FP32 bounds
+TOL = {0: (1e-12, 1e-12), 1: (1e-6, 1e-5), 3: (1e-6, 1e-5)}
 
 
 def cv(a):
@@ -29,7 +30,7 @@ def ok(got, ref, tol):
     return np.all(np.abs(np.asarray(got) - np.asarray(ref)) <= tol * np.maximum(1.0, np.abs(ref)))
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 3])
 @pytest.mark.parametrize("n,d,L", [(1, 1, 2), (2, 1, 5), (3, 2, 8), (5, 2, 33), (6, 1, 70), (8, 1, 20)])
 def test_local_cost_matches_oracle(dv, ctx, prec, n, d, L):
     rng = np.random.default_rng(900 + n + L)
@@ -46,7 +47,7 @@ def test_local_cost_matches_oracle(dv, ctx, prec, n, d, L):
     assert ok(c_only, ref["cost"], tc)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 3])
 def test_local_cost_throughput_system(dv, ctx, prec):
     """n = 10 Toeplitz, top-64: the paper's 90,112-circuit evaluation, with
     sampled gamma overlaps checked against their Hadamard-test circuits."""
@@ -89,3 +90,33 @@ def test_local_cost_batched_and_hbm(dv, ctx, prec):
         assert ok(costs[k].item(), ref["cost"], tc)
         assert ok(grads[off:off + n * (d + 1)].cpu().numpy(), ref["grad"], tg)
         off += n * (d + 1)
+
+
+def test_local_cost_batched_wht(dv, ctx):
+    """A batch the Walsh-Hadamard classes serve (every n <= 10, L <= 64), twice:
+    the second call reuses the class tables."""
+    rng = np.random.default_rng(31)
+    probs = []
+    for n, d, L in [(4, 1, 6), (7, 2, 9), (10, 1, 64), (1, 2, 2)]:
+        N = 1 << n
+        probs.append((n, d, rng.normal(size=L) + 1j * rng.normal(size=L), rng.integers(0, N, L).astype(np.uint32),
+                      rng.integers(0, N, L).astype(np.uint32), wl.random_angles(n * (d + 1), 40 + n)))
+    keep, items = [], []
+    for n, d, coef, xs, zs, alpha in probs:
+        t = (cv(coef), xs, zs, np.ascontiguousarray(alpha))
+        keep.append(t)
+        items.append((dv.make_ansatz(n, d), dv.make_lcu(len(xs), t[0], t[1], t[2]), t[3], None))
+    arr = dv.make_instances(items)
+    P = sum(p[0] * (p[1] + 1) for p in probs)
+    tc, tg = TOL[3]
+    for _ in range(2):
+        costs = torch.zeros(len(probs), device="cuda", dtype=torch.float64)
+        grads = torch.zeros(P, device="cuda", dtype=torch.float64)
+        dv.dvqls_local_cost_grad_batched(ctx, arr, 3, costs, grads)
+        dv.dvqls_sync(ctx)
+        off = 0
+        for k, (n, d, coef, xs, zs, alpha) in enumerate(probs):
+            ref = oterms.local_cost_grad(n, d, alpha, coef, xs, zs)
+            assert ok(costs[k].item(), ref["cost"], tc)
+            assert ok(grads[off:off + n * (d + 1)].cpu().numpy(), ref["grad"], tg)
+            off += n * (d + 1)
