@@ -71,7 +71,7 @@ typedef enum {
  *                  by 2^12, split into FP16 hi + lo; three products hi hi +
  *                  hi lo + lo hi, FP32 accumulation with periodic
  *                  round-to-nearest folding), which keeps FP32-level
- *                  accuracy (measured |beta - oracle| <= 2e-6 up to n = 14;
+ *                  accuracy (measured |beta - oracle| <= 3.4e-6 up to n = 14;
  *                  the FP32 bounds of the parity tests hold).  Weighted sums
  *                  in float-float (~2^-44 relative), combined in FP64.
  *                  Served for the global cost when every instance has
@@ -83,8 +83,11 @@ typedef enum {
  *                  Walsh-Hadamard transform of psi[i] psi[i ^ x] gives every
  *                  beta of a group (likewise delta by x_l); cost for
  *                  structured LCUs is (groups) x N log N instead of L^2 N.
- *                  Served for the global cost when every instance has
- *                  L <= 64 and n <= 10; other calls run as DVQLS_FP32_TC. */
+ *                  The local cost's flavour j reads the transform at
+ *                  x ^ e_j (X_j between the two terms).  Served for the
+ *                  global and the local cost when every instance has
+ *                  L <= 64 and n <= 10; other global-cost calls run as
+ *                  DVQLS_FP32_TC, other local-cost calls as DVQLS_FP32. */
 typedef enum { DVQLS_FP64 = 0, DVQLS_FP32 = 1, DVQLS_FP32_TC = 2, DVQLS_FP32_WHT = 3 } dvqls_precision;
 
 typedef enum { DVQLS_ANSATZ_RY_CZRING = 0 } dvqls_ansatz_kind;
