@@ -55,7 +55,7 @@ FP32_PEAK = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
 FP16_PER_BF16 = 1.0  # kind::f16 runs FP16 and BF16 operands at the same nominal dense rate (2.25 PFLOP/s)
 # DRAM bytes (read + write) per launch of the tensor-core term kernel on this workload, from the ncu
 # capture summarised in profiles/k_terms_tc_n10_L64_batch32.md; None once the kernel changes.
-TC_TRAFFIC_BYTES = None
+TC_TRAFFIC_BYTES = 1671680
 
 
 def measured_peaks():
@@ -94,10 +94,18 @@ class Clocks:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # The timed region starts once the sampler has written its first line.
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and self.proc.poll() is None:
+            self.f.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -278,7 +286,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="toeplitz10", choices=["toeplitz10", "uneven", "hele_shaw"])
