@@ -286,7 +286,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 2000 for this implementation, 200 for the reference arm)")
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="toeplitz10", choices=["toeplitz10", "uneven", "hele_shaw"])
@@ -295,6 +296,8 @@ def main():
                     help="term kernel: tcgen05 tensor cores with an FP32-accurate 3xFP16 split (served for "
                          "L <= 64; default), or FP32 on the CUDA cores")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 200 if args.impl == "reference" else 2000
     if args.impl == "reference":
         return run_reference(args)
     assert args.warmup >= 3, "at least 3 warm-up steps"
