@@ -657,8 +657,10 @@ int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, 
 // relative, dropped): three tcgen05.mma kind::f16 per k-step with FP32
 // accumulation in tensor memory.  FP16 carries the 11-bit significand of TF32
 // at twice its tensor rate and half its operand bytes.  The state is split
-// once per item (packed hi | lo << 16 per amplitude), so a term value costs a
-// permuted 32-bit load, a sign flip of both halves and half a byte permute.
+// once per item (packed hi | lo << 16 per amplitude) and kept in four copies
+// (copy t holds psi[k ^ t]), so a term's 16 amplitudes of a block are four
+// aligned 16-byte loads; a term value then costs a quarter load, half a byte
+// permute and one three-input XOR (the sign) per packed pair.
 //
 // A kernel that allocates tensor memory runs one CTA per SM, so a CTA holds
 // two independent pipelines of 8 warps.  Each takes items from the queue with
