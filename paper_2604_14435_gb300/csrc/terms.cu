@@ -230,6 +230,17 @@ __device__ __forceinline__ void load4r<double>(const double* p, double (&v)[4]) 
     v[2] = b.x;
     v[3] = b.y;
 }
+template <typename R>
+__device__ __forceinline__ void store4r(R* p, const R (&v)[4]);
+template <>
+__device__ __forceinline__ void store4r<float>(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void store4r<double>(double* p, const double (&v)[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
 
 // The Ry + CZ-ring state is real, so with the phase i^popc(x & z) in c~_l
 // every phi_l[j] = (-1)^popc(z_l & (j ^ x_l)) psi[j ^ x_l] is real and the
@@ -318,32 +329,42 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
     const int lcount = min(TT, L - tl * TT), mcount = min(TT, L - tm * TT);
 
     for (int j0 = kbeg; j0 < kend; j0 += JC) {
-        // phi chunk rows jj = 0..JC-1: a warp takes 32 consecutive rows of one
-        // term, so its gather reads one aligned 32-amplitude block of psi
-        // (permuted by the low bits of x_l): no bank conflicts.  Rows are
-        // stored with the 4-term groups XOR-swizzled by the row index.
-        for (int e = t; e < JC * TT; e += NT) {
-            const int jj = e & (JC - 1), l = e / JC, j = j0 + jj;
-            const int at = jj * TT + (l ^ ((jj & 15) << 2));
-            R v = (R)0;
-            if (j < kend && l < lcount) {
-                const int src = (j ^ int(sxl[l])) & (N - 1);  // masks >= 2^n are reported, never followed
-                v = psi_g ? psi_g[src] : psi_smem[src];
-                if (__popc(szl[l] & uint32_t(src)) & 1) v = -v;
+        // phi chunk rows jj = 0..JC-1, stored with the 4-term groups
+        // XOR-swizzled by the row index (group q of row jj at 4 (q ^ (jj & 15))).
+        // A thread fills one group of one row; a warp takes 32 consecutive
+        // rows of one group, so each of its four gathers reads one aligned
+        // 32-amplitude block of psi (permuted by the low bits of the term's
+        // x), and its 16-byte stores fall in distinct bank groups.
+        for (int e = t; e < JC * (TT / 4); e += NT) {
+            const int jj = e & (JC - 1), q = e / JC, j = j0 + jj;
+            R v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int l = 4 * q + k;
+                v[k] = (R)0;
+                if (j < kend && l < lcount) {
+                    const int src = (j ^ int(sxl[l])) & (N - 1);  // masks >= 2^n are reported, never followed
+                    v[k] = psi_g ? psi_g[src] : psi_smem[src];
+                    if (__popc(szl[l] & uint32_t(src)) & 1) v[k] = -v[k];
+                }
             }
-            Phl[at] = v;
+            store4r<R>(Phl + jj * TT + ((4 * q) ^ ((jj & 15) << 2)), v);
         }
         if (!same) {
-            for (int e = t; e < JC * mcols; e += NT) {
-                const int jj = e & (JC - 1), m = mofs + e / JC, j = j0 + jj;
-                const int at = jj * TT + (m ^ ((jj & 15) << 2));
-                R v = (R)0;
-                if (j < kend && m < mcount) {
-                    const int src = (j ^ int(sxm[m])) & (N - 1);
-                    v = psi_g ? psi_g[src] : psi_smem[src];
-                    if (__popc(szm[m] & uint32_t(src)) & 1) v = -v;
+            for (int e = t; e < JC * (mcols / 4); e += NT) {
+                const int jj = e & (JC - 1), q = mofs / 4 + e / JC, j = j0 + jj;
+                R v[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int m = 4 * q + k;
+                    v[k] = (R)0;
+                    if (j < kend && m < mcount) {
+                        const int src = (j ^ int(sxm[m])) & (N - 1);
+                        v[k] = psi_g ? psi_g[src] : psi_smem[src];
+                        if (__popc(szm[m] & uint32_t(src)) & 1) v[k] = -v[k];
+                    }
                 }
-                Phm[at] = v;
+                store4r<R>(Phm + jj * TT + ((4 * q) ^ ((jj & 15) << 2)), v);
             }
         }
         if (want_delta && t < JC) {
