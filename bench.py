@@ -551,6 +551,19 @@ def main():
                      "phase_launches_per_step": {k: v[0] / args.steps for k, v in phases.items()},
                      "profiled_pass_ms_per_step": prof_ms / args.steps})
         launches_per_step = sum(phases[k][0] for k in ("prepare", "terms", "combine", "hbm_states")) / args.steps
+        hbm = None
+        n_h, ms_h = phases["hbm_states"]
+        if n_h > 0:  # shifted states of n > 12 built in HBM: an HBM-bound phase of its own
+            # per real FP32 amplitude: the first pass writes 4 B; each layer reads and writes the
+            # state twice (low-qubit pass, high-qubit pass): 16 B
+            hbm_bytes = sum((2 * n * (d + 1) + 1) * (1 << n) * 4 * (1 + 4 * d) for n, d, L in shapes if n > 12)
+            peaks, peak_src = measured_peaks()
+            gbs = hbm_bytes / (ms_h / args.steps / 1000.0) / 1e9
+            hbm = {"bound": "hbm", "kernels": "k_hbm_init, k_hbm_lo, k_hbm_hi", "achieved": gbs,
+                   "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "frac_note": peak_src,
+                   "bytes_per_step": hbm_bytes, "ms_per_step": ms_h / args.steps,
+                   "achieved_note": "algorithmic bytes: 4 B written per amplitude by the product-state pass, "
+                                    "16 B read+written per amplitude per ansatz layer"}
         metric = METRIC if headline else "cost+grad evals/sec (%s workload)" % args.workload
         line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
@@ -559,6 +572,7 @@ def main():
                 "config": workload_config(args.workload, ws, shapes),
                 "terms_per_s": ws * terms * args.steps / (dev_ms / 1000.0),
                 "roofline": roof,
+                "hbm_states": hbm,
                 "gpu_launches": int(launches_per_step * args.steps),
                 "clocks": clk}
         if headline:
