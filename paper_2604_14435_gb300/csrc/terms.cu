@@ -592,9 +592,17 @@ __global__ void __launch_bounds__(256) k_hbm_lo(const Inst* __restrict__ insts, 
     const size_t N = size_t(1) << n;
     if (threadIdx.x < LOQ) shift_angle<R>(I, s, layer * n + threadIdx.x, cq[threadIdx.x], sq[threadIdx.x]);
     R* st = reinterpret_cast<R*>(I.states) + s * N + base;
-    for (int e = threadIdx.x; e < LOC; e += blockDim.x) {
-        const R v = st[e];
-        w[e] = czring_parity(base + e, n) ? -v : v;
+    constexpr int VE = 16 / sizeof(R);  // amplitudes per 16-byte vector: all of a thread's loads in flight
+#pragma unroll
+    for (int e4 = threadIdx.x; e4 < LOC / VE; e4 += 256) {
+        const uint4 u = reinterpret_cast<const uint4*>(st)[e4];
+        R v[VE];
+        memcpy(v, &u, 16);
+#pragma unroll
+        for (int k = 0; k < VE; ++k) {
+            const int e = e4 * VE + k;
+            w[e] = czring_parity(base + e, n) ? -v[k] : v[k];
+        }
     }
     __syncthreads();
     for (int q = 0; q < LOQ; ++q) {
@@ -607,7 +615,9 @@ __global__ void __launch_bounds__(256) k_hbm_lo(const Inst* __restrict__ insts, 
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < LOC; e += blockDim.x) st[e] = w[e];
+#pragma unroll
+    for (int e4 = threadIdx.x; e4 < LOC / VE; e4 += 256)
+        reinterpret_cast<uint4*>(st)[e4] = reinterpret_cast<const uint4*>(w)[e4];
 }
 
 template <typename R>
@@ -621,7 +631,12 @@ __global__ void __launch_bounds__(256) k_hbm_hi(const Inst* __restrict__ insts, 
     if (threadIdx.x < n - LOQ)
         shift_angle<R>(I, s, layer * n + LOQ + threadIdx.x, cq[threadIdx.x], sq[threadIdx.x]);
     R* st = reinterpret_cast<R*>(I.states) + s * N;
-    for (int e = threadIdx.x; e < H * HC; e += blockDim.x) w[e] = st[((size_t)(e / HC) << LOQ) + lo0 + e % HC];
+    constexpr int VE = 16 / sizeof(R);  // 16-byte vectors of a row's HC columns
+#pragma unroll 8
+    for (int e4 = threadIdx.x; e4 < H * HC / VE; e4 += 256) {
+        const int e = e4 * VE;
+        reinterpret_cast<uint4*>(w)[e4] = *reinterpret_cast<const uint4*>(st + ((size_t)(e / HC) << LOQ) + lo0 + e % HC);
+    }
     __syncthreads();
     for (int q = 0; q < n - LOQ; ++q) {
         const R c = cq[q], sn = sq[q];
@@ -634,7 +649,11 @@ __global__ void __launch_bounds__(256) k_hbm_hi(const Inst* __restrict__ insts, 
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < H * HC; e += blockDim.x) st[((size_t)(e / HC) << LOQ) + lo0 + e % HC] = w[e];
+#pragma unroll 8
+    for (int e4 = threadIdx.x; e4 < H * HC / VE; e4 += 256) {
+        const int e = e4 * VE;
+        *reinterpret_cast<uint4*>(st + ((size_t)(e / HC) << LOQ) + lo0 + e % HC) = reinterpret_cast<const uint4*>(w)[e4];
+    }
 }
 
 template <typename R>
