@@ -620,6 +620,63 @@ __global__ void __launch_bounds__(256) k_hbm_lo(const Inst* __restrict__ insts, 
         reinterpret_cast<uint4*>(st)[e4] = reinterpret_cast<const uint4*>(w)[e4];
 }
 
+// The same low-qubit pass for FP32 states with the chunk in registers (16
+// amplitudes per thread, as in the on-chip state builder): qubits 0..4 on
+// lane bits (shuffles) and 8..11 on register bits (in place); qubits 5..7 sit
+// on warp bits and are rotated after one padded, conflict-free transpose that
+// puts them on lanes.  A second transpose restores the coalesced order for the
+// store.  Three barriers per chunk instead of one per qubit.
+__global__ void __launch_bounds__(256) k_hbm_lo_regs(const Inst* __restrict__ insts, int idx, int layer) {
+    __shared__ float scr[LOC + LOC / 32];
+    __shared__ float cq[LOQ], sq[LOQ];
+    const Inst& I = insts[idx];
+    const int s = blockIdx.y, n = I.n, base = blockIdx.x << LOQ, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const size_t N = size_t(1) << n;
+    if (t < LOQ) shift_angle<float>(I, s, layer * n + t, cq[t], sq[t]);
+    float* st = reinterpret_cast<float*>(I.states) + s * N + base;
+    float v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = st[st_index(0, r, w, lane)];  // a warp reads 128 contiguous bytes per r
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+        if (czring_parity(base + st_index(0, r, w, lane), n)) v[r] = -v[r];
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {  // qubits 0..4: lane bits
+        const float c = cq[b], sn = sq[b];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = ry_lane(v[r], lane, b, c, sn);
+    }
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb) {  // qubits 8..11: register bits
+        const float c = cq[8 + kb], sn = sq[8 + kb];
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+            if (!((r >> kb) & 1)) {
+                const float a0 = v[r], a1 = v[r | (1 << kb)];
+                v[r] = c * a0 - sn * a1;
+                v[r | (1 << kb)] = sn * a0 + c * a1;
+            }
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) scr[st_pad(st_index(0, r, w, lane))] = v[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = scr[st_pad(st_index(1, r, w, lane))];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {  // qubits 5..7: lane bits 2..4 of the second mapping
+        const float c = cq[5 + j], sn = sq[5 + j];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = ry_lane(v[r], lane, 2 + j, c, sn);
+    }
+    __syncthreads();  // every read of the first layout is done
+#pragma unroll
+    for (int r = 0; r < 16; ++r) scr[st_pad(st_index(1, r, w, lane))] = v[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) st[st_index(0, r, w, lane)] = scr[st_pad(st_index(0, r, w, lane))];
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_hbm_hi(const Inst* __restrict__ insts, int idx, int layer) {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -667,7 +724,10 @@ int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, 
     if (marks) prof_end(ctx);
     for (int layer = 1; layer <= d; ++layer) {
         if (marks) prof_begin(ctx, 3);
-        k_hbm_lo<R><<<dim3(chunks, S), 256, lo_smem, ctx->stream>>>(dtable, idx, layer);
+        if constexpr (sizeof(R) == 4)
+            k_hbm_lo_regs<<<dim3(chunks, S), 256, 0, ctx->stream>>>(dtable, idx, layer);
+        else
+            k_hbm_lo<R><<<dim3(chunks, S), 256, lo_smem, ctx->stream>>>(dtable, idx, layer);
         if (marks) prof_end(ctx);
         if (marks) prof_begin(ctx, 3);
         k_hbm_hi<R><<<dim3(tiles, S), 256, hi_smem, ctx->stream>>>(dtable, idx, layer);
