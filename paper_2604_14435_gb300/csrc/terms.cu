@@ -713,6 +713,58 @@ __global__ void __launch_bounds__(256) k_hbm_hi(const Inst* __restrict__ insts, 
     }
 }
 
+// The high-qubit pass for FP32 states of 2^(12 + LOGH) amplitudes, LOGH >= 6
+// (n >= 18), in registers: a CTA takes the 2^LOGH rows x 32 columns of its
+// tile, lane = column.  Loaded with row h = (r << 3) | w (r: H/8 registers),
+// the qubits on h bits 3.. rotate in place; one padded, conflict-free transpose
+// to h = (w << (LOGH - 3)) | r puts h bits 0..2 (qubits 12..14) on registers,
+// and the tile is stored from there (a warp writes one 128-byte row segment per
+// register).  One barrier per tile instead of one per qubit.
+template <int LOGH>
+__global__ void __launch_bounds__(256) k_hbm_hi_regs(const Inst* __restrict__ insts, int idx, int layer) {
+    constexpr int H = 1 << LOGH, RG = H / 8;
+    __shared__ float scr[H * 33];
+    __shared__ float cq[LOGH], sq[LOGH];
+    const Inst& I = insts[idx];
+    const int s = blockIdx.y, n = I.n, lo0 = blockIdx.x * 32, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const size_t N = size_t(1) << n;
+    if (t < LOGH) shift_angle<float>(I, s, layer * n + LOQ + t, cq[t], sq[t]);
+    float* st = reinterpret_cast<float*>(I.states) + s * N + lo0 + lane;
+    float v[RG];
+#pragma unroll
+    for (int r = 0; r < RG; ++r) v[r] = st[(size_t)((r << 3) | w) << LOQ];
+    __syncthreads();
+#pragma unroll
+    for (int kb = 0; kb < LOGH - 3; ++kb) {  // h bit 3 + kb: qubit 15 + kb, register bit kb
+        const float c = cq[3 + kb], sn = sq[3 + kb];
+#pragma unroll
+        for (int r = 0; r < RG; ++r)
+            if (!((r >> kb) & 1)) {
+                const float a0 = v[r], a1 = v[r | (1 << kb)];
+                v[r] = c * a0 - sn * a1;
+                v[r | (1 << kb)] = sn * a0 + c * a1;
+            }
+    }
+#pragma unroll
+    for (int r = 0; r < RG; ++r) scr[((r << 3) | w) * 33 + lane] = v[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RG; ++r) v[r] = scr[((w << (LOGH - 3)) | r) * 33 + lane];
+#pragma unroll
+    for (int kb = 0; kb < 3; ++kb) {  // h bit kb: qubit 12 + kb, register bit kb
+        const float c = cq[kb], sn = sq[kb];
+#pragma unroll
+        for (int r = 0; r < RG; ++r)
+            if (!((r >> kb) & 1)) {
+                const float a0 = v[r], a1 = v[r | (1 << kb)];
+                v[r] = c * a0 - sn * a1;
+                v[r | (1 << kb)] = sn * a0 + c * a1;
+            }
+    }
+#pragma unroll
+    for (int r = 0; r < RG; ++r) st[(size_t)((w << (LOGH - 3)) | r) << LOQ] = v[r];
+}
+
 template <typename R>
 int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, int S, bool marks) {
     const int chunks = 1 << (n - LOQ), tiles = LOC / HC;
@@ -730,7 +782,14 @@ int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, 
             k_hbm_lo<R><<<dim3(chunks, S), 256, lo_smem, ctx->stream>>>(dtable, idx, layer);
         if (marks) prof_end(ctx);
         if (marks) prof_begin(ctx, 3);
-        k_hbm_hi<R><<<dim3(tiles, S), 256, hi_smem, ctx->stream>>>(dtable, idx, layer);
+        if (sizeof(R) == 4 && n == 20)
+            k_hbm_hi_regs<8><<<dim3(LOC / 32, S), 256, 0, ctx->stream>>>(dtable, idx, layer);
+        else if (sizeof(R) == 4 && n == 19)
+            k_hbm_hi_regs<7><<<dim3(LOC / 32, S), 256, 0, ctx->stream>>>(dtable, idx, layer);
+        else if (sizeof(R) == 4 && n == 18)
+            k_hbm_hi_regs<6><<<dim3(LOC / 32, S), 256, 0, ctx->stream>>>(dtable, idx, layer);
+        else
+            k_hbm_hi<R><<<dim3(tiles, S), 256, hi_smem, ctx->stream>>>(dtable, idx, layer);
         if (marks) prof_end(ctx);
     }
     DVQLS_CUDA_TRY(ctx, cudaGetLastError());

@@ -1,5 +1,6 @@
 """States streamed through HBM (n > 12) vs the oracle: full parity at
-n = 13..16 and sampled outputs / size-independent identities at n = 20."""
+n = 13..16, 18 and 19, and sampled outputs / size-independent identities at
+n = 20."""
 import numpy as np
 import pytest
 import torch
@@ -21,6 +22,23 @@ def test_hbm_states_match_definition(dv, ctx, prec, n, d, L):
     alpha = wl.random_angles(n * (d + 1), 800 + n)
     ref = oterms.cost_grad(n, d, alpha, b, coef, xs, zs)
     check(gpu_cost_grad(dv, ctx, n, d, alpha, b, coef, xs, zs, prec), ref, prec)
+
+
+_REG_CASES = {}
+
+
+@pytest.mark.parametrize("n", [18, 19])
+@pytest.mark.parametrize("prec", [1, 2])
+def test_hbm_states_register_passes(dv, ctx, prec, n):
+    """n = 18, 19: the FP32 high-qubit pass keeps its tiles in registers (as at
+    n = 20); full parity against the oracle with one ansatz layer."""
+    if n not in _REG_CASES:  # the oracle takes tens of seconds here: once per size
+        rng = np.random.default_rng(710 + n)
+        coef, xs, zs, b = random_problem(rng, n, 5)
+        alpha = wl.random_angles(n * 2, 810 + n)
+        _REG_CASES[n] = (coef, xs, zs, b, alpha, oterms.cost_grad(n, 1, alpha, b, coef, xs, zs))
+    coef, xs, zs, b, alpha, ref = _REG_CASES[n]
+    check(gpu_cost_grad(dv, ctx, n, 1, alpha, b, coef, xs, zs, prec), ref, prec)
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
