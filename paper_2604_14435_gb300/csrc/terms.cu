@@ -567,18 +567,39 @@ __device__ __forceinline__ void shift_angle(const Inst& I, int s, int a, R& c, R
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_hbm_init(const Inst* __restrict__ insts, int idx) {
+    // The product state factorises over bit groups: amplitude i of this chunk
+    // is t0[i & 63] t1[(i >> 6) & 63] h, the factors of qubits 0..5, 6..11 and
+    // of the chunk's high bits (two multiplies per amplitude).
     const Inst& I = insts[idx];
-    __shared__ R cq[32], sq[32];
-    const int s = blockIdx.y, n = I.n;
+    __shared__ R cq[32], sq[32], t0[64], t1[64], hc;
+    const int s = blockIdx.y, n = I.n, t = threadIdx.x;
     const size_t N = size_t(1) << n;
-    if (threadIdx.x < n) shift_angle<R>(I, s, threadIdx.x, cq[threadIdx.x], sq[threadIdx.x]);
+    if (t < n) shift_angle<R>(I, s, t, cq[t], sq[t]);
     __syncthreads();
-    R* st = reinterpret_cast<R*>(I.states) + s * N;
-    for (int e = threadIdx.x; e < LOC; e += blockDim.x) {
-        const int i = (blockIdx.x << LOQ) + e;
+    if (t < 128) {
+        const int g = t >> 6, k = t & 63;
         R v = (R)1;
-        for (int q = 0; q < n; ++q) v *= ((i >> q) & 1) ? sq[q] : cq[q];
-        st[i] = v;
+        for (int q = 0; q < 6; ++q) v *= ((k >> q) & 1) ? sq[6 * g + q] : cq[6 * g + q];
+        (g ? t1 : t0)[k] = v;
+    } else if (t == 128) {
+        R v = (R)1;
+        for (int q = LOQ; q < n; ++q) v *= ((blockIdx.x >> (q - LOQ)) & 1) ? sq[q] : cq[q];
+        hc = v;
+    }
+    __syncthreads();
+    R* st = reinterpret_cast<R*>(I.states) + s * N + ((size_t)blockIdx.x << LOQ);
+    constexpr int VE = 16 / sizeof(R);
+#pragma unroll 4
+    for (int e4 = t; e4 < LOC / VE; e4 += 256) {
+        R v[VE];
+#pragma unroll
+        for (int k = 0; k < VE; ++k) {
+            const int e = e4 * VE + k;
+            v[k] = t0[e & 63] * t1[(e >> 6) & 63] * hc;
+        }
+        uint4 u;
+        memcpy(&u, v, 16);
+        reinterpret_cast<uint4*>(st)[e4] = u;
     }
 }
 
