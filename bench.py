@@ -242,6 +242,34 @@ def cpu_oracle_rate(budget_s=10.0, max_shifts=101):
     return 1.0 / per_eval, threads, sample
 
 
+def cpu_definition_rate(reps=3):
+    """Definition-level oracle (each shifted state once, beta = Phi^H Phi and
+    delta by dense products, FP64 numpy) on instance 0: a second CPU baseline.
+    Returns (evals/s, sample description)."""
+    from oracle import decompose as odec
+    from oracle import terms as oterms
+    from paper_2604_14435_gb300 import workloads as wl
+    inst = wl.throughput_instance(0, n=N_QUBITS, d=DEPTH, L_max=L_TERMS)
+    dec = odec.decompose_banded(N_QUBITS, inst["offsets"], inst["bands"], 0.0, L_TERMS)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oterms.cost_grad(N_QUBITS, DEPTH, inst["alpha"], inst["b"], dec["coef"], dec["x"], dec["z"])
+    el = time.perf_counter() - t0
+    return reps / el, "%d whole cost+grad evaluations of instance 0 (%.1f s wall)" % (reps, el)
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def workload_config(name, n_gpus, shapes):
     base = {"parallelism": "dp%d" % n_gpus, "instances_per_gpu": len(shapes),
             "l2": "flushed between timed steps (256 MB write)"}
@@ -589,7 +617,10 @@ def main():
             if not args.no_cpu_baseline and ws == 1:
                 rate, cores, sample = cpu_oracle_rate(budget_s=10.0)
                 line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                        "sample": sample}
+                                        "sample": sample, "cpu": cpu_model(), "nproc": os.cpu_count()}
+                d_rate, d_sample = cpu_definition_rate()
+                line["cpu_definition_baseline"] = {"value": d_rate, "unit": UNIT, "kind": "oracle (definition level)",
+                                                   "sample": d_sample}
         print(json.dumps(line))
     D.dvqls_destroy(ctx)
     if pg:
