@@ -260,6 +260,13 @@ def cpu_definition_rate(reps=3):
 
 def cpu_model():
     try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
         with open("/proc/cpuinfo") as f:
             for line in f:
                 if line.lower().startswith(("model name", "cpu part")):
