@@ -102,6 +102,8 @@ def pruning_sweep(ctx, n, offsets, bands, taus=PAPER_TAUS, rhs=None, tol=1e-12, 
     Returns a dict with the full decomposition size and one row per tau."""
     bands = np.ascontiguousarray(bands, dtype=np.float64)
     probe = _decompose(ctx, n, offsets, bands, 0.0, 1)
+    if probe["L_pre"] < 1:
+        raise ValueError("A has no nonzero Pauli coefficient")
     full = _decompose(ctx, n, offsets, bands, 0.0, probe["L_pre"])
     total = _sum_sq(full["coef"])
     X = None
