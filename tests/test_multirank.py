@@ -4,6 +4,7 @@ The path shards instances across ranks with no data-path exchange; the only
 collectives are the timing barrier and the max over ranks.  These tests check
 that the ranks' batches are disjoint and cover the job, that every rank sees
 the slowest rank's time, and the whole-job rate."""
+import json
 import os
 import socket
 import sys
@@ -87,3 +88,30 @@ def test_reference_arm_nonzero_rank_does_no_work(monkeypatch):
 
     assert bench.run_reference(Args()) is None
     assert not called
+
+
+def test_reference_arm_line_on_rank0(monkeypatch, capsys):
+    """Rank 0 prints one JSON line in the bench contract, its value from the
+    CPU oracle (here stubbed to a fixed rate), e2e without copies."""
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setenv("RANK", "0")
+    calls = []
+
+    def fake_rate(budget_s, max_shifts):
+        calls.append(budget_s)
+        return 0.25, 16, "stub sample"
+
+    monkeypatch.setattr(bench, "cpu_oracle_rate", fake_rate)
+
+    class Args:
+        gpus, steps, warmup = 1, 3, 2
+
+    bench.run_reference(Args())
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert len(calls) == 5 and all(0.2 <= b <= 2.0 for b in calls)
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] == pytest.approx(0.25) and line["ms_per_step"] == pytest.approx(4000.0)
+    assert line["steps"] == 3 and line["warmup"] == 2 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 16
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
