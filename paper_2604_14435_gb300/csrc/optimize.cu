@@ -276,6 +276,206 @@ extern "C" int dvqls_fidelity(dvqls_ctx* ctx, const dvqls_ansatz* an, const doub
     return DVQLS_OK;
 }
 
+// ------------------------------------------------ grid-wide CG (large N)
+// The same conjugate gradients for one right-hand side of N >= CGM_MIN_N
+// amplitudes, spread over the whole GPU: each step is a grid kernel (the
+// matvec, the vector updates with per-block partial dot products) followed by
+// a one-CTA kernel that adds the partials in block order (deterministic) and
+// forms the CG scalars in device memory.  The host issues CGM_CHUNK
+// iterations at a time and reads the scalars between chunks; every kernel
+// returns at once after the stop flag is set.  Scalars: [0] r.r, [1] ||rhs||,
+// [2] alpha, [3] beta, [4] stop, [5] iterations, [6] relative residual,
+// [7] breakdown (p.Ap <= 0).
+constexpr long long CGM_MIN_N = 4096;
+constexpr int CGM_T = 256, CGM_CHUNK = 8;
+
+__device__ double cgm_block_sum(double v, double* red) {  // valid in thread 0
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < CGM_T / 32; ++k) s += red[k];
+    return s;
+}
+
+__global__ void __launch_bounds__(CGM_T) k_cgm_matvec(int n, int L, const double2* coef, const uint32_t* xm,
+                                                      const uint32_t* zm, const double2* v, double2* y, int conj_coef,
+                                                      const double* sc) {
+    if (sc[4] != 0.0) return;
+    const int N = 1 << n;
+    for (int j = blockIdx.x * CGM_T + threadIdx.x; j < N; j += gridDim.x * CGM_T) {
+        double yr = 0.0, yi = 0.0;
+        for (int l = 0; l < L; ++l) {
+            const uint32_t x = xm[l] & (N - 1), z = zm[l] & (N - 1);
+            double2 c = coef[l];
+            if (conj_coef) c.y = -c.y;
+            double2 ph;
+            switch (__popc(x & z) & 3) {
+                case 0: ph = make_double2(1, 0); break;
+                case 1: ph = make_double2(0, 1); break;
+                case 2: ph = make_double2(-1, 0); break;
+                default: ph = make_double2(0, -1); break;
+            }
+            const uint32_t src = uint32_t(j) ^ x;
+            const double sg = (__popc(z & src) & 1) ? -1.0 : 1.0;
+            const double2 a = v[src];
+            const double cr = c.x * ph.x - c.y * ph.y, ci = c.x * ph.y + c.y * ph.x;
+            yr += sg * (cr * a.x - ci * a.y);
+            yi += sg * (cr * a.y + ci * a.x);
+        }
+        y[j] = make_double2(yr, yi);
+    }
+}
+
+// r = b (copy_b) then x = 0, p = r, partial r.r; clears the flags.
+__global__ void __launch_bounds__(CGM_T) k_cgm_start(int N, const double2* b, int copy_b, double2* x, double2* r,
+                                                     double2* p, double* part) {
+    __shared__ double red[CGM_T / 32];
+    double s = 0.0;
+    for (int j = blockIdx.x * CGM_T + threadIdx.x; j < N; j += gridDim.x * CGM_T) {
+        const double2 v = copy_b ? b[j] : r[j];
+        if (copy_b) r[j] = v;
+        x[j] = make_double2(0.0, 0.0);
+        p[j] = v;
+        s += v.x * v.x + v.y * v.y;
+    }
+    s = cgm_block_sum(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_cgm_reset(double* sc) {
+    for (int k = 0; k < 8; ++k) sc[k] = 0.0;
+}
+
+__global__ void __launch_bounds__(CGM_T) k_cgm_scalar_start(int G, const double* part, double* sc, double tol) {
+    if (threadIdx.x != 0) return;
+    double rr = 0.0;
+    for (int k = 0; k < G; ++k) rr += part[k];
+    sc[0] = rr;
+    sc[1] = sqrt(rr);
+    sc[5] = 0.0;
+    sc[6] = sc[1] > 0.0 ? 1.0 : 0.0;
+    sc[7] = 0.0;
+    sc[4] = sc[6] <= tol ? 1.0 : 0.0;
+}
+
+__global__ void __launch_bounds__(CGM_T) k_cgm_dot(int N, const double2* a, const double2* b, double* part,
+                                                   const double* sc) {  // partial Re(a^dag b)
+    if (sc[4] != 0.0) return;
+    __shared__ double red[CGM_T / 32];
+    double s = 0.0;
+    for (int j = blockIdx.x * CGM_T + threadIdx.x; j < N; j += gridDim.x * CGM_T) {
+        const double2 x = a[j], y = b[j];
+        s += x.x * y.x + x.y * y.y;
+    }
+    s = cgm_block_sum(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_cgm_alpha(int G, const double* part, double* sc) {
+    if (sc[4] != 0.0) return;
+    double pAp = 0.0;
+    for (int k = 0; k < G; ++k) pAp += part[k];
+    if (!(pAp > 0.0)) {
+        sc[7] = 1.0;
+        sc[4] = 1.0;
+    } else {
+        sc[2] = sc[0] / pAp;
+    }
+}
+
+// x += alpha p, r -= alpha Ap, partial r.r
+__global__ void __launch_bounds__(CGM_T) k_cgm_update(int N, double2* x, double2* r, const double2* p,
+                                                      const double2* Ap, double* part, const double* sc) {
+    if (sc[4] != 0.0) return;
+    __shared__ double red[CGM_T / 32];
+    const double a = sc[2];
+    double s = 0.0;
+    for (int j = blockIdx.x * CGM_T + threadIdx.x; j < N; j += gridDim.x * CGM_T) {
+        double2 xv = x[j], rv = r[j];
+        const double2 pv = p[j], av = Ap[j];
+        xv.x += a * pv.x;
+        xv.y += a * pv.y;
+        rv.x -= a * av.x;
+        rv.y -= a * av.y;
+        x[j] = xv;
+        r[j] = rv;
+        s += rv.x * rv.x + rv.y * rv.y;
+    }
+    s = cgm_block_sum(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_cgm_beta(int G, const double* part, double* sc, double tol, int max_iter) {
+    if (sc[4] != 0.0) return;
+    double rr2 = 0.0;
+    for (int k = 0; k < G; ++k) rr2 += part[k];
+    sc[3] = rr2 / sc[0];
+    sc[0] = rr2;
+    sc[5] += 1.0;
+    sc[6] = sc[1] > 0.0 ? sqrt(rr2) / sc[1] : 0.0;
+    if (sc[6] <= tol || sc[5] >= max_iter) sc[4] = 1.0;
+}
+
+__global__ void __launch_bounds__(CGM_T) k_cgm_p(int N, const double2* r, double2* p, const double* sc) {
+    if (sc[4] != 0.0) return;
+    const double bet = sc[3];
+    for (int j = blockIdx.x * CGM_T + threadIdx.x; j < N; j += gridDim.x * CGM_T) {
+        const double2 rv = r[j], pv = p[j];
+        p[j] = make_double2(rv.x + bet * pv.x, rv.y + bet * pv.y);
+    }
+}
+
+// out as k_cg: iterations, relative residual, converged, normal equations used.
+__global__ void k_cgm_finish(const double* sc, double* out, double tol, int normal, int max_iter) {
+    const bool broke = sc[7] != 0.0;
+    out[0] = broke ? max_iter : sc[5];
+    out[1] = broke ? INFINITY : sc[6];
+    out[2] = (!broke && sc[6] <= tol) ? 1.0 : 0.0;
+    out[3] = normal;
+}
+
+static int cg_multi(dvqls_ctx* ctx, int n, int L, const double2* coef, const uint32_t* xm, const uint32_t* zm,
+                    const double2* b, double2* x, double2* r, double2* p, double2* Ap, double2* tmp, double tol,
+                    int max_iter, double* out, double* sc, double* part, int G) {
+    const int N = 1 << n;
+    cudaStream_t st = ctx->stream;
+    for (int normal = 0; normal < 2; ++normal) {
+        k_cgm_reset<<<1, 1, 0, st>>>(sc);
+        if (normal) k_cgm_matvec<<<G, CGM_T, 0, st>>>(n, L, coef, xm, zm, b, r, 1, sc);  // r = A~^dag b
+        k_cgm_start<<<G, CGM_T, 0, st>>>(N, b, normal ? 0 : 1, x, r, p, part);
+        k_cgm_scalar_start<<<1, CGM_T, 0, st>>>(G, part, sc, tol);
+        DVQLS_CUDA_TRY(ctx, cudaGetLastError());
+        double h[8];
+        for (;;) {
+            for (int k = 0; k < CGM_CHUNK; ++k) {
+                if (normal) {
+                    k_cgm_matvec<<<G, CGM_T, 0, st>>>(n, L, coef, xm, zm, p, tmp, 0, sc);
+                    k_cgm_matvec<<<G, CGM_T, 0, st>>>(n, L, coef, xm, zm, tmp, Ap, 1, sc);
+                } else {
+                    k_cgm_matvec<<<G, CGM_T, 0, st>>>(n, L, coef, xm, zm, p, Ap, 0, sc);
+                }
+                k_cgm_dot<<<G, CGM_T, 0, st>>>(N, p, Ap, part, sc);
+                k_cgm_alpha<<<1, 1, 0, st>>>(G, part, sc);
+                k_cgm_update<<<G, CGM_T, 0, st>>>(N, x, r, p, Ap, part, sc);
+                k_cgm_beta<<<1, 1, 0, st>>>(G, part, sc, tol, max_iter);
+                k_cgm_p<<<G, CGM_T, 0, st>>>(N, r, p, sc);
+            }
+            DVQLS_CUDA_TRY(ctx, cudaGetLastError());
+            DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(h, sc, sizeof h, cudaMemcpyDeviceToHost, st));
+            DVQLS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+            if (h[4] != 0.0) break;
+        }
+        if (h[7] == 0.0 || normal) {  // converged or out of iterations, or the normal equations broke down too
+            k_cgm_finish<<<1, 1, 0, st>>>(sc, out, tol, normal, max_iter);
+            DVQLS_CUDA_TRY(ctx, cudaGetLastError());
+            return DVQLS_OK;
+        }
+    }
+    return DVQLS_OK;
+}
+
 extern "C" int dvqls_lcu_solve_batched(dvqls_ctx* ctx, int n, const dvqls_lcu* lcu, int nrhs, const double* b,
                                        double tol, int max_iter, double* x, int* iters, double* rel_resid) {
     if (!ctx) return DVQLS_ERR_INVALID_ARG;
@@ -300,6 +500,9 @@ extern "C" int dvqls_lcu_solve_batched(dvqls_ctx* ctx, int n, const dvqls_lcu* l
     const size_t o_ap = ar.reserve(vec);
     const size_t o_tmp = ar.reserve(vec);
     const size_t o_out = ar.reserve(size_t(nrhs) * 32);
+    const bool multi = nrhs == 1 && N >= CGM_MIN_N;  // one large system: the grid-wide CG
+    const int G = multi ? (int)std::min<long long>(N / CGM_T, (long long)ctx->num_sms * 8) : 0;
+    const size_t o_sc = ar.reserve(64), o_part = ar.reserve(size_t(std::max(G, 1)) * 8);
     int rc = ensure_workspace(ctx, ar.total());
     if (!rc) rc = ensure_pinned(ctx, pin.total());
     if (!rc) rc = pin_acquire(ctx);
@@ -310,9 +513,16 @@ extern "C" int dvqls_lcu_solve_batched(dvqls_ctx* ctx, int n, const dvqls_lcu* l
     auto zm = (const uint32_t*)stage_in(ctx, lcu->zmask, size_t(L) * 4, p_zm, o_zm);
     auto bd = (const double2*)stage_in(ctx, b, vec, p_b, o_b);
     double* out = (double*)(ws + o_out);
-    k_cg<<<nrhs, CGT, 0, ctx->stream>>>(n, L, coef, xm, zm, bd, (double2*)(ws + o_x), (double2*)(ws + o_r),
-                                        (double2*)(ws + o_p), (double2*)(ws + o_ap), (double2*)(ws + o_tmp), tol,
-                                        max_iter, out);
+    if (multi) {
+        rc = cg_multi(ctx, n, L, coef, xm, zm, bd, (double2*)(ws + o_x), (double2*)(ws + o_r), (double2*)(ws + o_p),
+                      (double2*)(ws + o_ap), (double2*)(ws + o_tmp), tol, max_iter, out, (double*)(ws + o_sc),
+                      (double*)(ws + o_part), G);
+        if (rc) return rc;
+    } else {
+        k_cg<<<nrhs, CGT, 0, ctx->stream>>>(n, L, coef, xm, zm, bd, (double2*)(ws + o_x), (double2*)(ws + o_r),
+                                            (double2*)(ws + o_p), (double2*)(ws + o_ap), (double2*)(ws + o_tmp), tol,
+                                            max_iter, out);
+    }
     DVQLS_CUDA_TRY(ctx, cudaGetLastError());
     rc = pin_release(ctx);
     std::vector<PendingOut> pend;

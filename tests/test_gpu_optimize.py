@@ -143,3 +143,41 @@ def test_batched_optimizer_runs_each_instance(dv, ctx, prec):
             assert abs(r.iters - it_ref) <= 1
             if r.iters == it_ref:
                 assert np.abs(a - a_ref).max() <= 1e-8
+
+
+@pytest.mark.parametrize("case", ["toeplitz12", "indefinite12", "toeplitz20"])
+def test_grid_cg_large_systems(dv, ctx, case):
+    """One system of N >= 4096 runs the grid-wide CG: the residual of the
+    returned x, formed on the CPU with the oracle's Pauli action, meets the
+    tolerance (indefinite A~ through the normal equations)."""
+    if case == "indefinite12":  # 0.5 I + Z_0 + 0.3 X_1: CG breaks down, the normal equations converge
+        n = 12
+        dec = {"coef": np.array([0.5, 1.0, 0.3]), "x": np.array([0, 0, 2], np.uint32),
+               "z": np.array([0, 1, 0], np.uint32)}
+        b = np.random.default_rng(4).normal(size=1 << n) + 0j
+        tol = 1e-11
+    else:
+        n = 12 if case == "toeplitz12" else 20
+        inst = wl.throughput_instance(3, n=n)
+        dec = odec.decompose_banded(n, inst["offsets"], inst["bands"], 0.0, 64)
+        b = inst["b"].astype(np.complex128)
+        tol = 1e-12
+    lcu, keep = lcu_of(dv, dec["coef"], dec["x"], dec["z"])
+    x = np.zeros(2 << n)
+    it, rr = dv.dvqls_lcu_solve(ctx, n, lcu, cv(b), tol, 20000, x)
+    x = x.view(np.complex128)
+    Ax = np.zeros_like(x)
+    for c, xm, zm in zip(dec["coef"], dec["x"], dec["z"]):
+        Ax += c * oterms.apply_pauli(xm, zm, x)
+    if case == "indefinite12":  # the normal equations' residual is ||A^dag (A x - b)||
+        res = np.zeros_like(x)
+        for c, xm, zm in zip(dec["coef"], dec["x"], dec["z"]):
+            res += np.conj(c) * oterms.apply_pauli(xm, zm, Ax - b)
+        rhs = np.zeros_like(x)
+        for c, xm, zm in zip(dec["coef"], dec["x"], dec["z"]):
+            rhs += np.conj(c) * oterms.apply_pauli(xm, zm, b)
+        assert np.linalg.norm(res) <= 10 * tol * np.linalg.norm(rhs)
+        assert np.linalg.norm(Ax - b) <= 1e-8 * np.linalg.norm(b)
+    else:
+        assert np.linalg.norm(Ax - b) <= 10 * tol * np.linalg.norm(b)
+    assert rr <= tol and it > 0
