@@ -280,7 +280,9 @@ int dvqls_fidelity(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alp
  * A~ = sum_l c_l A_l applied as a Pauli-string matvec in FP64: conjugate
  * gradients (A~ Hermitian positive definite), falling back to CG on the
  * normal equations when CG breaks down (p^dag A~ p <= 0).  Stops when
- * ||r|| / ||rhs|| <= tol or after max_iter iterations.  x: N complex128
+ * ||r|| / ||rhs|| <= tol or after max_iter iterations.  N < 4096: one CTA;
+ * larger: the same iteration spread over the whole GPU (grid kernels, the dot
+ * products added in a fixed block order).  x: N complex128
  * (not normalised).  iters, rel_resid may be NULL.  Returns NUMERIC when tol
  * was not reached (x then holds the last iterate). */
 int dvqls_lcu_solve(dvqls_ctx* ctx, int n, const dvqls_lcu* lcu, const double* b, double tol,
