@@ -102,6 +102,10 @@ typedef enum { DVQLS_ANSATZ_RY_CZRING = 0 } dvqls_ansatz_kind;
 
 typedef struct dvqls_ctx dvqls_ctx;
 
+/* A context is not thread-safe: its workspace, staging buffers, graph cache
+ * and autotuning table are shared by its calls, so one thread at a time may
+ * use it (one context per host thread for concurrent work). */
+
 /* Create a context on CUDA device `device`.  `stream` is the cudaStream_t
  * every call of this context is ordered on (passed as void* so this header
  * needs no CUDA include); NULL is the default stream.  The context never
