@@ -115,3 +115,26 @@ def test_reference_arm_line_on_rank0(monkeypatch, capsys):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 16
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_bench_work_accounting():
+    """The headline's algorithmic and executed work per step (8N FLOP per paper
+    term; three 128 x 144 x 16 FP16 MMAs per 32 amplitudes on the tensor cores)."""
+    shapes = [(10, 4, 64)] * 32
+    terms, alg, exe = bench.work_of(shapes, tensor=True)
+    assert terms == 32 * 101 * (64 * 64 + 64) == 13_445_120
+    assert alg == terms * 8 * 1024  # 110.1 GFLOP
+    assert exe == 32 * 101 * 3 * 2 * 128 * 144 * 512 == 183_005_872_128
+    _, _, exe_cc = bench.work_of(shapes, tensor=False)
+    assert bench.executed_gram_entries(64) == 136 * 16
+    assert bench.executed_gram_entries(128) == 2 * 136 * 16 + 2 * 128 * 16
+    assert exe_cc == 32 * 101 * (136 * 16 * 2 * 1024 + 64 * 4 * 1024)
+
+
+def test_bench_peaks_measured_or_fallback(monkeypatch):
+    peaks, src = bench.measured_peaks()
+    if src == "of measured":
+        assert peaks["hbm_gbs"] > 1000 and peaks["bf16_tflops"] > 100
+    monkeypatch.setattr(bench.os.path, "exists", lambda p: False)
+    peaks, src = bench.measured_peaks()
+    assert src == "of fallback" and peaks == {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
