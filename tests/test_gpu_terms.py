@@ -92,6 +92,18 @@ def test_random_lcu_against_definition(dv, ctx, prec, n, d, L):
     check(gpu_cost_grad(dv, ctx, n, d, alpha, b, coef, xs, zs, prec), ref, prec)
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("n,d,L", [(11, 1, 24), (12, 1, 20)])
+def test_largest_on_chip_states(dv, ctx, prec, n, d, L):
+    """n = 11 (four state copies per pipeline, the largest that fit) and n = 12
+    (one copy; shared-memory gate passes) on the tensor-core and CUDA-core tiles."""
+    rng = np.random.default_rng(600 + n)
+    coef, xs, zs, b = random_problem(rng, n, L)
+    alpha = wl.random_angles(n * (d + 1), 610 + n)
+    ref = oterms.cost_grad(n, d, alpha, b, coef, xs, zs)
+    check(gpu_cost_grad(dv, ctx, n, d, alpha, b, coef, xs, zs, prec), ref, prec)
+
+
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_cost_only_and_host_pointers(dv, ctx, prec):
     rng = np.random.default_rng(77)
