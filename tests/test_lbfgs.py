@@ -65,3 +65,35 @@ def test_quadratic_closed_form():
     assert np.allclose(r["alpha"], target, atol=1e-9)
     r = lbfgsb_loop(fg, np.zeros(3), eps=1e-20, max_iter=100, bounds=(-1.0, 1.0))
     assert np.allclose(r["alpha"], np.clip(target, -1.0, 1.0), atol=1e-9)
+
+
+def test_solve_routes_to_the_library_calls(monkeypatch):
+    """lbfgs.solve evaluates through dvqls_cost_grad (global) or
+    dvqls_local_cost_grad (local) with the given precision; stand-ins driven
+    by the oracle take the place of the library here."""
+    from paper_2604_14435_gb300 import dvqls as D
+    from paper_2604_14435_gb300 import lbfgs
+
+    v, n, d, xhat, fun_grad, calls = _validation()
+    coef, xs, zs = _lcu(v)
+    seen = []
+
+    def fake_global(ctx, an, a, lcu, b, prec, cost, grad, beta=None, delta=None):
+        seen.append(("global", prec, an.n, an.depth))
+        r = oterms.cost_grad(n, d, np.asarray(a), v["b"], coef, xs, zs)
+        cost[0], grad[:] = r["cost"], r["grad"]
+
+    def fake_local(ctx, an, a, lcu, prec, cost, grad=None):
+        seen.append(("local", prec, an.n, an.depth))
+        r = oterms.local_cost_grad(n, d, np.asarray(a), coef, xs, zs)
+        cost[0], grad[:] = r["cost"], r["grad"]
+
+    monkeypatch.setattr(D, "dvqls_cost_grad", fake_global)
+    monkeypatch.setattr(D, "dvqls_local_cost_grad", fake_local)
+    r = lbfgs.solve(None, n, d, None, None, v["alphas"][0], precision=D.DVQLS_FP64, eps=1e-10, max_iter=200)
+    assert r["converged"] and {s[0] for s in seen} == {"global"} and {s[1:] for s in seen} == {(0, n, d)}
+    seen.clear()
+    r = lbfgs.solve(None, n, d, None, None, v["alphas"][0], precision=D.DVQLS_FP32, eps=1e-10, max_iter=200,
+                    local=True)
+    assert r["converged"] and {s[0] for s in seen} == {"local"} and {s[1] for s in seen} == {1}
+    assert oterms.local_cost_grad(n, d, r["alpha"], coef, xs, zs)["cost"] <= 1e-10
