@@ -53,9 +53,27 @@ UNIT = "evals/s"
 SMS, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
 FP16_PER_BF16 = 1.0  # kind::f16 runs FP16 and BF16 operands at the same nominal dense rate (2.25 PFLOP/s)
-# DRAM bytes (read + write) per launch of the tensor-core term kernel on this workload, from the ncu
-# capture summarised in profiles/k_terms_tc_n10_L64_batch32.md; None once the kernel changes.
-TC_TRAFFIC_BYTES = 1671680
+# DRAM bytes (read + write) per launch of the tensor-core term kernel on the headline workload, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), with the SHA-256 (first 16 hex digits) of the
+# kernel sources it was taken on.  The figure is reported only while those sources are unchanged.
+TC_TRAFFIC = {"sources_sha16": None, "bytes": None}
+TC_SOURCES = ("paper_2604_14435_gb300/csrc/terms.cu", "paper_2604_14435_gb300/csrc/state.cuh")
+
+
+def kernel_sources_sha16():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in TC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def tc_traffic():
+    """The captured DRAM traffic per launch, or None when the kernel changed since."""
+    if TC_TRAFFIC["bytes"] is None or kernel_sources_sha16() != TC_TRAFFIC["sources_sha16"]:
+        return None
+    return TC_TRAFFIC["bytes"]
 
 
 def measured_peaks():
@@ -295,6 +313,104 @@ def workload_config(name, n_gpus, shapes):
     return base
 
 
+def hbm_state_record(shapes, ms_per_step):
+    """HBM roofline of the shifted-state passes of the n > 12 instances."""
+    # per real FP32 amplitude: the first pass writes 4 B; each layer reads and writes the state twice
+    # (low-qubit pass, high-qubit pass): 16 B
+    hbm_bytes = sum((2 * n * (d + 1) + 1) * (1 << n) * 4 * (1 + 4 * d) for n, d, L in shapes if n > 12)
+    peaks, peak_src = measured_peaks()
+    gbs = hbm_bytes / (ms_per_step / 1000.0) / 1e9
+    return {"bound": "hbm", "kernels": "k_hbm_init, k_hbm_lo_regs, k_hbm_hi_regs", "achieved": gbs,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "frac_note": peak_src,
+            "bytes_per_step": hbm_bytes, "ms_per_step": ms_per_step,
+            "achieved_note": "algorithmic bytes: 4 B written per amplitude by the product-state pass, "
+                             "16 B read+written per amplitude per ansatz layer"}
+
+
+def side_workload(D, ctx, torch, rank, name, prec, steps, flush, stream, pg, ws):
+    """Device rate of another workload in the same run (same timing rules as
+    the headline: warm-up, L2 flushed between steps outside the timed
+    events), its per-phase kernel times, and the HBM roofline of its state
+    passes when it has states in HBM."""
+    dev_arr, _, keep, shapes = make_batch(D, ctx, torch, rank, name)
+    count = len(shapes)
+    P = sum(n * (d + 1) for n, d, L in shapes)
+    costs = torch.zeros(count, dtype=torch.float64, device="cuda")
+    grads = torch.zeros(P, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        D.dvqls_cost_grad_batched(ctx, dev_arr, prec, costs, grads)
+    D.dvqls_sync(ctx)
+    torch.cuda.synchronize()
+
+    def timed(profile):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            D.dvqls_profile_enable(ctx, 1)
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            D.dvqls_cost_grad_batched(ctx, dev_arr, prec, costs, grads)
+            ev[k][1].record(stream)
+        D.dvqls_sync(ctx)
+        torch.cuda.synchronize()
+        if profile:
+            D.dvqls_profile_enable(ctx, 0)
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    ms = max_over_ranks(pg, torch, timed(False), "cuda")
+    timed(True)
+    phases = {k: D.dvqls_profile_read(ctx, i) for i, k in enumerate(("prepare", "terms", "combine", "hbm_states"))}
+    terms, alg, _ = work_of(shapes)
+    n_t, ms_t = phases["terms"]
+    rec = {"workload": workload_config(name, ws, shapes)["workload"], "value": job_rate(ws, count, steps, ms),
+           "unit": UNIT, "steps": steps, "ms_per_step": ms / steps, "instances_per_gpu": count,
+           "terms_per_s": ws * terms * steps / (ms / 1000.0),
+           "term_kernel_ms_avg": ms_t / max(1, n_t),
+           "term_kernel_algorithmic_tflops": alg / (ms_t / max(1, n_t) / 1000.0) / 1e12,
+           "phase_ms_per_step": {k: v[1] / steps for k, v in phases.items()},
+           "phase_launches_per_step": {k: v[0] / steps for k, v in phases.items()},
+           "costs_finite": bool(torch.isfinite(costs).all().item())}
+    n_h, ms_h = phases["hbm_states"]
+    rec["hbm_states"] = hbm_state_record(shapes, ms_h / steps) if n_h > 0 else None
+    return rec
+
+
+def oracle_errors(D, ctx, torch, keep):
+    """Largest |GPU - FP64 oracle| of beta, delta, cost and gradient on
+    instance 0 of the headline batch, for each precision of the library
+    (part of the CPU-baseline leg: the definition-level oracle runs here)."""
+    from oracle import decompose as odec
+    from oracle import terms as oterms
+    from paper_2604_14435_gb300 import workloads as wl
+    inst = wl.throughput_instance(0, n=N_QUBITS, d=DEPTH, L_max=L_TERMS)
+    dec = odec.decompose_banded(N_QUBITS, inst["offsets"], inst["bands"], 0.0, L_TERMS)
+    t0 = time.perf_counter()
+    ref = oterms.cost_grad(N_QUBITS, DEPTH, inst["alpha"], inst["b"], dec["coef"], dec["x"], dec["z"])
+    oracle_s = time.perf_counter() - t0
+    coef0, xm0, zm0, alpha0, b0 = keep[0]
+    an = D.make_ansatz(N_QUBITS, DEPTH)
+    lcu0 = D.make_lcu(L_TERMS, coef0, xm0, zm0)
+    out = {"instance": "seed 0 of the headline batch (n=10, L=64, depth 4, all 101 shifts)",
+           "oracle": "definition-level FP64 (oracle/terms.py)", "oracle_s": oracle_s}
+    for name, prec in (("fp32_tc", D.DVQLS_FP32_TC), ("fp32", D.DVQLS_FP32), ("fp32_wht", D.DVQLS_FP32_WHT),
+                       ("fp64", D.DVQLS_FP64)):
+        cost = np.zeros(1)
+        grad = np.zeros(N_QUBITS * (DEPTH + 1))
+        beta = np.zeros(2 * L_TERMS * L_TERMS)
+        delta = np.zeros(2 * L_TERMS)
+        D.dvqls_cost_grad(ctx, an, alpha0, lcu0, b0, prec, cost, grad, beta, delta)
+        out[name] = {"beta": float(np.abs(beta.view(np.complex128).reshape(L_TERMS, L_TERMS) - ref["beta"]).max()),
+                     "delta": float(np.abs(delta.view(np.complex128) - ref["delta"]).max()),
+                     "cost": float(abs(cost[0] - ref["cost"])),
+                     "grad": float(np.abs(grad - ref["grad"]).max())}
+    out["bounds"] = {"fp64": "1e-12 relative (absolute for |beta|, |delta| <= 1)",
+                     "fp32 paths": "beta, delta 1e-5; cost 1e-6; grad 1e-5 (absolute)"}
+    return out
+
+
 def run_reference(args):
     rank, _, ws = dist_env()
     if ws > 1 and rank != 0:
@@ -326,7 +442,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="toeplitz10", choices=["toeplitz10", "uneven", "hele_shaw"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the CPU oracle leg (its timing and the per-quantity error against it)")
+    ap.add_argument("--no-side-workloads", action="store_true",
+                    help="headline only: skip the Hele-Shaw and uneven-batch records")
     ap.add_argument("--precision", default="fp32_tc", choices=["fp32", "fp32_tc"],
                     help="term kernel: tcgen05 tensor cores with an FP32-accurate 3xFP16 split (served for "
                          "L <= 64; default), or FP32 on the CUDA cores")
@@ -508,6 +627,15 @@ def main():
                  "note": "C_L of Eq. 2/4 for b = |+>^10: the paper's 90,112-circuit optimizer-iteration workload; "
                          "the paper reports 17.15 s per iteration on 4 A100s (context only, other hardware)"}
 
+    # The configs beside the headline (headline only), so that every run
+    # records them: the Hele-Shaw-type system (L = 256, depth 6) and the
+    # uneven batch (62 on-chip instances + two n = 20 with states in HBM).
+    sides = {}
+    if headline and not args.no_side_workloads:
+        side_steps = max(3, min(args.steps, 20))
+        for name in ("hele_shaw", "uneven"):
+            sides[name] = side_workload(D, ctx, torch, rank, name, PREC, side_steps, flush, stream, pg, ws)
+
     # Comparison path (headline only): the per-circuit FP64 evaluation of
     # instance 0 (all 840,320 circuits of one cost+grad) and its decomposition.
     circ = decomp = None
@@ -562,7 +690,7 @@ def main():
             peak = peaks["bf16_tflops"] * FP16_PER_BF16
             roof = {"bound": "tensor", "kernel": "k_terms_tc", "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": TC_TRAFFIC_BYTES if args.workload == "toeplitz10" else None,
+                    "traffic": tc_traffic() if args.workload == "toeplitz10" else None,
                     "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch (ncu)",
                     "peak_note": "FP16 dense = bf16 burst %.0f TFLOP/s (%s; same nominal rate)"
                                  % (peaks["bf16_tflops"], peak_src.split()[1]),
@@ -592,16 +720,7 @@ def main():
         hbm = None
         n_h, ms_h = phases["hbm_states"]
         if n_h > 0:  # shifted states of n > 12 built in HBM: an HBM-bound phase of its own
-            # per real FP32 amplitude: the first pass writes 4 B; each layer reads and writes the
-            # state twice (low-qubit pass, high-qubit pass): 16 B
-            hbm_bytes = sum((2 * n * (d + 1) + 1) * (1 << n) * 4 * (1 + 4 * d) for n, d, L in shapes if n > 12)
-            peaks, peak_src = measured_peaks()
-            gbs = hbm_bytes / (ms_h / args.steps / 1000.0) / 1e9
-            hbm = {"bound": "hbm", "kernels": "k_hbm_init, k_hbm_lo, k_hbm_hi", "achieved": gbs,
-                   "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "frac_note": peak_src,
-                   "bytes_per_step": hbm_bytes, "ms_per_step": ms_h / args.steps,
-                   "achieved_note": "algorithmic bytes: 4 B written per amplitude by the product-state pass, "
-                                    "16 B read+written per amplitude per ansatz layer"}
+            hbm = hbm_state_record(shapes, ms_h / args.steps)
         metric = METRIC if headline else "cost+grad evals/sec (%s workload)" % args.workload
         line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
@@ -621,6 +740,8 @@ def main():
             line["speedup_vs_fp64_circuit_path"] = value / circ["value"]
             line["decomposition"] = decomp
             line["local_cost"] = local
+            line["hele_shaw"] = sides.get("hele_shaw")
+            line["uneven"] = sides.get("uneven")
             if not args.no_cpu_baseline and ws == 1:
                 rate, cores, sample = cpu_oracle_rate(budget_s=10.0)
                 line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -628,6 +749,7 @@ def main():
                 d_rate, d_sample = cpu_definition_rate()
                 line["cpu_definition_baseline"] = {"value": d_rate, "unit": UNIT, "kind": "oracle (definition level)",
                                                    "sample": d_sample}
+                line["error_vs_fp64_oracle"] = oracle_errors(D, ctx, torch, keep)
         print(json.dumps(line))
     D.dvqls_destroy(ctx)
     if pg:

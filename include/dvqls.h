@@ -380,9 +380,10 @@ int dvqls_ws_load(dvqls_ctx* ctx, const char* path, dvqls_ws** out);
  * entry point exists for callers that must not allocate GPU memory, such as
  * code running inside a memory pool or allocator that owns the whole device,
  * a real-time loop whose allocation pattern is fixed, or a plugin host that
- * forbids cudaMalloc.  It computes exactly what dvqls_cost_grad computes
- * (same kernels, no beta/delta output) without a context: it calls no
- * cudaMalloc, cudaFree, cudaMallocHost or other allocating routine.
+ * forbids cudaMalloc.  It computes what dvqls_cost_grad computes in
+ * DVQLS_FP64 or DVQLS_FP32 (the same kernels; no beta / delta output)
+ * without a context: it calls no cudaMalloc, cudaFree, cudaMallocHost or
+ * other allocating routine.
  *
  * Its scratch is one fixed device array of DVQLS_NOALLOC_SCRATCH_BYTES
  * inside this library; every GPU that loads the library holds it until the
@@ -391,20 +392,27 @@ int dvqls_ws_load(dvqls_ctx* ctx, const char* path, dvqls_ws** out);
  * 256): sizeof record + 256 + 16 L + 16 L^2 + 48 P + 8 + 16 S T^2 k
  * + 16 S T k + 24 S, with S = 2P+1, T = ceil(L/64) and k <= 8 the split of
  * the amplitude range, plus 16 L^2 + 16 L in DVQLS_FP32 (the weights as
- * float pairs); for example n = 10, L = 64, P = 50 needs about 170 KB in
- * FP32, and L up to about 160 (FP32) or 200 (FP64) fits.
+ * float pairs).  With the largest split (k = 8), n = 10, depth 4 (P = 50)
+ * fits up to L = 160 in FP32 and L = 200 in FP64 on any GPU.
  *
  * The call runs on the current CUDA device, ordered on `stream` (a
- * cudaStream_t, NULL = default stream), and returns after cost and grad are
- * written.  alpha, b, the lcu arrays, cost and grad must all be device memory
- * of the current device (nothing is staged): a host pointer is INVALID_ARG.
+ * cudaStream_t, NULL = default stream); it waits for that stream before it
+ * returns, so cost and grad are written when it returns.  alpha, b, the lcu
+ * arrays, cost and grad must all be device memory of the current device
+ * (nothing is staged): a host pointer is INVALID_ARG.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) once; make that first call before any stream
- * capture.  Every call shares the one array: two calls that overlap on the
- * GPU (other streams, other threads) race and give wrong results, so keep
- * calls ordered on one stream or serialise them.
- * Errors: INVALID_ARG, UNSUPPORTED (n > DVQLS_MAX_SMEM_QUBITS or another
- * ansatz), NUMERIC, CUDA.  No error text is kept (there is no context). */
+ * (cudaGetSymbolAddress) once and keeps it for the process; make that first
+ * call before any stream capture.  Because the address is kept, the process
+ * must not reset the device (cudaDeviceReset) after its first call.
+ * Every call shares the one array and finds the previous call's contents
+ * there: two calls that overlap on the GPU (other streams, other threads)
+ * race and give wrong results, so keep calls ordered on one stream or
+ * serialise them.
+ * Errors: INVALID_ARG; UNSUPPORTED (n > DVQLS_MAX_SMEM_QUBITS, another
+ * ansatz, or precision DVQLS_FP32_TC / DVQLS_FP32_WHT); NUMERIC; CUDA, also
+ * returned without any work when the caller's thread already has a CUDA
+ * error pending (that error is left in place).  No error text is kept
+ * (there is no context). */
 #define DVQLS_NOALLOC_SCRATCH_BYTES (1u << 20)
 int dvqls_cost_grad_noalloc(void* stream, const dvqls_ansatz* ansatz, const double* alpha,
                             const dvqls_lcu* lcu, const double* b, int precision,

@@ -394,7 +394,7 @@ int run_circuits(dvqls_ctx* ctx, const dvqls_ansatz* an, const double* alpha, co
     k_circ_prepare<<<1, CT, 0, ctx->stream>>>(I, ctx->d_status);
     I.b = I.bhat;
     const size_t smem = size_t(P) * 16 + (size_t(2) << n) * 16;
-    DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_circuits, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    DVQLS_CUDA_TRY(ctx, allow_dynamic_smem((const void*)k_circuits));
     int bps = 0;
     DVQLS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_circuits, CT, smem));
     if (bps < 1) return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "circuit kernel does not fit");

@@ -26,6 +26,17 @@ bool is_device_ptr(const dvqls_ctx* ctx, const void* p) {
     return a.type == cudaMemoryTypeManaged;
 }
 
+cudaError_t allow_dynamic_smem(const void* fn) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - int(fa.sharedSizeBytes));
+    return e;
+}
+
 int ensure_workspace(dvqls_ctx* ctx, size_t bytes) {
     if (bytes <= ctx->ws_cap) return DVQLS_OK;
     DVQLS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));

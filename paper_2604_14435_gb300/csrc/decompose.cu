@@ -386,20 +386,20 @@ int decompose_common(dvqls_ctx* ctx, const double* A_in, int n, int nbands, cons
     double* key = (double*)(ws + o_key);
     if (n <= LO_BITS) {
         const size_t smem = size_t(N) * 8;
-        DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fwht_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        DVQLS_CUDA_TRY(ctx, allow_dynamic_smem((const void*)k_fwht_smem));
         k_fwht_smem<<<M, 512, smem, ctx->stream>>>(dense ? dA : nullptr, bd, dense ? nullptr : dA, n, masks, coef, key);
     } else {
         double* work = (double*)(ws + o_work);
         k_fwht_lo<<<M * int(N >> LO_BITS), 512, 0, ctx->stream>>>(dense ? dA : nullptr, bd, dense ? nullptr : dA, n,
                                                                   masks, work);
         const size_t smem = size_t(N >> LO_BITS) * HI_TILE * 8;
-        DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fwht_hi, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        DVQLS_CUDA_TRY(ctx, allow_dynamic_smem((const void*)k_fwht_hi));
         k_fwht_hi<<<M * (LO / HI_TILE), 512, smem, ctx->stream>>>(n, masks, work, coef, key);
     }
     k_key_stats<<<grid, 256, 0, ctx->stream>>>(key, E, kmax, misc + 1);
     k_count_post<<<grid, 256, 0, ctx->stream>>>(key, E, tau, kmax, misc + 2);
     const size_t sel_smem = SEL_CHUNK * sizeof(Cand);
-    DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_select_round, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sel_smem)));
+    DVQLS_CUDA_TRY(ctx, allow_dynamic_smem((const void*)k_select_round));
     Cand* bufA = (Cand*)(ws + o_candA);
     Cand* bufB = (Cand*)(ws + o_candB);
     long long cur = E;

@@ -161,6 +161,13 @@ void prof_end(dvqls_ctx* ctx);
 // Synchronise, then turn the device status word into a status code.
 int sync_and_check(dvqls_ctx* ctx);
 
+// Raises the dynamic shared-memory limit of kernel `fn` on the current device
+// to everything the device allows (its opt-in maximum less the kernel's
+// static shared memory).  Every caller sets the same value, so one caller
+// cannot lower the limit between another caller's set-up and its launch (two
+// contexts on two threads, or a context and the allocation-free entry point).
+cudaError_t allow_dynamic_smem(const void* fn);
+
 inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }
 
 }  // namespace dvqls

@@ -264,7 +264,7 @@ extern "C" int dvqls_fidelity(dvqls_ctx* ctx, const dvqls_ansatz* an, const doub
     memcpy(ctx->pin + p_t, &I, sizeof I);
     DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ws + o_t, ctx->pin + p_t, sizeof I, cudaMemcpyHostToDevice, ctx->stream));
     const size_t smem = size_t(N + P) * 16;
-    DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fidelity, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    DVQLS_CUDA_TRY(ctx, allow_dynamic_smem((const void*)k_fidelity));
     k_fidelity<<<1, FT, smem, ctx->stream>>>((const FidInst*)(ctx->ws + o_t), ctx->d_status);
     DVQLS_CUDA_TRY(ctx, cudaGetLastError());
     rc = pin_release(ctx);
@@ -638,7 +638,7 @@ extern "C" int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* i
         results[i].fidelity = NAN;
     }
     const size_t fsmem = (size_t(1) << nmax) * 16 + size_t(*std::max_element(P.begin(), P.end())) * 16;
-    DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fidelity, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsmem)));
+    DVQLS_CUDA_TRY(ctx, allow_dynamic_smem((const void*)k_fidelity));
     std::vector<int> active(count);
     for (int i = 0; i < count; ++i) active[i] = i;
     std::vector<double> hF(count), hC(count);

@@ -790,8 +790,8 @@ template <typename R>
 int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, int S, bool marks) {
     const int chunks = 1 << (n - LOQ), tiles = LOC / HC;
     const size_t lo_smem = sizeof(R) * LOC, hi_smem = sizeof(R) * ((size_t)chunks * HC);
-    DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_hbm_lo<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lo_smem)));
-    DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_hbm_hi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hi_smem)));
+    DVQLS_CUDA_TRY(ctx, allow_dynamic_smem((const void*)k_hbm_lo<R>));
+    DVQLS_CUDA_TRY(ctx, allow_dynamic_smem((const void*)k_hbm_hi<R>));
     if (marks) prof_begin(ctx, 3);  // one profiling mark per kernel
     k_hbm_init<R><<<dim3(chunks, S), 256, 0, ctx->stream>>>(dtable, idx);
     if (marks) prof_end(ctx);
@@ -2387,7 +2387,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     auto kfun = wht ? (const void*)k_terms_wht
                 : tc ? (const void*)k_terms_tc
                 : fp32 ? (const void*)k_terms_smem<float> : (const void*)k_terms_smem<double>;
-    DVQLS_CUDA_TRY(ctx, cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    DVQLS_CUDA_TRY(ctx, allow_dynamic_smem(kfun));
     int bps = 0;
     DVQLS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfun, wht ? WHT_NT : tc ? TCT : NT, smem));
     if (tc) bps = std::min(bps, 1);  // one CTA per SM, two item pipelines in it
@@ -2781,7 +2781,11 @@ extern "C" int dvqls_cost_grad_noalloc(void* stream_arg, const dvqls_ansatz* ans
                                        double* grad) {
     using namespace dvqls;
     cudaStream_t stream = (cudaStream_t)stream_arg;
+    // An error the caller's own CUDA work left pending is not this call's to
+    // clear: report it and leave it in place.
+    if (cudaPeekAtLastError() != cudaSuccess) return DVQLS_ERR_CUDA;
     if (!ansatz || !lcu || !cost || !grad) return DVQLS_ERR_INVALID_ARG;
+    if (precision == DVQLS_FP32_TC || precision == DVQLS_FP32_WHT) return DVQLS_ERR_UNSUPPORTED;
     if (precision != DVQLS_FP32 && precision != DVQLS_FP64) return DVQLS_ERR_INVALID_ARG;
     const int n = ansatz->n, d = ansatz->depth, L = lcu->L;
     if (n < 1 || n > DVQLS_MAX_QUBITS || d < 0 || L < 1) return DVQLS_ERR_INVALID_ARG;
@@ -2802,7 +2806,7 @@ extern "C" int dvqls_cost_grad_noalloc(void* stream_arg, const dvqls_ansatz* ans
     const long long N = 1LL << n;
     const size_t smem = fp32 ? smem_bytes<float>(n, P) : smem_bytes<double>(n, P);
     auto kfun = fp32 ? (const void*)k_terms_smem<float> : (const void*)k_terms_smem<double>;
-    if (cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) {
+    if (allow_dynamic_smem(kfun) != cudaSuccess) {
         cudaGetLastError();
         return DVQLS_ERR_CUDA;
     }

@@ -43,8 +43,10 @@ def same(got, ref):
     assert (got["L_out"], got["L_pre"], got["L_post"]) == (ref["L_out"], ref["L_pre"], ref["L_post"])
     assert np.array_equal(got["x"], ref["x"])
     assert np.array_equal(got["z"], ref["z"])
-    assert np.array_equal(got["coef"].view(np.float64), ref["coef"].view(np.float64)) or \
-        np.array_equal(got["coef"], ref["coef"])
+    # bit-exact: the float64 words themselves (a complex == would accept -0.0 for +0.0)
+    g = np.ascontiguousarray(got["coef"]).view(np.uint64)
+    r = np.ascontiguousarray(ref["coef"]).view(np.uint64)
+    assert g.shape == r.shape and np.array_equal(g, r)
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 9])

@@ -1,6 +1,6 @@
 """GPU cost / gradient / beta / delta vs the oracle.
 
-Tolerances (written here, derived in the design notes): FP64 path
+Tolerances: FP64 path
 |gpu - cpu| <= 1e-12 * max(1, |cpu|) for beta, delta, cost and gradient; FP32
 path <= 1e-5 absolute on beta and delta, <= 1e-6 on the cost, <= 1e-5 on the
 gradient."""
