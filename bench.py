@@ -48,6 +48,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_QUBITS, DEPTH, L_TERMS, BATCH = 10, 4, 64, 32
+# kernel phases of a cost pass, in the order the library's profiling hook numbers them
+PHASES = ("prepare", "terms", "combine", "hbm_states", "states")
 METRIC = "cost+grad evals/sec at n=10, L=64 (FP32 batched vs FP64 circuit path)"
 UNIT = "evals/s"
 SMS, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
@@ -221,18 +223,19 @@ def make_batch(D, ctx, torch, rank, name):
 
 def work_of(shapes, tensor=False):
     """Paper terms, algorithmic and executed FLOPs of one cost+grad pass.
-    The tensor-core kernel executes, per shift and pair of amplitudes, three
-    real 128 x 128 rank-1 updates (hi hi^T + hi lo^T + lo hi^T) of the term
-    rows of both halves of a stage."""
+    The tensor-core kernel executes, per k-step of 16 amplitudes of each half
+    of a stage, three MMAs with M = 128: hi hi^T with the b rows (N = 144),
+    hi (2 lo)^T (N = 128) and 2 lo hi(b)^T / 2 (N = 16)."""
     terms = alg = exe = 0
     for n, d, L in shapes:
         S = 2 * n * (d + 1) + 1
         N = 1 << n
         terms += S * (L * L + L)
         alg += S * (L * L + L) * 8 * N
-        # tensor cores: 3 MMAs of 128 x 144 x 16 per 32 amplitudes (Gram and delta rows); CUDA cores: one
-        # real FMA per Gram product (the ansatz state is real) and 4 flops per delta product (complex b)
-        exe += S * (3 * 2 * 128 * 144 * N // 2 if tensor else executed_gram_entries(L) * 2 * N + L * 4 * N)
+        # tensor cores: MMAs of 128 x (144 + 128 + 16) x 16 per 32 amplitudes (Gram and delta rows); CUDA
+        # cores: one real FMA per Gram product (the ansatz state is real) and 4 flops per delta product
+        exe += S * (2 * 128 * (144 + 128 + 16) * 16 * (N // 32) if tensor else
+                    executed_gram_entries(L) * 2 * N + L * 4 * N)
     return terms, alg, exe
 
 
@@ -362,7 +365,7 @@ def side_workload(D, ctx, torch, rank, name, prec, steps, flush, stream, pg, ws)
 
     ms = max_over_ranks(pg, torch, timed(False), "cuda")
     timed(True)
-    phases = {k: D.dvqls_profile_read(ctx, i) for i, k in enumerate(("prepare", "terms", "combine", "hbm_states"))}
+    phases = {k: D.dvqls_profile_read(ctx, i) for i, k in enumerate(PHASES)}
     terms, alg, _ = work_of(shapes)
     n_t, ms_t = phases["terms"]
     rec = {"workload": workload_config(name, ws, shapes)["workload"], "value": job_rate(ws, count, steps, ms),
@@ -519,8 +522,7 @@ def main():
     dev_ms = timed(profile=False)
     clk = clocks.stop()
     prof_ms = timed(profile=True)
-    phases = {name: D.dvqls_profile_read(ctx, k) for k, name in
-              enumerate(("prepare", "terms", "combine", "hbm_states"))}
+    phases = {name: D.dvqls_profile_read(ctx, k) for k, name in enumerate(PHASES)}
     dev_ms = max_over_ranks(pg, torch, dev_ms, "cuda")
     value = job_rate(ws, count, args.steps, dev_ms)
     head_costs = costs.cpu().numpy().copy()
@@ -697,8 +699,9 @@ def main():
                     "frac_note": peak_src,
                     "achieved_note": "algorithmic: 8N FLOP per paper term, all L^2 ordered pairs + L",
                     "executed": {"tflops": executed, "frac": executed / peak, "flops_per_launch": exe,
-                                 "note": "three FP16 passes (hi hi, hi lo, lo hi) of 128 x 144 x 16 MMAs, "
-                                         "each covering 2 x 16 amplitudes of a 64-term tile and of b"}}
+                                 "note": "per 2 x 16 amplitudes of a 64-term tile: FP16 MMAs hi hi^T with the b "
+                                         "rows (128 x 144 x 16), hi (2 lo)^T (128 x 128 x 16) and "
+                                         "2 lo hi(b)^T / 2 (128 x 16 x 16)"}}
         else:
             roof = {"bound": "alu", "kernel": "k_terms_smem<float>", "achieved": achieved,
                     "peak": FP32_PEAK, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK, "traffic": None,
@@ -716,7 +719,7 @@ def main():
                      "phase_ms_per_step": {k: v[1] / args.steps for k, v in phases.items()},
                      "phase_launches_per_step": {k: v[0] / args.steps for k, v in phases.items()},
                      "profiled_pass_ms_per_step": prof_ms / args.steps})
-        launches_per_step = sum(phases[k][0] for k in ("prepare", "terms", "combine", "hbm_states")) / args.steps
+        launches_per_step = sum(phases[k][0] for k in PHASES) / args.steps
         hbm = None
         n_h, ms_h = phases["hbm_states"]
         if n_h > 0:  # shifted states of n > 12 built in HBM: an HBM-bound phase of its own

@@ -131,12 +131,28 @@ int dvqls_sync(dvqls_ctx* ctx);
  * batched cost pass is bracketed by CUDA events recorded on the context's
  * stream.  Enabling (enable = 1) resets the counters; disabling keeps them.
  * dvqls_profile_read synchronises the stream and returns, for `phase`
- * (0: prepare, 1: term tiles, 2: combine, 3: state passes in HBM for n > 12),
- * the number of launches and their
- * total duration in milliseconds since the last reset.
+ * (0: prepare, 1: term tiles, 2: combine, 3: state passes in HBM for n > 12,
+ * 4: the on-chip state build of the tensor-core pass), the number of
+ * launches and their total duration in milliseconds since the last reset.
  * Errors: INVALID_ARG (phase out of range), CUDA. */
 int dvqls_profile_enable(dvqls_ctx* ctx, int enable);
 int dvqls_profile_read(dvqls_ctx* ctx, int phase, long long* launches, double* ms);
+
+/* Failure detection: the timeout budget of the device waits.  The warp roles
+ * of the tensor-core term kernel (DVQLS_FP32_TC) hand work to each other
+ * through shared-memory barriers; every wait on one gives up after
+ * `microseconds` of the GPU's global timer (<= 0 restores the default of one
+ * second; at most an hour).  A wait that gives up stops the kernel cleanly --
+ * each role leaves at its next check and waits no more, the tensor memory is
+ * freed only after every issued MMA has completed -- and the call (or the
+ * next dvqls_sync) returns DVQLS_ERR_TIMEOUT; the context stays usable.  A
+ * budget far below the time the work takes makes calls time out; a healthy
+ * kernel's waits last microseconds.  The paper has no counterpart: there
+ * every circuit is its own asynchronous job (Sec. 2.3), here one kernel holds
+ * the whole pass, so a stuck hand-over must end in an error instead of a wait
+ * without end.
+ * Errors: INVALID_ARG (ctx NULL). */
+int dvqls_set_wait_budget(dvqls_ctx* ctx, long long microseconds);
 
 /* ------------------------------------------------------------------------
  * Pauli decomposition (Sec. 2.2, Eq. 5; Algorithm 1, Steps 1-2).
@@ -235,6 +251,36 @@ typedef struct {
  * the caller is capturing the stream, kernels are launched directly. */
 int dvqls_cost_grad_batched(dvqls_ctx* ctx, int count, const dvqls_instance* inst,
                             int precision, double* costs, double* grads);
+
+/* One instance split across ranks (Sec. 2.3 Stage III; Algorithm 1, Step
+ * 4c).  A rank evaluates the shifts s_begin .. s_end - 1 of the 2P + 1
+ * parameter-shift evaluations (0 <= s_begin < s_end <= 2P + 1; shift 0 is
+ * alpha, 2k + 1 is alpha + (pi/2) e_k, 2k + 2 is alpha - (pi/2) e_k) and
+ * writes, for every shift g of the instance, the four doubles
+ *     partials[4 g .. 4 g + 3] = (Re T_g, Im T_g, Re D_g, Im D_g),
+ *     T_g = sum_l c_l delta_l (b normalised), D_g = sum_lm c_l^* c_m beta_lm,
+ * with zeros for the shifts outside its range.  The arrays of ranks whose
+ * ranges cover 0 .. 2P without overlap add up, element by element (one SUM
+ * allreduce of (2P + 1) x 4 doubles, the paper's exchange of two scalars per
+ * evaluated cost), to the whole instance's; N_g = |T_g|^2 is formed only
+ * after that sum, by dvqls_combine_partials.  partials: (2P + 1) x 4
+ * doubles, host or device.  Other arguments as dvqls_cost_grad.
+ * Errors: as dvqls_cost_grad; INVALID_ARG for an empty or out-of-range shift
+ * range. */
+int dvqls_cost_grad_partials(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alpha,
+                             const dvqls_lcu* lcu, const double* b, int precision, int s_begin, int s_end,
+                             double* partials);
+
+/* Cost and parameter-shift gradient of one instance from its complete
+ * per-shift sums (the layout dvqls_cost_grad_partials writes, summed over
+ * the ranks): N_g = |T_g|^2, C = 1 - N_0 / D_0 and dC/dalpha_k =
+ * -(N'_k D_0 - N_0 D'_k) / D_0^2 with N'_k, D'_k half the difference of the
+ * shifted values (Eq. 1; the shift rule), in FP64 on the GPU.  n, depth give
+ * P = n (depth + 1); partials: (2P + 1) x 4 doubles; cost: 1 double; grad:
+ * P doubles; host or device.
+ * Errors: INVALID_ARG, UNSUPPORTED (P > 1024), NUMERIC (D_0 <= 0 or not
+ * finite), ALLOC, CUDA. */
+int dvqls_combine_partials(dvqls_ctx* ctx, int n, int depth, const double* partials, double* cost, double* grad);
 
 /* Local cost (Eq. 2, expanded in Eq. 4; closed form of Sec. 2.3 Stage III):
  *   C_L = 1 - (1/n) sum_j <x|A^dag U_b P_j U_b^dag A|x> / <x|A^dag A|x>,

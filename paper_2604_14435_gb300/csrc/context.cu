@@ -1,4 +1,6 @@
 // Context life cycle, workspace and staging for the D-VQLS C-ABI.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace dvqls {
@@ -224,7 +226,7 @@ extern "C" int dvqls_profile_enable(dvqls_ctx* ctx, int enable) {
     int rc = prof_drain(ctx);
     if (rc) return rc;
     if (enable) {
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 5; ++k) {
             ctx->prof_launches[k] = 0;
             ctx->prof_ms[k] = 0.0;
         }
@@ -234,7 +236,7 @@ extern "C" int dvqls_profile_enable(dvqls_ctx* ctx, int enable) {
 }
 
 extern "C" int dvqls_profile_read(dvqls_ctx* ctx, int phase, long long* launches, double* ms) {
-    if (!ctx || phase < 0 || phase > 3 || !launches || !ms) return DVQLS_ERR_INVALID_ARG;
+    if (!ctx || phase < 0 || phase > 4 || !launches || !ms) return DVQLS_ERR_INVALID_ARG;
     cudaSetDevice(ctx->device);
     int rc = prof_drain(ctx);
     if (rc) return rc;
@@ -299,6 +301,12 @@ extern "C" void dvqls_destroy(dvqls_ctx* ctx) {
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     cudaGetLastError();
     delete ctx;
+}
+
+extern "C" int dvqls_set_wait_budget(dvqls_ctx* ctx, long long microseconds) {
+    if (!ctx) return DVQLS_ERR_INVALID_ARG;
+    ctx->wait_budget_us = microseconds > 0 ? std::min(microseconds, 3600LL * 1000000LL) : 1000000LL;
+    return DVQLS_OK;
 }
 
 extern "C" const char* dvqls_last_error(const dvqls_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }

@@ -65,8 +65,12 @@ struct dvqls_ctx {
     struct Mark { int phase; cudaEvent_t a, b; };
     std::vector<Mark> marks;
     std::vector<cudaEvent_t> event_pool;
-    long long prof_launches[4] = {0, 0, 0, 0};
-    double prof_ms[4] = {0, 0, 0, 0};
+    long long prof_launches[5] = {0, 0, 0, 0, 0};
+    double prof_ms[5] = {0, 0, 0, 0, 0};
+
+    // Time each bounded device wait of the tensor-core term kernel allows
+    // before it gives up, in microseconds (dvqls_set_wait_budget).
+    long long wait_budget_us = 1000000;
 
     // Cached batched-call state (see terms.cu): the last captured graph of a
     // cost pass, the private stream graphs are captured on, and the
@@ -169,5 +173,18 @@ int sync_and_check(dvqls_ctx* ctx);
 cudaError_t allow_dynamic_smem(const void* fn);
 
 inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }
+
+// A cost pass over the shifts s0 .. s1 - 1 of one instance that writes the
+// per-shift sums (4 doubles per shift of the instance, zeros outside the
+// range) to `partials` instead of forming the cost (terms.cu).
+struct ShiftRange {
+    int s0, s1;
+    double* partials;
+};
+
+// The batched cost pass (terms.cu): cost and gradient (or, with a shift range,
+// per-shift sums) of `count` instances.
+int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precision, bool want_grad, double* costs,
+              double* grads, double* beta_out, double* delta_out, bool local, const ShiftRange* range = nullptr);
 
 }  // namespace dvqls

@@ -19,8 +19,6 @@
 
 namespace dvqls {
 
-int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precision, bool want_grad, double* costs,
-              double* grads, double* beta_out, double* delta_out, bool local);
 
 namespace {
 

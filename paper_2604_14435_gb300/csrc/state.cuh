@@ -216,10 +216,12 @@ __device__ inline void build_state_real(R* psi, typename V2<R>::t* scs, int n, i
 // alternating M1 and M2 from layer to layer.  Ry gates of a layer commute, so
 // the layer splits across the transpose; the CZ ring is a sign per amplitude.
 
-// x = hi + lo with hi = RN_fp16(x), lo = RN_fp16(x - hi), packed as hi | lo << 16.
-__device__ __forceinline__ uint32_t split_hl(float x) {
+// The tensor-core operand pair of x: hi = RN_fp16(x) in the low half-word and
+// RN_fp16(2 (x - hi)) -- the low part, doubled -- in the high one (x - hi is
+// exact in FP32).  x ~ hi + (high half) / 2.
+__device__ __forceinline__ uint32_t split_h2l(float x) {
     const __half h = __float2half_rn(x);
-    const __half l = __float2half_rn(x - __half2float(h));
+    const __half l = __float2half_rn(2.f * (x - __half2float(h)));
     return (uint32_t)__half_as_ushort(h) | ((uint32_t)__half_as_ushort(l) << 16);
 }
 
@@ -234,10 +236,10 @@ __device__ __forceinline__ float ry_lane(float v, int lane, int b, float c, floa
     return fmaf(c, v, ((lane >> b) & 1) ? s * p : -s * p);
 }
 
-// Final store of an amplitude: packed FP16 (hi, lo) (PACK) or FP32.
+// Final store of an amplitude: packed FP16 (hi, 2 lo) (PACK) or FP32.
 template <bool PACK>
 __device__ __forceinline__ void st_out(void* psi, int i, float v) {
-    if (PACK) reinterpret_cast<uint32_t*>(psi)[i] = split_hl(v);
+    if (PACK) reinterpret_cast<uint32_t*>(psi)[i] = split_h2l(v);
     else reinterpret_cast<float*>(psi)[i] = v;
 }
 
@@ -343,8 +345,8 @@ __device__ void state_regs_warp(void* psi, const float2* scs, int n, int d, int 
 }
 
 // The real state of shift s, times `scale`, for a group of 256 threads (ids t,
-// named barrier `bar`) into psi[0 .. 2^n), as packed FP16 (hi, lo) pairs
-// (split_hl; PACK) or as FP32; n <= 12.  scratch: 2 x (2^n + 2^n / 32) floats
+// named barrier `bar`) into psi[0 .. 2^n), as packed FP16 (hi, 2 lo) pairs
+// (split_h2l; PACK) or as FP32; n <= 12.  scratch: 2 x (2^n + 2^n / 32) floats
 // of shared memory that nothing else uses meanwhile.
 template <bool PACK>
 __device__ inline void build_state_regs(void* psi, float* scratch, float2* scs, int n, int d, int P,

@@ -42,6 +42,7 @@ constexpr int MAX_ANGLES = 1024;
 struct Inst {
     int n, d, L, P, S, T, ks;
     int F;      // term flavors per shift: 1 (global cost) or n + 1 (local cost)
+    int s0;     // first shift of the pass: its shift s selects the angles of shift s0 + s (0 unless split)
     int local;  // 1: local cost C_L (b = |+>^n), 0: global cost
     int items;
     long long item_base;
@@ -65,6 +66,7 @@ struct Inst {
     void* dpart;     // ks*L   (shift 0 only; null when delta is not requested)
     double* NsDs;    // 3S: N_s, Re D_s, Im D_s
     void* states;    // n > 12: the S shifted states in HBM (S x N), else null
+    void* tcst;      // tensor-core pass, n <= 12: the S shifted states as packed FP16 pairs (S x N words), else null
     double* cost;
     double* grad;    // P or null
     double2* beta;   // L*L or null
@@ -298,7 +300,7 @@ __device__ void process_item(const Inst& I, int local, unsigned char* smem, uint
         szm[t] = m < L ? I.zm[m] : 0u;
     }
     if (I.states) __syncthreads();
-    else build_state_real<R>(psi_smem, scs, I.n, I.d, I.P, I.cs, s, t, NT, 0, (R)1);
+    else build_state_real<R>(psi_smem, scs, I.n, I.d, I.P, I.cs, s + I.s0, t, NT, 0, (R)1);
 
     // Task of this thread: block (a, b) = rows 4a.., columns 4b.. of the tile.
     const int g = t / KSLOT, slot = t % KSLOT;
@@ -556,9 +558,10 @@ constexpr int LOQ = 12, LOC = 1 << LOQ, HC = 32;
 template <typename R>
 __device__ __forceinline__ void shift_angle(const Inst& I, int s, int a, R& c, R& sn) {
     int k = -1, which = 0;
-    if (s > 0) {
-        k = (s - 1) >> 1;
-        which = ((s - 1) & 1) ? 2 : 1;
+    const int sg = s + I.s0;  // the shift's index in the instance
+    if (sg > 0) {
+        k = (sg - 1) >> 1;
+        which = ((sg - 1) & 1) ? 2 : 1;
     }
     const double2 v = I.cs[(a == k ? which : 0) * I.P + a];
     c = (R)v.x;
@@ -825,93 +828,108 @@ int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, 
 // laid out as the 128 x 64 matrix Z whose rows 0..63 hold phi_l on the first
 // half of the stage's amplitudes and rows 64..127 phi_l on the second half, so
 //   G~_lm = sum over stages of (Z Z^T)[l][m] + (Z Z^T)[64+l][64+m]
-// (the two diagonal quadrants; the off-diagonal ones are not used).  The B
-// operand carries four more rows, Re b and Im b on each half of the stage, so
-// the same MMA also gives delta_l = sum_j conj(b_j) phi_l[j] in columns
-// 128..131 of the accumulator (M = 128, N = 144, K = 16: 32 amplitudes of 64
-// terms and of b per instruction).
-// Every entry of 2^12 Z (and of 2^e b, e from ||b||) is split x = hi + lo into
-// two FP16 numbers (round to nearest; the scale keeps lo clear of FP16
-// subnormals for amplitudes above ~3e-5, and below that lo's absolute error
-// stays under 2^-37) and Z B^T ~ hi hi^T + hi lo^T + lo hi^T (lo lo^T, ~2^-22
-// relative, dropped): three tcgen05.mma kind::f16 per k-step with FP32
-// accumulation in tensor memory.  FP16 carries the 11-bit significand of TF32
-// at twice its tensor rate and half its operand bytes.  The state is split
-// once per item (packed hi | lo << 16 per amplitude) and kept in four copies
-// (copy t holds psi[k ^ t]), so a term's 16 amplitudes of a block are four
-// aligned 16-byte loads; a term value then costs a quarter load, half a byte
-// permute and one three-input XOR (the sign) per packed pair.
+// (the two diagonal quadrants; the off-diagonal ones are not used).
 //
-// A kernel that allocates tensor memory runs one CTA per SM, so a CTA holds
-// two independent pipelines of 8 warps.  Each takes items from the queue with
-// its own named barrier, half of the shared memory and 256 tensor-memory
-// columns; one pipeline's state preparation, operand building and epilogue
-// overlap the other's MMAs.  Within a pipeline all threads stage the operands
-// in shared memory (K-major, no swizzle: core matrices of 8 rows x 16 bytes;
-// LBO 128 B between the two halves of a k-step, SBO 256 B between 8-row
-// groups, 18 row groups per k-step), two stages deep; one thread issues the
-// MMAs and commits each stage to an mbarrier (bounded polls).
-// The tensor core folds each MMA's sum into the accumulator with a rounding
-// that is not to nearest (measured with TF32 operands: a one-sided drift of
-// ~2^-24 |acc| per MMA, 1.2e-5 on a unit diagonal after 384 MMAs).  So the
-// accumulator (columns 0..143 of a pipeline) restarts every TC_FLUSH stages
-// and the used parts of each block (the two diagonal Gram quadrants, two delta
-// columns per lane) are added into FP32 running sums (columns 144..209) with
-// round-to-nearest adds: the drift is bounded by the MMAs of one block.  The
-// epilogue adds the two quadrants into G~ and weights it in float-float
-// arithmetic (two-product by FMA, two-sum; ~2^-44 relative), since FP64
-// instructions issue at 1/64 of the FP32 rate on this part; only the last
-// partial sums per pipeline are added in FP64.
+// Split.  Every entry of 2^12 Z (and of 2^e b, e from ||b||) is split
+// x = hi + lo into FP16 (round to nearest; the scale keeps lo clear of FP16
+// subnormals for amplitudes above ~3e-5, and below that lo's absolute error
+// stays under 2^-37), and Z Z^T ~ hi hi^T + hi lo^T + lo hi^T (lo lo^T, ~2^-22
+// relative, dropped).  Only sum_lm Re(w_lm) G~_lm is formed and Re(w) is
+// symmetric, so hi lo^T + lo hi^T may be replaced by hi (2 lo)^T: the
+// accumulator holds G' = hi hi^T + hi (2 lo)^T, whose symmetric part is G~.
+// That is two tcgen05.mma kind::f16 per k-step of 16 amplitudes instead of
+// three: (A = hi, B = hi, N = 144) and (A = hi, B = 2 lo, N = 128).  The first
+// B also carries the rows hi and lo of Re b and Im b on both halves of the
+// stage (accumulator columns 128..135), and a narrow third MMA (A = 2 lo,
+// B = hi(b) / 2, N = 16) adds lo hi(b) into columns 128..131, so
+// delta_l = sum_j conj(b_j) phi_l[j] comes out of the same accumulator.
+// FP16 carries the 11-bit significand of TF32 at twice its tensor rate and
+// half its operand bytes.
+//
+// Work split.  The shifted states are built before the term kernel
+// (k_tc_states; packed pairs hi | (2 lo) << 16 of 2^12 psi, L2-resident), so
+// the term kernel only streams.  One CTA per SM (it allocates tensor memory)
+// with three warp roles:
+//   - 16 builder warps take items from the queue, load an item's state into
+//     shared memory in four copies (copy t holds psi[k ^ t], so a term's 16
+//     amplitudes of a block are four aligned 16-byte loads: the low two bits
+//     of x_l pick the copy, the next two permute the loads), and write the
+//     operands of each stage (K-major, no swizzle: core matrices of 8 rows x
+//     16 bytes; LBO 128 B between the two halves of a k-step, SBO 256 B between
+//     8-row groups, 18 row groups per k-step) into a ring of TC_NSTG stages,
+//     one 16-amplitude half-row of one term per thread;
+//   - one MMA warp issues each stage into the accumulator of its block and
+//     commits the stage's buffer back to the builders;
+//   - 4 epilogue warps (one per quarter of the tensor-memory lanes) fold each
+//     finished accumulator block, read out an item's Gram and delta and weight
+//     them, while the builders and the MMA warp go on with the next items.
+// The tensor core adds each MMA's sum into the accumulator with a rounding
+// that is not to nearest (measured: a one-sided drift of ~2^-24 |acc| per
+// MMA), so an accumulator block covers TC_FLUSH stages and the epilogue folds
+// its used parts (the two diagonal Gram quadrants, two delta columns per lane)
+// into FP32 running sums in tensor memory with round-to-nearest adds.  Two
+// accumulators alternate between blocks, so the MMAs of a block never wait for
+// the fold of the previous one.  The weighting runs in float-float arithmetic
+// (two-product by FMA, two-sum; ~2^-44 relative) -- FP64 instructions issue at
+// 1/64 of the FP32 rate on this part -- and only the final partial sums are
+// formed in FP64.
+// Every wait is bounded (a time budget, set per context); a role whose wait
+// gives up raises the abort flag, every role stops at its next check, the MMA
+// warp waits for its issued MMAs before the tensor memory is freed, and the
+// host gets DVQLS_ERR_TIMEOUT.
 // Served for tiles with L <= 64 (T = 1) of the global cost.
-constexpr int TCK = 128;       // amplitudes per stage: 2 x 64, i.e. 4 MMA k-steps of 16 in each row half
-constexpr int TCH = 256;       // threads per pipeline
-constexpr int TCT = 2 * TCH + 32;  // threads per CTA: two builder pipelines and the MMA issuer warp
-constexpr int TC_FLUSH = 4;    // stages per accumulator block (16 MMAs of each pass: max |beta| error 3.4e-6 to n = 14)
-constexpr int TC_COLS = 256;   // TMEM columns per pipeline
-constexpr int TC_NB = 144;     // B rows: 128 term rows, then Re b / Im b of both halves (4 rows) and 12 unused
-constexpr int TC_SUM = 144;    // TMEM: running sum of the Gram quadrants (64 columns)
-constexpr int TC_DSUM = 208;   // TMEM: running sum of the two delta columns of a lane
+constexpr int TCK = 128;            // amplitudes per stage: 2 x 64, i.e. 4 MMA k-steps of 16 in each row half
+constexpr int TC_BW = 16;           // builder warps
+constexpr int TC_BT = 32 * TC_BW;   // builder threads: one 16-amplitude half-row of one term per stage each
+constexpr int TC_EW = 4;            // epilogue warps, one per quarter of the tensor-memory lanes
+constexpr int TC_ET = 32 * TC_EW;
+constexpr int TCT = TC_BT + 32 + TC_ET;  // builders, the MMA warp, the epilogue warps
+constexpr int TC_NSTG = 4;          // operand stages in flight
+constexpr int TC_NIT = 4;           // item records in flight from the builders to the epilogue
+constexpr int TC_FLUSH = 4;         // stages per accumulator block (8 MMAs of each Gram entry per stage)
+constexpr int TC_NB = 144;          // B rows: 128 term rows, hi and lo of b (8 rows), 8 zero rows
+constexpr uint32_t TC_ACC1 = 256;   // tensor-memory column of the second accumulator (the first starts at 0)
+constexpr int TC_SUM = 144;         // tensor memory: running sums of the Gram quadrants (64 columns) ...
+constexpr int TC_DSUM = 208;        // ... and of the two delta columns of a lane
+constexpr int TC_COLS = 512;        // tensor-memory columns allocated
 // kind::f16 instruction descriptor: F32 accumulator (bits 4-5 = 1), A and B
 // FP16 (bits 7-9, 10-12 = 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t TC_IDESC = (1u << 4) | ((uint32_t(TC_NB) >> 3) << 17) | ((128u >> 4) << 24);
-constexpr long long TC_POLLS = 1LL << 26;
+constexpr uint32_t tc_idesc(uint32_t nn) { return (1u << 4) | ((nn >> 3) << 17) | ((128u >> 4) << 24); }
+constexpr long long TC_DRAIN_NS = 1000000000LL;  // 1 s for issued MMAs to complete (they take microseconds)
 constexpr float TC_SCALE = 4096.f;                     // 2^12 on the state
 constexpr float TC_UNSCALE = 1.f / (4096.f * 4096.f);  // 2^-24 on the Gram
-constexpr int TC_KSTEP_BYTES = (TC_NB / 8) * 2 * 128;           // 18 row groups x 2 halves x 128 B
-constexpr int TC_OPND_BYTES = (TCK / 32) * TC_KSTEP_BYTES;      // one operand array (hi or lo) of a stage
+constexpr int TC_KSTEP_BYTES = (TC_NB / 8) * 2 * 128;       // 18 row groups x 2 halves x 128 B
+constexpr int TC_OPND_BYTES = (TCK / 32) * TC_KSTEP_BYTES;  // one operand array (hi or 2 lo) of a stage
 constexpr int TC_STAGE_BYTES = 2 * TC_OPND_BYTES;
-constexpr int TC_X = 64 * 65;                                   // readout floats: lower quadrant, then G~ [64][65]
-constexpr int TC_REGION_BYTES = 2 * TC_STAGE_BYTES;
-constexpr int TC_BOP_STAGE = 1024;  // bytes of the b rows of one stage (hi and lo)
-static_assert(TC_REGION_BYTES >= (2 * TC_X + 128) * 4, "the readout fits the two stages");
-static_assert(TC_REGION_BYTES >= 2 * (4096 + 128) * 4, "the state transposes fit the two stages");
+constexpr int TC_BROW = 16 * 256;   // offset of row group 16 (the b rows) inside a k-step
+constexpr int TC_X = 64 * 65;       // readout floats of one Gram quadrant ([64][65])
+constexpr int TC_EPI_BYTES = 2 * TC_X * 4 + 2 * 64 * 8;  // both quadrants and their delta sums
+constexpr int TC_BOP_STAGE = 2048;  // bytes of the b rows of one stage (both operand arrays)
+constexpr uint32_t TC_EXIT = 0xFFFFFFFFu;  // stage record of builders that have no more items
+static_assert(TC_STAGE_BYTES % 1024 == 0, "stages keep the 1024-byte alignment of the ring");
 
 // States in shared memory of 2^4 .. 2^copy_nmax amplitudes are kept in four
-// copies, copy t holding psi[k ^ t] at word t (N + 8) + k: a term's 16
-// amplitudes of a block are then four aligned 16-byte loads in order (the low
-// two bits of x_l pick the copy, the next two permute the loads), and the
-// copies start 32 bytes apart in the banks.  copy_nmax <= TC_COPY_NMAX is
-// chosen per batch so that both pipelines still fit one CTA.
+// copies, copy t holding psi[k ^ t] at word t (N + 8) + k; the copies start 32
+// bytes apart in the banks.  copy_nmax <= TC_COPY_NMAX is chosen per batch so
+// that the CTA's shared memory fits.
 constexpr int TC_COPY_NMAX = 11;
 __host__ __device__ inline size_t tc_psi_bytes(int n, bool copies) {
     const size_t N = size_t(1) << n;
-    return copies ? 4 * (4 * N + 32) : ((N * 4 + 7) & ~size_t(7));
+    return copies ? 4 * (4 * N + 32) : ((N * 4 + 15) & ~size_t(15));
 }
 __host__ __device__ inline bool tc_copies(int n, int copy_nmax) { return n >= 4 && n <= copy_nmax; }
-// Shared bytes of one pipeline for states of up to 2^nmax amplitudes in
-// shared memory (0: states in HBM), copies up to 2^copy_nmax and Pmax angles,
-// and of the whole CTA.
-inline size_t tc_half_bytes(int nmax_smem, int Pmax, int copy_nmax) {
+// Shared bytes of the term kernel for states of up to 2^nmax amplitudes in
+// shared memory (0: every state in HBM) and copies up to 2^copy_nmax.
+inline size_t tc_psi_region(int nmax_smem, int copy_nmax) {
     size_t psi = 0;
     if (nmax_smem > 0) {
         const int nc = std::min(nmax_smem, copy_nmax);
         psi = std::max(tc_psi_bytes(nmax_smem, tc_copies(nmax_smem, copy_nmax)), tc_psi_bytes(nc, tc_copies(nc, copy_nmax)));
     }
-    const size_t off = (psi + (size_t)Pmax * 8 + 1023) & ~size_t(1023);
-    return off + TC_REGION_BYTES;
+    return (psi + 1023) & ~size_t(1023);
 }
-inline size_t tc_smem_bytes(int nmax_smem, int Pmax, int copy_nmax) {
-    return 2 * tc_half_bytes(nmax_smem, Pmax, copy_nmax) + 1024;
+inline size_t tc_smem_bytes(int nmax_smem, int copy_nmax) {
+    return 1024 + (size_t)TC_NSTG * TC_STAGE_BYTES + tc_psi_region(nmax_smem, copy_nmax) + TC_EPI_BYTES;
 }
 // Stages of the b rows of an instance with 2^n amplitudes.
 __host__ __device__ inline long long tc_bop_stages(long long N) { return (N + TCK - 1) / TCK; }
@@ -923,33 +941,37 @@ __device__ __forceinline__ float tc_bscale(double bn2) {
     return ldexpf(1.f, 12 - ex);
 }
 
-// The b rows of the B operand, stage by stage, as FP16 hi / lo in the
-// shared-memory order of one stage: [hi, lo][k-step 0..3][half 0..1][row
-// 128..131][8 values], rows Re b and Im b of the stage's first half (128, 129)
-// and of its second half (130, 131), scaled by tc_bscale.  Grid (instances,
-// parts) of 256 threads, after k_prepare (which forms ||b||^2).
-// The b rows of the tensor-core B operand for stages blk, blk + nblk, ...
-// (chunks of 8 amplitudes, FP16 hi / lo of b scaled by tc_bscale(||b||^2)).
+// The b rows of both B operands for stages blk, blk + nblk, ..., in the
+// shared-memory order of a stage's row group 16: [array (hi, 2 lo)][k-step
+// 0..3][k half 0..1][row 0..7][8 FP16 values].  Array hi: rows 0..3 hold hi of
+// Re b and Im b on the stage's first half and on its second half, rows 4..7
+// their lo parts; array 2 lo: rows 0..3 hold hi / 2 (exact), rows 4..7 zero.
+// b is scaled by tc_bscale(||b||^2).
 __device__ __forceinline__ void tc_fill_bop(const Inst& I, double bn2, int blk, int nblk) {
     const long long N = 1LL << I.n, chunks = tc_bop_stages(N) * (TC_BOP_STAGE / 16);
     const float sb = tc_bscale(bn2);
     for (long long c = (long long)blk * 256 + threadIdx.x; c < chunks; c += 256LL * nblk) {
-        const long long stage = c >> 6;
-        const int u = int(c & 63), which = u >> 5, ks4 = (u >> 3) & 3, hh = (u >> 2) & 1, row = u & 3;
-        uint32_t w[4];
+        const long long stage = c >> 7;
+        const int u = int(c & 127), arr = u >> 6, ks4 = (u >> 4) & 3, kh = (u >> 3) & 1, row = u & 7;
+        const int part = row >> 2, r4 = row & 3;  // part 0: hi, 1: lo; r4: (half, Re / Im)
+        uint32_t wv[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-            float x[2];
+            uint16_t hv[2];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-                const long long j = stage * TCK + (row >= 2 ? TCK / 2 : 0) + ks4 * 16 + hh * 8 + e + q;
-                const double v = j < N ? ((row & 1) ? I.b[j].y : I.b[j].x) : 0.0;
-                x[q] = (float)(v * (double)sb);
+                const long long j = stage * TCK + (r4 >= 2 ? TCK / 2 : 0) + ks4 * 16 + kh * 8 + e + q;
+                const double v = j < N ? ((r4 & 1) ? I.b[j].y : I.b[j].x) : 0.0;
+                const float x = (float)(v * (double)sb);
+                const __half h = __float2half_rn(x);
+                __half o;
+                if (arr == 0) o = part == 0 ? h : __float2half_rn(x - __half2float(h));
+                else o = part == 0 ? __float2half_rn(0.5f * __half2float(h)) : __float2half_rn(0.f);
+                hv[q] = __half_as_ushort(o);
             }
-            const uint32_t a = split_hl(x[0]), b = split_hl(x[1]);
-            w[e >> 1] = which ? ((a >> 16) | (b & 0xFFFF0000u)) : ((a & 0xFFFFu) | (b << 16));
+            wv[e >> 1] = (uint32_t)hv[0] | ((uint32_t)hv[1] << 16);
         }
-        reinterpret_cast<uint4*>(I.bop)[c] = make_uint4(w[0], w[1], w[2], w[3]);
+        reinterpret_cast<uint4*>(I.bop)[c] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
     }
 }
 // States of up to this many amplitudes get their b rows from the prepare
@@ -1050,6 +1072,65 @@ __global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, 
     }
 }
 
+// Shifted states of the on-chip instances of a tensor-core pass (Stage I):
+// 2^12 psi_s as packed pairs (split_h2l), S x N words per instance in
+// workspace (I.tcst), built once per (instance, shift) before the term kernel.
+// Grid (jobs, instances) of 256 threads: n <= 10 builds eight states per CTA,
+// one per warp, in registers (qubits on lane bits by shuffles, the others in
+// place) with no barrier; n = 11, 12 build one state per CTA with the
+// 256-thread builder and copy it out.
+constexpr int TCS_WARP_NMAX = 10;
+__host__ __device__ inline int tcs_jobs(int n, int S) { return n <= TCS_WARP_NMAX ? (S + 7) / 8 : S; }
+__host__ __device__ inline size_t tcs_smem(int n, int P) {
+    const size_t N = size_t(1) << n;
+    return n <= TCS_WARP_NMAX ? 8 * (size_t)P * sizeof(float2)
+                              : N * 4 + 2 * (N + N / 32) * 4 + (size_t)P * sizeof(float2);
+}
+
+__global__ void __launch_bounds__(256) k_tc_states(const Inst* __restrict__ insts) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Inst& I = insts[blockIdx.y];
+    if (!I.tcst) return;
+    const int n = I.n, N = 1 << n, P = I.P, t = threadIdx.x, w = t >> 5, lane = t & 31;
+    uint32_t* out = reinterpret_cast<uint32_t*>(I.tcst);
+    if (n <= TCS_WARP_NMAX) {
+        const int s = blockIdx.x * 8 + w;
+        if (s >= I.S) return;  // this warp only: nothing below waits on other warps
+        float2* scs = reinterpret_cast<float2*>(smem) + (size_t)w * P;
+        int k = -1, which = 0;
+        const int sg = s + I.s0;  // the shift's index in the instance
+        if (sg > 0) {
+            k = (sg - 1) >> 1;
+            which = ((sg - 1) & 1) ? 2 : 1;
+        }
+        for (int a = lane; a < P; a += 32) {
+            const double2 v = I.cs[(a == k ? which : 0) * P + a];
+            scs[a] = make_float2((float)v.x, (float)v.y);
+        }
+        __syncwarp();
+        void* psi = out + (size_t)s * N;
+        switch (n) {
+            case 6: state_regs_warp<2, 1, true>(psi, scs, n, I.d, lane, TC_SCALE); break;
+            case 7: state_regs_warp<4, 2, true>(psi, scs, n, I.d, lane, TC_SCALE); break;
+            case 8: state_regs_warp<8, 3, true>(psi, scs, n, I.d, lane, TC_SCALE); break;
+            case 9: state_regs_warp<16, 4, true>(psi, scs, n, I.d, lane, TC_SCALE); break;
+            case 10: state_regs_warp<32, 5, true>(psi, scs, n, I.d, lane, TC_SCALE); break;
+            default: state_regs_warp<1, 0, true>(psi, scs, n, I.d, lane, TC_SCALE); break;  // n <= 5
+        }
+        return;
+    }
+    const int s = blockIdx.x;
+    if (s >= I.S) return;  // the whole CTA
+    uint32_t* psi = reinterpret_cast<uint32_t*>(smem);
+    float* scratch = reinterpret_cast<float*>(smem + (size_t)N * 4);
+    float2* scs = reinterpret_cast<float2*>(smem + (size_t)N * 4 + 2 * (size_t)(N + N / 32) * 4);
+    build_state_regs<true>(psi, scratch, scs, n, I.d, P, I.cs, s + I.s0, t, 0, TC_SCALE);  // ends with a barrier
+    uint4* dst = reinterpret_cast<uint4*>(out + (size_t)s * N);
+    for (int c = t; c < N / 4; c += 256) dst[c] = reinterpret_cast<const uint4*>(psi)[c];
+}
+
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
@@ -1060,17 +1141,52 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
     return d;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-    for (long long it = 0; it < TC_POLLS; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(phase)
-            : "memory");
-        if (done) return true;
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for phase `phase` of an mbarrier for at most budget_ns nanoseconds of
+// the global timer (and at most 2^32 tries, should the timer not advance).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long budget_ns) {
+    if (mbar_try(bar, phase)) return true;
+    const unsigned long long t0 = gtimer_ns();
+    for (long long it = 0; it < (1LL << 32); ++it) {
+        if (mbar_try(bar, phase)) return true;
+        if ((long long)(gtimer_ns() - t0) > budget_ns) return false;
     }
     return false;
+}
+// The abort flag as other roles may have just written it.
+__device__ __forceinline__ bool aborted(const int* f) { return *reinterpret_cast<const volatile int*>(f) != 0; }
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(bar) : "memory");
+}
+
+// Named barrier of `nthreads` threads that also returns the OR of a predicate
+// over them: every thread gets the same answer, so a group decides to stop
+// together.
+__device__ __forceinline__ bool bar_or(int id, int nthreads, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void bar_n(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 // Byte offset of Z[row][kk .. kk+7] (FP16, kk a multiple of 8 below TCK/2)
@@ -1078,8 +1194,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
 __device__ __forceinline__ int tc_off16(int row, int kk) {
     return (((kk >> 4) * (TC_NB / 8) + (row >> 3)) * 2 + ((kk >> 3) & 1)) * 128 + (row & 7) * 16;
 }
-
-__device__ __forceinline__ void half_sync(int bar) { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(TCH) : "memory"); }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
@@ -1118,275 +1232,235 @@ __device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v) {
                  : "memory");
 }
 
-// Adds the used parts of a pipeline's block accumulator into its running sums,
-// or starts the sums with them: the two diagonal Gram quadrants (lanes 0..63 x
-// columns 0..63 and lanes 64..127 x columns 64..127, into columns 144..207)
-// and each lane's two delta columns (128, 129 for lanes 0..63, which carry the
-// first half of a stage; 130, 131 for lanes 64..127; into columns 208, 209).
-// Warp wl of the pipeline owns TMEM lanes 32 (wl % 4) .. + 31 (the lanes its
-// position in the warpgroup may access) and 32 of its quadrant's columns; warps
-// 0..3 also take the delta columns.  On the last block, lanes 64..127 go to
-// X[row - 64][col - 64] and XD[row - 64] in shared memory for the readout.
-__device__ __forceinline__ void tc_flush(uint32_t tmem, int wl, int lane, bool first, bool last, float* X, float2* XD) {
-    const uint32_t lrow = 32u * uint32_t(wl & 3);
-    const int c0 = (wl >> 2) * 32;  // column within the quadrant
-    const int cq = lrow < 64 ? 0 : 64;
-    const uint32_t base = tmem + (lrow << 16);
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-        const int col = c0 + 16 * g;
+// One finished accumulator block (columns acc ..) folded by an epilogue warp
+// whose tensor-memory lanes are 32 q .. 32 q + 31: lanes 0..63 carry the first
+// half of every stage (Gram columns 0..63; delta columns 128, 129 from hi b
+// and 132, 133 from lo b), lanes 64..127 the second half (columns 64..127;
+// delta 130, 131 and 134, 135).  The first block of an item starts the running
+// sums (columns TC_SUM.., TC_DSUM..), later ones add to them with
+// round-to-nearest adds; the last block goes to X[half][row][col] and
+// XD[half][row] in shared memory instead.
+__device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t acc, int q, int lane, bool first, bool last, float* X,
+                                        float2* XD) {
+    const uint32_t base = tmem + ((32u * uint32_t(q)) << 16);
+    const int cq = q < 2 ? 0 : 64, dq = q < 2 ? 0 : 2;
+    const int xr = (q & 1) * 32 + lane;  // row within the half
+    float* Xq = X + (q >> 1) * TC_X;
+#pragma unroll 1
+    for (int g = 0; g < 4; ++g) {
         float v[16];
-        tmem_ld16(base + cq + col, v);
+        tmem_ld16(base + acc + cq + 16 * g, v);
         if (!first) {
             float u[16];
-            tmem_ld16(base + TC_SUM + col, u);
+            tmem_ld16(base + TC_SUM + 16 * g, u);
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] += u[j];
         }
-        if (last && lrow >= 64) {
-            const int row = int(lrow) + lane - 64;
+        if (last) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) X[row * 65 + col + j] = v[j];
+            for (int j = 0; j < 16; ++j) Xq[xr * 65 + 16 * g + j] = v[j];
         } else {
-            tmem_st16(base + TC_SUM + col, v);
+            tmem_st16(base + TC_SUM + 16 * g, v);
         }
     }
-    if ((wl >> 2) == 0) {
-        float2 dv = tmem_ld2(base + 128 + (lrow < 64 ? 0 : 2));
-        if (!first) {
-            const float2 du = tmem_ld2(base + TC_DSUM);
-            dv.x += du.x;
-            dv.y += du.y;
-        }
-        if (last && lrow >= 64) XD[int(lrow) + lane - 64] = dv;
-        else tmem_st2(base + TC_DSUM, dv);
+    const float2 d0 = tmem_ld2(base + acc + 128 + dq), d1 = tmem_ld2(base + acc + 132 + dq);
+    float2 dv = make_float2(d0.x + d1.x, d0.y + d1.y);
+    if (!first) {
+        const float2 du = tmem_ld2(base + TC_DSUM);
+        dv.x += du.x;
+        dv.y += du.y;
     }
+    if (last) XD[(q >> 1) * 64 + xr] = dv;
+    else tmem_st2(base + TC_DSUM, dv);
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// Builds the FP16 hi / lo operands of term l for MMA k-step `sub` of a stage:
-// the 16 amplitudes at jb = j0 + sub * 16 (row l) and at jb + TCK/2 (row
-// 64 + l).  With jb a multiple of 16, the sources j ^ x_l of a block are
-// rb | (i ^ xlo) with rb = (jb ^ x_l) & ~15: a permutation of 16 consecutive
-// amplitudes, whose signs are the parity of z_l & rb times the per-term 16-bit
-// pattern smask (bit i: parity of z_l & (i ^ xlo)).  psi_hl holds 2^12 psi as
-// packed FP16 (hi, lo) (shared memory); psi_g the FP32 real state in HBM.
+// A builder thread's share of a stage: the 16 amplitudes jb .. jb + 15 of term
+// l's row `row` (l, or 64 + l for the stage's second half) at k = kk0 ..
+// kk0 + 15 of its half.  With jb a multiple of 16, the sources j ^ x_l of the
+// block are rb | (i ^ xlo) with rb = (jb ^ x_l) & ~15: a permutation of 16
+// consecutive amplitudes, whose signs are the parity of z_l & rb times the
+// per-term 16-bit pattern sgn (bit i: parity of z_l & (i ^ xlo)).  psi_hl holds
+// the packed pairs (shared memory; four copies when `copies`), psi_g the FP32
+// state in HBM.
 template <bool HBM>
-__device__ __forceinline__ void tc_build_stage(const uint32_t* psi_hl, const float* psi_g, int N, int j0, int kend,
-                                               bool act, uint32_t xl, uint32_t zl, const uint32_t (&sgn)[8], int sub,
-                                               int l, unsigned char* zhi, unsigned char* zlo, bool copies) {
+__device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const float* psi_g, int N, int jb, int kend,
+                                              bool act, uint32_t xl, uint32_t zl, const uint32_t (&sgn)[8], int row,
+                                              int kk0, unsigned char* zhi, unsigned char* zlo, bool copies) {
     const uint32_t xhi = xl & ~15u, xlo = xl & 15u & uint32_t(N - 1);
-    const uint32_t* cpy = psi_hl + (xlo & 3u) * uint32_t(N + 8);  // copy holding psi[k ^ (x_l & 3)]
-    const uint32_t xc = xlo >> 2;
-#pragma unroll 1
-    for (int hf = 0; hf < 2; ++hf) {
-        const int jb = j0 + hf * (TCK / 2) + sub * 16;
-        const int nval = act ? min(16, max(0, kend - jb)) : 0;
-        const uint32_t rb = (uint32_t(jb) ^ xhi) & uint32_t(N - 1) & ~15u;
-        const uint32_t flip = (__popc(zl & rb) & 1) ? 0x80008000u : 0u;  // the block's common sign
-        uint32_t w[16];
-        if (!HBM && copies && nval == 16) {
-            // w[4c + r] = psi[rb + 4 (c ^ xc) + (r ^ (x_l & 3))] = cpy[rb + 4 (c ^ xc) + r]
+    const int nval = act ? min(16, max(0, kend - jb)) : 0;
+    const uint32_t rb = (uint32_t(jb) ^ xhi) & uint32_t(N - 1) & ~15u;
+    const uint32_t flip = (__popc(zl & rb) & 1) ? 0x80008000u : 0u;  // the block's common sign
+    uint32_t w[16];
+    if (!HBM && copies && nval == 16) {
+        // w[4c + r] = psi[rb + 4 (c ^ xc) + (r ^ (x_l & 3))] = cpy[rb + 4 (c ^ xc) + r]
+        const uint32_t* cpy = psi_hl + (xlo & 3u) * uint32_t(N + 8);  // copy holding psi[k ^ (x_l & 3)]
+        const uint32_t xc = xlo >> 2;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const uint4 v = *reinterpret_cast<const uint4*>(cpy + rb + 4u * (uint32_t(c) ^ xc));
-                w[4 * c + 0] = v.x;
-                w[4 * c + 1] = v.y;
-                w[4 * c + 2] = v.z;
-                w[4 * c + 3] = v.w;
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                uint32_t x = 0u;
-                if (i < nval) {
-                    const uint32_t src = rb | (uint32_t(i) ^ xlo);
-                    x = HBM ? split_hl(psi_g[src] * TC_SCALE) : psi_hl[src];
-                }
-                w[i] = x;
-            }
+        for (int c = 0; c < 4; ++c) {
+            const uint4 v = *reinterpret_cast<const uint4*>(cpy + rb + 4u * (uint32_t(c) ^ xc));
+            w[4 * c + 0] = v.x;
+            w[4 * c + 1] = v.y;
+            w[4 * c + 2] = v.z;
+            w[4 * c + 3] = v.w;
         }
-        const int row = hf ? 64 + l : l;
+    } else {
 #pragma unroll
-        for (int g = 0; g < 2; ++g) {
-            // Sign bits of packed pairs sit at bits 15 and 31 of a hi (or lo)
-            // word: one three-input XOR applies the term's and the block's sign.
-            uint4 hi, lo;
-            hi.x = __byte_perm(w[8 * g + 0], w[8 * g + 1], 0x5410) ^ sgn[4 * g + 0] ^ flip;
-            hi.y = __byte_perm(w[8 * g + 2], w[8 * g + 3], 0x5410) ^ sgn[4 * g + 1] ^ flip;
-            hi.z = __byte_perm(w[8 * g + 4], w[8 * g + 5], 0x5410) ^ sgn[4 * g + 2] ^ flip;
-            hi.w = __byte_perm(w[8 * g + 6], w[8 * g + 7], 0x5410) ^ sgn[4 * g + 3] ^ flip;
-            lo.x = __byte_perm(w[8 * g + 0], w[8 * g + 1], 0x7632) ^ sgn[4 * g + 0] ^ flip;
-            lo.y = __byte_perm(w[8 * g + 2], w[8 * g + 3], 0x7632) ^ sgn[4 * g + 1] ^ flip;
-            lo.z = __byte_perm(w[8 * g + 4], w[8 * g + 5], 0x7632) ^ sgn[4 * g + 2] ^ flip;
-            lo.w = __byte_perm(w[8 * g + 6], w[8 * g + 7], 0x7632) ^ sgn[4 * g + 3] ^ flip;
-            const int kk = sub * 16 + 8 * g;  // k within the stage's TCK/2
-            *reinterpret_cast<uint4*>(zhi + tc_off16(row, kk)) = hi;
-            *reinterpret_cast<uint4*>(zlo + tc_off16(row, kk)) = lo;
+        for (int i = 0; i < 16; ++i) {
+            uint32_t x = 0u;
+            if (i < nval) {
+                const uint32_t src = rb | (uint32_t(i) ^ xlo);
+                x = HBM ? split_h2l(psi_g[src] * TC_SCALE) : psi_hl[src];
+            }
+            w[i] = x;
         }
+    }
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        // Sign bits of packed pairs sit at bits 15 and 31 of a hi (or 2 lo)
+        // word: one three-input XOR applies the term's and the block's sign.
+        uint4 hi, lo;
+        hi.x = __byte_perm(w[8 * g + 0], w[8 * g + 1], 0x5410) ^ sgn[4 * g + 0] ^ flip;
+        hi.y = __byte_perm(w[8 * g + 2], w[8 * g + 3], 0x5410) ^ sgn[4 * g + 1] ^ flip;
+        hi.z = __byte_perm(w[8 * g + 4], w[8 * g + 5], 0x5410) ^ sgn[4 * g + 2] ^ flip;
+        hi.w = __byte_perm(w[8 * g + 6], w[8 * g + 7], 0x5410) ^ sgn[4 * g + 3] ^ flip;
+        lo.x = __byte_perm(w[8 * g + 0], w[8 * g + 1], 0x7632) ^ sgn[4 * g + 0] ^ flip;
+        lo.y = __byte_perm(w[8 * g + 2], w[8 * g + 3], 0x7632) ^ sgn[4 * g + 1] ^ flip;
+        lo.z = __byte_perm(w[8 * g + 4], w[8 * g + 5], 0x7632) ^ sgn[4 * g + 2] ^ flip;
+        lo.w = __byte_perm(w[8 * g + 6], w[8 * g + 7], 0x7632) ^ sgn[4 * g + 3] ^ flip;
+        const int kk = kk0 + 8 * g;  // k within the stage's TCK/2
+        *reinterpret_cast<uint4*>(zhi + tc_off16(row, kk)) = hi;
+        *reinterpret_cast<uint4*>(zlo + tc_off16(row, kk)) = lo;
     }
 }
 
-// One non-blocking look at an mbarrier phase.
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t phase) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(phase)
-        : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(bar) : "memory");
-}
-
-constexpr uint32_t TC_EXIT = 0xFFFFFFFFu;  // stage record of a pipeline that has no more items
-constexpr long long TC_IDLE_POLLS = 1LL << 30;
-
-// Warp roles: warps 0..7 and 8..15 are the two builder pipelines; warp 16
-// issues the MMAs of both.  A pipeline hands a stage over by arriving on its
-// `full` mbarrier (all 256 threads, after a proxy fence); the stage record
-// (shared address of the hi operands, first-of-block flag) is written before.
-// The issuer commits each stage's MMAs to the stage's `empty` mbarrier, which
-// the builders wait on before they write the buffer again or read the
-// accumulator.  Neither side waits at a CTA barrier per stage.
+// Warp roles: warps 0..15 build operands, warp 16 issues the MMAs, warps
+// 17..20 run the epilogue.  Hand-overs: a stage by its `full` mbarrier (all
+// builder threads arrive after a proxy fence; the stage record -- address of
+// the hi array, first / last stage of an accumulator block -- is written
+// first) and back by `empty` (the MMA warp's commit); an accumulator block by
+// `accf` (commit after its last stage) and back by `acce` (every epilogue
+// thread, after its tensor-memory loads); an item record (instance, shift,
+// amplitude part, stages) from the builders to the epilogue by `itf` and back
+// by `ite`.  Every wait gives up after budget_ns nanoseconds; a thread that has
+// seen the abort flag waits no more.
 __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ insts, int count, long long total,
-                                                     unsigned long long* queue, int* status, int half_bytes,
-                                                     int copy_nmax) {
+                                                     unsigned long long* queue, int* status, int copy_nmax,
+                                                     int psi_region, long long budget_ns) {
     pdl_wait();
     pdl_trigger();
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ __align__(8) unsigned long long full[2][2], empty[2][2];
-    __shared__ uint32_t srec[2][2][2];  // per pipeline and buffer: hi operand address, first-of-block flag
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long fullb[TC_NSTG], emptyb[TC_NSTG], accf[2], acce[2], itf[TC_NIT],
+        ite[TC_NIT], drainb;
+    __shared__ uint32_t srec[TC_NSTG][2];
+    __shared__ int4 irec[TC_NIT];
     __shared__ uint32_t s_tmem;
-    __shared__ long long s_item[2];
-    __shared__ int s_abort[3];  // per pipeline (set by its own threads), and the issuer
-    __shared__ uint32_t sxl[2][TT], szl[2][TT];
-    __shared__ float sred[2][3][2][8];  // per pipeline: D, Re T, Im T as float-float, per warp
+    __shared__ long long s_item;
+    __shared__ int s_abort;
+    __shared__ uint32_t sxl[64], szl[64];
+    __shared__ float sred[3][2][TC_EW];
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    if (t == 0) {
-        for (int k = 0; k < 4; ++k) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&full[k >> 1][k & 1])), "r"(TCH));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&empty[k >> 1][k & 1])), "r"(1));
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;");
-        s_abort[0] = s_abort[1] = s_abort[2] = 0;
+    unsigned char* base;
+    {
+        const uint32_t a = su32(smem_raw);
+        base = smem_raw + ((1024u - (a & 1023u)) & 1023u);
     }
+    uint32_t* psi_hl = reinterpret_cast<uint32_t*>(base + TC_NSTG * TC_STAGE_BYTES);
+    float* X = reinterpret_cast<float*>(base + TC_NSTG * TC_STAGE_BYTES + psi_region);
+    float2* XD = reinterpret_cast<float2*>(X + 2 * TC_X);
+    if (t == 0) {
+        for (int k = 0; k < TC_NSTG; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&fullb[k])), "r"(TC_BT));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&emptyb[k])), "r"(1));
+        }
+        for (int k = 0; k < 2; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&accf[k])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&acce[k])), "r"(TC_ET));
+        }
+        for (int k = 0; k < TC_NIT; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&itf[k])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ite[k])), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&drainb)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        s_abort = 0;
+    }
+    // Row group 17 of both operand arrays of every stage stays zero (the MMAs
+    // read it as B rows 136..143; nothing writes it later).
+    for (int c = t; c < TC_NSTG * 2 * (TCK / 32) * 16; c += TCT) {
+        const int st = c >> 7, arr = (c >> 6) & 1, ks4 = (c >> 4) & 3, u = c & 15;
+        *reinterpret_cast<uint4*>(base + st * TC_STAGE_BYTES + arr * TC_OPND_BYTES + ks4 * TC_KSTEP_BYTES +
+                                  (17 * 2) * 128 + u * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (w == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
-                     "r"(2 * TC_COLS));
+                     "r"(TC_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
 
-    if (w == 2 * (TCH / 32)) {  // ------------------------------------------------ issuer warp
-        if (lane == 0) {
-            uint32_t fph = 0u, nst = 0u;  // bit 2h+st: parity of full[h][st]; bit h: next buffer of pipeline h
-            bool done0 = false, done1 = false;
-            long long idle = 0;
-            while (!(done0 && done1)) {
-                bool progressed = false;
-                for (int h = 0; h < 2; ++h) {
-                    if (h == 0 ? done0 : done1) continue;
-                    const int st = (nst >> h) & 1, pb = 2 * h + st;
-                    if (!mbar_test(su32(&full[h][st]), (fph >> pb) & 1u)) continue;
-                    fph ^= 1u << pb;
-                    nst ^= 1u << h;
-                    progressed = true;
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t hb = srec[h][st][0], first = srec[h][st][1];
-                    if (hb == TC_EXIT) {
-                        if (h == 0) done0 = true;
-                        else done1 = true;
-                        continue;
-                    }
-                    const uint32_t lb = hb + TC_OPND_BYTES, tm = s_tmem + uint32_t(h * TC_COLS);
-#pragma unroll
-                    for (int ksx = 0; ksx < TCK / 32; ++ksx) {
-                        const uint64_t dh = tc_desc(hb + ksx * TC_KSTEP_BYTES), dl = tc_desc(lb + ksx * TC_KSTEP_BYTES);
-                        const uint32_t acc0 = (first && ksx == 0) ? 0u : 1u;
-                        asm volatile(
-                            "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.eq.b32 q, %4, %4;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %1, %3, p;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %1, %3, q;\n\t}\n" ::"r"(tm),
-                            "l"(dh), "l"(dl), "r"(TC_IDESC), "r"(acc0));
-                    }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        su32(&empty[h][st])));
-                }
-                if (progressed) idle = 0;
-                else if (++idle > TC_IDLE_POLLS) {
-                    s_abort[2] = 1;
-                    break;
-                }
-            }
-        }
-        __syncwarp();
-    } else {  // ------------------------------------------------------------------ builders
-        const int h = t >> 8, tt = t & (TCH - 1), wl = tt >> 5;
-        const int bar = 1 + h;
-        const uint32_t tmem = s_tmem + uint32_t(h * TC_COLS);  // column offset in the low half
-        unsigned char* hbase;
-        {
-            const uint32_t a = su32(smem);
-            hbase = smem + ((1024u - (a & 1023u)) & 1023u) + (size_t)h * half_bytes;
-        }
-        uint32_t phase = 0u, pending = 0u;  // bit st: parity of empty[h][st] to wait for / commit outstanding
-        uint32_t gc = 0u;                   // stages handed over so far (the buffer is gc & 1)
-        // A pipeline checks only its own flag after its barriers (the issuer's
-        // flag can change between two threads' reads; an issuer that gave up
-        // shows here as bounded `empty` waits that give up too).
-        auto abort_seen = [&]() { return s_abort[h]; };
-
+    if (w < TC_BW) {  // ---------------------------------------------------------------- builders
+        const int tt = t;
+        const int l = (tt & 7) | ((w & 7) << 3), sub = (lane >> 3) & 3, hf = w >> 3;
+        uint32_t eph = 0u, pend = 0u;  // bit st: parity of empty[st] to wait for; stage st in flight
+        uint32_t iph = 0u, iused = 0u;  // item ring (thread 0): parity of ite[r]; slot r used before
+        int ir = 0;
+        uint32_t gc = 0u;  // stages handed over so far
+        bool ab = false;   // this thread saw a wait give up (shared with the group at its barriers)
         for (;;) {
-            if (tt == 0) s_item[h] = (s_abort[0] | s_abort[1] | s_abort[2]) ? total : (long long)atomicAdd(queue, 1ull);
-            half_sync(bar);
-            const long long gi = s_item[h];
-            half_sync(bar);
-            if (gi >= total) break;
-            const Inst& I = insts[find_instance(insts, count, gi)];
+            if (tt == 0) s_item = (aborted(&s_abort) || ab) ? total : (long long)atomicAdd(queue, 1ull);
+            ab = bar_or(1, TC_BT, ab);
+            const long long gi = s_item;
+            ab = bar_or(1, TC_BT, ab);
+            if (ab || gi >= total) break;
+            const int ii = find_instance(insts, count, gi);
+            const Inst& I = insts[ii];
             const int local = int(gi - I.item_base);
             const int n = I.n, N = 1 << n, L = I.L, ks = I.ks;
-            const int ksi = local % ks, s = (local / ks) / I.F;
+            const int ksi = local % ks, s = local / ks;
             const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
-            uint32_t* psi_hl = reinterpret_cast<uint32_t*>(hbase);  // 2^12 psi as packed FP16 (hi, lo)
+            const int nch = (kend - kbeg + TCK - 1) / TCK;
+            if (tt == 0) {  // the item's record for the epilogue
+                if ((iused >> ir) & 1u) {
+                    if (!ab && (aborted(&s_abort) || !mbar_wait(su32(&ite[ir]), (iph >> ir) & 1u, budget_ns))) ab = true;
+                    iph ^= 1u << ir;
+                }
+                iused |= 1u << ir;
+                irec[ir] = make_int4(ii, s, ksi, nch);
+                mbar_arrive(su32(&itf[ir]));
+            }
+            ir = (ir + 1) % TC_NIT;
+            if (tt < 64) {
+                sxl[tt] = tt < L ? I.xm[tt] : 0u;
+                szl[tt] = tt < L ? I.zm[tt] : 0u;
+            }
             const float* psi_g = I.states ? reinterpret_cast<const float*>(I.states) + (size_t)s * N : nullptr;
             const bool copies = !I.states && tc_copies(n, copy_nmax);
-            const size_t psi_bytes = I.states ? 0 : tc_psi_bytes(n, copies);
-            float2* scs = reinterpret_cast<float2*>(hbase + psi_bytes);
-            unsigned char* stage0;  // two stages of TC_STAGE_BYTES, then the readout overlay
-            {
-                const size_t off = psi_bytes + (size_t)I.P * 8;
-                stage0 = hbase + ((off + 1023) & ~size_t(1023));
+            if (!I.states) {  // the packed state of shift s (built by k_tc_states)
+                const uint32_t* src = reinterpret_cast<const uint32_t*>(I.tcst) + (size_t)s * N;
+                if (N >= 4) {
+                    for (int k = 4 * tt; k < N; k += 4 * TC_BT)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(psi_hl + k)),
+                                     "l"(__cvta_generic_to_global(src + k))
+                                     : "memory");
+                    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+                } else if (tt < N) {
+                    psi_hl[tt] = src[tt];
+                }
             }
-            if (tt < TT) {
-                sxl[h][tt] = tt < L ? I.xm[tt] : 0u;
-                szl[h][tt] = tt < L ? I.zm[tt] : 0u;
-            }
-            if (I.states) half_sync(bar);
-            else  // in registers; the operand stages are free and serve as transpose scratch; ends with a barrier
-                build_state_regs<true>(psi_hl, reinterpret_cast<float*>(stage0), scs, n, I.d, I.P, I.cs, s, tt, bar,
-                                       TC_SCALE);
+            ab = bar_or(1, TC_BT, ab);
             if (copies) {  // copy t: psi[k ^ t] at word t (N + 8) + k
-                for (int k = tt; k < N; k += TCH) {
+                for (int k = tt; k < N; k += TC_BT) {
                     const uint32_t v = psi_hl[k];
 #pragma unroll
                     for (int t3 = 1; t3 < 4; ++t3) psi_hl[t3 * (N + 8) + (k ^ t3)] = v;
                 }
-                half_sync(bar);
+                bar_n(1, TC_BT);
             }
-
-            // Build mapping: term l = 8 * warp + lane % 8 and MMA k-step sub =
-            // lane / 8: amplitudes sub*16 .. sub*16+15 of the stage go to row l,
-            // the same 16 of its second half to row 64 + l; each quarter-warp
-            // stores contiguous 128-byte core-matrix columns.
-            const int l = (tt & 7) | (wl << 3), sub = (lane >> 3) & 3;
-            const uint32_t xl = sxl[h][l], zl = szl[h][l];
+            const uint32_t xl = sxl[l], zl = szl[l];
             uint32_t sgn[8];  // word g: sign bits of elements 2g (bit 15) and 2g + 1 (bit 31) of a 16-block
             {
                 const uint32_t xlo = xl & 15u & uint32_t(N - 1);
@@ -1395,162 +1469,220 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                     sgn[g] = ((__popc(zl & 15u & (uint32_t(2 * g) ^ xlo)) & 1) ? 0x8000u : 0u) |
                              ((__popc(zl & 15u & (uint32_t(2 * g + 1) ^ xlo)) & 1) ? 0x80000000u : 0u);
             }
-            const int nch = (kend - kbeg + TCK - 1) / TCK;
-            float* X = reinterpret_cast<float*>(stage0);  // [64][65] readout of the lower quadrant, once every MMA is done
-            float2* XD = reinterpret_cast<float2*>(X + 2 * TC_X);  // [64] lower delta sums
+            const int row = hf ? 64 + l : l;
             for (int c = 0; c < nch; ++c, ++gc) {
-                const int j0 = kbeg + c * TCK;
-                const int st = gc & 1;
-                if ((pending >> st) & 1u) {  // MMAs that read this buffer two stages ago must be done
-                    if (!mbar_wait(su32(&empty[h][st]), (phase >> st) & 1u)) s_abort[h] = 1;
-                    phase ^= 1u << st;
-                    pending &= ~(1u << st);
+                const int st = int(gc % TC_NSTG);
+                if ((pend >> st) & 1u) {  // the MMAs that read this buffer last time must be done
+                    if (!ab && (aborted(&s_abort) || !mbar_wait(su32(&emptyb[st]), (eph >> st) & 1u, budget_ns)))
+                        ab = true;
+                    eph ^= 1u << st;
+                    pend &= ~(1u << st);
                 }
-                unsigned char* zhi = stage0 + st * TC_STAGE_BYTES;
+                unsigned char* zhi = base + st * TC_STAGE_BYTES;
                 unsigned char* zlo = zhi + TC_OPND_BYTES;
+                const int j0 = kbeg + c * TCK;
                 const bool brow = tt < TC_BOP_STAGE / 16;
-                if (brow) {  // the b rows of this stage (j0 is a multiple of TCK), copied while the terms are built
-                    const uint4* src = reinterpret_cast<const uint4*>(I.bop) + (long long)(j0 / TCK) * (TC_BOP_STAGE / 16) + tt;
-                    const int which = tt >> 5, ks4 = (tt >> 3) & 3, hh = (tt >> 2) & 1, row = tt & 3;
-                    const uint32_t dst =
-                        su32((which ? zlo : zhi) + ((ks4 * (TC_NB / 8) + 16) * 2 + hh) * 128 + row * 16);
+                if (brow) {  // the stage's b rows (j0 is a multiple of TCK), copied while the terms are built
+                    const uint4* srcb = reinterpret_cast<const uint4*>(I.bop) + (long long)(j0 / TCK) * (TC_BOP_STAGE / 16) + tt;
+                    const int arr = tt >> 6, ks4 = (tt >> 4) & 3, kh = (tt >> 3) & 1, br = tt & 7;
+                    const uint32_t dst = su32((arr ? zlo : zhi) + ks4 * TC_KSTEP_BYTES + TC_BROW + kh * 128 + br * 16);
                     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n\tcp.async.commit_group;" ::"r"(dst),
-                                 "l"(__cvta_generic_to_global(src))
+                                 "l"(__cvta_generic_to_global(srcb))
                                  : "memory");
                 }
+                const int jb = j0 + hf * (TCK / 2) + sub * 16;
                 if (I.states)
-                    tc_build_stage<true>(nullptr, psi_g, N, j0, kend, l < L, xl, zl, sgn, sub, l, zhi, zlo, false);
+                    tc_build_half<true>(nullptr, psi_g, N, jb, kend, l < L, xl, zl, sgn, row, sub * 16, zhi, zlo, false);
                 else
-                    tc_build_stage<false>(psi_hl, nullptr, N, j0, kend, l < L, xl, zl, sgn, sub, l, zhi, zlo,
-                                          copies);
+                    tc_build_half<false>(psi_hl, nullptr, N, jb, kend, l < L, xl, zl, sgn, row, sub * 16, zhi, zlo,
+                                         copies);
                 if (brow) asm volatile("cp.async.wait_all;" ::: "memory");
                 if (tt == 0) {
-                    srec[h][st][0] = su32(zhi);
-                    srec[h][st][1] = (c % TC_FLUSH == 0) ? 1u : 0u;
+                    srec[st][0] = su32(zhi);
+                    srec[st][1] = (c % TC_FLUSH == 0 ? 1u : 0u) | ((c % TC_FLUSH == TC_FLUSH - 1 || c + 1 == nch) ? 2u : 0u);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                mbar_arrive(su32(&full[h][st]));
-                pending |= 1u << st;
-                const bool last = c + 1 == nch;
-                if (last || (c + 1) % TC_FLUSH == 0) {
-                    // Every MMA of the block has completed once both buffers are drained.
-                    for (int q = 0; q < 2; ++q)
-                        if ((pending >> q) & 1u) {
-                            if (!mbar_wait(su32(&empty[h][q]), (phase >> q) & 1u)) s_abort[h] = 1;
-                            phase ^= 1u << q;
-                            pending &= ~(1u << q);
+                mbar_arrive(su32(&fullb[st]));
+                pend |= 1u << st;
+            }
+        }
+        // No more items: an exit stage for the MMA warp and an exit record
+        // for the epilogue (their waits are bounded whatever happens here).
+        {
+            const int st = int(gc % TC_NSTG);
+            if (((pend >> st) & 1u) && !ab && !aborted(&s_abort)) mbar_wait(su32(&emptyb[st]), (eph >> st) & 1u, budget_ns);
+            if (tt == 0) srec[st][0] = TC_EXIT;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(su32(&fullb[st]));
+            if (tt == 0) {
+                if (((iused >> ir) & 1u) && !ab && !aborted(&s_abort)) mbar_wait(su32(&ite[ir]), (iph >> ir) & 1u, budget_ns);
+                irec[ir] = make_int4(-1, 0, 0, 0);
+                mbar_arrive(su32(&itf[ir]));
+            }
+        }
+        if (ab) s_abort = 1;
+    } else if (w == TC_BW) {  // ------------------------------------------------------------- MMA warp
+        if (lane == 0) {
+            uint32_t fph = 0u, aph = 0u, aused = 0u;  // parity of full[st]; parity of acce[a]; accumulator a used
+            uint32_t acc = 0u;
+            for (int st = 0;; st = (st + 1) % TC_NSTG) {
+                if (aborted(&s_abort) || !mbar_wait(su32(&fullb[st]), (fph >> st) & 1u, budget_ns)) {
+                    s_abort = 1;
+                    break;
+                }
+                fph ^= 1u << st;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t hb = srec[st][0], fl = srec[st][1];
+                if (hb == TC_EXIT) break;
+                if (fl & 1u) {  // first stage of a block: the epilogue must have read this accumulator's last block
+                    if ((aused >> acc) & 1u) {
+                        if (aborted(&s_abort) || !mbar_wait(su32(&acce[acc]), (aph >> acc) & 1u, budget_ns)) {
+                            s_abort = 1;
+                            break;
                         }
-                    half_sync(bar);
-                    if (abort_seen()) break;
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    tc_flush(tmem, wl, lane, c < TC_FLUSH, last, X, XD);
-                    asm volatile("tcgen05.fence::before_thread_sync;");
-                }
-            }
-            half_sync(bar);
-            if (abort_seen()) break;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-
-            // Readout: the lower quadrant's sum is in X; lanes 0..63 (warps 0, 1,
-            // 4, 5 of the pipeline) add the upper one into G~ (64 x 64, real,
-            // scaled by 2^24).  Row strides of 65 floats keep the accesses free of
-            // bank conflicts.  Warps 0 and 1 also form delta_l and its product
-            // with c~_l.
-            float* G = X + TC_X;  // [64][65]
-            float TrS = 0.f, TrE = 0.f, TiS = 0.f, TiE = 0.f;
-            if ((wl & 3) < 2) {
-                const int row = 32 * (wl & 3) + lane;  // = l
-                const uint32_t base = tmem + ((uint32_t)(32 * (wl & 3)) << 16);
-                const int c0 = (wl >> 2) * 32;
-#pragma unroll
-                for (int g = 0; g < 2; ++g) {
-                    float v[16];
-                    tmem_ld16(base + TC_SUM + c0 + 16 * g, v);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) G[row * 65 + c0 + 16 * g + j] = v[j] + X[row * 65 + c0 + 16 * g + j];
-                }
-                if ((wl >> 2) == 0) {
-                    const float2 du = tmem_ld2(base + TC_DSUM), dl = XD[row];
-                    const float dsc = 1.f / (TC_SCALE * tc_bscale(*I.bn2));  // exact: a power of two
-                    const float2 dacc = make_float2((du.x + dl.x) * dsc, -(du.y + dl.y) * dsc);  // conj(b) phi
-                    if (row < L) {
-                        const float4 cv = I.cf[row];  // c~_l as (Re hi, Re lo, Im hi, Im lo)
-                        ff_mac(TrS, TrE, cv.x, cv.y, dacc.x);
-                        ff_mac(TrS, TrE, -cv.z, -cv.w, dacc.y);
-                        ff_mac(TiS, TiE, cv.x, cv.y, dacc.y);
-                        ff_mac(TiS, TiE, cv.z, cv.w, dacc.x);
-                        if (s == 0 && I.dpart) reinterpret_cast<float2*>(I.dpart)[(long long)ksi * L + row] = dacc;
+                        aph ^= 1u << acc;
+                        asm volatile("tcgen05.fence::after_thread_sync;");
                     }
+                    aused |= 1u << acc;
+                }
+                const uint32_t lb = hb + TC_OPND_BYTES, tm = s_tmem + acc * TC_ACC1;
+#pragma unroll
+                for (int ksx = 0; ksx < TCK / 32; ++ksx) {
+                    const uint64_t dh = tc_desc(hb + ksx * TC_KSTEP_BYTES), dl = tc_desc(lb + ksx * TC_KSTEP_BYTES);
+                    const uint64_t db = tc_desc(lb + ksx * TC_KSTEP_BYTES + TC_BROW);
+                    const uint32_t acc0 = ((fl & 1u) && ksx == 0) ? 0u : 1u;
+                    asm volatile(
+                        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %6, 0;\n\tsetp.eq.b32 q, %6, %6;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %2, %4, p;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %3, %5, q;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%1], %3, %7, %8, q;\n\t}\n" ::"r"(tm),
+                        "r"(tm + 128u), "l"(dh), "l"(dl), "r"(tc_idesc(TC_NB)), "r"(tc_idesc(128)), "r"(acc0),
+                        "l"(db), "r"(tc_idesc(16)));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    su32(&emptyb[st])));
+                if (fl & 2u) {
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        su32(&accf[acc])));
+                    acc ^= 1u;
                 }
             }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            half_sync(bar);
-            // Weighting.  G~ is real symmetric and only the real part of the sum
-            // is used: Re(w) G~ over the upper triangle, doubled off the diagonal.
-            // Entries (a, b) with b = tt % 64 and a = tt / 64 + 4k; the weights of
-            // four rows are loaded before they are used.
-            float S = 0.f, E = 0.f;
+            // Every MMA issued has completed before the tensor memory is freed.
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                su32(&drainb)));
+            if (!mbar_wait(su32(&drainb), 0u, TC_DRAIN_NS)) s_abort = 1;
+        }
+        __syncwarp();
+    } else {  // ----------------------------------------------------------------------------- epilogue
+        const int et = t - (TC_BT + 32), ew = et >> 5, q = w & 3;  // q: this warp's quarter of the TMEM lanes
+        uint32_t fph = 0u, aph = 0u, acc = 0u;
+        int r = 0;
+        bool ab = false;
+        for (;;) {
+            if (et == 0 && (aborted(&s_abort) || !mbar_wait(su32(&itf[r]), (fph >> r) & 1u, budget_ns))) ab = true;
+            fph ^= 1u << r;
+            ab = bar_or(2, TC_ET, ab);
+            if (ab) break;
+            const int4 rc = irec[r];
+            if (rc.x < 0) break;
+            const Inst& I = insts[rc.x];
+            const int s = rc.y, ksi = rc.z, nch = rc.w, L = I.L, ks = I.ks;
+            const int nblk = (nch + TC_FLUSH - 1) / TC_FLUSH;
+            for (int b = 0; b < nblk; ++b) {
+                if (et == 0 && (aborted(&s_abort) || !mbar_wait(su32(&accf[acc]), (aph >> acc) & 1u, budget_ns)))
+                    ab = true;
+                aph ^= 1u << acc;
+                ab = bar_or(2, TC_ET, ab);
+                if (ab) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                tc_fold(s_tmem, acc * TC_ACC1, q, lane, b == 0, b + 1 == nblk, X, XD);
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                mbar_arrive(su32(&acce[acc]));
+                acc ^= 1u;
+            }
+            if (ab) break;
+            bar_n(2, TC_ET);  // both Gram quadrants and the delta sums are in X, XD
+            // Weighting.  G' = hi hi^T + hi (2 lo)^T has the symmetric part G~
+            // (scaled by 2^24), and Re(w) is symmetric: sum_lm Re(w_lm) G~_lm =
+            // sum over l <= m of Re(w_lm) g_lm with g_ll = G'_ll and g_lm = G'_lm +
+            // G'_ml (both quadrants).  Entries (a, b) with b = et % 64 and
+            // a = et / 64 + 2k; the weights of eight rows are loaded before use.
+            const float* Xu = X;
+            const float* Xl = X + TC_X;
+            float S = 0.f, E = 0.f, TrS = 0.f, TrE = 0.f, TiS = 0.f, TiE = 0.f;
             {
-                const int b = tt & 63, a0 = tt >> 6;
+                const int bcol = et & 63, a0 = et >> 6;
                 float2* Gp = (s == 0 && I.Gpart) ? reinterpret_cast<float2*>(I.Gpart) + (long long)ksi * L * L : nullptr;
 #pragma unroll 1
-                for (int kb = 0; kb < 16; kb += 4) {
-                    float2 wv[4];
+                for (int kb = 0; kb < 32; kb += 8) {
+                    float2 wv[8];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int a = a0 + 4 * (kb + k);
-                        const float4 w4 = (a <= b && b < L) ? I.wf[a * L + b] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int k = 0; k < 8; ++k) {
+                        const int a = a0 + 2 * (kb + k);
+                        const float4 w4 = (a <= bcol && bcol < L) ? I.wf[a * L + bcol] : make_float4(0.f, 0.f, 0.f, 0.f);
                         wv[k] = make_float2(w4.x, w4.y);  // Re hi, Re lo
                     }
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int a = a0 + 4 * (kb + k);
-                        const float gv = G[a * 65 + b];
-                        ff_mac(S, E, wv[k].x, wv[k].y, a < b ? 2.f * gv : gv);
-                        if (Gp && a < L && b < L) Gp[(long long)a * L + b] = make_float2(gv * TC_UNSCALE, 0.f);
+                    for (int k = 0; k < 8; ++k) {
+                        const int a = a0 + 2 * (kb + k);
+                        if (a > bcol) continue;
+                        float g = Xu[a * 65 + bcol] + Xl[a * 65 + bcol];
+                        if (a < bcol) g += Xu[bcol * 65 + a] + Xl[bcol * 65 + a];
+                        ff_mac(S, E, wv[k].x, wv[k].y, g);
+                        if (Gp && bcol < L) {
+                            const float2 gv = make_float2((a < bcol ? 0.5f * g : g) * TC_UNSCALE, 0.f);
+                            Gp[(long long)a * L + bcol] = gv;
+                            Gp[(long long)bcol * L + a] = gv;
+                        }
                     }
                 }
+            }
+            if (et < 64 && et < L) {  // delta~_l and its product with c~_l
+                const float2 du = XD[et], dl = XD[64 + et];
+                const float dsc = 1.f / (TC_SCALE * tc_bscale(*I.bn2));  // exact: a power of two
+                const float2 dacc = make_float2((du.x + dl.x) * dsc, -(du.y + dl.y) * dsc);  // conj(b) phi
+                const float4 cv = I.cf[et];  // c~_l as (Re hi, Re lo, Im hi, Im lo)
+                ff_mac(TrS, TrE, cv.x, cv.y, dacc.x);
+                ff_mac(TrS, TrE, -cv.z, -cv.w, dacc.y);
+                ff_mac(TiS, TiE, cv.x, cv.y, dacc.y);
+                ff_mac(TiS, TiE, cv.z, cv.w, dacc.x);
+                if (s == 0 && I.dpart) reinterpret_cast<float2*>(I.dpart)[(long long)ksi * L + et] = dacc;
             }
             ff_warp_sum(S, E);
             ff_warp_sum(TrS, TrE);
             ff_warp_sum(TiS, TiE);
             if (lane == 0) {
-                sred[h][0][0][wl] = S;
-                sred[h][0][1][wl] = E;
-                sred[h][1][0][wl] = TrS;
-                sred[h][1][1][wl] = TrE;
-                sred[h][2][0][wl] = TiS;
-                sred[h][2][1][wl] = TiE;
+                sred[0][0][ew] = S;
+                sred[0][1][ew] = E;
+                sred[1][0][ew] = TrS;
+                sred[1][1][ew] = TrE;
+                sred[2][0][ew] = TiS;
+                sred[2][1][ew] = TiE;
             }
-            half_sync(bar);
-            if (tt < 3) {  // one quantity per thread; FP64 only for the final pair
-                float S2 = 0.f, E2 = 0.f;
-                for (int v = 0; v < 8; ++v) {
-                    ff_add(S2, E2, sred[h][tt][0][v]);
-                    E2 += sred[h][tt][1][v];
+            bar_n(2, TC_ET);
+            if (et == 0) {  // FP64 only for the final pairs, added in a fixed order
+                double qv[3];
+                for (int k = 0; k < 3; ++k) {
+                    float S2 = 0.f, E2 = 0.f;
+                    for (int v = 0; v < TC_EW; ++v) {
+                        ff_add(S2, E2, sred[k][0][v]);
+                        E2 += sred[k][1][v];
+                    }
+                    qv[k] = (double)S2 + (double)E2;
                 }
-                sred[h][tt][0][0] = S2;
-                sred[h][tt][1][0] = E2;
+                I.Dpart[(long long)s * ks + ksi] = make_double2(qv[0] * (double)TC_UNSCALE, 0.0);
+                I.Tpart[(long long)s * ks + ksi] = make_double2(qv[1], qv[2]);
             }
-            half_sync(bar);
-            if (tt == 0) {
-                double q[3];
-                for (int k = 0; k < 3; ++k) q[k] = (double)sred[h][k][0][0] + (double)sred[h][k][1][0];
-                I.Dpart[(long long)s * ks + ksi] = make_double2(q[0] * (double)TC_UNSCALE, 0.0);
-                I.Tpart[(long long)s * ks + ksi] = make_double2(q[1], q[2]);
-            }
+            bar_n(2, TC_ET);  // X and the item record are free again
+            if (et == 0) mbar_arrive(su32(&ite[r]));
+            r = (r + 1) % TC_NIT;
         }
-        // No more items: tell the issuer (every stage of this pipeline has
-        // drained, so the next buffer is free).
-        if (tt == 0) srec[h][gc & 1][0] = TC_EXIT;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(su32(&full[h][gc & 1]));
+        if (ab) s_abort = 1;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (t == 0 && (s_abort[0] | s_abort[1] | s_abort[2])) atomicCAS(status, 0, DEV_TIMEOUT);
-    if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(2 * TC_COLS));
+    if (t == 0 && s_abort) atomicCAS(status, 0, DEV_TIMEOUT);
+    if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(TC_COLS));
 }
 
 // ------------------------------------------- Walsh-Hadamard term classes
@@ -2021,7 +2153,7 @@ __global__ void __launch_bounds__(WHT_NT, 4) k_terms_wht(const Inst* __restrict_
             dre[t] = dim[t] = 0.f;
         }
         for (int j = t; !I.local && j < (1 << I.n); j += WHT_NT) sb[j] = I.bf[j];
-        build_state_regs<false>(psi, scratch, scs, I.n, I.d, I.P, I.cs, s, t, 0, 1.f);  // ends with a barrier
+        build_state_regs<false>(psi, scratch, scs, I.n, I.d, I.P, I.cs, s + I.s0, t, 0, 1.f);  // ends with a barrier
         float S = 0.f, E = 0.f;
         if (I.local) {
             float SL = 0.f, EL = 0.f;
@@ -2167,6 +2299,59 @@ __global__ void __launch_bounds__(NT) k_combine(const Inst* __restrict__ insts, 
     }
 }
 
+// Stage III of Sec. 2.3 across ranks (Algorithm 1, Step 4c): the per-shift
+// partial sums of a pass over the shift range s0 .. s0 + S - 1 of one
+// instance.  out[4 g .. 4 g + 3] = (Re T, Im T, Re D, Im D) of the instance's
+// shift g, with T = sum_l c_l delta_l for the normalised b and
+// D = sum_lm conj(c_l) c_m beta_lm; zeros for the shifts outside the range,
+// so the arrays of ranks that cover disjoint ranges add up (one SUM
+// allreduce) to the whole instance's.
+__global__ void __launch_bounds__(NT) k_partials(const Inst* __restrict__ insts, int S_full, double* out) {
+    pdl_wait();
+    const Inst& I = insts[0];
+    const int T = I.T, ks = I.ks;
+    const double inv = 1.0 / sqrt(*I.bn2);
+    for (int g = threadIdx.x; g < S_full; g += NT) {
+        const int s = g - I.s0;
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        if (s >= 0 && s < I.S) {
+            const double2* dp = I.Dpart + (long long)s * T * T * ks;
+            for (int e = 0; e < T * T * ks; ++e) {
+                v[2] += dp[e].x;
+                v[3] += dp[e].y;
+            }
+            const double2* tp = I.Tpart + (long long)s * T * ks;
+            for (int e = 0; e < T * ks; ++e) {
+                v[0] += tp[e].x;
+                v[1] += tp[e].y;
+            }
+            v[0] *= inv;
+            v[1] *= inv;
+        }
+        for (int k = 0; k < 4; ++k) out[4 * g + k] = v[k];
+    }
+}
+
+// Cost and parameter-shift gradient from the reduced per-shift sums of
+// k_partials (all 2P + 1 shifts): N_s = |T_s|^2, C = 1 - N_0 / D_0 and
+// dC/dalpha_k = -(N'_k D_0 - N_0 D'_k) / D_0^2 (Eq. 1; the shift rule).
+__global__ void __launch_bounds__(NT) k_combine_partials(const double* __restrict__ part, int P, int* status,
+                                                         double* cost, double* grad) {
+    const int t = threadIdx.x;
+    const double N0 = part[0] * part[0] + part[1] * part[1], D0 = part[2];
+    if (t == 0) {
+        if (!(D0 > 0.0) || !isfinite(D0) || !isfinite(N0)) set_status(status, DEV_BAD_DENOMINATOR);
+        *cost = 1.0 - N0 / D0;
+    }
+    for (int k = t; k < P; k += NT) {
+        const double* a = part + 4 * (2 * k + 1);
+        const double* b = part + 4 * (2 * k + 2);
+        const double dN = 0.5 * ((a[0] * a[0] + a[1] * a[1]) - (b[0] * b[0] + b[1] * b[1]));
+        const double dD = 0.5 * (a[2] - b[2]);
+        grad[k] = -(dN * D0 - N0 * dD) / (D0 * D0);
+    }
+}
+
 // ------------------------------------------------------------------- host
 struct HostInst {
     int n, d, L, P, S, T, ks, F;
@@ -2191,8 +2376,13 @@ struct PassShape {
     int fp32, tc, wht, count, grid;
     long long total;
     size_t smem;
-    int half;        // tensor-core kernel: shared bytes of one pipeline
     int copy_nmax;   // tensor-core kernel: states of 2^4 .. 2^copy_nmax amplitudes kept in four copies (0: none)
+    int psi_region;  // tensor-core kernel: shared bytes of its state copies
+    int st_grid;     // tensor-core pass: CTAs per instance of k_tc_states (0: no state in shared memory)
+    int st_smem;     // and its dynamic shared bytes
+    long long budget_ns;  // tensor-core kernel: time limit of each bounded wait
+    double* partials;     // shift-range pass (one instance): per-shift sums here instead of the combine
+    int S_full;           // and the instance's 2P + 1 shifts
     int prep_parts;  // CTAs per instance of k_prepare (weights split ~256 per CTA)
     int bop_parts;   // CTAs per instance building the tensor-core b rows
     int bop_fused;   // 1: those CTAs are part of k_prepare (every state has <= TC_BOP_FUSED_N amplitudes)
@@ -2236,6 +2426,12 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
         DVQLS_CUDA_TRY(ctx, launch_pdl(k_wht_classes, dim3(ps.count), dim3(WHT_CT), 0, st, dtable));
         if (marks) prof_end(ctx);
     }
+    if (ps.tc && ps.st_grid > 0) {  // shifted states of the on-chip instances, packed for the term kernel
+        if (marks) prof_begin(ctx, 4);
+        DVQLS_CUDA_TRY(ctx, launch_pdl(k_tc_states, dim3(ps.st_grid, ps.count), dim3(256), size_t(ps.st_smem), st,
+                                       dtable));
+        if (marks) prof_end(ctx);
+    }
     for (int oi = 0; oi < ps.count; ++oi) {
         const HostInst& h = *tab[oi];
         if (!h.hbm) continue;
@@ -2252,7 +2448,7 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
                                        ps.total, ctx->d_queue));
     else if (ps.tc)
         DVQLS_CUDA_TRY(ctx, launch_pdl(k_terms_tc, dim3(ps.grid), dim3(TCT), ps.smem, st, dtable, ps.count, ps.total,
-                                       ctx->d_queue, ctx->d_status, ps.half, ps.copy_nmax));
+                                       ctx->d_queue, ctx->d_status, ps.copy_nmax, ps.psi_region, ps.budget_ns));
     else if (ps.fp32)
         DVQLS_CUDA_TRY(ctx, launch_pdl(k_terms_smem<float>, dim3(ps.grid), dim3(NT), ps.smem, st, dtable, ps.count,
                                        ps.total, ctx->d_queue));
@@ -2261,7 +2457,10 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
                                        ps.total, ctx->d_queue));
     if (marks) prof_end(ctx);
     if (marks) prof_begin(ctx, 2);
-    if (ps.fp32) DVQLS_CUDA_TRY(ctx, launch_pdl(k_combine<float>, dim3(ps.count), dim3(NT), 0, st, dtable, ctx->d_status));
+    if (ps.partials)
+        DVQLS_CUDA_TRY(ctx, launch_pdl(k_partials, dim3(1), dim3(NT), 0, st, dtable, ps.S_full, ps.partials));
+    else if (ps.fp32)
+        DVQLS_CUDA_TRY(ctx, launch_pdl(k_combine<float>, dim3(ps.count), dim3(NT), 0, st, dtable, ctx->d_status));
     else DVQLS_CUDA_TRY(ctx, launch_pdl(k_combine<double>, dim3(ps.count), dim3(NT), 0, st, dtable, ctx->d_status));
     if (marks) prof_end(ctx);
     DVQLS_CUDA_TRY(ctx, cudaGetLastError());
@@ -2315,8 +2514,11 @@ static int run_pass(dvqls_ctx* ctx, const Inst* dtable, const PassShape& ps, con
 }
 
 int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precision, bool want_grad,
-              double* costs, double* grads, double* beta_out, double* delta_out, bool local) {
+              double* costs, double* grads, double* beta_out, double* delta_out, bool local,
+              const ShiftRange* range) {
     if (!ctx) return DVQLS_ERR_INVALID_ARG;
+    if (range && (count != 1 || local || !want_grad || beta_out || delta_out || costs || grads || !range->partials))
+        return set_error(ctx, DVQLS_ERR_INVALID_ARG, "a shift-range pass takes one global-cost instance");
     if (local && (beta_out || delta_out))
         return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "the local cost has no beta / delta output");
     ctx->err.clear();
@@ -2347,6 +2549,12 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         h.L = L;
         h.P = int(P);
         h.S = want_grad ? 2 * h.P + 1 : 1;
+        if (range) {
+            if (range->s0 < 0 || range->s1 > h.S || range->s0 >= range->s1)
+                return set_error(ctx, DVQLS_ERR_INVALID_ARG, "shift range [%d, %d) outside [0, %d)", range->s0,
+                                 range->s1, h.S);
+            h.S = range->s1 - range->s0;
+        }
         h.T = ceil_div(L, TT);
         h.N = 1LL << n;
         h.order = i;
@@ -2375,13 +2583,22 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         cudaFuncAttributes fa;
         DVQLS_CUDA_TRY(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
         DVQLS_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, (const void*)k_terms_tc));
-        tc = tc_smem_bytes(any_smem ? nmax : 0, Pmax, 0) + fa.sharedSizeBytes <= (size_t)optin;
+        tc = tc_smem_bytes(any_smem ? nmax : 0, 0) + fa.sharedSizeBytes <= (size_t)optin;
         for (int c = TC_COPY_NMAX; tc && any_smem && c >= 4 && !copy_nmax; --c)
-            if (tc_smem_bytes(nmax, Pmax, c) + fa.sharedSizeBytes <= (size_t)optin) copy_nmax = c;
+            if (tc_smem_bytes(nmax, c) + fa.sharedSizeBytes <= (size_t)optin) copy_nmax = c;
     }
-    const int tc_half = tc ? (int)tc_half_bytes(any_smem ? nmax : 0, Pmax, copy_nmax) : 0;
+    // The tensor-core pass builds the on-chip states in a kernel of its own.
+    int st_grid = 0;
+    size_t st_smem = 0;
+    if (tc)
+        for (const auto& h : hi)
+            if (!h.hbm) {
+                st_grid = std::max(st_grid, tcs_jobs(h.n, h.S));
+                st_smem = std::max(st_smem, tcs_smem(h.n, h.P));
+            }
+    if (st_grid > 0) DVQLS_CUDA_TRY(ctx, allow_dynamic_smem((const void*)k_tc_states));
     const size_t smem = wht  ? wht_smem_bytes(Pmax)
-                        : tc ? tc_smem_bytes(any_smem ? nmax : 0, Pmax, copy_nmax)
+                        : tc ? tc_smem_bytes(any_smem ? nmax : 0, copy_nmax)
                         : fp32 ? smem_bytes<float>(nmax, Pmax) : smem_bytes<double>(nmax, Pmax);
     const size_t r2 = fp32 ? 8 : 16;
     auto kfun = wht ? (const void*)k_terms_wht
@@ -2390,7 +2607,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     DVQLS_CUDA_TRY(ctx, allow_dynamic_smem(kfun));
     int bps = 0;
     DVQLS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfun, wht ? WHT_NT : tc ? TCT : NT, smem));
-    if (tc) bps = std::min(bps, 1);  // one CTA per SM, two item pipelines in it
+    if (tc) bps = std::min(bps, 1);  // one CTA per SM (it allocates tensor memory)
     if (bps < 1) return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "term kernel does not fit (%zu B shared)", smem);
     const long long slots = (long long)ctx->num_sms * bps;
 
@@ -2398,7 +2615,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     // signature (first call times each candidate); states in HBM take a fixed
     // HBM_K amplitudes per item.
     std::string sig = std::to_string(precision) + (want_grad ? "g" : "c") + (beta_out ? "b" : "") +
-                      (delta_out ? "d" : "") + (local ? "L" : "");
+                      (delta_out ? "d" : "") + (local ? "L" : "") +
+                      (range ? "R" + std::to_string(range->s1 - range->s0) : std::string());
     for (const auto& h : hi) sig += "|" + std::to_string(h.n) + "," + std::to_string(h.d) + "," + std::to_string(h.L);
     const int cands[] = {1, 2, 4, 8};
     auto tuned = ctx->tune.find(sig);
@@ -2415,12 +2633,16 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     struct Off {
         size_t coef, xm, zm, alpha, b;       // staged inputs (ws) ...
         size_t pcoef, pxm, pzm, palpha, pb;  // ... and their pinned slots
-        size_t ctil, w, wf, cf, bop, wht, bf, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta, states;
+        size_t ctil, w, wf, cf, bop, wht, bf, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta, states, tcst;
         size_t pcost, pgrad, pbeta, pdelta;
     };
     std::vector<Off> off(count);
     const size_t o_table = ar.reserve(sizeof(Inst) * count);
     const size_t p_table = pin.reserve(sizeof(Inst) * count);
+    const int S_full = range ? 2 * hi[0].P + 1 : 0;
+    const bool dev_part = range && is_device_ptr(ctx, range->partials);
+    const size_t o_part = range && !dev_part ? ar.reserve(size_t(S_full) * 32) : 0;
+    const size_t p_part = range && !dev_part ? pin.reserve(size_t(S_full) * 32) : 0;
     const int ks_plan_smem = tuning ? 8 : (tuned != ctx->tune.end() ? tuned->second : 1);
     // Staged inputs of all instances first, then the results, each reserved
     // in both arenas in the same order, so that the copies of a call merge
@@ -2473,6 +2695,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         o.dp = delta_out ? ar.reserve(size_t(kp) * L * r2) : 0;
         o.NsDs = ar.reserve(size_t(h.S) * 24);
         o.states = h.hbm ? ar.reserve(size_t(h.S) * size_t(h.N) * (r2 / 2)) : 0;  // real amplitudes
+        o.tcst = tc && !h.hbm ? ar.reserve(size_t(h.S) * size_t(h.N) * 4) : 0;     // packed FP16 pairs
     }
     int rc = ensure_workspace(ctx, ar.total());
     if (!rc) rc = ensure_pinned(ctx, pin.total());
@@ -2527,6 +2750,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         I.alpha = (const double*)stage_in(ctx, q.alpha, size_t(h.P) * 8, o.palpha, o.alpha);
         I.b = local ? nullptr : (const double2*)stage_in(ctx, q.b, size_t(h.N) * 16, o.pb, o.b);
         I.F = h.F;
+        I.s0 = range ? range->s0 : 0;
         I.local = local ? 1 : 0;
         I.ctil = (double2*)(ws + o.ctil);
         I.w = (double2*)(ws + o.w);
@@ -2543,6 +2767,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         I.dpart = delta_out ? (void*)(ws + o.dp) : nullptr;
         I.NsDs = (double*)(ws + o.NsDs);
         I.states = h.hbm ? (void*)(ws + o.states) : nullptr;
+        I.tcst = tc && !h.hbm ? (void*)(ws + o.tcst) : nullptr;
         // Device outputs are written in place by the combine kernel.
         I.cost = dev_cost ? costs + i : (double*)(ws + o.cost);
         I.grad = !want_grad ? nullptr : dev_grad ? grads + grad_off[i] : (double*)(ws + o.grad);
@@ -2582,10 +2807,15 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         ps.wht = wht;
         ps.count = count;
         ps.total = base;
-        ps.grid = (int)std::min<long long>(tc ? (base + 1) / 2 : base, slots);
+        ps.grid = (int)std::min<long long>(base, slots);
         ps.smem = smem;
-        ps.half = tc_half;
         ps.copy_nmax = copy_nmax;
+        ps.psi_region = tc ? (int)tc_psi_region(any_smem ? nmax : 0, copy_nmax) : 0;
+        ps.st_grid = st_grid;
+        ps.st_smem = (int)st_smem;
+        ps.budget_ns = ctx->wait_budget_us * 1000;
+        ps.partials = !range ? nullptr : dev_part ? range->partials : (double*)(ws + o_part);
+        ps.S_full = S_full;
         ps.prep_parts = (int)std::min<long long>(16, std::max<long long>(1, LLmax / NT));
         ps.bop_parts = (int)std::min<long long>(64, std::max<long long>(1, tc_bop_stages(Nmax) * (TC_BOP_STAGE / 16) / 256));
         ps.bop_fused = Nmax <= TC_BOP_FUSED_N;
@@ -2634,6 +2864,10 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        // A pass that reported an error (a bounded wait that gave up, bad input)
+        // timed nothing meaningful: report it and keep no choice.
+        rc = sync_and_check(ctx);
+        if (rc) return rc;
         ctx->tune[sig] = ks_use;
     }
     build_table(ks_use, ps);
@@ -2645,6 +2879,10 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
 
     // Results.
     std::vector<PendingOut> pend;
+    if (range && !dev_part) {
+        rc = enqueue_out(ctx, range->partials, ws + o_part, size_t(S_full) * 32, p_part, pend);
+        if (rc) return rc;
+    }
     for (int i = 0; i < count; ++i) {
         const Off& o = off[i];
         const HostInst& h = hi[i];
@@ -2667,7 +2905,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     }
     rc = flush_out(ctx);
     if (rc) return rc;
-    const bool async_ok = all_device && pend.empty() && !beta_out && !delta_out;
+    const bool async_ok = all_device && pend.empty() && !beta_out && !delta_out && !range;
     if (async_ok) return DVQLS_OK;
     rc = sync_and_check(ctx);
     if (rc) return rc;
@@ -2727,6 +2965,54 @@ extern "C" int dvqls_local_cost_grad(dvqls_ctx* ctx, const dvqls_ansatz* ansatz,
     int rc = run_batch(ctx, 1, &in, precision, grad != nullptr, cost, grad, nullptr, nullptr, true);
     if (rc == DVQLS_OK && is_device_ptr(ctx, cost)) rc = sync_and_check(ctx);
     return rc;
+}
+
+extern "C" int dvqls_cost_grad_partials(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alpha,
+                                        const dvqls_lcu* lcu, const double* b, int precision, int s_begin,
+                                        int s_end, double* partials) {
+    if (!ctx) return DVQLS_ERR_INVALID_ARG;
+    if (!ansatz || !lcu || !partials) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "NULL ansatz, lcu or partials");
+    dvqls_instance in;
+    in.ansatz = *ansatz;
+    in.lcu = *lcu;
+    in.alpha = alpha;
+    in.b = b;
+    const ShiftRange range{s_begin, s_end, partials};
+    return run_batch(ctx, 1, &in, precision, true, nullptr, nullptr, nullptr, nullptr, false, &range);
+}
+
+extern "C" int dvqls_combine_partials(dvqls_ctx* ctx, int n, int depth, const double* partials, double* cost,
+                                      double* grad) {
+    if (!ctx) return DVQLS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (n < 1 || n > DVQLS_MAX_QUBITS || depth < 0 || !partials || !cost || !grad)
+        return set_error(ctx, DVQLS_ERR_INVALID_ARG, "n, depth or a pointer out of range");
+    const long long Pl = (long long)n * (depth + 1);
+    if (Pl > MAX_ANGLES) return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "%lld angles", Pl);
+    const int P = int(Pl), S = 2 * P + 1;
+    cudaSetDevice(ctx->device);
+    Arena ar, pin;
+    const size_t o_in = ar.reserve(size_t(S) * 32), p_in = pin.reserve(size_t(S) * 32);
+    const size_t o_cost = ar.reserve(8), p_cost = pin.reserve(8);
+    const size_t o_grad = ar.reserve(size_t(P) * 8), p_grad = pin.reserve(size_t(P) * 8);
+    int rc = ensure_workspace(ctx, ar.total());
+    if (!rc) rc = ensure_pinned(ctx, pin.total());
+    if (!rc) rc = pin_acquire(ctx);
+    if (rc) return rc;
+    const double* dpart = (const double*)stage_in(ctx, partials, size_t(S) * 32, p_in, o_in);
+    rc = pin_release(ctx);
+    if (rc) return rc;
+    const bool dcost = is_device_ptr(ctx, cost), dgrad = is_device_ptr(ctx, grad);
+    double* c_out = dcost ? cost : (double*)(ctx->ws + o_cost);
+    double* g_out = dgrad ? grad : (double*)(ctx->ws + o_grad);
+    k_combine_partials<<<1, NT, 0, ctx->stream>>>(dpart, P, ctx->d_status, c_out, g_out);
+    DVQLS_CUDA_TRY(ctx, cudaGetLastError());
+    std::vector<PendingOut> pend;
+    if (!dcost) rc = enqueue_out(ctx, cost, c_out, 8, p_cost, pend);
+    if (!rc && !dgrad) rc = enqueue_out(ctx, grad, g_out, size_t(P) * 8, p_grad, pend);
+    if (!rc) rc = sync_and_check(ctx);
+    if (rc) return rc;
+    return finish_out(ctx, pend);
 }
 
 // ------------------------------------------------- allocation-free variant

@@ -33,12 +33,13 @@ EXPORTED = [
     "dvqls_create", "dvqls_destroy", "dvqls_last_error", "dvqls_sync",
     "dvqls_pauli_decompose", "dvqls_pauli_decompose_banded",
     "dvqls_cost", "dvqls_cost_grad", "dvqls_cost_grad_batched",
-    "dvqls_profile_enable", "dvqls_profile_read", "dvqls_cost_grad_noalloc",
+    "dvqls_profile_enable", "dvqls_profile_read", "dvqls_set_wait_budget", "dvqls_cost_grad_noalloc",
     "dvqls_circuit_cost_grad_fp64", "dvqls_fidelity", "dvqls_lcu_solve", "dvqls_lcu_solve_batched",
     "dvqls_optimize",
     "dvqls_ws_param_count", "dvqls_ws_create", "dvqls_ws_destroy", "dvqls_ws_infer", "dvqls_ws_grad",
     "dvqls_ws_train_step", "dvqls_ws_get_params", "dvqls_ws_save", "dvqls_ws_load",
     "dvqls_local_cost_grad", "dvqls_local_cost_grad_batched",
+    "dvqls_cost_grad_partials", "dvqls_combine_partials",
 ]
 
 
@@ -102,6 +103,7 @@ def lib():
         L.dvqls_cost_grad_batched.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dvqls_instance), ctypes.c_int,
                                               dp, dp]
         L.dvqls_profile_enable.argtypes = [vp, ctypes.c_int]
+        L.dvqls_set_wait_budget.argtypes = [vp, ctypes.c_longlong]
         L.dvqls_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(ctypes.c_double)]
         L.dvqls_cost_grad_noalloc.argtypes = [vp, ctypes.POINTER(dvqls_ansatz), dp, ctypes.POINTER(dvqls_lcu), dp,
@@ -130,6 +132,9 @@ def lib():
                                             ctypes.c_int, dp, dp]
         L.dvqls_local_cost_grad_batched.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dvqls_instance), ctypes.c_int,
                                                     dp, dp]
+        L.dvqls_cost_grad_partials.argtypes = [vp, ctypes.POINTER(dvqls_ansatz), dp, ctypes.POINTER(dvqls_lcu), dp,
+                                               ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+        L.dvqls_combine_partials.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -227,6 +232,11 @@ def dvqls_cost_grad_batched(ctx, instances, precision, costs, grads):
 
 def dvqls_profile_enable(ctx, enable):
     _check(ctx, lib().dvqls_profile_enable(ctx, int(enable)))
+
+
+def dvqls_set_wait_budget(ctx, microseconds):
+    """Time limit of each bounded device wait of the tensor-core term kernel."""
+    _check(ctx, lib().dvqls_set_wait_budget(ctx, int(microseconds)))
 
 
 def dvqls_profile_read(ctx, phase):
@@ -353,3 +363,15 @@ def dvqls_local_cost_grad(ctx, ansatz, alpha, lcu, precision, cost, grad=None):
 def dvqls_local_cost_grad_batched(ctx, instances, precision, costs, grads):
     _check(ctx, lib().dvqls_local_cost_grad_batched(ctx, len(instances), instances, int(precision), ptr(costs),
                                                     ptr(grads)))
+
+
+def dvqls_cost_grad_partials(ctx, ansatz, alpha, lcu, b, precision, s_begin, s_end, partials):
+    """Per-shift sums (Re T, Im T, Re D, Im D) of the shifts s_begin .. s_end - 1
+    of one instance into partials ((2P+1) x 4 doubles; zeros elsewhere)."""
+    _check(ctx, lib().dvqls_cost_grad_partials(ctx, ctypes.byref(ansatz), ptr(alpha), ctypes.byref(lcu), ptr(b),
+                                               int(precision), int(s_begin), int(s_end), ptr(partials)))
+
+
+def dvqls_combine_partials(ctx, n, depth, partials, cost, grad):
+    """Cost and gradient of one instance from its summed per-shift sums."""
+    _check(ctx, lib().dvqls_combine_partials(ctx, int(n), int(depth), ptr(partials), ptr(cost), ptr(grad)))
