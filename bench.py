@@ -223,9 +223,11 @@ def make_batch(D, ctx, torch, rank, name):
 
 def work_of(shapes, tensor=False):
     """Paper terms, algorithmic and executed FLOPs of one cost+grad pass.
-    The tensor-core kernel executes, per k-step of 16 amplitudes of each half
-    of a stage, three MMAs with M = 128: hi hi^T with the b rows (N = 144),
-    hi (2 lo)^T (N = 128) and 2 lo hi(b)^T / 2 (N = 16)."""
+    The tensor-core kernel executes, for a diagonal 64-term tile, per k-step
+    of 16 amplitudes of each half of a stage, three MMAs with M = 128: hi hi^T
+    with the b rows (N = 144), hi (2 lo)^T (N = 128) and 2 lo hi(b)^T / 2
+    (N = 16); for a pair of tiles, per 16 amplitudes, one 128 x 128 x 16 MMA of
+    [hi; lo] against [hi; lo]."""
     terms = alg = exe = 0
     for n, d, L in shapes:
         S = 2 * n * (d + 1) + 1
@@ -234,8 +236,9 @@ def work_of(shapes, tensor=False):
         alg += S * (L * L + L) * 8 * N
         # tensor cores: MMAs of 128 x (144 + 128 + 16) x 16 per 32 amplitudes (Gram and delta rows); CUDA
         # cores: one real FMA per Gram product (the ansatz state is real) and 4 flops per delta product
-        exe += S * (2 * 128 * (144 + 128 + 16) * 16 * (N // 32) if tensor else
-                    executed_gram_entries(L) * 2 * N + L * 4 * N)
+        T = (L + 63) // 64
+        exe += S * (T * 2 * 128 * (144 + 128 + 16) * 16 * (N // 32) + T * (T - 1) // 2 * 2 * 128 * 128 * 16 * (N // 16)
+                    if tensor else executed_gram_entries(L) * 2 * N + L * 4 * N)
     return terms, alg, exe
 
 
@@ -414,6 +417,92 @@ def oracle_errors(D, ctx, torch, keep):
     return out
 
 
+def run_split(args):
+    """One instance split across ranks (Stage III of Sec. 2.3): every rank
+    evaluates its block of each n = 20 instance's 441 shifted evaluations,
+    one SUM allreduce of the per-shift sums (NCCL) per instance, then every
+    rank forms the cost and gradient.  Strong scaling: the job is the same
+    two instances at any number of GPUs."""
+    import torch
+    rank, local, ws = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    import __graft_entry__
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if pg:
+        pg.barrier()
+    from paper_2604_14435_gb300 import dvqls as D
+    from paper_2604_14435_gb300 import stage3
+    from paper_2604_14435_gb300 import workloads as wl
+    stream = torch.cuda.current_stream()
+    ctx = D.dvqls_create(local, stream.cuda_stream)
+    prec = D.DVQLS_FP32_TC if args.precision == "fp32_tc" else D.DVQLS_FP32
+    big = [i for i in wl.uneven_batch(seed=0) if i["n"] == 20]
+    keep, probs = [], []
+    for inst in big:
+        n, d = inst["n"], inst["d"]
+        coef = torch.zeros(2 * inst["L_max"], dtype=torch.float64, device="cuda")
+        xm = torch.zeros(inst["L_max"], dtype=torch.int32, device="cuda")
+        zm = torch.zeros(inst["L_max"], dtype=torch.int32, device="cuda")
+        bands = torch.tensor(inst["bands"], dtype=torch.float64, device="cuda")
+        L, _, _ = D.dvqls_pauli_decompose_banded(ctx, n, inst["offsets"], bands, inst["tau"], inst["L_max"],
+                                                 coef, xm, zm)
+        alpha = torch.tensor(inst["alpha"], dtype=torch.float64, device="cuda")
+        b = torch.tensor(np.ascontiguousarray(inst["b"]).view(np.float64), dtype=torch.float64, device="cuda")
+        keep.append((coef, xm, zm, alpha, b))
+        probs.append((D.make_ansatz(n, d), D.make_lcu(L, coef, xm, zm), alpha, b, (n, d, L)))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        out = []
+        for an, lcu, alpha, b, _ in probs:
+            out.append(stage3.cost_grad_split(D, ctx, an, alpha, lcu, b, prec, pg, torch, "cuda"))
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        res = step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = max_over_ranks(pg, torch, sum(a.elapsed_time(b) for a, b in ev), "cuda")
+    if rank == 0:
+        S = [2 * p[4][0] * (p[4][1] + 1) + 1 for p in probs]
+        line = {"metric": "cost+grad evals/sec (one n=20 instance split across ranks by shift ranges)",
+                "value": len(probs) * args.steps / (ms / 1000.0), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32 (3xf16 split)" if prec == D.DVQLS_FP32_TC
+                else "f32", "data": "synthetic", "precision": args.precision,
+                "config": {"workload": "the two tridiagonal n=20 instances of the uneven batch (depth 10, "
+                                       "P = 220, S = 441 shifted states each, L <= 64 at tau = 0.01), each "
+                                       "split into contiguous shift ranges over the ranks; one SUM allreduce "
+                                       "of 441 x 4 doubles per instance", "parallelism": "shift split x%d" % ws,
+                           "shape": [p[4] for p in probs], "shifts": S,
+                           "l2": "flushed between timed steps (256 MB write)"},
+                "costs": [float(c.item()) for c, _ in res],
+                "clocks": clk}
+        print(json.dumps(line))
+    D.dvqls_destroy(ctx)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
 def run_reference(args):
     rank, _, ws = dist_env()
     if ws > 1 and rank != 0:
@@ -444,7 +533,9 @@ def main():
                     help="timed steps (default 2000 for this implementation, 200 for the reference arm)")
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="toeplitz10", choices=["toeplitz10", "uneven", "hele_shaw"])
+    ap.add_argument("--workload", default="toeplitz10", choices=["toeplitz10", "uneven", "hele_shaw", "split_n20"],
+                    help="split_n20: the two n = 20 instances of the uneven batch, each split by shift ranges "
+                         "across the ranks with one allreduce of its per-shift sums (strong scaling)")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the CPU oracle leg (its timing and the per-quantity error against it)")
     ap.add_argument("--no-side-workloads", action="store_true",
@@ -458,6 +549,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     assert args.warmup >= 3, "at least 3 warm-up steps"
+    if args.workload == "split_n20":
+        return run_split(args)
     headline = args.workload == "toeplitz10"
 
     import torch
@@ -479,7 +572,7 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = D.dvqls_create(local, stream.cuda_stream)
     dev_arr, host_arr, keep, shapes = make_batch(D, ctx, torch, rank, args.workload)
-    tensor = args.precision == "fp32_tc" and all(L <= 64 for _, _, L in shapes)
+    tensor = args.precision == "fp32_tc"
     count = len(shapes)
     P = sum(n * (d + 1) for n, d, L in shapes)
     costs = torch.zeros(count, dtype=torch.float64, device="cuda")
@@ -615,12 +708,19 @@ def main():
         r_cost = local_rate(False, max(20, args.steps))
         r_grad = local_rate(True, max(5, args.steps // 10))
         ref_costs = lcosts.clone()
+        t_cost = local_rate(False, max(20, args.steps), D.DVQLS_FP32_TC)
+        t_grad = local_rate(True, max(5, args.steps // 10), D.DVQLS_FP32_TC)
+        t_diff = float((lcosts - ref_costs).abs().max())
         w_cost = local_rate(False, max(20, args.steps), D.DVQLS_FP32_WHT)
         w_grad = local_rate(True, max(5, args.steps // 10), D.DVQLS_FP32_WHT)
         circuits = 2 * (N_QUBITS + 1) * L_TERMS ** 2
         local = {"cost_evals_per_s": r_cost, "cost_grad_evals_per_s": r_grad,
                  "circuits_per_cost_eval": circuits, "circuit_equivalents_per_s": r_cost * circuits,
                  "precision": "fp32",
+                 "tensor_cores": {"precision": "fp32_tc", "cost_evals_per_s": t_cost, "cost_grad_evals_per_s": t_grad,
+                                  "max_abs_cost_diff_vs_fp32": t_diff,
+                                  "note": "flavour j as the Gram of each 64-term tile against its strings with "
+                                          "x ^ e_j, [hi; lo] against [hi; lo] on the tensor cores"},
                  "wht_reformulation": {"precision": "fp32_wht", "cost_evals_per_s": w_cost,
                                        "cost_grad_evals_per_s": w_grad,
                                        "max_abs_cost_diff_vs_fp32": float((lcosts - ref_costs).abs().max()),

@@ -66,17 +66,15 @@ typedef enum {
  * keep the coefficient-weighted L^2 sum, the cost ratio and the gradient
  * combine in FP64.
  *   DVQLS_FP32:    FP32 states, FP32 term reductions on the CUDA cores.
- *   DVQLS_FP32_TC: FP32 states; the term Gram of each 64-term tile on the
- *                  tensor cores (tcgen05 kind::f16: every amplitude, scaled
- *                  by 2^12, split into FP16 hi + lo; three products hi hi +
- *                  hi lo + lo hi, FP32 accumulation with periodic
- *                  round-to-nearest folding), which keeps FP32-level
- *                  accuracy (measured |beta - oracle| <= 3.4e-6 up to n = 14;
- *                  the FP32 bounds of the parity tests hold).  Weighted sums
- *                  in float-float (~2^-44 relative), combined in FP64.
- *                  Served for the global cost when every instance has
- *                  L <= 64 and both on-chip pipelines' shared memory fits;
- *                  other calls run as DVQLS_FP32.
+ *   DVQLS_FP32_TC: FP32 states; the term Gram on the tensor cores
+ *                  (tcgen05 kind::f16: every amplitude, scaled by 2^12,
+ *                  split into FP16 hi + lo; the products hi hi + hi lo +
+ *                  lo hi with FP32 accumulation and periodic round-to-nearest
+ *                  folding), 64-term tiles and pairs of tiles for any L,
+ *                  which keeps FP32-level accuracy (the FP32 bounds of the
+ *                  parity tests hold).  Weighted sums in float-float (~2^-44
+ *                  relative), combined in FP64.  Served for the global cost;
+ *                  the local cost runs as DVQLS_FP32.
  *   DVQLS_FP32_WHT: an exact reformulation of the same terms (not the
  *                  paper's per-term evaluation): the pairs (l, m) are
  *                  grouped by x_l ^ x_m and one FP32
@@ -322,7 +320,11 @@ int dvqls_circuit_cost_grad_fp64(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, con
 
 /* F = |<xhat|psi(alpha)>|^2 / ||xhat||^2 with psi(alpha) = V(alpha)|0> built
  * in FP64 (Sec. 3.1: fidelity against the classical solution).  xhat: N
- * complex128, any nonzero norm.  n <= DVQLS_MAX_SMEM_QUBITS. */
+ * complex128, any nonzero norm.  n <= DVQLS_MAX_QUBITS: above
+ * DVQLS_MAX_SMEM_QUBITS the state is built in HBM (N doubles of workspace) and
+ * the overlap is summed over the GPU in a fixed block order.
+ * Errors: INVALID_ARG (n, depth, NULL, a non-finite angle, xhat = 0),
+ * UNSUPPORTED (another ansatz), ALLOC, CUDA. */
 int dvqls_fidelity(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alpha,
                    const double* xhat, double* F);
 
@@ -373,6 +375,30 @@ typedef struct {
  * call and frees it before returning. */
 int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* inst, const double* xhat,
                    const dvqls_adam* opt, double* alpha_out, dvqls_opt_result* results);
+
+/* Checkpoint and resume of the optimizer loop.  The Adam state of `count`
+ * instances: the first and second moments (packed P_i doubles per instance,
+ * like the angles) and the number of updates each instance has had (its bias
+ * corrections are 1 - beta^steps).  Host or device memory, read and written
+ * by dvqls_optimize_resume. */
+typedef struct {
+    double* m;        /* sum_i P_i doubles                     */
+    double* v;        /* sum_i P_i doubles                     */
+    long long* steps; /* count updates made so far             */
+} dvqls_adam_state;
+
+/* dvqls_optimize from a checkpoint: starts from inst[i].alpha with the given
+ * Adam state (m = v = 0, steps = 0 is a fresh start, identical to
+ * dvqls_optimize), runs at most opt->max_iter updates, and writes the final
+ * angles to alpha_out and the final state back to *state.  Saving alpha_out
+ * and the state after K updates and resuming from them gives, bit for bit,
+ * the angles and state of one run of K + K' updates (the bias-correction
+ * products are formed in the same order).
+ * Errors: as dvqls_optimize; INVALID_ARG for a NULL state array or a
+ * negative update count. */
+int dvqls_optimize_resume(dvqls_ctx* ctx, int count, const dvqls_instance* inst, const double* xhat,
+                          const dvqls_adam* opt, dvqls_adam_state* state, double* alpha_out,
+                          dvqls_opt_result* results);
 
 /* ------------------------------------------------------------------------
  * Learned warm start.  Algorithm 1, Step 3 initialises theta randomly; this

@@ -182,6 +182,10 @@ struct ShiftRange {
     double* partials;
 };
 
+// F = |<xhat|psi(alpha)>|^2 / ||xhat||^2 with psi built in HBM (terms.cu), for
+// n above the shared-memory size.
+int fidelity_hbm(dvqls_ctx* ctx, int n, int d, const double* alpha, const double* xhat, double* F);
+
 // The batched cost pass (terms.cu): cost and gradient (or, with a shift range,
 // per-shift sums) of `count` instances.
 int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precision, bool want_grad, double* costs,

@@ -202,8 +202,11 @@ __global__ void __launch_bounds__(CGT) k_cg(int n, int L, const double2* coef, c
     }
 }
 
+// One Adam update of the active angles: element i is angle gmap[i], whose
+// instance has the bias corrections c1[i] = 1 - beta1^t and c2[i] = 1 - beta2^t.
 __global__ void k_adam(int count, const int* __restrict__ gmap, const double* __restrict__ g, double* alpha,
-                       double* m, double* v, double lr, double b1, double b2, double eps, double c1, double c2) {
+                       double* m, double* v, double lr, double b1, double b2, double eps, const double* __restrict__ c1,
+                       const double* __restrict__ c2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const int k = gmap[i];
@@ -212,7 +215,7 @@ __global__ void k_adam(int count, const int* __restrict__ gmap, const double* __
     const double vi = b2 * v[k] + (1.0 - b2) * gi * gi;
     m[k] = mi;
     v[k] = vi;
-    alpha[k] -= lr * (mi / c1) / (sqrt(vi / c2) + eps);
+    alpha[k] -= lr * (mi / c1[i]) / (sqrt(vi / c2[i]) + eps);
 }
 
 // cudaMalloc'd block owned by one optimizer call.
@@ -236,8 +239,11 @@ extern "C" int dvqls_fidelity(dvqls_ctx* ctx, const dvqls_ansatz* an, const doub
     if (!an || !alpha || !xhat || !F) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "NULL argument");
     const int n = an->n, d = an->depth;
     if (n < 1 || n > DVQLS_MAX_QUBITS || d < 0) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "n = %d", n);
-    if (n > DVQLS_MAX_SMEM_QUBITS) return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "n = %d above %d", n, DVQLS_MAX_SMEM_QUBITS);
     if (an->kind != DVQLS_ANSATZ_RY_CZRING) return set_error(ctx, DVQLS_ERR_UNSUPPORTED, "ansatz kind");
+    if (n > DVQLS_MAX_SMEM_QUBITS) {  // the state in HBM
+        cudaSetDevice(ctx->device);
+        return fidelity_hbm(ctx, n, d, alpha, xhat, F);
+    }
     const int P = n * (d + 1);
     const long long N = 1LL << n;
     cudaSetDevice(ctx->device);
@@ -549,12 +555,16 @@ extern "C" int dvqls_lcu_solve(dvqls_ctx* ctx, int n, const dvqls_lcu* lcu, cons
     return dvqls_lcu_solve_batched(ctx, n, lcu, 1, b, tol, max_iter, x, iters, rel_resid);
 }
 
-extern "C" int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* inst, const double* xhat,
-                              const dvqls_adam* opt, double* alpha_out, dvqls_opt_result* results) {
+// The optimizer loop; `state` (may be NULL: a fresh start) carries the Adam
+// moments and update counts in and out.
+static int optimize(dvqls_ctx* ctx, int count, const dvqls_instance* inst, const double* xhat, const dvqls_adam* opt,
+                    dvqls_adam_state* state, double* alpha_out, dvqls_opt_result* results) {
     if (!ctx) return DVQLS_ERR_INVALID_ARG;
     ctx->err.clear();
     if (count < 1 || !inst || !xhat || !opt || !alpha_out || !results)
         return set_error(ctx, DVQLS_ERR_INVALID_ARG, "NULL argument or count < 1");
+    if (state && (!state->m || !state->v || !state->steps))
+        return set_error(ctx, DVQLS_ERR_INVALID_ARG, "NULL moment or step array");
     if (!(opt->lr > 0.0) || opt->max_iter < 0 || !(opt->beta1 >= 0.0 && opt->beta1 < 1.0) ||
         !(opt->beta2 >= 0.0 && opt->beta2 < 1.0) || !(opt->eps > 0.0))
         return set_error(ctx, DVQLS_ERR_INVALID_ARG, "bad Adam settings");
@@ -581,6 +591,7 @@ extern "C" int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* i
     Arena ar;
     const size_t o_al = ar.reserve(size_t(Pt) * 8), o_m = ar.reserve(size_t(Pt) * 8), o_v = ar.reserve(size_t(Pt) * 8);
     const size_t o_g = ar.reserve(size_t(Pt) * 8), o_gm = ar.reserve(size_t(Pt) * 4);
+    const size_t o_c1 = ar.reserve(size_t(Pt) * 8), o_c2 = ar.reserve(size_t(Pt) * 8);
     const size_t o_x = ar.reserve(size_t(Nt) * 16), o_b = ar.reserve(size_t(Nt) * 16);
     const size_t o_c = ar.reserve(size_t(Lt) * 16), o_xm = ar.reserve(size_t(Lt) * 4), o_zm = ar.reserve(size_t(Lt) * 4);
     const size_t o_cost = ar.reserve(size_t(count) * 8), o_F = ar.reserve(size_t(count) * 8);
@@ -598,8 +609,29 @@ extern "C" int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* i
     int* gmap = (int*)(base + o_gm);
     double* costs = (double*)(base + o_cost);
     double* F = (double*)(base + o_F);
-    DVQLS_CUDA_TRY(ctx, cudaMemsetAsync(m, 0, size_t(Pt) * 8, ctx->stream));
-    DVQLS_CUDA_TRY(ctx, cudaMemsetAsync(v, 0, size_t(Pt) * 8, ctx->stream));
+    double* c1d = (double*)(base + o_c1);
+    double* c2d = (double*)(base + o_c2);
+    // Adam state: zero moments and no updates, or the caller's checkpoint.  The
+    // bias corrections 1 - beta^t are kept as products formed on the host in
+    // the same order as a run that never stopped, so a resumed run continues
+    // bit for bit.
+    std::vector<long long> steps(count, 0);
+    std::vector<double> p1(count, 1.0), p2(count, 1.0);  // beta1^t, beta2^t per instance
+    if (state) {
+        DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(m, state->m, size_t(Pt) * 8, cudaMemcpyDefault, ctx->stream));
+        DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(v, state->v, size_t(Pt) * 8, cudaMemcpyDefault, ctx->stream));
+        DVQLS_CUDA_TRY(ctx, cudaMemcpy(steps.data(), state->steps, size_t(count) * 8, cudaMemcpyDefault));
+        for (int i = 0; i < count; ++i) {
+            if (steps[i] < 0) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "instance %d: negative update count", i);
+            for (long long t = 0; t < steps[i]; ++t) {
+                p1[i] *= opt->beta1;
+                p2[i] *= opt->beta2;
+            }
+        }
+    } else {
+        DVQLS_CUDA_TRY(ctx, cudaMemsetAsync(m, 0, size_t(Pt) * 8, ctx->stream));
+        DVQLS_CUDA_TRY(ctx, cudaMemsetAsync(v, 0, size_t(Pt) * 8, ctx->stream));
+    }
     std::vector<dvqls_instance> dinst(count);
     std::vector<FidInst> fid(count);
     for (int i = 0; i < count; ++i) {
@@ -645,7 +677,7 @@ extern "C" int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* i
     std::vector<FidInst> afid;
     bool dirty = true;
     long long Pa = 0;
-    double c1 = 1.0, c2 = 1.0;
+    std::vector<double> hc1, hc2;
     int rc = DVQLS_OK;
     for (int it = 0; it <= opt->max_iter && !active.empty(); ++it) {
         if (dirty) {
@@ -707,13 +739,40 @@ extern "C" int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* i
             dirty = true;
         }
         if (active.empty() || Pa == 0) break;
-        c1 *= opt->beta1;
-        c2 *= opt->beta2;
+        hc1.clear();
+        hc2.clear();
+        for (int i : active) {  // the update of instance i is its (steps[i] + 1)-th
+            p1[i] *= opt->beta1;
+            p2[i] *= opt->beta2;
+            ++steps[i];
+            hc1.insert(hc1.end(), size_t(P[i]), 1.0 - p1[i]);
+            hc2.insert(hc2.end(), size_t(P[i]), 1.0 - p2[i]);
+        }
+        DVQLS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        DVQLS_CUDA_TRY(ctx, cudaMemcpy(c1d, hc1.data(), hc1.size() * 8, cudaMemcpyHostToDevice));
+        DVQLS_CUDA_TRY(ctx, cudaMemcpy(c2d, hc2.data(), hc2.size() * 8, cudaMemcpyHostToDevice));
         k_adam<<<ceil_div(Pa, 256), 256, 0, ctx->stream>>>(int(Pa), gmap, g, alpha, m, v, opt->lr, opt->beta1,
-                                                          opt->beta2, opt->eps, 1.0 - c1, 1.0 - c2);
+                                                          opt->beta2, opt->eps, c1d, c2d);
         DVQLS_CUDA_TRY(ctx, cudaGetLastError());
     }
     DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(alpha_out, alpha, size_t(Pt) * 8, cudaMemcpyDefault, ctx->stream));
+    if (state) {
+        DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(state->m, m, size_t(Pt) * 8, cudaMemcpyDefault, ctx->stream));
+        DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(state->v, v, size_t(Pt) * 8, cudaMemcpyDefault, ctx->stream));
+    }
     DVQLS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (state) DVQLS_CUDA_TRY(ctx, cudaMemcpy(state->steps, steps.data(), size_t(count) * 8, cudaMemcpyDefault));
     return DVQLS_OK;
+}
+
+extern "C" int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* inst, const double* xhat,
+                              const dvqls_adam* opt, double* alpha_out, dvqls_opt_result* results) {
+    return optimize(ctx, count, inst, xhat, opt, nullptr, alpha_out, results);
+}
+
+extern "C" int dvqls_optimize_resume(dvqls_ctx* ctx, int count, const dvqls_instance* inst, const double* xhat,
+                                     const dvqls_adam* opt, dvqls_adam_state* state, double* alpha_out,
+                                     dvqls_opt_result* results) {
+    if (ctx && !state) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "NULL optimizer state");
+    return optimize(ctx, count, inst, xhat, opt, state, alpha_out, results);
 }

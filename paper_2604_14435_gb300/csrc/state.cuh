@@ -303,28 +303,41 @@ __device__ void state_regs_multiwarp(void* psi, float* scr0, float* scr1, const 
     group_sync(bar, 256);
 }
 
-// n <= 8: one warp holds the whole state (i = (r << 5) | lane; for n < 5 lane
-// i is lane mod 2^n), no barrier inside.
+// n <= 10: one warp holds the whole state (i = (r << 5) | lane; for n < 5 lane
+// i is lane mod 2^n), no barrier inside.  The initial Ry layer on |0> is a
+// product state: a lane factor (qubits on lane bits) times register factors
+// built by doubling (qubits on register bits).  The CZ-ring signs depend only
+// on the amplitude index, so they are one bit mask per lane for every layer.
 template <int A, int LOGA, bool PACK>
 __device__ void state_regs_warp(void* psi, const float2* scs, int n, int d, int lane, float scale) {
-    const int N = 1 << n, lmask = N < 32 ? N - 1 : 31, nl = n < 5 ? n : 5;
+    const int N = 1 << n, lmask = N < 32 ? N - 1 : 31, nl = n < 5 ? n : 5, li = lane & lmask;
     float v[A];
+    {
+        float f = scale;  // qubits 0 .. nl - 1 on the lane bits
+        for (int q = 0; q < nl; ++q) f *= ((li >> q) & 1) ? scs[q].y : scs[q].x;
+        v[0] = f;
 #pragma unroll
-    for (int r = 0; r < A; ++r) {
-        const int i = (r << 5) | (lane & lmask);
-        float x = scale;
-        for (int q = 0; q < n; ++q) x *= ((i >> q) & 1) ? scs[q].y : scs[q].x;
-        v[r] = x;
+        for (int kb = 0; kb < LOGA; ++kb) {  // qubit 5 + kb on register bit kb
+            const float c = scs[5 + kb].x, sn = scs[5 + kb].y;
+#pragma unroll
+            for (int r = 0; r < (1 << kb); ++r) {
+                v[r + (1 << kb)] = v[r] * sn;
+                v[r] *= c;
+            }
+        }
     }
+    uint32_t czm = 0u;  // bit r: the CZ ring flips the sign of amplitude (r << 5) | lane
+#pragma unroll
+    for (int r = 0; r < A; ++r) czm |= uint32_t(czring_parity((r << 5) | li, n)) << r;
     for (int layer = 1; layer <= d; ++layer) {
         const float2* ang = scs + layer * n;
 #pragma unroll
         for (int r = 0; r < A; ++r)
-            if (czring_parity((r << 5) | (lane & lmask), n)) v[r] = -v[r];
+            v[r] = __uint_as_float(__float_as_uint(v[r]) ^ (((czm >> r) & 1u) << 31));
         for (int b = 0; b < nl; ++b) {
-            const float c = ang[b].x, sn = ang[b].y;
+            const float c = ang[b].x, sb = ((lane >> b) & 1) ? ang[b].y : -ang[b].y;
 #pragma unroll
-            for (int r = 0; r < A; ++r) v[r] = ry_lane(v[r], lane, b, c, sn);
+            for (int r = 0; r < A; ++r) v[r] = fmaf(c, v[r], sb * __shfl_xor_sync(0xffffffffu, v[r], 1 << b));
         }
 #pragma unroll
         for (int kb = 0; kb < LOGA; ++kb) {  // register-bit qubits 5 + kb

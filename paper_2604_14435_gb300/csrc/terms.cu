@@ -55,6 +55,8 @@ struct Inst {
     double2* w;      // L*L: conj(ctil_l) ctil_m
     float4* wf;      // L*L or null: w as float pairs (Re hi, Re lo, Im hi, Im lo)
     float4* cf;      // L or null: ctil as float pairs
+    float2* wt;      // tensor-core pass: Re w_lm as a float pair (hi, lo) for the entries l <= m of each
+                     // diagonal 64-term tile in row-major order (TC_TRI per tile; zero past L), or null
     void* bop;       // tensor-core tiles: the b rows of the B operand, TC_BOP_STAGE bytes per stage, or null
     void* wht;       // Walsh-Hadamard classes: the class table (WHT_TABLE_BYTES), or null
     float2* bf;      // Walsh-Hadamard classes: b in FP32, or null
@@ -820,6 +822,11 @@ int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, 
     return DVQLS_OK;
 }
 
+// Amplitudes per work item for states in HBM (each FP32 sum runs over half
+// of them; items are added in FP64), and its log2.
+constexpr long long HBM_K = 2048;
+constexpr int HBM_KQ = 11;
+
 // ------------------------------------------------- tensor-core term tiles
 // Precision DVQLS_FP32_TC: the Gram of a 64-term tile on the tensor cores.
 // The Ry + CZ-ring ansatz state is real, so with the phase i^popc(x & z) in
@@ -881,7 +888,7 @@ int build_hbm_states(dvqls_ctx* ctx, const Inst* dtable, int idx, int n, int d, 
 constexpr int TCK = 128;            // amplitudes per stage: 2 x 64, i.e. 4 MMA k-steps of 16 in each row half
 constexpr int TC_BW = 16;           // builder warps
 constexpr int TC_BT = 32 * TC_BW;   // builder threads: one 16-amplitude half-row of one term per stage each
-constexpr int TC_EW = 4;            // epilogue warps, one per quarter of the tensor-memory lanes
+constexpr int TC_EW = 8;            // epilogue warps, two per quarter of the tensor-memory lanes
 constexpr int TC_ET = 32 * TC_EW;
 constexpr int TCT = TC_BT + 32 + TC_ET;  // builders, the MMA warp, the epilogue warps
 constexpr int TC_NSTG = 4;          // operand stages in flight
@@ -905,6 +912,27 @@ constexpr int TC_BROW = 16 * 256;   // offset of row group 16 (the b rows) insid
 constexpr int TC_X = 64 * 65;       // readout floats of one Gram quadrant ([64][65])
 constexpr int TC_EPI_BYTES = 2 * TC_X * 4 + 2 * 64 * 8;  // both quadrants and their delta sums
 constexpr int TC_BOP_STAGE = 2048;  // bytes of the b rows of one stage (both operand arrays)
+constexpr int TC_TRI = 64 * 65 / 2;  // entries l <= m of a 64-term tile
+// Position of entry (l, m), l <= m < 64, in the row-major upper triangle.
+__host__ __device__ constexpr int tc_tri(int l, int m) { return 64 * l - l * (l - 1) / 2 + (m - l); }
+constexpr int TC_WPT = (TC_TRI + 32 * 8 - 1) / (32 * 8);  // triangle entries per epilogue thread
+// Tile item u of a shift for T = ceil(L/64) tiles: u < T is the diagonal tile
+// (u, u); u >= T the off-diagonal pair number u - T, pairs (tl < tm) in
+// row-major order.
+__host__ __device__ inline void tc_tile_pair(int u, int T, int& tl, int& tm) {
+    if (u < T) {
+        tl = tm = u;
+        return;
+    }
+    int a = 0, rem = u - T;
+    while (rem >= T - 1 - a) {
+        rem -= T - 1 - a;
+        ++a;
+    }
+    tl = a;
+    tm = a + 1 + rem;
+}
+
 constexpr uint32_t TC_EXIT = 0xFFFFFFFFu;  // stage record of builders that have no more items
 static_assert(TC_STAGE_BYTES % 1024 == 0, "stages keep the 1024-byte alignment of the ring");
 
@@ -1070,6 +1098,23 @@ __global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, 
         I.w[e] = wv;
         if (I.wf) I.wf[e] = split_ff(wv);
     }
+    if (I.wt) {  // Re w of the diagonal tiles' triangles, in the tensor-core epilogue's order
+        const long long tot = (long long)I.T * TT * TT;
+        const long long tper = (tot + parts - 1) / parts, q0 = part * tper, q1 = min(tot, q0 + tper);
+        for (long long qq = q0 + t; qq < q1; qq += NT) {
+            const int tl = int(qq / (TT * TT)), q = int(qq % (TT * TT)), a = q >> 6, bb = q & 63;
+            if (a > bb) continue;
+            const int l = tl * TT + a, m = tl * TT + bb;
+            float2 v = make_float2(0.f, 0.f);
+            if (l < I.L && m < I.L) {
+                const double2 x = ctil_of(I, l), y = ctil_of(I, m);
+                const double re = x.x * y.x + x.y * y.y;
+                const float hi = (float)re;
+                v = make_float2(hi, (float)(re - (double)hi));
+            }
+            I.wt[(long long)tl * TC_TRI + tc_tri(a, bb)] = v;
+        }
+    }
 }
 
 // Shifted states of the on-chip instances of a tensor-core pass (Stage I):
@@ -1173,6 +1218,58 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(bar) : "memory");
 }
 
+// Instance of work item g, from the cached bases of the first TC_MAXC
+// instances (shared memory) or from the table.
+constexpr int TC_MAXC = 128;
+// What the state prefetch needs of an instance, kept in shared memory: the
+// packed states (null: none to prefetch) and n, T, ks, F.
+struct TcPlan {
+    const uint32_t* tcst;
+    int n, T, ks, F;
+};
+__device__ __forceinline__ int find_instance_cached(const Inst* insts, const long long* sbase, int count,
+                                                    long long g) {
+    if (count > TC_MAXC) return find_instance(insts, count, g);
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sbase[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Starts the bulk copy of work item g's packed state into `raw` (one thread;
+// completion is signalled on mbarrier `bar` with the byte count).  Returns
+// false when the item's state is not a packed on-chip state.  Reads only
+// shared memory when the batch has at most TC_MAXC instances.
+__device__ __forceinline__ bool tc_prefetch_state(const Inst* insts, const long long* sbase, const TcPlan* plan,
+                                                  int count, long long g, uint32_t* raw, uint32_t bar) {
+    const int ii = find_instance_cached(insts, sbase, count, g);
+    TcPlan p;
+    long long base;
+    if (count <= TC_MAXC) {
+        p = plan[ii];
+        base = sbase[ii];
+    } else {
+        const Inst& I = insts[ii];
+        p = TcPlan{I.states ? nullptr : reinterpret_cast<const uint32_t*>(I.tcst), I.n, I.T, I.ks, I.F};
+        base = I.item_base;
+    }
+    if (!p.tcst || p.n < 2) return false;
+    const int N = 1 << p.n, NU = p.T * (p.T + 1) / 2;
+    const long long s = ((g - base) / p.ks) / NU / p.F;
+    const uint32_t* src = p.tcst + (size_t)s * N;
+    const uint32_t bytes = uint32_t(N) * 4u;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of raw come first
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     su32(raw)),
+                 "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+    return true;
+}
+
 // Named barrier of `nthreads` threads that also returns the OR of a predicate
 // over them: every thread gets the same answer, so a group decides to stop
 // together.
@@ -1233,23 +1330,33 @@ __device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v) {
 }
 
 // One finished accumulator block (columns acc ..) folded by an epilogue warp
-// whose tensor-memory lanes are 32 q .. 32 q + 31: lanes 0..63 carry the first
+// whose tensor-memory lanes are 32 q .. 32 q + 31 (columns 32 ch .. 32 ch + 31
+// of its quadrant; the delta columns when ch = 0).  Off-diagonal pair (`off`):
+// lanes 0..63 are the first tile's hi rows, whose Gram with the second tile is
+// the sum of columns c (its hi) and 64 + c (its lo); lanes 64..127 its lo
+// rows, column c (lo lo is dropped).  Diagonal tile: lanes 0..63 carry the first
 // half of every stage (Gram columns 0..63; delta columns 128, 129 from hi b
 // and 132, 133 from lo b), lanes 64..127 the second half (columns 64..127;
 // delta 130, 131 and 134, 135).  The first block of an item starts the running
 // sums (columns TC_SUM.., TC_DSUM..), later ones add to them with
 // round-to-nearest adds; the last block goes to X[half][row][col] and
 // XD[half][row] in shared memory instead.
-__device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t acc, int q, int lane, bool first, bool last, float* X,
-                                        float2* XD) {
+__device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t acc, int q, int ch, int lane, bool first, bool last,
+                                        bool off, float* X, float2* XD) {
     const uint32_t base = tmem + ((32u * uint32_t(q)) << 16);
-    const int cq = q < 2 ? 0 : 64, dq = q < 2 ? 0 : 2;
+    const int cq = (q < 2 || off) ? 0 : 64, dq = q < 2 ? 0 : 2;
     const int xr = (q & 1) * 32 + lane;  // row within the half
     float* Xq = X + (q >> 1) * TC_X;
 #pragma unroll 1
-    for (int g = 0; g < 4; ++g) {
+    for (int g = 2 * ch; g < 2 * ch + 2; ++g) {  // this warp's 32 of the quadrant's 64 columns
         float v[16];
         tmem_ld16(base + acc + cq + 16 * g, v);
+        if (off && q < 2) {  // hi rows of the first tile: hi and lo columns of the second
+            float u[16];
+            tmem_ld16(base + acc + 64 + 16 * g, u);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] += u[j];
+        }
         if (!first) {
             float u[16];
             tmem_ld16(base + TC_SUM + 16 * g, u);
@@ -1263,42 +1370,56 @@ __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t acc, int q, int 
             tmem_st16(base + TC_SUM + 16 * g, v);
         }
     }
-    const float2 d0 = tmem_ld2(base + acc + 128 + dq), d1 = tmem_ld2(base + acc + 132 + dq);
-    float2 dv = make_float2(d0.x + d1.x, d0.y + d1.y);
-    if (!first) {
-        const float2 du = tmem_ld2(base + TC_DSUM);
-        dv.x += du.x;
-        dv.y += du.y;
+    if (ch == 0 && !off) {  // the delta columns
+        const float2 d0 = tmem_ld2(base + acc + 128 + dq), d1 = tmem_ld2(base + acc + 132 + dq);
+        float2 dv = make_float2(d0.x + d1.x, d0.y + d1.y);
+        if (!first) {
+            const float2 du = tmem_ld2(base + TC_DSUM);
+            dv.x += du.x;
+            dv.y += du.y;
+        }
+        if (last) XD[(q >> 1) * 64 + xr] = dv;
+        else tmem_st2(base + TC_DSUM, dv);
     }
-    if (last) XD[(q >> 1) * 64 + xr] = dv;
-    else tmem_st2(base + TC_DSUM, dv);
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// A builder thread's share of a stage: the 16 amplitudes jb .. jb + 15 of term
-// l's row `row` (l, or 64 + l for the stage's second half) at k = kk0 ..
-// kk0 + 15 of its half.  With jb a multiple of 16, the sources j ^ x_l of the
+// A builder thread's share of a stage: the 16 amplitudes jb .. jb + 15 of one
+// term at k = kk0 .. kk0 + 15, hi into row rhi of dhi and the low part into
+// row rlo of dlo (doubled as stored, or halved back when HALVE).  psi_hl holds
+// the Na amplitudes of the state's block that contains the sources (Na = N for
+// states in shared memory).  With jb a multiple of 16, the sources j ^ x_l of the
 // block are rb | (i ^ xlo) with rb = (jb ^ x_l) & ~15: a permutation of 16
 // consecutive amplitudes, whose signs are the parity of z_l & rb times the
 // per-term 16-bit pattern sgn (bit i: parity of z_l & (i ^ xlo)).  psi_hl holds
 // the packed pairs (shared memory; four copies when `copies`), psi_g the FP32
 // state in HBM.
-template <bool HBM>
-__device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const float* psi_g, int N, int jb, int kend,
-                                              bool act, uint32_t xl, uint32_t zl, const uint32_t (&sgn)[8], int row,
-                                              int kk0, unsigned char* zhi, unsigned char* zlo, bool copies) {
+// Two packed FP16 values times 1/2 (the low parts of an off-diagonal tile
+// pair, stored doubled): exact, but for values that fall below the normal
+// range (|lo| < 2^-14 of the scaled state, an error under 2^-25).
+__device__ __forceinline__ uint32_t halve2(uint32_t v) {
+    __half2 h = *reinterpret_cast<__half2*>(&v);
+    h = __hmul2(h, __float2half2_rn(0.5f));
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+template <bool HBM, bool HALVE>
+__device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const float* psi_g, int N, int Na, int jb, int kend,
+                                              bool act, uint32_t xl, uint32_t zl, const uint32_t (&sgn)[8], int kk0,
+                                              unsigned char* dhi, int rhi, unsigned char* dlo, int rlo, bool copies) {
     const uint32_t xhi = xl & ~15u, xlo = xl & 15u & uint32_t(N - 1);
     const int nval = act ? min(16, max(0, kend - jb)) : 0;
     const uint32_t rb = (uint32_t(jb) ^ xhi) & uint32_t(N - 1) & ~15u;
     const uint32_t flip = (__popc(zl & rb) & 1) ? 0x80008000u : 0u;  // the block's common sign
+    const uint32_t ra = rb & uint32_t(Na - 1);  // the sources' offset in psi_hl (a block of Na amplitudes)
     uint32_t w[16];
     if (!HBM && copies && nval == 16) {
-        // w[4c + r] = psi[rb + 4 (c ^ xc) + (r ^ (x_l & 3))] = cpy[rb + 4 (c ^ xc) + r]
-        const uint32_t* cpy = psi_hl + (xlo & 3u) * uint32_t(N + 8);  // copy holding psi[k ^ (x_l & 3)]
+        // w[4c + r] = psi[rb + 4 (c ^ xc) + (r ^ (x_l & 3))] = cpy[ra + 4 (c ^ xc) + r]
+        const uint32_t* cpy = psi_hl + (xlo & 3u) * uint32_t(Na + 8);  // copy holding psi[k ^ (x_l & 3)]
         const uint32_t xc = xlo >> 2;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const uint4 v = *reinterpret_cast<const uint4*>(cpy + rb + 4u * (uint32_t(c) ^ xc));
+            const uint4 v = *reinterpret_cast<const uint4*>(cpy + ra + 4u * (uint32_t(c) ^ xc));
             w[4 * c + 0] = v.x;
             w[4 * c + 1] = v.y;
             w[4 * c + 2] = v.z;
@@ -1308,10 +1429,7 @@ __device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const floa
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             uint32_t x = 0u;
-            if (i < nval) {
-                const uint32_t src = rb | (uint32_t(i) ^ xlo);
-                x = HBM ? split_h2l(psi_g[src] * TC_SCALE) : psi_hl[src];
-            }
+            if (i < nval) x = HBM ? split_h2l(psi_g[rb | (uint32_t(i) ^ xlo)] * TC_SCALE) : psi_hl[ra | (uint32_t(i) ^ xlo)];
             w[i] = x;
         }
     }
@@ -1328,9 +1446,15 @@ __device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const floa
         lo.y = __byte_perm(w[8 * g + 2], w[8 * g + 3], 0x7632) ^ sgn[4 * g + 1] ^ flip;
         lo.z = __byte_perm(w[8 * g + 4], w[8 * g + 5], 0x7632) ^ sgn[4 * g + 2] ^ flip;
         lo.w = __byte_perm(w[8 * g + 6], w[8 * g + 7], 0x7632) ^ sgn[4 * g + 3] ^ flip;
-        const int kk = kk0 + 8 * g;  // k within the stage's TCK/2
-        *reinterpret_cast<uint4*>(zhi + tc_off16(row, kk)) = hi;
-        *reinterpret_cast<uint4*>(zlo + tc_off16(row, kk)) = lo;
+        if (HALVE) {
+            lo.x = halve2(lo.x);
+            lo.y = halve2(lo.y);
+            lo.z = halve2(lo.z);
+            lo.w = halve2(lo.w);
+        }
+        const int kk = kk0 + 8 * g;  // k within the stage's 64-amplitude k range
+        *reinterpret_cast<uint4*>(dhi + tc_off16(rhi, kk)) = hi;
+        *reinterpret_cast<uint4*>(dlo + tc_off16(rlo, kk)) = lo;
     }
 }
 
@@ -1344,9 +1468,11 @@ __device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const floa
 // amplitude part, stages) from the builders to the epilogue by `itf` and back
 // by `ite`.  Every wait gives up after budget_ns nanoseconds; a thread that has
 // seen the abort flag waits no more.
+// The CTA's 25 warps are spread over the SM's four sub-partitions (16,384
+// registers each, seven warps on one of them): at most 72 registers a thread.
 __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ insts, int count, long long total,
                                                      unsigned long long* queue, int* status, int copy_nmax,
-                                                     int psi_region, long long budget_ns) {
+                                                     int psi_region, int raw_off, long long budget_ns) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1357,8 +1483,12 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
     __shared__ uint32_t s_tmem;
     __shared__ long long s_item;
     __shared__ int s_abort;
-    __shared__ uint32_t sxl[64], szl[64];
+    __shared__ uint32_t sxl[128], szl[128];  // masks of the item's tile (and of the pair's second tile)
     __shared__ float sred[3][2][TC_EW];
+    __shared__ uint16_t stri[TC_TRI];  // (l, m) of triangle entry e: l | m << 8
+    __shared__ long long s_ibase[TC_MAXC];  // item bases of the first TC_MAXC instances
+    __shared__ TcPlan s_plan[TC_MAXC];       // and what their state prefetch needs
+    __shared__ __align__(8) unsigned long long stb;  // the next state's bulk copy
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     unsigned char* base;
     {
@@ -1366,6 +1496,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         base = smem_raw + ((1024u - (a & 1023u)) & 1023u);
     }
     uint32_t* psi_hl = reinterpret_cast<uint32_t*>(base + TC_NSTG * TC_STAGE_BYTES);
+    uint32_t* raw = raw_off >= 0 ? reinterpret_cast<uint32_t*>(base + raw_off) : nullptr;  // prefetched state
     float* X = reinterpret_cast<float*>(base + TC_NSTG * TC_STAGE_BYTES + psi_region);
     float2* XD = reinterpret_cast<float2*>(X + 2 * TC_X);
     if (t == 0) {
@@ -1382,6 +1513,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ite[k])), "r"(1));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&drainb)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&stb)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_abort = 0;
     }
@@ -1391,6 +1523,15 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         const int st = c >> 7, arr = (c >> 6) & 1, ks4 = (c >> 4) & 3, u = c & 15;
         *reinterpret_cast<uint4*>(base + st * TC_STAGE_BYTES + arr * TC_OPND_BYTES + ks4 * TC_KSTEP_BYTES +
                                   (17 * 2) * 128 + u * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int q = t; q < 64 * 64; q += TCT) {
+        const int l = q >> 6, m = q & 63;
+        if (l <= m) stri[tc_tri(l, m)] = uint16_t(l | (m << 8));
+    }
+    for (int i = t; i < min(count, TC_MAXC); i += TCT) {
+        const Inst& I = insts[i];
+        s_ibase[i] = I.item_base;
+        s_plan[i] = TcPlan{I.states ? nullptr : reinterpret_cast<const uint32_t*>(I.tcst), I.n, I.T, I.ks, I.F};
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (w == 0) {
@@ -1404,42 +1545,108 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
 
     if (w < TC_BW) {  // ---------------------------------------------------------------- builders
         const int tt = t;
+        // task of this thread in a stage: term l of the tile, 16-amplitude block
+        // `sub`, and side hf: the stage's second 64 amplitudes (diagonal tile) or
+        // the pair's second tile (off-diagonal pair)
         const int l = (tt & 7) | ((w & 7) << 3), sub = (lane >> 3) & 3, hf = w >> 3;
         uint32_t eph = 0u, pend = 0u;  // bit st: parity of empty[st] to wait for; stage st in flight
         uint32_t iph = 0u, iused = 0u;  // item ring (thread 0): parity of ite[r]; slot r used before
         int ir = 0;
         uint32_t gc = 0u;  // stages handed over so far
         bool ab = false;   // this thread saw a wait give up (shared with the group at its barriers)
+        // Thread 0 takes items one ahead: `cur` is the next item to run, `nxt` the
+        // one after (its queue position is fetched while `cur` runs), and the
+        // state of `cur` is copied into `raw` by the bulk-copy engine meanwhile.
+        long long cur = total, nxt = total;
+        bool pf = false;   // thread 0: a state copy is in flight
+        uint32_t sph = 0u;  // parity of the state copy's mbarrier
+        if (tt == 0) {
+            cur = (long long)atomicAdd(queue, 1ull);
+            if (cur < total) {
+                nxt = (long long)atomicAdd(queue, 1ull);
+                if (raw) pf = tc_prefetch_state(insts, s_ibase, s_plan, count, cur, raw, su32(&stb));
+            }
+        }
         for (;;) {
-            if (tt == 0) s_item = (aborted(&s_abort) || ab) ? total : (long long)atomicAdd(queue, 1ull);
+            if (tt == 0) s_item = (aborted(&s_abort) || ab) ? total : cur;
             ab = bar_or(1, TC_BT, ab);
             const long long gi = s_item;
             ab = bar_or(1, TC_BT, ab);
             if (ab || gi >= total) break;
-            const int ii = find_instance(insts, count, gi);
+            const int ii = find_instance_cached(insts, s_ibase, count, gi);
             const Inst& I = insts[ii];
             const int local = int(gi - I.item_base);
-            const int n = I.n, N = 1 << n, L = I.L, ks = I.ks;
-            const int ksi = local % ks, s = local / ks;
+            const int n = I.n, N = 1 << n, L = I.L, ks = I.ks, T = I.T, NU = T * (T + 1) / 2;
+            const int ksi = local % ks, u = (local / ks) % NU, f = (local / ks / NU) % I.F, s = (local / ks / NU) / I.F;
+            int tl, tm;
+            tc_tile_pair(u, T, tl, tm);
+            // a pair of different tiles, or a local-cost flavour f > 0 (the second side's
+            // strings X_j A_m = sigma(x_m ^ e_j, z_m), j = f - 1): stages of 64 amplitudes,
+            // [hi; lo] rows on both sides
+            const bool off = tl != tm || f > 0;
+            const uint32_t xflip = f > 0 ? (1u << (f - 1)) : 0u;
             const int kper = N / ks, kbeg = ksi * kper, kend = kbeg + kper;
-            const int nch = (kend - kbeg + TCK - 1) / TCK;
+            const int step = off ? TCK / 2 : TCK;
+            const int nch = (kend - kbeg + step - 1) / step;
             if (tt == 0) {  // the item's record for the epilogue
                 if ((iused >> ir) & 1u) {
                     if (!ab && (aborted(&s_abort) || !mbar_wait(su32(&ite[ir]), (iph >> ir) & 1u, budget_ns))) ab = true;
                     iph ^= 1u << ir;
                 }
                 iused |= 1u << ir;
-                irec[ir] = make_int4(ii, s, ksi, nch);
+                irec[ir] = make_int4(ii, s, ksi | (u << 16), nch | (f << 16));  // ksi < 2^16 (2^20 / 2048 parts)
                 mbar_arrive(su32(&itf[ir]));
             }
             ir = (ir + 1) % TC_NIT;
-            if (tt < 64) {
-                sxl[tt] = tt < L ? I.xm[tt] : 0u;
-                szl[tt] = tt < L ? I.zm[tt] : 0u;
+            if (tt < 128) {
+                const int gt = (tt < 64 ? tl : tm) * TT + (tt & 63);
+                sxl[tt] = gt < L ? I.xm[gt] ^ (tt < 64 ? 0u : xflip) : 0u;
+                szl[tt] = gt < L ? I.zm[gt] : 0u;
             }
             const float* psi_g = I.states ? reinterpret_cast<const float*>(I.states) + (size_t)s * N : nullptr;
-            const bool copies = !I.states && tc_copies(n, copy_nmax);
-            if (!I.states) {  // the packed state of shift s (built by k_tc_states)
+            // A state in HBM whose item reads only its own block of HBM_K amplitudes
+            // (every X-mask of the item's tiles below HBM_K) is staged once in shared
+            // memory and gathered from there like an on-chip state.
+            bool blk = false;
+            if (I.states) {
+                const int gt = (tt < 64 ? tl : tm) * TT + (tt & 63);
+                const bool far = tt < 128 && gt < L && sxl[tt] >= uint32_t(HBM_K);
+                blk = kper == HBM_K && !bar_or(1, TC_BT, far);
+            }
+            const int Na = blk ? int(HBM_K) : N;  // amplitudes in shared memory
+            const bool copies = (!I.states || blk) && tc_copies(blk ? HBM_KQ : n, copy_nmax);
+            const bool in_raw = raw && !I.states && n >= 2;  // the state was copied into raw
+            if (in_raw) {
+                if (!ab && (aborted(&s_abort) || !mbar_wait(su32(&stb), sph, budget_ns))) ab = true;
+                sph ^= 1u;
+                if (tt == 0) pf = false;
+                // copy t (t = 0 only without copies): psi[k ^ t] at word t (N + 8) + k
+                const int ncp = copies ? 4 : 1;
+                for (int k = tt; k < N; k += TC_BT) {
+                    const uint32_t v = raw[k];
+                    for (int t3 = 0; t3 < ncp; ++t3) psi_hl[t3 * (N + 8) + (k ^ t3)] = v;
+                }
+            } else if (blk) {  // the item's block of the FP32 state in HBM, split into packed pairs here
+                // the FP32 block lands in the last copy's room (with copies) or in place
+                float* stage = reinterpret_cast<float*>(psi_hl + (copies ? 3 * (Na + 8) : 0));
+                for (int k = 4 * tt; k < Na; k += 4 * TC_BT)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(stage + k)),
+                                 "l"(__cvta_generic_to_global(psi_g + kbeg + k))
+                                 : "memory");
+                asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+                bar_n(1, TC_BT);
+                float vb[HBM_K / TC_BT];
+#pragma unroll
+                for (int e = 0; e < HBM_K / TC_BT; ++e) vb[e] = stage[tt * (HBM_K / TC_BT) + e];
+                bar_n(1, TC_BT);
+                const int ncp = copies ? 4 : 1;
+#pragma unroll
+                for (int e = 0; e < HBM_K / TC_BT; ++e) {
+                    const int k = tt * (HBM_K / TC_BT) + e;
+                    const uint32_t v = split_h2l(vb[e] * TC_SCALE);
+                    for (int t3 = 0; t3 < ncp; ++t3) psi_hl[t3 * (Na + 8) + (k ^ t3)] = v;
+                }
+            } else if (!I.states) {  // the packed state of shift s (built by k_tc_states)
                 const uint32_t* src = reinterpret_cast<const uint32_t*>(I.tcst) + (size_t)s * N;
                 if (N >= 4) {
                     for (int k = 4 * tt; k < N; k += 4 * TC_BT)
@@ -1452,7 +1659,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 }
             }
             ab = bar_or(1, TC_BT, ab);
-            if (copies) {  // copy t: psi[k ^ t] at word t (N + 8) + k
+            if (copies && !in_raw && !blk) {  // copy t: psi[k ^ t] at word t (N + 8) + k
                 for (int k = tt; k < N; k += TC_BT) {
                     const uint32_t v = psi_hl[k];
 #pragma unroll
@@ -1460,7 +1667,16 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 }
                 bar_n(1, TC_BT);
             }
-            const uint32_t xl = sxl[l], zl = szl[l];
+            if (tt == 0) {  // raw is free again: the next item's state, and the queue position after it
+                cur = nxt;
+                if (cur < total && !ab && !aborted(&s_abort)) {
+                    nxt = (long long)atomicAdd(queue, 1ull);
+                    if (raw) pf = tc_prefetch_state(insts, s_ibase, s_plan, count, cur, raw, su32(&stb));
+                }
+            }
+            const int side = off ? hf : 0;
+            const bool act = (off && hf ? tm : tl) * TT + l < L;
+            const uint32_t xl = sxl[side * 64 + l], zl = szl[side * 64 + l];
             uint32_t sgn[8];  // word g: sign bits of elements 2g (bit 15) and 2g + 1 (bit 31) of a 16-block
             {
                 const uint32_t xlo = xl & 15u & uint32_t(N - 1);
@@ -1480,8 +1696,8 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 }
                 unsigned char* zhi = base + st * TC_STAGE_BYTES;
                 unsigned char* zlo = zhi + TC_OPND_BYTES;
-                const int j0 = kbeg + c * TCK;
-                const bool brow = tt < TC_BOP_STAGE / 16;
+                const int j0 = kbeg + c * step;
+                const bool brow = !off && I.bop && tt < TC_BOP_STAGE / 16;
                 if (brow) {  // the stage's b rows (j0 is a multiple of TCK), copied while the terms are built
                     const uint4* srcb = reinterpret_cast<const uint4*>(I.bop) + (long long)(j0 / TCK) * (TC_BOP_STAGE / 16) + tt;
                     const int arr = tt >> 6, ks4 = (tt >> 4) & 3, kh = (tt >> 3) & 1, br = tt & 7;
@@ -1490,16 +1706,33 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                                  "l"(__cvta_generic_to_global(srcb))
                                  : "memory");
                 }
-                const int jb = j0 + hf * (TCK / 2) + sub * 16;
-                if (I.states)
-                    tc_build_half<true>(nullptr, psi_g, N, jb, kend, l < L, xl, zl, sgn, row, sub * 16, zhi, zlo, false);
-                else
-                    tc_build_half<false>(psi_hl, nullptr, N, jb, kend, l < L, xl, zl, sgn, row, sub * 16, zhi, zlo,
-                                         copies);
+                // diagonal: hi to array hi, 2 lo to array 2 lo, row l or 64 + l by half;
+                // off-diagonal: the side's array (hi: first tile, lo: second), hi to
+                // row l and lo (halved back) to row 64 + l
+                const bool gl = I.states && !blk;  // gather from the state in HBM
+                if (!off) {
+                    const int jb = j0 + hf * (TCK / 2) + sub * 16;
+                    if (gl)
+                        tc_build_half<true, false>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, sub * 16, zhi, row,
+                                                   zlo, row, false);
+                    else
+                        tc_build_half<false, false>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, sub * 16, zhi,
+                                                    row, zlo, row, copies);
+                } else {
+                    const int jb = j0 + sub * 16;
+                    unsigned char* dst = hf ? zlo : zhi;
+                    if (gl)
+                        tc_build_half<true, true>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, sub * 16, dst, l,
+                                                  dst, 64 + l, false);
+                    else
+                        tc_build_half<false, true>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, sub * 16, dst, l,
+                                                   dst, 64 + l, copies);
+                }
                 if (brow) asm volatile("cp.async.wait_all;" ::: "memory");
                 if (tt == 0) {
                     srec[st][0] = su32(zhi);
-                    srec[st][1] = (c % TC_FLUSH == 0 ? 1u : 0u) | ((c % TC_FLUSH == TC_FLUSH - 1 || c + 1 == nch) ? 2u : 0u);
+                    srec[st][1] = (c % TC_FLUSH == 0 ? 1u : 0u) | ((c % TC_FLUSH == TC_FLUSH - 1 || c + 1 == nch) ? 2u : 0u) |
+                                  (off ? 4u : 0u);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(su32(&fullb[st]));
@@ -1518,6 +1751,8 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 if (((iused >> ir) & 1u) && !ab && !aborted(&s_abort)) mbar_wait(su32(&ite[ir]), (iph >> ir) & 1u, budget_ns);
                 irec[ir] = make_int4(-1, 0, 0, 0);
                 mbar_arrive(su32(&itf[ir]));
+                // a state copy still in flight lands before the shared memory is released
+                if (pf && !mbar_wait(su32(&stb), sph, TC_DRAIN_NS)) ab = true;
             }
         }
         if (ab) s_abort = 1;
@@ -1546,6 +1781,17 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                     aused |= 1u << acc;
                 }
                 const uint32_t lb = hb + TC_OPND_BYTES, tm = s_tmem + acc * TC_ACC1;
+                if (fl & 4u) {  // off-diagonal pair: [hi; lo] of the first tile against [hi; lo] of the second
+#pragma unroll
+                    for (int ksx = 0; ksx < TCK / 32; ++ksx) {
+                        const uint32_t acc0 = ((fl & 1u) && ksx == 0) ? 0u : 1u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tm),
+                            "l"(tc_desc(hb + ksx * TC_KSTEP_BYTES)), "l"(tc_desc(lb + ksx * TC_KSTEP_BYTES)),
+                            "r"(tc_idesc(128)), "r"(acc0));
+                    }
+                } else
 #pragma unroll
                 for (int ksx = 0; ksx < TCK / 32; ++ksx) {
                     const uint64_t dh = tc_desc(hb + ksx * TC_KSTEP_BYTES), dl = tc_desc(lb + ksx * TC_KSTEP_BYTES);
@@ -1553,8 +1799,8 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                     const uint32_t acc0 = ((fl & 1u) && ksx == 0) ? 0u : 1u;
                     asm volatile(
                         "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %6, 0;\n\tsetp.eq.b32 q, %6, %6;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %2, %4, p;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %3, %5, q;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %2, %2, %4, p;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %2, %3, %5, q;\n\t"
                         "tcgen05.mma.cta_group::1.kind::f16 [%1], %3, %7, %8, q;\n\t}\n" ::"r"(tm),
                         "r"(tm + 128u), "l"(dh), "l"(dl), "r"(tc_idesc(TC_NB)), "r"(tc_idesc(128)), "r"(acc0),
                         "l"(db), "r"(tc_idesc(16)));
@@ -1574,7 +1820,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         }
         __syncwarp();
     } else {  // ----------------------------------------------------------------------------- epilogue
-        const int et = t - (TC_BT + 32), ew = et >> 5, q = w & 3;  // q: this warp's quarter of the TMEM lanes
+        const int et = t - (TC_BT + 32), ew = et >> 5, q = w & 3, ch = ew >> 2;  // q: this warp's TMEM lane quarter
         uint32_t fph = 0u, aph = 0u, acc = 0u;
         int r = 0;
         bool ab = false;
@@ -1586,8 +1832,28 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             const int4 rc = irec[r];
             if (rc.x < 0) break;
             const Inst& I = insts[rc.x];
-            const int s = rc.y, ksi = rc.z, nch = rc.w, L = I.L, ks = I.ks;
+            const int s = rc.y, ksi = rc.z & 0xFFFF, u = rc.z >> 16, nch = rc.w & 0xFFFF, f = rc.w >> 16;
+            const int L = I.L, ks = I.ks, T = I.T;
+            int tl, tm;
+            tc_tile_pair(u, T, tl, tm);
+            const bool off = tl != tm || f > 0;
             const int nblk = (nch + TC_FLUSH - 1) / TC_FLUSH;
+            const int nl = min(TT, L - tl * TT), nm = min(TT, L - tm * TT);  // terms in the two tiles
+            // this thread's first weights, loaded while the item's MMAs run: entries et + 256 k of
+            // the diagonal tile's triangle (Re w as float pairs), or of the 64 x 64 block
+            float2 wv[TC_WPT];
+#pragma unroll
+            for (int k = 0; k < TC_WPT; ++k) {
+                const int e = et + TC_ET * k;
+                if (!off) {
+                    wv[k] = e < TC_TRI ? I.wt[(long long)tl * TC_TRI + e] : make_float2(0.f, 0.f);
+                } else {
+                    const int a = e >> 6, bcol = e & 63;
+                    const float4 w4 = (a < nl && bcol < nm) ? I.wf[(long long)(tl * TT + a) * L + tm * TT + bcol]
+                                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+                    wv[k] = make_float2(w4.x, w4.y);
+                }
+            }
             for (int b = 0; b < nblk; ++b) {
                 if (et == 0 && (aborted(&s_abort) || !mbar_wait(su32(&accf[acc]), (aph >> acc) & 1u, budget_ns)))
                     ab = true;
@@ -1595,58 +1861,78 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 ab = bar_or(2, TC_ET, ab);
                 if (ab) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                tc_fold(s_tmem, acc * TC_ACC1, q, lane, b == 0, b + 1 == nblk, X, XD);
+                tc_fold(s_tmem, acc * TC_ACC1, q, ch, lane, b == 0, b + 1 == nblk, off, X, XD);
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 mbar_arrive(su32(&acce[acc]));
                 acc ^= 1u;
             }
             if (ab) break;
-            bar_n(2, TC_ET);  // both Gram quadrants and the delta sums are in X, XD
-            // Weighting.  G' = hi hi^T + hi (2 lo)^T has the symmetric part G~
-            // (scaled by 2^24), and Re(w) is symmetric: sum_lm Re(w_lm) G~_lm =
-            // sum over l <= m of Re(w_lm) g_lm with g_ll = G'_ll and g_lm = G'_lm +
-            // G'_ml (both quadrants).  Entries (a, b) with b = et % 64 and
-            // a = et / 64 + 2k; the weights of eight rows are loaded before use.
+            bar_n(2, TC_ET);  // the readout is in X (and XD)
             const float* Xu = X;
             const float* Xl = X + TC_X;
             float S = 0.f, E = 0.f, TrS = 0.f, TrE = 0.f, TiS = 0.f, TiE = 0.f;
-            {
-                const int bcol = et & 63, a0 = et >> 6;
-                float2* Gp = (s == 0 && I.Gpart) ? reinterpret_cast<float2*>(I.Gpart) + (long long)ksi * L * L : nullptr;
-#pragma unroll 1
-                for (int kb = 0; kb < 32; kb += 8) {
-                    float2 wv[8];
+            float2* Gp = (s == 0 && I.Gpart) ? reinterpret_cast<float2*>(I.Gpart) + (long long)ksi * L * L : nullptr;
+            if (!off) {
+                // Diagonal tile.  G' = hi hi^T + hi (2 lo)^T has the symmetric part G~
+                // (scaled by 2^24), and Re(w) is symmetric: sum_lm Re(w_lm) G~_lm =
+                // sum over l <= m of Re(w_lm) g_lm with g_ll = G'_ll and g_lm = G'_lm +
+                // G'_ml (both halves).  The 2080 entries l <= m are dealt out evenly:
+                // thread et takes entries et + 256 k of the row-major triangle.
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const int a = a0 + 2 * (kb + k);
-                        const float4 w4 = (a <= bcol && bcol < L) ? I.wf[a * L + bcol] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        wv[k] = make_float2(w4.x, w4.y);  // Re hi, Re lo
-                    }
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const int a = a0 + 2 * (kb + k);
-                        if (a > bcol) continue;
-                        float g = Xu[a * 65 + bcol] + Xl[a * 65 + bcol];
-                        if (a < bcol) g += Xu[bcol * 65 + a] + Xl[bcol * 65 + a];
-                        ff_mac(S, E, wv[k].x, wv[k].y, g);
-                        if (Gp && bcol < L) {
-                            const float2 gv = make_float2((a < bcol ? 0.5f * g : g) * TC_UNSCALE, 0.f);
-                            Gp[(long long)a * L + bcol] = gv;
-                            Gp[(long long)bcol * L + a] = gv;
-                        }
+                for (int k = 0; k < TC_WPT; ++k) {
+                    const int e = et + TC_ET * k;
+                    if (e >= TC_TRI) break;
+                    const int a = stri[e] & 0xFF, bcol = stri[e] >> 8;
+                    if (bcol >= nl) continue;
+                    float g = Xu[a * 65 + bcol] + Xl[a * 65 + bcol];
+                    if (a < bcol) g += Xu[bcol * 65 + a] + Xl[bcol * 65 + a];
+                    ff_mac(S, E, wv[k].x, wv[k].y, g);
+                    if (Gp) {
+                        const float2 gv = make_float2((a < bcol ? 0.5f * g : g) * TC_UNSCALE, 0.f);
+                        const long long ga = tl * TT + a, gb = tl * TT + bcol;
+                        Gp[ga * L + gb] = gv;
+                        Gp[gb * L + ga] = gv;
                     }
                 }
-            }
-            if (et < 64 && et < L) {  // delta~_l and its product with c~_l
-                const float2 du = XD[et], dl = XD[64 + et];
-                const float dsc = 1.f / (TC_SCALE * tc_bscale(*I.bn2));  // exact: a power of two
-                const float2 dacc = make_float2((du.x + dl.x) * dsc, -(du.y + dl.y) * dsc);  // conj(b) phi
-                const float4 cv = I.cf[et];  // c~_l as (Re hi, Re lo, Im hi, Im lo)
-                ff_mac(TrS, TrE, cv.x, cv.y, dacc.x);
-                ff_mac(TrS, TrE, -cv.z, -cv.w, dacc.y);
-                ff_mac(TiS, TiE, cv.x, cv.y, dacc.y);
-                ff_mac(TiS, TiE, cv.z, cv.w, dacc.x);
-                if (s == 0 && I.dpart) reinterpret_cast<float2*>(I.dpart)[(long long)ksi * L + et] = dacc;
+                if (et < 64 && et < nl && !I.local) {  // delta~_l and its product with c~_l
+                    const int gl = tl * TT + et;
+                    const float2 du = XD[et], dl = XD[64 + et];
+                    const float dsc = 1.f / (TC_SCALE * tc_bscale(*I.bn2));  // exact: a power of two
+                    const float2 dacc = make_float2((du.x + dl.x) * dsc, -(du.y + dl.y) * dsc);  // conj(b) phi
+                    const float4 cv = I.cf[gl];  // c~_l as (Re hi, Re lo, Im hi, Im lo)
+                    ff_mac(TrS, TrE, cv.x, cv.y, dacc.x);
+                    ff_mac(TrS, TrE, -cv.z, -cv.w, dacc.y);
+                    ff_mac(TiS, TiE, cv.x, cv.y, dacc.y);
+                    ff_mac(TiS, TiE, cv.z, cv.w, dacc.x);
+                    if (s == 0 && I.dpart) reinterpret_cast<float2*>(I.dpart)[(long long)ksi * L + gl] = dacc;
+                }
+            } else {
+                // Pair item: G~_ab = X_hi[a][b] + X_lo[a][b] for term a of the first tile
+                // and b of the second (for flavour f > 0, gamma^j_ab).  Different tiles
+                // stand for both orders of the pair (the Gram and gamma^j are symmetric,
+                // as is Re w), so each product counts twice (exact doubling).
+                const float fac = tl != tm ? 2.f : 1.f;
+#pragma unroll 2
+                for (int k = 0; k < TT * TT / TC_ET; ++k) {
+                    const int e = et + TC_ET * k, a = e >> 6, bcol = e & 63;
+                    float2 wk;
+                    if (k < TC_WPT) {
+                        wk = wv[k];
+                    } else {
+                        const float4 w4 = (a < nl && bcol < nm) ? I.wf[(long long)(tl * TT + a) * L + tm * TT + bcol]
+                                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                        wk = make_float2(w4.x, w4.y);
+                    }
+                    if (a >= nl || bcol >= nm) continue;
+                    const float g = Xu[a * 65 + bcol] + Xl[a * 65 + bcol];
+                    ff_mac(S, E, fac * wk.x, fac * wk.y, g);
+                    if (Gp && f == 0) {
+                        const float2 gv = make_float2(g * TC_UNSCALE, 0.f);
+                        const long long ga = tl * TT + a, gb = tm * TT + bcol;
+                        Gp[ga * L + gb] = gv;
+                        Gp[gb * L + ga] = gv;
+                    }
+                }
             }
             ff_warp_sum(S, E);
             ff_warp_sum(TrS, TrE);
@@ -1670,8 +1956,13 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                     }
                     qv[k] = (double)S2 + (double)E2;
                 }
-                I.Dpart[(long long)s * ks + ksi] = make_double2(qv[0] * (double)TC_UNSCALE, 0.0);
-                I.Tpart[(long long)s * ks + ksi] = make_double2(qv[1], qv[2]);
+                // slots as the CUDA-core tiles use them: diagonal tile u at u, pair p at
+                // T + 2p (and T + 2p + 1, which the tiles use for the pair's second half)
+                // (per flavour f of the local cost: slots (s F + f) T^2 ..)
+                const long long slot = ((long long)s * I.F + f) * T * T + (tl != tm ? T + 2 * (u - T) : u);
+                I.Dpart[slot * ks + ksi] = make_double2(qv[0] * (double)TC_UNSCALE, 0.0);
+                if (tl != tm) I.Dpart[(slot + 1) * ks + ksi] = make_double2(0.0, 0.0);
+                else if (f == 0 && !I.local) I.Tpart[((long long)s * T + tl) * ks + ksi] = make_double2(qv[1], qv[2]);
             }
             bar_n(2, TC_ET);  // X and the item record are free again
             if (et == 0) mbar_arrive(su32(&ite[r]));
@@ -2360,9 +2651,7 @@ struct HostInst {
     bool hbm;   // n > 12: states built in HBM
 };
 
-// Amplitudes per work item for states in HBM (each FP32 sum runs over half
-// of them; items are added in FP64).
-constexpr long long HBM_K = 2048;
+
 
 template <typename R>
 size_t smem_bytes(int nmax, int Pmax) {  // real state (padded to 4 values), two real chunks, b chunk, angles
@@ -2378,6 +2667,7 @@ struct PassShape {
     size_t smem;
     int copy_nmax;   // tensor-core kernel: states of 2^4 .. 2^copy_nmax amplitudes kept in four copies (0: none)
     int psi_region;  // tensor-core kernel: shared bytes of its state copies
+    int raw_off;     // tensor-core kernel: offset of the prefetched state's buffer (-1: no prefetch)
     int st_grid;     // tensor-core pass: CTAs per instance of k_tc_states (0: no state in shared memory)
     int st_smem;     // and its dynamic shared bytes
     long long budget_ns;  // tensor-core kernel: time limit of each bounded wait
@@ -2448,7 +2738,8 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
                                        ps.total, ctx->d_queue));
     else if (ps.tc)
         DVQLS_CUDA_TRY(ctx, launch_pdl(k_terms_tc, dim3(ps.grid), dim3(TCT), ps.smem, st, dtable, ps.count, ps.total,
-                                       ctx->d_queue, ctx->d_status, ps.copy_nmax, ps.psi_region, ps.budget_ns));
+                                       ctx->d_queue, ctx->d_status, ps.copy_nmax, ps.psi_region, ps.raw_off,
+                                       ps.budget_ns));
     else if (ps.fp32)
         DVQLS_CUDA_TRY(ctx, launch_pdl(k_terms_smem<float>, dim3(ps.grid), dim3(NT), ps.smem, st, dtable, ps.count,
                                        ps.total, ctx->d_queue));
@@ -2575,17 +2866,28 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     // classes); anything else runs the FP32 CUDA-core tiles.
     bool wht = precision == DVQLS_FP32_WHT;
     for (const auto& h : hi) wht = wht && h.T == 1 && h.n <= WHT_MAXN;
-    bool tc = !wht && (precision == DVQLS_FP32_TC || precision == DVQLS_FP32_WHT) && !local;
-    for (const auto& h : hi) tc = tc && h.T == 1;
-    int copy_nmax = 0;
-    if (tc) {  // and when both pipelines' shared memory fits one CTA
+    bool tc = !wht && (precision == DVQLS_FP32_TC || (precision == DVQLS_FP32_WHT && !local));
+    int copy_nmax = 0, raw_off = -1;
+    size_t raw_bytes = 0;
+    // the tensor-core kernel's shared state region: the largest on-chip state, and
+    // a staged block of HBM_K amplitudes when some state lives in HBM
+    bool any_hbm = false;
+    for (const auto& h : hi) any_hbm = any_hbm || h.hbm;
+    const int tc_nsm = std::max(any_smem ? nmax : 0, any_hbm ? HBM_KQ : 0);
+    if (tc) {  // and when the kernel's shared memory fits one CTA
         int optin = 0;
         cudaFuncAttributes fa;
         DVQLS_CUDA_TRY(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
         DVQLS_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, (const void*)k_terms_tc));
-        tc = tc_smem_bytes(any_smem ? nmax : 0, 0) + fa.sharedSizeBytes <= (size_t)optin;
-        for (int c = TC_COPY_NMAX; tc && any_smem && c >= 4 && !copy_nmax; --c)
-            if (tc_smem_bytes(nmax, c) + fa.sharedSizeBytes <= (size_t)optin) copy_nmax = c;
+        tc = tc_smem_bytes(tc_nsm, 0) + fa.sharedSizeBytes <= (size_t)optin;
+        for (int c = TC_COPY_NMAX; tc && tc_nsm > 0 && c >= 4 && !copy_nmax; --c)
+            if (tc_smem_bytes(tc_nsm, c) + fa.sharedSizeBytes <= (size_t)optin) copy_nmax = c;
+        // the next item's state is prefetched into a buffer of its own when it fits
+        if (tc && any_smem && nmax >= 2 &&
+            tc_smem_bytes(tc_nsm, copy_nmax) + (size_t(4) << nmax) + fa.sharedSizeBytes <= (size_t)optin) {
+            raw_off = int(size_t(TC_NSTG) * TC_STAGE_BYTES + tc_psi_region(tc_nsm, copy_nmax) + TC_EPI_BYTES);
+            raw_bytes = size_t(4) << nmax;
+        }
     }
     // The tensor-core pass builds the on-chip states in a kernel of its own.
     int st_grid = 0;
@@ -2598,7 +2900,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
             }
     if (st_grid > 0) DVQLS_CUDA_TRY(ctx, allow_dynamic_smem((const void*)k_tc_states));
     const size_t smem = wht  ? wht_smem_bytes(Pmax)
-                        : tc ? tc_smem_bytes(any_smem ? nmax : 0, copy_nmax)
+                        : tc ? tc_smem_bytes(tc_nsm, copy_nmax) + raw_bytes
                         : fp32 ? smem_bytes<float>(nmax, Pmax) : smem_bytes<double>(nmax, Pmax);
     const size_t r2 = fp32 ? 8 : 16;
     auto kfun = wht ? (const void*)k_terms_wht
@@ -2633,7 +2935,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     struct Off {
         size_t coef, xm, zm, alpha, b;       // staged inputs (ws) ...
         size_t pcoef, pxm, pzm, palpha, pb;  // ... and their pinned slots
-        size_t ctil, w, wf, cf, bop, wht, bf, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta, states, tcst;
+        size_t ctil, w, wf, cf, wt, bop, wht, bf, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta, states, tcst;
         size_t pcost, pgrad, pbeta, pdelta;
     };
     std::vector<Off> off(count);
@@ -2684,7 +2986,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         o.w = ar.reserve(L * L * 16);
         o.wf = fp32 ? ar.reserve(L * L * 16) : 0;  // float-float weights of the FP32 term kernels
         o.cf = fp32 ? ar.reserve(L * 16) : 0;
-        o.bop = tc ? ar.reserve(size_t(tc_bop_stages(h.N)) * TC_BOP_STAGE) : 0;
+        o.wt = tc ? ar.reserve(size_t(h.T) * TC_TRI * 8) : 0;
+        o.bop = tc && !local ? ar.reserve(size_t(tc_bop_stages(h.N)) * TC_BOP_STAGE) : 0;
         o.wht = wht ? ar.reserve(WHT_TABLE_BYTES) : 0;
         o.bf = wht ? ar.reserve(size_t(h.N) * 8) : 0;
         o.cs = ar.reserve(size_t(3) * h.P * 16);
@@ -2756,7 +3059,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         I.w = (double2*)(ws + o.w);
         I.wf = fp32 ? (float4*)(ws + o.wf) : nullptr;
         I.cf = fp32 ? (float4*)(ws + o.cf) : nullptr;
-        I.bop = tc ? (void*)(ws + o.bop) : nullptr;
+        I.wt = tc ? (float2*)(ws + o.wt) : nullptr;
+        I.bop = tc && !local ? (void*)(ws + o.bop) : nullptr;
         I.wht = wht ? (void*)(ws + o.wht) : nullptr;
         I.bf = wht ? (float2*)(ws + o.bf) : nullptr;
         I.cs = (double2*)(ws + o.cs);
@@ -2796,7 +3100,9 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
             const int i = ord[oi];
             Inst I = rec[i];
             I.ks = kk[i];
-            I.items = wht ? I.S : I.S * I.F * I.T * I.T * I.ks;  // a Walsh-Hadamard item covers every flavour
+            // a Walsh-Hadamard item covers every flavour; the tensor-core tiles take
+            // each pair of tiles once (T (T + 1) / 2 per shift), the CUDA-core tiles T^2
+            I.items = wht ? I.S : tc ? I.S * I.F * (I.T * (I.T + 1) / 2) * I.ks : I.S * I.F * I.T * I.T * I.ks;
             I.item_base = base;
             base += I.items;
             table[oi] = I;
@@ -2810,7 +3116,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         ps.grid = (int)std::min<long long>(base, slots);
         ps.smem = smem;
         ps.copy_nmax = copy_nmax;
-        ps.psi_region = tc ? (int)tc_psi_region(any_smem ? nmax : 0, copy_nmax) : 0;
+        ps.psi_region = tc ? (int)tc_psi_region(tc_nsm, copy_nmax) : 0;
+        ps.raw_off = raw_off;
         ps.st_grid = st_grid;
         ps.st_smem = (int)st_smem;
         ps.budget_ns = ctx->wait_budget_us * 1000;
@@ -2911,6 +3218,114 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     if (rc) return rc;
     finish_out(ctx, pend);
     return DVQLS_OK;
+}
+
+// ------------------------------------------------ fidelity of a state in HBM
+// F = |<xhat|psi(alpha)>|^2 / ||xhat||^2 (Sec. 3.1) for states above the
+// shared-memory size: psi in FP64 by the HBM state passes (one shift), then a
+// reduction whose block partials are added in a fixed order.
+constexpr int FIDH_T = 256;
+
+__global__ void __launch_bounds__(FIDH_T) k_fid_angles(const Inst* __restrict__ insts, int* status) {
+    const Inst& I = insts[0];
+    for (int a = threadIdx.x; a < I.P; a += FIDH_T) {
+        const double al = I.alpha[a];
+        if (!isfinite(al)) set_status(status, DEV_NONFINITE_INPUT);
+        double sn, c;
+        sincos(0.5 * al, &sn, &c);
+        I.cs[a] = make_double2(c, sn);
+    }
+}
+
+// Block b: sum over its share of j of conj(xhat_j) psi_j (psi real) and |xhat_j|^2.
+__global__ void __launch_bounds__(FIDH_T) k_fid_partial(const Inst* __restrict__ insts, const double2* __restrict__ xh,
+                                                        double* part) {
+    const Inst& I = insts[0];
+    const long long N = 1LL << I.n;
+    const double* psi = reinterpret_cast<const double*>(I.states);
+    double re = 0.0, im = 0.0, nr = 0.0;
+    for (long long j = (long long)blockIdx.x * FIDH_T + threadIdx.x; j < N; j += (long long)gridDim.x * FIDH_T) {
+        const double2 x = xh[j];
+        const double p = psi[j];
+        re += x.x * p;
+        im -= x.y * p;
+        nr += x.x * x.x + x.y * x.y;
+    }
+    __shared__ double red[3][FIDH_T / 32];
+    for (int o = 16; o; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+        nr += __shfl_xor_sync(0xffffffffu, nr, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][w] = re;
+        red[1][w] = im;
+        red[2][w] = nr;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double v = 0.0;
+        for (int k = 0; k < FIDH_T / 32; ++k) v += red[threadIdx.x][k];
+        part[3 * blockIdx.x + threadIdx.x] = v;
+    }
+}
+
+__global__ void k_fid_final(const double* __restrict__ part, int nb, int* status, double* F) {
+    if (threadIdx.x != 0) return;
+    double re = 0.0, im = 0.0, nr = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        re += part[3 * b];
+        im += part[3 * b + 1];
+        nr += part[3 * b + 2];
+    }
+    if (!(nr > 0.0) || !isfinite(nr)) set_status(status, DEV_BAD_NORM);
+    *F = (re * re + im * im) / nr;
+}
+
+int fidelity_hbm(dvqls_ctx* ctx, int n, int d, const double* alpha, const double* xhat, double* F) {
+    const int P = n * (d + 1);
+    const long long N = 1LL << n;
+    const int nb = (int)std::min<long long>(4LL * ctx->num_sms, (N + FIDH_T - 1) / FIDH_T);
+    Arena ar, pin;
+    const size_t o_t = ar.reserve(sizeof(Inst)), p_t = pin.reserve(sizeof(Inst));
+    const size_t o_al = ar.reserve(size_t(P) * 8), p_al = pin.reserve(size_t(P) * 8);
+    const size_t o_x = ar.reserve(size_t(N) * 16), p_x = pin.reserve(size_t(N) * 16);
+    const size_t o_cs = ar.reserve(size_t(P) * 16);
+    const size_t o_st = ar.reserve(size_t(N) * 8);
+    const size_t o_pt = ar.reserve(size_t(nb) * 24);
+    const size_t o_F = ar.reserve(8), p_F = pin.reserve(8);
+    int rc = ensure_workspace(ctx, ar.total());
+    if (!rc) rc = ensure_pinned(ctx, pin.total());
+    if (!rc) rc = pin_acquire(ctx);
+    if (rc) return rc;
+    Inst I;
+    memset(&I, 0, sizeof I);
+    I.n = n;
+    I.d = d;
+    I.P = P;
+    I.S = 1;
+    I.alpha = (const double*)stage_in(ctx, alpha, size_t(P) * 8, p_al, o_al);
+    const double2* xd = (const double2*)stage_in(ctx, xhat, size_t(N) * 16, p_x, o_x);
+    I.cs = (double2*)(ctx->ws + o_cs);
+    I.states = ctx->ws + o_st;
+    Inst* dt = (Inst*)(ctx->ws + o_t);
+    memcpy(ctx->pin + p_t, &I, sizeof I);
+    DVQLS_CUDA_TRY(ctx, cudaMemcpyAsync(dt, ctx->pin + p_t, sizeof I, cudaMemcpyHostToDevice, ctx->stream));
+    rc = pin_release(ctx);
+    if (rc) return rc;
+    k_fid_angles<<<1, FIDH_T, 0, ctx->stream>>>(dt, ctx->d_status);
+    rc = build_hbm_states<double>(ctx, dt, 0, n, d, 1, false);
+    if (rc) return rc;
+    k_fid_partial<<<nb, FIDH_T, 0, ctx->stream>>>(dt, xd, (double*)(ctx->ws + o_pt));
+    k_fid_final<<<1, 32, 0, ctx->stream>>>((const double*)(ctx->ws + o_pt), nb, ctx->d_status,
+                                           (double*)(ctx->ws + o_F));
+    DVQLS_CUDA_TRY(ctx, cudaGetLastError());
+    std::vector<PendingOut> pend;
+    rc = enqueue_out(ctx, F, ctx->ws + o_F, 8, p_F, pend);
+    if (!rc) rc = sync_and_check(ctx);
+    if (rc) return rc;
+    return finish_out(ctx, pend);
 }
 
 }  // namespace dvqls

@@ -35,7 +35,7 @@ EXPORTED = [
     "dvqls_cost", "dvqls_cost_grad", "dvqls_cost_grad_batched",
     "dvqls_profile_enable", "dvqls_profile_read", "dvqls_set_wait_budget", "dvqls_cost_grad_noalloc",
     "dvqls_circuit_cost_grad_fp64", "dvqls_fidelity", "dvqls_lcu_solve", "dvqls_lcu_solve_batched",
-    "dvqls_optimize",
+    "dvqls_optimize", "dvqls_optimize_resume",
     "dvqls_ws_param_count", "dvqls_ws_create", "dvqls_ws_destroy", "dvqls_ws_infer", "dvqls_ws_grad",
     "dvqls_ws_train_step", "dvqls_ws_get_params", "dvqls_ws_save", "dvqls_ws_load",
     "dvqls_local_cost_grad", "dvqls_local_cost_grad_batched",
@@ -67,6 +67,10 @@ class dvqls_adam(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("eps", ctypes.c_double), ("max_iter", ctypes.c_int), ("target_fidelity", ctypes.c_double),
                 ("precision", ctypes.c_int), ("targets", ctypes.c_void_p)]
+
+
+class dvqls_adam_state(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_void_p), ("v", ctypes.c_void_p), ("steps", ctypes.c_void_p)]
 
 
 class dvqls_opt_result(ctypes.Structure):
@@ -117,6 +121,9 @@ def lib():
                                               ctypes.c_double, ctypes.c_int, dp, vp, dp]
         L.dvqls_optimize.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dvqls_instance), dp, ctypes.POINTER(dvqls_adam),
                                      dp, ctypes.POINTER(dvqls_opt_result)]
+        L.dvqls_optimize_resume.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dvqls_instance), dp,
+                                            ctypes.POINTER(dvqls_adam), ctypes.POINTER(dvqls_adam_state), dp,
+                                            ctypes.POINTER(dvqls_opt_result)]
         L.dvqls_ws_param_count.argtypes = [ctypes.c_int] * 3
         L.dvqls_ws_param_count.restype = ctypes.c_longlong
         L.dvqls_ws_create.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_void_p)]
@@ -292,6 +299,17 @@ def dvqls_optimize(ctx, instances, xhat, opt, alpha_out):
     res = (dvqls_opt_result * len(instances))()
     _check(ctx, lib().dvqls_optimize(ctx, len(instances), instances, ptr(xhat), ctypes.byref(opt), ptr(alpha_out),
                                      res))
+    return list(res)
+
+
+def dvqls_optimize_resume(ctx, instances, xhat, opt, m, v, steps, alpha_out):
+    """dvqls_optimize from the Adam state (m, v: packed angle-sized arrays;
+    steps: int64 per instance), which is updated in place.  Returns the
+    per-instance results."""
+    res = (dvqls_opt_result * len(instances))()
+    st = dvqls_adam_state(ptr(m), ptr(v), ptr(steps))
+    _check(ctx, lib().dvqls_optimize_resume(ctx, len(instances), instances, ptr(xhat), ctypes.byref(opt),
+                                            ctypes.byref(st), ptr(alpha_out), res))
     return list(res)
 
 

@@ -27,17 +27,19 @@ def shift_ranges(S, world_size):
 
 def cost_grad_split(lib, ctx, ansatz, alpha, lcu, b, precision, dist, torch, device, group=None):
     """Cost and gradient of one instance whose shifts are shared among the
-    ranks of `dist` (an initialised torch.distributed).  Returns (cost,
-    grad) as tensors on `device`, identical on every rank."""
+    ranks of `dist` (an initialised torch.distributed; None: one rank takes
+    every shift).  Returns (cost, grad) as tensors on `device`, identical on
+    every rank."""
     n, depth = ansatz.n, ansatz.depth
     P = n * (depth + 1)
     S = 2 * P + 1
-    rank, ws = dist.get_rank(group), dist.get_world_size(group)
+    rank, ws = (dist.get_rank(group), dist.get_world_size(group)) if dist is not None else (0, 1)
     s0, s1 = shift_ranges(S, ws)[rank]
     part = torch.zeros(S * 4, dtype=torch.float64, device=device)
     if s1 > s0:
         lib.dvqls_cost_grad_partials(ctx, ansatz, alpha, lcu, b, precision, s0, s1, part)
-    dist.all_reduce(part, op=dist.ReduceOp.SUM, group=group)
+    if dist is not None:
+        dist.all_reduce(part, op=dist.ReduceOp.SUM, group=group)
     cost = torch.zeros(1, dtype=torch.float64, device=device)
     grad = torch.zeros(P, dtype=torch.float64, device=device)
     lib.dvqls_combine_partials(ctx, n, depth, part, cost, grad)

@@ -10,8 +10,9 @@ from paper_2604_14435_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-# 3: the Walsh-Hadamard classes (served for L <= 64, n <= 10; FP32 otherwise), held to the FP32 bounds
-TOL = {0: (1e-12, 1e-12), 1: (1e-6, 1e-5), 3: (1e-6, 1e-5)}
+# 2: the tensor-core tiles (flavour j as a Gram of the tile against its strings with x ^ e_j);
+# 3: the Walsh-Hadamard classes (served for L <= 64, n <= 10; FP32 otherwise); both held to the FP32 bounds
+TOL = {0: (1e-12, 1e-12), 1: (1e-6, 1e-5), 2: (1e-6, 1e-5), 3: (1e-6, 1e-5)}
 
 
 def cv(a):
@@ -30,7 +31,7 @@ def ok(got, ref, tol):
     return np.all(np.abs(np.asarray(got) - np.asarray(ref)) <= tol * np.maximum(1.0, np.abs(ref)))
 
 
-@pytest.mark.parametrize("prec", [0, 1, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("n,d,L", [(1, 1, 2), (2, 1, 5), (3, 2, 8), (5, 2, 33), (6, 1, 70), (8, 1, 20)])
 def test_local_cost_matches_oracle(dv, ctx, prec, n, d, L):
     rng = np.random.default_rng(900 + n + L)
@@ -47,7 +48,7 @@ def test_local_cost_matches_oracle(dv, ctx, prec, n, d, L):
     assert ok(c_only, ref["cost"], tc)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_local_cost_throughput_system(dv, ctx, prec):
     """n = 10 Toeplitz, top-64: the paper's 90,112-circuit evaluation, with
     sampled gamma overlaps checked against their Hadamard-test circuits."""
@@ -64,7 +65,7 @@ def test_local_cost_throughput_system(dv, ctx, prec):
     assert np.abs(cg - gamma).max() < 1e-13
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_local_cost_batched_and_hbm(dv, ctx, prec):
     rng = np.random.default_rng(3)
     probs = []

@@ -31,6 +31,21 @@ def test_fidelity_matches_oracle(dv, ctx, n, d):
     assert abs(F[0] - ref) <= 1e-12
 
 
+@pytest.mark.parametrize("n,d", [(13, 1), (16, 2), (20, 3)])
+def test_fidelity_states_in_hbm(dv, ctx, n, d):
+    """n > 12: the FP64 state is built in HBM; xhat near psi keeps F of order one."""
+    rng = np.random.default_rng(70 + n)
+    alpha = wl.random_angles(n * (d + 1), 71 + n)
+    psi = oterms.ansatz_state(n, d, alpha)
+    noise = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    xhat = psi + 0.7 * noise / np.linalg.norm(noise)
+    F = np.zeros(1)
+    dv.dvqls_fidelity(ctx, dv.make_ansatz(n, d), alpha, cv(xhat), F)
+    ref = oterms.fidelity(psi, xhat / np.linalg.norm(xhat))
+    assert 0.3 < ref < 0.9
+    assert abs(F[0] - ref) <= 1e-12
+
+
 def test_fidelity_of_planted_state_is_one(dv, ctx):
     n, d = 5, 2
     alpha = wl.random_angles(n * (d + 1), 1)
@@ -181,3 +196,54 @@ def test_grid_cg_large_systems(dv, ctx, case):
     else:
         assert np.linalg.norm(Ax - b) <= 10 * tol * np.linalg.norm(b)
     assert rr <= tol and it > 0
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_optimizer_checkpoint_resume_is_bit_exact(dv, ctx, prec):
+    """K1 updates, a checkpoint of (angles, Adam moments, update counts), then K2
+    more updates from it give, bit for bit, the angles and state of one run of
+    K1 + K2 updates; a fresh state reproduces dvqls_optimize."""
+    items, keeps, xh, P = [], [], [], []
+    for k, n in enumerate([3, 5]):
+        d = 2
+        A = wl.toeplitz_dense(n, 2.2 + 0.3 * k, -0.7)
+        dec = odec.decompose(A, 0.0, 64)
+        b = wl.plus_state(n)
+        xh.append(oterms.classical_solution(oterms.lcu_matrix(dec["coef"], dec["x"], dec["z"], n), b))
+        alpha0 = wl.random_angles(n * (d + 1), 300 + k)
+        lcu, keep = lcu_of(dv, dec["coef"], dec["x"], dec["z"])
+        keeps.append((keep, cv(b), alpha0))
+        items.append((dv.make_ansatz(n, d), lcu, alpha0, keeps[-1][1]))
+        P.append(n * (d + 1))
+    inst = dv.make_instances(items)
+    xhat = np.concatenate([cv(x) for x in xh])
+    Pt = sum(P)
+
+    def opt(iters):  # an unreachable target: every instance runs all its updates
+        return dv.make_adam(lr=0.03, max_iter=iters, target_fidelity=2.0, precision=prec)
+
+    # one run of 20 updates
+    m, v, steps = np.zeros(Pt), np.zeros(Pt), np.zeros(2, np.int64)
+    a_full = np.zeros(Pt)
+    dv.dvqls_optimize_resume(ctx, inst, xhat, opt(20), m, v, steps, a_full)
+    assert list(steps) == [20, 20]
+    plain = np.zeros(Pt)
+    dv.dvqls_optimize(ctx, inst, xhat, opt(20), plain)
+    assert np.array_equal(plain.view(np.uint64), a_full.view(np.uint64))
+    # 8 updates, checkpoint, 12 more
+    m2, v2, st2 = np.zeros(Pt), np.zeros(Pt), np.zeros(2, np.int64)
+    a8 = np.zeros(Pt)
+    dv.dvqls_optimize_resume(ctx, inst, xhat, opt(8), m2, v2, st2, a8)
+    assert list(st2) == [8, 8]
+    items2, off = [], 0
+    for (an, lcu, _, b), p in zip(items, P):
+        items2.append((an, lcu, a8[off:off + p].copy(), b))
+        off += p
+    keep_a = [it[2] for it in items2]
+    inst2 = dv.make_instances(items2)
+    a20 = np.zeros(Pt)
+    dv.dvqls_optimize_resume(ctx, inst2, xhat, opt(12), m2, v2, st2, a20)
+    assert list(st2) == [20, 20]
+    for x, y in ((a20, a_full), (m2, m), (v2, v)):
+        assert np.array_equal(x.view(np.uint64), y.view(np.uint64))
+    assert len(keep_a) == 2
