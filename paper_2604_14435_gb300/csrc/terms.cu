@@ -895,8 +895,8 @@ constexpr int TC_NSTG = 4;          // operand stages in flight
 constexpr int TC_NIT = 4;           // item records in flight from the builders to the epilogue
 constexpr int TC_FLUSH = 4;         // stages per accumulator block (8 MMAs of each Gram entry per stage)
 constexpr int TC_NB = 144;          // B rows: 128 term rows, hi and lo of b (8 rows), 8 zero rows
-constexpr uint32_t TC_ACC1 = 256;   // tensor-memory column of the second accumulator (the first starts at 0)
-constexpr int TC_SUM = 144;         // tensor memory: running sums of the Gram quadrants (64 columns) ...
+constexpr uint32_t TC_ACC1 = 256;   // tensor-memory columns of builder half h's accumulator: 256 h ..
+constexpr int TC_SUM = 144;         // after it: running sums of the Gram quadrants (64 columns) ...
 constexpr int TC_DSUM = 208;        // ... and of the two delta columns of a lane
 constexpr int TC_COLS = 512;        // tensor-memory columns allocated
 // kind::f16 instruction descriptor: F32 accumulator (bits 4-5 = 1), A and B
@@ -956,8 +956,8 @@ inline size_t tc_psi_region(int nmax_smem, int copy_nmax) {
     }
     return (psi + 1023) & ~size_t(1023);
 }
-inline size_t tc_smem_bytes(int nmax_smem, int copy_nmax) {
-    return 1024 + (size_t)TC_NSTG * TC_STAGE_BYTES + tc_psi_region(nmax_smem, copy_nmax) + TC_EPI_BYTES;
+inline size_t tc_smem_bytes(int nmax_smem, int copy_nmax) {  // a state region for each builder half
+    return 1024 + (size_t)TC_NSTG * TC_STAGE_BYTES + 2 * tc_psi_region(nmax_smem, copy_nmax) + TC_EPI_BYTES;
 }
 // Stages of the b rows of an instance with 2^n amplitudes.
 __host__ __device__ inline long long tc_bop_stages(long long N) { return (N + TCK - 1) / TCK; }
@@ -1221,12 +1221,6 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // Instance of work item g, from the cached bases of the first TC_MAXC
 // instances (shared memory) or from the table.
 constexpr int TC_MAXC = 128;
-// What the state prefetch needs of an instance, kept in shared memory: the
-// packed states (null: none to prefetch) and n, T, ks, F.
-struct TcPlan {
-    const uint32_t* tcst;
-    int n, T, ks, F;
-};
 __device__ __forceinline__ int find_instance_cached(const Inst* insts, const long long* sbase, int count,
                                                     long long g) {
     if (count > TC_MAXC) return find_instance(insts, count, g);
@@ -1237,37 +1231,6 @@ __device__ __forceinline__ int find_instance_cached(const Inst* insts, const lon
         else hi = mid - 1;
     }
     return lo;
-}
-
-// Starts the bulk copy of work item g's packed state into `raw` (one thread;
-// completion is signalled on mbarrier `bar` with the byte count).  Returns
-// false when the item's state is not a packed on-chip state.  Reads only
-// shared memory when the batch has at most TC_MAXC instances.
-__device__ __forceinline__ bool tc_prefetch_state(const Inst* insts, const long long* sbase, const TcPlan* plan,
-                                                  int count, long long g, uint32_t* raw, uint32_t bar) {
-    const int ii = find_instance_cached(insts, sbase, count, g);
-    TcPlan p;
-    long long base;
-    if (count <= TC_MAXC) {
-        p = plan[ii];
-        base = sbase[ii];
-    } else {
-        const Inst& I = insts[ii];
-        p = TcPlan{I.states ? nullptr : reinterpret_cast<const uint32_t*>(I.tcst), I.n, I.T, I.ks, I.F};
-        base = I.item_base;
-    }
-    if (!p.tcst || p.n < 2) return false;
-    const int N = 1 << p.n, NU = p.T * (p.T + 1) / 2;
-    const long long s = ((g - base) / p.ks) / NU / p.F;
-    const uint32_t* src = p.tcst + (size_t)s * N;
-    const uint32_t bytes = uint32_t(N) * 4u;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of raw come first
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     su32(raw)),
-                 "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(bar)
-                 : "memory");
-    return true;
 }
 
 // Named barrier of `nthreads` threads that also returns the OR of a predicate
@@ -1338,7 +1301,7 @@ __device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v) {
 // half of every stage (Gram columns 0..63; delta columns 128, 129 from hi b
 // and 132, 133 from lo b), lanes 64..127 the second half (columns 64..127;
 // delta 130, 131 and 134, 135).  The first block of an item starts the running
-// sums (columns TC_SUM.., TC_DSUM..), later ones add to them with
+// sums (columns acc + TC_SUM.., acc + TC_DSUM..), later ones add to them with
 // round-to-nearest adds; the last block goes to X[half][row][col] and
 // XD[half][row] in shared memory instead.
 __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t acc, int q, int ch, int lane, bool first, bool last,
@@ -1359,7 +1322,7 @@ __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t acc, int q, int 
         }
         if (!first) {
             float u[16];
-            tmem_ld16(base + TC_SUM + 16 * g, u);
+            tmem_ld16(base + acc + TC_SUM + 16 * g, u);
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] += u[j];
         }
@@ -1367,19 +1330,19 @@ __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t acc, int q, int 
 #pragma unroll
             for (int j = 0; j < 16; ++j) Xq[xr * 65 + 16 * g + j] = v[j];
         } else {
-            tmem_st16(base + TC_SUM + 16 * g, v);
+            tmem_st16(base + acc + TC_SUM + 16 * g, v);
         }
     }
     if (ch == 0 && !off) {  // the delta columns
         const float2 d0 = tmem_ld2(base + acc + 128 + dq), d1 = tmem_ld2(base + acc + 132 + dq);
         float2 dv = make_float2(d0.x + d1.x, d0.y + d1.y);
         if (!first) {
-            const float2 du = tmem_ld2(base + TC_DSUM);
+            const float2 du = tmem_ld2(base + acc + TC_DSUM);
             dv.x += du.x;
             dv.y += du.y;
         }
         if (last) XD[(q >> 1) * 64 + xr] = dv;
-        else tmem_st2(base + TC_DSUM, dv);
+        else tmem_st2(base + acc + TC_DSUM, dv);
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -1458,62 +1421,63 @@ __device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const floa
     }
 }
 
-// Warp roles: warps 0..15 build operands, warp 16 issues the MMAs, warps
-// 17..20 run the epilogue.  Hand-overs: a stage by its `full` mbarrier (all
-// builder threads arrive after a proxy fence; the stage record -- address of
-// the hi array, first / last stage of an accumulator block -- is written
-// first) and back by `empty` (the MMA warp's commit); an accumulator block by
-// `accf` (commit after its last stage) and back by `acce` (every epilogue
-// thread, after its tensor-memory loads); an item record (instance, shift,
-// amplitude part, stages) from the builders to the epilogue by `itf` and back
-// by `ite`.  Every wait gives up after budget_ns nanoseconds; a thread that has
-// seen the abort flag waits no more.
-// The CTA's 25 warps are spread over the SM's four sub-partitions (16,384
-// registers each, seven warps on one of them): at most 72 registers a thread.
+// Warp roles: two builder halves of 8 warps (warps 0..7 and 8..15), each
+// running its own items -- its own queue fetches, state copies, masks, two of
+// the ring's stages (slots 2h, 2h + 1), item records and accumulator (TMEM
+// columns 256 h ..) -- so one half's item set-up (fetch, state load, masks)
+// overlaps the other half's stages; warp 16 issues the MMAs of both halves,
+// taking whichever half has a stage ready; warps 17..24 run the epilogue of
+// both, taking whichever accumulator block has finished.  Hand-overs, per half
+// h: a stage by its `full` mbarrier (the half's 256 builder threads arrive
+// after a proxy fence; the stage record -- address of the hi array, first /
+// last stage of an accumulator block, pair flag -- is written first) and back
+// by `empty` (the MMA warp's commit); an accumulator block by accf[h] (commit
+// after its last stage) and back by acce[h] (every epilogue thread, after its
+// tensor-memory loads); an item record (instance, shift, amplitude part, tile
+// item, stages, flavour) by itf[h][r] and back by ite[h][r].  Every wait
+// gives up after budget_ns nanoseconds; a thread that has seen the abort flag
+// waits no more.
+constexpr int TC_HT = TC_BT / 2;  // threads of a builder half
 __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ insts, int count, long long total,
                                                      unsigned long long* queue, int* status, int copy_nmax,
-                                                     int psi_region, int raw_off, long long budget_ns) {
+                                                     int psi_half, long long budget_ns) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long fullb[TC_NSTG], emptyb[TC_NSTG], accf[2], acce[2], itf[TC_NIT],
-        ite[TC_NIT], drainb;
+    __shared__ __align__(8) unsigned long long fullb[TC_NSTG], emptyb[TC_NSTG], accf[2], acce[2], itf[2][TC_NIT],
+        ite[2][TC_NIT], drainb;
     __shared__ uint32_t srec[TC_NSTG][2];
-    __shared__ int4 irec[TC_NIT];
+    __shared__ int4 irec[2][TC_NIT];
+    __shared__ int4 s_cur[2];  // epilogue: the item record each half is on
     __shared__ uint32_t s_tmem;
-    __shared__ long long s_item;
-    __shared__ int s_abort;
-    __shared__ uint32_t sxl[128], szl[128];  // masks of the item's tile (and of the pair's second tile)
+    __shared__ long long s_item[2];
+    __shared__ int s_abort, s_pick;
+    __shared__ uint32_t sxl[2][128], szl[2][128];  // per half: masks of the item's tile (and of a pair's second)
     __shared__ float sred[3][2][TC_EW];
-    __shared__ uint16_t stri[TC_TRI];  // (l, m) of triangle entry e: l | m << 8
+    __shared__ uint16_t stri[TC_TRI];        // (l, m) of triangle entry e: l | m << 8
     __shared__ long long s_ibase[TC_MAXC];  // item bases of the first TC_MAXC instances
-    __shared__ TcPlan s_plan[TC_MAXC];       // and what their state prefetch needs
-    __shared__ __align__(8) unsigned long long stb;  // the next state's bulk copy
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     unsigned char* base;
     {
         const uint32_t a = su32(smem_raw);
         base = smem_raw + ((1024u - (a & 1023u)) & 1023u);
     }
-    uint32_t* psi_hl = reinterpret_cast<uint32_t*>(base + TC_NSTG * TC_STAGE_BYTES);
-    uint32_t* raw = raw_off >= 0 ? reinterpret_cast<uint32_t*>(base + raw_off) : nullptr;  // prefetched state
-    float* X = reinterpret_cast<float*>(base + TC_NSTG * TC_STAGE_BYTES + psi_region);
+    float* X = reinterpret_cast<float*>(base + TC_NSTG * TC_STAGE_BYTES + 2 * psi_half);
     float2* XD = reinterpret_cast<float2*>(X + 2 * TC_X);
     if (t == 0) {
         for (int k = 0; k < TC_NSTG; ++k) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&fullb[k])), "r"(TC_BT));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&fullb[k])), "r"(TC_HT));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&emptyb[k])), "r"(1));
         }
         for (int k = 0; k < 2; ++k) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&accf[k])), "r"(1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&acce[k])), "r"(TC_ET));
-        }
-        for (int k = 0; k < TC_NIT; ++k) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&itf[k])), "r"(1));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ite[k])), "r"(1));
+            for (int r = 0; r < TC_NIT; ++r) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&itf[k][r])), "r"(1));
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ite[k][r])), "r"(1));
+            }
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&drainb)), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&stb)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_abort = 0;
     }
@@ -1528,11 +1492,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         const int l = q >> 6, m = q & 63;
         if (l <= m) stri[tc_tri(l, m)] = uint16_t(l | (m << 8));
     }
-    for (int i = t; i < min(count, TC_MAXC); i += TCT) {
-        const Inst& I = insts[i];
-        s_ibase[i] = I.item_base;
-        s_plan[i] = TcPlan{I.states ? nullptr : reinterpret_cast<const uint32_t*>(I.tcst), I.n, I.T, I.ks, I.F};
-    }
+    for (int i = t; i < min(count, TC_MAXC); i += TCT) s_ibase[i] = insts[i].item_base;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (w == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
@@ -1543,36 +1503,38 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
 
-    if (w < TC_BW) {  // ---------------------------------------------------------------- builders
-        const int tt = t;
-        // task of this thread in a stage: term l of the tile, 16-amplitude block
-        // `sub`, and side hf: the stage's second 64 amplitudes (diagonal tile) or
-        // the pair's second tile (off-diagonal pair)
-        const int l = (tt & 7) | ((w & 7) << 3), sub = (lane >> 3) & 3, hf = w >> 3;
-        uint32_t eph = 0u, pend = 0u;  // bit st: parity of empty[st] to wait for; stage st in flight
-        uint32_t iph = 0u, iused = 0u;  // item ring (thread 0): parity of ite[r]; slot r used before
+    if (w < TC_BW) {  // ------------------------------------------------------------ builder halves
+        const int h = w >> 3, wl = w & 7, tt = t & (TC_HT - 1), bar = 1 + h;
+        uint32_t* psi_hl = reinterpret_cast<uint32_t*>(base + TC_NSTG * TC_STAGE_BYTES + h * psi_half);
+        uint32_t* xs = sxl[h];
+        uint32_t* zs = szl[h];
+        // Tasks of a thread in a stage: a diagonal tile's term l = lane % 8 + 8 wl,
+        // block `sub` = (lane / 8) % 4 of 16 amplitudes, in both halves of the
+        // stage; a pair's term l of side `side` (lane bit 3), blocks 2 sp and
+        // 2 sp + 1 (sp: lane bit 4) of the stage's 64 amplitudes.  Either way
+        // both tasks share the term's masks.
+        const int l = (lane & 7) | (wl << 3), sub = (lane >> 3) & 3;
+        const int pside = (lane >> 3) & 1, psp = (lane >> 4) & 1;
+        uint32_t eph = 0u, pend = 0u;   // bit q: parity of empty[2h + q] to wait for; stage in flight
+        uint32_t iph = 0u, iused = 0u;  // item ring (thread 0 of the half): parity of ite[h][r]; slot used
         int ir = 0;
-        uint32_t gc = 0u;  // stages handed over so far
-        bool ab = false;   // this thread saw a wait give up (shared with the group at its barriers)
-        // Thread 0 takes items one ahead: `cur` is the next item to run, `nxt` the
-        // one after (its queue position is fetched while `cur` runs), and the
-        // state of `cur` is copied into `raw` by the bulk-copy engine meanwhile.
-        long long cur = total, nxt = total;
-        bool pf = false;   // thread 0: a state copy is in flight
-        uint32_t sph = 0u;  // parity of the state copy's mbarrier
+        uint32_t gc = 0u;  // stages the half has handed over
+        bool ab = false;
+        long long cur = total, nxt = total;  // thread 0 of the half: this item and the next from the queue
         if (tt == 0) {
             cur = (long long)atomicAdd(queue, 1ull);
-            if (cur < total) {
-                nxt = (long long)atomicAdd(queue, 1ull);
-                if (raw) pf = tc_prefetch_state(insts, s_ibase, s_plan, count, cur, raw, su32(&stb));
-            }
+            nxt = cur < total ? (long long)atomicAdd(queue, 1ull) : total;
         }
         for (;;) {
-            if (tt == 0) s_item = (aborted(&s_abort) || ab) ? total : cur;
-            ab = bar_or(1, TC_BT, ab);
-            const long long gi = s_item;
-            ab = bar_or(1, TC_BT, ab);
+            if (tt == 0) s_item[h] = (aborted(&s_abort) || ab) ? total : cur;
+            ab = bar_or(bar, TC_HT, ab);
+            const long long gi = s_item[h];
+            ab = bar_or(bar, TC_HT, ab);
             if (ab || gi >= total) break;
+            if (tt == 0) {  // the next queue position, fetched while this item runs
+                cur = nxt;
+                nxt = cur < total && !aborted(&s_abort) ? (long long)atomicAdd(queue, 1ull) : total;
+            }
             const int ii = find_instance_cached(insts, s_ibase, count, gi);
             const Inst& I = insts[ii];
             const int local = int(gi - I.item_base);
@@ -1590,18 +1552,19 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             const int nch = (kend - kbeg + step - 1) / step;
             if (tt == 0) {  // the item's record for the epilogue
                 if ((iused >> ir) & 1u) {
-                    if (!ab && (aborted(&s_abort) || !mbar_wait(su32(&ite[ir]), (iph >> ir) & 1u, budget_ns))) ab = true;
+                    if (!ab && (aborted(&s_abort) || !mbar_wait(su32(&ite[h][ir]), (iph >> ir) & 1u, budget_ns)))
+                        ab = true;
                     iph ^= 1u << ir;
                 }
                 iused |= 1u << ir;
-                irec[ir] = make_int4(ii, s, ksi | (u << 16), nch | (f << 16));  // ksi < 2^16 (2^20 / 2048 parts)
-                mbar_arrive(su32(&itf[ir]));
+                irec[h][ir] = make_int4(ii, s, ksi | (u << 16), nch | (f << 16));  // ksi < 2^16
+                mbar_arrive(su32(&itf[h][ir]));
             }
             ir = (ir + 1) % TC_NIT;
             if (tt < 128) {
                 const int gt = (tt < 64 ? tl : tm) * TT + (tt & 63);
-                sxl[tt] = gt < L ? I.xm[gt] ^ (tt < 64 ? 0u : xflip) : 0u;
-                szl[tt] = gt < L ? I.zm[gt] : 0u;
+                xs[tt] = gt < L ? I.xm[gt] ^ (tt < 64 ? 0u : xflip) : 0u;
+                zs[tt] = gt < L ? I.zm[gt] : 0u;
             }
             const float* psi_g = I.states ? reinterpret_cast<const float*>(I.states) + (size_t)s * N : nullptr;
             // A state in HBM whose item reads only its own block of HBM_K amplitudes
@@ -1610,46 +1573,35 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             bool blk = false;
             if (I.states) {
                 const int gt = (tt < 64 ? tl : tm) * TT + (tt & 63);
-                const bool far = tt < 128 && gt < L && sxl[tt] >= uint32_t(HBM_K);
-                blk = kper == HBM_K && !bar_or(1, TC_BT, far);
+                const bool far = tt < 128 && gt < L && xs[tt] >= uint32_t(HBM_K);
+                blk = kper == HBM_K && !bar_or(bar, TC_HT, far);
             }
             const int Na = blk ? int(HBM_K) : N;  // amplitudes in shared memory
             const bool copies = (!I.states || blk) && tc_copies(blk ? HBM_KQ : n, copy_nmax);
-            const bool in_raw = raw && !I.states && n >= 2;  // the state was copied into raw
-            if (in_raw) {
-                if (!ab && (aborted(&s_abort) || !mbar_wait(su32(&stb), sph, budget_ns))) ab = true;
-                sph ^= 1u;
-                if (tt == 0) pf = false;
-                // copy t (t = 0 only without copies): psi[k ^ t] at word t (N + 8) + k
-                const int ncp = copies ? 4 : 1;
-                for (int k = tt; k < N; k += TC_BT) {
-                    const uint32_t v = raw[k];
-                    for (int t3 = 0; t3 < ncp; ++t3) psi_hl[t3 * (N + 8) + (k ^ t3)] = v;
-                }
-            } else if (blk) {  // the item's block of the FP32 state in HBM, split into packed pairs here
+            if (blk) {  // the item's block of the FP32 state in HBM, split into packed pairs here
                 // the FP32 block lands in the last copy's room (with copies) or in place
                 float* stage = reinterpret_cast<float*>(psi_hl + (copies ? 3 * (Na + 8) : 0));
-                for (int k = 4 * tt; k < Na; k += 4 * TC_BT)
+                for (int k = 4 * tt; k < Na; k += 4 * TC_HT)
                     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(stage + k)),
                                  "l"(__cvta_generic_to_global(psi_g + kbeg + k))
                                  : "memory");
                 asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
-                bar_n(1, TC_BT);
-                float vb[HBM_K / TC_BT];
+                bar_n(bar, TC_HT);
+                float vb[HBM_K / TC_HT];
 #pragma unroll
-                for (int e = 0; e < HBM_K / TC_BT; ++e) vb[e] = stage[tt * (HBM_K / TC_BT) + e];
-                bar_n(1, TC_BT);
+                for (int e = 0; e < HBM_K / TC_HT; ++e) vb[e] = stage[tt * (HBM_K / TC_HT) + e];
+                bar_n(bar, TC_HT);
                 const int ncp = copies ? 4 : 1;
 #pragma unroll
-                for (int e = 0; e < HBM_K / TC_BT; ++e) {
-                    const int k = tt * (HBM_K / TC_BT) + e;
+                for (int e = 0; e < HBM_K / TC_HT; ++e) {
+                    const int k = tt * (HBM_K / TC_HT) + e;
                     const uint32_t v = split_h2l(vb[e] * TC_SCALE);
                     for (int t3 = 0; t3 < ncp; ++t3) psi_hl[t3 * (Na + 8) + (k ^ t3)] = v;
                 }
             } else if (!I.states) {  // the packed state of shift s (built by k_tc_states)
                 const uint32_t* src = reinterpret_cast<const uint32_t*>(I.tcst) + (size_t)s * N;
                 if (N >= 4) {
-                    for (int k = 4 * tt; k < N; k += 4 * TC_BT)
+                    for (int k = 4 * tt; k < N; k += 4 * TC_HT)
                         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(psi_hl + k)),
                                      "l"(__cvta_generic_to_global(src + k))
                                      : "memory");
@@ -1658,25 +1610,18 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                     psi_hl[tt] = src[tt];
                 }
             }
-            ab = bar_or(1, TC_BT, ab);
-            if (copies && !in_raw && !blk) {  // copy t: psi[k ^ t] at word t (N + 8) + k
-                for (int k = tt; k < N; k += TC_BT) {
+            ab = bar_or(bar, TC_HT, ab);
+            if (copies && !blk) {  // copy t: psi[k ^ t] at word t (N + 8) + k
+                for (int k = tt; k < N; k += TC_HT) {
                     const uint32_t v = psi_hl[k];
 #pragma unroll
                     for (int t3 = 1; t3 < 4; ++t3) psi_hl[t3 * (N + 8) + (k ^ t3)] = v;
                 }
-                bar_n(1, TC_BT);
+                bar_n(bar, TC_HT);
             }
-            if (tt == 0) {  // raw is free again: the next item's state, and the queue position after it
-                cur = nxt;
-                if (cur < total && !ab && !aborted(&s_abort)) {
-                    nxt = (long long)atomicAdd(queue, 1ull);
-                    if (raw) pf = tc_prefetch_state(insts, s_ibase, s_plan, count, cur, raw, su32(&stb));
-                }
-            }
-            const int side = off ? hf : 0;
-            const bool act = (off && hf ? tm : tl) * TT + l < L;
-            const uint32_t xl = sxl[side * 64 + l], zl = szl[side * 64 + l];
+            const int side = off ? pside : 0;
+            const bool act = (side ? tm : tl) * TT + l < L;
+            const uint32_t xl = xs[side * 64 + l], zl = zs[side * 64 + l];
             uint32_t sgn[8];  // word g: sign bits of elements 2g (bit 15) and 2g + 1 (bit 31) of a 16-block
             {
                 const uint32_t xlo = xl & 15u & uint32_t(N - 1);
@@ -1685,14 +1630,14 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                     sgn[g] = ((__popc(zl & 15u & (uint32_t(2 * g) ^ xlo)) & 1) ? 0x8000u : 0u) |
                              ((__popc(zl & 15u & (uint32_t(2 * g + 1) ^ xlo)) & 1) ? 0x80000000u : 0u);
             }
-            const int row = hf ? 64 + l : l;
+            const bool gl = I.states && !blk;  // gather from the state in HBM
             for (int c = 0; c < nch; ++c, ++gc) {
-                const int st = int(gc % TC_NSTG);
-                if ((pend >> st) & 1u) {  // the MMAs that read this buffer last time must be done
-                    if (!ab && (aborted(&s_abort) || !mbar_wait(su32(&emptyb[st]), (eph >> st) & 1u, budget_ns)))
+                const int q = int(gc & 1u), st = 2 * h + q;
+                if ((pend >> q) & 1u) {  // the MMAs that read this buffer last time must be done
+                    if (!ab && (aborted(&s_abort) || !mbar_wait(su32(&emptyb[st]), (eph >> q) & 1u, budget_ns)))
                         ab = true;
-                    eph ^= 1u << st;
-                    pend &= ~(1u << st);
+                    eph ^= 1u << q;
+                    pend &= ~(1u << q);
                 }
                 unsigned char* zhi = base + st * TC_STAGE_BYTES;
                 unsigned char* zlo = zhi + TC_OPND_BYTES;
@@ -1706,27 +1651,33 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                                  "l"(__cvta_generic_to_global(srcb))
                                  : "memory");
                 }
-                // diagonal: hi to array hi, 2 lo to array 2 lo, row l or 64 + l by half;
-                // off-diagonal: the side's array (hi: first tile, lo: second), hi to
-                // row l and lo (halved back) to row 64 + l
-                const bool gl = I.states && !blk;  // gather from the state in HBM
                 if (!off) {
-                    const int jb = j0 + hf * (TCK / 2) + sub * 16;
-                    if (gl)
-                        tc_build_half<true, false>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, sub * 16, zhi, row,
-                                                   zlo, row, false);
-                    else
-                        tc_build_half<false, false>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, sub * 16, zhi,
-                                                    row, zlo, row, copies);
+                    // diagonal: hi to array hi, 2 lo to array 2 lo; row l (first 64
+                    // amplitudes of the stage) and row 64 + l (the next 64)
+#pragma unroll 1
+                    for (int hf = 0; hf < 2; ++hf) {
+                        const int jb = j0 + hf * (TCK / 2) + sub * 16, row = hf * 64 + l;
+                        if (gl)
+                            tc_build_half<true, false>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, sub * 16, zhi,
+                                                       row, zlo, row, false);
+                        else
+                            tc_build_half<false, false>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, sub * 16,
+                                                        zhi, row, zlo, row, copies);
+                    }
                 } else {
-                    const int jb = j0 + sub * 16;
-                    unsigned char* dst = hf ? zlo : zhi;
-                    if (gl)
-                        tc_build_half<true, true>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, sub * 16, dst, l,
-                                                  dst, 64 + l, false);
-                    else
-                        tc_build_half<false, true>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, sub * 16, dst, l,
-                                                   dst, 64 + l, copies);
+                    // pair: the side's array (hi array: first tile, 2 lo array: second),
+                    // hi to row l and lo (halved back) to row 64 + l
+                    unsigned char* dst = pside ? zlo : zhi;
+#pragma unroll 1
+                    for (int qb = 0; qb < 2; ++qb) {
+                        const int sb = 2 * psp + qb, jb = j0 + sb * 16;
+                        if (gl)
+                            tc_build_half<true, true>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, sb * 16, dst, l,
+                                                      dst, 64 + l, false);
+                        else
+                            tc_build_half<false, true>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, sb * 16, dst,
+                                                       l, dst, 64 + l, copies);
+                    }
                 }
                 if (brow) asm volatile("cp.async.wait_all;" ::: "memory");
                 if (tt == 0) {
@@ -1736,81 +1687,90 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(su32(&fullb[st]));
-                pend |= 1u << st;
+                pend |= 1u << q;
             }
         }
-        // No more items: an exit stage for the MMA warp and an exit record
-        // for the epilogue (their waits are bounded whatever happens here).
+        // No more items: an exit stage for the MMA warp and an exit record for
+        // the epilogue (their waits are bounded whatever happens here).
         {
-            const int st = int(gc % TC_NSTG);
-            if (((pend >> st) & 1u) && !ab && !aborted(&s_abort)) mbar_wait(su32(&emptyb[st]), (eph >> st) & 1u, budget_ns);
+            const int q = int(gc & 1u), st = 2 * h + q;
+            if (((pend >> q) & 1u) && !ab && !aborted(&s_abort)) mbar_wait(su32(&emptyb[st]), (eph >> q) & 1u, budget_ns);
             if (tt == 0) srec[st][0] = TC_EXIT;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(su32(&fullb[st]));
             if (tt == 0) {
-                if (((iused >> ir) & 1u) && !ab && !aborted(&s_abort)) mbar_wait(su32(&ite[ir]), (iph >> ir) & 1u, budget_ns);
-                irec[ir] = make_int4(-1, 0, 0, 0);
-                mbar_arrive(su32(&itf[ir]));
-                // a state copy still in flight lands before the shared memory is released
-                if (pf && !mbar_wait(su32(&stb), sph, TC_DRAIN_NS)) ab = true;
+                if (((iused >> ir) & 1u) && !ab && !aborted(&s_abort))
+                    mbar_wait(su32(&ite[h][ir]), (iph >> ir) & 1u, budget_ns);
+                irec[h][ir] = make_int4(-1, 0, 0, 0);
+                mbar_arrive(su32(&itf[h][ir]));
             }
         }
         if (ab) s_abort = 1;
     } else if (w == TC_BW) {  // ------------------------------------------------------------- MMA warp
         if (lane == 0) {
-            uint32_t fph = 0u, aph = 0u, aused = 0u;  // parity of full[st]; parity of acce[a]; accumulator a used
-            uint32_t acc = 0u;
-            for (int st = 0;; st = (st + 1) % TC_NSTG) {
-                if (aborted(&s_abort) || !mbar_wait(su32(&fullb[st]), (fph >> st) & 1u, budget_ns)) {
-                    s_abort = 1;
-                    break;
-                }
-                fph ^= 1u << st;
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t hb = srec[st][0], fl = srec[st][1];
-                if (hb == TC_EXIT) break;
-                if (fl & 1u) {  // first stage of a block: the epilogue must have read this accumulator's last block
-                    if ((aused >> acc) & 1u) {
-                        if (aborted(&s_abort) || !mbar_wait(su32(&acce[acc]), (aph >> acc) & 1u, budget_ns)) {
-                            s_abort = 1;
-                            break;
-                        }
-                        aph ^= 1u << acc;
+            // per half: next slot (bit h), parity of full[2h + q] (bit 2h + q), parity of acce[h] (bit h),
+            // accumulator used before (bit h), done (bit h)
+            uint32_t nq = 0u, fph = 0u, aph = 0u, aused = 0u, done = 0u;
+            unsigned long long idle0 = gtimer_ns();
+            while (done != 3u) {
+                bool progressed = false;
+                for (int h = 0; h < 2; ++h) {
+                    if ((done >> h) & 1u) continue;
+                    const int q = (nq >> h) & 1, st = 2 * h + q;
+                    if (!mbar_try(su32(&fullb[st]), (fph >> st) & 1u)) continue;
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t hb = srec[st][0], fl = srec[st][1];
+                    if (hb != TC_EXIT && (fl & 1u) && ((aused >> h) & 1u)) {
+                        // first stage of a block: the epilogue must have read the half's last block
+                        if (!mbar_try(su32(&acce[h]), (aph >> h) & 1u)) continue;  // the other half meanwhile
+                        aph ^= 1u << h;
                         asm volatile("tcgen05.fence::after_thread_sync;");
                     }
-                    aused |= 1u << acc;
-                }
-                const uint32_t lb = hb + TC_OPND_BYTES, tm = s_tmem + acc * TC_ACC1;
-                if (fl & 4u) {  // off-diagonal pair: [hi; lo] of the first tile against [hi; lo] of the second
-#pragma unroll
-                    for (int ksx = 0; ksx < TCK / 32; ++ksx) {
-                        const uint32_t acc0 = ((fl & 1u) && ksx == 0) ? 0u : 1u;
-                        asm volatile(
-                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tm),
-                            "l"(tc_desc(hb + ksx * TC_KSTEP_BYTES)), "l"(tc_desc(lb + ksx * TC_KSTEP_BYTES)),
-                            "r"(tc_idesc(128)), "r"(acc0));
+                    fph ^= 1u << st;
+                    nq ^= 1u << h;
+                    progressed = true;
+                    if (hb == TC_EXIT) {
+                        done |= 1u << h;
+                        continue;
                     }
-                } else
+                    if (fl & 1u) aused |= 1u << h;
+                    const uint32_t lb = hb + TC_OPND_BYTES, tm = s_tmem + uint32_t(h) * TC_ACC1;
+                    if (fl & 4u) {  // pair: [hi; lo] of the first tile against [hi; lo] of the second
 #pragma unroll
-                for (int ksx = 0; ksx < TCK / 32; ++ksx) {
-                    const uint64_t dh = tc_desc(hb + ksx * TC_KSTEP_BYTES), dl = tc_desc(lb + ksx * TC_KSTEP_BYTES);
-                    const uint64_t db = tc_desc(lb + ksx * TC_KSTEP_BYTES + TC_BROW);
-                    const uint32_t acc0 = ((fl & 1u) && ksx == 0) ? 0u : 1u;
-                    asm volatile(
-                        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %6, 0;\n\tsetp.eq.b32 q, %6, %6;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %2, %2, %4, p;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %2, %3, %5, q;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%1], %3, %7, %8, q;\n\t}\n" ::"r"(tm),
-                        "r"(tm + 128u), "l"(dh), "l"(dl), "r"(tc_idesc(TC_NB)), "r"(tc_idesc(128)), "r"(acc0),
-                        "l"(db), "r"(tc_idesc(16)));
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    su32(&emptyb[st])));
-                if (fl & 2u) {
+                        for (int ksx = 0; ksx < TCK / 32; ++ksx) {
+                            const uint32_t acc0 = ((fl & 1u) && ksx == 0) ? 0u : 1u;
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tm),
+                                "l"(tc_desc(hb + ksx * TC_KSTEP_BYTES)), "l"(tc_desc(lb + ksx * TC_KSTEP_BYTES)),
+                                "r"(tc_idesc(128)), "r"(acc0));
+                        }
+                    } else {
+#pragma unroll
+                        for (int ksx = 0; ksx < TCK / 32; ++ksx) {
+                            const uint64_t dh = tc_desc(hb + ksx * TC_KSTEP_BYTES), dl = tc_desc(lb + ksx * TC_KSTEP_BYTES);
+                            const uint64_t db = tc_desc(lb + ksx * TC_KSTEP_BYTES + TC_BROW);
+                            const uint32_t acc0 = ((fl & 1u) && ksx == 0) ? 0u : 1u;
+                            asm volatile(
+                                "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %6, 0;\n\tsetp.eq.b32 q, %6, %6;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %2, %2, %4, p;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %2, %3, %5, q;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%1], %3, %7, %8, q;\n\t}\n" ::"r"(tm),
+                                "r"(tm + 128u), "l"(dh), "l"(dl), "r"(tc_idesc(TC_NB)), "r"(tc_idesc(128)), "r"(acc0),
+                                "l"(db), "r"(tc_idesc(16)));
+                        }
+                    }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        su32(&accf[acc])));
-                    acc ^= 1u;
+                        su32(&emptyb[st])));
+                    if (fl & 2u)
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            su32(&accf[h])));
+                }
+                if (progressed) {
+                    idle0 = gtimer_ns();
+                } else if (aborted(&s_abort) || (long long)(gtimer_ns() - idle0) > budget_ns) {
+                    s_abort = 1;
+                    break;
                 }
             }
             // Every MMA issued has completed before the tensor memory is freed.
@@ -1821,53 +1781,69 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         __syncwarp();
     } else {  // ----------------------------------------------------------------------------- epilogue
         const int et = t - (TC_BT + 32), ew = et >> 5, q = w & 3, ch = ew >> 2;  // q: this warp's TMEM lane quarter
-        uint32_t fph = 0u, aph = 0u, acc = 0u;
-        int r = 0;
+        // Thread 0 keeps, per half, the item-ring position, the ring's parities and
+        // whether it holds the current record; every thread keeps the block count.
+        uint32_t fph = 0u, aph = 0u, have = 0u, done = 0u;
+        int r[2] = {0, 0}, blkc[2] = {0, 0}, last_pick = 1;
         bool ab = false;
         for (;;) {
-            if (et == 0 && (aborted(&s_abort) || !mbar_wait(su32(&itf[r]), (fph >> r) & 1u, budget_ns))) ab = true;
-            fph ^= 1u << r;
-            ab = bar_or(2, TC_ET, ab);
-            if (ab) break;
-            const int4 rc = irec[r];
-            if (rc.x < 0) break;
+            if (et == 0) {  // the half whose accumulator block is ready next
+                int pick = -1;
+                const unsigned long long t0 = gtimer_ns();
+                for (;;) {
+                    for (int k = 1; k <= 2 && pick < 0; ++k) {
+                        const int hh = (last_pick + k) & 1;
+                        if ((done >> hh) & 1u) continue;
+                        if (!((have >> hh) & 1u)) {
+                            const uint32_t pb = hh * TC_NIT + r[hh];
+                            if (!mbar_try(su32(&itf[hh][r[hh]]), (fph >> pb) & 1u)) continue;
+                            fph ^= 1u << pb;
+                            const int4 rc = irec[hh][r[hh]];
+                            s_cur[hh] = rc;
+                            if (rc.x < 0) {
+                                done |= 1u << hh;
+                                continue;
+                            }
+                            have |= 1u << hh;
+                        }
+                        if (mbar_try(su32(&accf[hh]), (aph >> hh) & 1u)) {
+                            aph ^= 1u << hh;
+                            pick = hh;
+                        }
+                    }
+                    if (pick >= 0 || done == 3u) break;
+                    if (aborted(&s_abort) || (long long)(gtimer_ns() - t0) > budget_ns) {
+                        pick = -2;
+                        break;
+                    }
+                }
+                if (pick >= 0) last_pick = pick;
+                s_pick = pick;
+            }
+            bar_n(3, TC_ET);
+            const int pick = s_pick;
+            if (pick == -2) ab = true;
+            if (pick < 0) break;
+            const int4 rc = s_cur[pick];
             const Inst& I = insts[rc.x];
             const int s = rc.y, ksi = rc.z & 0xFFFF, u = rc.z >> 16, nch = rc.w & 0xFFFF, f = rc.w >> 16;
             const int L = I.L, ks = I.ks, T = I.T;
             int tl, tm;
             tc_tile_pair(u, T, tl, tm);
             const bool off = tl != tm || f > 0;
-            const int nblk = (nch + TC_FLUSH - 1) / TC_FLUSH;
+            const int nblk = (nch + TC_FLUSH - 1) / TC_FLUSH, b = blkc[pick];
+            const bool lastb = b + 1 == nblk;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            tc_fold(s_tmem, uint32_t(pick) * TC_ACC1, q, ch, lane, b == 0, lastb, off, X, XD);
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(su32(&acce[pick]));
+            blkc[pick] = lastb ? 0 : b + 1;
+            if (!lastb) {
+                bar_n(3, TC_ET);  // s_pick and s_cur are read before thread 0 writes them again
+                continue;
+            }
+            bar_n(3, TC_ET);  // the readout is in X (and XD)
             const int nl = min(TT, L - tl * TT), nm = min(TT, L - tm * TT);  // terms in the two tiles
-            // this thread's first weights, loaded while the item's MMAs run: entries et + 256 k of
-            // the diagonal tile's triangle (Re w as float pairs), or of the 64 x 64 block
-            float2 wv[TC_WPT];
-#pragma unroll
-            for (int k = 0; k < TC_WPT; ++k) {
-                const int e = et + TC_ET * k;
-                if (!off) {
-                    wv[k] = e < TC_TRI ? I.wt[(long long)tl * TC_TRI + e] : make_float2(0.f, 0.f);
-                } else {
-                    const int a = e >> 6, bcol = e & 63;
-                    const float4 w4 = (a < nl && bcol < nm) ? I.wf[(long long)(tl * TT + a) * L + tm * TT + bcol]
-                                                            : make_float4(0.f, 0.f, 0.f, 0.f);
-                    wv[k] = make_float2(w4.x, w4.y);
-                }
-            }
-            for (int b = 0; b < nblk; ++b) {
-                if (et == 0 && (aborted(&s_abort) || !mbar_wait(su32(&accf[acc]), (aph >> acc) & 1u, budget_ns)))
-                    ab = true;
-                aph ^= 1u << acc;
-                ab = bar_or(2, TC_ET, ab);
-                if (ab) break;
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                tc_fold(s_tmem, acc * TC_ACC1, q, ch, lane, b == 0, b + 1 == nblk, off, X, XD);
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                mbar_arrive(su32(&acce[acc]));
-                acc ^= 1u;
-            }
-            if (ab) break;
-            bar_n(2, TC_ET);  // the readout is in X (and XD)
             const float* Xu = X;
             const float* Xl = X + TC_X;
             float S = 0.f, E = 0.f, TrS = 0.f, TrE = 0.f, TiS = 0.f, TiE = 0.f;
@@ -1878,6 +1854,12 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 // sum over l <= m of Re(w_lm) g_lm with g_ll = G'_ll and g_lm = G'_lm +
                 // G'_ml (both halves).  The 2080 entries l <= m are dealt out evenly:
                 // thread et takes entries et + 256 k of the row-major triangle.
+                float2 wv[TC_WPT];
+#pragma unroll
+                for (int k = 0; k < TC_WPT; ++k) {
+                    const int e = et + TC_ET * k;
+                    wv[k] = e < TC_TRI ? I.wt[(long long)tl * TC_TRI + e] : make_float2(0.f, 0.f);
+                }
 #pragma unroll
                 for (int k = 0; k < TC_WPT; ++k) {
                     const int e = et + TC_ET * k;
@@ -1912,20 +1894,13 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 // stand for both orders of the pair (the Gram and gamma^j are symmetric,
                 // as is Re w), so each product counts twice (exact doubling).
                 const float fac = tl != tm ? 2.f : 1.f;
-#pragma unroll 2
+#pragma unroll 4
                 for (int k = 0; k < TT * TT / TC_ET; ++k) {
                     const int e = et + TC_ET * k, a = e >> 6, bcol = e & 63;
-                    float2 wk;
-                    if (k < TC_WPT) {
-                        wk = wv[k];
-                    } else {
-                        const float4 w4 = (a < nl && bcol < nm) ? I.wf[(long long)(tl * TT + a) * L + tm * TT + bcol]
-                                                                : make_float4(0.f, 0.f, 0.f, 0.f);
-                        wk = make_float2(w4.x, w4.y);
-                    }
                     if (a >= nl || bcol >= nm) continue;
+                    const float4 w4 = I.wf[(long long)(tl * TT + a) * L + tm * TT + bcol];
                     const float g = Xu[a * 65 + bcol] + Xl[a * 65 + bcol];
-                    ff_mac(S, E, fac * wk.x, fac * wk.y, g);
+                    ff_mac(S, E, fac * w4.x, fac * w4.y, g);
                     if (Gp && f == 0) {
                         const float2 gv = make_float2(g * TC_UNSCALE, 0.f);
                         const long long ga = tl * TT + a, gb = tm * TT + bcol;
@@ -1945,7 +1920,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 sred[2][0][ew] = TiS;
                 sred[2][1][ew] = TiE;
             }
-            bar_n(2, TC_ET);
+            bar_n(3, TC_ET);
             if (et == 0) {  // FP64 only for the final pairs, added in a fixed order
                 double qv[3];
                 for (int k = 0; k < 3; ++k) {
@@ -1957,16 +1932,18 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                     qv[k] = (double)S2 + (double)E2;
                 }
                 // slots as the CUDA-core tiles use them: diagonal tile u at u, pair p at
-                // T + 2p (and T + 2p + 1, which the tiles use for the pair's second half)
-                // (per flavour f of the local cost: slots (s F + f) T^2 ..)
+                // T + 2p (and T + 2p + 1, which the tiles use for the pair's second half);
+                // per flavour f of the local cost: slots (s F + f) T^2 ..
                 const long long slot = ((long long)s * I.F + f) * T * T + (tl != tm ? T + 2 * (u - T) : u);
                 I.Dpart[slot * ks + ksi] = make_double2(qv[0] * (double)TC_UNSCALE, 0.0);
                 if (tl != tm) I.Dpart[(slot + 1) * ks + ksi] = make_double2(0.0, 0.0);
                 else if (f == 0 && !I.local) I.Tpart[((long long)s * T + tl) * ks + ksi] = make_double2(qv[1], qv[2]);
+                // the half's item record is free again
+                mbar_arrive(su32(&ite[pick][r[pick]]));
+                r[pick] = (r[pick] + 1) % TC_NIT;
+                have &= ~(1u << pick);
             }
-            bar_n(2, TC_ET);  // X and the item record are free again
-            if (et == 0) mbar_arrive(su32(&ite[r]));
-            r = (r + 1) % TC_NIT;
+            bar_n(3, TC_ET);  // X, sred and s_cur are free again
         }
         if (ab) s_abort = 1;
     }
@@ -2666,8 +2643,7 @@ struct PassShape {
     long long total;
     size_t smem;
     int copy_nmax;   // tensor-core kernel: states of 2^4 .. 2^copy_nmax amplitudes kept in four copies (0: none)
-    int psi_region;  // tensor-core kernel: shared bytes of its state copies
-    int raw_off;     // tensor-core kernel: offset of the prefetched state's buffer (-1: no prefetch)
+    int psi_region;  // tensor-core kernel: shared bytes of a builder half's state copies
     int st_grid;     // tensor-core pass: CTAs per instance of k_tc_states (0: no state in shared memory)
     int st_smem;     // and its dynamic shared bytes
     long long budget_ns;  // tensor-core kernel: time limit of each bounded wait
@@ -2738,8 +2714,7 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
                                        ps.total, ctx->d_queue));
     else if (ps.tc)
         DVQLS_CUDA_TRY(ctx, launch_pdl(k_terms_tc, dim3(ps.grid), dim3(TCT), ps.smem, st, dtable, ps.count, ps.total,
-                                       ctx->d_queue, ctx->d_status, ps.copy_nmax, ps.psi_region, ps.raw_off,
-                                       ps.budget_ns));
+                                       ctx->d_queue, ctx->d_status, ps.copy_nmax, ps.psi_region, ps.budget_ns));
     else if (ps.fp32)
         DVQLS_CUDA_TRY(ctx, launch_pdl(k_terms_smem<float>, dim3(ps.grid), dim3(NT), ps.smem, st, dtable, ps.count,
                                        ps.total, ctx->d_queue));
@@ -2867,8 +2842,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     bool wht = precision == DVQLS_FP32_WHT;
     for (const auto& h : hi) wht = wht && h.T == 1 && h.n <= WHT_MAXN;
     bool tc = !wht && (precision == DVQLS_FP32_TC || (precision == DVQLS_FP32_WHT && !local));
-    int copy_nmax = 0, raw_off = -1;
-    size_t raw_bytes = 0;
+    int copy_nmax = 0;
     // the tensor-core kernel's shared state region: the largest on-chip state, and
     // a staged block of HBM_K amplitudes when some state lives in HBM
     bool any_hbm = false;
@@ -2882,12 +2856,6 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         tc = tc_smem_bytes(tc_nsm, 0) + fa.sharedSizeBytes <= (size_t)optin;
         for (int c = TC_COPY_NMAX; tc && tc_nsm > 0 && c >= 4 && !copy_nmax; --c)
             if (tc_smem_bytes(tc_nsm, c) + fa.sharedSizeBytes <= (size_t)optin) copy_nmax = c;
-        // the next item's state is prefetched into a buffer of its own when it fits
-        if (tc && any_smem && nmax >= 2 &&
-            tc_smem_bytes(tc_nsm, copy_nmax) + (size_t(4) << nmax) + fa.sharedSizeBytes <= (size_t)optin) {
-            raw_off = int(size_t(TC_NSTG) * TC_STAGE_BYTES + tc_psi_region(tc_nsm, copy_nmax) + TC_EPI_BYTES);
-            raw_bytes = size_t(4) << nmax;
-        }
     }
     // The tensor-core pass builds the on-chip states in a kernel of its own.
     int st_grid = 0;
@@ -2900,7 +2868,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
             }
     if (st_grid > 0) DVQLS_CUDA_TRY(ctx, allow_dynamic_smem((const void*)k_tc_states));
     const size_t smem = wht  ? wht_smem_bytes(Pmax)
-                        : tc ? tc_smem_bytes(tc_nsm, copy_nmax) + raw_bytes
+                        : tc ? tc_smem_bytes(tc_nsm, copy_nmax)
                         : fp32 ? smem_bytes<float>(nmax, Pmax) : smem_bytes<double>(nmax, Pmax);
     const size_t r2 = fp32 ? 8 : 16;
     auto kfun = wht ? (const void*)k_terms_wht
@@ -3117,7 +3085,6 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         ps.smem = smem;
         ps.copy_nmax = copy_nmax;
         ps.psi_region = tc ? (int)tc_psi_region(tc_nsm, copy_nmax) : 0;
-        ps.raw_off = raw_off;
         ps.st_grid = st_grid;
         ps.st_smem = (int)st_smem;
         ps.budget_ns = ctx->wait_budget_us * 1000;
