@@ -223,22 +223,22 @@ def make_batch(D, ctx, torch, rank, name):
 
 def work_of(shapes, tensor=False):
     """Paper terms, algorithmic and executed FLOPs of one cost+grad pass.
-    The tensor-core kernel executes, for a diagonal 64-term tile, per k-step
-    of 16 amplitudes of each half of a stage, three MMAs with M = 128: hi hi^T
-    with the b rows (N = 144), hi (2 lo)^T (N = 128) and 2 lo hi(b)^T / 2
-    (N = 16); for a pair of tiles, per 16 amplitudes, one 128 x 128 x 16 MMA of
-    [hi; lo] against [hi; lo]."""
+    The tensor-core kernel executes, for a diagonal 64-term tile, one MMA of
+    M = 128 ([2 lo; hi] of the 64 terms), N = 80 ([hi; b rows]), K = 16 per 16
+    amplitudes, over stages of 128 amplitudes; for a pair of tiles, one
+    128 x 128 x 16 MMA of [hi; lo] against [hi; lo] per 16 amplitudes, over
+    stages of 64 amplitudes."""
     terms = alg = exe = 0
     for n, d, L in shapes:
         S = 2 * n * (d + 1) + 1
         N = 1 << n
         terms += S * (L * L + L)
         alg += S * (L * L + L) * 8 * N
-        # tensor cores: MMAs of 128 x (144 + 128 + 16) x 16 per 32 amplitudes (Gram and delta rows); CUDA
-        # cores: one real FMA per Gram product (the ansatz state is real) and 4 flops per delta product
+        # CUDA cores: one real FMA per Gram product (the ansatz state is real) and 4 flops per delta product
         T = (L + 63) // 64
-        exe += S * (T * 2 * 128 * (144 + 128 + 16) * 16 * (N // 32) + T * (T - 1) // 2 * 2 * 128 * 128 * 16 * (N // 16)
-                    if tensor else executed_gram_entries(L) * 2 * N + L * 4 * N)
+        diag = T * 8 * -(-N // 128) * 2 * 128 * 80 * 16
+        pairs = T * (T - 1) // 2 * 4 * -(-N // 64) * 2 * 128 * 128 * 16
+        exe += S * (diag + pairs if tensor else executed_gram_entries(L) * 2 * N + L * 4 * N)
     return terms, alg, exe
 
 
@@ -800,9 +800,8 @@ def main():
                     "frac_note": peak_src,
                     "achieved_note": "algorithmic: 8N FLOP per paper term, all L^2 ordered pairs + L",
                     "executed": {"tflops": executed, "frac": executed / peak, "flops_per_launch": exe,
-                                 "note": "per 2 x 16 amplitudes of a 64-term tile: FP16 MMAs hi hi^T with the b "
-                                         "rows (128 x 144 x 16), hi (2 lo)^T (128 x 128 x 16) and "
-                                         "2 lo hi(b)^T / 2 (128 x 16 x 16)"}}
+                                 "note": "per 16 amplitudes of a 64-term tile: one FP16 MMA [2 lo; hi] "
+                                         "[hi; b rows]^T (128 x 80 x 16)"}}
         else:
             roof = {"bound": "alu", "kernel": "k_terms_smem<float>", "achieved": achieved,
                     "peak": FP32_PEAK, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK, "traffic": None,

@@ -831,27 +831,24 @@ constexpr int HBM_KQ = 11;
 // Precision DVQLS_FP32_TC: the Gram of a 64-term tile on the tensor cores.
 // The Ry + CZ-ring ansatz state is real, so with the phase i^popc(x & z) in
 // c~_l every phi_l[j] = (-1)^popc(z_l & (j ^ x_l)) psi[j ^ x_l] is real and
-// G~ is a real symmetric 64 x 64 Gram.  A stage of TCK = 128 amplitudes is
-// laid out as the 128 x 64 matrix Z whose rows 0..63 hold phi_l on the first
-// half of the stage's amplitudes and rows 64..127 phi_l on the second half, so
-//   G~_lm = sum over stages of (Z Z^T)[l][m] + (Z Z^T)[64+l][64+m]
-// (the two diagonal quadrants; the off-diagonal ones are not used).
+// G~ is a real symmetric 64 x 64 Gram: G~ = Z Z^T for the 64 x N matrix Z of
+// the tile's phi_l.
 //
 // Split.  Every entry of 2^12 Z (and of 2^e b, e from ||b||) is split
 // x = hi + lo into FP16 (round to nearest; the scale keeps lo clear of FP16
 // subnormals for amplitudes above ~3e-5, and below that lo's absolute error
 // stays under 2^-37), and Z Z^T ~ hi hi^T + hi lo^T + lo hi^T (lo lo^T, ~2^-22
 // relative, dropped).  Only sum_lm Re(w_lm) G~_lm is formed and Re(w) is
-// symmetric, so hi lo^T + lo hi^T may be replaced by hi (2 lo)^T: the
-// accumulator holds G' = hi hi^T + hi (2 lo)^T, whose symmetric part is G~.
-// That is two tcgen05.mma kind::f16 per k-step of 16 amplitudes instead of
-// three: (A = hi, B = hi, N = 144) and (A = hi, B = 2 lo, N = 128).  The first
-// B also carries the rows hi and lo of Re b and Im b on both halves of the
-// stage (accumulator columns 128..135), and a narrow third MMA (A = 2 lo,
-// B = hi(b) / 2, N = 16) adds lo hi(b) into columns 128..131, so
-// delta_l = sum_j conj(b_j) phi_l[j] comes out of the same accumulator.
-// FP16 carries the 11-bit significand of TF32 at twice its tensor rate and
-// half its operand bytes.
+// symmetric, so hi lo^T + lo hi^T may be replaced by (2 lo) hi^T: the sum
+// G' = hi hi^T + (2 lo) hi^T has the symmetric part G~.  One tcgen05.mma
+// kind::f16 per k-step of 16 amplitudes gives both terms: A = [2 lo; hi]
+// (128 rows: the tile's 64 terms twice) against B = [hi; b] (80 rows: the
+// same 64 hi rows, then hi and lo of Re b and Im b and 12 zero rows), so
+// accumulator lanes 0..63 hold (2 lo) hi^T and lanes 64..127 hi hi^T (columns
+// 0..63), with columns 64..67 the products with b that give
+// delta_l = sum_j conj(b_j) phi_l[j] (hi hi(b) + hi lo(b) + lo hi(b)).  Every
+// accumulator entry is a wanted one.  FP16 carries the 11-bit significand of
+// TF32 at twice its tensor rate and half its operand bytes.
 //
 // Work split.  The shifted states are built before the term kernel
 // (k_tc_states; packed pairs hi | (2 lo) << 16 of 2^12 psi, L2-resident), so
@@ -863,8 +860,9 @@ constexpr int HBM_KQ = 11;
 //     of x_l pick the copy, the next two permute the loads), and write the
 //     operands of each stage (K-major, no swizzle: core matrices of 8 rows x
 //     16 bytes; LBO 128 B between the two halves of a k-step, SBO 256 B between
-//     8-row groups, 18 row groups per k-step) into a ring of TC_NSTG stages,
-//     one 16-amplitude half-row of one term per thread;
+//     8-row groups, 18 row groups per k-step: 2 lo rows in groups 0..7, hi
+//     rows in 8..15, the b rows in 16, zeros in 17) into a ring of TC_NSTG
+//     stages, one term's 16 amplitudes at two places of the stage per thread;
 //   - one MMA warp issues each stage into the accumulator of its block and
 //     commits the stage's buffer back to the builders;
 //   - 4 epilogue warps (one per quarter of the tensor-memory lanes) fold each
@@ -873,7 +871,7 @@ constexpr int HBM_KQ = 11;
 // The tensor core adds each MMA's sum into the accumulator with a rounding
 // that is not to nearest (measured: a one-sided drift of ~2^-24 |acc| per
 // MMA), so an accumulator block covers TC_FLUSH stages and the epilogue folds
-// its used parts (the two diagonal Gram quadrants, two delta columns per lane)
+// its used parts (the Gram columns and two delta columns per lane)
 // into FP32 running sums in tensor memory with round-to-nearest adds.  Two
 // accumulators alternate between blocks, so the MMAs of a block never wait for
 // the fold of the previous one.  The weighting runs in float-float arithmetic
@@ -885,7 +883,7 @@ constexpr int HBM_KQ = 11;
 // warp waits for its issued MMAs before the tensor memory is freed, and the
 // host gets DVQLS_ERR_TIMEOUT.
 // Served for tiles with L <= 64 (T = 1) of the global cost.
-constexpr int TCK = 128;            // amplitudes per stage: 2 x 64, i.e. 4 MMA k-steps of 16 in each row half
+constexpr int TCK = 128;            // amplitudes per stage of a diagonal tile: 8 MMA k-steps of 16
 constexpr int TC_BW = 16;           // builder warps
 constexpr int TC_BT = 32 * TC_BW;   // builder threads: one 16-amplitude half-row of one term per stage each
 constexpr int TC_EW = 8;            // epilogue warps, two per quarter of the tensor-memory lanes
@@ -894,7 +892,7 @@ constexpr int TCT = TC_BT + 32 + TC_ET;  // builders, the MMA warp, the epilogue
 constexpr int TC_NSTG = 4;          // operand stages in flight
 constexpr int TC_NIT = 4;           // item records in flight from the builders to the epilogue
 constexpr int TC_FLUSH = 4;         // stages per accumulator block (8 MMAs of each Gram entry per stage)
-constexpr int TC_NB = 144;          // B rows: 128 term rows, hi and lo of b (8 rows), 8 zero rows
+constexpr int TC_NB = 144;          // row groups per k-step x 8: 2 lo and hi of 64 terms, b rows, zero rows
 constexpr uint32_t TC_ACC1 = 256;   // tensor-memory columns of builder half h's accumulator: 256 h ..
 constexpr int TC_SUM = 144;         // after it: running sums of the Gram quadrants (64 columns) ...
 constexpr int TC_DSUM = 208;        // ... and of the two delta columns of a lane
@@ -906,12 +904,14 @@ constexpr long long TC_DRAIN_NS = 1000000000LL;  // 1 s for issued MMAs to compl
 constexpr float TC_SCALE = 4096.f;                     // 2^12 on the state
 constexpr float TC_UNSCALE = 1.f / (4096.f * 4096.f);  // 2^-24 on the Gram
 constexpr int TC_KSTEP_BYTES = (TC_NB / 8) * 2 * 128;       // 18 row groups x 2 halves x 128 B
-constexpr int TC_OPND_BYTES = (TCK / 32) * TC_KSTEP_BYTES;  // one operand array (hi or 2 lo) of a stage
-constexpr int TC_STAGE_BYTES = 2 * TC_OPND_BYTES;
+constexpr int TC_OPND_BYTES = (TCK / 32) * TC_KSTEP_BYTES;  // a pair stage's operand array (first or second tile)
+constexpr int TC_STAGE_BYTES = 2 * TC_OPND_BYTES;           // = TCK / 16 k-steps of a diagonal stage
 constexpr int TC_BROW = 16 * 256;   // offset of row group 16 (the b rows) inside a k-step
+constexpr int TC_HIROW = 64;        // first hi row of a diagonal k-step (rows 0..63: 2 lo)
+constexpr int TC_ND = 80;           // B rows of a diagonal k-step: 64 hi rows, 4 b rows, 12 zero rows
 constexpr int TC_X = 64 * 65;       // readout floats of one Gram quadrant ([64][65])
 constexpr int TC_EPI_BYTES = 2 * TC_X * 4 + 2 * 64 * 8;  // both quadrants and their delta sums
-constexpr int TC_BOP_STAGE = 2048;  // bytes of the b rows of one stage (both operand arrays)
+constexpr int TC_BOP_STAGE = 1024;  // bytes of the b rows of one stage (4 rows x 128 amplitudes)
 constexpr int TC_TRI = 64 * 65 / 2;  // entries l <= m of a 64-term tile
 // Position of entry (l, m), l <= m < 64, in the row-major upper triangle.
 __host__ __device__ constexpr int tc_tri(int l, int m) { return 64 * l - l * (l - 1) / 2 + (m - l); }
@@ -969,32 +969,28 @@ __device__ __forceinline__ float tc_bscale(double bn2) {
     return ldexpf(1.f, 12 - ex);
 }
 
-// The b rows of both B operands for stages blk, blk + nblk, ..., in the
-// shared-memory order of a stage's row group 16: [array (hi, 2 lo)][k-step
-// 0..3][k half 0..1][row 0..7][8 FP16 values].  Array hi: rows 0..3 hold hi of
-// Re b and Im b on the stage's first half and on its second half, rows 4..7
-// their lo parts; array 2 lo: rows 0..3 hold hi / 2 (exact), rows 4..7 zero.
-// b is scaled by tc_bscale(||b||^2).
+// The b rows of the diagonal tiles' B operand for stages blk, blk + nblk,
+// ..., in the shared-memory order of row group 16: [k-step 0..7][k half
+// 0..1][row 0..3][8 FP16 values], rows 0..3 being hi of Re b, hi of Im b, lo
+// of Re b and lo of Im b.  b is scaled by tc_bscale(||b||^2).
 __device__ __forceinline__ void tc_fill_bop(const Inst& I, double bn2, int blk, int nblk) {
     const long long N = 1LL << I.n, chunks = tc_bop_stages(N) * (TC_BOP_STAGE / 16);
     const float sb = tc_bscale(bn2);
     for (long long c = (long long)blk * 256 + threadIdx.x; c < chunks; c += 256LL * nblk) {
-        const long long stage = c >> 7;
-        const int u = int(c & 127), arr = u >> 6, ks4 = (u >> 4) & 3, kh = (u >> 3) & 1, row = u & 7;
-        const int part = row >> 2, r4 = row & 3;  // part 0: hi, 1: lo; r4: (half, Re / Im)
+        const long long stage = c >> 6;
+        const int u = int(c & 63), ks = u >> 3, kh = (u >> 2) & 1, row = u & 3;
+        const int part = row >> 1, im = row & 1;  // part 0: hi, 1: lo
         uint32_t wv[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
             uint16_t hv[2];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-                const long long j = stage * TCK + (r4 >= 2 ? TCK / 2 : 0) + ks4 * 16 + kh * 8 + e + q;
-                const double v = j < N ? ((r4 & 1) ? I.b[j].y : I.b[j].x) : 0.0;
+                const long long j = stage * TCK + ks * 16 + kh * 8 + e + q;
+                const double v = j < N ? (im ? I.b[j].y : I.b[j].x) : 0.0;
                 const float x = (float)(v * (double)sb);
                 const __half h = __float2half_rn(x);
-                __half o;
-                if (arr == 0) o = part == 0 ? h : __float2half_rn(x - __half2float(h));
-                else o = part == 0 ? __float2half_rn(0.5f * __half2float(h)) : __float2half_rn(0.f);
+                const __half o = part == 0 ? h : __float2half_rn(x - __half2float(h));
                 hv[q] = __half_as_ushort(o);
             }
             wv[e >> 1] = (uint32_t)hv[0] | ((uint32_t)hv[1] << 16);
@@ -1293,27 +1289,26 @@ __device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v) {
 }
 
 // One finished accumulator block (columns acc ..) folded by an epilogue warp
-// whose tensor-memory lanes are 32 q .. 32 q + 31 (columns 32 ch .. 32 ch + 31
-// of its quadrant; the delta columns when ch = 0).  Off-diagonal pair (`off`):
-// lanes 0..63 are the first tile's hi rows, whose Gram with the second tile is
-// the sum of columns c (its hi) and 64 + c (its lo); lanes 64..127 its lo
-// rows, column c (lo lo is dropped).  Diagonal tile: lanes 0..63 carry the first
-// half of every stage (Gram columns 0..63; delta columns 128, 129 from hi b
-// and 132, 133 from lo b), lanes 64..127 the second half (columns 64..127;
-// delta 130, 131 and 134, 135).  The first block of an item starts the running
-// sums (columns acc + TC_SUM.., acc + TC_DSUM..), later ones add to them with
-// round-to-nearest adds; the last block goes to X[half][row][col] and
-// XD[half][row] in shared memory instead.
+// whose tensor-memory lanes are 32 q .. 32 q + 31 (Gram columns 32 ch .. 32 ch
+// + 31; the delta columns when ch = 0).  Off-diagonal pair (`off`): lanes
+// 0..63 are the first tile's hi rows, whose Gram with the second tile is the
+// sum of columns c (its hi) and 64 + c (its lo); lanes 64..127 its lo rows,
+// column c (lo lo is dropped).  Diagonal tile: lanes 0..63 are the 2 lo rows
+// (delta: 2 lo hi(b) in columns 64, 65, halved here; 2 lo lo(b) in 66, 67 is
+// dropped), lanes 64..127 the hi rows (delta: columns 64 + 66, 65 + 67), Gram
+// columns 0..63 in both.  The first block of an item starts the running sums
+// (columns acc + TC_SUM.., acc + TC_DSUM..), later ones add to them with
+// round-to-nearest adds; the last block goes to X[part][row][col] and
+// XD[part][row] in shared memory instead (part: lane half).
 __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t acc, int q, int ch, int lane, bool first, bool last,
                                         bool off, float* X, float2* XD) {
     const uint32_t base = tmem + ((32u * uint32_t(q)) << 16);
-    const int cq = (q < 2 || off) ? 0 : 64, dq = q < 2 ? 0 : 2;
-    const int xr = (q & 1) * 32 + lane;  // row within the half
+    const int xr = (q & 1) * 32 + lane;  // row within the lane half
     float* Xq = X + (q >> 1) * TC_X;
 #pragma unroll 1
     for (int g = 2 * ch; g < 2 * ch + 2; ++g) {  // this warp's 32 of the quadrant's 64 columns
         float v[16];
-        tmem_ld16(base + acc + cq + 16 * g, v);
+        tmem_ld16(base + acc + 16 * g, v);
         if (off && q < 2) {  // hi rows of the first tile: hi and lo columns of the second
             float u[16];
             tmem_ld16(base + acc + 64 + 16 * g, u);
@@ -1334,8 +1329,14 @@ __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t acc, int q, int 
         }
     }
     if (ch == 0 && !off) {  // the delta columns
-        const float2 d0 = tmem_ld2(base + acc + 128 + dq), d1 = tmem_ld2(base + acc + 132 + dq);
-        float2 dv = make_float2(d0.x + d1.x, d0.y + d1.y);
+        const float2 d0 = tmem_ld2(base + acc + 64);
+        float2 dv;
+        if (q < 2) {
+            dv = make_float2(0.5f * d0.x, 0.5f * d0.y);  // exact
+        } else {
+            const float2 d1 = tmem_ld2(base + acc + 66);
+            dv = make_float2(d0.x + d1.x, d0.y + d1.y);
+        }
         if (!first) {
             const float2 du = tmem_ld2(base + acc + TC_DSUM);
             dv.x += du.x;
@@ -1481,12 +1482,13 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_abort = 0;
     }
-    // Row group 17 of both operand arrays of every stage stays zero (the MMAs
-    // read it as B rows 136..143; nothing writes it later).
-    for (int c = t; c < TC_NSTG * 2 * (TCK / 32) * 16; c += TCT) {
-        const int st = c >> 7, arr = (c >> 6) & 1, ks4 = (c >> 4) & 3, u = c & 15;
-        *reinterpret_cast<uint4*>(base + st * TC_STAGE_BYTES + arr * TC_OPND_BYTES + ks4 * TC_KSTEP_BYTES +
-                                  (17 * 2) * 128 + u * 16) = make_uint4(0u, 0u, 0u, 0u);
+    // Rows 4..7 of row group 16 and row group 17 of every k-step of every stage
+    // stay zero (a diagonal stage's MMA reads them as B rows 68..79; the pair
+    // stages use row groups 0..15 only, and only rows 0..3 of group 16 take b).
+    for (int c = t; c < TC_NSTG * (TC_STAGE_BYTES / TC_KSTEP_BYTES) * 24; c += TCT) {
+        const int blk = c / 24, u = c % 24;  // 16-byte chunk u of the zero area of k-step block blk
+        const int off16 = u < 8 ? TC_BROW + (u >> 2) * 128 + 64 + (u & 3) * 16 : TC_BROW + 256 + (u - 8) * 16;
+        *reinterpret_cast<uint4*>(base + blk * TC_KSTEP_BYTES + off16) = make_uint4(0u, 0u, 0u, 0u);
     }
     for (int q = t; q < 64 * 64; q += TCT) {
         const int l = q >> 6, m = q & 63;
@@ -1645,24 +1647,24 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 const bool brow = !off && I.bop && tt < TC_BOP_STAGE / 16;
                 if (brow) {  // the stage's b rows (j0 is a multiple of TCK), copied while the terms are built
                     const uint4* srcb = reinterpret_cast<const uint4*>(I.bop) + (long long)(j0 / TCK) * (TC_BOP_STAGE / 16) + tt;
-                    const int arr = tt >> 6, ks4 = (tt >> 4) & 3, kh = (tt >> 3) & 1, br = tt & 7;
-                    const uint32_t dst = su32((arr ? zlo : zhi) + ks4 * TC_KSTEP_BYTES + TC_BROW + kh * 128 + br * 16);
+                    const int ks8 = tt >> 3, kh = (tt >> 2) & 1, br = tt & 3;
+                    const uint32_t dst = su32(zhi + ks8 * TC_KSTEP_BYTES + TC_BROW + kh * 128 + br * 16);
                     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n\tcp.async.commit_group;" ::"r"(dst),
                                  "l"(__cvta_generic_to_global(srcb))
                                  : "memory");
                 }
                 if (!off) {
-                    // diagonal: hi to array hi, 2 lo to array 2 lo; row l (first 64
-                    // amplitudes of the stage) and row 64 + l (the next 64)
+                    // diagonal: amplitudes kk = 64 hf + 16 sub .. of the stage, hi to row
+                    // TC_HIROW + l and 2 lo to row l of the same k-steps
 #pragma unroll 1
                     for (int hf = 0; hf < 2; ++hf) {
-                        const int jb = j0 + hf * (TCK / 2) + sub * 16, row = hf * 64 + l;
+                        const int kk = hf * (TCK / 2) + sub * 16, jb = j0 + kk;
                         if (gl)
-                            tc_build_half<true, false>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, sub * 16, zhi,
-                                                       row, zlo, row, false);
+                            tc_build_half<true, false>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, kk, zhi,
+                                                       TC_HIROW + l, zhi, l, false);
                         else
-                            tc_build_half<false, false>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, sub * 16,
-                                                        zhi, row, zlo, row, copies);
+                            tc_build_half<false, false>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, kk, zhi,
+                                                        TC_HIROW + l, zhi, l, copies);
                     }
                 } else {
                     // pair: the side's array (hi array: first tile, 2 lo array: second),
@@ -1745,19 +1747,16 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                                 "l"(tc_desc(hb + ksx * TC_KSTEP_BYTES)), "l"(tc_desc(lb + ksx * TC_KSTEP_BYTES)),
                                 "r"(tc_idesc(128)), "r"(acc0));
                         }
-                    } else {
+                    } else {  // diagonal: A = [2 lo; hi] (row groups 0..15), B = [hi; b] (8..17)
 #pragma unroll
-                        for (int ksx = 0; ksx < TCK / 32; ++ksx) {
-                            const uint64_t dh = tc_desc(hb + ksx * TC_KSTEP_BYTES), dl = tc_desc(lb + ksx * TC_KSTEP_BYTES);
-                            const uint64_t db = tc_desc(lb + ksx * TC_KSTEP_BYTES + TC_BROW);
+                        for (int ksx = 0; ksx < TCK / 16; ++ksx) {
+                            const uint32_t ka = hb + ksx * TC_KSTEP_BYTES;
                             const uint32_t acc0 = ((fl & 1u) && ksx == 0) ? 0u : 1u;
                             asm volatile(
-                                "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %6, 0;\n\tsetp.eq.b32 q, %6, %6;\n\t"
-                                "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %2, %2, %4, p;\n\t"
-                                "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %2, %3, %5, q;\n\t"
-                                "tcgen05.mma.cta_group::1.kind::f16 [%1], %3, %7, %8, q;\n\t}\n" ::"r"(tm),
-                                "r"(tm + 128u), "l"(dh), "l"(dl), "r"(tc_idesc(TC_NB)), "r"(tc_idesc(128)), "r"(acc0),
-                                "l"(db), "r"(tc_idesc(16)));
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tm),
+                                "l"(tc_desc(ka)), "l"(tc_desc(ka + (TC_HIROW / 8) * 256)), "r"(tc_idesc(TC_ND)),
+                                "r"(acc0));
                         }
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(

@@ -2,24 +2,32 @@
 Algorithm 1, Step 3 with a prediction; random / fixed initialisation stays
 the fallback, and the exact cost and the fidelity measure the result).
 
-Every numeric step runs in the CUDA library: decomposition
-(dvqls_pauli_decompose_banded), classical solve (dvqls_lcu_solve), optimizer
-runs (dvqls_optimize: batched cost + parameter-shift gradient, FP64
-fidelity), network training and inference (dvqls_ws_*).  This module only
+Every numeric step of the method runs in the CUDA library: decomposition
+(dvqls_pauli_decompose_banded), classical solve (dvqls_lcu_solve), cost and
+parameter-shift gradient (dvqls_cost_grad_batched, FP64 for the training
+targets), Adam runs (dvqls_optimize, FP64 fidelity), network training and
+inference (dvqls_ws_*).  The training targets come from the paper's
+optimizer family, limited-memory BFGS (Sec. 3), carried to convergence: the
+L-BFGS steps of all systems run in lock step on the host (a few hundred
+flops per system and iteration, lbfgs.lbfgs_lockstep), each round one
+batched FP64 device pass of all running systems, until L-BFGS-B's
+projected-gradient or relative-decrease test holds.  This module
 orchestrates the calls and builds the feature / target arrays.
 
 Problem family (tridiagonal Toeplitz, Sec. 2.5.1): n in 6..10, a ~ U(2,4),
 c ~ U(-1.5,-0.5) with a > 2|c|, b = |+>^n, top-64 Pauli terms, depth-4
 Ry + CZ-ring ansatz (P = 5n <= 50 angles).  Features: [a/4, c/1.5,
-one-hot(n - 6) (5)].  Targets: the converged angles of runs started from the
-|+> initialisation (first-layer angles pi/2, the rest 0: with an even depth
-the CZ rings cancel and V|0> = |+>^n), zero-padded to 50 with a mask.
+one-hot(n - 6) (5)].  Targets: the converged angles of FP64 runs started from
+the |+> initialisation (first-layer angles pi/2, the rest 0: with an even depth
+the CZ rings cancel and V|0> = |+>^n) moved off its saddle (plus_start),
+zero-padded to 50 with a mask.
 """
 import time
 
 import numpy as np
 
 from . import dvqls as D
+from . import lbfgs
 from . import workloads as wl
 
 DEPTH = 4
@@ -41,6 +49,19 @@ def plus_init(n, d=DEPTH):
     alpha = np.zeros(n * (d + 1))
     alpha[:n] = 0.5 * np.pi
     return alpha
+
+
+def plus_start(n, d=DEPTH, scale=1e-2):
+    """The |+> start moved off the stationary point it is for this family:
+    with J = X^(x)n, a persymmetric A (J A J = A; its Pauli terms all have an
+    even number of Z / Y factors, so a pruned LCU keeps it) and b = |+>^n
+    (J b = b), V(alpha)|0> = |+>^n at the |+> angles, and the derivative of
+    the state along any angle is J-odd there (J Y_k J = -Y_k, J CZ-ring J =
+    +-CZ-ring for n >= 3, and an even depth), so <b|A|dpsi> = <psi|A^T A|dpsi>
+    = 0 and the gradient of the cost vanishes.  A fixed seeded perturbation of
+    `scale` rad per angle, the same for every system of a given n (so the
+    runs leave the saddle the same way), is added."""
+    return plus_init(n, d) + scale * np.random.default_rng(7_000 + 100 * d + n).normal(size=n * (d + 1))
 
 
 class Problem:
@@ -69,14 +90,17 @@ def prepare(ctx, seeds_and_n):
     return [Problem(ctx, s, n) for s, n in seeds_and_n]
 
 
-def optimize(ctx, problems, inits, precision=D.DVQLS_FP32, lr=0.02, max_iter=3000, target=0.9999):
+def optimize(ctx, problems, inits, precision=D.DVQLS_FP32, lr=0.02, max_iter=3000, target=0.9999, depth=DEPTH):
     """Adam runs of all problems in lock step; `target` is one fidelity for all
     or an array with one per problem.  Returns (results, final angles, seconds)."""
     keep = [np.ascontiguousarray(a, dtype=np.float64) for a in inits]
-    items = [(D.make_ansatz(p.n, DEPTH), p.lcu, a, p.b) for p, a in zip(problems, keep)]
+    sizes = [p.n * (depth + 1) for p in problems]
+    if len(keep) != len(problems) or any(a.size != P for a, P in zip(keep, sizes)):
+        raise ValueError("one start of n (depth + 1) angles per problem is required")
+    items = [(D.make_ansatz(p.n, depth), p.lcu, a, p.b) for p, a in zip(problems, keep)]
     inst = D.make_instances(items)
     xhat = np.concatenate([p.xhat for p in problems])
-    out = np.zeros(sum(p.P for p in problems))
+    out = np.zeros(sum(sizes))
     targets = None
     if np.ndim(target) == 1:
         targets = np.ascontiguousarray(target, dtype=np.float64)
@@ -86,10 +110,45 @@ def optimize(ctx, problems, inits, precision=D.DVQLS_FP32, lr=0.02, max_iter=300
     res = D.dvqls_optimize(ctx, inst, xhat, opt, out)
     secs = time.perf_counter() - t0
     alphas, off = [], 0
-    for p in problems:
-        alphas.append(out[off:off + p.P].copy())
-        off += p.P
+    for P in sizes:
+        alphas.append(out[off:off + P].copy())
+        off += P
     return res, alphas, secs
+
+
+def fidelities(ctx, problems, alphas, depth=DEPTH):
+    """F(alpha) against the classical solution (FP64, on the GPU)."""
+    res, _, _ = optimize(ctx, problems, alphas, max_iter=0, target=2.0, depth=depth)
+    return np.array([r.fidelity for r in res])
+
+
+def converged(ctx, problems, inits, depth=DEPTH, precision=D.DVQLS_FP64, gtol=1e-5, ftol=2.2e-9, max_iter=5000):
+    """L-BFGS (the paper's optimizer family) from `inits` to convergence on
+    the FP64 cost and gradient, all problems in lock step: each run ends on
+    L-BFGS-B's stopping tests with its default tolerances (max |grad| <= gtol,
+    relative decrease <= ftol), on a failed line search at the rounding floor,
+    or after max_iter iterations.  Returns (results, fidelities, seconds)."""
+    specs = [(p.n, depth, p.lcu, p.b) for p in problems]
+    t0 = time.perf_counter()
+    res = lbfgs.solve_batched(ctx, specs, [np.asarray(a, dtype=np.float64) for a in inits], precision=precision,
+                              max_iter=max_iter, gtol=gtol, ftol=ftol)
+    secs = time.perf_counter() - t0
+    return res, fidelities(ctx, problems, [r["alpha"] for r in res], depth), secs
+
+
+def lbfgs_summary(res, F, secs):
+    it = np.array([r["iters"] for r in res])
+    ev = np.array([r["evals"] for r in res])
+    gmax = np.array([np.abs(r["grad"]).max() for r in res])
+    stops = {}
+    for r in res:
+        stops[r["stopped"]] = stops.get(r["stopped"], 0) + 1
+    return {"runs": len(res), "seconds": secs, "iters_median": float(np.median(it)), "iters_max": int(it.max()),
+            "evals_median": float(np.median(ev)), "evals_total": int(ev.sum()), "stopped": stops,
+            "grad_maxnorm_median": float(np.median(gmax)), "grad_maxnorm_max": float(gmax.max()),
+            "cost_median": float(np.median([r["cost"] for r in res])),
+            "fidelity_median": float(np.median(F)), "fidelity_min": float(F.min()), "fidelity_max": float(F.max()),
+            "reach_0.9999": int((F >= 0.9999).sum())}
 
 
 def training_arrays(problems, alphas):
@@ -149,61 +208,80 @@ def summarize(res, secs, cap):
 
 def attainable(ctx, problems, iters):
     """Fidelity each problem reaches after `iters` Adam updates from the |+>
-    start with an unreachable target: the reference the evaluation is
-    measured against (the ansatz caps the fidelity below 1)."""
+    start with an unreachable target."""
     res, alphas, secs = optimize(ctx, problems, [plus_init(p.n) for p in problems], max_iter=iters, target=2.0)
     return np.array([r.fidelity for r in res]), alphas, secs
 
 
-def run(ctx, n_train=2000, n_eval=200, train_iters=1000, max_iter=3000, train_steps=3000, gap=1e-4, seed=0,
-        log=print):
-    """The full pipeline: training targets from optimizer runs, training, and
-    the held-out comparison of initialisations.  Returns a summary dict.
+def run(ctx, n_train=2000, n_eval=200, max_iter=3000, train_steps=3000, gap=1e-4, seed=0, gtol=1e-5, ftol=2.2e-9,
+        lbfgs_max_iter=5000, n_deep=50, deep_depth=6, log=print):
+    """The full pipeline: converged FP64 training targets, training, and the
+    held-out comparison of initialisations.  Returns a summary dict.
 
-    Training targets: the angles after `train_iters` updates from the |+>
-    start.  Evaluation: iterations (and wall time) for each initialisation to
-    reach F >= F_ref - gap, F_ref being what `train_iters` updates from |+>
-    reach on that problem; also the counts reaching F >= 0.99 and 0.9999."""
+    Training targets: the angles where FP64 L-BFGS from the (perturbed) |+>
+    start converges (gtol, ftol).  Evaluation on the held-out systems, for each
+    start (learned, zero, random, |+>):
+    - Adam (FP32 cost pass, FP64 fidelity): iterations and wall time to reach
+      F >= F_ref - gap, F_ref being the fidelity of the converged FP64
+      L-BFGS run from |+> on that system, and to F >= 0.99 and 0.9999;
+    - FP64 L-BFGS to convergence: iterations, evaluations, wall time and
+      the fidelity it ends at.
+    The |+> start is plus_start (|+> itself is a stationary point).
+    A depth-`deep_depth` converged run on the first `n_deep` held-out
+    systems shows what a deeper ansatz of the same family attains."""
     rng = np.random.default_rng(seed)
     train_specs = [(10_000 + k, int(rng.integers(N_MIN, N_MAX + 1))) for k in range(n_train)]
     eval_specs = [(90_000 + k, N_MAX) for k in range(n_eval)]
+    conv = dict(gtol=gtol, ftol=ftol, max_iter=lbfgs_max_iter)
     t0 = time.perf_counter()
     tr = prepare(ctx, train_specs)
     ev = prepare(ctx, eval_specs)
     log("prepared %d + %d problems in %.1f s" % (len(tr), len(ev), time.perf_counter() - t0))
-    F_tr, alphas, secs = attainable(ctx, tr, train_iters)
-    log("training targets: %d runs of %d updates in %.1f s, median F %.6f" % (len(tr), train_iters, secs,
-                                                                             np.median(F_tr)))
-    X, Y, M = training_arrays(tr, alphas)
+    res_tr, F_tr, secs = converged(ctx, tr, [plus_start(p.n) for p in tr], **conv)
+    targets = lbfgs_summary(res_tr, F_tr, secs)
+    log("training targets: %s" % targets)
+    X, Y, M = training_arrays(tr, [r["alpha"] for r in res_tr])
     t1 = time.perf_counter()
     ws, losses = train(ctx, X, Y, M, steps=train_steps, log_every=max(1, train_steps // 10))
     train_s = time.perf_counter() - t1
     log("trained in %.1f s, loss %s" % (train_s, losses[-1] if losses else None))
-    F_ref, _, ref_s = attainable(ctx, ev, train_iters)
-    out = {"train": {"runs": len(tr), "updates_per_run": train_iters, "optimizer_seconds": secs,
-                     "median_fidelity": float(np.median(F_tr)), "train_seconds": train_s, "loss_curve": losses},
-           "eval": {"problems": len(ev), "n": N_MAX, "gap": gap,
-                    "reference_fidelity_median": float(np.median(F_ref)),
-                    "reference_fidelity_min": float(F_ref.min()), "reference_fidelity_max": float(F_ref.max())},
-           "inits": {}}
     inits = {
+        "mlp": predict(ws, ev),
         "zero": [np.zeros(p.P) for p in ev],
         "random": [np.random.default_rng(p.seed).uniform(-np.pi, np.pi, p.P) for p in ev],
-        "plus": [plus_init(p.n) for p in ev],
-        "mlp": predict(ws, ev),
+        "plus": [plus_start(p.n) for p in ev],
     }
-    for name, a0 in inits.items():
-        row = {}
-        r, _, s = optimize(ctx, ev, a0, max_iter=max_iter, target=F_ref - gap)
-        row["to_reference"] = summarize(r, s, max_iter)
-        for level in (0.99, 0.9999):
-            r, _, s = optimize(ctx, ev, a0, max_iter=max_iter, target=level)
-            row["to_%g" % level] = summarize(r, s, max_iter)
-        r, _, s = optimize(ctx, ev, a0, max_iter=0, target=2.0)
-        row["initial_fidelity_median"] = float(np.median([x.fidelity for x in r]))
-        out["inits"][name] = row
-        log("eval %-6s %s" % (name, row))
     D.dvqls_ws_destroy(ws)
+    out = {"train": {"targets": targets, "gtol": gtol, "ftol": ftol, "train_seconds": train_s,
+                     "loss_curve": losses},
+           "eval": {"problems": len(ev), "n": N_MAX, "gap": gap}, "inits": {}}
+    lb = {}
+    for name, a0 in inits.items():
+        r, F, s_ = converged(ctx, ev, a0, **conv)
+        lb[name] = (r, F)
+        out["inits"][name] = {"lbfgs_fp64": lbfgs_summary(r, F, s_)}
+        log("eval %-6s L-BFGS %s" % (name, out["inits"][name]["lbfgs_fp64"]))
+    F_ref = lb["plus"][1]
+    out["eval"].update({"reference": "FP64 L-BFGS from |+> (plus_start) to convergence",
+                        "reference_fidelity_median": float(np.median(F_ref)),
+                        "reference_fidelity_min": float(F_ref.min()), "reference_fidelity_max": float(F_ref.max())})
+    for name, a0 in inits.items():
+        row = out["inits"][name]
+        r, _, s_ = optimize(ctx, ev, a0, max_iter=max_iter, target=F_ref - gap)
+        row["adam_to_reference"] = summarize(r, s_, max_iter)
+        for level in (0.99, 0.9999):
+            r, _, s_ = optimize(ctx, ev, a0, max_iter=max_iter, target=level)
+            row["adam_to_%g" % level] = summarize(r, s_, max_iter)
+        row["initial_fidelity_median"] = float(np.median(fidelities(ctx, ev, a0)))
+        log("eval %-6s Adam %s" % (name, {k: v for k, v in row.items() if k != "lbfgs_fp64"}))
+    if n_deep > 0:
+        deep = ev[:n_deep]
+        r, F, s_ = converged(ctx, deep, [plus_start(p.n, deep_depth) for p in deep], depth=deep_depth, **conv)
+        F4 = F_ref[:n_deep]
+        out["deep"] = {"depth": deep_depth, "angles": N_MAX * (deep_depth + 1), **lbfgs_summary(r, F, s_),
+                       "depth4_fidelity_median_same_systems": float(np.median(F4)),
+                       "improved_over_depth4": int((F > F4).sum())}
+        log("depth %d: %s" % (deep_depth, out["deep"]))
     return out
 
 
@@ -216,14 +294,19 @@ def main():
     ap = argparse.ArgumentParser(description="learned warm start: train and evaluate")
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--eval", type=int, default=200)
-    ap.add_argument("--train-iters", type=int, default=1000)
-    ap.add_argument("--max-iter", type=int, default=3000)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--max-iter", type=int, default=3000, help="Adam updates at most in the evaluation")
+    ap.add_argument("--steps", type=int, default=3000, help="network training steps")
+    ap.add_argument("--gtol", type=float, default=1e-5)
+    ap.add_argument("--ftol", type=float, default=2.2e-9)
+    ap.add_argument("--lbfgs-max-iter", type=int, default=5000)
+    ap.add_argument("--deep", type=int, default=50, help="held-out systems of the deeper-ansatz run")
+    ap.add_argument("--deep-depth", type=int, default=6)
     args = ap.parse_args()
     assert torch.cuda.is_available()
     ctx = D.dvqls_create(0, torch.cuda.current_stream().cuda_stream)
     try:
-        out = run(ctx, args.train, args.eval, args.train_iters, args.max_iter, args.steps)
+        out = run(ctx, args.train, args.eval, args.max_iter, args.steps, gtol=args.gtol, ftol=args.ftol,
+                  lbfgs_max_iter=args.lbfgs_max_iter, n_deep=args.deep, deep_depth=args.deep_depth)
     finally:
         D.dvqls_destroy(ctx)
     print(json.dumps(out))

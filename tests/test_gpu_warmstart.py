@@ -91,21 +91,26 @@ def test_checkpoint_round_trip(dv, ctx, tmp_path):
 
 
 def test_learned_start_beats_fallback(dv, ctx):
-    """Reduced pipeline (n = 6..8): starting from the network's angles reaches
-    the attainable fidelity (within 1e-4 of what 600 updates from |+> reach)
-    in fewer optimizer iterations than the zero start, and starts closer."""
+    """Reduced pipeline (n = 6..8).  Training targets: FP64 L-BFGS runs from
+    the perturbed |+> start carried to convergence (L-BFGS-B's default
+    stopping tests).  Held out: starting from the network's angles, Adam
+    reaches F_ref - 1e-4 (F_ref: the converged FP64 run from |+>) in fewer
+    iterations than from the zero start and starts closer, and FP64 L-BFGS
+    from it converges in fewer iterations than from |+>."""
     rng = np.random.default_rng(3)
     train = W.prepare(ctx, [(20_000 + k, int(rng.integers(6, 9))) for k in range(160)])
     held = W.prepare(ctx, [(95_000 + k, 8) for k in range(16)])
-    F_tr, alphas, _ = W.attainable(ctx, train, 600)
-    X, Y, M = W.training_arrays(train, alphas)
+    res_tr, F_tr, _ = W.converged(ctx, train, [W.plus_start(p.n) for p in train])
+    assert all(r["stopped"] in ("gtol", "ftol", "ls") and r["iters"] > 0 for r in res_tr)
+    assert np.median([np.abs(r["grad"]).max() for r in res_tr]) <= 1e-2
+    X, Y, M = W.training_arrays(train, [r["alpha"] for r in res_tr])
     ws, losses = W.train(ctx, X, Y, M, hidden=256, steps=1500, lr=2e-3, log_every=500)
     assert losses[-1][1] < losses[0][1]
     try:
         a_mlp = W.predict(ws, held)
     finally:
         dv.dvqls_ws_destroy(ws)
-    F_ref, _, _ = W.attainable(ctx, held, 600)
+    res_plus, F_ref, _ = W.converged(ctx, held, [W.plus_start(p.n) for p in held])
     target = F_ref - 1e-4
     r_mlp, _, _ = W.optimize(ctx, held, a_mlp, max_iter=2000, target=target)
     r_zero, _, _ = W.optimize(ctx, held, [np.zeros(p.P) for p in held], max_iter=2000, target=target)
@@ -113,6 +118,7 @@ def test_learned_start_beats_fallback(dv, ctx):
     it_zero = np.array([r.iters if r.converged else 2000 for r in r_zero])
     assert sum(r.converged for r in r_mlp) >= sum(r.converged for r in r_zero)
     assert np.median(it_mlp) < np.median(it_zero)
-    f0_mlp = [r.fidelity for r in W.optimize(ctx, held, a_mlp, max_iter=0, target=2.0)[0]]
-    f0_zero = [r.fidelity for r in W.optimize(ctx, held, [np.zeros(p.P) for p in held], max_iter=0, target=2.0)[0]]
-    assert np.median(f0_mlp) > np.median(f0_zero)
+    zero = [np.zeros(p.P) for p in held]
+    assert np.median(W.fidelities(ctx, held, a_mlp)) > np.median(W.fidelities(ctx, held, zero))
+    res_mlp, _, _ = W.converged(ctx, held, a_mlp)
+    assert np.median([r["iters"] for r in res_mlp]) < np.median([r["iters"] for r in res_plus])

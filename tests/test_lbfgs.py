@@ -97,3 +97,101 @@ def test_solve_routes_to_the_library_calls(monkeypatch):
                     local=True)
     assert r["converged"] and {s[0] for s in seen} == {"local"} and {s[1] for s in seen} == {1}
     assert oterms.local_cost_grad(n, d, r["alpha"], coef, xs, zs)["cost"] <= 1e-10
+
+
+def test_stopping_tests_and_final_gradient():
+    """gtol / ftol end the run by L-BFGS-B's own tests; the returned gradient
+    is the one evaluated at the returned angles."""
+    v, n, d, xhat, fun_grad, calls = _validation()
+    r = lbfgsb_loop(fun_grad, v["alphas"][2], eps=-1.0, max_iter=2000, gtol=1e-7, ftol=1e-14)
+    assert r["stopped"] == "gtol/ftol" and not r["converged"]
+    ref = oterms.cost_grad(n, d, r["alpha"], v["b"], *_lcu(v))
+    assert r["cost"] == ref["cost"] and np.array_equal(r["grad"], ref["grad"])
+    assert np.abs(r["grad"]).max() <= 1e-5
+    r = lbfgsb_loop(fun_grad, v["alphas"][2], eps=-1.0, max_iter=4)
+    assert r["stopped"] == "max_iter" and r["iters"] == 4
+
+
+def _oracle_batched():
+    v, n, d, xhat, fun_grad, calls = _validation()
+    coef, xs, zs = _lcu(v)
+    batches = []
+
+    def fgb(idx, alphas):
+        batches.append(list(idx))
+        rs = [oterms.cost_grad(n, d, np.asarray(a), v["b"], coef, xs, zs) for a in alphas]
+        return [r["cost"] for r in rs], [r["grad"] for r in rs]
+
+    return v, n, d, xhat, fgb, batches
+
+
+def test_lockstep_quadratic_and_rosenbrock():
+    """Problems of different sizes in one run: a separable quadratic (minimum
+    at a known point) and the Rosenbrock function (minimum at (1, 1))."""
+    from paper_2604_14435_gb300.lbfgs import lbfgs_lockstep
+
+    target = np.array([0.5, -1.25, 2.0])
+
+    def fgb(idx, alphas):
+        out_f, out_g = [], []
+        for k, a in zip(idx, alphas):
+            if k == 0:
+                out_f.append(float(np.sum((a - target) ** 2)))
+                out_g.append(2.0 * (a - target))
+            else:
+                x, y = a
+                out_f.append((1 - x) ** 2 + 100 * (y - x * x) ** 2)
+                out_g.append(np.array([-2 * (1 - x) - 400 * x * (y - x * x), 200 * (y - x * x)]))
+        return out_f, out_g
+
+    r = lbfgs_lockstep(fgb, [np.zeros(3), np.array([-1.2, 1.0])], gtol=1e-9, ftol=0.0, max_iter=500, first_step=1.0)
+    assert r[0]["stopped"] == "gtol" and np.allclose(r[0]["alpha"], target, atol=1e-9)
+    assert r[1]["stopped"] == "gtol" and np.allclose(r[1]["alpha"], [1.0, 1.0], atol=1e-7)
+    assert r[0]["iters"] < r[1]["iters"] < 200
+    assert all(np.all(np.diff(x["history"]) <= 0) for x in r)  # Armijo: the cost never rises
+
+
+def test_lockstep_reaches_the_solution_and_batches_rounds():
+    """On the n = 3 validation system (oracle cost and gradient) every start
+    converges to C ~ 0 and F >= 0.9999; each round evaluates the running
+    problems together, and a problem's result does not depend on the others
+    it ran with."""
+    from paper_2604_14435_gb300.lbfgs import lbfgs_lockstep
+
+    v, n, d, xhat, fgb, batches = _oracle_batched()
+    starts = [np.asarray(a) for a in v["alphas"][:4]]
+    res = lbfgs_lockstep(fgb, starts, gtol=1e-8, ftol=0.0, max_iter=300)
+    for r in res:
+        # at C ~ 1e-15 the FP64 cost is rounding noise: a run may end there on a failed line search
+        assert r["stopped"] in ("gtol", "ls") and r["cost"] <= 1e-10 and np.abs(r["grad"]).max() <= 1e-7
+        assert oterms.fidelity(oterms.ansatz_state(n, d, r["alpha"]), xhat) >= 0.9999
+        assert r["evals"] >= r["iters"] + 1 and len(r["history"]) == r["iters"]
+    assert batches[0] == [0, 1, 2, 3] and sum(len(b) for b in batches) == sum(r["evals"] for r in res)
+    alone = lbfgs_lockstep(fgb, starts[2:3], gtol=1e-8, ftol=0.0, max_iter=300)[0]
+    assert alone["iters"] == res[2]["iters"] and alone["stopped"] == res[2]["stopped"]
+    assert np.allclose(alone["alpha"], res[2]["alpha"], atol=1e-12, rtol=0)
+
+
+def test_lockstep_stopping_tests():
+    """ftol ends a run on a small relative decrease; max_iter caps it; a
+    stationary start (zero gradient) ends at once; evaluation errors reach
+    the caller."""
+    from paper_2604_14435_gb300.lbfgs import lbfgs_lockstep
+
+    v, n, d, xhat, fgb, batches = _oracle_batched()
+    a0 = np.asarray(v["alphas"][1])
+    r = lbfgs_lockstep(fgb, [a0], gtol=0.0, ftol=1e-6, max_iter=1000)[0]
+    assert r["stopped"] == "ftol"
+    h = [fgb([0], [a0])[0][0]] + r["history"]
+    assert h[-2] - h[-1] <= 1e-6 * max(abs(h[-2]), abs(h[-1]), 1.0)
+    assert all(h[k] - h[k + 1] > 1e-6 * max(abs(h[k]), abs(h[k + 1]), 1.0) for k in range(len(h) - 2))
+    r = lbfgs_lockstep(fgb, [a0], gtol=0.0, ftol=0.0, max_iter=3)[0]
+    assert r["stopped"] == "max_iter" and r["iters"] == 3
+    flat = lbfgs_lockstep(lambda idx, al: ([1.0] * len(idx), [np.zeros_like(a) for a in al]), [np.ones(4)])[0]
+    assert flat["stopped"] == "gtol" and flat["iters"] == 0 and flat["evals"] == 1
+
+    def boom(idx, alphas):
+        raise RuntimeError("device failure")
+
+    with pytest.raises(RuntimeError, match="device failure"):
+        lbfgs_lockstep(boom, [np.zeros(3)])

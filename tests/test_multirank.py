@@ -119,17 +119,19 @@ def test_reference_arm_line_on_rank0(monkeypatch, capsys):
 
 def test_bench_work_accounting():
     """The headline's algorithmic and executed work per step (8N FLOP per paper
-    term; per 32 amplitudes of a 64-term tile, FP16 MMAs of 128 x 144 x 16,
-    128 x 128 x 16 and 128 x 16 x 16 on the tensor cores; per 16 amplitudes of
-    a pair of tiles one 128 x 128 x 16)."""
+    term; per 16 amplitudes of a 64-term tile one FP16 MMA of 128 x 80 x 16 on
+    the tensor cores, and of a pair of tiles one 128 x 128 x 16)."""
     shapes = [(10, 4, 64)] * 32
     terms, alg, exe = bench.work_of(shapes, tensor=True)
     assert terms == 32 * 101 * (64 * 64 + 64) == 13_445_120
     assert alg == terms * 8 * 1024  # 110.1 GFLOP
-    assert exe == 32 * 101 * 2 * 128 * (144 + 128 + 16) * 16 * (1024 // 32) == 122_003_914_752
+    assert exe == 32 * 101 * 2 * 128 * 80 * 16 * (1024 // 16) == 67_779_952_640
     # L = 256: four diagonal tiles and six pairs of tiles per shift
     _, _, exe_hs = bench.work_of([(10, 6, 256)], tensor=True)
-    assert exe_hs == 141 * (4 * 2 * 128 * 288 * 16 * 32 + 6 * 2 * 128 * 128 * 16 * 64)
+    assert exe_hs == 141 * (4 * 2 * 128 * 80 * 16 * 64 + 6 * 2 * 128 * 128 * 16 * 64)
+    # a state smaller than a stage still runs the stage's MMAs (zero rows)
+    _, _, exe_small = bench.work_of([(4, 2, 16)], tensor=True)
+    assert exe_small == 25 * 8 * 2 * 128 * 80 * 16
     _, _, exe_cc = bench.work_of(shapes, tensor=False)
     assert bench.executed_gram_entries(64) == 136 * 16
     assert bench.executed_gram_entries(128) == 2 * 136 * 16 + 2 * 128 * 16
