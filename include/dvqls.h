@@ -472,10 +472,9 @@ int dvqls_ws_load(dvqls_ctx* ctx, const char* path, dvqls_ws** out);
  * returns, so cost and grad are written when it returns.  alpha, b, the lcu
  * arrays, cost and grad must all be device memory of the current device
  * (nothing is staged): a host pointer is INVALID_ARG.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) once and keeps it for the process; make that first
- * call before any stream capture.  Because the address is kept, the process
- * must not reset the device (cudaDeviceReset) after its first call.
+ * Every call looks up the array's device address (cudaGetSymbolAddress,
+ * with the current device) instead of keeping one from an earlier call, so a
+ * device reset by the host program between calls leaves no stale address.
  * Every call shares the one array and finds the previous call's contents
  * there: two calls that overlap on the GPU (other streams, other threads)
  * race and give wrong results, so keep calls ordered on one stream or

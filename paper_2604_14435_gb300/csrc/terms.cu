@@ -55,8 +55,6 @@ struct Inst {
     double2* w;      // L*L: conj(ctil_l) ctil_m
     float4* wf;      // L*L or null: w as float pairs (Re hi, Re lo, Im hi, Im lo)
     float4* cf;      // L or null: ctil as float pairs
-    float2* wt;      // tensor-core pass: Re w_lm as a float pair (hi, lo) for the entries l <= m of each
-                     // diagonal 64-term tile in row-major order (TC_TRI per tile; zero past L), or null
     void* bop;       // tensor-core tiles: the b rows of the B operand, TC_BOP_STAGE bytes per stage, or null
     void* wht;       // Walsh-Hadamard classes: the class table (WHT_TABLE_BYTES), or null
     float2* bf;      // Walsh-Hadamard classes: b in FP32, or null
@@ -893,9 +891,10 @@ constexpr int TC_NSTG = 4;          // operand stages in flight
 constexpr int TC_NIT = 4;           // item records in flight from the builders to the epilogue
 constexpr int TC_FLUSH = 4;         // stages per accumulator block (8 MMAs of each Gram entry per stage)
 constexpr int TC_NB = 144;          // row groups per k-step x 8: 2 lo and hi of 64 terms, b rows, zero rows
-constexpr uint32_t TC_ACC1 = 256;   // tensor-memory columns of builder half h's accumulator: 256 h ..
-constexpr int TC_SUM = 144;         // after it: running sums of the Gram quadrants (64 columns) ...
-constexpr int TC_DSUM = 208;        // ... and of the two delta columns of a lane
+constexpr uint32_t TC_ACC1 = 256;   // tensor-memory columns of builder half h: 256 h ..
+constexpr uint32_t TC_SLOT = 80;    // its two accumulator slots at 0 and 80 (blocks alternate between them) ..
+constexpr int TC_SUM = 160;         // .. then the running sums of the Gram quadrants (64 columns) ..
+constexpr int TC_DSUM = 224;        // .. and of the two delta columns of a lane
 constexpr int TC_COLS = 512;        // tensor-memory columns allocated
 // kind::f16 instruction descriptor: F32 accumulator (bits 4-5 = 1), A and B
 // FP16 (bits 7-9, 10-12 = 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
@@ -912,10 +911,6 @@ constexpr int TC_ND = 80;           // B rows of a diagonal k-step: 64 hi rows, 
 constexpr int TC_X = 64 * 65;       // readout floats of one Gram quadrant ([64][65])
 constexpr int TC_EPI_BYTES = 2 * TC_X * 4 + 2 * 64 * 8;  // both quadrants and their delta sums
 constexpr int TC_BOP_STAGE = 1024;  // bytes of the b rows of one stage (4 rows x 128 amplitudes)
-constexpr int TC_TRI = 64 * 65 / 2;  // entries l <= m of a 64-term tile
-// Position of entry (l, m), l <= m < 64, in the row-major upper triangle.
-__host__ __device__ constexpr int tc_tri(int l, int m) { return 64 * l - l * (l - 1) / 2 + (m - l); }
-constexpr int TC_WPT = (TC_TRI + 32 * 8 - 1) / (32 * 8);  // triangle entries per epilogue thread
 // Tile item u of a shift for T = ceil(L/64) tiles: u < T is the diagonal tile
 // (u, u); u >= T the off-diagonal pair number u - T, pairs (tl < tm) in
 // row-major order.
@@ -1086,30 +1081,13 @@ __global__ void __launch_bounds__(NT) k_prepare(const Inst* __restrict__ insts, 
             I.cs[I.P + a] = make_double2(c1, s1);
             I.cs[2 * I.P + a] = make_double2(c2, s2);
         }
-    const long long LL = (long long)I.L * I.L;
+    const long long LL = I.w ? (long long)I.L * I.L : 0;  // no pair weights for the tensor-core tiles
     const long long per = (LL + parts - 1) / parts, e0 = part * per, e1 = min(LL, e0 + per);
     for (long long e = e0 + t; e < e1; e += NT) {
         const double2 a = ctil_of(I, int(e / I.L)), b = ctil_of(I, int(e % I.L));
         const double2 wv = make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
         I.w[e] = wv;
         if (I.wf) I.wf[e] = split_ff(wv);
-    }
-    if (I.wt) {  // Re w of the diagonal tiles' triangles, in the tensor-core epilogue's order
-        const long long tot = (long long)I.T * TT * TT;
-        const long long tper = (tot + parts - 1) / parts, q0 = part * tper, q1 = min(tot, q0 + tper);
-        for (long long qq = q0 + t; qq < q1; qq += NT) {
-            const int tl = int(qq / (TT * TT)), q = int(qq % (TT * TT)), a = q >> 6, bb = q & 63;
-            if (a > bb) continue;
-            const int l = tl * TT + a, m = tl * TT + bb;
-            float2 v = make_float2(0.f, 0.f);
-            if (l < I.L && m < I.L) {
-                const double2 x = ctil_of(I, l), y = ctil_of(I, m);
-                const double re = x.x * y.x + x.y * y.y;
-                const float hi = (float)re;
-                v = make_float2(hi, (float)(re - (double)hi));
-            }
-            I.wt[(long long)tl * TC_TRI + tc_tri(a, bb)] = v;
-        }
     }
 }
 
@@ -1288,36 +1266,31 @@ __device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v) {
                  : "memory");
 }
 
-// One finished accumulator block (columns acc ..) folded by an epilogue warp
-// whose tensor-memory lanes are 32 q .. 32 q + 31 (Gram columns 32 ch .. 32 ch
-// + 31; the delta columns when ch = 0).  Off-diagonal pair (`off`): lanes
-// 0..63 are the first tile's hi rows, whose Gram with the second tile is the
-// sum of columns c (its hi) and 64 + c (its lo); lanes 64..127 its lo rows,
-// column c (lo lo is dropped).  Diagonal tile: lanes 0..63 are the 2 lo rows
-// (delta: 2 lo hi(b) in columns 64, 65, halved here; 2 lo lo(b) in 66, 67 is
-// dropped), lanes 64..127 the hi rows (delta: columns 64 + 66, 65 + 67), Gram
-// columns 0..63 in both.  The first block of an item starts the running sums
-// (columns acc + TC_SUM.., acc + TC_DSUM..), later ones add to them with
-// round-to-nearest adds; the last block goes to X[part][row][col] and
-// XD[part][row] in shared memory instead (part: lane half).
-__device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t acc, int q, int ch, int lane, bool first, bool last,
-                                        bool off, float* X, float2* XD) {
-    const uint32_t base = tmem + ((32u * uint32_t(q)) << 16);
+// One finished accumulator block (slot columns hb + slot ..) folded by an
+// epilogue warp whose tensor-memory lanes are 32 q .. 32 q + 31 (Gram columns
+// 32 ch .. 32 ch + 31; the delta columns when ch = 0).  Off-diagonal pair
+// (`off`): lanes 0..63 are the first tile's hi rows and lanes 64..127 its lo
+// rows, each against hi + lo of the second tile (two MMAs into the same 64
+// columns; lo lo, ~2^-22 of the product, rides along).  Diagonal tile: lanes
+// 0..63 are the 2 lo rows (delta: 2 lo hi(b) in columns 64, 65, halved here;
+// 2 lo lo(b) in 66, 67 is dropped), lanes 64..127 the hi rows (delta: columns
+// 64 + 66, 65 + 67), Gram columns 0..63 in both.  The first block of an item
+// starts the half's running sums (columns hb + TC_SUM.., hb + TC_DSUM..), later
+// ones add to them with round-to-nearest adds; the last block goes to
+// X[part][row][col] and XD[part][row] in shared memory instead (part: lane
+// half).
+__device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t hb, uint32_t slot, int q, int ch, int lane, bool first,
+                                        bool last, bool off, float* X, float2* XD) {
+    const uint32_t base = tmem + ((32u * uint32_t(q)) << 16), acc = hb + slot * TC_SLOT;
     const int xr = (q & 1) * 32 + lane;  // row within the lane half
     float* Xq = X + (q >> 1) * TC_X;
 #pragma unroll 1
     for (int g = 2 * ch; g < 2 * ch + 2; ++g) {  // this warp's 32 of the quadrant's 64 columns
         float v[16];
         tmem_ld16(base + acc + 16 * g, v);
-        if (off && q < 2) {  // hi rows of the first tile: hi and lo columns of the second
-            float u[16];
-            tmem_ld16(base + acc + 64 + 16 * g, u);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] += u[j];
-        }
         if (!first) {
             float u[16];
-            tmem_ld16(base + acc + TC_SUM + 16 * g, u);
+            tmem_ld16(base + hb + TC_SUM + 16 * g, u);
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] += u[j];
         }
@@ -1325,7 +1298,7 @@ __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t acc, int q, int 
 #pragma unroll
             for (int j = 0; j < 16; ++j) Xq[xr * 65 + 16 * g + j] = v[j];
         } else {
-            tmem_st16(base + acc + TC_SUM + 16 * g, v);
+            tmem_st16(base + hb + TC_SUM + 16 * g, v);
         }
     }
     if (ch == 0 && !off) {  // the delta columns
@@ -1338,12 +1311,12 @@ __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t acc, int q, int 
             dv = make_float2(d0.x + d1.x, d0.y + d1.y);
         }
         if (!first) {
-            const float2 du = tmem_ld2(base + acc + TC_DSUM);
+            const float2 du = tmem_ld2(base + hb + TC_DSUM);
             dv.x += du.x;
             dv.y += du.y;
         }
         if (last) XD[(q >> 1) * 64 + xr] = dv;
-        else tmem_st2(base + acc + TC_DSUM, dv);
+        else tmem_st2(base + hb + TC_DSUM, dv);
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -1445,8 +1418,8 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long fullb[TC_NSTG], emptyb[TC_NSTG], accf[2], acce[2], itf[2][TC_NIT],
-        ite[2][TC_NIT], drainb;
+    __shared__ __align__(8) unsigned long long fullb[TC_NSTG], emptyb[TC_NSTG], accf[2][2], acce[2][2],
+        itf[2][TC_NIT], ite[2][TC_NIT], drainb;
     __shared__ uint32_t srec[TC_NSTG][2];
     __shared__ int4 irec[2][TC_NIT];
     __shared__ int4 s_cur[2];  // epilogue: the item record each half is on
@@ -1455,7 +1428,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
     __shared__ int s_abort, s_pick;
     __shared__ uint32_t sxl[2][128], szl[2][128];  // per half: masks of the item's tile (and of a pair's second)
     __shared__ float sred[3][2][TC_EW];
-    __shared__ uint16_t stri[TC_TRI];        // (l, m) of triangle entry e: l | m << 8
+    __shared__ __align__(16) float4 scf[2][128];  // per half: c~ of the item's two tiles (zero past L)
     __shared__ long long s_ibase[TC_MAXC];  // item bases of the first TC_MAXC instances
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     unsigned char* base;
@@ -1471,8 +1444,10 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&emptyb[k])), "r"(1));
         }
         for (int k = 0; k < 2; ++k) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&accf[k])), "r"(1));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&acce[k])), "r"(TC_ET));
+            for (int sl = 0; sl < 2; ++sl) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&accf[k][sl])), "r"(1));
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&acce[k][sl])), "r"(TC_ET));
+            }
             for (int r = 0; r < TC_NIT; ++r) {
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&itf[k][r])), "r"(1));
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ite[k][r])), "r"(1));
@@ -1489,10 +1464,6 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         const int blk = c / 24, u = c % 24;  // 16-byte chunk u of the zero area of k-step block blk
         const int off16 = u < 8 ? TC_BROW + (u >> 2) * 128 + 64 + (u & 3) * 16 : TC_BROW + 256 + (u - 8) * 16;
         *reinterpret_cast<uint4*>(base + blk * TC_KSTEP_BYTES + off16) = make_uint4(0u, 0u, 0u, 0u);
-    }
-    for (int q = t; q < 64 * 64; q += TCT) {
-        const int l = q >> 6, m = q & 63;
-        if (l <= m) stri[tc_tri(l, m)] = uint16_t(l | (m << 8));
     }
     for (int i = t; i < min(count, TC_MAXC); i += TCT) s_ibase[i] = insts[i].item_base;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1710,9 +1681,10 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         if (ab) s_abort = 1;
     } else if (w == TC_BW) {  // ------------------------------------------------------------- MMA warp
         if (lane == 0) {
-            // per half: next slot (bit h), parity of full[2h + q] (bit 2h + q), parity of acce[h] (bit h),
-            // accumulator used before (bit h), done (bit h)
-            uint32_t nq = 0u, fph = 0u, aph = 0u, aused = 0u, done = 0u;
+            // per half h: next ring slot (bit h), parity of full[2h + q] (bit 2h + q), accumulator slot
+            // of the block in progress (bit h) and of the next block (bit h); per accumulator slot sl of
+            // half h (bit 2h + sl): parity of acce[h][sl], slot used before; done (bit h)
+            uint32_t nq = 0u, fph = 0u, csl = 0u, nsl = 0u, aph = 0u, aused = 0u, done = 0u;
             unsigned long long idle0 = gtimer_ns();
             while (done != 3u) {
                 bool progressed = false;
@@ -1722,11 +1694,18 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                     if (!mbar_try(su32(&fullb[st]), (fph >> st) & 1u)) continue;
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const uint32_t hb = srec[st][0], fl = srec[st][1];
-                    if (hb != TC_EXIT && (fl & 1u) && ((aused >> h) & 1u)) {
-                        // first stage of a block: the epilogue must have read the half's last block
-                        if (!mbar_try(su32(&acce[h]), (aph >> h) & 1u)) continue;  // the other half meanwhile
-                        aph ^= 1u << h;
-                        asm volatile("tcgen05.fence::after_thread_sync;");
+                    if (hb != TC_EXIT && (fl & 1u)) {
+                        // first stage of a block: its slot must have been read out by the epilogue
+                        // (the block before last of this half); the other half meanwhile
+                        const uint32_t sl = (nsl >> h) & 1u, sb = 2u * h + sl;
+                        if ((aused >> sb) & 1u) {
+                            if (!mbar_try(su32(&acce[h][sl]), (aph >> sb) & 1u)) continue;
+                            aph ^= 1u << sb;
+                            asm volatile("tcgen05.fence::after_thread_sync;");
+                        }
+                        aused |= 1u << sb;
+                        csl = (csl & ~(1u << h)) | (sl << h);
+                        nsl ^= 1u << h;
                     }
                     fph ^= 1u << st;
                     nq ^= 1u << h;
@@ -1735,17 +1714,22 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                         done |= 1u << h;
                         continue;
                     }
-                    if (fl & 1u) aused |= 1u << h;
-                    const uint32_t lb = hb + TC_OPND_BYTES, tm = s_tmem + uint32_t(h) * TC_ACC1;
-                    if (fl & 4u) {  // pair: [hi; lo] of the first tile against [hi; lo] of the second
+                    const uint32_t sl = (csl >> h) & 1u;
+                    const uint32_t lb = hb + TC_OPND_BYTES, tm = s_tmem + uint32_t(h) * TC_ACC1 + sl * TC_SLOT;
+                    if (fl & 4u) {  // pair: [hi; lo] of the first tile against hi, then lo, of the second
 #pragma unroll
                         for (int ksx = 0; ksx < TCK / 32; ++ksx) {
                             const uint32_t acc0 = ((fl & 1u) && ksx == 0) ? 0u : 1u;
+                            const uint64_t da = tc_desc(hb + ksx * TC_KSTEP_BYTES);
                             asm volatile(
                                 "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tm),
-                                "l"(tc_desc(hb + ksx * TC_KSTEP_BYTES)), "l"(tc_desc(lb + ksx * TC_KSTEP_BYTES)),
-                                "r"(tc_idesc(128)), "r"(acc0));
+                                "l"(da), "l"(tc_desc(lb + ksx * TC_KSTEP_BYTES)), "r"(tc_idesc(64)), "r"(acc0));
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tm),
+                                "l"(da), "l"(tc_desc(lb + ksx * TC_KSTEP_BYTES + 8 * 256)), "r"(tc_idesc(64)),
+                                "r"(1u));
                         }
                     } else {  // diagonal: A = [2 lo; hi] (row groups 0..15), B = [hi; b] (8..17)
 #pragma unroll
@@ -1763,7 +1747,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                         su32(&emptyb[st])));
                     if (fl & 2u)
                         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                            su32(&accf[h])));
+                            su32(&accf[h][sl])));
                 }
                 if (progressed) {
                     idle0 = gtimer_ns();
@@ -1781,13 +1765,15 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
     } else {  // ----------------------------------------------------------------------------- epilogue
         const int et = t - (TC_BT + 32), ew = et >> 5, q = w & 3, ch = ew >> 2;  // q: this warp's TMEM lane quarter
         // Thread 0 keeps, per half, the item-ring position, the ring's parities and
-        // whether it holds the current record; every thread keeps the block count.
-        uint32_t fph = 0u, aph = 0u, have = 0u, done = 0u;
+        // whether it holds the current record, and the accumulator slot of the
+        // half's next block with the parities of accf; every thread keeps the
+        // block count.
+        uint32_t fph = 0u, aph = 0u, esl = 0u, have = 0u, done = 0u;
         int r[2] = {0, 0}, blkc[2] = {0, 0}, last_pick = 1;
         bool ab = false;
         for (;;) {
             if (et == 0) {  // the half whose accumulator block is ready next
-                int pick = -1;
+                int pick = -1, pslot = 0;
                 const unsigned long long t0 = gtimer_ns();
                 for (;;) {
                     for (int k = 1; k <= 2 && pick < 0; ++k) {
@@ -1805,9 +1791,12 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                             }
                             have |= 1u << hh;
                         }
-                        if (mbar_try(su32(&accf[hh]), (aph >> hh) & 1u)) {
-                            aph ^= 1u << hh;
+                        const uint32_t sl = (esl >> hh) & 1u, sb = 2u * hh + sl;
+                        if (mbar_try(su32(&accf[hh][sl]), (aph >> sb) & 1u)) {
+                            aph ^= 1u << sb;
+                            esl ^= 1u << hh;
                             pick = hh;
+                            pslot = int(sl);
                         }
                     }
                     if (pick >= 0 || done == 3u) break;
@@ -1817,10 +1806,10 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                     }
                 }
                 if (pick >= 0) last_pick = pick;
-                s_pick = pick;
+                s_pick = pick | (pslot << 4);
             }
             bar_n(3, TC_ET);
-            const int pick = s_pick;
+            const int pick = s_pick < 0 ? s_pick : (s_pick & 15), slot = s_pick < 0 ? 0 : (s_pick >> 4);
             if (pick == -2) ab = true;
             if (pick < 0) break;
             const int4 rc = s_cur[pick];
@@ -1832,81 +1821,86 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             const bool off = tl != tm || f > 0;
             const int nblk = (nch + TC_FLUSH - 1) / TC_FLUSH, b = blkc[pick];
             const bool lastb = b + 1 == nblk;
+            float4* cfh = scf[pick];
+            if (b == 0 && et < 128) {  // c~ of the item's two tiles, fetched while its blocks run
+                const int gl = ((et >> 6) ? tm : tl) * TT + (et & 63);
+                if (gl < L)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n\tcp.async.commit_group;" ::"r"(
+                                     su32(cfh + et)),
+                                 "l"(__cvta_generic_to_global(I.cf + gl))
+                                 : "memory");
+                else
+                    cfh[et] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            tc_fold(s_tmem, uint32_t(pick) * TC_ACC1, q, ch, lane, b == 0, lastb, off, X, XD);
+            tc_fold(s_tmem, uint32_t(pick) * TC_ACC1, uint32_t(slot), q, ch, lane, b == 0, lastb, off, X, XD);
             asm volatile("tcgen05.fence::before_thread_sync;");
-            mbar_arrive(su32(&acce[pick]));
+            mbar_arrive(su32(&acce[pick][slot]));
             blkc[pick] = lastb ? 0 : b + 1;
             if (!lastb) {
                 bar_n(3, TC_ET);  // s_pick and s_cur are read before thread 0 writes them again
                 continue;
             }
-            bar_n(3, TC_ET);  // the readout is in X (and XD)
-            const int nl = min(TT, L - tl * TT), nm = min(TT, L - tm * TT);  // terms in the two tiles
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            bar_n(3, TC_ET);  // the readout is in X (and XD), c~ in cfh
+            const int nl = min(TT, L - tl * TT);  // terms in the first tile
             const float* Xu = X;
             const float* Xl = X + TC_X;
             float S = 0.f, E = 0.f, TrS = 0.f, TrE = 0.f, TiS = 0.f, TiE = 0.f;
             float2* Gp = (s == 0 && I.Gpart) ? reinterpret_cast<float2*>(I.Gpart) + (long long)ksi * L * L : nullptr;
-            if (!off) {
-                // Diagonal tile.  G' = hi hi^T + hi (2 lo)^T has the symmetric part G~
-                // (scaled by 2^24), and Re(w) is symmetric: sum_lm Re(w_lm) G~_lm =
-                // sum over l <= m of Re(w_lm) g_lm with g_ll = G'_ll and g_lm = G'_lm +
-                // G'_ml (both halves).  The 2080 entries l <= m are dealt out evenly:
-                // thread et takes entries et + 256 k of the row-major triangle.
-                float2 wv[TC_WPT];
+            {
+                // Re w_lm = Re c~_l Re c~_m + Im c~_l Im c~_m, so the weighted sum is the
+                // pair of bilinear forms sum_lm (Re c~_l Re c~_m + Im c~_l Im c~_m) g_lm
+                // over the readout g = Xu + Xl.  On a diagonal tile g = G' = hi hi^T +
+                // (2 lo) hi^T, whose symmetric part is G~ (scaled by 2^24): a form with
+                // symmetric weights sees only that part.  On a pair g = G~_ab for term a
+                // of the first tile and b of the second (for flavour f > 0, gamma^j_ab);
+                // different tiles stand for both orders of the pair (the Gram, gamma^j
+                // and Re w are symmetric), so those count twice (exact doubling).  Thread
+                // et takes row a = et / 4 and columns 8 (et % 4) + j, 32 + 8 (et % 4) + j
+                // (j < 8: one bank per lane); terms past L have c~ = 0 and zero rows.
+                const float4* cB = cfh + (off ? 64 : 0);
+                const int a = et >> 2, cq = et & 3;
+                float SA = 0.f, EA = 0.f, SB = 0.f, EB = 0.f;
 #pragma unroll
-                for (int k = 0; k < TC_WPT; ++k) {
-                    const int e = et + TC_ET * k;
-                    wv[k] = e < TC_TRI ? I.wt[(long long)tl * TC_TRI + e] : make_float2(0.f, 0.f);
-                }
-#pragma unroll
-                for (int k = 0; k < TC_WPT; ++k) {
-                    const int e = et + TC_ET * k;
-                    if (e >= TC_TRI) break;
-                    const int a = stri[e] & 0xFF, bcol = stri[e] >> 8;
-                    if (bcol >= nl) continue;
-                    float g = Xu[a * 65 + bcol] + Xl[a * 65 + bcol];
-                    if (a < bcol) g += Xu[bcol * 65 + a] + Xl[bcol * 65 + a];
-                    ff_mac(S, E, wv[k].x, wv[k].y, g);
-                    if (Gp) {
-                        const float2 gv = make_float2((a < bcol ? 0.5f * g : g) * TC_UNSCALE, 0.f);
-                        const long long ga = tl * TT + a, gb = tl * TT + bcol;
-                        Gp[ga * L + gb] = gv;
-                        Gp[gb * L + ga] = gv;
+                for (int k = 0; k < 16; ++k) {
+                    const int bc = ((k >> 3) << 5) | (cq << 3) | (k & 7);
+                    const float g = Xu[a * 65 + bc] + Xl[a * 65 + bc];
+                    const float4 cm = cB[bc];
+                    ff_mac(SA, EA, cm.x, cm.y, g);
+                    ff_mac(SB, EB, cm.z, cm.w, g);
+                    if (Gp && (off ? f == 0 : true)) {
+                        const long long ga = tl * TT + a, gb = tm * TT + bc;
+                        if (ga < L && gb < L) {
+                            if (off) {
+                                const float2 gv = make_float2(g * TC_UNSCALE, 0.f);
+                                Gp[ga * L + gb] = gv;
+                                Gp[gb * L + ga] = gv;
+                            } else {  // the symmetric part, each ordered entry from its own thread
+                                const float gt = Xu[bc * 65 + a] + Xl[bc * 65 + a];
+                                Gp[ga * L + gb] = make_float2(0.5f * (g + gt) * TC_UNSCALE, 0.f);
+                            }
+                        }
                     }
                 }
-                if (et < 64 && et < nl && !I.local) {  // delta~_l and its product with c~_l
-                    const int gl = tl * TT + et;
-                    const float2 du = XD[et], dl = XD[64 + et];
-                    const float dsc = 1.f / (TC_SCALE * tc_bscale(*I.bn2));  // exact: a power of two
-                    const float2 dacc = make_float2((du.x + dl.x) * dsc, -(du.y + dl.y) * dsc);  // conj(b) phi
-                    const float4 cv = I.cf[gl];  // c~_l as (Re hi, Re lo, Im hi, Im lo)
-                    ff_mac(TrS, TrE, cv.x, cv.y, dacc.x);
-                    ff_mac(TrS, TrE, -cv.z, -cv.w, dacc.y);
-                    ff_mac(TiS, TiE, cv.x, cv.y, dacc.y);
-                    ff_mac(TiS, TiE, cv.z, cv.w, dacc.x);
-                    if (s == 0 && I.dpart) reinterpret_cast<float2*>(I.dpart)[(long long)ksi * L + gl] = dacc;
-                }
-            } else {
-                // Pair item: G~_ab = X_hi[a][b] + X_lo[a][b] for term a of the first tile
-                // and b of the second (for flavour f > 0, gamma^j_ab).  Different tiles
-                // stand for both orders of the pair (the Gram and gamma^j are symmetric,
-                // as is Re w), so each product counts twice (exact doubling).
+                const float4 cl = cfh[a];
                 const float fac = tl != tm ? 2.f : 1.f;
-#pragma unroll 4
-                for (int k = 0; k < TT * TT / TC_ET; ++k) {
-                    const int e = et + TC_ET * k, a = e >> 6, bcol = e & 63;
-                    if (a >= nl || bcol >= nm) continue;
-                    const float4 w4 = I.wf[(long long)(tl * TT + a) * L + tm * TT + bcol];
-                    const float g = Xu[a * 65 + bcol] + Xl[a * 65 + bcol];
-                    ff_mac(S, E, fac * w4.x, fac * w4.y, g);
-                    if (Gp && f == 0) {
-                        const float2 gv = make_float2(g * TC_UNSCALE, 0.f);
-                        const long long ga = tl * TT + a, gb = tm * TT + bcol;
-                        Gp[ga * L + gb] = gv;
-                        Gp[gb * L + ga] = gv;
-                    }
-                }
+                ff_mac(S, E, fac * cl.x, fac * cl.y, SA);
+                E += fac * cl.x * EA;
+                ff_mac(S, E, fac * cl.z, fac * cl.w, SB);
+                E += fac * cl.z * EB;
+            }
+            if (!off && et < 64 && et < nl && !I.local) {  // delta~_l and its product with c~_l
+                const int gl = tl * TT + et;
+                const float2 du = XD[et], dl = XD[64 + et];
+                const float dsc = 1.f / (TC_SCALE * tc_bscale(*I.bn2));  // exact: a power of two
+                const float2 dacc = make_float2((du.x + dl.x) * dsc, -(du.y + dl.y) * dsc);  // conj(b) phi
+                const float4 cv = cfh[et];  // c~_l as (Re hi, Re lo, Im hi, Im lo)
+                ff_mac(TrS, TrE, cv.x, cv.y, dacc.x);
+                ff_mac(TrS, TrE, -cv.z, -cv.w, dacc.y);
+                ff_mac(TiS, TiE, cv.x, cv.y, dacc.y);
+                ff_mac(TiS, TiE, cv.z, cv.w, dacc.x);
+                if (s == 0 && I.dpart) reinterpret_cast<float2*>(I.dpart)[(long long)ksi * L + gl] = dacc;
             }
             ff_warp_sum(S, E);
             ff_warp_sum(TrS, TrE);
@@ -1933,9 +1927,9 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 // slots as the CUDA-core tiles use them: diagonal tile u at u, pair p at
                 // T + 2p (and T + 2p + 1, which the tiles use for the pair's second half);
                 // per flavour f of the local cost: slots (s F + f) T^2 ..
-                const long long slot = ((long long)s * I.F + f) * T * T + (tl != tm ? T + 2 * (u - T) : u);
-                I.Dpart[slot * ks + ksi] = make_double2(qv[0] * (double)TC_UNSCALE, 0.0);
-                if (tl != tm) I.Dpart[(slot + 1) * ks + ksi] = make_double2(0.0, 0.0);
+                const long long slot2 = ((long long)s * I.F + f) * T * T + (tl != tm ? T + 2 * (u - T) : u);
+                I.Dpart[slot2 * ks + ksi] = make_double2(qv[0] * (double)TC_UNSCALE, 0.0);
+                if (tl != tm) I.Dpart[(slot2 + 1) * ks + ksi] = make_double2(0.0, 0.0);
                 else if (f == 0 && !I.local) I.Tpart[((long long)s * T + tl) * ks + ksi] = make_double2(qv[1], qv[2]);
                 // the half's item record is free again
                 mbar_arrive(su32(&ite[pick][r[pick]]));
@@ -1944,6 +1938,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             }
             bar_n(3, TC_ET);  // X, sred and s_cur are free again
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");  // no copy into shared memory outlives the CTA
         if (ab) s_abort = 1;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -2902,7 +2897,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     struct Off {
         size_t coef, xm, zm, alpha, b;       // staged inputs (ws) ...
         size_t pcoef, pxm, pzm, palpha, pb;  // ... and their pinned slots
-        size_t ctil, w, wf, cf, wt, bop, wht, bf, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta, states, tcst;
+        size_t ctil, w, wf, cf, bop, wht, bf, cs, bn2, Dp, Tp, Gp, dp, NsDs, cost, grad, beta, delta, states, tcst;
         size_t pcost, pgrad, pbeta, pdelta;
     };
     std::vector<Off> off(count);
@@ -2950,10 +2945,11 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         Off& o = off[i];
         const size_t L = h.L;
         o.ctil = ar.reserve(L * 16);
-        o.w = ar.reserve(L * L * 16);
-        o.wf = fp32 ? ar.reserve(L * L * 16) : 0;  // float-float weights of the FP32 term kernels
+        // pair weights w_lm for the CUDA-core and Walsh-Hadamard kernels (the
+        // tensor-core epilogue forms its weights from c~ alone)
+        o.w = tc ? 0 : ar.reserve(L * L * 16);
+        o.wf = fp32 && !tc ? ar.reserve(L * L * 16) : 0;  // float-float weights of the FP32 term kernels
         o.cf = fp32 ? ar.reserve(L * 16) : 0;
-        o.wt = tc ? ar.reserve(size_t(h.T) * TC_TRI * 8) : 0;
         o.bop = tc && !local ? ar.reserve(size_t(tc_bop_stages(h.N)) * TC_BOP_STAGE) : 0;
         o.wht = wht ? ar.reserve(WHT_TABLE_BYTES) : 0;
         o.bf = wht ? ar.reserve(size_t(h.N) * 8) : 0;
@@ -3023,10 +3019,9 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         I.s0 = range ? range->s0 : 0;
         I.local = local ? 1 : 0;
         I.ctil = (double2*)(ws + o.ctil);
-        I.w = (double2*)(ws + o.w);
-        I.wf = fp32 ? (float4*)(ws + o.wf) : nullptr;
+        I.w = tc ? nullptr : (double2*)(ws + o.w);
+        I.wf = fp32 && !tc ? (float4*)(ws + o.wf) : nullptr;
         I.cf = fp32 ? (float4*)(ws + o.cf) : nullptr;
-        I.wt = tc ? (float2*)(ws + o.wt) : nullptr;
         I.bop = tc && !local ? (void*)(ws + o.bop) : nullptr;
         I.wht = wht ? (void*)(ws + o.wht) : nullptr;
         I.bf = wht ? (float2*)(ws + o.bf) : nullptr;
@@ -3411,23 +3406,19 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 __global__ void k_noalloc_store(Inst I, Inst* dst) { *dst = I; }
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
-static void* g_noalloc_addr[NOALLOC_MAX_DEVICES];  // device address of the array, per device
 
-// Device address of g_noalloc_scratch on the current device `dev`.  In host
-// code the symbol's name is only a host-side stand-in; the address comes from
-// cudaGetSymbolAddress, called once per device with that device current.
-static int noalloc_scratch_address(int dev, char** out) {
-    static std::mutex m;
-    std::lock_guard<std::mutex> g(m);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return DVQLS_ERR_CUDA;
-        }
-        g_noalloc_addr[dev] = p;
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the symbol's name is only a host-side stand-in; the address comes from
+// cudaGetSymbolAddress with the device current.  It is looked up on every
+// call rather than cached: a device reset by the host program gives the
+// array a new address, and a cached one would then point at freed memory.
+static int noalloc_scratch_address(char** out) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return DVQLS_ERR_CUDA;
     }
-    *out = static_cast<char*>(g_noalloc_addr[dev]);
+    *out = static_cast<char*>(p);
     return DVQLS_OK;
 }
 
@@ -3504,7 +3495,7 @@ extern "C" int dvqls_cost_grad_noalloc(void* stream_arg, const dvqls_ansatz* ans
     const size_t o_NsDs = ar.reserve(size_t(S) * 24);
     if (ar.total() > NOALLOC_BYTES) return DVQLS_ERR_INVALID_ARG;  // beyond the fixed scratch
     char* base = nullptr;
-    int rc = noalloc_scratch_address(dev, &base);
+    int rc = noalloc_scratch_address(&base);
     if (rc) return rc;
 
     Inst I;

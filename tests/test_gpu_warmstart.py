@@ -91,34 +91,22 @@ def test_checkpoint_round_trip(dv, ctx, tmp_path):
 
 
 def test_learned_start_beats_fallback(dv, ctx):
-    """Reduced pipeline (n = 6..8).  Training targets: FP64 L-BFGS runs from
-    the perturbed |+> start carried to convergence (L-BFGS-B's default
-    stopping tests).  Held out: starting from the network's angles, Adam
-    reaches F_ref - 1e-4 (F_ref: the converged FP64 run from |+>) in fewer
-    iterations than from the zero start and starts closer, and FP64 L-BFGS
-    from it converges in fewer iterations than from |+>."""
-    rng = np.random.default_rng(3)
-    train = W.prepare(ctx, [(20_000 + k, int(rng.integers(6, 9))) for k in range(160)])
-    held = W.prepare(ctx, [(95_000 + k, 8) for k in range(16)])
-    res_tr, F_tr, _ = W.converged(ctx, train, [W.plus_start(p.n) for p in train])
-    assert all(r["stopped"] in ("gtol", "ftol", "ls") and r["iters"] > 0 for r in res_tr)
-    assert np.median([np.abs(r["grad"]).max() for r in res_tr]) <= 1e-2
-    X, Y, M = W.training_arrays(train, [r["alpha"] for r in res_tr])
-    ws, losses = W.train(ctx, X, Y, M, hidden=256, steps=1500, lr=2e-3, log_every=500)
-    assert losses[-1][1] < losses[0][1]
-    try:
-        a_mlp = W.predict(ws, held)
-    finally:
-        dv.dvqls_ws_destroy(ws)
-    res_plus, F_ref, _ = W.converged(ctx, held, [W.plus_start(p.n) for p in held])
-    target = F_ref - 1e-4
-    r_mlp, _, _ = W.optimize(ctx, held, a_mlp, max_iter=2000, target=target)
-    r_zero, _, _ = W.optimize(ctx, held, [np.zeros(p.P) for p in held], max_iter=2000, target=target)
-    it_mlp = np.array([r.iters if r.converged else 2000 for r in r_mlp])
-    it_zero = np.array([r.iters if r.converged else 2000 for r in r_zero])
-    assert sum(r.converged for r in r_mlp) >= sum(r.converged for r in r_zero)
-    assert np.median(it_mlp) < np.median(it_zero)
-    zero = [np.zeros(p.P) for p in held]
-    assert np.median(W.fidelities(ctx, held, a_mlp)) > np.median(W.fidelities(ctx, held, zero))
-    res_mlp, _, _ = W.converged(ctx, held, a_mlp)
-    assert np.median([r["iters"] for r in res_mlp]) < np.median([r["iters"] for r in res_plus])
+    """The warm-start pipeline at reduced size (200 training systems of n =
+    6..10, 20 held-out systems of n = 10).  Training targets: FP64 L-BFGS runs
+    from the perturbed |+> start carried to convergence (L-BFGS-B's default
+    stopping tests).  Held out, the network's angles start closer than the zero
+    start; Adam from them reaches F_ref - 1e-4 (F_ref: the converged FP64 run
+    from |+>) in at least three runs of four and in fewer iterations (median)
+    than from the zero start; FP64 L-BFGS from them converges in fewer
+    iterations (median) than from |+>."""
+    out = W.run(ctx, n_train=200, n_eval=20, max_iter=2000, train_steps=1500, n_deep=0, log=lambda *a: None)
+    tg = out["train"]["targets"]
+    assert sum(tg["stopped"].get(k, 0) for k in ("gtol", "ftol", "ls")) == tg["runs"] == 200
+    assert tg["grad_maxnorm_median"] <= 1e-2
+    loss = out["train"]["loss_curve"]
+    assert loss[-1][1] < loss[0][1]
+    mlp, zero, plus = (out["inits"][k] for k in ("mlp", "zero", "plus"))
+    assert mlp["initial_fidelity_median"] > zero["initial_fidelity_median"]
+    assert mlp["adam_to_reference"]["reached"] >= (3 * 20) // 4
+    assert mlp["adam_to_reference"]["iters_median"] < zero["adam_to_reference"]["iters_median"]
+    assert mlp["lbfgs_fp64"]["iters_median"] < plus["lbfgs_fp64"]["iters_median"]
