@@ -58,7 +58,7 @@ FP16_PER_BF16 = 1.0  # kind::f16 runs FP16 and BF16 operands at the same nominal
 # DRAM bytes (read + write) per launch of the tensor-core term kernel on the headline workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), with the SHA-256 (first 16 hex digits) of the
 # kernel sources it was taken on.  The figure is reported only while those sources are unchanged.
-TC_TRAFFIC = {"sources_sha16": "28a3d4d0b1516dd1", "bytes": 14436352 + 256}
+TC_TRAFFIC = {"sources_sha16": "c80376ba1a016844", "bytes": 13644800 + 0}
 TC_SOURCES = ("paper_2604_14435_gb300/csrc/terms.cu", "paper_2604_14435_gb300/csrc/state.cuh")
 
 
@@ -541,8 +541,8 @@ def main():
     ap.add_argument("--no-side-workloads", action="store_true",
                     help="headline only: skip the Hele-Shaw and uneven-batch records")
     ap.add_argument("--precision", default="fp32_tc", choices=["fp32", "fp32_tc"],
-                    help="term kernel: tcgen05 tensor cores with an FP32-accurate 3xFP16 split (served for "
-                         "L <= 64; default), or FP32 on the CUDA cores")
+                    help="term kernel: tcgen05 tensor cores with an FP32-accurate 3xFP16 split (64-term tiles "
+                         "and pairs of tiles, any L; default), or FP32 on the CUDA cores")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 200 if args.impl == "reference" else 2000

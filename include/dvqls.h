@@ -73,8 +73,9 @@ typedef enum {
  *                  folding), 64-term tiles and pairs of tiles for any L,
  *                  which keeps FP32-level accuracy (the FP32 bounds of the
  *                  parity tests hold).  Weighted sums in float-float (~2^-44
- *                  relative), combined in FP64.  Served for the global cost;
- *                  the local cost runs as DVQLS_FP32.
+ *                  relative), combined in FP64.  Served for the global
+ *                  and the local cost (flavour j of the local cost as the
+ *                  Gram of a tile against its strings with x ^ e_j).
  *   DVQLS_FP32_WHT: an exact reformulation of the same terms (not the
  *                  paper's per-term evaluation): the pairs (l, m) are
  *                  grouped by x_l ^ x_m and one FP32
