@@ -1169,6 +1169,17 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase) {
         : "memory");
     return done != 0;
 }
+// Non-blocking test of an mbarrier phase: for loops that poll several
+// barriers, where a blocking try_wait on one could hold up work on another.
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t phase) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    return done != 0;
+}
 __device__ __forceinline__ unsigned long long gtimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -1279,8 +1290,14 @@ __device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v) {
 // ones add to them with round-to-nearest adds; the last block goes to
 // X[part][row][col] and XD[part][row] in shared memory instead (part: lane
 // half).
+// With `toX` false the last block is not stored: each of its entries meets its
+// column weight c~_m (cB, float4 (Re hi, Re lo, Im hi, Im lo) per column) in
+// the float-float sums (SA, EA) = sum_m Re c~_m g_am and (SB, EB) =
+// sum_m Im c~_m g_am of this thread's row a, and the delta columns are
+// returned in dr.
 __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t hb, uint32_t slot, int q, int ch, int lane, bool first,
-                                        bool last, bool off, float* X, float2* XD) {
+                                        bool last, bool off, bool toX, float* X, float2* XD, const float4* cB,
+                                        float& SA, float& EA, float& SB, float& EB, float2& dr) {
     const uint32_t base = tmem + ((32u * uint32_t(q)) << 16), acc = hb + slot * TC_SLOT;
     const int xr = (q & 1) * 32 + lane;  // row within the lane half
     float* Xq = X + (q >> 1) * TC_X;
@@ -1294,9 +1311,16 @@ __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t hb, uint32_t slo
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] += u[j];
         }
-        if (last) {
+        if (last && toX) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) Xq[xr * 65 + 16 * g + j] = v[j];
+        } else if (last) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float4 cm = cB[16 * g + j];  // one address per warp: a broadcast
+                ff_mac(SA, EA, cm.x, cm.y, v[j]);
+                ff_mac(SB, EB, cm.z, cm.w, v[j]);
+            }
         } else {
             tmem_st16(base + hb + TC_SUM + 16 * g, v);
         }
@@ -1315,7 +1339,8 @@ __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t hb, uint32_t slo
             dv.x += du.x;
             dv.y += du.y;
         }
-        if (last) XD[(q >> 1) * 64 + xr] = dv;
+        if (last && toX) XD[(q >> 1) * 64 + xr] = dv;
+        else if (last) dr = dv;
         else tmem_st2(base + hb + TC_DSUM, dv);
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -1691,7 +1716,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 for (int h = 0; h < 2; ++h) {
                     if ((done >> h) & 1u) continue;
                     const int q = (nq >> h) & 1, st = 2 * h + q;
-                    if (!mbar_try(su32(&fullb[st]), (fph >> st) & 1u)) continue;
+                    if (!mbar_test(su32(&fullb[st]), (fph >> st) & 1u)) continue;
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const uint32_t hb = srec[st][0], fl = srec[st][1];
                     if (hb != TC_EXIT && (fl & 1u)) {
@@ -1699,7 +1724,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                         // (the block before last of this half); the other half meanwhile
                         const uint32_t sl = (nsl >> h) & 1u, sb = 2u * h + sl;
                         if ((aused >> sb) & 1u) {
-                            if (!mbar_try(su32(&acce[h][sl]), (aph >> sb) & 1u)) continue;
+                            if (!mbar_test(su32(&acce[h][sl]), (aph >> sb) & 1u)) continue;
                             aph ^= 1u << sb;
                             asm volatile("tcgen05.fence::after_thread_sync;");
                         }
@@ -1717,30 +1742,42 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                     const uint32_t sl = (csl >> h) & 1u;
                     const uint32_t lb = hb + TC_OPND_BYTES, tm = s_tmem + uint32_t(h) * TC_ACC1 + sl * TC_SLOT;
                     if (fl & 4u) {  // pair: [hi; lo] of the first tile against hi, then lo, of the second
+                        const uint64_t dA = tc_desc(hb), dB = tc_desc(lb);
+                        const uint32_t aLo = uint32_t(dA), aHi = uint32_t(dA >> 32), bLo = uint32_t(dB), bHi = uint32_t(dB >> 32);
+                        const uint32_t acc0 = (fl & 1u) ? 0u : 1u;
 #pragma unroll
                         for (int ksx = 0; ksx < TCK / 32; ++ksx) {
-                            const uint32_t acc0 = ((fl & 1u) && ksx == 0) ? 0u : 1u;
-                            const uint64_t da = tc_desc(hb + ksx * TC_KSTEP_BYTES);
+                            const uint32_t kofs = uint32_t(ksx * (TC_KSTEP_BYTES >> 4));
                             asm volatile(
-                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tm),
-                                "l"(da), "l"(tc_desc(lb + ksx * TC_KSTEP_BYTES)), "r"(tc_idesc(64)), "r"(acc0));
+                                "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+                                "mov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}\n" ::"r"(tm),
+                                "r"(aLo + kofs), "r"(aHi), "r"(bLo + kofs), "r"(bHi), "r"(tc_idesc(64)),
+                                "r"(ksx == 0 ? acc0 : 1u));
                             asm volatile(
-                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tm),
-                                "l"(da), "l"(tc_desc(lb + ksx * TC_KSTEP_BYTES + 8 * 256)), "r"(tc_idesc(64)),
-                                "r"(1u));
+                                "{\n\t.reg .b64 da, db;\n\t"
+                                "mov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, 1;\n\t}\n" ::"r"(tm),
+                                "r"(aLo + kofs), "r"(aHi), "r"(bLo + kofs + uint32_t((8 * 256) >> 4)), "r"(bHi),
+                                "r"(tc_idesc(64)));
                         }
                     } else {  // diagonal: A = [2 lo; hi] (row groups 0..15), B = [hi; b] (8..17)
+                        const uint64_t dA = tc_desc(hb), dB = tc_desc(hb + (TC_HIROW / 8) * 256);
+                        const uint32_t aLo = uint32_t(dA), aHi = uint32_t(dA >> 32), bLo = uint32_t(dB), bHi = uint32_t(dB >> 32);
+                        const uint32_t acc0 = (fl & 1u) ? 0u : 1u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+                            "mov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}\n" ::"r"(tm),
+                            "r"(aLo), "r"(aHi), "r"(bLo), "r"(bHi), "r"(tc_idesc(TC_ND)), "r"(acc0));
 #pragma unroll
-                        for (int ksx = 0; ksx < TCK / 16; ++ksx) {
-                            const uint32_t ka = hb + ksx * TC_KSTEP_BYTES;
-                            const uint32_t acc0 = ((fl & 1u) && ksx == 0) ? 0u : 1u;
+                        for (int ksx = 1; ksx < TCK / 16; ++ksx) {
                             asm volatile(
-                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tm),
-                                "l"(tc_desc(ka)), "l"(tc_desc(ka + (TC_HIROW / 8) * 256)), "r"(tc_idesc(TC_ND)),
-                                "r"(acc0));
+                                "{\n\t.reg .b64 da, db;\n\t"
+                                "mov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, 1;\n\t}\n" ::"r"(tm),
+                                "r"(aLo + uint32_t(ksx * (TC_KSTEP_BYTES >> 4))), "r"(aHi),
+                                "r"(bLo + uint32_t(ksx * (TC_KSTEP_BYTES >> 4))), "r"(bHi), "r"(tc_idesc(TC_ND)));
                         }
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -1781,7 +1818,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                         if ((done >> hh) & 1u) continue;
                         if (!((have >> hh) & 1u)) {
                             const uint32_t pb = hh * TC_NIT + r[hh];
-                            if (!mbar_try(su32(&itf[hh][r[hh]]), (fph >> pb) & 1u)) continue;
+                            if (!mbar_test(su32(&itf[hh][r[hh]]), (fph >> pb) & 1u)) continue;
                             fph ^= 1u << pb;
                             const int4 rc = irec[hh][r[hh]];
                             s_cur[hh] = rc;
@@ -1792,7 +1829,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                             have |= 1u << hh;
                         }
                         const uint32_t sl = (esl >> hh) & 1u, sb = 2u * hh + sl;
-                        if (mbar_try(su32(&accf[hh][sl]), (aph >> sb) & 1u)) {
+                        if (mbar_test(su32(&accf[hh][sl]), (aph >> sb) & 1u)) {
                             aph ^= 1u << sb;
                             esl ^= 1u << hh;
                             pick = hh;
@@ -1832,8 +1869,19 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 else
                     cfh[et] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
+            // The beta / delta outputs of shift 0 need the two quadrants added entry by entry:
+            // that item's last block goes through shared memory (X, XD); every other item's last
+            // block is weighted in the fold, straight from the tensor-memory loads.
+            const bool toX = s == 0 && (I.Gpart || I.dpart);
+            if (lastb && !toX) {
+                asm volatile("cp.async.wait_all;" ::: "memory");
+                bar_n(3, TC_ET);  // c~ of the item's tiles is in cfh
+            }
+            float SA = 0.f, EA = 0.f, SB = 0.f, EB = 0.f;
+            float2 dr = make_float2(0.f, 0.f);
             asm volatile("tcgen05.fence::after_thread_sync;");
-            tc_fold(s_tmem, uint32_t(pick) * TC_ACC1, uint32_t(slot), q, ch, lane, b == 0, lastb, off, X, XD);
+            tc_fold(s_tmem, uint32_t(pick) * TC_ACC1, uint32_t(slot), q, ch, lane, b == 0, lastb, off, toX, X, XD,
+                    cfh + (off ? 64 : 0), SA, EA, SB, EB, dr);
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(su32(&acce[pick][slot]));
             blkc[pick] = lastb ? 0 : b + 1;
@@ -1841,14 +1889,36 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 bar_n(3, TC_ET);  // s_pick and s_cur are read before thread 0 writes them again
                 continue;
             }
-            asm volatile("cp.async.wait_all;" ::: "memory");
-            bar_n(3, TC_ET);  // the readout is in X (and XD), c~ in cfh
+            if (toX) {
+                asm volatile("cp.async.wait_all;" ::: "memory");
+                bar_n(3, TC_ET);  // the readout is in X (and XD), c~ in cfh
+            }
             const int nl = min(TT, L - tl * TT);  // terms in the first tile
             const float* Xu = X;
             const float* Xl = X + TC_X;
             float S = 0.f, E = 0.f, TrS = 0.f, TrE = 0.f, TiS = 0.f, TiE = 0.f;
             float2* Gp = (s == 0 && I.Gpart) ? reinterpret_cast<float2*>(I.Gpart) + (long long)ksi * L * L : nullptr;
-            {
+            if (!toX) {
+                // Row a of this thread's quadrant (2 lo or hi rows of a diagonal tile, hi or lo rows
+                // of a pair's first tile): the two quadrants of a row hold two parts of the same
+                // entries, so each adds its own share of sum_am Re w_am g_am, with
+                // Re w_am = Re c~_a Re c~_m + Im c~_a Im c~_m (terms past L: c~ = 0, zero rows).
+                const int a = (q & 1) * 32 + lane;
+                const float4 cl = cfh[a];
+                const float fac = tl != tm ? 2.f : 1.f;
+                ff_mac(S, E, fac * cl.x, fac * cl.y, SA);
+                E += fac * cl.x * EA;
+                ff_mac(S, E, fac * cl.z, fac * cl.w, SB);
+                E += fac * cl.z * EB;
+                if (!off && ch == 0 && a < nl && !I.local) {  // this quadrant's part of delta~_a
+                    const float dsc = 1.f / (TC_SCALE * tc_bscale(*I.bn2));  // exact: a power of two
+                    const float2 dacc = make_float2(dr.x * dsc, -dr.y * dsc);  // conj(b) phi
+                    ff_mac(TrS, TrE, cl.x, cl.y, dacc.x);
+                    ff_mac(TrS, TrE, -cl.z, -cl.w, dacc.y);
+                    ff_mac(TiS, TiE, cl.x, cl.y, dacc.y);
+                    ff_mac(TiS, TiE, cl.z, cl.w, dacc.x);
+                }
+            } else {
                 // Re w_lm = Re c~_l Re c~_m + Im c~_l Im c~_m, so the weighted sum is the
                 // pair of bilinear forms sum_lm (Re c~_l Re c~_m + Im c~_l Im c~_m) g_lm
                 // over the readout g = Xu + Xl.  On a diagonal tile g = G' = hi hi^T +
@@ -1890,7 +1960,7 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 ff_mac(S, E, fac * cl.z, fac * cl.w, SB);
                 E += fac * cl.z * EB;
             }
-            if (!off && et < 64 && et < nl && !I.local) {  // delta~_l and its product with c~_l
+            if (toX && !off && et < 64 && et < nl && !I.local) {  // delta~_l and its product with c~_l
                 const int gl = tl * TT + et;
                 const float2 du = XD[et], dl = XD[64 + et];
                 const float dsc = 1.f / (TC_SCALE * tc_bscale(*I.bn2));  // exact: a power of two
