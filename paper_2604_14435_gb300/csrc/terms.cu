@@ -1314,6 +1314,16 @@ __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t hb, uint32_t slo
         if (last && toX) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) Xq[xr * 65 + 16 * g + j] = v[j];
+        } else if (last && (off ? q >= 2 : q < 2)) {
+            // the correction quadrant (2 lo hi^T of a diagonal tile, or the lo rows of a pair's
+            // first tile) is ~2^-10 of the main one: FP32 products and sums leave its rounding
+            // near 2^-34 of the weighted sum
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float4 cm = cB[16 * g + j];  // one address per warp: a broadcast
+                SA = fmaf(cm.x, v[j], SA);
+                SB = fmaf(cm.z, v[j], SB);
+            }
         } else if (last) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
