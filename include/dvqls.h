@@ -243,8 +243,9 @@ typedef struct {
  * results are in place.
  * Launch: the first call of a problem signature (precision and every
  * instance's n, depth, L) times each split of the amplitude range among the
- * candidates 1, 2, 4, 8 on the real inputs and keeps the fastest for the
- * context (an autotuner; that call is synchronous).  The kernel sequence of a
+ * candidates 1, 2, 4, 8 on the real inputs (the fastest of three passes per
+ * candidate) and keeps the fastest for the context (an autotuner; that call
+ * is synchronous).  The kernel sequence of a
  * pass is captured once as a CUDA graph and replayed while the instance
  * table (shapes and pointers) is unchanged; with profiling enabled, or when
  * the caller is capturing the stream, kernels are launched directly. */

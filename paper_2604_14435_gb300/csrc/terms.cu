@@ -644,61 +644,83 @@ __global__ void __launch_bounds__(256) k_hbm_lo(const Inst* __restrict__ insts, 
         reinterpret_cast<uint4*>(st)[e4] = reinterpret_cast<const uint4*>(w)[e4];
 }
 
-// The same low-qubit pass for FP32 states with the chunk in registers (16
-// amplitudes per thread, as in the on-chip state builder): qubits 0..4 on
-// lane bits (shuffles) and 8..11 on register bits (in place); qubits 5..7 sit
-// on warp bits and are rotated after one padded, conflict-free transpose that
-// puts them on lanes.  A second transpose restores the coalesced order for the
-// store.  Three barriers per chunk instead of one per qubit.
+// The same low-qubit pass for FP32 states with the chunk in registers, 16
+// amplitudes per thread, every Ry on register bits (no shuffles): the chunk is
+// read with each thread holding 16 consecutive amplitudes (qubits 0..3 on its
+// register bits, four 16-byte loads), then two transposes through shared
+// memory put qubits 4..7 and then 8..11 on the register bits; the last layout
+// stores 128 contiguous bytes per warp and register.  The CZ-ring signs come
+// from the thread's part of the index and the register's (the ring's pairs
+// split into those within each part, the pair across bits 3 and 4 and the
+// wrap-around pair).  Amplitude e sits at word e + 4 (e >> 5) + 16 (e >> 8), so
+// both transposes read and write without bank conflicts (the 16-byte stores of
+// eight consecutive threads, 64 bytes apart, fall in eight different bank
+// groups; the two half-warps of a 256-strided read sit 16 banks apart).
+__device__ __forceinline__ int lo_pad(int e) { return e + ((e >> 5) << 2) + ((e >> 8) << 4); }
+__device__ __forceinline__ void ry_regs(float (&v)[16], int kb, float c, float sn) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+        if (!((r >> kb) & 1)) {
+            const float a0 = v[r], a1 = v[r | (1 << kb)];
+            v[r] = c * a0 - sn * a1;
+            v[r | (1 << kb)] = sn * a0 + c * a1;
+        }
+}
 __global__ void __launch_bounds__(256) k_hbm_lo_regs(const Inst* __restrict__ insts, int idx, int layer) {
-    __shared__ float scr[LOC + LOC / 32];
+    constexpr int PADW = LOC + (LOC >> 5) * 4 + (LOC >> 8) * 16;
+    __shared__ __align__(16) float scr[2][PADW];
     __shared__ float cq[LOQ], sq[LOQ];
     const Inst& I = insts[idx];
-    const int s = blockIdx.y, n = I.n, base = blockIdx.x << LOQ, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int s = blockIdx.y, n = I.n, base = blockIdx.x << LOQ, t = threadIdx.x;
     const size_t N = size_t(1) << n;
     if (t < LOQ) shift_angle<float>(I, s, layer * n + t, cq[t], sq[t]);
     float* st = reinterpret_cast<float*>(I.states) + s * N + base;
     float v[16];
+    // layout A: amplitude 16 t + r
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = st[st_index(0, r, w, lane)];  // a warp reads 128 contiguous bytes per r
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 16; ++r)
-        if (czring_parity(base + st_index(0, r, w, lane), n)) v[r] = -v[r];
-#pragma unroll
-    for (int b = 0; b < 5; ++b) {  // qubits 0..4: lane bits
-        const float c = cq[b], sn = sq[b];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = ry_lane(v[r], lane, b, c, sn);
+    for (int c = 0; c < 4; ++c) {
+        const float4 x = reinterpret_cast<const float4*>(st)[4 * t + c];
+        v[4 * c + 0] = x.x;
+        v[4 * c + 1] = x.y;
+        v[4 * c + 2] = x.z;
+        v[4 * c + 3] = x.w;
     }
+    {
+        // CZ ring: parity of popc(i & (i >> 1)) over bits 0..n-2, plus bit n-1 times bit 0, for
+        // i = base | 16 t | r: the thread's part, the pairs inside r, the pair (3, 4) and the wrap.
+        const int pt = czring_parity(base | (t << 4), n);
+        const int t0 = t & 1, bn1 = (base >> (n - 1)) & 1;
 #pragma unroll
-    for (int kb = 0; kb < 4; ++kb) {  // qubits 8..11: register bits
-        const float c = cq[8 + kb], sn = sq[8 + kb];
-#pragma unroll
-        for (int r = 0; r < 16; ++r)
-            if (!((r >> kb) & 1)) {
-                const float a0 = v[r], a1 = v[r | (1 << kb)];
-                v[r] = c * a0 - sn * a1;
-                v[r | (1 << kb)] = sn * a0 + c * a1;
-            }
+        for (int r = 0; r < 16; ++r) {
+            int p = pt ^ (__popc(r & (r >> 1)) & 1);
+            if (r & 8) p ^= t0;
+            if (r & 1) p ^= bn1;
+            v[r] = __int_as_float(__float_as_int(v[r]) ^ (p << 31));
+        }
     }
+    __syncthreads();  // the angles
 #pragma unroll
-    for (int r = 0; r < 16; ++r) scr[st_pad(st_index(0, r, w, lane))] = v[r];
+    for (int kb = 0; kb < 4; ++kb) ry_regs(v, kb, cq[kb], sq[kb]);  // qubits 0..3
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        *reinterpret_cast<float4*>(&scr[0][lo_pad(16 * t + 4 * c)]) = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
     __syncthreads();
+    // layout B: amplitude (t & 15) | 16 r | 256 (t >> 4)
+    const int eb = (t & 15) | ((t >> 4) << 8);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = scr[st_pad(st_index(1, r, w, lane))];
+    for (int r = 0; r < 16; ++r) v[r] = scr[0][lo_pad(eb | (r << 4))];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {  // qubits 5..7: lane bits 2..4 of the second mapping
-        const float c = cq[5 + j], sn = sq[5 + j];
+    for (int kb = 0; kb < 4; ++kb) ry_regs(v, kb, cq[4 + kb], sq[4 + kb]);  // qubits 4..7
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = ry_lane(v[r], lane, 2 + j, c, sn);
-    }
-    __syncthreads();  // every read of the first layout is done
-#pragma unroll
-    for (int r = 0; r < 16; ++r) scr[st_pad(st_index(1, r, w, lane))] = v[r];
+    for (int r = 0; r < 16; ++r) scr[1][lo_pad(eb | (r << 4))] = v[r];
     __syncthreads();
+    // layout C: amplitude t | 256 r
 #pragma unroll
-    for (int r = 0; r < 16; ++r) st[st_index(0, r, w, lane)] = scr[st_pad(st_index(0, r, w, lane))];
+    for (int r = 0; r < 16; ++r) v[r] = scr[1][lo_pad(t | (r << 8))];
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb) ry_regs(v, kb, cq[8 + kb], sq[8 + kb]);  // qubits 8..11
+#pragma unroll
+    for (int r = 0; r < 16; ++r) st[t | (r << 8)] = v[r];
 }
 
 template <typename R>
@@ -951,8 +973,10 @@ inline size_t tc_psi_region(int nmax_smem, int copy_nmax) {
     }
     return (psi + 1023) & ~size_t(1023);
 }
-inline size_t tc_smem_bytes(int nmax_smem, int copy_nmax) {  // a state region for each builder half
-    return 1024 + (size_t)TC_NSTG * TC_STAGE_BYTES + 2 * tc_psi_region(nmax_smem, copy_nmax) + TC_EPI_BYTES;
+// A state region for each builder half; the shared-memory readout of the
+// epilogue only for passes that return beta or delta (no other item touches it).
+inline size_t tc_smem_bytes(int nmax_smem, int copy_nmax, bool readout) {
+    return 1024 + (size_t)TC_NSTG * TC_STAGE_BYTES + 2 * tc_psi_region(nmax_smem, copy_nmax) + (readout ? TC_EPI_BYTES : 0);
 }
 // Stages of the b rows of an instance with 2^n amplitudes.
 __host__ __device__ inline long long tc_bop_stages(long long N) { return (N + TCK - 1) / TCK; }
@@ -1297,7 +1321,7 @@ __device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v) {
 // returned in dr.
 __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t hb, uint32_t slot, int q, int ch, int lane, bool first,
                                         bool last, bool off, bool toX, float* X, float2* XD, const float4* cB,
-                                        float& SA, float& EA, float& SB, float& EB, float2& dr) {
+                                        float& SA, float& EA, float& SB, float& EB, float2& dr, bool imz) {
     const uint32_t base = tmem + ((32u * uint32_t(q)) << 16), acc = hb + slot * TC_SLOT;
     const int xr = (q & 1) * 32 + lane;  // row within the lane half
     float* Xq = X + (q >> 1) * TC_X;
@@ -1322,8 +1346,11 @@ __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t hb, uint32_t slo
             for (int j = 0; j < 16; ++j) {
                 const float4 cm = cB[16 * g + j];  // one address per warp: a broadcast
                 SA = fmaf(cm.x, v[j], SA);
-                SB = fmaf(cm.z, v[j], SB);
+                if (!imz) SB = fmaf(cm.z, v[j], SB);
             }
+        } else if (last && imz) {  // every Im c~_m of the columns is zero: the second form is zero
+#pragma unroll
+            for (int j = 0; j < 16; ++j) ff_mac(SA, EA, cB[16 * g + j].x, cB[16 * g + j].y, v[j]);
         } else if (last) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -1471,6 +1498,8 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         const uint32_t a = su32(smem_raw);
         base = smem_raw + ((1024u - (a & 1023u)) & 1023u);
     }
+    // The readout (X, XD) is allocated only when the pass returns beta or delta; only
+    // shift-0 items of such a pass touch it.
     float* X = reinterpret_cast<float*>(base + TC_NSTG * TC_STAGE_BYTES + 2 * psi_half);
     float2* XD = reinterpret_cast<float2*>(X + 2 * TC_X);
     if (t == 0) {
@@ -1883,15 +1912,18 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
             // that item's last block goes through shared memory (X, XD); every other item's last
             // block is weighted in the fold, straight from the tensor-memory loads.
             const bool toX = s == 0 && (I.Gpart || I.dpart);
+            bool imz = false;  // the column weights c~_m of the item are all real (a real A gives real c~)
             if (lastb && !toX) {
                 asm volatile("cp.async.wait_all;" ::: "memory");
                 bar_n(3, TC_ET);  // c~ of the item's tiles is in cfh
+                const float4 c0 = cfh[(off ? 64 : 0) + lane], c1 = cfh[(off ? 64 : 0) + 32 + lane];
+                imz = __all_sync(0xffffffffu, c0.z == 0.f && c0.w == 0.f && c1.z == 0.f && c1.w == 0.f);
             }
             float SA = 0.f, EA = 0.f, SB = 0.f, EB = 0.f;
             float2 dr = make_float2(0.f, 0.f);
             asm volatile("tcgen05.fence::after_thread_sync;");
             tc_fold(s_tmem, uint32_t(pick) * TC_ACC1, uint32_t(slot), q, ch, lane, b == 0, lastb, off, toX, X, XD,
-                    cfh + (off ? 64 : 0), SA, EA, SB, EB, dr);
+                    cfh + (off ? 64 : 0), SA, EA, SB, EB, dr, imz);
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(su32(&acce[pick][slot]));
             blkc[pick] = lastb ? 0 : b + 1;
@@ -2917,6 +2949,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     for (const auto& h : hi) wht = wht && h.T == 1 && h.n <= WHT_MAXN;
     bool tc = !wht && (precision == DVQLS_FP32_TC || (precision == DVQLS_FP32_WHT && !local));
     int copy_nmax = 0;
+    const bool readout = beta_out || delta_out;
     // the tensor-core kernel's shared state region: the largest on-chip state, and
     // a staged block of HBM_K amplitudes when some state lives in HBM
     bool any_hbm = false;
@@ -2927,9 +2960,9 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         cudaFuncAttributes fa;
         DVQLS_CUDA_TRY(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
         DVQLS_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, (const void*)k_terms_tc));
-        tc = tc_smem_bytes(tc_nsm, 0) + fa.sharedSizeBytes <= (size_t)optin;
+        tc = tc_smem_bytes(tc_nsm, 0, readout) + fa.sharedSizeBytes <= (size_t)optin;
         for (int c = TC_COPY_NMAX; tc && tc_nsm > 0 && c >= 4 && !copy_nmax; --c)
-            if (tc_smem_bytes(tc_nsm, c) + fa.sharedSizeBytes <= (size_t)optin) copy_nmax = c;
+            if (tc_smem_bytes(tc_nsm, c, readout) + fa.sharedSizeBytes <= (size_t)optin) copy_nmax = c;
     }
     // The tensor-core pass builds the on-chip states in a kernel of its own.
     int st_grid = 0;
@@ -2942,7 +2975,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
             }
     if (st_grid > 0) DVQLS_CUDA_TRY(ctx, allow_dynamic_smem((const void*)k_tc_states));
     const size_t smem = wht  ? wht_smem_bytes(Pmax)
-                        : tc ? tc_smem_bytes(tc_nsm, copy_nmax)
+                        : tc ? tc_smem_bytes(tc_nsm, copy_nmax, readout)
                         : fp32 ? smem_bytes<float>(nmax, Pmax) : smem_bytes<double>(nmax, Pmax);
     const size_t r2 = fp32 ? 8 : 16;
     auto kfun = wht ? (const void*)k_terms_wht
@@ -3190,23 +3223,31 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         DVQLS_CUDA_TRY(ctx, cudaEventCreate(&e0));
         DVQLS_CUDA_TRY(ctx, cudaEventCreate(&e1));
         float best = 0.f;
+        // Each candidate runs TUNE_REPS passes back to back and keeps the fastest: the
+        // first pass of a candidate (and of the whole call) also pays one-time costs
+        // (cold caches, first launches) that a single timing would charge to it.
+        constexpr int TUNE_REPS = 3;
         for (int c : cands) {
             build_table(c, ps);
             rc = upload();
-            if (!rc) rc = (cudaEventRecord(e0, ctx->stream) == cudaSuccess) ? DVQLS_OK : DVQLS_ERR_CUDA;
-            if (!rc) rc = launch_pass(ctx, ctx->stream, dtable, ps, tab, false);
-            if (!rc) rc = (cudaEventRecord(e1, ctx->stream) == cudaSuccess) ? DVQLS_OK : DVQLS_ERR_CUDA;
-            if (!rc) rc = (cudaEventSynchronize(e1) == cudaSuccess) ? DVQLS_OK : DVQLS_ERR_CUDA;
-            float ms = 0.f;
-            if (!rc) rc = (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ? DVQLS_OK : DVQLS_ERR_CUDA;
+            float cbest = 0.f;
+            for (int rep = 0; rep < TUNE_REPS && !rc; ++rep) {
+                rc = (cudaEventRecord(e0, ctx->stream) == cudaSuccess) ? DVQLS_OK : DVQLS_ERR_CUDA;
+                if (!rc) rc = launch_pass(ctx, ctx->stream, dtable, ps, tab, false);
+                if (!rc) rc = (cudaEventRecord(e1, ctx->stream) == cudaSuccess) ? DVQLS_OK : DVQLS_ERR_CUDA;
+                if (!rc) rc = (cudaEventSynchronize(e1) == cudaSuccess) ? DVQLS_OK : DVQLS_ERR_CUDA;
+                float ms = 0.f;
+                if (!rc) rc = (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ? DVQLS_OK : DVQLS_ERR_CUDA;
+                if (!rc && (rep == 0 || ms < cbest)) cbest = ms;
+            }
             if (rc) {
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
                 cudaGetLastError();
                 return rc == DVQLS_ERR_CUDA ? set_error(ctx, rc, "autotune pass failed") : rc;
             }
-            if (c == cands[0] || ms < best) {
-                best = ms;
+            if (c == cands[0] || cbest < best) {
+                best = cbest;
                 ks_use = c;
             }
         }
