@@ -230,6 +230,52 @@ __device__ __forceinline__ int st_index(int M, int r, int w, int lane) {
 }
 __device__ __forceinline__ int st_pad(int i) { return i + (i >> 5); }
 
+// Ry(theta) on a register bit in scaled form.  With c = cos(theta/2) and
+// s = sin(theta/2), Ry = c [[1, -t], [t, 1]] (t = s/c) when |c| >= |s|, else
+// s [[u, -1], [1, u]] (u = c/s): the bracketed matrix takes one FMA per
+// amplitude (two per pair instead of four), and the factor (c or s) is
+// applied once for all the rotations of a pass.  |t|, |u| <= 1 keeps every
+// step as well conditioned as the plain rotation.
+struct RyScaled {
+    float r, fac;
+    int sform;
+};
+__device__ __forceinline__ RyScaled ry_scaled(float c, float s) {
+    RyScaled q;
+    if (fabsf(c) >= fabsf(s)) {
+        q.r = s / c;
+        q.fac = c;
+        q.sform = 0;
+    } else {
+        q.r = c / s;
+        q.fac = s;
+        q.sform = 1;
+    }
+    return q;
+}
+// The bracketed matrix on register bit kb (a compile-time constant in the
+// unrolled callers) of the A amplitudes v.
+template <int A>
+__device__ __forceinline__ void ry_regs_scaled(float (&v)[A], int kb, float r, int sform) {
+    if (sform) {
+#pragma unroll
+        for (int i = 0; i < A; ++i)
+            if (!((i >> kb) & 1)) {
+                const float a0 = v[i], a1 = v[i | (1 << kb)];
+                v[i] = fmaf(r, a0, -a1);
+                v[i | (1 << kb)] = fmaf(r, a1, a0);
+            }
+    } else {
+#pragma unroll
+        for (int i = 0; i < A; ++i)
+            if (!((i >> kb) & 1)) {
+                const float a0 = v[i], a1 = v[i | (1 << kb)];
+                v[i] = fmaf(-r, a1, a0);
+                v[i | (1 << kb)] = fmaf(r, a0, a1);
+            }
+    }
+}
+
 // Ry(theta) on the qubit of lane bit b: v' = c v -+ s v_partner.
 __device__ __forceinline__ float ry_lane(float v, int lane, int b, float c, float s) {
     const float p = __shfl_xor_sync(0xffffffffu, v, 1 << b);

@@ -657,23 +657,22 @@ __global__ void __launch_bounds__(256) k_hbm_lo(const Inst* __restrict__ insts, 
 // eight consecutive threads, 64 bytes apart, fall in eight different bank
 // groups; the two half-warps of a 256-strided read sit 16 banks apart).
 __device__ __forceinline__ int lo_pad(int e) { return e + ((e >> 5) << 2) + ((e >> 8) << 4); }
-__device__ __forceinline__ void ry_regs(float (&v)[16], int kb, float c, float sn) {
-#pragma unroll
-    for (int r = 0; r < 16; ++r)
-        if (!((r >> kb) & 1)) {
-            const float a0 = v[r], a1 = v[r | (1 << kb)];
-            v[r] = c * a0 - sn * a1;
-            v[r | (1 << kb)] = sn * a0 + c * a1;
-        }
-}
 __global__ void __launch_bounds__(256) k_hbm_lo_regs(const Inst* __restrict__ insts, int idx, int layer) {
     constexpr int PADW = LOC + (LOC >> 5) * 4 + (LOC >> 8) * 16;
     __shared__ __align__(16) float scr[2][PADW];
-    __shared__ float cq[LOQ], sq[LOQ];
+    __shared__ float rq[LOQ], fq[LOQ];
+    __shared__ int sfq[LOQ];
     const Inst& I = insts[idx];
     const int s = blockIdx.y, n = I.n, base = blockIdx.x << LOQ, t = threadIdx.x;
     const size_t N = size_t(1) << n;
-    if (t < LOQ) shift_angle<float>(I, s, layer * n + t, cq[t], sq[t]);
+    if (t < LOQ) {  // the rotations in scaled form; their factors are applied at the store
+        float c, sn;
+        shift_angle<float>(I, s, layer * n + t, c, sn);
+        const RyScaled q = ry_scaled(c, sn);
+        rq[t] = q.r;
+        fq[t] = q.fac;
+        sfq[t] = q.sform;
+    }
     float* st = reinterpret_cast<float*>(I.states) + s * N + base;
     float v[16];
     // layout A: amplitude 16 t + r
@@ -700,7 +699,7 @@ __global__ void __launch_bounds__(256) k_hbm_lo_regs(const Inst* __restrict__ in
     }
     __syncthreads();  // the angles
 #pragma unroll
-    for (int kb = 0; kb < 4; ++kb) ry_regs(v, kb, cq[kb], sq[kb]);  // qubits 0..3
+    for (int kb = 0; kb < 4; ++kb) ry_regs_scaled<16>(v, kb, rq[kb], sfq[kb]);  // qubits 0..3
 #pragma unroll
     for (int c = 0; c < 4; ++c)
         *reinterpret_cast<float4*>(&scr[0][lo_pad(16 * t + 4 * c)]) = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
@@ -710,7 +709,7 @@ __global__ void __launch_bounds__(256) k_hbm_lo_regs(const Inst* __restrict__ in
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = scr[0][lo_pad(eb | (r << 4))];
 #pragma unroll
-    for (int kb = 0; kb < 4; ++kb) ry_regs(v, kb, cq[4 + kb], sq[4 + kb]);  // qubits 4..7
+    for (int kb = 0; kb < 4; ++kb) ry_regs_scaled<16>(v, kb, rq[4 + kb], sfq[4 + kb]);  // qubits 4..7
 #pragma unroll
     for (int r = 0; r < 16; ++r) scr[1][lo_pad(eb | (r << 4))] = v[r];
     __syncthreads();
@@ -718,9 +717,12 @@ __global__ void __launch_bounds__(256) k_hbm_lo_regs(const Inst* __restrict__ in
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = scr[1][lo_pad(t | (r << 8))];
 #pragma unroll
-    for (int kb = 0; kb < 4; ++kb) ry_regs(v, kb, cq[8 + kb], sq[8 + kb]);  // qubits 8..11
+    for (int kb = 0; kb < 4; ++kb) ry_regs_scaled<16>(v, kb, rq[8 + kb], sfq[8 + kb]);  // qubits 8..11
+    float fac = 1.f;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) st[t | (r << 8)] = v[r];
+    for (int q = 0; q < LOQ; ++q) fac *= fq[q];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) st[t | (r << 8)] = v[r] * fac;
 }
 
 template <typename R>
@@ -770,45 +772,40 @@ template <int LOGH>
 __global__ void __launch_bounds__(256) k_hbm_hi_regs(const Inst* __restrict__ insts, int idx, int layer) {
     constexpr int H = 1 << LOGH, RG = H / 8;
     __shared__ float scr[H * 33];
-    __shared__ float cq[LOGH], sq[LOGH];
+    __shared__ float rq[LOGH], fq[LOGH];
+    __shared__ int sfq[LOGH];
     const Inst& I = insts[idx];
     const int s = blockIdx.y, n = I.n, lo0 = blockIdx.x * 32, t = threadIdx.x, lane = t & 31, w = t >> 5;
     const size_t N = size_t(1) << n;
-    if (t < LOGH) shift_angle<float>(I, s, layer * n + LOQ + t, cq[t], sq[t]);
+    if (t < LOGH) {  // the rotations in scaled form; their factors are applied at the store
+        float c, sn;
+        shift_angle<float>(I, s, layer * n + LOQ + t, c, sn);
+        const RyScaled q = ry_scaled(c, sn);
+        rq[t] = q.r;
+        fq[t] = q.fac;
+        sfq[t] = q.sform;
+    }
     float* st = reinterpret_cast<float*>(I.states) + s * N + lo0 + lane;
     float v[RG];
 #pragma unroll
     for (int r = 0; r < RG; ++r) v[r] = st[(size_t)((r << 3) | w) << LOQ];
     __syncthreads();
 #pragma unroll
-    for (int kb = 0; kb < LOGH - 3; ++kb) {  // h bit 3 + kb: qubit 15 + kb, register bit kb
-        const float c = cq[3 + kb], sn = sq[3 + kb];
-#pragma unroll
-        for (int r = 0; r < RG; ++r)
-            if (!((r >> kb) & 1)) {
-                const float a0 = v[r], a1 = v[r | (1 << kb)];
-                v[r] = c * a0 - sn * a1;
-                v[r | (1 << kb)] = sn * a0 + c * a1;
-            }
-    }
+    for (int kb = 0; kb < LOGH - 3; ++kb)  // h bit 3 + kb: qubit 15 + kb, register bit kb
+        ry_regs_scaled<RG>(v, kb, rq[3 + kb], sfq[3 + kb]);
 #pragma unroll
     for (int r = 0; r < RG; ++r) scr[((r << 3) | w) * 33 + lane] = v[r];
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RG; ++r) v[r] = scr[((w << (LOGH - 3)) | r) * 33 + lane];
 #pragma unroll
-    for (int kb = 0; kb < 3; ++kb) {  // h bit kb: qubit 12 + kb, register bit kb
-        const float c = cq[kb], sn = sq[kb];
+    for (int kb = 0; kb < 3; ++kb)  // h bit kb: qubit 12 + kb, register bit kb
+        ry_regs_scaled<RG>(v, kb, rq[kb], sfq[kb]);
+    float fac = 1.f;
 #pragma unroll
-        for (int r = 0; r < RG; ++r)
-            if (!((r >> kb) & 1)) {
-                const float a0 = v[r], a1 = v[r | (1 << kb)];
-                v[r] = c * a0 - sn * a1;
-                v[r | (1 << kb)] = sn * a0 + c * a1;
-            }
-    }
+    for (int q = 0; q < LOGH; ++q) fac *= fq[q];
 #pragma unroll
-    for (int r = 0; r < RG; ++r) st[(size_t)((w << (LOGH - 3)) | r) << LOQ] = v[r];
+    for (int r = 0; r < RG; ++r) st[(size_t)((w << (LOGH - 3)) | r) << LOQ] = v[r] * fac;
 }
 
 template <typename R>
