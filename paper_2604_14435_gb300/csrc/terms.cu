@@ -925,6 +925,7 @@ constexpr int TC_KSTEP_BYTES = (TC_NB / 8) * 2 * 128;       // 18 row groups x 2
 constexpr int TC_OPND_BYTES = (TCK / 32) * TC_KSTEP_BYTES;  // a pair stage's operand array (first or second tile)
 constexpr int TC_STAGE_BYTES = 2 * TC_OPND_BYTES;           // = TCK / 16 k-steps of a diagonal stage
 constexpr int TC_BROW = 16 * 256;   // offset of row group 16 (the b rows) inside a k-step
+constexpr int TC_OFF_HALF = (TCK / 2 / 16) * TC_KSTEP_BYTES;  // 64 amplitudes further along k in a stage
 constexpr int TC_HIROW = 64;        // first hi row of a diagonal k-step (rows 0..63: 2 lo)
 constexpr int TC_ND = 80;           // B rows of a diagonal k-step: 64 hi rows, 4 b rows, 12 zero rows
 constexpr int TC_X = 64 * 65;       // readout floats of one Gram quadrant ([64][65])
@@ -1399,10 +1400,12 @@ __device__ __forceinline__ uint32_t halve2(uint32_t v) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// oh, ol: byte offsets tc_off16(rhi, kk0), tc_off16(rlo, kk0) of the two rows
+// (kk0 a multiple of 16, so the second 8 amplitudes sit 128 bytes further).
 template <bool HBM, bool HALVE>
 __device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const float* psi_g, int N, int Na, int jb, int kend,
-                                              bool act, uint32_t xl, uint32_t zl, const uint32_t (&sgn)[8], int kk0,
-                                              unsigned char* dhi, int rhi, unsigned char* dlo, int rlo, bool copies) {
+                                              bool act, uint32_t xl, uint32_t zl, const uint32_t (&sgn)[8],
+                                              unsigned char* dhi, int oh, unsigned char* dlo, int ol, bool copies) {
     const uint32_t xhi = xl & ~15u, xlo = xl & 15u & uint32_t(N - 1);
     const int nval = act ? min(16, max(0, kend - jb)) : 0;
     const uint32_t rb = (uint32_t(jb) ^ xhi) & uint32_t(N - 1) & ~15u;
@@ -1448,9 +1451,8 @@ __device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const floa
             lo.z = halve2(lo.z);
             lo.w = halve2(lo.w);
         }
-        const int kk = kk0 + 8 * g;  // k within the stage's 64-amplitude k range
-        *reinterpret_cast<uint4*>(dhi + tc_off16(rhi, kk)) = hi;
-        *reinterpret_cast<uint4*>(dlo + tc_off16(rlo, kk)) = lo;
+        *reinterpret_cast<uint4*>(dhi + oh + 128 * g) = hi;
+        *reinterpret_cast<uint4*>(dlo + ol + 128 * g) = lo;
     }
 }
 
@@ -1549,6 +1551,11 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
         // both tasks share the term's masks.
         const int l = (lane & 7) | (wl << 3), sub = (lane >> 3) & 3;
         const int pside = (lane >> 3) & 1, psp = (lane >> 4) & 1;
+        // Byte offsets of this thread's rows at its first k in a stage: diagonal (hi row
+        // TC_HIROW + l, 2 lo row l, k = 16 sub; the second half of the stage TC_OFF_HALF
+        // further) and pair (hi row l, lo row 64 + l, k = 32 psp; the next 16 one k-step further).
+        const int ohd = tc_off16(TC_HIROW + l, sub * 16), old = tc_off16(l, sub * 16);
+        const int ohp = tc_off16(l, 32 * psp), olp = tc_off16(64 + l, 32 * psp);
         uint32_t eph = 0u, pend = 0u;   // bit q: parity of empty[2h + q] to wait for; stage in flight
         uint32_t iph = 0u, iused = 0u;  // item ring (thread 0 of the half): parity of ite[h][r]; slot used
         int ir = 0;
@@ -1690,13 +1697,13 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                     // TC_HIROW + l and 2 lo to row l of the same k-steps
 #pragma unroll 1
                     for (int hf = 0; hf < 2; ++hf) {
-                        const int kk = hf * (TCK / 2) + sub * 16, jb = j0 + kk;
+                        const int jb = j0 + hf * (TCK / 2) + sub * 16, dk = hf * TC_OFF_HALF;
                         if (gl)
-                            tc_build_half<true, false>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, kk, zhi,
-                                                       TC_HIROW + l, zhi, l, false);
+                            tc_build_half<true, false>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, zhi,
+                                                       ohd + dk, zhi, old + dk, false);
                         else
-                            tc_build_half<false, false>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, kk, zhi,
-                                                        TC_HIROW + l, zhi, l, copies);
+                            tc_build_half<false, false>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, zhi,
+                                                        ohd + dk, zhi, old + dk, copies);
                     }
                 } else {
                     // pair: the side's array (hi array: first tile, 2 lo array: second),
@@ -1704,13 +1711,13 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                     unsigned char* dst = pside ? zlo : zhi;
 #pragma unroll 1
                     for (int qb = 0; qb < 2; ++qb) {
-                        const int sb = 2 * psp + qb, jb = j0 + sb * 16;
+                        const int jb = j0 + (2 * psp + qb) * 16, dk = qb * TC_KSTEP_BYTES;
                         if (gl)
-                            tc_build_half<true, true>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, sb * 16, dst, l,
-                                                      dst, 64 + l, false);
+                            tc_build_half<true, true>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, dst, ohp + dk,
+                                                      dst, olp + dk, false);
                         else
-                            tc_build_half<false, true>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, sb * 16, dst,
-                                                       l, dst, 64 + l, copies);
+                            tc_build_half<false, true>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, dst, ohp + dk,
+                                                       dst, olp + dk, copies);
                     }
                 }
                 if (brow) asm volatile("cp.async.wait_all;" ::: "memory");
