@@ -961,20 +961,36 @@ __host__ __device__ inline size_t tc_psi_bytes(int n, bool copies) {
     return copies ? 4 * (4 * N + 32) : ((N * 4 + 15) & ~size_t(15));
 }
 __host__ __device__ inline bool tc_copies(int n, int copy_nmax) { return n >= 4 && n <= copy_nmax; }
+// States of 2^4 .. 2^split_nmax amplitudes (split_nmax <= TC_SPLIT_NMAX, chosen
+// per batch like copy_nmax, and taking precedence) are instead kept as separate
+// FP16 arrays of the hi and the 2 lo parts, eight copies of each: copy t holds
+// element k ^ t (t < 8) at half t S + k, S = 2^n + 8 halves (the pad puts the
+// copies 16 bytes apart in the banks); hi copy t starts at byte 2 t S, lo copy
+// t at byte 2 (8 + t) S.  A term's 16 amplitudes of a block are then two
+// 16-byte loads of hi and two of lo, already in order (the low three bits of
+// x_l pick the copy, bit 3 the order of the loads): no byte permutes.
+constexpr int TC_SPLIT_NMAX = 10;
+__host__ __device__ inline bool tc_split(int n, int split_nmax) { return n >= 4 && n <= split_nmax; }
+__host__ __device__ inline int tc_split_stride(int n) { return 2 * (1 << n) + 16; }  // bytes of one array
+__host__ __device__ inline size_t tc_split_bytes(int n) { return 16 * (size_t)tc_split_stride(n); }
 // Shared bytes of the term kernel for states of up to 2^nmax amplitudes in
-// shared memory (0: every state in HBM) and copies up to 2^copy_nmax.
-inline size_t tc_psi_region(int nmax_smem, int copy_nmax) {
+// shared memory (0: every state in HBM), split arrays up to 2^split_nmax and
+// packed copies up to 2^copy_nmax.
+inline size_t tc_psi_region(int nmax_smem, int copy_nmax, int split_nmax) {
     size_t psi = 0;
     if (nmax_smem > 0) {
-        const int nc = std::min(nmax_smem, copy_nmax);
-        psi = std::max(tc_psi_bytes(nmax_smem, tc_copies(nmax_smem, copy_nmax)), tc_psi_bytes(nc, tc_copies(nc, copy_nmax)));
+        auto one = [&](int n) {
+            return tc_split(n, split_nmax) ? tc_split_bytes(n) : tc_psi_bytes(n, tc_copies(n, copy_nmax));
+        };
+        psi = std::max(one(nmax_smem), std::max(one(std::min(nmax_smem, copy_nmax)), one(std::min(nmax_smem, split_nmax))));
     }
     return (psi + 1023) & ~size_t(1023);
 }
 // A state region for each builder half; the shared-memory readout of the
 // epilogue only for passes that return beta or delta (no other item touches it).
-inline size_t tc_smem_bytes(int nmax_smem, int copy_nmax, bool readout) {
-    return 1024 + (size_t)TC_NSTG * TC_STAGE_BYTES + 2 * tc_psi_region(nmax_smem, copy_nmax) + (readout ? TC_EPI_BYTES : 0);
+inline size_t tc_smem_bytes(int nmax_smem, int copy_nmax, int split_nmax, bool readout) {
+    return 1024 + (size_t)TC_NSTG * TC_STAGE_BYTES + 2 * tc_psi_region(nmax_smem, copy_nmax, split_nmax) +
+           (readout ? TC_EPI_BYTES : 0);
 }
 // Stages of the b rows of an instance with 2^n amplitudes.
 __host__ __device__ inline long long tc_bop_stages(long long N) { return (N + TCK - 1) / TCK; }
@@ -1402,15 +1418,36 @@ __device__ __forceinline__ uint32_t halve2(uint32_t v) {
 
 // oh, ol: byte offsets tc_off16(rhi, kk0), tc_off16(rlo, kk0) of the two rows
 // (kk0 a multiple of 16, so the second 8 amplitudes sit 128 bytes further).
+// split: psi_hl holds the split arrays (stride sst bytes) instead of packed words.
 template <bool HBM, bool HALVE>
 __device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const float* psi_g, int N, int Na, int jb, int kend,
                                               bool act, uint32_t xl, uint32_t zl, const uint32_t (&sgn)[8],
-                                              unsigned char* dhi, int oh, unsigned char* dlo, int ol, bool copies) {
+                                              unsigned char* dhi, int oh, unsigned char* dlo, int ol, bool copies,
+                                              bool split, int sst) {
     const uint32_t xhi = xl & ~15u, xlo = xl & 15u & uint32_t(N - 1);
     const int nval = act ? min(16, max(0, kend - jb)) : 0;
     const uint32_t rb = (uint32_t(jb) ^ xhi) & uint32_t(N - 1) & ~15u;
     const uint32_t flip = (__popc(zl & rb) & 1) ? 0x80008000u : 0u;  // the block's common sign
     const uint32_t ra = rb & uint32_t(Na - 1);  // the sources' offset in psi_hl (a block of Na amplitudes)
+    uint32_t hw[8], lw[8];  // word j: elements 2j, 2j + 1 of the hi and of the (2) lo row
+    if (!HBM && split) {
+        // target elements 8c .. 8c + 7 = copy (x_l & 7) at ra + 8 (c ^ bit 3 of x_l): one 16-byte load each
+        const unsigned char* hb = reinterpret_cast<const unsigned char*>(psi_hl) + (xlo & 7u) * uint32_t(sst) + 2u * ra;
+        const uint32_t o0 = (xlo & 8u) ? 16u : 0u;
+        const uint4 h0 = *reinterpret_cast<const uint4*>(hb + o0), h1 = *reinterpret_cast<const uint4*>(hb + (o0 ^ 16u));
+        const unsigned char* lb = hb + 8u * uint32_t(sst);
+        const uint4 l0 = *reinterpret_cast<const uint4*>(lb + o0), l1 = *reinterpret_cast<const uint4*>(lb + (o0 ^ 16u));
+        hw[0] = h0.x; hw[1] = h0.y; hw[2] = h0.z; hw[3] = h0.w; hw[4] = h1.x; hw[5] = h1.y; hw[6] = h1.z; hw[7] = h1.w;
+        lw[0] = l0.x; lw[1] = l0.y; lw[2] = l0.z; lw[3] = l0.w; lw[4] = l1.x; lw[5] = l1.y; lw[6] = l1.z; lw[7] = l1.w;
+        if (nval < 16) {  // elements past the range (or of an inactive term) are zero
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t m = (2 * j < nval ? 0x0000FFFFu : 0u) | (2 * j + 1 < nval ? 0xFFFF0000u : 0u);
+                hw[j] &= m;
+                lw[j] &= m;
+            }
+        }
+    } else {
     uint32_t w[16];
     if (!HBM && copies && nval == 16) {
         // w[4c + r] = psi[rb + 4 (c ^ xc) + (r ^ (x_l & 3))] = cpy[ra + 4 (c ^ xc) + r]
@@ -1433,18 +1470,24 @@ __device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const floa
         }
     }
 #pragma unroll
+    for (int j = 0; j < 8; ++j) {  // packed words to hi and lo words
+        hw[j] = __byte_perm(w[2 * j], w[2 * j + 1], 0x5410);
+        lw[j] = __byte_perm(w[2 * j], w[2 * j + 1], 0x7632);
+    }
+    }
+#pragma unroll
     for (int g = 0; g < 2; ++g) {
         // Sign bits of packed pairs sit at bits 15 and 31 of a hi (or 2 lo)
         // word: one three-input XOR applies the term's and the block's sign.
         uint4 hi, lo;
-        hi.x = __byte_perm(w[8 * g + 0], w[8 * g + 1], 0x5410) ^ sgn[4 * g + 0] ^ flip;
-        hi.y = __byte_perm(w[8 * g + 2], w[8 * g + 3], 0x5410) ^ sgn[4 * g + 1] ^ flip;
-        hi.z = __byte_perm(w[8 * g + 4], w[8 * g + 5], 0x5410) ^ sgn[4 * g + 2] ^ flip;
-        hi.w = __byte_perm(w[8 * g + 6], w[8 * g + 7], 0x5410) ^ sgn[4 * g + 3] ^ flip;
-        lo.x = __byte_perm(w[8 * g + 0], w[8 * g + 1], 0x7632) ^ sgn[4 * g + 0] ^ flip;
-        lo.y = __byte_perm(w[8 * g + 2], w[8 * g + 3], 0x7632) ^ sgn[4 * g + 1] ^ flip;
-        lo.z = __byte_perm(w[8 * g + 4], w[8 * g + 5], 0x7632) ^ sgn[4 * g + 2] ^ flip;
-        lo.w = __byte_perm(w[8 * g + 6], w[8 * g + 7], 0x7632) ^ sgn[4 * g + 3] ^ flip;
+        hi.x = hw[4 * g + 0] ^ sgn[4 * g + 0] ^ flip;
+        hi.y = hw[4 * g + 1] ^ sgn[4 * g + 1] ^ flip;
+        hi.z = hw[4 * g + 2] ^ sgn[4 * g + 2] ^ flip;
+        hi.w = hw[4 * g + 3] ^ sgn[4 * g + 3] ^ flip;
+        lo.x = lw[4 * g + 0] ^ sgn[4 * g + 0] ^ flip;
+        lo.y = lw[4 * g + 1] ^ sgn[4 * g + 1] ^ flip;
+        lo.z = lw[4 * g + 2] ^ sgn[4 * g + 2] ^ flip;
+        lo.w = lw[4 * g + 3] ^ sgn[4 * g + 3] ^ flip;
         if (HALVE) {
             lo.x = halve2(lo.x);
             lo.y = halve2(lo.y);
@@ -1475,7 +1518,7 @@ __device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const floa
 constexpr int TC_HT = TC_BT / 2;  // threads of a builder half
 __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ insts, int count, long long total,
                                                      unsigned long long* queue, int* status, int copy_nmax,
-                                                     int psi_half, long long budget_ns) {
+                                                     int split_nmax, int psi_half, long long budget_ns) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1618,7 +1661,9 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 blk = kper == HBM_K && !bar_or(bar, TC_HT, far);
             }
             const int Na = blk ? int(HBM_K) : N;  // amplitudes in shared memory
-            const bool copies = (!I.states || blk) && tc_copies(blk ? HBM_KQ : n, copy_nmax);
+            const bool split = (!I.states || blk) && tc_split(blk ? HBM_KQ : n, split_nmax);
+            const bool copies = !split && (!I.states || blk) && tc_copies(blk ? HBM_KQ : n, copy_nmax);
+            const int sst = tc_split_stride(blk ? HBM_KQ : n);  // bytes of one split array
             if (blk) {  // the item's block of the FP32 state in HBM, split into packed pairs here
                 // the FP32 block lands in the last copy's room (with copies) or in place
                 float* stage = reinterpret_cast<float*>(psi_hl + (copies ? 3 * (Na + 8) : 0));
@@ -1641,17 +1686,56 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 }
             } else if (!I.states) {  // the packed state of shift s (built by k_tc_states)
                 const uint32_t* src = reinterpret_cast<const uint32_t*>(I.tcst) + (size_t)s * N;
+                // split arrays: the packed words land in the room of the last two lo copies
+                uint32_t* dst = split ? reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(psi_hl) + 14 * sst)
+                                      : psi_hl;
                 if (N >= 4) {
                     for (int k = 4 * tt; k < N; k += 4 * TC_HT)
-                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(psi_hl + k)),
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst + k)),
                                      "l"(__cvta_generic_to_global(src + k))
                                      : "memory");
                     asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
                 } else if (tt < N) {
-                    psi_hl[tt] = src[tt];
+                    dst[tt] = src[tt];
                 }
             }
             ab = bar_or(bar, TC_HT, ab);
+            if (split) {
+                // Group gi of 8 amplitudes (one per thread: N / 8 <= 128 groups): its packed words
+                // p_i = hi_i | (2 lo)_i << 16 go to the hi and lo copies t = 0..7, whose words j hold
+                // elements (2j) ^ t, (2j + 1) ^ t of the group: word j ^ (t >> 1) of the pairs in order
+                // (t even) or swapped (t odd).
+                unsigned char* pb = reinterpret_cast<unsigned char*>(psi_hl);
+                const int gi = tt;
+                uint4 p0 = make_uint4(0u, 0u, 0u, 0u), p1 = p0;
+                if (gi < N / 8) {
+                    const uint4* stg = reinterpret_cast<const uint4*>(pb + 14 * sst);
+                    p0 = stg[2 * gi];
+                    p1 = stg[2 * gi + 1];
+                }
+                bar_n(bar, TC_HT);  // every staged word is read before the copies overwrite them
+                if (gi < N / 8) {
+                    const uint32_t pw[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+                    uint32_t HP[4], HS[4], LP[4], LS[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        HP[k] = __byte_perm(pw[2 * k], pw[2 * k + 1], 0x5410);
+                        HS[k] = __byte_perm(pw[2 * k], pw[2 * k + 1], 0x1054);
+                        LP[k] = __byte_perm(pw[2 * k], pw[2 * k + 1], 0x7632);
+                        LS[k] = __byte_perm(pw[2 * k], pw[2 * k + 1], 0x3276);
+                    }
+#pragma unroll
+                    for (int t8 = 0; t8 < 8; ++t8) {
+                        const int u = t8 >> 1;
+                        const uint32_t* H = (t8 & 1) ? HS : HP;
+                        const uint32_t* Lw = (t8 & 1) ? LS : LP;
+                        *reinterpret_cast<uint4*>(pb + t8 * sst + 16 * gi) = make_uint4(H[0 ^ u], H[1 ^ u], H[2 ^ u], H[3 ^ u]);
+                        *reinterpret_cast<uint4*>(pb + (8 + t8) * sst + 16 * gi) =
+                            make_uint4(Lw[0 ^ u], Lw[1 ^ u], Lw[2 ^ u], Lw[3 ^ u]);
+                    }
+                }
+                bar_n(bar, TC_HT);
+            }
             if (copies && !blk) {  // copy t: psi[k ^ t] at word t (N + 8) + k
                 for (int k = tt; k < N; k += TC_HT) {
                     const uint32_t v = psi_hl[k];
@@ -1700,10 +1784,10 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                         const int jb = j0 + hf * (TCK / 2) + sub * 16, dk = hf * TC_OFF_HALF;
                         if (gl)
                             tc_build_half<true, false>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, zhi,
-                                                       ohd + dk, zhi, old + dk, false);
+                                                       ohd + dk, zhi, old + dk, false, false, sst);
                         else
                             tc_build_half<false, false>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, zhi,
-                                                        ohd + dk, zhi, old + dk, copies);
+                                                        ohd + dk, zhi, old + dk, copies, split, sst);
                     }
                 } else {
                     // pair: the side's array (hi array: first tile, 2 lo array: second),
@@ -1714,10 +1798,10 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                         const int jb = j0 + (2 * psp + qb) * 16, dk = qb * TC_KSTEP_BYTES;
                         if (gl)
                             tc_build_half<true, true>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, dst, ohp + dk,
-                                                      dst, olp + dk, false);
+                                                      dst, olp + dk, false, false, sst);
                         else
                             tc_build_half<false, true>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, dst, ohp + dk,
-                                                       dst, olp + dk, copies);
+                                                       dst, olp + dk, copies, split, sst);
                     }
                 }
                 if (brow) asm volatile("cp.async.wait_all;" ::: "memory");
@@ -2753,6 +2837,7 @@ struct PassShape {
     long long total;
     size_t smem;
     int copy_nmax;   // tensor-core kernel: states of 2^4 .. 2^copy_nmax amplitudes kept in four copies (0: none)
+    int split_nmax;  // tensor-core kernel: states of 2^4 .. 2^split_nmax amplitudes kept as split hi / lo arrays
     int psi_region;  // tensor-core kernel: shared bytes of a builder half's state copies
     int st_grid;     // tensor-core pass: CTAs per instance of k_tc_states (0: no state in shared memory)
     int st_smem;     // and its dynamic shared bytes
@@ -2824,7 +2909,7 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
                                        ps.total, ctx->d_queue));
     else if (ps.tc)
         DVQLS_CUDA_TRY(ctx, launch_pdl(k_terms_tc, dim3(ps.grid), dim3(TCT), ps.smem, st, dtable, ps.count, ps.total,
-                                       ctx->d_queue, ctx->d_status, ps.copy_nmax, ps.psi_region, ps.budget_ns));
+                                       ctx->d_queue, ctx->d_status, ps.copy_nmax, ps.split_nmax, ps.psi_region, ps.budget_ns));
     else if (ps.fp32)
         DVQLS_CUDA_TRY(ctx, launch_pdl(k_terms_smem<float>, dim3(ps.grid), dim3(NT), ps.smem, st, dtable, ps.count,
                                        ps.total, ctx->d_queue));
@@ -2952,7 +3037,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     bool wht = precision == DVQLS_FP32_WHT;
     for (const auto& h : hi) wht = wht && h.T == 1 && h.n <= WHT_MAXN;
     bool tc = !wht && (precision == DVQLS_FP32_TC || (precision == DVQLS_FP32_WHT && !local));
-    int copy_nmax = 0;
+    int copy_nmax = 0, split_nmax = 0;
     const bool readout = beta_out || delta_out;
     // the tensor-core kernel's shared state region: the largest on-chip state, and
     // a staged block of HBM_K amplitudes when some state lives in HBM
@@ -2964,9 +3049,11 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         cudaFuncAttributes fa;
         DVQLS_CUDA_TRY(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
         DVQLS_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, (const void*)k_terms_tc));
-        tc = tc_smem_bytes(tc_nsm, 0, readout) + fa.sharedSizeBytes <= (size_t)optin;
+        tc = tc_smem_bytes(tc_nsm, 0, 0, readout) + fa.sharedSizeBytes <= (size_t)optin;
         for (int c = TC_COPY_NMAX; tc && tc_nsm > 0 && c >= 4 && !copy_nmax; --c)
-            if (tc_smem_bytes(tc_nsm, c, readout) + fa.sharedSizeBytes <= (size_t)optin) copy_nmax = c;
+            if (tc_smem_bytes(tc_nsm, c, 0, readout) + fa.sharedSizeBytes <= (size_t)optin) copy_nmax = c;
+        for (int c = std::min(TC_SPLIT_NMAX, tc_nsm); tc && c >= 4 && !split_nmax; --c)
+            if (tc_smem_bytes(tc_nsm, copy_nmax, c, readout) + fa.sharedSizeBytes <= (size_t)optin) split_nmax = c;
     }
     // The tensor-core pass builds the on-chip states in a kernel of its own.
     int st_grid = 0;
@@ -2979,7 +3066,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
             }
     if (st_grid > 0) DVQLS_CUDA_TRY(ctx, allow_dynamic_smem((const void*)k_tc_states));
     const size_t smem = wht  ? wht_smem_bytes(Pmax)
-                        : tc ? tc_smem_bytes(tc_nsm, copy_nmax, readout)
+                        : tc ? tc_smem_bytes(tc_nsm, copy_nmax, split_nmax, readout)
                         : fp32 ? smem_bytes<float>(nmax, Pmax) : smem_bytes<double>(nmax, Pmax);
     const size_t r2 = fp32 ? 8 : 16;
     auto kfun = wht ? (const void*)k_terms_wht
@@ -3195,7 +3282,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         ps.grid = (int)std::min<long long>(base, slots);
         ps.smem = smem;
         ps.copy_nmax = copy_nmax;
-        ps.psi_region = tc ? (int)tc_psi_region(tc_nsm, copy_nmax) : 0;
+        ps.split_nmax = split_nmax;
+        ps.psi_region = tc ? (int)tc_psi_region(tc_nsm, copy_nmax, split_nmax) : 0;
         ps.st_grid = st_grid;
         ps.st_smem = (int)st_smem;
         ps.budget_ns = ctx->wait_budget_us * 1000;
