@@ -31,9 +31,10 @@
  *     exp(-i a Y / 2) gate: f' = [f(a + pi/2) - f(a - pi/2)] / 2.
  *
  * Memory: every pointer argument may be host memory or device memory of the
- * context's device (told apart with cudaPointerGetAttributes).  The caller
- * owns all buffers; the library never frees caller memory and never keeps a
- * caller pointer after the call returns.  The context owns its workspace,
+ * context's device (told apart with cudaPointerGetAttributes; a context
+ * remembers the addresses it found to be host memory and does not ask
+ * again).  The caller owns all buffers; the library never frees caller
+ * memory and never dereferences a caller pointer after the call returns.  The context owns its workspace,
  * staging buffers and CUDA graphs.  Work is ordered on the context's stream.
  * Unless a function says otherwise it returns after its results are in the
  * caller's buffers.
@@ -243,9 +244,11 @@ typedef struct {
  * results are in place.
  * Launch: the first call of a problem signature (precision and every
  * instance's n, depth, L) times each split of the amplitude range among the
- * candidates 1, 2, 4, 8 on the real inputs (the fastest of three passes per
- * candidate) and keeps the fastest for the context (an autotuner; that call
- * is synchronous).  The kernel sequence of a
+ * candidates 1, 2, 4, 8 -- for the tensor-core kernel each with the layouts
+ * of the on-chip states (split hi / lo arrays, for every size or only from
+ * 2^9 amplitudes, or packed copies) where they fit -- on the real inputs (the
+ * fastest of three passes per candidate) and keeps the fastest for the
+ * context (an autotuner; that call is synchronous).  The kernel sequence of a
  * pass is captured once as a CUDA graph and replayed while the instance
  * table (shapes and pointers) is unchanged; with profiling enabled, or when
  * the caller is capturing the stream, kernels are launched directly. */

@@ -19,13 +19,19 @@ int set_error(dvqls_ctx* ctx, int code, const char* fmt, ...) {
 
 bool is_device_ptr(const dvqls_ctx* ctx, const void* p) {
     if (!p) return false;
+    auto& seen = const_cast<dvqls_ctx*>(ctx)->host_ptrs;
+    if (seen.count(p)) return false;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    if (a.type == cudaMemoryTypeDevice) return a.device == ctx->device;
-    return a.type == cudaMemoryTypeManaged;
+    const bool dev = a.type == cudaMemoryTypeDevice ? a.device == ctx->device : a.type == cudaMemoryTypeManaged;
+    if (!dev && a.type != cudaMemoryTypeDevice) {  // host memory (device memory of another GPU is not cached)
+        if (seen.size() >= 4096) seen.clear();
+        seen.insert(p);
+    }
+    return dev;
 }
 
 cudaError_t allow_dynamic_smem(const void* fn) {

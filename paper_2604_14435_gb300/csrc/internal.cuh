@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/dvqls.h"
@@ -71,6 +72,13 @@ struct dvqls_ctx {
     // Time each bounded device wait of the tensor-core term kernel allows
     // before it gives up, in microseconds (dvqls_set_wait_budget).
     long long wait_budget_us = 1000000;
+
+    // Addresses already found to be host memory (not device memory of this
+    // device, not managed): a later call skips their pointer-kind query.  A
+    // host address stays outside the range the driver reserves for device
+    // allocations, so the answer cannot turn into "device"; at worst memory
+    // that became managed there is staged through the pinned buffer.
+    std::unordered_set<const void*> host_ptrs;
 
     // Cached batched-call state (see terms.cu): the last captured graph of a
     // cost pass, the private stream graphs are captured on, and the

@@ -1518,7 +1518,7 @@ __device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const floa
 constexpr int TC_HT = TC_BT / 2;  // threads of a builder half
 __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ insts, int count, long long total,
                                                      unsigned long long* queue, int* status, int copy_nmax,
-                                                     int split_nmax, int psi_half, long long budget_ns) {
+                                                     int split_range, int psi_half, long long budget_ns) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1661,7 +1661,9 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                 blk = kper == HBM_K && !bar_or(bar, TC_HT, far);
             }
             const int Na = blk ? int(HBM_K) : N;  // amplitudes in shared memory
-            const bool split = (!I.states || blk) && tc_split(blk ? HBM_KQ : n, split_nmax);
+            // split_range: the largest n of the split arrays in bits 0..7, the smallest (at least 4) in 8..15
+            const int sn = blk ? HBM_KQ : n;
+            const bool split = (!I.states || blk) && tc_split(sn, split_range & 255) && sn >= (split_range >> 8);
             const bool copies = !split && (!I.states || blk) && tc_copies(blk ? HBM_KQ : n, copy_nmax);
             const int sst = tc_split_stride(blk ? HBM_KQ : n);  // bytes of one split array
             if (blk) {  // the item's block of the FP32 state in HBM, split into packed pairs here
@@ -2837,7 +2839,8 @@ struct PassShape {
     long long total;
     size_t smem;
     int copy_nmax;   // tensor-core kernel: states of 2^4 .. 2^copy_nmax amplitudes kept in four copies (0: none)
-    int split_nmax;  // tensor-core kernel: states of 2^4 .. 2^split_nmax amplitudes kept as split hi / lo arrays
+    int split_nmax;  // tensor-core kernel: states of 2^split_nmin .. 2^split_nmax amplitudes kept as split
+    int split_nmin;  // hi / lo arrays (split_nmax 0: none)
     int psi_region;  // tensor-core kernel: shared bytes of a builder half's state copies
     int st_grid;     // tensor-core pass: CTAs per instance of k_tc_states (0: no state in shared memory)
     int st_smem;     // and its dynamic shared bytes
@@ -2909,7 +2912,8 @@ static int launch_pass(dvqls_ctx* ctx, cudaStream_t st, const Inst* dtable, cons
                                        ps.total, ctx->d_queue));
     else if (ps.tc)
         DVQLS_CUDA_TRY(ctx, launch_pdl(k_terms_tc, dim3(ps.grid), dim3(TCT), ps.smem, st, dtable, ps.count, ps.total,
-                                       ctx->d_queue, ctx->d_status, ps.copy_nmax, ps.split_nmax, ps.psi_region, ps.budget_ns));
+                                       ctx->d_queue, ctx->d_status, ps.copy_nmax, ps.split_nmax | (ps.split_nmin << 8), ps.psi_region,
+                                       ps.budget_ns));
     else if (ps.fp32)
         DVQLS_CUDA_TRY(ctx, launch_pdl(k_terms_smem<float>, dim3(ps.grid), dim3(NT), ps.smem, st, dtable, ps.count,
                                        ps.total, ctx->d_queue));
@@ -3111,7 +3115,9 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     const bool dev_part = range && is_device_ptr(ctx, range->partials);
     const size_t o_part = range && !dev_part ? ar.reserve(size_t(S_full) * 32) : 0;
     const size_t p_part = range && !dev_part ? pin.reserve(size_t(S_full) * 32) : 0;
-    const int ks_plan_smem = tuning ? 8 : (tuned != ctx->tune.end() ? tuned->second : 1);
+    // A tuned choice: amplitude split in bits 0..7, the state layout (see the tuning loop) in bits 8..9.
+    const int ks_plan_smem = tuning ? 8 : (tuned != ctx->tune.end() ? (tuned->second & 255) : 1);
+    int split_use = split_nmax, split_min = 4;
     // Staged inputs of all instances first, then the results, each reserved
     // in both arenas in the same order, so that the copies of a call merge
     // into one host-to-device and one device-to-host transfer.
@@ -3282,7 +3288,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         ps.grid = (int)std::min<long long>(base, slots);
         ps.smem = smem;
         ps.copy_nmax = copy_nmax;
-        ps.split_nmax = split_nmax;
+        ps.split_nmax = split_use;
+        ps.split_nmin = split_min;
         ps.psi_region = tc ? (int)tc_psi_region(tc_nsm, copy_nmax, split_nmax) : 0;
         ps.st_grid = st_grid;
         ps.st_smem = (int)st_smem;
@@ -3308,9 +3315,12 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     };
 
     PassShape ps{};
-    int ks_use = tuned != ctx->tune.end() ? tuned->second : 1;
+    int ks_use = tuned != ctx->tune.end() ? (tuned->second & 255) : 1;
+    int lay_use = tuned != ctx->tune.end() ? (tuned->second >> 8) & 3 : 0;
     if (tuning) {
-        // Time one full pass per candidate split and keep the fastest.
+        // Time full passes per candidate -- the amplitude split, and the state layout of the
+        // tensor-core builders (split hi / lo arrays or packed copies) where both fit -- and
+        // keep the fastest.
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         DVQLS_CUDA_TRY(ctx, cudaEventCreate(&e0));
         DVQLS_CUDA_TRY(ctx, cudaEventCreate(&e1));
@@ -3319,7 +3329,16 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         // first pass of a candidate (and of the whole call) also pays one-time costs
         // (cold caches, first launches) that a single timing would charge to it.
         constexpr int TUNE_REPS = 3;
+        bool first = true;
+        // layouts: 0 split arrays for 2^4 .. 2^split_nmax amplitudes, 1 only from 2^9 (small items keep
+        // the packed copies, whose set-up has one barrier less), 2 packed copies only
+        bool small = false;
+        for (const auto& h : hi) small = small || (!h.hbm && h.n >= 4 && h.n < 9);
+        for (int lay = 0; lay < (split_nmax > 0 ? 3 : 1); ++lay) {
+        if (lay == 1 && (!small || split_nmax < 9)) continue;
         for (int c : cands) {
+            split_use = lay == 2 ? 0 : split_nmax;
+            split_min = lay == 1 ? 9 : 4;
             build_table(c, ps);
             rc = upload();
             float cbest = 0.f;
@@ -3338,10 +3357,13 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
                 cudaGetLastError();
                 return rc == DVQLS_ERR_CUDA ? set_error(ctx, rc, "autotune pass failed") : rc;
             }
-            if (c == cands[0] || cbest < best) {
+            if (first || cbest < best) {
                 best = cbest;
                 ks_use = c;
+                lay_use = lay;
             }
+            first = false;
+        }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -3349,8 +3371,10 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         // timed nothing meaningful: report it and keep no choice.
         rc = sync_and_check(ctx);
         if (rc) return rc;
-        ctx->tune[sig] = ks_use;
+        ctx->tune[sig] = ks_use | (lay_use << 8);
     }
+    split_use = lay_use == 2 ? 0 : split_nmax;
+    split_min = lay_use == 1 ? 9 : 4;
     build_table(ks_use, ps);
     rc = upload();
     if (!rc && !all_device) rc = pin_release(ctx);
