@@ -1,7 +1,7 @@
 """The identities the fast kernels rest on, checked in plain numpy on small
 random cases (CPU): the Walsh-Hadamard form of the real Gram terms (global
 cost, and the local cost's X_j flavours), and the index algebra of the
-four-copy state layout of the tensor-core tiles."""
+four-copy and the split state layouts of the tensor-core tiles."""
 import numpy as np
 import pytest
 
@@ -71,3 +71,50 @@ def test_four_copy_layout_index_algebra():
             for i in range(16):
                 c, r = i >> 2, i & 3
                 assert psi[rb | (i ^ xlo)] == copies[xlo & 3][rb + 4 * (c ^ (xlo >> 2)) + r]
+
+
+def prmt(a, b, sel):
+    """Byte permute of the eight bytes of (a, b): byte i of the result is
+    byte (nibble i of sel) & 7 of b:a."""
+    src = [(a >> (8 * k)) & 0xFF for k in range(4)] + [(b >> (8 * k)) & 0xFF for k in range(4)]
+    return sum(src[(sel >> (4 * i)) & 7] << (8 * i) for i in range(4))
+
+
+def test_split_copy_layout_index_algebra():
+    """The split state layout: from the packed words p_k = hi_k | lo_k << 16,
+    group g of eight amplitudes of hi copy t (t < 8) is the words
+    W[j ^ (t >> 1)], j = 0..3, with W = byte permutes 0x5410 (t even) or 0x1054
+    (t odd) of the word pairs (p_{8g+2k}, p_{8g+2k+1}); lo the same with 0x7632 /
+    0x3276.  Copy t then holds hi_{k ^ t}, and target elements 8c .. 8c + 7 of a
+    term's 16-block are copy (x & 7) at rb + 8 (c ^ bit 3 of x)."""
+    N = 64
+    rng = np.random.default_rng(3)
+    hi = rng.integers(0, 1 << 16, N)
+    lo = rng.integers(0, 1 << 16, N)
+    packed = [int(h) | (int(l) << 16) for h, l in zip(hi, lo)]
+    H = np.zeros((8, N), dtype=np.int64)
+    Lo = np.zeros((8, N), dtype=np.int64)
+    for g in range(N // 8):
+        pw = packed[8 * g:8 * g + 8]
+        HP = [prmt(pw[2 * k], pw[2 * k + 1], 0x5410) for k in range(4)]
+        HS = [prmt(pw[2 * k], pw[2 * k + 1], 0x1054) for k in range(4)]
+        LP = [prmt(pw[2 * k], pw[2 * k + 1], 0x7632) for k in range(4)]
+        LS = [prmt(pw[2 * k], pw[2 * k + 1], 0x3276) for k in range(4)]
+        for t in range(8):
+            u = t >> 1
+            Wh, Wl = (HS, LS) if t & 1 else (HP, LP)
+            for j in range(4):
+                for half in range(2):
+                    H[t, 8 * g + 2 * j + half] = (Wh[j ^ u] >> (16 * half)) & 0xFFFF
+                    Lo[t, 8 * g + 2 * j + half] = (Wl[j ^ u] >> (16 * half)) & 0xFFFF
+    for t in range(8):
+        assert np.array_equal(H[t], hi[np.arange(N) ^ t])
+        assert np.array_equal(Lo[t], lo[np.arange(N) ^ t])
+    for xl in range(N):
+        xlo = xl & 15
+        for rb in range(0, N, 16):
+            for i in range(16):
+                c, e = i >> 3, i & 7
+                src = rb + 8 * (c ^ (xlo >> 3)) + e
+                assert hi[rb | (i ^ xlo)] == H[xlo & 7, src]
+                assert lo[rb | (i ^ xlo)] == Lo[xlo & 7, src]
