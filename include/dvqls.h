@@ -255,6 +255,19 @@ typedef struct {
 int dvqls_cost_grad_batched(dvqls_ctx* ctx, int count, const dvqls_instance* inst,
                             int precision, double* costs, double* grads);
 
+/* Fixes the autotuner's choices for this context's later batched and single
+ * calls instead of timing candidates (A9; the paper has no autotuner): the
+ * amplitude split `split` (1, 2, 4 or 8; 0 = tune again) and, for the
+ * tensor-core kernel, the state layout `layout` (0: split hi / lo arrays for
+ * states of 2^4 .. 2^10 amplitudes, 1: split arrays only from 2^9, 2: packed
+ * copies; -1 = tuned, or 0 when the split is fixed).  A layout that does not
+ * fit the CTA's shared memory falls back as the tuner would.  For callers
+ * that cannot afford the synchronous tuning call, and for comparing layouts:
+ * the layouts give bit-identical results (the same operand values reach the
+ * tensor cores), the splits differ only in summation order.
+ * Errors: INVALID_ARG (ctx NULL, split not 0, 1, 2, 4, 8, layout not -1..2). */
+int dvqls_set_tuning(dvqls_ctx* ctx, int split, int layout);
+
 /* One instance split across ranks (Sec. 2.3 Stage III; Algorithm 1, Step
  * 4c).  A rank evaluates the shifts s_begin .. s_end - 1 of the 2P + 1
  * parameter-shift evaluations (0 <= s_begin < s_end <= 2P + 1; shift 0 is

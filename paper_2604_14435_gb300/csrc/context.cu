@@ -315,6 +315,16 @@ extern "C" int dvqls_set_wait_budget(dvqls_ctx* ctx, long long microseconds) {
     return DVQLS_OK;
 }
 
+extern "C" int dvqls_set_tuning(dvqls_ctx* ctx, int split, int layout) {
+    if (!ctx) return DVQLS_ERR_INVALID_ARG;
+    if (split != 0 && split != 1 && split != 2 && split != 4 && split != 8)
+        return set_error(ctx, DVQLS_ERR_INVALID_ARG, "split %d is not 0, 1, 2, 4 or 8", split);
+    if (layout < -1 || layout > 2) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "layout %d is not -1 .. 2", layout);
+    ctx->fixed_split = split;
+    ctx->fixed_layout = layout;
+    return DVQLS_OK;
+}
+
 extern "C" const char* dvqls_last_error(const dvqls_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 extern "C" int dvqls_sync(dvqls_ctx* ctx) {

@@ -73,6 +73,9 @@ struct dvqls_ctx {
     // before it gives up, in microseconds (dvqls_set_wait_budget).
     long long wait_budget_us = 1000000;
 
+    // dvqls_set_tuning: a fixed amplitude split (0: tune) and state layout (-1: tune).
+    int fixed_split = 0, fixed_layout = -1;
+
     // Addresses already found to be host memory (not device memory of this
     // device, not managed): a later call skips their pointer-kind query.  A
     // host address stays outside the range the driver reserves for device

@@ -3090,9 +3090,11 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
                       (delta_out ? "d" : "") + (local ? "L" : "") +
                       (range ? "R" + std::to_string(range->s1 - range->s0) : std::string());
     for (const auto& h : hi) sig += "|" + std::to_string(h.n) + "," + std::to_string(h.d) + "," + std::to_string(h.L);
+    if (ctx->fixed_layout >= 0) sig += "|F" + std::to_string(ctx->fixed_layout);  // tuned under a fixed layout
     const int cands[] = {1, 2, 4, 8};
     auto tuned = ctx->tune.find(sig);
-    const bool tuning = any_smem && !wht && tuned == ctx->tune.end();
+    const bool fixed = ctx->fixed_split > 0;  // dvqls_set_tuning
+    const bool tuning = any_smem && !wht && tuned == ctx->tune.end() && !fixed;
     auto ks_for = [&](const HostInst& h, int ks) {  // tensor-core items start on whole 128-amplitude stages
         if (wht) return 1;                            // a class item covers a whole state
         return h.hbm ? (int)std::max<long long>(1, h.N / HBM_K)
@@ -3116,7 +3118,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     const size_t o_part = range && !dev_part ? ar.reserve(size_t(S_full) * 32) : 0;
     const size_t p_part = range && !dev_part ? pin.reserve(size_t(S_full) * 32) : 0;
     // A tuned choice: amplitude split in bits 0..7, the state layout (see the tuning loop) in bits 8..9.
-    const int ks_plan_smem = tuning ? 8 : (tuned != ctx->tune.end() ? (tuned->second & 255) : 1);
+    const int ks_plan_smem = fixed ? ctx->fixed_split : tuning ? 8 : (tuned != ctx->tune.end() ? (tuned->second & 255) : 1);
     int split_use = split_nmax, split_min = 4;
     // Staged inputs of all instances first, then the results, each reserved
     // in both arenas in the same order, so that the copies of a call merge
@@ -3315,8 +3317,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     };
 
     PassShape ps{};
-    int ks_use = tuned != ctx->tune.end() ? (tuned->second & 255) : 1;
-    int lay_use = tuned != ctx->tune.end() ? (tuned->second >> 8) & 3 : 0;
+    int ks_use = fixed ? ctx->fixed_split : tuned != ctx->tune.end() ? (tuned->second & 255) : 1;
+    int lay_use = fixed ? std::max(0, ctx->fixed_layout) : tuned != ctx->tune.end() ? (tuned->second >> 8) & 3 : 0;
     if (tuning) {
         // Time full passes per candidate -- the amplitude split, and the state layout of the
         // tensor-core builders (split hi / lo arrays or packed copies) where both fit -- and
@@ -3335,7 +3337,8 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
         bool small = false;
         for (const auto& h : hi) small = small || (!h.hbm && h.n >= 4 && h.n < 9);
         for (int lay = 0; lay < (split_nmax > 0 ? 3 : 1); ++lay) {
-        if (lay == 1 && (!small || split_nmax < 9)) continue;
+        if (lay == 1 && ctx->fixed_layout != 1 && (!small || split_nmax < 9)) continue;
+        if (ctx->fixed_layout >= 0 && lay != ctx->fixed_layout) continue;  // dvqls_set_tuning
         for (int c : cands) {
             split_use = lay == 2 ? 0 : split_nmax;
             split_min = lay == 1 ? 9 : 4;

@@ -33,7 +33,8 @@ EXPORTED = [
     "dvqls_create", "dvqls_destroy", "dvqls_last_error", "dvqls_sync",
     "dvqls_pauli_decompose", "dvqls_pauli_decompose_banded",
     "dvqls_cost", "dvqls_cost_grad", "dvqls_cost_grad_batched",
-    "dvqls_profile_enable", "dvqls_profile_read", "dvqls_set_wait_budget", "dvqls_cost_grad_noalloc",
+    "dvqls_profile_enable", "dvqls_profile_read", "dvqls_set_wait_budget", "dvqls_set_tuning",
+    "dvqls_cost_grad_noalloc",
     "dvqls_circuit_cost_grad_fp64", "dvqls_fidelity", "dvqls_lcu_solve", "dvqls_lcu_solve_batched",
     "dvqls_optimize", "dvqls_optimize_resume",
     "dvqls_ws_param_count", "dvqls_ws_create", "dvqls_ws_destroy", "dvqls_ws_infer", "dvqls_ws_grad",
@@ -108,6 +109,7 @@ def lib():
                                               dp, dp]
         L.dvqls_profile_enable.argtypes = [vp, ctypes.c_int]
         L.dvqls_set_wait_budget.argtypes = [vp, ctypes.c_longlong]
+        L.dvqls_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.dvqls_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(ctypes.c_double)]
         L.dvqls_cost_grad_noalloc.argtypes = [vp, ctypes.POINTER(dvqls_ansatz), dp, ctypes.POINTER(dvqls_lcu), dp,
@@ -244,6 +246,11 @@ def dvqls_profile_enable(ctx, enable):
 def dvqls_set_wait_budget(ctx, microseconds):
     """Time limit of each bounded device wait of the tensor-core term kernel."""
     _check(ctx, lib().dvqls_set_wait_budget(ctx, int(microseconds)))
+
+
+def dvqls_set_tuning(ctx, split, layout=-1):
+    """Fix the amplitude split (0: tune) and the tensor-core state layout (-1: tune)."""
+    _check(ctx, lib().dvqls_set_tuning(ctx, int(split), int(layout)))
 
 
 def dvqls_profile_read(ctx, phase):
