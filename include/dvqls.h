@@ -42,6 +42,10 @@
  * Errors: every function returns a dvqls_status.  No exception crosses the
  * ABI.  dvqls_last_error() gives a one-line description of the last failure
  * on the context.
+ *
+ * Tracing: the main calls, and inside a cost pass the autotuning and the
+ * pass kernels, are NVTX ranges on a profiler's timeline (nothing happens
+ * without a profiler attached); dvqls_profile_* times the kernels of a pass.
  */
 #ifndef DVQLS_H
 #define DVQLS_H

@@ -425,5 +425,6 @@ int run_circuits(dvqls_ctx* ctx, const dvqls_ansatz* an, const double* alpha, co
 extern "C" int dvqls_circuit_cost_grad_fp64(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const double* alpha,
                                             const dvqls_lcu* lcu, const double* b, double* cost, double* grad,
                                             double* beta, double* delta) {
+    DVQLS_NVTX("dvqls_circuit_cost_grad_fp64");
     return dvqls::run_circuits(ctx, ansatz, alpha, lcu, b, true, cost, grad, beta, delta);
 }

@@ -447,6 +447,7 @@ int decompose_common(dvqls_ctx* ctx, const double* A_in, int n, int nbands, cons
 
 extern "C" int dvqls_pauli_decompose(dvqls_ctx* ctx, const double* A, int n, double tau, int L_max, double* coef,
                                      uint32_t* xmask, uint32_t* zmask, int* L_out, int* L_pre, int* L_post) {
+    DVQLS_NVTX("dvqls_pauli_decompose");
     if (!A) return ctx ? dvqls::set_error(ctx, DVQLS_ERR_INVALID_ARG, "A is NULL") : DVQLS_ERR_INVALID_ARG;
     return decompose_common(ctx, A, n, 0, nullptr, nullptr, tau, L_max, coef, xmask, zmask, L_out, L_pre, L_post);
 }
@@ -454,6 +455,7 @@ extern "C" int dvqls_pauli_decompose(dvqls_ctx* ctx, const double* A, int n, dou
 extern "C" int dvqls_pauli_decompose_banded(dvqls_ctx* ctx, int n, int nbands, const int* offsets,
                                             const double* band_values, double tau, int L_max, double* coef,
                                             uint32_t* xmask, uint32_t* zmask, int* L_out, int* L_pre, int* L_post) {
+    DVQLS_NVTX("dvqls_pauli_decompose_banded");
     return decompose_common(ctx, nullptr, n, nbands, offsets, band_values, tau, L_max, coef, xmask, zmask, L_out,
                             L_pre, L_post);
 }

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cstdarg>
@@ -31,6 +32,19 @@ enum DeviceStatus : int {
 struct GraphCacheEntry;  // defined in terms.cu
 
 }  // namespace dvqls
+
+namespace dvqls {
+// An NVTX range over a scope: names the library's API phases on a profiler's
+// timeline (Nsight Systems and the like); without a profiler attached the
+// calls return at once.
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope&) = delete;
+    NvtxScope& operator=(const NvtxScope&) = delete;
+};
+}  // namespace dvqls
+#define DVQLS_NVTX(name) ::dvqls::NvtxScope dvqls_nvtx_scope_(name)
 
 struct dvqls_ctx {
     int device = 0;

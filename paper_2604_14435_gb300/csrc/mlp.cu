@@ -291,6 +291,7 @@ extern "C" int dvqls_ws_create(dvqls_ctx* ctx, int I, int H, int O, const float*
 }
 
 extern "C" int dvqls_ws_infer(dvqls_ws* w, int batch, const float* feats, float* out) {
+    DVQLS_NVTX("dvqls_ws_infer");
     if (!w) return DVQLS_ERR_INVALID_ARG;
     dvqls_ctx* ctx = w->ctx;
     ctx->err.clear();
@@ -341,6 +342,7 @@ extern "C" int dvqls_ws_grad(dvqls_ws* w, int batch, const float* feats, const f
 
 extern "C" int dvqls_ws_train_step(dvqls_ws* w, int batch, const float* feats, const float* target, const float* mask,
                                    float lr, float* loss) {
+    DVQLS_NVTX("dvqls_ws_train_step");
     if (!w) return DVQLS_ERR_INVALID_ARG;
     w->ctx->err.clear();
     if (!(lr > 0.f)) return set_error(w->ctx, DVQLS_ERR_INVALID_ARG, "lr must be > 0");

@@ -234,6 +234,7 @@ using namespace dvqls;
 
 extern "C" int dvqls_fidelity(dvqls_ctx* ctx, const dvqls_ansatz* an, const double* alpha, const double* xhat,
                               double* F) {
+    DVQLS_NVTX("dvqls_fidelity");
     if (!ctx) return DVQLS_ERR_INVALID_ARG;
     ctx->err.clear();
     if (!an || !alpha || !xhat || !F) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "NULL argument");
@@ -482,6 +483,7 @@ static int cg_multi(dvqls_ctx* ctx, int n, int L, const double2* coef, const uin
 
 extern "C" int dvqls_lcu_solve_batched(dvqls_ctx* ctx, int n, const dvqls_lcu* lcu, int nrhs, const double* b,
                                        double tol, int max_iter, double* x, int* iters, double* rel_resid) {
+    DVQLS_NVTX("dvqls_lcu_solve_batched");
     if (!ctx) return DVQLS_ERR_INVALID_ARG;
     ctx->err.clear();
     if (!lcu || !b || !x || lcu->L < 1 || !lcu->coef || !lcu->xmask || !lcu->zmask)
@@ -552,6 +554,7 @@ extern "C" int dvqls_lcu_solve_batched(dvqls_ctx* ctx, int n, const dvqls_lcu* l
 
 extern "C" int dvqls_lcu_solve(dvqls_ctx* ctx, int n, const dvqls_lcu* lcu, const double* b, double tol, int max_iter,
                                double* x, int* iters, double* rel_resid) {
+    DVQLS_NVTX("dvqls_lcu_solve");
     return dvqls_lcu_solve_batched(ctx, n, lcu, 1, b, tol, max_iter, x, iters, rel_resid);
 }
 
@@ -767,12 +770,14 @@ static int optimize(dvqls_ctx* ctx, int count, const dvqls_instance* inst, const
 
 extern "C" int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* inst, const double* xhat,
                               const dvqls_adam* opt, double* alpha_out, dvqls_opt_result* results) {
+    DVQLS_NVTX("dvqls_optimize");
     return optimize(ctx, count, inst, xhat, opt, nullptr, alpha_out, results);
 }
 
 extern "C" int dvqls_optimize_resume(dvqls_ctx* ctx, int count, const dvqls_instance* inst, const double* xhat,
                                      const dvqls_adam* opt, dvqls_adam_state* state, double* alpha_out,
                                      dvqls_opt_result* results) {
+    DVQLS_NVTX("dvqls_optimize_resume");
     if (ctx && !state) return set_error(ctx, DVQLS_ERR_INVALID_ARG, "NULL optimizer state");
     return optimize(ctx, count, inst, xhat, opt, state, alpha_out, results);
 }

@@ -2981,6 +2981,7 @@ static int run_pass(dvqls_ctx* ctx, const Inst* dtable, const PassShape& ps, con
 int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precision, bool want_grad,
               double* costs, double* grads, double* beta_out, double* delta_out, bool local,
               const ShiftRange* range) {
+    DVQLS_NVTX(range ? "dvqls cost pass (shift range)" : local ? "dvqls local cost pass" : "dvqls cost pass");
     if (!ctx) return DVQLS_ERR_INVALID_ARG;
     if (range && (count != 1 || local || !want_grad || beta_out || delta_out || costs || grads || !range->partials))
         return set_error(ctx, DVQLS_ERR_INVALID_ARG, "a shift-range pass takes one global-cost instance");
@@ -3320,6 +3321,7 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     int ks_use = fixed ? ctx->fixed_split : tuned != ctx->tune.end() ? (tuned->second & 255) : 1;
     int lay_use = fixed ? std::max(0, ctx->fixed_layout) : tuned != ctx->tune.end() ? (tuned->second >> 8) & 3 : 0;
     if (tuning) {
+        DVQLS_NVTX("dvqls autotune");
         // Time full passes per candidate -- the amplitude split, and the state layout of the
         // tensor-core builders (split hi / lo arrays or packed copies) where both fit -- and
         // keep the fastest.
@@ -3382,7 +3384,10 @@ int run_batch(dvqls_ctx* ctx, int count, const dvqls_instance* inst, int precisi
     rc = upload();
     if (!rc && !all_device) rc = pin_release(ctx);
     if (rc) return rc;
-    rc = run_pass(ctx, dtable, ps, tab, ctx->last_table);
+    {
+        DVQLS_NVTX("dvqls pass kernels");
+        rc = run_pass(ctx, dtable, ps, tab, ctx->last_table);
+    }
     if (rc) return rc;
 
     // Results.
