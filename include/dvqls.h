@@ -252,7 +252,8 @@ typedef struct {
  * of the on-chip states (split hi / lo arrays, for every size or only from
  * 2^9 amplitudes, or packed copies) where they fit -- on the real inputs (the
  * fastest of three passes per candidate) and keeps the fastest for the
- * context (an autotuner; that call is synchronous).  The kernel sequence of a
+ * context (an autotuner; that call is synchronous), unless dvqls_set_tuning
+ * fixed the choices.  The kernel sequence of a
  * pass is captured once as a CUDA graph and replayed while the instance
  * table (shapes and pointers) is unchanged; with profiling enabled, or when
  * the caller is capturing the stream, kernels are launched directly. */
