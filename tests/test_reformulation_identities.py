@@ -1,7 +1,8 @@
 """The identities the fast kernels rest on, checked in plain numpy on small
 random cases (CPU): the Walsh-Hadamard form of the real Gram terms (global
-cost, and the local cost's X_j flavours), and the index algebra of the
-four-copy and the split state layouts of the tensor-core tiles."""
+cost, and the local cost's X_j flavours), the index algebra of the
+four-copy and the split state layouts of the tensor-core tiles, and the
+rotation form, CZ-ring sign and transpose layouts of the HBM state passes."""
 import numpy as np
 import pytest
 
@@ -118,3 +119,93 @@ def test_split_copy_layout_index_algebra():
                 src = rb + 8 * (c ^ (xlo >> 3)) + e
                 assert hi[rb | (i ^ xlo)] == H[xlo & 7, src]
                 assert lo[rb | (i ^ xlo)] == Lo[xlo & 7, src]
+
+
+def test_scaled_rotation_form():
+    """Ry(theta) = c [[1, -t], [t, 1]] (t = s / c) when |c| >= |s|, else
+    s [[u, -1], [1, u]] (u = c / s): the HBM passes apply the bracketed
+    matrices (one FMA per amplitude) and the product of the factors at the end;
+    |t|, |u| <= 1 always."""
+    rng = np.random.default_rng(7)
+    for theta in np.concatenate([rng.uniform(-4 * np.pi, 4 * np.pi, 200), [0.0, np.pi, -np.pi, np.pi / 2, 3 * np.pi]]):
+        c, s = np.cos(theta / 2), np.sin(theta / 2)
+        ry = np.array([[c, -s], [s, c]])
+        if abs(c) >= abs(s):
+            r, fac, m = s / c, c, np.array([[1.0, -s / c], [s / c, 1.0]])
+        else:
+            r, fac, m = c / s, s, np.array([[c / s, -1.0], [1.0, c / s]])
+        assert abs(r) <= 1.0
+        assert np.allclose(fac * m, ry, atol=1e-15)
+    # twelve rotations with the factors deferred to the end
+    v = rng.normal(size=(2,))
+    w = v.copy()
+    fac = 1.0
+    for theta in rng.uniform(-np.pi, np.pi, 12):
+        c, s = np.cos(theta / 2), np.sin(theta / 2)
+        v = np.array([[c, -s], [s, c]]) @ v
+        if abs(c) >= abs(s):
+            t = s / c
+            w = np.array([w[0] - t * w[1], w[1] + t * w[0]])
+            fac *= c
+        else:
+            u = c / s
+            w = np.array([u * w[0] - w[1], u * w[1] + w[0]])
+            fac *= s
+    assert np.allclose(fac * w, v, atol=1e-13)
+
+
+def czring_parity(i, n):
+    """Sign bit of the CZ ring on amplitude i: pairs (k, k + 1), k < n - 1, and (n - 1, 0)."""
+    p = popc(i & (i >> 1) & ((1 << (n - 1)) - 1))
+    if n >= 3:
+        p += (i >> (n - 1)) & i & 1
+    return p & 1
+
+
+def test_czring_sign_from_index_parts():
+    """The low-qubit HBM pass forms the CZ-ring sign of i = base | 16 t | r
+    (base: bits 12.., t: bits 4..11, r: bits 0..3) from its parts: the thread's
+    part czring(base | 16 t), the pairs inside r, the pair (3, 4) and the
+    wrap-around pair (n - 1, 0)."""
+    rng = np.random.default_rng(11)
+    for n in (13, 16, 20):
+        for _ in range(3000):
+            base = int(rng.integers(0, 1 << (n - 12))) << 12
+            t, r = int(rng.integers(0, 256)), int(rng.integers(0, 16))
+            p = czring_parity(base | (t << 4), n) ^ (popc(r & (r >> 1)) & 1)
+            if r & 8:
+                p ^= t & 1
+            if r & 1:
+                p ^= (base >> (n - 1)) & 1
+            assert p == czring_parity(base | (t << 4) | r, n)
+
+
+def test_low_pass_transpose_layouts():
+    """The low-qubit HBM pass's chunk of 4096 amplitudes: the three thread
+    layouts (16 consecutive amplitudes per thread; bits 4..7 on the registers;
+    bits 8..11 on the registers) each cover the chunk once, and the padded word
+    e + 4 (e >> 5) + 16 (e >> 8) is one-to-one, keeps 16-byte groups whole, puts
+    the 16-byte stores of eight consecutive threads in eight bank groups, and
+    the 256-strided half-warps of the second layout 16 banks apart."""
+    LOC = 4096
+    pad = lambda e: e + ((e >> 5) << 2) + ((e >> 8) << 4)
+    words = [pad(e) for e in range(LOC)]
+    assert len(set(words)) == LOC
+    A = sorted(16 * t + r for t in range(256) for r in range(16))
+    B = sorted(((t & 15) | ((t >> 4) << 8)) | (r << 4) for t in range(256) for r in range(16))
+    C = sorted(t | (r << 8) for t in range(256) for r in range(16))
+    assert A == B == C == list(range(LOC))
+    for t in range(256):
+        for c in range(4):
+            e = 16 * t + 4 * c
+            assert pad(e) % 4 == 0 and all(pad(e + k) == pad(e) + k for k in range(4))
+    for t0 in range(0, 256, 8):
+        for c in range(4):
+            groups = {(pad(16 * t + 4 * c) // 4) % 8 for t in range(t0, t0 + 8)}
+            assert len(groups) == 8
+    for w in range(8):
+        for r in range(16):
+            lanes = range(32 * w, 32 * w + 32)
+            for layout in (lambda t: ((t & 15) | ((t >> 4) << 8)) | (r << 4), lambda t: t | (r << 8)):
+                banks = [pad(layout(t)) % 32 for t in lanes]
+                assert len(set(banks)) == 32
