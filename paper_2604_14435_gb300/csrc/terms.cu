@@ -1325,14 +1325,15 @@ __device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v) {
 // 2 lo lo(b) in 66, 67 is dropped), lanes 64..127 the hi rows (delta: columns
 // 64 + 66, 65 + 67), Gram columns 0..63 in both.  The first block of an item
 // starts the half's running sums (columns hb + TC_SUM.., hb + TC_DSUM..), later
-// ones add to them with round-to-nearest adds; the last block goes to
-// X[part][row][col] and XD[part][row] in shared memory instead (part: lane
-// half).
-// With `toX` false the last block is not stored: each of its entries meets its
-// column weight c~_m (cB, float4 (Re hi, Re lo, Im hi, Im lo) per column) in
-// the float-float sums (SA, EA) = sum_m Re c~_m g_am and (SB, EB) =
-// sum_m Im c~_m g_am of this thread's row a, and the delta columns are
-// returned in dr.
+// ones add to them with round-to-nearest adds.  The last block (plus the running
+// sums) is either stored to X[part][row][col] and XD[part][row] in shared
+// memory (`toX`: shift-0 items whose beta / delta are returned; part: lane
+// half) or weighted here: each entry meets its column weight c~_m (cB, float4
+// (Re hi, Re lo, Im hi, Im lo) per column) in the sums (SA, EA) =
+// sum_m Re c~_m g_am and (SB, EB) = sum_m Im c~_m g_am of this thread's row a --
+// float-float for the main quadrant, FP32 for the correction quadrant (2 lo hi^T,
+// or a pair's lo rows), SB skipped when every Im c~_m is zero (`imz`) -- and the
+// delta columns are returned in dr.
 __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t hb, uint32_t slot, int q, int ch, int lane, bool first,
                                         bool last, bool off, bool toX, float* X, float2* XD, const float4* cB,
                                         float& SA, float& EA, float& SB, float& EB, float2& dr, bool imz) {
@@ -1405,8 +1406,9 @@ __device__ __forceinline__ void tc_fold(uint32_t tmem, uint32_t hb, uint32_t slo
 // block are rb | (i ^ xlo) with rb = (jb ^ x_l) & ~15: a permutation of 16
 // consecutive amplitudes, whose signs are the parity of z_l & rb times the
 // per-term 16-bit pattern sgn (bit i: parity of z_l & (i ^ xlo)).  psi_hl holds
-// the packed pairs (shared memory; four copies when `copies`), psi_g the FP32
-// state in HBM.
+// the state in shared memory -- the split hi / lo arrays (`split`), four
+// packed copies (`copies`) or one packed copy -- and psi_g the FP32 state in
+// HBM (HBM).
 // Two packed FP16 values times 1/2 (the low parts of an off-diagonal tile
 // pair, stored doubled): exact, but for values that fall below the normal
 // range (|lo| < 2^-14 of the scaled state, an error under 2^-25).
@@ -1417,8 +1419,8 @@ __device__ __forceinline__ uint32_t halve2(uint32_t v) {
 }
 
 // oh, ol: byte offsets tc_off16(rhi, kk0), tc_off16(rlo, kk0) of the two rows
-// (kk0 a multiple of 16, so the second 8 amplitudes sit 128 bytes further).
-// split: psi_hl holds the split arrays (stride sst bytes) instead of packed words.
+// (kk0 a multiple of 16, so the second 8 amplitudes sit 128 bytes further);
+// sst: bytes of one split array.
 template <bool HBM, bool HALVE>
 __device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const float* psi_g, int N, int Na, int jb, int kend,
                                               bool act, uint32_t xl, uint32_t zl, const uint32_t (&sgn)[8],
@@ -1500,17 +1502,19 @@ __device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const floa
 }
 
 // Warp roles: two builder halves of 8 warps (warps 0..7 and 8..15), each
-// running its own items -- its own queue fetches, state copies, masks, two of
-// the ring's stages (slots 2h, 2h + 1), item records and accumulator (TMEM
-// columns 256 h ..) -- so one half's item set-up (fetch, state load, masks)
-// overlaps the other half's stages; warp 16 issues the MMAs of both halves,
-// taking whichever half has a stage ready; warps 17..24 run the epilogue of
-// both, taking whichever accumulator block has finished.  Hand-overs, per half
-// h: a stage by its `full` mbarrier (the half's 256 builder threads arrive
-// after a proxy fence; the stage record -- address of the hi array, first /
-// last stage of an accumulator block, pair flag -- is written first) and back
-// by `empty` (the MMA warp's commit); an accumulator block by accf[h] (commit
-// after its last stage) and back by acce[h] (every epilogue thread, after its
+// running its own items -- its own queue fetches, state layout, masks, two of
+// the ring's stages (slots 2h, 2h + 1), item records and two accumulator slots
+// (TMEM columns 256 h .., its blocks alternating between them) -- so one
+// half's item set-up (fetch, state load, masks) overlaps the other half's
+// stages; warp 16 issues the MMAs of both halves, taking whichever half has a
+// stage ready; warps 17..24 run the epilogue of both, taking whichever
+// accumulator block has finished (both poll with non-blocking test_wait, so a
+// barrier of one half never holds up the other).  Hand-overs, per half h: a
+// stage by its `full` mbarrier (the half's 256 builder threads arrive after a
+// proxy fence; the stage record -- address of the hi array, first / last stage
+// of an accumulator block, pair flag -- is written first) and back by `empty`
+// (the MMA warp's commit); an accumulator block by accf[h][slot] (commit after
+// its last stage) and back by acce[h][slot] (every epilogue thread, after its
 // tensor-memory loads); an item record (instance, shift, amplitude part, tile
 // item, stages, flavour) by itf[h][r] and back by ite[h][r].  Every wait
 // gives up after budget_ns nanoseconds; a thread that has seen the abort flag
