@@ -256,7 +256,9 @@ typedef struct {
  * fixed the choices.  The kernel sequence of a
  * pass is captured once as a CUDA graph and replayed while the instance
  * table (shapes and pointers) is unchanged; with profiling enabled, or when
- * the caller is capturing the stream, kernels are launched directly. */
+ * the caller is capturing the stream, kernels are launched directly.
+ * Errors: as dvqls_cost_grad, for any instance; INVALID_ARG for count < 1
+ * (an empty batch) or inst NULL. */
 int dvqls_cost_grad_batched(dvqls_ctx* ctx, int count, const dvqls_instance* inst,
                             int precision, double* costs, double* grads);
 
@@ -318,8 +320,8 @@ int dvqls_local_cost_grad(dvqls_ctx* ctx, const dvqls_ansatz* ansatz, const doub
                           const dvqls_lcu* lcu, int precision, double* cost, double* grad);
 
 /* Local cost of `count` instances in one pass (inst[i].b is ignored); costs,
- * grads and the asynchronous behaviour as dvqls_cost_grad_batched; grads NULL
- * evaluates the cost only. */
+ * grads, the asynchronous behaviour and the errors as dvqls_cost_grad_batched;
+ * grads NULL evaluates the cost only. */
 int dvqls_local_cost_grad_batched(dvqls_ctx* ctx, int count, const dvqls_instance* inst,
                                   int precision, double* costs, double* grads);
 
@@ -395,7 +397,9 @@ typedef struct {
  * xhat: packed N_i complex128 per instance (the classical solution).
  * alpha_out: packed P_i doubles per instance (final angles).  results: count
  * entries (host memory).  The optimizer allocates its own state for the
- * call and frees it before returning. */
+ * call and frees it before returning.
+ * Errors: INVALID_ARG for count < 1 or a NULL argument, else as
+ * dvqls_cost_grad_batched and dvqls_fidelity. */
 int dvqls_optimize(dvqls_ctx* ctx, int count, const dvqls_instance* inst, const double* xhat,
                    const dvqls_adam* opt, double* alpha_out, dvqls_opt_result* results);
 

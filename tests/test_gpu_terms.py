@@ -205,3 +205,21 @@ def test_invalid_inputs_report_status(dv, ctx):
     # still usable
     ref = oterms.cost_grad(3, 1, np.zeros(6), b, coef, xs, zs)
     check(gpu_cost_grad(dv, ctx, 3, 1, np.zeros(6), b, coef, xs, zs, 0), ref, 0)
+
+
+def test_empty_batch_is_rejected(dv, ctx):
+    """An empty batch is INVALID_ARG for the batched global and local calls and the
+    optimizer; the context stays usable."""
+    empty = dv.make_instances([])
+    costs = torch.zeros(1, device="cuda", dtype=torch.float64)
+    for call in (dv.dvqls_cost_grad_batched, dv.dvqls_local_cost_grad_batched):
+        with pytest.raises(dv.DvqlsError) as e:
+            call(ctx, empty, dv.DVQLS_FP32, costs, None)
+        assert e.value.code == dv.DVQLS_ERR_INVALID_ARG
+    with pytest.raises(dv.DvqlsError) as e:
+        dv.dvqls_optimize(ctx, empty, np.zeros(2), dv.make_adam(max_iter=1), np.zeros(1))
+    assert e.value.code == dv.DVQLS_ERR_INVALID_ARG
+    rng = np.random.default_rng(2)
+    coef, xs, zs, b = random_problem(rng, 3, 4)
+    ref = oterms.cost_grad(3, 1, np.zeros(6), b, coef, xs, zs)
+    check(gpu_cost_grad(dv, ctx, 3, 1, np.zeros(6), b, coef, xs, zs, 0), ref, 0)
