@@ -1419,25 +1419,28 @@ __device__ __forceinline__ uint32_t halve2(uint32_t v) {
 }
 
 // oh, ol: byte offsets tc_off16(rhi, kk0), tc_off16(rlo, kk0) of the two rows
-// (kk0 a multiple of 16, so the second 8 amplitudes sit 128 bytes further);
-// sst: bytes of one split array.
+// (kk0 a multiple of 16, so the second 8 amplitudes sit 128 bytes further).
+// The split arrays' stride is recomputed here from Na rather than passed in:
+// one argument fewer live across the stage loop keeps the kernel's spills
+// at a few bytes under its 72-register cap.
 template <bool HBM, bool HALVE>
 __device__ __forceinline__ void tc_build_half(const uint32_t* psi_hl, const float* psi_g, int N, int Na, int jb, int kend,
                                               bool act, uint32_t xl, uint32_t zl, const uint32_t (&sgn)[8],
                                               unsigned char* dhi, int oh, unsigned char* dlo, int ol, bool copies,
-                                              bool split, int sst) {
+                                              bool split) {
     const uint32_t xhi = xl & ~15u, xlo = xl & 15u & uint32_t(N - 1);
     const int nval = act ? min(16, max(0, kend - jb)) : 0;
     const uint32_t rb = (uint32_t(jb) ^ xhi) & uint32_t(N - 1) & ~15u;
     const uint32_t flip = (__popc(zl & rb) & 1) ? 0x80008000u : 0u;  // the block's common sign
     const uint32_t ra = rb & uint32_t(Na - 1);  // the sources' offset in psi_hl (a block of Na amplitudes)
+    const uint32_t sst = 2u * uint32_t(Na) + 16u;  // bytes of one split array (tc_split_stride)
     uint32_t hw[8], lw[8];  // word j: elements 2j, 2j + 1 of the hi and of the (2) lo row
     if (!HBM && split) {
         // target elements 8c .. 8c + 7 = copy (x_l & 7) at ra + 8 (c ^ bit 3 of x_l): one 16-byte load each
-        const unsigned char* hb = reinterpret_cast<const unsigned char*>(psi_hl) + (xlo & 7u) * uint32_t(sst) + 2u * ra;
+        const unsigned char* hb = reinterpret_cast<const unsigned char*>(psi_hl) + (xlo & 7u) * sst + 2u * ra;
         const uint32_t o0 = (xlo & 8u) ? 16u : 0u;
         const uint4 h0 = *reinterpret_cast<const uint4*>(hb + o0), h1 = *reinterpret_cast<const uint4*>(hb + (o0 ^ 16u));
-        const unsigned char* lb = hb + 8u * uint32_t(sst);
+        const unsigned char* lb = hb + 8u * sst;
         const uint4 l0 = *reinterpret_cast<const uint4*>(lb + o0), l1 = *reinterpret_cast<const uint4*>(lb + (o0 ^ 16u));
         hw[0] = h0.x; hw[1] = h0.y; hw[2] = h0.z; hw[3] = h0.w; hw[4] = h1.x; hw[5] = h1.y; hw[6] = h1.z; hw[7] = h1.w;
         lw[0] = l0.x; lw[1] = l0.y; lw[2] = l0.z; lw[3] = l0.w; lw[4] = l1.x; lw[5] = l1.y; lw[6] = l1.z; lw[7] = l1.w;
@@ -1790,10 +1793,10 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                         const int jb = j0 + hf * (TCK / 2) + sub * 16, dk = hf * TC_OFF_HALF;
                         if (gl)
                             tc_build_half<true, false>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, zhi,
-                                                       ohd + dk, zhi, old + dk, false, false, sst);
+                                                       ohd + dk, zhi, old + dk, false, false);
                         else
                             tc_build_half<false, false>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, zhi,
-                                                        ohd + dk, zhi, old + dk, copies, split, sst);
+                                                        ohd + dk, zhi, old + dk, copies, split);
                     }
                 } else {
                     // pair: the side's array (hi array: first tile, 2 lo array: second),
@@ -1804,10 +1807,10 @@ __global__ void __launch_bounds__(TCT, 1) k_terms_tc(const Inst* __restrict__ in
                         const int jb = j0 + (2 * psp + qb) * 16, dk = qb * TC_KSTEP_BYTES;
                         if (gl)
                             tc_build_half<true, true>(nullptr, psi_g, N, Na, jb, kend, act, xl, zl, sgn, dst, ohp + dk,
-                                                      dst, olp + dk, false, false, sst);
+                                                      dst, olp + dk, false, false);
                         else
                             tc_build_half<false, true>(psi_hl, nullptr, N, Na, jb, kend, act, xl, zl, sgn, dst, ohp + dk,
-                                                       dst, olp + dk, copies, split, sst);
+                                                       dst, olp + dk, copies, split);
                     }
                 }
                 if (brow) asm volatile("cp.async.wait_all;" ::: "memory");
