@@ -33,9 +33,11 @@
  * Memory: every pointer argument may be host memory or device memory of the
  * context's device (told apart with cudaPointerGetAttributes; a context
  * remembers the addresses it found to be host memory and does not ask
- * again).  The caller owns all buffers; the library never frees caller
- * memory and never dereferences a caller pointer after the call returns.  The context owns its workspace,
- * staging buffers and CUDA graphs.  Work is ordered on the context's stream.
+ * again; host addresses lie outside the range the driver reserves for device
+ * allocations).  The caller owns all buffers; the library never frees caller
+ * memory and never dereferences a caller pointer after the call returns.  The
+ * context owns its workspace, staging buffers and CUDA graphs.  Work is
+ * ordered on the context's stream.
  * Unless a function says otherwise it returns after its results are in the
  * caller's buffers.
  *
