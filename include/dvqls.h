@@ -34,7 +34,9 @@
  * context's device (told apart with cudaPointerGetAttributes; a context
  * remembers the addresses it found to be host memory and does not ask
  * again; host addresses lie outside the range the driver reserves for device
- * allocations).  The caller owns all buffers; the library never frees caller
+ * allocations).  Every array argument is dense: its elements follow each
+ * other in memory in the order the function names them (only the address
+ * crosses the ABI).  The caller owns all buffers; the library never frees caller
  * memory and never dereferences a caller pointer after the call returns.  The
  * context owns its workspace, staging buffers and CUDA graphs.  Work is
  * ordered on the context's stream.

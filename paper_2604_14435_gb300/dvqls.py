@@ -149,7 +149,8 @@ def lib():
 
 
 def ptr(a):
-    """Address of a numpy array or torch tensor (None -> NULL)."""
+    """Address of a numpy array or torch tensor (None -> NULL).  Only the
+    address crosses the ABI, so the array must be dense (C-contiguous)."""
     if a is None:
         return None
     if hasattr(a, "data_ptr"):
